@@ -1,0 +1,193 @@
+"""FP64 CPU oracle for convex-polygon IoU and its gradient (DGAL, arXiv:2011.11134).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference arm are the only callers.  The product
+path never imports this package.
+
+The arithmetic lives in ``dgal_oracle.c`` (plain C, IEEE double, no FMA
+contraction); this module builds it with gcc and wraps it with ctypes and
+numpy.  Every function cites the passage of the paper it follows in the C
+file.  Pins against independent results (closed forms, exact rational
+clipping, point sampling, finite differences) are in ``tests/``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dgal_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# status bits (mirror of the C defines)
+ST_BAD_COUNT = 1
+ST_OVERFLOW = 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (portable flags, no contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            # DGAL_ORACLE_SO names another build of dgal_oracle.c (the mutation
+            # test uses it to check that the pins catch planted mistakes).
+            alt = os.environ.get("DGAL_ORACLE_SO")
+            if not alt:
+                build()
+            lib = ctypes.CDLL(alt or _LIB)
+            P = ctypes.c_void_p
+            lib.oracle_iou_paired.argtypes = [ctypes.c_int64, ctypes.c_int, P, P, P, P, P, P, P, P, P]
+            lib.oracle_iou_paired.restype = ctypes.c_int
+            lib.oracle_iou_backward_paired.argtypes = [ctypes.c_int64, ctypes.c_int, P, P, P, P, P, P, P, P, P]
+            lib.oracle_iou_backward_paired.restype = ctypes.c_int
+            lib.oracle_iou_pairwise.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, P, P, P, P, P, P]
+            lib.oracle_iou_pairwise.restype = ctypes.c_int
+            lib.oracle_iou_pair_f64.argtypes = [ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int, P, P, P, P]
+            lib.oracle_iou_pair_f64.restype = ctypes.c_int
+            lib.oracle_iou_backward_pair_f64.argtypes = [ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int,
+                                                         ctypes.c_double, ctypes.c_int, P, P, P]
+            lib.oracle_iou_backward_pair_f64.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _u8(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.uint8)
+
+
+def _chunks(n, threads):
+    threads = max(1, min(threads, n)) if n > 0 else 1
+    step = (n + threads - 1) // threads if n > 0 else 0
+    return [(s, min(n, s + step)) for s in range(0, n, step)] if n > 0 else []
+
+
+def iou_paired(p1, p2, c1=None, c2=None, threads: int = 1):
+    """Forward on paired polygons [n, K, 2] (float32).
+
+    Returns dict(iou=float64[n], nx=uint8[n], xflags=uint8[n, 2K],
+    degen=uint8[n], areas=float64[n, 3] (A_i, A_1, A_2), status=int)."""
+    lib = _load()
+    p1, p2, c1, c2 = _f32(p1), _f32(p2), _u8(c1), _u8(c2)
+    n, K = p1.shape[0], p1.shape[1]
+    out = dict(iou=np.zeros(n, np.float64), nx=np.zeros(n, np.uint8),
+               xflags=np.full((n, 2 * K), 0xFF, np.uint8), degen=np.zeros(n, np.uint8),
+               areas=np.zeros((n, 3), np.float64))
+    status = [0]
+
+    def run(rng):
+        s, e = rng
+        m = e - s
+        st = lib.oracle_iou_paired(
+            m, K, _ptr(p1[s:e]), _ptr(None if c1 is None else c1[s:e]), _ptr(p2[s:e]),
+            _ptr(None if c2 is None else c2[s:e]), _ptr(out["iou"][s:e]), _ptr(out["nx"][s:e]),
+            _ptr(out["xflags"][s:e]), _ptr(out["degen"][s:e]), _ptr(out["areas"][s:e]))
+        status[0] |= st
+
+    _run_parallel(run, _chunks(n, threads))
+    out["status"] = status[0]
+    return out
+
+
+def iou_backward_paired(p1, p2, grad, nx, xflags, c1=None, c2=None, threads: int = 1):
+    """Backward on paired polygons; returns (g1, g2) float64 [n, K, 2]."""
+    lib = _load()
+    p1, p2, c1, c2 = _f32(p1), _f32(p2), _u8(c1), _u8(c2)
+    grad = np.ascontiguousarray(grad, dtype=np.float64)
+    nx = np.ascontiguousarray(nx, dtype=np.uint8)
+    xflags = np.ascontiguousarray(xflags, dtype=np.uint8)
+    n, K = p1.shape[0], p1.shape[1]
+    g1 = np.zeros((n, K, 2), np.float64)
+    g2 = np.zeros((n, K, 2), np.float64)
+
+    def run(rng):
+        s, e = rng
+        lib.oracle_iou_backward_paired(
+            e - s, K, _ptr(p1[s:e]), _ptr(None if c1 is None else c1[s:e]), _ptr(p2[s:e]),
+            _ptr(None if c2 is None else c2[s:e]), _ptr(grad[s:e]), _ptr(nx[s:e]), _ptr(xflags[s:e]),
+            _ptr(g1[s:e]), _ptr(g2[s:e]))
+
+    _run_parallel(run, _chunks(n, threads))
+    return g1, g2
+
+
+def iou_pairwise(a, b, ca=None, cb=None, threads: int = 1):
+    """N x M IoU matrix (float64) and nx (uint8)."""
+    lib = _load()
+    a, b, ca, cb = _f32(a), _f32(b), _u8(ca), _u8(cb)
+    N, M, K = a.shape[0], b.shape[0], a.shape[1]
+    iou = np.zeros((N, M), np.float64)
+    nx = np.zeros((N, M), np.uint8)
+
+    def run(rng):
+        s, e = rng
+        lib.oracle_iou_pairwise(e - s, M, K, _ptr(a[s:e]), _ptr(None if ca is None else ca[s:e]), _ptr(b),
+                                _ptr(cb), _ptr(iou[s:e]), _ptr(nx[s:e]))
+
+    _run_parallel(run, _chunks(N, threads))
+    return iou, nx
+
+
+def iou_pair_f64(p1, p2, K=None):
+    """Single pair in double: returns (iou, ai, a1, a2, nx, codes, degen, status)."""
+    lib = _load()
+    p1 = np.ascontiguousarray(p1, dtype=np.float64)
+    p2 = np.ascontiguousarray(p2, dtype=np.float64)
+    n1, n2 = p1.shape[0], p2.shape[0]
+    K = K or max(n1, n2)
+    out = np.zeros(4, np.float64)
+    nx = ctypes.c_int(0)
+    dg = ctypes.c_int(0)
+    code = np.full(2 * K, 0xFF, np.uint8)
+    st = lib.oracle_iou_pair_f64(K, _ptr(p1), n1, _ptr(p2), n2, _ptr(out), ctypes.byref(nx), _ptr(code),
+                                 ctypes.byref(dg))
+    return out[0], out[1], out[2], out[3], nx.value, code, dg.value, st
+
+
+def iou_backward_pair_f64(p1, p2, grad, nx, code, K=None):
+    """Single pair backward in double; returns (g1 [n1,2], g2 [n2,2])."""
+    lib = _load()
+    p1 = np.ascontiguousarray(p1, dtype=np.float64)
+    p2 = np.ascontiguousarray(p2, dtype=np.float64)
+    n1, n2 = p1.shape[0], p2.shape[0]
+    K = K or max(n1, n2)
+    code = np.ascontiguousarray(code, dtype=np.uint8)
+    g1 = np.zeros((K, 2), np.float64)
+    g2 = np.zeros((K, 2), np.float64)
+    lib.oracle_iou_backward_pair_f64(K, _ptr(p1), n1, _ptr(p2), n2, float(grad), int(nx), _ptr(code), _ptr(g1),
+                                     _ptr(g2))
+    return g1[:n1], g2[:n2]
+
+
+def _run_parallel(fn, ranges):
+    if len(ranges) <= 1:
+        for r in ranges:
+            fn(r)
+        return
+    # ctypes releases the GIL during the foreign call, so threads use all cores.
+    with ThreadPoolExecutor(max_workers=len(ranges)) as ex:
+        list(ex.map(fn, ranges))

@@ -1,0 +1,465 @@
+/*
+ * FP64 CPU oracle for convex-polygon intersection-over-union and its gradient
+ * (DGAL, "Differentiable Computational Geometry for 2D and 3D machine
+ * learning", arXiv:2011.11134).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline / reference arm may load this library.  The
+ * product path (the CUDA library and its Python binding) never calls it and
+ * shares no code with it.
+ *
+ * What it computes (paper Sec. II-B listing, `iou` and `iou_backward`):
+ *   IoU(P1, P2) = A_i / (A_1 + A_2 - A_i), where A_i is the area of the
+ *   intersection polygon P1 ∩ P2 (`intersect`, `area`), A_1, A_2 the areas of
+ *   the inputs; `nx` is the vertex count of the intersection polygon and
+ *   `xflags` records where each of its vertices comes from, so that the
+ *   backward can map dL/dIoU onto the input vertices without re-clipping.
+ * Polygons are convex, counter-clockwise, stored in a fixed-capacity point
+ * array (paper Sec. II-C and Sec. III "(Convex) Polygons"); gradients have
+ * the shape of the polygons (Sec. III, last paragraph).
+ *
+ * The paper leaves the clipping algorithm, the flag encoding, the vertex
+ * order and degenerate handling open.  This file fixes them as follows
+ * (plain definitions, written out without any blocking or fusion):
+ *   - candidates: every P1 vertex inside-or-on P2 (orient >= 0 for all P2
+ *     edges); every P2 vertex inside-or-on P1 that is not bit-identical to a
+ *     P1 vertex; every proper crossing of a P1 edge with a P2 edge
+ *     (D != 0, 0 < t < 1, 0 < u < 1);
+ *   - the intersection polygon is these points in counter-clockwise order
+ *     (sorted by atan2 about their centroid), rotated so the smallest code
+ *     comes first;
+ *   - codes: P1 vertex i -> i, P2 vertex j -> 0x40|j, crossing of P1 edge i
+ *     with P2 edge j -> 0x80|(i<<3)|j, unused slots -> 0xFF;
+ *   - fewer than three candidates -> empty intersection (nx = 0, IoU = 0).
+ * The backward is the shoelace adjoint over the ordered vertices, routed by
+ * code: vertex codes go straight to that vertex, crossing codes go through
+ * the adjoint of P = a + t r, t = cross(c-a, s) / cross(r, s).
+ *
+ * All arithmetic is IEEE double with no contraction (built with
+ * -ffp-contract=off so x86 and Arm give identical results).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAXK 8
+#define ORC_MAXC (2 * ORC_MAXK)
+#define ORC_MAXCAND (ORC_MAXK + ORC_MAXK + ORC_MAXK * ORC_MAXK)
+
+/* Relative threshold of the near-degenerate classifier. */
+#define ORC_DEGEN_REL 1e-5
+
+/* Status bits returned by the per-pair routines. */
+#define ORC_ST_BAD_COUNT 1   /* vertex count outside [3, K] */
+#define ORC_ST_OVERFLOW 2    /* more candidates than K1 + K2 slots */
+
+typedef struct {
+    double x, y;
+} opt;
+
+typedef struct {
+    opt p;
+    uint8_t code;
+    double ang;
+} ocand;
+
+/* Per-pair forward result. */
+typedef struct {
+    double iou, ai, a1, a2;
+    int nx;
+    uint8_t code[ORC_MAXC];
+    int degen;
+    int status;
+} ofwd;
+
+static double cross2(opt a, opt b) { return a.x * b.y - a.y * b.x; }
+static opt sub2(opt a, opt b) { opt r = {a.x - b.x, a.y - b.y}; return r; }
+
+/* orient(a, b, p) > 0 when p is left of the directed line a -> b. */
+static double orient(opt a, opt b, opt p) { return cross2(sub2(b, a), sub2(p, a)); }
+
+/* Shoelace area of an ordered point list (paper Sec. II-B, `area`). */
+static double shoelace(const opt* v, int n)
+{
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += cross2(v[k], v[(k + 1) % n]);
+    return 0.5 * s;
+}
+
+/* Crossing parameters of segment a->b with segment c->d.
+ * r = b - a, s = d - c, q = c - a, D = cross(r, s),
+ * a + t r = c + u s  =>  t = cross(q, s) / D, u = cross(q, r) / D. */
+static int edge_cross(opt a, opt b, opt c, opt d, double* t, double* u, double* D)
+{
+    opt r = sub2(b, a), s = sub2(d, c), q = sub2(c, a);
+    *D = cross2(r, s);
+    if (*D == 0.0) return 0;
+    *t = cross2(q, s) / *D;
+    *u = cross2(q, r) / *D;
+    return (*t > 0.0 && *t < 1.0 && *u > 0.0 && *u < 1.0);
+}
+
+static int bbox_overlap(opt a, opt b, opt c, opt d)
+{
+    double ax0 = fmin(a.x, b.x), ax1 = fmax(a.x, b.x), ay0 = fmin(a.y, b.y), ay1 = fmax(a.y, b.y);
+    double cx0 = fmin(c.x, d.x), cx1 = fmax(c.x, d.x), cy0 = fmin(c.y, d.y), cy1 = fmax(c.y, d.y);
+    return ax0 <= cx1 && cx0 <= ax1 && ay0 <= cy1 && cy0 <= ay1;
+}
+
+/* Near-degenerate classifier.  L is the largest |coordinate| of either
+ * polygon in the frame whose origin is P1's vertex 0.  A pair is flagged when
+ *   (i)   some vertex-vs-edge orientation has |orient| <= 1e-5 L^2, or
+ *   (ii)  some proper crossing has t or u within 1e-5 of 0 or 1, or
+ *   (iii) some pair of edges with overlapping bounding boxes has
+ *         |cross(r, s)| <= 1e-5 |r| |s|. */
+static int classify_degenerate(const opt* P, int n1, const opt* Q, int n2)
+{
+    opt o = P[0];
+    double L = 0.0;
+    for (int i = 0; i < n1; ++i) { L = fmax(L, fabs(P[i].x - o.x)); L = fmax(L, fabs(P[i].y - o.y)); }
+    for (int j = 0; j < n2; ++j) { L = fmax(L, fabs(Q[j].x - o.x)); L = fmax(L, fabs(Q[j].y - o.y)); }
+    if (L == 0.0) return 1;
+    double thr = ORC_DEGEN_REL * L * L;
+    for (int i = 0; i < n1; ++i) {
+        opt a = P[i], b = P[(i + 1) % n1];
+        for (int j = 0; j < n2; ++j) {
+            opt c = Q[j], d = Q[(j + 1) % n2];
+            if (fabs(orient(c, d, a)) <= thr) return 1;
+            if (fabs(orient(a, b, c)) <= thr) return 1;
+            double t, u, D;
+            if (edge_cross(a, b, c, d, &t, &u, &D)) {
+                if (t <= ORC_DEGEN_REL || t >= 1.0 - ORC_DEGEN_REL) return 1;
+                if (u <= ORC_DEGEN_REL || u >= 1.0 - ORC_DEGEN_REL) return 1;
+            }
+            opt r = sub2(b, a), s = sub2(d, c);
+            double nr = sqrt(r.x * r.x + r.y * r.y), ns = sqrt(s.x * s.x + s.y * s.y);
+            if (fabs(cross2(r, s)) <= ORC_DEGEN_REL * nr * ns && bbox_overlap(a, b, c, d)) return 1;
+        }
+    }
+    return 0;
+}
+
+static int inside_or_on(opt p, const opt* poly, int n)
+{
+    for (int j = 0; j < n; ++j)
+        if (orient(poly[j], poly[(j + 1) % n], p) < 0.0) return 0;
+    return 1;
+}
+
+/* Forward on one pair of double polygons (paper Sec. II-B `iou`). */
+static void forward_pair(const opt* P, int n1, const opt* Q, int n2, int K, ofwd* out)
+{
+    int C = 2 * K;
+    memset(out, 0, sizeof(*out));
+    memset(out->code, 0xFF, sizeof(out->code));
+    if (n1 < 3 || n1 > K || n2 < 3 || n2 > K) {
+        out->status = ORC_ST_BAD_COUNT;
+        return;
+    }
+    out->a1 = shoelace(P, n1);
+    out->a2 = shoelace(Q, n2);
+    out->degen = classify_degenerate(P, n1, Q, n2);
+
+    ocand cand[ORC_MAXCAND];
+    int m = 0;
+    /* P1 vertices inside-or-on P2. */
+    for (int i = 0; i < n1; ++i)
+        if (inside_or_on(P[i], Q, n2)) { cand[m].p = P[i]; cand[m].code = (uint8_t)i; ++m; }
+    /* P2 vertices inside-or-on P1, minus exact duplicates of P1 vertices. */
+    for (int j = 0; j < n2; ++j) {
+        int dup = 0;
+        for (int i = 0; i < n1; ++i)
+            if (Q[j].x == P[i].x && Q[j].y == P[i].y) dup = 1;
+        if (!dup && inside_or_on(Q[j], P, n1)) { cand[m].p = Q[j]; cand[m].code = (uint8_t)(0x40 | j); ++m; }
+    }
+    /* Proper edge crossings. */
+    for (int i = 0; i < n1; ++i) {
+        opt a = P[i], b = P[(i + 1) % n1];
+        for (int j = 0; j < n2; ++j) {
+            double t, u, D;
+            if (edge_cross(a, b, Q[j], Q[(j + 1) % n2], &t, &u, &D)) {
+                opt x = {a.x + t * (b.x - a.x), a.y + t * (b.y - a.y)};
+                cand[m].p = x;
+                cand[m].code = (uint8_t)(0x80 | (i << 3) | j);
+                ++m;
+            }
+        }
+    }
+    if (m > C) {
+        out->status = ORC_ST_OVERFLOW;
+        out->degen = 1;
+        return;
+    }
+    if (m < 3) return; /* empty: nx = 0, IoU = 0 */
+
+    /* Counter-clockwise order: sort by angle about the centroid (ties by code). */
+    double cx = 0.0, cy = 0.0;
+    for (int k = 0; k < m; ++k) { cx += cand[k].p.x; cy += cand[k].p.y; }
+    cx /= m;
+    cy /= m;
+    for (int k = 0; k < m; ++k) cand[k].ang = atan2(cand[k].p.y - cy, cand[k].p.x - cx);
+    for (int k = 1; k < m; ++k) {
+        ocand v = cand[k];
+        int l = k - 1;
+        while (l >= 0 && (cand[l].ang > v.ang || (cand[l].ang == v.ang && cand[l].code > v.code))) {
+            cand[l + 1] = cand[l];
+            --l;
+        }
+        cand[l + 1] = v;
+    }
+    /* Rotate so that the smallest code is first. */
+    int s0 = 0;
+    for (int k = 1; k < m; ++k)
+        if (cand[k].code < cand[s0].code) s0 = k;
+    opt w[ORC_MAXC];
+    for (int k = 0; k < m; ++k) {
+        out->code[k] = cand[(s0 + k) % m].code;
+        w[k] = cand[(s0 + k) % m].p;
+    }
+    out->nx = m;
+    out->ai = shoelace(w, m);
+    double U = out->a1 + out->a2 - out->ai;
+    out->iou = (U > 0.0) ? out->ai / U : 0.0;
+}
+
+/* Point named by a code (the backward's reconstruction from saved flags). */
+static int point_of_code(uint8_t code, const opt* P, int n1, const opt* Q, int n2, opt* w)
+{
+    int kind = code >> 6;
+    if (kind == 0) {
+        int i = code & 0x3F;
+        if (i >= n1) return 0;
+        *w = P[i];
+        return 1;
+    }
+    if (kind == 1) {
+        int j = code & 0x3F;
+        if (j >= n2) return 0;
+        *w = Q[j];
+        return 1;
+    }
+    if (kind == 2) {
+        int i = (code >> 3) & 7, j = code & 7;
+        if (i >= n1 || j >= n2) return 0;
+        opt a = P[i], b = P[(i + 1) % n1], c = Q[j], d = Q[(j + 1) % n2];
+        opt r = sub2(b, a), s = sub2(d, c), q = sub2(c, a);
+        double D = cross2(r, s);
+        if (D == 0.0) return 0;
+        double t = cross2(q, s) / D;
+        w->x = a.x + t * r.x;
+        w->y = a.y + t * r.y;
+        return 1;
+    }
+    return 0;
+}
+
+/* Backward on one pair (paper Sec. II-B `iou_grad`): dL/dIoU -> dL/dP1,
+ * dL/dP2 through the recorded (nx, codes).  Gradients are overwritten. */
+static int backward_pair(const opt* P, int n1, const opt* Q, int n2, double g, int nx, const uint8_t* code,
+                         opt* g1, opt* g2)
+{
+    for (int i = 0; i < ORC_MAXK; ++i) { g1[i].x = g1[i].y = 0.0; g2[i].x = g2[i].y = 0.0; }
+    if (n1 < 3 || n2 < 3) return ORC_ST_BAD_COUNT;
+    if (nx < 3) return 0;
+    opt w[ORC_MAXC];
+    for (int k = 0; k < nx; ++k)
+        if (!point_of_code(code[k], P, n1, Q, n2, &w[k])) return ORC_ST_OVERFLOW;
+    double a1 = shoelace(P, n1), a2 = shoelace(Q, n2), ai = shoelace(w, nx);
+    double U = a1 + a2 - ai;
+    if (!(U > 0.0)) return 0;
+    /* IoU = ai / U, U = a1 + a2 - ai. */
+    double gai = g * (a1 + a2) / (U * U);
+    double ga12 = -g * ai / (U * U);
+
+    /* Shoelace adjoint: dA/dw_k = 1/2 (y_{k+1} - y_{k-1}, x_{k-1} - x_{k+1}). */
+    for (int k = 0; k < nx; ++k) {
+        opt wp = w[(k + nx - 1) % nx], wn = w[(k + 1) % nx];
+        opt gw = {0.5 * gai * (wn.y - wp.y), 0.5 * gai * (wp.x - wn.x)};
+        uint8_t c = code[k];
+        int kind = c >> 6;
+        if (kind == 0) {
+            g1[c & 0x3F].x += gw.x;
+            g1[c & 0x3F].y += gw.y;
+        } else if (kind == 1) {
+            g2[c & 0x3F].x += gw.x;
+            g2[c & 0x3F].y += gw.y;
+        } else {
+            int i = (c >> 3) & 7, j = c & 7, i1 = (i + 1) % n1, j1 = (j + 1) % n2;
+            opt a = P[i], b = P[i1], cc = Q[j], d = Q[j1];
+            opt r = sub2(b, a), s = sub2(d, cc), q = sub2(cc, a);
+            double N = cross2(q, s), D = cross2(r, s), t = N / D;
+            /* P = a + t r */
+            double gt = gw.x * r.x + gw.y * r.y;
+            opt gr = {t * gw.x, t * gw.y};
+            opt ga = gw;
+            /* t = N / D */
+            double gN = gt / D, gD = -gt * t / D;
+            /* N = cross(q, s), D = cross(r, s) */
+            opt gq = {gN * s.y, -gN * s.x};
+            opt gs = {gN * (-q.y) + gD * (-r.y), gN * q.x + gD * r.x};
+            gr.x += gD * s.y;
+            gr.y += -gD * s.x;
+            /* q = c - a, r = b - a, s = d - c */
+            ga.x -= gq.x + gr.x;
+            ga.y -= gq.y + gr.y;
+            g1[i].x += ga.x;
+            g1[i].y += ga.y;
+            g1[i1].x += gr.x;
+            g1[i1].y += gr.y;
+            g2[j].x += gq.x - gs.x;
+            g2[j].y += gq.y - gs.y;
+            g2[j1].x += gs.x;
+            g2[j1].y += gs.y;
+        }
+    }
+    /* Areas of the inputs: same shoelace adjoint on P1 and P2. */
+    for (int i = 0; i < n1; ++i) {
+        opt pp = P[(i + n1 - 1) % n1], pn = P[(i + 1) % n1];
+        g1[i].x += 0.5 * ga12 * (pn.y - pp.y);
+        g1[i].y += 0.5 * ga12 * (pp.x - pn.x);
+    }
+    for (int j = 0; j < n2; ++j) {
+        opt qp = Q[(j + n2 - 1) % n2], qn = Q[(j + 1) % n2];
+        g2[j].x += 0.5 * ga12 * (qn.y - qp.y);
+        g2[j].y += 0.5 * ga12 * (qp.x - qn.x);
+    }
+    return 0;
+}
+
+static int load_f32(const float* src, int n, opt* dst)
+{
+    for (int v = 0; v < n; ++v) { dst[v].x = (double)src[2 * v]; dst[v].y = (double)src[2 * v + 1]; }
+    return n;
+}
+
+static int count_of(const uint8_t* c, int64_t k, int K) { return c ? (int)c[k] : K; }
+
+/* ---------------------------------------------------------------- exports */
+
+/* Batch forward on FP32 polygons [n][K][2] (promoted exactly to double).
+ * counts may be NULL (all K).  xflags is [n][2K].  Returns OR of status bits. */
+int oracle_iou_paired(int64_t n, int K, const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2,
+                      double* iou, uint8_t* nx, uint8_t* xflags, uint8_t* degen, double* areas /* [n][3] or NULL */)
+{
+    if (K < 3 || K > ORC_MAXK) return -1;
+    int st = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        opt P[ORC_MAXK], Q[ORC_MAXK];
+        int n1 = count_of(c1, k, K), n2 = count_of(c2, k, K);
+        ofwd f;
+        if (n1 < 3 || n1 > K || n2 < 3 || n2 > K) {
+            memset(&f, 0, sizeof(f));
+            memset(f.code, 0xFF, sizeof(f.code));
+            f.status = ORC_ST_BAD_COUNT;
+        } else {
+            load_f32(p1 + k * 2 * K, n1, P);
+            load_f32(p2 + k * 2 * K, n2, Q);
+            forward_pair(P, n1, Q, n2, K, &f);
+        }
+        st |= f.status;
+        iou[k] = f.iou;
+        if (nx) nx[k] = (uint8_t)f.nx;
+        if (xflags) memcpy(xflags + k * 2 * K, f.code, (size_t)(2 * K));
+        if (degen) degen[k] = (uint8_t)f.degen;
+        if (areas) { areas[3 * k] = f.ai; areas[3 * k + 1] = f.a1; areas[3 * k + 2] = f.a2; }
+    }
+    return st;
+}
+
+/* Batch backward: grad [n], (nx, xflags) as recorded, grads [n][K][2] double. */
+int oracle_iou_backward_paired(int64_t n, int K, const float* p1, const uint8_t* c1, const float* p2,
+                               const uint8_t* c2, const double* grad, const uint8_t* nx, const uint8_t* xflags,
+                               double* g1, double* g2)
+{
+    if (K < 3 || K > ORC_MAXK) return -1;
+    int st = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        opt P[ORC_MAXK], Q[ORC_MAXK], G1[ORC_MAXK], G2[ORC_MAXK];
+        int n1 = count_of(c1, k, K), n2 = count_of(c2, k, K);
+        memset(G1, 0, sizeof(G1));
+        memset(G2, 0, sizeof(G2));
+        if (n1 < 3 || n1 > K || n2 < 3 || n2 > K) {
+            st |= ORC_ST_BAD_COUNT;
+        } else {
+            load_f32(p1 + k * 2 * K, n1, P);
+            load_f32(p2 + k * 2 * K, n2, Q);
+            st |= backward_pair(P, n1, Q, n2, grad[k], nx[k], xflags + k * 2 * K, G1, G2);
+        }
+        for (int v = 0; v < K; ++v) {
+            g1[(k * K + v) * 2] = G1[v].x;
+            g1[(k * K + v) * 2 + 1] = G1[v].y;
+            g2[(k * K + v) * 2] = G2[v].x;
+            g2[(k * K + v) * 2 + 1] = G2[v].y;
+        }
+    }
+    return st;
+}
+
+/* N x M matrix of IoU and nx (row i = a[i], column j = b[j]). */
+int oracle_iou_pairwise(int64_t N, int64_t M, int K, const float* a, const uint8_t* ca, const float* b,
+                        const uint8_t* cb, double* iou, uint8_t* nx)
+{
+    if (K < 3 || K > ORC_MAXK) return -1;
+    int st = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        opt P[ORC_MAXK];
+        int n1 = count_of(ca, i, K);
+        if (n1 >= 3 && n1 <= K) load_f32(a + i * 2 * K, n1, P);
+        for (int64_t j = 0; j < M; ++j) {
+            opt Q[ORC_MAXK];
+            int n2 = count_of(cb, j, K);
+            ofwd f;
+            if (n1 < 3 || n1 > K || n2 < 3 || n2 > K) {
+                memset(&f, 0, sizeof(f));
+                f.status = ORC_ST_BAD_COUNT;
+            } else {
+                load_f32(b + j * 2 * K, n2, Q);
+                forward_pair(P, n1, Q, n2, K, &f);
+            }
+            st |= f.status;
+            iou[i * M + j] = f.iou;
+            if (nx) nx[i * M + j] = (uint8_t)f.nx;
+        }
+    }
+    return st;
+}
+
+/* Double-precision single-pair forward (for finite differences).
+ * out = {iou, ai, a1, a2}; code has 2K slots. */
+int oracle_iou_pair_f64(int K, const double* p1, int n1, const double* p2, int n2, double* out, int* nx,
+                        uint8_t* code, int* degen)
+{
+    if (K < 3 || K > ORC_MAXK) return -1;
+    opt P[ORC_MAXK], Q[ORC_MAXK];
+    for (int v = 0; v < n1 && v < ORC_MAXK; ++v) { P[v].x = p1[2 * v]; P[v].y = p1[2 * v + 1]; }
+    for (int v = 0; v < n2 && v < ORC_MAXK; ++v) { Q[v].x = p2[2 * v]; Q[v].y = p2[2 * v + 1]; }
+    ofwd f;
+    forward_pair(P, n1, Q, n2, K, &f);
+    out[0] = f.iou;
+    out[1] = f.ai;
+    out[2] = f.a1;
+    out[3] = f.a2;
+    *nx = f.nx;
+    memcpy(code, f.code, (size_t)(2 * K));
+    *degen = f.degen;
+    return f.status;
+}
+
+/* Double-precision single-pair backward; g1, g2 are [K][2]. */
+int oracle_iou_backward_pair_f64(int K, const double* p1, int n1, const double* p2, int n2, double grad, int nx,
+                                 const uint8_t* code, double* g1, double* g2)
+{
+    if (K < 3 || K > ORC_MAXK) return -1;
+    opt P[ORC_MAXK], Q[ORC_MAXK], G1[ORC_MAXK], G2[ORC_MAXK];
+    for (int v = 0; v < n1 && v < ORC_MAXK; ++v) { P[v].x = p1[2 * v]; P[v].y = p1[2 * v + 1]; }
+    for (int v = 0; v < n2 && v < ORC_MAXK; ++v) { Q[v].x = p2[2 * v]; Q[v].y = p2[2 * v + 1]; }
+    int st = backward_pair(P, n1, Q, n2, grad, nx, code, G1, G2);
+    for (int v = 0; v < K; ++v) {
+        g1[2 * v] = G1[v].x;
+        g1[2 * v + 1] = G1[v].y;
+        g2[2 * v] = G2[v].x;
+        g2[2 * v + 1] = G2[v].y;
+    }
+    return st;
+}

@@ -1,0 +1,49 @@
+"""Planted mistakes in a copy of the oracle must make the pins fail.
+
+Each mutation is a plausible slip (a flipped sign, a dropped term, a wrong
+index, a transposed operand, a wrong comparison).  The test compiles a
+mutated copy of oracle/dgal_oracle.c into a temporary library, runs the pin
+suite against it in a child process and expects a failure.  The shipped
+oracle is never modified.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "dgal_oracle.c")
+
+MUTATIONS = [
+    ("orient operands transposed", "return cross2(sub2(b, a), sub2(p, a));", "return cross2(sub2(p, a), sub2(b, a));"),
+    ("crossing t operands transposed", "*t = cross2(q, s) / *D;", "*t = cross2(s, q) / *D;"),
+    ("crossing strictness lost", "return (*t > 0.0 && *t < 1.0", "return (*t >= 0.0 && *t <= 1.0"),
+    ("duplicate-vertex rule dropped", "if (!dup && inside_or_on(Q[j], P, n1))", "if (inside_or_on(Q[j], P, n1))"),
+    ("rotation to largest code", "if (cand[k].code < cand[s0].code) s0 = k;", "if (cand[k].code > cand[s0].code) s0 = k;"),
+    ("union without -A_i", "double U = out->a1 + out->a2 - out->ai;", "double U = out->a1 + out->a2;"),
+    ("shoelace adjoint term dropped", "opt gw = {0.5 * gai * (wn.y - wp.y), 0.5 * gai * (wp.x - wn.x)};",
+     "opt gw = {0.5 * gai * (wn.y), 0.5 * gai * (wp.x - wn.x)};"),
+    ("dD sign flipped", "double gN = gt / D, gD = -gt * t / D;", "double gN = gt / D, gD = gt * t / D;"),
+    ("crossing grad to wrong vertex", "g1[i1].x += gr.x;", "g1[i].x += gr.x;"),
+    ("area-gradient sign flipped", "double ga12 = -g * ai / (U * U);", "double ga12 = g * ai / (U * U);"),
+    ("gs term dropped", "opt gs = {gN * (-q.y) + gD * (-r.y), gN * q.x + gD * r.x};",
+     "opt gs = {gN * (-q.y), gN * q.x + gD * r.x};"),
+    ("P2 gradient index shifted", "g2[j1].x += gs.x;", "g2[j].x += gs.x;"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_mutation(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not found: {name}"
+    mut = tmp_path / "oracle_mut.c"
+    mut.write_text(src.replace(old, new))
+    so = tmp_path / "liboracle_mut.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", str(so), str(mut), "-lm"],
+                   check=True)
+    env = dict(os.environ, DGAL_ORACLE_SO=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
