@@ -1,0 +1,350 @@
+"""Benchmark: paired rotated-rectangle IoU forward + backward on GB300.
+
+Workload: the IoU-loss recipe with 1,000,000 pairs of rotated rectangles
+(K = 4, FP32): target center ~ U[0,10]^2, w,h ~ U[0.5,4], theta ~ U[-pi,pi);
+prediction = target + center N(0,0.5)^2, log-size N(0,0.2), angle N(0,0.2);
+dL/dIoU = 1.  One step = forward (IoU, nx, xflags saved) + backward from the
+saved flags, i.e. every step of the hot path.  "Plain" = the same pairs
+through the plain form (FP32 only, no flags saved, backward recomputes).
+
+Prints one JSON line (rank 0).  Options: --gpus N --steps K --warmup W
+[--impl reference] [--n PAIRS].
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IoU pairs/s fwd+bwd, batched vs plain on one GB300, ≤1e-5 err vs FP64 oracle"
+UNIT = "pairs/s"
+WORKLOAD = ("paired rotated-rectangle IoU forward+backward (IoU-loss recipe), 1,000,000 pairs, K=4, FP32, "
+            "flags saved in the forward and consumed by the backward")
+FWD_BYTES = 2 * 32 + 4 + 1 + 8          # read both polygons, write IoU, nx, xflags
+BWD_BYTES = 2 * 32 + 4 + 1 + 8 + 2 * 32  # read polygons, dL/dIoU, nx, xflags; write both gradients
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_run(d, threads):
+    """One fwd+bwd pass of the FP64 oracle over the arrays in d; returns seconds."""
+    import oracle
+
+    t0 = time.perf_counter()
+    o = oracle.iou_paired(d["p1"], d["p2"], threads=threads)
+    oracle.iou_backward_paired(d["p1"], d["p2"], d["grad"].astype(np.float64), o["nx"], o["xflags"],
+                               threads=threads)
+    return time.perf_counter() - t0
+
+
+def reference_arm(args):
+    """The reference arm: the FP64 oracle (plain C, all host cores) on bounded
+    samples of the same workload, timed per step."""
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return
+    from paper_2011_11134_gb300 import workloads as W
+
+    threads = os.cpu_count() or 1
+    sample = args.ref_sample
+    d = W.loss_pairs_1m(seed=0, n=sample)
+    for _ in range(args.warmup):
+        cpu_oracle_run(d, threads)
+    times = [cpu_oracle_run(d, threads) for _ in range(args.steps)]
+    total = sum(times)
+    value = sample * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pairs_per_step": sample, "K": 4,
+                   "note": "each step is a bounded sample of the 1M-pair workload"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"first {sample} pairs of the workload per step, fwd+bwd"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--ref-sample", type=int, default=200_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2011_11134_gb300 as dg
+    from paper_2011_11134_gb300 import workloads as W
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    d = W.loss_pairs_1m(seed=rank, n=n)
+    p1 = torch.from_numpy(d["p1"]).to(dev)
+    p2 = torch.from_numpy(d["p2"]).to(dev)
+    grad = torch.ones(n, device=dev)
+    iou = torch.empty(n, device=dev)
+    nx = torch.empty(n, device=dev, dtype=torch.uint8)
+    xf = torch.empty((n, 8), device=dev, dtype=torch.uint8)
+    g1 = torch.empty_like(p1)
+    g2 = torch.empty_like(p2)
+    flush = torch.empty(256 << 20, device=dev, dtype=torch.uint8)
+    stream = torch.cuda.current_stream(dev)
+    L = dg._lib
+    lib = L.lib()
+    sp = L.stream_ptr(stream)
+    FLAGS = dg.DGAL_FP64_REFINE
+
+    def fwd():
+        st = lib.dgal_iou_paired(L.ptr(p1), None, L.ptr(p2), None, n, 4, L.ptr(iou), L.ptr(nx), L.ptr(xf), None,
+                                 FLAGS, sp)
+        assert st == 0, dg.dgal_last_error()
+
+    def bwd():
+        st = lib.dgal_iou_backward(L.ptr(p1), None, L.ptr(p2), None, n, 4, L.ptr(grad), L.ptr(nx), L.ptr(xf),
+                                   L.ptr(g1), L.ptr(g2), FLAGS, sp)
+        assert st == 0, dg.dgal_last_error()
+
+    def fwd_plain():
+        st = lib.dgal_iou_paired(L.ptr(p1), None, L.ptr(p2), None, n, 4, L.ptr(iou), None, None, None,
+                                 dg.DGAL_PLAIN, sp)
+        assert st == 0, dg.dgal_last_error()
+
+    def bwd_plain():
+        st = lib.dgal_iou_backward(L.ptr(p1), None, L.ptr(p2), None, n, 4, L.ptr(grad), None, None, L.ptr(g1),
+                                   L.ptr(g2), dg.DGAL_PLAIN, sp)
+        assert st == 0, dg.dgal_last_error()
+
+    def timed(steps, f, b):
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        for s in range(steps):
+            flush.fill_(s & 0xFF)  # evict the inputs from L2 between steps (outside the timed events)
+            ev[s][0].record(stream)
+            f()
+            ev[s][1].record(stream)
+            b()
+            ev[s][2].record(stream)
+        torch.cuda.synchronize(dev)
+        fw = [ev[s][0].elapsed_time(ev[s][1]) for s in range(steps)]
+        bw = [ev[s][1].elapsed_time(ev[s][2]) for s in range(steps)]
+        return fw, bw
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        fwd()
+        bwd()
+        fwd_plain()
+        bwd_plain()
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    fw, bw = timed(args.steps, fwd, bwd)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    step_ms = [a + b for a, b in zip(fw, bw)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = n * world * args.steps / (total_ms / 1e3)
+
+    # parity of the timed outputs on a sample (FP64 oracle)
+    err = None
+    if rank == 0:
+        import oracle
+
+        idx = np.random.Generator(np.random.PCG64(7)).choice(n, size=min(n, 20000), replace=False)
+        idx.sort()
+        ref = oracle.iou_paired(d["p1"][idx], d["p2"][idx], threads=os.cpu_count() or 1)
+        r1, r2 = oracle.iou_backward_paired(d["p1"][idx], d["p2"][idx], np.ones(len(idx)), ref["nx"],
+                                            ref["xflags"], threads=os.cpu_count() or 1)
+        gi = iou.cpu().numpy()[idx].astype(np.float64)
+        G = np.concatenate([g1.cpu().numpy()[idx], g2.cpu().numpy()[idx]], 1).astype(np.float64)
+        R = np.concatenate([r1, r2], 1)
+        gen = ref["degen"] == 0
+        rel = np.abs(G - R).max(axis=(1, 2)) / np.maximum(np.abs(R).max(axis=(1, 2)), 1e-6)
+        flags_ok = bool(((xf.cpu().numpy()[idx] == ref["xflags"]).all(1) | ~gen).all())
+        err = {"iou_max_abs": float(np.abs(gi - ref["iou"]).max()), "grad_max_rel": float(rel[gen].max()),
+               "xflags_bit_exact_generic": flags_ok, "sample_pairs": int(len(idx))}
+
+    # plain form on the same pairs
+    pfw, pbw = timed(args.steps, fwd_plain, bwd_plain)
+    plain_ms = sum(pfw) + sum(pbw)
+    plain_value = n * world * args.steps / (plain_ms / 1e3)
+
+    # end to end through the public API with pinned host buffers
+    h_p1 = torch.from_numpy(d["p1"]).pin_memory()
+    h_p2 = torch.from_numpy(d["p2"]).pin_memory()
+    h_grad = torch.ones(n).pin_memory()
+    h_iou = torch.empty(n).pin_memory()
+    h_g1 = torch.empty((n, 4, 2)).pin_memory()
+    h_g2 = torch.empty((n, 4, 2)).pin_memory()
+    for _ in range(2):
+        a1 = h_p1.to(dev, non_blocking=True)
+        a2 = h_p2.to(dev, non_blocking=True)
+        gg = h_grad.to(dev, non_blocking=True)
+        iv, nv, xv, _ = dg.dgal_iou_paired(a1, a2)
+        o1, o2 = dg.dgal_iou_backward(a1, a2, gg, nv, xv)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        a1 = h_p1.to(dev, non_blocking=True)
+        a2 = h_p2.to(dev, non_blocking=True)
+        gg = h_grad.to(dev, non_blocking=True)
+        iv, nv, xv, _ = dg.dgal_iou_paired(a1, a2)
+        o1, o2 = dg.dgal_iou_backward(a1, a2, gg, nv, xv)
+        h_iou.copy_(iv, non_blocking=True)
+        h_g1.copy_(o1, non_blocking=True)
+        h_g2.copy_(o2, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_value = n * world * args.steps / (e2e_ms / 1e3)
+    h2d = 2 * n * 32 + 4 * n
+    d2h = 4 * n + 2 * n * 32
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    peaks = _peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    fw_ms, bw_ms = statistics.mean(fw), statistics.mean(bw)
+    fw_gbs = FWD_BYTES * n / (fw_ms * 1e-3) / 1e9
+    bw_gbs = BWD_BYTES * n / (bw_ms * 1e-3) / 1e9
+    dom = "forward" if fw_ms >= bw_ms else "backward"
+    ach = fw_gbs if dom == "forward" else bw_gbs
+    roofline = {"bound": "hbm", "kernel": f"k_paired_{'fwd' if dom == 'forward' else 'bwd'}<4>", "achieved": ach,
+                "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
+                "per_kernel": {"forward": {"ms": fw_ms, "alg_bytes_per_pair": FWD_BYTES, "GB_s": fw_gbs},
+                               "backward": {"ms": bw_ms, "alg_bytes_per_pair": BWD_BYTES, "GB_s": bw_gbs}}}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        threads = os.cpu_count() or 1
+        sample = min(n, args.ref_sample)
+        ds = {k: v[:sample] for k, v in d.items()}
+        cpu_oracle_run(ds, threads)
+        secs = cpu_oracle_run(ds, threads)
+        cpu = {"value": sample / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first {sample} pairs of the workload, fwd+bwd, FP64 C oracle on all host cores"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pairs_per_gpu": n, "K": 4, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between steps (256 MiB write outside the timed events); inputs 64 MB"},
+        "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": plain_ms / args.steps,
+                  "form": "FP32 only, no saved flags, backward recomputes the clip",
+                  "batched_over_plain": value / plain_value},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "parity": err,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

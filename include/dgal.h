@@ -1,0 +1,185 @@
+/*
+ * dgal.h — C ABI of libdgal, a GB300 (sm_103a) implementation of batched
+ * convex-polygon intersection-over-union and its hand-written backward, after
+ * DGAL ("Differentiable Computational Geometry for 2D and 3D machine
+ * learning", arXiv:2011.11134).
+ *
+ * The calls follow the paper's `iou` / `iou_backward` listing (Sec. II-B):
+ *   iou(p1, p2, nx, xflags)  = area(intersect(p1, p2)) / (area(p1) + area(p2)
+ *                              - area(intersect(p1, p2))), recording nx (vertex
+ *                              count of the intersection) and xflags (where each
+ *                              intersection vertex comes from);
+ *   iou_grad(p1, p2, grad, nx, xflags) -> (grad1, grad2), gradients shaped like
+ *                              the polygons (Sec. III, last paragraph).
+ * They are batched: `paired` (n independent pairs), `pairwise` (an N x M
+ * matrix) and `pairwise_batched` (many ragged N_s x M_s matrices in one launch).
+ *
+ * Data layout (all device memory, caller-owned):
+ *   polygons  float [n][K][2], x/y interleaved, convex, counter-clockwise
+ *             (paper Sec. III: fixed-capacity point array, CCW), K in {4, 8};
+ *             base pointer 16-byte aligned.
+ *   counts    uint8 [n] vertex counts in [3, K], or NULL meaning "all K".
+ *             Padded slots (index >= count) are ignored on input and receive
+ *             zero gradient.
+ *   iou       float [n] (paired) or [N][M] row-major (pairwise).
+ *   nx        uint8 per pair / entry: intersection vertex count, 0 when the
+ *             intersection has fewer than three vertices (then IoU = 0).
+ *   xflags    uint8 [n][2K] (the paper's std::array<uint8_t, 8> for K = 4):
+ *             code of each intersection vertex in counter-clockwise order,
+ *             starting from the smallest code; unused slots are 0xFF.
+ *               P1 vertex i                      -> i
+ *               P2 vertex j                      -> 0x40 | j
+ *               crossing of P1 edge i, P2 edge j -> 0x80 | (i << 3) | j
+ *             (edge i joins vertex i to vertex i+1 mod count).
+ *   degen     uint8 per pair, optional: bit 0 = near-degenerate pair (some
+ *             |orientation| <= 1e-5 L^2, or a crossing within 1e-5 of an edge
+ *             end, or nearly parallel crossing edges; L = largest |coordinate|
+ *             relative to P1's vertex 0); bit 1 = FP64 orientation tests were
+ *             used for this pair.
+ *
+ * Ownership and execution: the library never allocates on these paths and
+ * never synchronises; every call enqueues kernels on `stream` (a
+ * cudaStream_t; NULL = the legacy default stream) and returns.  n = 0 (or
+ * N = 0 / M = 0 / S = 0) returns DGAL_OK without a launch.
+ *
+ * Errors: status codes only.  Arguments are validated on the host before any
+ * launch (NULL required pointers, K not in {4, 8}, negative sizes, polygon or
+ * output pointers not 16-byte aligned).  Problems only the device can see
+ * (a count outside [3, K], a recorded nx or code out of range) set bits of a
+ * per-device status word read by dgal_get_device_status(); kernels never trap.
+ * dgal_last_error() returns a message for the last failing call on the calling
+ * host thread.
+ */
+#ifndef DGAL_H
+#define DGAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DGAL_OK = 0,
+    DGAL_ERR_INVALID_ARG = 1,
+    DGAL_ERR_UNSUPPORTED_K = 2,
+    DGAL_ERR_ALIGNMENT = 3,
+    DGAL_ERR_CUDA = 4,
+    DGAL_ERR_WORKSPACE = 5,
+    DGAL_ERR_DEVICE_STATUS = 6
+} dgal_status;
+
+/* Option bits for `flags`. */
+#define DGAL_FP64_REFINE 0x1u /* near-degenerate pairs: orientation tests and crossing
+                                 parameters in FP64 from the unrounded inputs */
+#define DGAL_PLAIN 0x2u       /* the plain form: FP32 only, no refinement, one
+                                 straightforward launch; the backward recomputes the clip */
+
+/* Device status bits (dgal_get_device_status). */
+#define DGAL_DEV_BAD_COUNT 0x1u /* a vertex count outside [3, K] (pair treated as empty) */
+#define DGAL_DEV_OVERFLOW 0x2u  /* more than 2K intersection candidates (pair treated as empty) */
+#define DGAL_DEV_BAD_FLAGS 0x4u /* backward: nx > 2K or a code naming a missing vertex/edge */
+
+/*
+ * Paired IoU forward (paper Sec. II-B, `iou`): for k < n,
+ *   iou[k] = A_i / (A_1 + A_2 - A_i) of p1[k], p2[k],
+ * with nx[k], xflags[k][0..2K) and degen[k] recorded when the pointers are
+ * non-NULL (nx and xflags must be both NULL or both set).
+ * p1, p2: float [n][K][2]; c1, c2: uint8 [n] or NULL; iou: float [n] (required).
+ */
+dgal_status dgal_iou_paired(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                            int K, float* iou, uint8_t* nx, uint8_t* xflags, uint8_t* degen, uint32_t flags,
+                            void* stream);
+
+/*
+ * Paired IoU backward (paper Sec. II-B, `iou_backward` / `iou_grad`): maps
+ * grad_iou[k] = dL/dIoU onto both polygons' vertices through the recorded
+ * intersection (nx, xflags).  grad_p1, grad_p2: float [n][K][2], overwritten
+ * (padded slots set to 0).  When nx and xflags are both NULL (or DGAL_PLAIN is
+ * set) the clip is recomputed from p1, p2 instead of read.
+ */
+dgal_status dgal_iou_backward(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                              int K, const float* grad_iou, const uint8_t* nx, const uint8_t* xflags,
+                              float* grad_p1, float* grad_p2, uint32_t flags, void* stream);
+
+/*
+ * Pairwise IoU matrix (the `iou` operation over all N x M pairs):
+ *   iou[i*M + j] = IoU(a[i], b[j]), nx[i*M + j] likewise (nx may be NULL).
+ * a: float [N][K][2], b: float [M][K][2]; ca, cb counts or NULL.
+ */
+dgal_status dgal_iou_pairwise(const float* a, const uint8_t* ca, int64_t N, const float* b, const uint8_t* cb,
+                              int64_t M, int K, float* iou, uint8_t* nx, uint32_t flags, void* stream);
+
+/*
+ * Ragged batch of S pairwise matrices in one persistent launch.
+ * Scene s compares a[a_off[s] .. a_off[s+1]) with b[b_off[s] .. b_off[s+1]);
+ * its N_s x M_s matrix is written row-major at iou + out_off[s] (and nx +
+ * out_off[s]); out_off[s+1] - out_off[s] must equal N_s * M_s.
+ * a_off, b_off, out_off: device int64 [S + 1], non-decreasing, a_off[0] =
+ * b_off[0] = out_off[0] = 0 (read only on the device, so the call can be
+ * captured in a CUDA graph).  workspace: device memory of at least
+ * dgal_batched_workspace_bytes(S, K) bytes, 16-byte aligned, owned by the
+ * caller; its contents on entry are ignored (the call re-initialises it).
+ * Calls that share a workspace must not overlap in time.
+ */
+size_t dgal_batched_workspace_bytes(int S, int K);
+dgal_status dgal_iou_pairwise_batched(int S, const int64_t* a_off, const int64_t* b_off, const int64_t* out_off,
+                                      const float* a, const uint8_t* ca, const float* b, const uint8_t* cb, int K,
+                                      float* iou, uint8_t* nx, void* workspace, size_t ws_bytes, uint32_t flags,
+                                      void* stream);
+
+/*
+ * The plain form of the ragged batch: one pairwise launch per scene with
+ * host-side offsets (a_off_h, b_off_h, out_off_h are HOST int64 [S + 1]).
+ */
+dgal_status dgal_iou_pairwise_per_scene(int S, const int64_t* a_off_h, const int64_t* b_off_h,
+                                        const int64_t* out_off_h, const float* a, const uint8_t* ca, const float* b,
+                                        const uint8_t* cb, int K, float* iou, uint8_t* nx, uint32_t flags,
+                                        void* stream);
+
+/*
+ * CUDA-graph form of dgal_iou_pairwise_batched: captures the call (with these
+ * exact pointers and S) into an executable graph; dgal_graph_launch replays
+ * it on `stream`.  Inputs may be rewritten in place between replays.
+ * *graph receives an opaque handle; free it with dgal_graph_destroy.
+ */
+typedef struct dgal_graph_s* dgal_graph;
+dgal_status dgal_batched_graph_create(dgal_graph* graph, int S, const int64_t* a_off, const int64_t* b_off,
+                                      const int64_t* out_off, const float* a, const uint8_t* ca, const float* b,
+                                      const uint8_t* cb, int K, float* iou, uint8_t* nx, void* workspace,
+                                      size_t ws_bytes, uint32_t flags);
+dgal_status dgal_graph_launch(dgal_graph graph, void* stream);
+dgal_status dgal_graph_destroy(dgal_graph graph);
+
+/*
+ * Autotuner for the ragged batch: times candidate launch shapes (entries per
+ * tile, threads per block, resident blocks per SM) on a synthetic ragged
+ * problem generated on the current device and keeps the fastest per (device,
+ * K).  cache_path (or, when NULL, the environment variable DGAL_TUNE_CACHE)
+ * names a JSON file that is read first and rewritten with the result; NULL and
+ * no variable means an in-memory cache only.  config_class is reserved (0).
+ * This call allocates device memory and synchronises: call it before timing
+ * or capturing, never inside a capture.
+ */
+dgal_status dgal_autotune(int K, int config_class, const char* cache_path);
+
+/* The launch shape currently used by dgal_iou_pairwise_batched for K:
+ * out[0] = entries per tile, out[1] = threads per block, out[2] = blocks per SM. */
+dgal_status dgal_get_batched_config(int K, int32_t out[3]);
+
+/* Reads (and, if clear != 0, resets) the current device's status word;
+ * synchronises the device. */
+dgal_status dgal_get_device_status(uint32_t* out, int clear);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* dgal_last_error(void);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int dgal_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGAL_H */

@@ -1,0 +1,270 @@
+"""GB300 (sm_103a) convex-polygon IoU with a hand-written backward (DGAL, arXiv:2011.11134).
+
+Python binding of libdgal's C ABI (include/dgal.h), with the same call names:
+
+    dgal_iou_paired            paper Sec. II-B `iou`: IoU, nx, xflags per pair
+    dgal_iou_backward          paper Sec. II-B `iou_backward`: dL/dIoU -> vertex grads
+    dgal_iou_pairwise          N x M IoU matrix
+    dgal_iou_pairwise_batched  ragged scenes in one persistent launch
+    dgal_iou_pairwise_per_scene  the plain one-launch-per-scene form
+    BatchedGraph               the ragged batch captured in a CUDA graph
+    dgal_autotune              launch-shape tuner for the ragged batch
+    dgal_get_device_status     device-side error bits
+
+and ``IoU`` / ``iou``: a ``torch.autograd.Function`` whose backward consumes
+the recorded (nx, xflags) or, in recompute mode, re-runs the clip.
+
+Polygons are float32 CUDA tensors [n, K, 2] (K = 4 or 8, counter-clockwise,
+convex) with optional uint8 vertex counts [n].  Everything runs in the
+library's kernels on the current CUDA stream; this module only checks and
+marshals arguments.  ``workloads`` (seeded inputs) imports without CUDA.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import (DGAL_DEV_BAD_COUNT, DGAL_DEV_BAD_FLAGS, DGAL_DEV_BAD_OFFSETS, DGAL_DEV_OVERFLOW,
+                   DGAL_FP64_REFINE, DGAL_PLAIN, DgalError)
+
+__all__ = [
+    "dgal_iou_paired", "dgal_iou_backward", "dgal_iou_pairwise", "dgal_iou_pairwise_batched",
+    "dgal_iou_pairwise_per_scene", "dgal_batched_workspace_bytes", "BatchedGraph", "dgal_autotune",
+    "dgal_get_batched_config", "dgal_get_device_status", "dgal_last_error", "dgal_version", "IoU", "iou",
+    "DGAL_FP64_REFINE", "DGAL_PLAIN", "DGAL_DEV_BAD_COUNT", "DGAL_DEV_OVERFLOW", "DGAL_DEV_BAD_FLAGS",
+    "DGAL_DEV_BAD_OFFSETS", "DgalError",
+]
+
+
+def _poly(t, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or t.dim() != 3 or t.shape[2] != 2 or t.shape[1] not in (4, 8):
+        raise ValueError(f"{name} must be float32 [n, K, 2] with K in (4, 8), got {tuple(t.shape)} {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _counts(c, n, name, device):
+    if c is None:
+        return None
+    if not isinstance(c, torch.Tensor) or c.dtype != torch.uint8 or c.shape != (n,) or not c.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous uint8 tensor of shape ({n},)")
+    if c.device != device:
+        raise ValueError(f"{name} must be on {device}")
+    return c
+
+
+def dgal_iou_paired(p1, p2, c1=None, c2=None, save_flags=True, with_degen=False, flags=DGAL_FP64_REFINE,
+                    stream=None):
+    """IoU of paired polygons; returns (iou [n], nx [n] | None, xflags [n, 2K] | None, degen [n] | None)."""
+    _poly(p1, "p1")
+    _poly(p2, "p2")
+    if p1.shape != p2.shape or p1.device != p2.device:
+        raise ValueError("p1 and p2 must have the same shape and device")
+    n, K = p1.shape[0], p1.shape[1]
+    c1 = _counts(c1, n, "c1", p1.device)
+    c2 = _counts(c2, n, "c2", p1.device)
+    iou = torch.empty(n, device=p1.device, dtype=torch.float32)
+    nx = torch.empty(n, device=p1.device, dtype=torch.uint8) if save_flags else None
+    xflags = torch.empty((n, 2 * K), device=p1.device, dtype=torch.uint8) if save_flags else None
+    degen = torch.empty(n, device=p1.device, dtype=torch.uint8) if with_degen else None
+    _lib.call("dgal_iou_paired", _lib.ptr(p1), _lib.ptr(c1), _lib.ptr(p2), _lib.ptr(c2), n, K, _lib.ptr(iou),
+              _lib.ptr(nx), _lib.ptr(xflags), _lib.ptr(degen), flags, _lib.stream_ptr(stream))
+    return iou, nx, xflags, degen
+
+
+def dgal_iou_backward(p1, p2, grad_iou, nx=None, xflags=None, c1=None, c2=None, flags=DGAL_FP64_REFINE,
+                      stream=None):
+    """dL/dIoU [n] -> (dL/dp1, dL/dp2), each [n, K, 2].  nx/xflags None -> recompute the clip."""
+    _poly(p1, "p1")
+    _poly(p2, "p2")
+    n, K = p1.shape[0], p1.shape[1]
+    if grad_iou.dtype != torch.float32 or grad_iou.shape != (n,) or not grad_iou.is_cuda:
+        raise ValueError("grad_iou must be a CUDA float32 tensor of shape (n,)")
+    grad_iou = grad_iou.contiguous()
+    c1 = _counts(c1, n, "c1", p1.device)
+    c2 = _counts(c2, n, "c2", p1.device)
+    if (nx is None) != (xflags is None):
+        raise ValueError("nx and xflags must be given together")
+    if nx is not None and (nx.shape != (n,) or xflags.shape != (n, 2 * K)):
+        raise ValueError("nx must be [n] and xflags [n, 2K]")
+    g1 = torch.empty_like(p1)
+    g2 = torch.empty_like(p2)
+    _lib.call("dgal_iou_backward", _lib.ptr(p1), _lib.ptr(c1), _lib.ptr(p2), _lib.ptr(c2), n, K,
+              _lib.ptr(grad_iou), _lib.ptr(nx), _lib.ptr(xflags), _lib.ptr(g1), _lib.ptr(g2), flags,
+              _lib.stream_ptr(stream))
+    return g1, g2
+
+
+def dgal_iou_pairwise(a, b, ca=None, cb=None, with_nx=True, flags=DGAL_FP64_REFINE, stream=None, out=None):
+    """N x M IoU matrix; returns (iou [N, M], nx [N, M] | None)."""
+    _poly(a, "a")
+    _poly(b, "b")
+    N, M, K = a.shape[0], b.shape[0], a.shape[1]
+    if b.shape[1] != K:
+        raise ValueError("a and b must have the same K")
+    ca = _counts(ca, N, "ca", a.device)
+    cb = _counts(cb, M, "cb", a.device)
+    if out is None:
+        iou = torch.empty((N, M), device=a.device, dtype=torch.float32)
+        nx = torch.empty((N, M), device=a.device, dtype=torch.uint8) if with_nx else None
+    else:
+        iou, nx = out
+    _lib.call("dgal_iou_pairwise", _lib.ptr(a), _lib.ptr(ca), N, _lib.ptr(b), _lib.ptr(cb), M, K, _lib.ptr(iou),
+              _lib.ptr(nx), flags, _lib.stream_ptr(stream))
+    return iou, nx
+
+
+def dgal_batched_workspace_bytes(S, K=4):
+    return int(_lib.lib().dgal_batched_workspace_bytes(S, K))
+
+
+def _offsets(t, S, name):
+    if t.dtype != torch.int64 or t.shape != (S + 1,) or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA int64 tensor of shape ({S + 1},)")
+    return t
+
+
+def dgal_iou_pairwise_batched(a, b, a_off, b_off, out_off, total=None, ca=None, cb=None, workspace=None,
+                              with_nx=True, flags=DGAL_FP64_REFINE, stream=None, out=None):
+    """Ragged batch (device offsets); returns (iou packed [total], nx packed | None).
+
+    ``total`` = out_off[S] (pass it to avoid a device->host read)."""
+    _poly(a, "a")
+    _poly(b, "b")
+    S = a_off.shape[0] - 1
+    K = a.shape[1]
+    for t, nm in ((a_off, "a_off"), (b_off, "b_off"), (out_off, "out_off")):
+        _offsets(t, S, nm)
+    if workspace is None:
+        workspace = torch.empty(dgal_batched_workspace_bytes(S, K), device=a.device, dtype=torch.uint8)
+    if out is None:
+        if total is None:
+            total = int(out_off[-1].item())
+        iou = torch.empty(total, device=a.device, dtype=torch.float32)
+        nx = torch.empty(total, device=a.device, dtype=torch.uint8) if with_nx else None
+    else:
+        iou, nx = out
+    _lib.call("dgal_iou_pairwise_batched", S, _lib.ptr(a_off), _lib.ptr(b_off), _lib.ptr(out_off), _lib.ptr(a),
+              _lib.ptr(ca), _lib.ptr(b), _lib.ptr(cb), K, _lib.ptr(iou), _lib.ptr(nx), _lib.ptr(workspace),
+              workspace.numel(), flags, _lib.stream_ptr(stream))
+    return iou, nx
+
+
+def dgal_iou_pairwise_per_scene(a, b, a_off_h, b_off_h, out_off_h, ca=None, cb=None, with_nx=True,
+                                flags=DGAL_FP64_REFINE | DGAL_PLAIN, stream=None, out=None):
+    """The plain form: one pairwise launch per scene (host int64 offsets, numpy or CPU tensor)."""
+    import numpy as np
+
+    _poly(a, "a")
+    _poly(b, "b")
+    ao = np.ascontiguousarray(a_off_h, dtype=np.int64)
+    bo = np.ascontiguousarray(b_off_h, dtype=np.int64)
+    oo = np.ascontiguousarray(out_off_h, dtype=np.int64)
+    S = ao.shape[0] - 1
+    K = a.shape[1]
+    if out is None:
+        iou = torch.empty(int(oo[-1]), device=a.device, dtype=torch.float32)
+        nx = torch.empty(int(oo[-1]), device=a.device, dtype=torch.uint8) if with_nx else None
+    else:
+        iou, nx = out
+    _lib.call("dgal_iou_pairwise_per_scene", S, ao.ctypes.data_as(ctypes.c_void_p),
+              bo.ctypes.data_as(ctypes.c_void_p), oo.ctypes.data_as(ctypes.c_void_p), _lib.ptr(a), _lib.ptr(ca),
+              _lib.ptr(b), _lib.ptr(cb), K, _lib.ptr(iou), _lib.ptr(nx), flags, _lib.stream_ptr(stream))
+    return iou, nx
+
+
+class BatchedGraph:
+    """The ragged batch captured once into a CUDA graph; ``launch()`` replays it.
+
+    The graph keeps the pointers of the tensors given here: rewrite them in
+    place between replays, keep them alive while the graph exists."""
+
+    def __init__(self, a, b, a_off, b_off, out_off, total, ca=None, cb=None, with_nx=True,
+                 flags=DGAL_FP64_REFINE):
+        _poly(a, "a")
+        _poly(b, "b")
+        S = a_off.shape[0] - 1
+        K = a.shape[1]
+        for t, nm in ((a_off, "a_off"), (b_off, "b_off"), (out_off, "out_off")):
+            _offsets(t, S, nm)
+        self.workspace = torch.empty(dgal_batched_workspace_bytes(S, K), device=a.device, dtype=torch.uint8)
+        self.iou = torch.empty(total, device=a.device, dtype=torch.float32)
+        self.nx = torch.empty(total, device=a.device, dtype=torch.uint8) if with_nx else None
+        self._keep = (a, b, a_off, b_off, out_off, ca, cb)
+        h = ctypes.c_void_p()
+        _lib.call("dgal_batched_graph_create", ctypes.byref(h), S, _lib.ptr(a_off), _lib.ptr(b_off),
+                  _lib.ptr(out_off), _lib.ptr(a), _lib.ptr(ca), _lib.ptr(b), _lib.ptr(cb), K, _lib.ptr(self.iou),
+                  _lib.ptr(self.nx), _lib.ptr(self.workspace), self.workspace.numel(), flags)
+        self._h = h
+
+    def launch(self, stream=None):
+        _lib.call("dgal_graph_launch", self._h, _lib.stream_ptr(stream))
+        return self.iou, self.nx
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.lib().dgal_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dgal_autotune(K=4, cache_path=None):
+    _lib.call("dgal_autotune", K, 0, None if cache_path is None else str(cache_path).encode())
+    return dgal_get_batched_config(K)
+
+
+def dgal_get_batched_config(K=4):
+    out = (ctypes.c_int32 * 3)()
+    _lib.call("dgal_get_batched_config", K, out)
+    return dict(tile=out[0], threads=out[1], blocks_per_sm=out[2])
+
+
+def dgal_get_device_status(clear=False):
+    v = ctypes.c_uint32(0)
+    _lib.call("dgal_get_device_status", ctypes.byref(v), 1 if clear else 0)
+    return v.value
+
+
+def dgal_last_error():
+    return _lib.lib().dgal_last_error().decode(errors="replace")
+
+
+def dgal_version():
+    return int(_lib.lib().dgal_version())
+
+
+class IoU(torch.autograd.Function):
+    """IoU of paired convex polygons with the library's hand-written backward.
+
+    Saved-flag mode records (nx, xflags) in the forward (K + 1... 2K + 1 bytes
+    per pair) and the backward reads them; recompute mode stores nothing and
+    the backward re-runs the clip."""
+
+    @staticmethod
+    def forward(ctx, p1, p2, c1=None, c2=None, recompute=False, flags=DGAL_FP64_REFINE):
+        p1c, p2c = p1.contiguous(), p2.contiguous()
+        iou_v, nx, xflags, _ = dgal_iou_paired(p1c, p2c, c1, c2, save_flags=not recompute, flags=flags)
+        ctx.save_for_backward(p1c, p2c, nx, xflags, c1, c2)
+        ctx.flags = flags
+        return iou_v
+
+    @staticmethod
+    def backward(ctx, grad):
+        p1, p2, nx, xflags, c1, c2 = ctx.saved_tensors
+        g1, g2 = dgal_iou_backward(p1, p2, grad.contiguous().float(), nx, xflags, c1, c2, flags=ctx.flags)
+        return g1, g2, None, None, None, None
+
+
+def iou(p1, p2, c1=None, c2=None, recompute=False, flags=DGAL_FP64_REFINE):
+    """Differentiable paired IoU (see ``IoU``)."""
+    return IoU.apply(p1, p2, c1, c2, recompute, flags)

@@ -1,0 +1,512 @@
+// C ABI of libdgal (declared in include/dgal.h): argument validation,
+// per-thread error messages, the device status word, CUDA-graph capture of
+// the ragged batch, and the launch-shape autotuner with its JSON cache.
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "dgal_geom.cuh"
+#include "dgal_internal.h"
+
+namespace dgal {
+
+static thread_local std::string t_last_error;
+
+dgal_status fail(dgal_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_last_error = buf;
+    return st;
+}
+
+dgal_status check_launch(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(DGAL_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return DGAL_OK;
+}
+
+namespace {
+std::mutex g_mu;
+std::map<int, int> g_sms;
+std::map<int, uint32_t*> g_status_ptr;
+std::map<std::pair<int, int>, BatchedConfig> g_cfg; // (device, K)
+
+int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+} // namespace
+
+int sm_count() {
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_sms.find(d);
+    if (it != g_sms.end()) return it->second;
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
+    if (n <= 0) n = 1;
+    g_sms[d] = n;
+    return n;
+}
+
+uint32_t* device_status_ptr() {
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_status_ptr.find(d);
+    if (it != g_status_ptr.end()) return it->second;
+    uint32_t* p = status_symbol_address();
+    g_status_ptr[d] = p;
+    return p;
+}
+
+BatchedConfig batched_config(int K) {
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cfg.find({d, K});
+    if (it != g_cfg.end()) return it->second;
+    return BatchedConfig{1024, 128, 8};
+}
+
+void set_batched_config(int K, BatchedConfig c) {
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_cfg[{d, K}] = c;
+}
+
+} // namespace dgal
+
+using namespace dgal;
+
+namespace {
+
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+dgal_status check_K(int K) {
+    if (K != 4 && K != 8) return fail(DGAL_ERR_UNSUPPORTED_K, "K = %d is not supported (K must be 4 or 8)", K);
+    return DGAL_OK;
+}
+
+dgal_status check_poly_ptr(const void* p, const char* name) {
+    if (!p) return fail(DGAL_ERR_INVALID_ARG, "%s is NULL", name);
+    if (!aligned(p, 16)) return fail(DGAL_ERR_ALIGNMENT, "%s is not 16-byte aligned", name);
+    return DGAL_OK;
+}
+
+#define DGAL_TRY(expr)                  \
+    do {                                \
+        dgal_status _st = (expr);       \
+        if (_st != DGAL_OK) return _st; \
+    } while (0)
+
+} // namespace
+
+extern "C" {
+
+int dgal_version(void) { return 100; }
+
+const char* dgal_last_error(void) { return t_last_error.c_str(); }
+
+dgal_status dgal_iou_paired(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                            int K, float* iou, uint8_t* nx, uint8_t* xflags, uint8_t* degen, uint32_t flags,
+                            void* stream) {
+    t_last_error.clear();
+    DGAL_TRY(check_K(K));
+    if (n < 0) return fail(DGAL_ERR_INVALID_ARG, "n = %lld is negative", (long long)n);
+    if (n == 0) return DGAL_OK;
+    DGAL_TRY(check_poly_ptr(p1, "p1"));
+    DGAL_TRY(check_poly_ptr(p2, "p2"));
+    if (!iou) return fail(DGAL_ERR_INVALID_ARG, "iou is NULL");
+    if (!aligned(iou, 4)) return fail(DGAL_ERR_ALIGNMENT, "iou is not 4-byte aligned");
+    if ((nx == nullptr) != (xflags == nullptr))
+        return fail(DGAL_ERR_INVALID_ARG, "nx and xflags must be both NULL or both set");
+    if (xflags && !aligned(xflags, K == 4 ? 8 : 16))
+        return fail(DGAL_ERR_ALIGNMENT, "xflags is not %d-byte aligned", K == 4 ? 8 : 16);
+    return launch_paired_fwd(p1, c1, p2, c2, n, K, iou, nx, xflags, degen, flags, (cudaStream_t)stream);
+}
+
+dgal_status dgal_iou_backward(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                              int K, const float* grad_iou, const uint8_t* nx, const uint8_t* xflags,
+                              float* grad_p1, float* grad_p2, uint32_t flags, void* stream) {
+    t_last_error.clear();
+    DGAL_TRY(check_K(K));
+    if (n < 0) return fail(DGAL_ERR_INVALID_ARG, "n = %lld is negative", (long long)n);
+    if (n == 0) return DGAL_OK;
+    DGAL_TRY(check_poly_ptr(p1, "p1"));
+    DGAL_TRY(check_poly_ptr(p2, "p2"));
+    DGAL_TRY(check_poly_ptr(grad_p1, "grad_p1"));
+    DGAL_TRY(check_poly_ptr(grad_p2, "grad_p2"));
+    if (!grad_iou) return fail(DGAL_ERR_INVALID_ARG, "grad_iou is NULL");
+    if (!aligned(grad_iou, 4)) return fail(DGAL_ERR_ALIGNMENT, "grad_iou is not 4-byte aligned");
+    if ((nx == nullptr) != (xflags == nullptr))
+        return fail(DGAL_ERR_INVALID_ARG, "nx and xflags must be both NULL or both set");
+    if (xflags && !aligned(xflags, K == 4 ? 8 : 16))
+        return fail(DGAL_ERR_ALIGNMENT, "xflags is not %d-byte aligned", K == 4 ? 8 : 16);
+    return launch_paired_bwd(p1, c1, p2, c2, n, K, grad_iou, nx, xflags, grad_p1, grad_p2, flags,
+                             (cudaStream_t)stream);
+}
+
+dgal_status dgal_iou_pairwise(const float* a, const uint8_t* ca, int64_t N, const float* b, const uint8_t* cb,
+                              int64_t M, int K, float* iou, uint8_t* nx, uint32_t flags, void* stream) {
+    t_last_error.clear();
+    DGAL_TRY(check_K(K));
+    if (N < 0 || M < 0) return fail(DGAL_ERR_INVALID_ARG, "negative size N = %lld, M = %lld", (long long)N, (long long)M);
+    if (N == 0 || M == 0) return DGAL_OK;
+    if (N > (int64_t)1 << 40 || M > (int64_t)1 << 40) return fail(DGAL_ERR_INVALID_ARG, "N x M too large");
+    DGAL_TRY(check_poly_ptr(a, "a"));
+    DGAL_TRY(check_poly_ptr(b, "b"));
+    if (!iou) return fail(DGAL_ERR_INVALID_ARG, "iou is NULL");
+    if (!aligned(iou, 4)) return fail(DGAL_ERR_ALIGNMENT, "iou is not 4-byte aligned");
+    return launch_pairwise(a, ca, N, b, cb, M, K, iou, nx, flags, (cudaStream_t)stream);
+}
+
+size_t dgal_batched_workspace_bytes(int S, int K) {
+    (void)K;
+    return S < 0 ? 0 : batched_workspace_bytes(S);
+}
+
+static dgal_status check_batched(int S, const int64_t* a_off, const int64_t* b_off, const int64_t* out_off,
+                                 const float* a, const float* b, int K, float* iou, void* ws, size_t ws_bytes) {
+    DGAL_TRY(check_K(K));
+    if (S < 0) return fail(DGAL_ERR_INVALID_ARG, "S = %d is negative", S);
+    if (!a_off || !b_off || !out_off) return fail(DGAL_ERR_INVALID_ARG, "offset arrays must not be NULL");
+    if (!aligned(a_off, 8) || !aligned(b_off, 8) || !aligned(out_off, 8))
+        return fail(DGAL_ERR_ALIGNMENT, "offset arrays are not 8-byte aligned");
+    DGAL_TRY(check_poly_ptr(a, "a"));
+    DGAL_TRY(check_poly_ptr(b, "b"));
+    if (!iou) return fail(DGAL_ERR_INVALID_ARG, "iou is NULL");
+    if (!aligned(iou, 4)) return fail(DGAL_ERR_ALIGNMENT, "iou is not 4-byte aligned");
+    if (!ws) return fail(DGAL_ERR_WORKSPACE, "workspace is NULL");
+    if (!aligned(ws, 16)) return fail(DGAL_ERR_ALIGNMENT, "workspace is not 16-byte aligned");
+    if (ws_bytes < batched_workspace_bytes(S))
+        return fail(DGAL_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", ws_bytes, batched_workspace_bytes(S));
+    return DGAL_OK;
+}
+
+dgal_status dgal_iou_pairwise_batched(int S, const int64_t* a_off, const int64_t* b_off, const int64_t* out_off,
+                                      const float* a, const uint8_t* ca, const float* b, const uint8_t* cb, int K,
+                                      float* iou, uint8_t* nx, void* workspace, size_t ws_bytes, uint32_t flags,
+                                      void* stream) {
+    t_last_error.clear();
+    if (S == 0) return DGAL_OK;
+    DGAL_TRY(check_batched(S, a_off, b_off, out_off, a, b, K, iou, workspace, ws_bytes));
+    return launch_batched(S, a_off, b_off, out_off, a, ca, b, cb, K, iou, nx, workspace, flags, batched_config(K),
+                          (cudaStream_t)stream);
+}
+
+dgal_status dgal_iou_pairwise_per_scene(int S, const int64_t* a_off_h, const int64_t* b_off_h,
+                                        const int64_t* out_off_h, const float* a, const uint8_t* ca, const float* b,
+                                        const uint8_t* cb, int K, float* iou, uint8_t* nx, uint32_t flags,
+                                        void* stream) {
+    t_last_error.clear();
+    DGAL_TRY(check_K(K));
+    if (S < 0) return fail(DGAL_ERR_INVALID_ARG, "S = %d is negative", S);
+    if (S == 0) return DGAL_OK;
+    if (!a_off_h || !b_off_h || !out_off_h) return fail(DGAL_ERR_INVALID_ARG, "offset arrays must not be NULL");
+    DGAL_TRY(check_poly_ptr(a, "a"));
+    DGAL_TRY(check_poly_ptr(b, "b"));
+    if (!iou) return fail(DGAL_ERR_INVALID_ARG, "iou is NULL");
+    for (int s = 0; s < S; ++s) {
+        const int64_t N = a_off_h[s + 1] - a_off_h[s], M = b_off_h[s + 1] - b_off_h[s];
+        if (N < 0 || M < 0 || out_off_h[s + 1] - out_off_h[s] != N * M)
+            return fail(DGAL_ERR_INVALID_ARG, "scene %d: inconsistent offsets", s);
+    }
+    for (int s = 0; s < S; ++s) {
+        const int64_t N = a_off_h[s + 1] - a_off_h[s], M = b_off_h[s + 1] - b_off_h[s];
+        if (N == 0 || M == 0) continue;
+        DGAL_TRY(launch_pairwise(a + a_off_h[s] * 2 * K, ca ? ca + a_off_h[s] : nullptr, N, b + b_off_h[s] * 2 * K,
+                                 cb ? cb + b_off_h[s] : nullptr, M, K, iou + out_off_h[s],
+                                 nx ? nx + out_off_h[s] : nullptr, flags, (cudaStream_t)stream));
+    }
+    return DGAL_OK;
+}
+
+struct dgal_graph_s {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+dgal_status dgal_batched_graph_create(dgal_graph* out, int S, const int64_t* a_off, const int64_t* b_off,
+                                      const int64_t* out_off, const float* a, const uint8_t* ca, const float* b,
+                                      const uint8_t* cb, int K, float* iou, uint8_t* nx, void* workspace,
+                                      size_t ws_bytes, uint32_t flags) {
+    t_last_error.clear();
+    if (!out) return fail(DGAL_ERR_INVALID_ARG, "graph is NULL");
+    *out = nullptr;
+    if (S <= 0) return fail(DGAL_ERR_INVALID_ARG, "S = %d: nothing to capture", S);
+    DGAL_TRY(check_batched(S, a_off, b_off, out_off, a, b, K, iou, workspace, ws_bytes));
+    // resolve cached per-device state before the capture starts
+    (void)sm_count();
+    (void)device_status_ptr();
+    const BatchedConfig cfg = batched_config(K);
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(DGAL_ERR_CUDA, "cudaStreamCreate failed");
+    dgal_graph_s* g = new dgal_graph_s();
+    dgal_status st = DGAL_OK;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        st = fail(DGAL_ERR_CUDA, "cudaStreamBeginCapture failed");
+    } else {
+        st = launch_batched(S, a_off, b_off, out_off, a, ca, b, cb, K, iou, nx, workspace, flags, cfg, s);
+        cudaError_t e = cudaStreamEndCapture(s, &g->graph);
+        if (st == DGAL_OK && e != cudaSuccess) st = fail(DGAL_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
+        if (st == DGAL_OK) {
+            e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+            if (e != cudaSuccess) st = fail(DGAL_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    cudaStreamDestroy(s);
+    if (st != DGAL_OK) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return st;
+    }
+    *out = g;
+    return DGAL_OK;
+}
+
+dgal_status dgal_graph_launch(dgal_graph graph, void* stream) {
+    t_last_error.clear();
+    if (!graph || !graph->exec) return fail(DGAL_ERR_INVALID_ARG, "graph is NULL");
+    cudaError_t e = cudaGraphLaunch(graph->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(DGAL_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+    return DGAL_OK;
+}
+
+dgal_status dgal_graph_destroy(dgal_graph graph) {
+    t_last_error.clear();
+    if (!graph) return DGAL_OK;
+    if (graph->exec) cudaGraphExecDestroy(graph->exec);
+    if (graph->graph) cudaGraphDestroy(graph->graph);
+    delete graph;
+    return DGAL_OK;
+}
+
+dgal_status dgal_get_device_status(uint32_t* out, int clear) {
+    t_last_error.clear();
+    if (!out) return fail(DGAL_ERR_INVALID_ARG, "out is NULL");
+    uint32_t* p = device_status_ptr();
+    if (!p) return fail(DGAL_ERR_CUDA, "status word not available on this device");
+    cudaError_t e = cudaMemcpy(out, p, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(DGAL_ERR_CUDA, "reading status: %s", cudaGetErrorString(e));
+    if (clear) {
+        e = cudaMemset(p, 0, sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return fail(DGAL_ERR_CUDA, "clearing status: %s", cudaGetErrorString(e));
+    }
+    return DGAL_OK;
+}
+
+dgal_status dgal_get_batched_config(int K, int32_t out[3]) {
+    t_last_error.clear();
+    DGAL_TRY(check_K(K));
+    if (!out) return fail(DGAL_ERR_INVALID_ARG, "out is NULL");
+    BatchedConfig c = batched_config(K);
+    out[0] = c.tile;
+    out[1] = c.threads;
+    out[2] = c.blocks_sm;
+    return DGAL_OK;
+}
+
+} // extern "C"
+
+// ---------------------------------------------------------------- autotuner
+
+namespace dgal_tune {
+
+// splitmix64: counter-based generator for the tuner's synthetic boxes
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ float unit(uint64_t z) { return (float)(mix64(z) >> 40) * (1.0f / 16777216.0f); }
+
+// Car-like boxes in a 70 m plane, 40 clusters per scene (the tuning problem).
+__global__ void k_synth_boxes(float* __restrict__ out, const int64_t* __restrict__ scene_of_off, int S,
+                              int64_t n, uint64_t seed, int K) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int lo = 0, hi = S;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (scene_of_off[mid] <= k) lo = mid; else hi = mid;
+    }
+    const uint64_t base = seed * 0x100000001B3ull + (uint64_t)k * 16u;
+    const int cl = (int)(unit(base) * 40.f);
+    const uint64_t cbase = seed * 7919u + (uint64_t)lo * 131u + (uint64_t)cl;
+    const float cx = 70.f * unit(cbase * 3u + 1u), cy = 70.f * unit(cbase * 3u + 2u);
+    const float gx = (unit(base + 1) + unit(base + 2) + unit(base + 3) - 1.5f) * 6.f;
+    const float gy = (unit(base + 4) + unit(base + 5) + unit(base + 6) - 1.5f) * 6.f;
+    const float w = 1.5f + 0.7f * unit(base + 7), l = 3.5f + 1.5f * unit(base + 8);
+    const float th = 6.2831853f * unit(base + 9) - 3.1415927f;
+    float s, c;
+    sincosf(th, &s, &c);
+    const float lx[4] = {-l / 2, l / 2, l / 2, -l / 2}, ly[4] = {-w / 2, -w / 2, w / 2, w / 2};
+    float* p = out + k * 2 * K;
+    for (int v = 0; v < K; ++v) {
+        const int q = (K == 4) ? v : (v < 4 ? v : 0);
+        p[2 * v] = cx + gx + c * lx[q] - s * ly[q];
+        p[2 * v + 1] = cy + gy + s * lx[q] + c * ly[q];
+    }
+}
+
+std::string device_key(int K) {
+    cudaDeviceProp prop;
+    int d = 0;
+    cudaGetDevice(&d);
+    cudaGetDeviceProperties(&prop, d);
+    char buf[320];
+    snprintf(buf, sizeof(buf), "%s|sm%d%d|K=%d", prop.name, prop.major, prop.minor, K);
+    return buf;
+}
+
+// Tiny JSON map {"key": [tile, threads, blocks_sm], ...} (one line per entry).
+std::map<std::string, BatchedConfig> read_cache(const std::string& path) {
+    std::map<std::string, BatchedConfig> m;
+    FILE* f = fopen(path.c_str(), "r");
+    if (!f) return m;
+    char line[1024];
+    while (fgets(line, sizeof(line), f)) {
+        char* q1 = strchr(line, '"');
+        if (!q1) continue;
+        char* q2 = strchr(q1 + 1, '"');
+        if (!q2) continue;
+        std::string key(q1 + 1, q2);
+        int t = 0, th = 0, b = 0;
+        char* br = strchr(q2, '[');
+        if (br && sscanf(br, "[%d, %d, %d]", &t, &th, &b) == 3 && t > 0 && th > 0 && b > 0) m[key] = BatchedConfig{t, th, b};
+    }
+    fclose(f);
+    return m;
+}
+
+bool write_cache(const std::string& path, const std::map<std::string, BatchedConfig>& m) {
+    std::string tmp = path + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    fprintf(f, "{\n");
+    size_t k = 0;
+    for (auto& kv : m) {
+        fprintf(f, "  \"%s\": [%d, %d, %d]%s\n", kv.first.c_str(), kv.second.tile, kv.second.threads,
+                kv.second.blocks_sm, (++k < m.size()) ? "," : "");
+    }
+    fprintf(f, "}\n");
+    fclose(f);
+    return rename(tmp.c_str(), path.c_str()) == 0;
+}
+
+} // namespace dgal_tune
+
+using namespace dgal_tune;
+
+extern "C" dgal_status dgal_autotune(int K, int config_class, const char* cache_path) {
+    t_last_error.clear();
+    DGAL_TRY(check_K(K));
+    (void)config_class;
+    std::string path;
+    if (cache_path) path = cache_path;
+    else if (const char* env = getenv("DGAL_TUNE_CACHE")) path = env;
+    const std::string key = device_key(K);
+    if (!path.empty()) {
+        auto m = read_cache(path);
+        auto it = m.find(key);
+        if (it != m.end()) {
+            set_batched_config(K, it->second);
+            return DGAL_OK;
+        }
+    }
+
+    // synthetic ragged problem: 64 scenes, N_s in [50, 3000], M_s in [5, 200]
+    const int S = 64;
+    std::vector<int64_t> ao(S + 1, 0), bo(S + 1, 0), oo(S + 1, 0);
+    uint64_t lcg = 0x2545F4914F6CDD1Dull;
+    auto nextu = [&lcg](uint64_t m) {
+        lcg = lcg * 6364136223846793005ull + 1442695040888963407ull;
+        return (lcg >> 33) % m;
+    };
+    for (int s = 0; s < S; ++s) {
+        const int64_t N = 50 + (int64_t)nextu(2951), M = 5 + (int64_t)nextu(196);
+        ao[s + 1] = ao[s] + N;
+        bo[s + 1] = bo[s] + M;
+        oo[s + 1] = oo[s] + N * M;
+    }
+    const size_t ws_bytes = batched_workspace_bytes(S);
+    float *a = nullptr, *b = nullptr, *iou = nullptr;
+    uint8_t* nx = nullptr;
+    int64_t* offs = nullptr;
+    void* ws = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    dgal_status st = DGAL_OK;
+    auto cleanup = [&]() {
+        cudaFree(a); cudaFree(b); cudaFree(iou); cudaFree(nx); cudaFree(offs); cudaFree(ws);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (cudaMalloc(&a, ao[S] * 2 * K * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&b, bo[S] * 2 * K * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&iou, oo[S] * sizeof(float)) != cudaSuccess || cudaMalloc(&nx, oo[S]) != cudaSuccess ||
+        cudaMalloc(&offs, 3 * (S + 1) * sizeof(int64_t)) != cudaSuccess || cudaMalloc(&ws, ws_bytes) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cleanup();
+        return fail(DGAL_ERR_CUDA, "autotune: allocation failed");
+    }
+    cudaMemcpy(offs, ao.data(), (S + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(offs + (S + 1), bo.data(), (S + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(offs + 2 * (S + 1), oo.data(), (S + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+    k_synth_boxes<<<(unsigned)((ao[S] + 255) / 256), 256>>>(a, offs, S, ao[S], 1, K);
+    k_synth_boxes<<<(unsigned)((bo[S] + 255) / 256), 256>>>(b, offs + (S + 1), S, bo[S], 2, K);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cleanup();
+        return fail(DGAL_ERR_CUDA, "autotune: synthetic input generation failed");
+    }
+    const int tiles[] = {256, 512, 1024, 2048, 4096};
+    const int threads[] = {128, 256};
+    const int bps[] = {2, 4, 8, 12};
+    BatchedConfig best{1024, 128, 8};
+    float best_ms = 1e30f;
+    for (int t : tiles)
+        for (int th : threads)
+            for (int bp : bps) {
+                if (th * bp > 2048) continue;
+                BatchedConfig c{t, th, bp};
+                float ms_min = 1e30f;
+                for (int rep = 0; rep < 4 && st == DGAL_OK; ++rep) {
+                    cudaEventRecord(e0, 0);
+                    st = launch_batched(S, offs, offs + (S + 1), offs + 2 * (S + 1), a, nullptr, b, nullptr, K, iou,
+                                        nx, ws, kFlagRefine, c, 0);
+                    cudaEventRecord(e1, 0);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0 && ms < ms_min) ms_min = ms;
+                }
+                if (st != DGAL_OK) {
+                    cleanup();
+                    return st;
+                }
+                if (ms_min < best_ms) {
+                    best_ms = ms_min;
+                    best = c;
+                }
+            }
+    cleanup();
+    set_batched_config(K, best);
+    if (!path.empty()) {
+        auto m = read_cache(path);
+        m[key] = best;
+        if (!write_cache(path, m)) return fail(DGAL_ERR_INVALID_ARG, "autotune: cannot write %s", path.c_str());
+    }
+    return DGAL_OK;
+}

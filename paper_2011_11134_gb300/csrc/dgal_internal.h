@@ -1,0 +1,46 @@
+// Internal host-side declarations shared by the libdgal translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dgal.h"
+
+namespace dgal {
+
+// Records a message for dgal_last_error() and returns `st`.
+dgal_status fail(dgal_status st, const char* fmt, ...);
+// Checks cudaGetLastError after a launch.
+dgal_status check_launch(const char* what);
+// Number of SMs of the current device (cached per device).
+int sm_count();
+// Address of the device status word on the current device (cached per device).
+uint32_t* device_status_ptr();
+// Uncached lookup of that address (paired.cu owns the symbol).
+uint32_t* status_symbol_address();
+
+// Launch shape of the ragged batched kernel.
+struct BatchedConfig {
+    int tile;       // entries per tile (one queue pop)
+    int threads;    // threads per block
+    int blocks_sm;  // resident blocks per SM of the persistent grid
+};
+BatchedConfig batched_config(int K);
+void set_batched_config(int K, BatchedConfig c);
+
+// Launchers (no validation; called from the C ABI after checks).
+dgal_status launch_paired_fwd(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                              int K, float* iou, uint8_t* nx, uint8_t* xflags, uint8_t* degen, uint32_t flags,
+                              cudaStream_t s);
+dgal_status launch_paired_bwd(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                              int K, const float* grad, const uint8_t* nx, const uint8_t* xflags, float* g1,
+                              float* g2, uint32_t flags, cudaStream_t s);
+dgal_status launch_pairwise(const float* a, const uint8_t* ca, int64_t N, const float* b, const uint8_t* cb,
+                            int64_t M, int K, float* iou, uint8_t* nx, uint32_t flags, cudaStream_t s);
+size_t batched_workspace_bytes(int S);
+dgal_status launch_batched(int S, const int64_t* a_off, const int64_t* b_off, const int64_t* out_off,
+                           const float* a, const uint8_t* ca, const float* b, const uint8_t* cb, int K, float* iou,
+                           uint8_t* nx, void* ws, uint32_t flags, const BatchedConfig& cfg, cudaStream_t s);
+
+} // namespace dgal

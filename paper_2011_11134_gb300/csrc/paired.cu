@@ -1,0 +1,190 @@
+// Paired IoU kernels: n independent pairs, one thread per pair.
+//
+// Forward (paper Sec. II-B `iou`): loads both polygons with 128-bit loads,
+// clips in registers (dgal_geom.cuh), stores IoU (4 B), nx (1 B) and the
+// 2K code bytes as one 64/128-bit store, plus an optional degeneracy byte.
+// Backward (paper Sec. II-B `iou_backward`): reads the polygons, dL/dIoU and
+// the recorded (nx, xflags), or recomputes the clip, and writes both
+// gradients with 128-bit stores.
+#include "dgal_geom.cuh"
+#include "dgal_internal.h"
+
+namespace dgal {
+
+// One status word per device; every kernel of the library ORs into it through
+// a pointer argument (see device_status_ptr in api.cu).
+__device__ uint32_t g_status;
+
+uint32_t* status_symbol_address() {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
+    return static_cast<uint32_t*>(p);
+}
+
+constexpr int kPairThreads = 128;
+
+template <int K> __device__ __forceinline__ void store_codes(uint8_t* __restrict__ xf, int64_t k, const Codes<K>& c) {
+    if constexpr (K == 4) {
+        reinterpret_cast<uint64_t*>(xf)[k] = c.w[0];
+    } else {
+        reinterpret_cast<uint4*>(xf)[k] =
+            make_uint4((uint32_t)c.w[0], (uint32_t)(c.w[0] >> 32), (uint32_t)c.w[1], (uint32_t)(c.w[1] >> 32));
+    }
+}
+
+template <int K> __device__ __forceinline__ void load_codes(const uint8_t* __restrict__ xf, int64_t k, Codes<K>& c) {
+    if constexpr (K == 4) {
+        c.w[0] = __ldg(reinterpret_cast<const unsigned long long*>(xf) + k);
+    } else {
+        uint4 u = __ldg(reinterpret_cast<const uint4*>(xf) + k);
+        c.w[0] = (uint64_t)u.x | ((uint64_t)u.y << 32);
+        c.w[1] = (uint64_t)u.z | ((uint64_t)u.w << 32);
+    }
+}
+
+template <int K> __device__ __forceinline__ void store_poly(float* __restrict__ p, const float (&x)[K], const float (&y)[K]) {
+    float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int v = 0; v < K / 2; ++v) q[v] = make_float4(x[2 * v], y[2 * v], x[2 * v + 1], y[2 * v + 1]);
+}
+
+template <int K, bool COUNTS, bool SAVE>
+__global__ void __launch_bounds__(kPairThreads)
+k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
+             const uint8_t* __restrict__ c2, int64_t n, float* __restrict__ iou, uint8_t* __restrict__ nx,
+             uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        int n1 = K, n2 = K;
+        if (COUNTS) {
+            n1 = c1 ? (int)c1[k] : K;
+            n2 = c2 ? (int)c2[k] : K;
+        }
+        FwdOut<K> o;
+        Geo<K> g;
+        if (COUNTS && (n1 < 3 || n1 > K || n2 < 3 || n2 > K)) {
+            o.err = kDevBadCount;
+            o.nx = 0;
+            o.ai = o.a1 = o.a2 = 0.f;
+            o.degen = 0;
+            codes_fill<K>(o.codes, ~0ull);
+        } else {
+            fwd_pair<K, COUNTS>(p1 + k * 2 * K, p2 + k * 2 * K, n1, n2, flags, g, o);
+        }
+        iou[k] = iou_of(o.ai, o.a1, o.a2, o.nx);
+        if (SAVE) {
+            nx[k] = (uint8_t)o.nx;
+            store_codes<K>(xflags, k, o.codes);
+        }
+        if (degen) degen[k] = (uint8_t)o.degen;
+        if (o.err) atomicOr(status, o.err);
+    }
+}
+
+template <int K, bool COUNTS, bool RECOMPUTE>
+__global__ void __launch_bounds__(kPairThreads)
+k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
+             const uint8_t* __restrict__ c2, int64_t n, const float* __restrict__ grad,
+             const uint8_t* __restrict__ nxs, const uint8_t* __restrict__ xflags, float* __restrict__ g1,
+             float* __restrict__ g2, uint32_t flags, uint32_t* status) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        int n1 = K, n2 = K;
+        if (COUNTS) {
+            n1 = c1 ? (int)c1[k] : K;
+            n2 = c2 ? (int)c2[k] : K;
+        }
+        float g1x[K], g1y[K], g2x[K], g2y[K];
+        uint32_t err = 0;
+        if (COUNTS && (n1 < 3 || n1 > K || n2 < 3 || n2 > K)) {
+            err = kDevBadCount;
+#pragma unroll
+            for (int v = 0; v < K; ++v) { g1x[v] = g1y[v] = g2x[v] = g2y[v] = 0.f; }
+        } else {
+            Geo<K> g;
+            Codes<K> codes;
+            uint32_t nx;
+            if (RECOMPUTE) {
+                FwdOut<K> o;
+                fwd_pair<K, COUNTS>(p1 + k * 2 * K, p2 + k * 2 * K, n1, n2, flags, g, o);
+                codes = o.codes;
+                nx = o.nx;
+                err |= o.err;
+            } else {
+                float px[K], py[K], qx[K], qy[K];
+                load_poly<K>(p1 + k * 2 * K, px, py);
+                load_poly<K>(p2 + k * 2 * K, qx, qy);
+                make_geo<K, COUNTS>(px, py, qx, qy, n1, n2, g);
+                nx = nxs[k];
+                load_codes<K>(xflags, k, codes);
+            }
+            err |= bwd_pair<K, COUNTS>(g, __ldg(grad + k), nx, codes, g1x, g1y, g2x, g2y);
+            if (err & kDevBadFlags) {
+#pragma unroll
+                for (int v = 0; v < K; ++v) { g1x[v] = g1y[v] = g2x[v] = g2y[v] = 0.f; }
+            }
+        }
+        store_poly<K>(g1 + k * 2 * K, g1x, g1y);
+        store_poly<K>(g2 + k * 2 * K, g2x, g2y);
+        if (err) atomicOr(status, err);
+    }
+}
+
+static unsigned grid_for(int64_t n, int threads) {
+    int64_t blocks = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)sm_count() * 64;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    return (unsigned)blocks;
+}
+
+template <int K, bool COUNTS>
+static void fwd_dispatch(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                         float* iou, uint8_t* nx, uint8_t* xflags, uint8_t* degen, uint32_t flags, cudaStream_t s) {
+    const unsigned grid = grid_for(n, kPairThreads);
+    uint32_t* st = device_status_ptr();
+    if (nx) k_paired_fwd<K, COUNTS, true><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st);
+    else k_paired_fwd<K, COUNTS, false><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st);
+}
+
+dgal_status launch_paired_fwd(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                              int K, float* iou, uint8_t* nx, uint8_t* xflags, uint8_t* degen, uint32_t flags,
+                              cudaStream_t s) {
+    const bool counts = c1 || c2;
+    if (K == 4) {
+        if (counts) fwd_dispatch<4, true>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, s);
+        else fwd_dispatch<4, false>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, s);
+    } else {
+        if (counts) fwd_dispatch<8, true>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, s);
+        else fwd_dispatch<8, false>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, s);
+    }
+    return check_launch("paired forward");
+}
+
+template <int K, bool COUNTS>
+static void bwd_dispatch(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                         const float* grad, const uint8_t* nx, const uint8_t* xflags, float* g1, float* g2,
+                         uint32_t flags, cudaStream_t s) {
+    const unsigned grid = grid_for(n, kPairThreads);
+    uint32_t* st = device_status_ptr();
+    if (nx && xflags && !(flags & kFlagPlain))
+        k_paired_bwd<K, COUNTS, false><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, st);
+    else
+        k_paired_bwd<K, COUNTS, true><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, st);
+}
+
+dgal_status launch_paired_bwd(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                              int K, const float* grad, const uint8_t* nx, const uint8_t* xflags, float* g1,
+                              float* g2, uint32_t flags, cudaStream_t s) {
+    const bool counts = c1 || c2;
+    if (K == 4) {
+        if (counts) bwd_dispatch<4, true>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, s);
+        else bwd_dispatch<4, false>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, s);
+    } else {
+        if (counts) bwd_dispatch<8, true>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, s);
+        else bwd_dispatch<8, false>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, s);
+    }
+    return check_launch("paired backward");
+}
+
+} // namespace dgal

@@ -1,0 +1,245 @@
+// Pairwise IoU matrices: one N x M matrix, or a ragged batch of S matrices
+// in one persistent launch.
+//
+// Each thread owns one (i, j) entry of a row-major matrix, so consecutive
+// lanes write consecutive IoU floats and nx bytes (coalesced).  Row polygon
+// a_i is the same for most lanes of a warp (a broadcast load), column polygons
+// b_j are consecutive 32/64-byte rows; both sets are small and stay in L1/L2.
+// An exact axis-aligned bounding-box test (comparisons on the float inputs,
+// no rounding) rejects disjoint pairs before the clip: they have IoU 0 and
+// nx 0 by definition (no vertex inside, no crossing).
+//
+// Ragged batch: a setup kernel turns the device-side offsets into a tile
+// prefix (tiles of `tile` consecutive entries of one scene's matrix) and
+// resets a queue counter; persistent blocks (SMs x blocks_sm) pop tile
+// numbers with one atomicAdd each until the queue is empty.  The queue only
+// grows, nothing waits on it, so the launch cannot hang; everything it reads
+// lives on the device, so the pair of launches can be captured in a graph.
+#include "dgal_geom.cuh"
+#include "dgal_internal.h"
+
+namespace dgal {
+
+constexpr int kPwThreads = 128;
+
+template <int K, bool COUNTS>
+__device__ __forceinline__ void pw_entry(const float* __restrict__ pa, const float* __restrict__ pb, int n1, int n2,
+                                         uint32_t flags, float& iou, uint32_t& nxo, uint32_t& err) {
+    iou = 0.f;
+    nxo = 0u;
+    if (COUNTS && (n1 < 3 || n1 > K || n2 < 3 || n2 > K)) {
+        err |= kDevBadCount;
+        return;
+    }
+    float px[K], py[K], qx[K], qy[K];
+    load_poly<K>(pa, px, py);
+    load_poly<K>(pb, qx, qy);
+    float ax0 = px[0], ax1 = px[0], ay0 = py[0], ay1 = py[0];
+    float bx0 = qx[0], bx1 = qx[0], by0 = qy[0], by1 = qy[0];
+#pragma unroll
+    for (int v = 1; v < K; ++v) {
+        const bool va = !COUNTS || v < n1, vb = !COUNTS || v < n2;
+        ax0 = va ? fminf(ax0, px[v]) : ax0;
+        ax1 = va ? fmaxf(ax1, px[v]) : ax1;
+        ay0 = va ? fminf(ay0, py[v]) : ay0;
+        ay1 = va ? fmaxf(ay1, py[v]) : ay1;
+        bx0 = vb ? fminf(bx0, qx[v]) : bx0;
+        bx1 = vb ? fmaxf(bx1, qx[v]) : bx1;
+        by0 = vb ? fminf(by0, qy[v]) : by0;
+        by1 = vb ? fmaxf(by1, qy[v]) : by1;
+    }
+    if (ax1 < bx0 || bx1 < ax0 || ay1 < by0 || by1 < ay0) return;
+    Geo<K> g;
+    FwdOut<K> o;
+    fwd_loaded<K, COUNTS>(px, py, qx, qy, pa, pb, n1, n2, flags, g, o);
+    err |= o.err;
+    nxo = o.nx;
+    iou = iou_of(o.ai, o.a1, o.a2, o.nx);
+}
+
+template <int K, bool COUNTS>
+__global__ void __launch_bounds__(kPwThreads)
+k_pairwise(const float* __restrict__ a, const uint8_t* __restrict__ ca, int64_t N, const float* __restrict__ b,
+           const uint8_t* __restrict__ cb, int64_t M, float* __restrict__ iou, uint8_t* __restrict__ nx,
+           uint32_t flags, uint32_t* status) {
+    const int64_t total = N * M;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    int64_t i = e / M, j = e - (e / M) * M;
+    const int64_t di = stride / M, dj = stride - di * M;
+    uint32_t err = 0;
+    for (; e < total; e += stride) {
+        const int n1 = (COUNTS && ca) ? (int)ca[i] : K;
+        const int n2 = (COUNTS && cb) ? (int)cb[j] : K;
+        float v;
+        uint32_t c;
+        pw_entry<K, COUNTS>(a + i * 2 * K, b + j * 2 * K, n1, n2, flags, v, c, err);
+        iou[e] = v;
+        if (nx) nx[e] = (uint8_t)c;
+        i += di;
+        j += dj;
+        if (j >= M) {
+            j -= M;
+            ++i;
+        }
+    }
+    if (err) atomicOr(status, err);
+}
+
+// ------------------------------------------------------------ ragged batch
+
+// workspace: [0] uint32 queue counter, [16 B ..] int64 tile_start[S + 1]
+size_t batched_workspace_bytes(int S) { return 16 + (((size_t)(S + 1) * 8 + 15) / 16) * 16; }
+
+constexpr int kSetupThreads = 1024;
+
+__global__ void __launch_bounds__(kSetupThreads)
+k_batched_setup(int S, const int64_t* __restrict__ a_off, const int64_t* __restrict__ b_off,
+                const int64_t* __restrict__ out_off, int64_t tile, uint32_t* __restrict__ counter,
+                int64_t* __restrict__ tile_start, uint32_t* status) {
+    __shared__ int64_t part[kSetupThreads];
+    const int t = threadIdx.x;
+    const int chunk = (S + kSetupThreads - 1) / kSetupThreads;
+    const int s0 = t * chunk, s1 = min(S, s0 + chunk);
+    int64_t sum = 0;
+    uint32_t err = 0;
+    for (int s = s0; s < s1; ++s) {
+        const int64_t Ns = a_off[s + 1] - a_off[s], Ms = b_off[s + 1] - b_off[s];
+        const int64_t E = out_off[s + 1] - out_off[s];
+        const bool ok = Ns >= 0 && Ms >= 0 && E == Ns * Ms && a_off[0] == 0 && b_off[0] == 0 && out_off[0] == 0;
+        err |= ok ? 0u : kDevBadOffsets;
+        sum += ok ? (E + tile - 1) / tile : 0;
+    }
+    part[t] = sum;
+    __syncthreads();
+    // inclusive scan over the per-thread sums (Hillis-Steele)
+    for (int off = 1; off < kSetupThreads; off <<= 1) {
+        int64_t v = (t >= off) ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int64_t run = part[t] - sum;
+    for (int s = s0; s < s1; ++s) {
+        tile_start[s] = run;
+        const int64_t Ns = a_off[s + 1] - a_off[s], Ms = b_off[s + 1] - b_off[s];
+        const int64_t E = out_off[s + 1] - out_off[s];
+        const bool ok = Ns >= 0 && Ms >= 0 && E == Ns * Ms && a_off[0] == 0 && b_off[0] == 0 && out_off[0] == 0;
+        run += ok ? (E + tile - 1) / tile : 0;
+    }
+    if (t == kSetupThreads - 1) {
+        tile_start[S] = part[t];
+        *counter = 0u;
+    }
+    if (err) atomicOr(status, err);
+}
+
+template <int K, bool COUNTS>
+__global__ void k_batched(int S, const int64_t* __restrict__ a_off, const int64_t* __restrict__ b_off,
+                          const int64_t* __restrict__ out_off, const float* __restrict__ a,
+                          const uint8_t* __restrict__ ca, const float* __restrict__ b, const uint8_t* __restrict__ cb,
+                          float* __restrict__ iou, uint8_t* __restrict__ nx, uint32_t* __restrict__ counter,
+                          const int64_t* __restrict__ tile_start, int64_t tile, uint32_t flags, uint32_t* status) {
+    __shared__ int64_t s_tile;
+    __shared__ int s_scene;
+    const int64_t total = tile_start[S];
+    uint32_t err = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int64_t t = (int64_t)atomicAdd(counter, 1u);
+            int lo = 0, hi = S; // largest s with tile_start[s] <= t (tile_start[S] = total > t)
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (tile_start[mid] <= t) lo = mid; else hi = mid;
+            }
+            s_tile = t;
+            s_scene = lo;
+        }
+        __syncthreads();
+        const int64_t t = s_tile;
+        const int s = s_scene;
+        __syncthreads();
+        if (t >= total) break;
+        const int64_t a0 = a_off[s], b0 = b_off[s], o0 = out_off[s];
+        const int64_t Ms = b_off[s + 1] - b0, E = out_off[s + 1] - o0;
+        const int64_t e0 = (t - tile_start[s]) * tile;
+        const int64_t e1 = min(e0 + tile, E);
+        int64_t e = e0 + threadIdx.x;
+        if (e >= e1) continue;
+        int64_t i = e / Ms, j = e - (e / Ms) * Ms;
+        const int64_t di = (int64_t)blockDim.x / Ms, dj = (int64_t)blockDim.x - di * Ms;
+        for (; e < e1; e += blockDim.x) {
+            const int n1 = (COUNTS && ca) ? (int)ca[a0 + i] : K;
+            const int n2 = (COUNTS && cb) ? (int)cb[b0 + j] : K;
+            float v;
+            uint32_t c;
+            pw_entry<K, COUNTS>(a + (a0 + i) * 2 * K, b + (b0 + j) * 2 * K, n1, n2, flags, v, c, err);
+            iou[o0 + e] = v;
+            if (nx) nx[o0 + e] = (uint8_t)c;
+            i += di;
+            j += dj;
+            if (j >= Ms) {
+                j -= Ms;
+                ++i;
+            }
+        }
+    }
+    if (err) atomicOr(status, err);
+}
+
+template <int K, bool COUNTS>
+static void pairwise_dispatch(const float* a, const uint8_t* ca, int64_t N, const float* b, const uint8_t* cb,
+                              int64_t M, float* iou, uint8_t* nx, uint32_t flags, cudaStream_t s) {
+    const int64_t total = N * M;
+    int64_t blocks = (total + kPwThreads - 1) / kPwThreads;
+    const int64_t cap = (int64_t)sm_count() * 32;
+    if (blocks > cap) blocks = cap;
+    k_pairwise<K, COUNTS><<<(unsigned)blocks, kPwThreads, 0, s>>>(a, ca, N, b, cb, M, iou, nx, flags,
+                                                                   device_status_ptr());
+}
+
+dgal_status launch_pairwise(const float* a, const uint8_t* ca, int64_t N, const float* b, const uint8_t* cb,
+                            int64_t M, int K, float* iou, uint8_t* nx, uint32_t flags, cudaStream_t s) {
+    const bool counts = ca || cb;
+    if (K == 4) {
+        if (counts) pairwise_dispatch<4, true>(a, ca, N, b, cb, M, iou, nx, flags, s);
+        else pairwise_dispatch<4, false>(a, ca, N, b, cb, M, iou, nx, flags, s);
+    } else {
+        if (counts) pairwise_dispatch<8, true>(a, ca, N, b, cb, M, iou, nx, flags, s);
+        else pairwise_dispatch<8, false>(a, ca, N, b, cb, M, iou, nx, flags, s);
+    }
+    return check_launch("pairwise");
+}
+
+template <int K, bool COUNTS>
+static void batched_dispatch(int S, const int64_t* a_off, const int64_t* b_off, const int64_t* out_off,
+                             const float* a, const uint8_t* ca, const float* b, const uint8_t* cb, float* iou,
+                             uint8_t* nx, uint32_t* counter, const int64_t* tile_start, uint32_t flags,
+                             const BatchedConfig& cfg, cudaStream_t s) {
+    const unsigned grid = (unsigned)(sm_count() * cfg.blocks_sm);
+    k_batched<K, COUNTS><<<grid, cfg.threads, 0, s>>>(S, a_off, b_off, out_off, a, ca, b, cb, iou, nx, counter,
+                                                       tile_start, (int64_t)cfg.tile, flags, device_status_ptr());
+}
+
+dgal_status launch_batched(int S, const int64_t* a_off, const int64_t* b_off, const int64_t* out_off,
+                           const float* a, const uint8_t* ca, const float* b, const uint8_t* cb, int K, float* iou,
+                           uint8_t* nx, void* ws, uint32_t flags, const BatchedConfig& cfg, cudaStream_t s) {
+    uint32_t* counter = static_cast<uint32_t*>(ws);
+    int64_t* tile_start = reinterpret_cast<int64_t*>(static_cast<char*>(ws) + 16);
+    k_batched_setup<<<1, kSetupThreads, 0, s>>>(S, a_off, b_off, out_off, (int64_t)cfg.tile, counter, tile_start,
+                                                device_status_ptr());
+    dgal_status st = check_launch("batched setup");
+    if (st != DGAL_OK) return st;
+    const bool counts = ca || cb;
+    if (K == 4) {
+        if (counts) batched_dispatch<4, true>(S, a_off, b_off, out_off, a, ca, b, cb, iou, nx, counter, tile_start, flags, cfg, s);
+        else batched_dispatch<4, false>(S, a_off, b_off, out_off, a, ca, b, cb, iou, nx, counter, tile_start, flags, cfg, s);
+    } else {
+        if (counts) batched_dispatch<8, true>(S, a_off, b_off, out_off, a, ca, b, cb, iou, nx, counter, tile_start, flags, cfg, s);
+        else batched_dispatch<8, false>(S, a_off, b_off, out_off, a, ca, b, cb, iou, nx, counter, tile_start, flags, cfg, s);
+    }
+    return check_launch("batched");
+}
+
+} // namespace dgal

@@ -1,0 +1,69 @@
+"""The C ABI library builds for sm_103a, loads, and exports every symbol the
+header declares (no compute calls: these run without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libdgal():
+    from paper_2011_11134_gb300 import build
+
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "dgal.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dgal_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_calls():
+    names = _declared()
+    for n in ("dgal_iou_paired", "dgal_iou_pairwise", "dgal_iou_backward", "dgal_iou_pairwise_batched",
+              "dgal_batched_workspace_bytes", "dgal_autotune", "dgal_last_error", "dgal_get_device_status"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libdgal):
+    for name in _declared():
+        assert hasattr(libdgal, name), name
+
+
+def test_binding_covers_header():
+    from paper_2011_11134_gb300 import _lib
+
+    assert sorted(_lib.exported_symbols()) == _declared()
+
+
+def test_host_only_calls(libdgal):
+    libdgal.dgal_version.restype = ctypes.c_int
+    assert libdgal.dgal_version() == 100
+    libdgal.dgal_batched_workspace_bytes.restype = ctypes.c_size_t
+    libdgal.dgal_batched_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
+    assert libdgal.dgal_batched_workspace_bytes(64, 4) >= 16 + 65 * 8
+    assert libdgal.dgal_batched_workspace_bytes(64, 4) % 16 == 0
+
+
+def test_validation_rejects_before_any_launch(libdgal):
+    """Argument errors are caught on the host, so they are testable without a GPU."""
+    f = libdgal.dgal_iou_paired
+    P = ctypes.c_void_p
+    f.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_int, P, P, P, P, ctypes.c_uint32, P]
+    f.restype = ctypes.c_int
+    libdgal.dgal_last_error.restype = ctypes.c_char_p
+    buf = (ctypes.c_float * 64)()
+    base = ctypes.addressof(buf)
+    al = base + (-base % 16)
+    assert f(al, None, al, None, 4, 5, al, None, None, None, 0, None) == 2  # K unsupported
+    assert f(al, None, al, None, -1, 4, al, None, None, None, 0, None) == 1  # negative n
+    assert f(al, None, al, None, 0, 4, al, None, None, None, 0, None) == 0  # n = 0: no launch
+    assert f(al + 4, None, al, None, 1, 4, al, None, None, None, 0, None) == 3  # misaligned polygons
+    assert f(al, None, al, None, 1, 4, None, None, None, None, 0, None) == 1  # iou NULL
+    assert f(al, None, al, None, 1, 4, al, al, None, None, 0, None) == 1  # nx without xflags
+    assert b"xflags" in libdgal.dgal_last_error()

@@ -1,0 +1,211 @@
+"""GPU parity of the paired forward / backward against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_2011_11134_gb300 import workloads as W
+
+from .gpu_helpers import GRAD_RTOL, THREADS, check_forward, dev, grad_rel_err, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dg():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2011_11134_gb300 as m
+
+    m.dgal_get_device_status(clear=True)
+    return m
+
+
+def _fwd(dg, p1, p2, c1=None, c2=None, flags=None):
+    kw = {} if flags is None else dict(flags=flags)
+    iou, nx, xf, degen = dg.dgal_iou_paired(dev(p1), dev(p2), None if c1 is None else dev(c1),
+                                            None if c2 is None else dev(c2), with_degen=True, **kw)
+    return host(iou), host(nx), host(xf), host(degen)
+
+
+@pytest.mark.parametrize("n", [4096, 4096 + 37, 1])
+def test_paired_rect_forward(dg, orc, n):
+    d = W.paired_rect_4096(seed=0, n=n)
+    iou, nx, xf, degen = _fwd(dg, d["p1"], d["p2"])
+    ref = orc.iou_paired(d["p1"], d["p2"], threads=THREADS)
+    gen = check_forward(iou, nx, xf, degen, ref, "paired K=4")
+    assert gen.mean() > 0.99 or n < 10
+    assert dg.dgal_get_device_status() == 0
+
+
+def test_paired_rect_backward_saved_and_recompute(dg, orc):
+    import torch
+
+    d = W.paired_rect_4096(seed=0)
+    n = d["p1"].shape[0]
+    p1, p2 = dev(d["p1"]), dev(d["p2"])
+    grad = torch.from_numpy(np.linspace(-1.5, 2.0, n).astype(np.float32)).cuda()
+    iou, nx, xf, degen = dg.dgal_iou_paired(p1, p2, with_degen=True)
+    g1, g2 = dg.dgal_iou_backward(p1, p2, grad, nx, xf)
+    r1, r2 = dg.dgal_iou_backward(p1, p2, grad)  # recompute
+    ref = orc.iou_paired(d["p1"], d["p2"])
+    o1, o2 = orc.iou_backward_paired(d["p1"], d["p2"], host(grad).astype(np.float64), ref["nx"], ref["xflags"])
+    gen = (ref["degen"] == 0) & ((host(degen) & 1) == 0)
+    rel = grad_rel_err(host(g1), host(g2), o1, o2, gen)
+    assert rel.max() <= GRAD_RTOL, f"saved-flag grads: max rel err {rel.max():.3e}"
+    # recompute mode reproduces the saved-flag gradients exactly (same arithmetic)
+    assert torch.equal(g1, r1) and torch.equal(g2, r2)
+
+
+def test_loss_pairs_full_size(dg, orc):
+    """The 1M-pair IoU-loss workload, forward + backward on every pair."""
+    import torch
+
+    d = W.loss_pairs_1m(seed=0)
+    p1, p2 = dev(d["p1"]), dev(d["p2"])
+    grad = torch.ones(p1.shape[0], device="cuda")
+    iou, nx, xf, degen = dg.dgal_iou_paired(p1, p2, with_degen=True)
+    g1, g2 = dg.dgal_iou_backward(p1, p2, grad, nx, xf)
+    ref = orc.iou_paired(d["p1"], d["p2"], threads=THREADS)
+    gen = check_forward(host(iou), host(nx), host(xf), host(degen), ref, "loss 1M")
+    o1, o2 = orc.iou_backward_paired(d["p1"], d["p2"], np.ones(p1.shape[0]), ref["nx"], ref["xflags"],
+                                     threads=THREADS)
+    rel = grad_rel_err(host(g1), host(g2), o1, o2, gen)
+    assert rel.max() <= GRAD_RTOL, f"1M grads: max rel err {rel.max():.3e} at {int(rel.argmax())}"
+
+
+def test_finite_differences_1000(dg, orc):
+    """GPU gradients vs central differences of the FP64 oracle on 1000 pairs."""
+    d = W.loss_pairs_1m(seed=0, n=1000)
+    p1, p2 = dev(d["p1"]), dev(d["p2"])
+    import torch
+
+    iou, nx, xf, degen = dg.dgal_iou_paired(p1, p2, with_degen=True)
+    g1, g2 = dg.dgal_iou_backward(p1, p2, torch.ones(1000, device="cuda"), nx, xf)
+    g1, g2, degen = host(g1), host(g2), host(degen)
+    checked = 0
+    for k in range(1000):
+        P, Q = d["p1"][k].astype(np.float64), d["p2"][k].astype(np.float64)
+        base = orc.iou_pair_f64(P, Q, 4)
+        if base[6] or (degen[k] & 1) or base[4] == 0:
+            continue
+        L = max(np.abs(P - P[0]).max(), np.abs(Q - P[0]).max())
+        h = 1e-6 * L
+        num = np.zeros((2, 4, 2))
+        ok = True
+        for w in range(2):
+            for v in range(4):
+                for c in range(2):
+                    vals = []
+                    for sg in (1, -1):
+                        A, B = P.copy(), Q.copy()
+                        (A if w == 0 else B)[v, c] += sg * h
+                        r = orc.iou_pair_f64(A, B, 4)
+                        ok &= r[4] == base[4] and list(r[5]) == list(base[5])
+                        vals.append(r[0])
+                    num[w, v, c] = (vals[0] - vals[1]) / (2 * h)
+        if not ok:
+            continue
+        G = np.stack([g1[k], g2[k]]).astype(np.float64)
+        rel = np.abs(G - num).max() / max(np.abs(num).max(), 1e-6)
+        assert rel <= GRAD_RTOL, f"pair {k}: FD rel err {rel:.3e}"
+        checked += 1
+    assert checked >= 900
+
+
+def test_autograd_function(dg):
+    import torch
+
+    d = W.paired_rect_4096(seed=2, n=777)
+    p1 = dev(d["p1"]).requires_grad_(True)
+    p2 = dev(d["p2"]).requires_grad_(True)
+    w = torch.rand(777, device="cuda")
+    (dg.iou(p1, p2) * w).sum().backward()
+    a1, a2 = p1.grad.clone(), p2.grad.clone()
+    p1.grad = None
+    p2.grad = None
+    (dg.iou(p1, p2, recompute=True) * w).sum().backward()
+    assert torch.equal(a1, p1.grad) and torch.equal(a2, p2.grad)
+    _, nx, xf, _ = dg.dgal_iou_paired(p1.detach(), p2.detach())
+    b1, b2 = dg.dgal_iou_backward(p1.detach(), p2.detach(), w, nx, xf)
+    assert torch.equal(a1, b1) and torch.equal(a2, b2)
+
+
+def test_convex_k8_with_degenerate(dg, orc):
+    """General convex polygons (K=8, counts 3..8) with 5% constructed
+    near-degenerate pairs; FP64 refinement on.  IoU within 1e-5 on every
+    pair (generic and degenerate), flags exact and grads within 1e-3 on
+    generic pairs."""
+    import torch
+
+    d = W.convex_pairs_4m(seed=0, n=200_000)
+    p1, p2, c1, c2 = dev(d["p1"]), dev(d["p2"]), dev(d["c1"]), dev(d["c2"])
+    iou, nx, xf, degen = dg.dgal_iou_paired(p1, p2, c1, c2, with_degen=True)
+    ref = orc.iou_paired(d["p1"], d["p2"], d["c1"], d["c2"], threads=THREADS)
+    gen = check_forward(host(iou), host(nx), host(xf), host(degen), ref, "convex K=8")
+    kind = d["kind"]
+    hd = host(degen)
+    assert (hd[kind > 0] & 1).all(), "every constructed degenerate pair is flagged"
+    assert (hd[kind > 0] & 2).all(), "and refined in FP64"
+    grad = torch.ones(p1.shape[0], device="cuda")
+    g1, g2 = dg.dgal_iou_backward(p1, p2, grad, nx, xf, c1, c2)
+    o1, o2 = orc.iou_backward_paired(d["p1"], d["p2"], np.ones(p1.shape[0]), ref["nx"], ref["xflags"], d["c1"],
+                                     d["c2"], threads=THREADS)
+    rel = grad_rel_err(host(g1), host(g2), o1, o2, gen)
+    assert rel.max() <= GRAD_RTOL, f"K=8 grads: max rel err {rel.max():.3e} at {int(np.nonzero(gen)[0][rel.argmax()])}"
+    # padded slots get exactly zero gradient
+    cnt1 = d["c1"].astype(int)
+    pad = np.arange(8)[None, :] >= cnt1[:, None]
+    assert (host(g1)[pad] == 0).all()
+    assert dg.dgal_get_device_status() == 0
+
+
+def test_plain_form_generic_parity(dg, orc):
+    """DGAL_PLAIN (FP32 only, recompute backward) matches on generic pairs."""
+    d = W.paired_rect_4096(seed=4)
+    iou, nx, xf, degen = _fwd(dg, d["p1"], d["p2"], flags=dg.DGAL_PLAIN)
+    ref = orc.iou_paired(d["p1"], d["p2"])
+    check_forward(iou, nx, xf, degen, ref, "plain")
+
+
+def test_edge_cases(dg, orc):
+    import torch
+
+    # empty batch: no launch, empty outputs
+    z = torch.zeros((0, 4, 2), device="cuda")
+    iou, nx, xf, _ = dg.dgal_iou_paired(z, z)
+    assert iou.shape == (0,)
+    g1, g2 = dg.dgal_iou_backward(z, z, torch.zeros(0, device="cuda"), nx, xf)
+    assert g1.shape == (0, 4, 2)
+    # identical, disjoint, nested
+    d = W.paired_rect_4096(seed=9, n=300)
+    same, _, _, _ = _fwd(dg, d["p1"], d["p1"])
+    assert np.abs(same - 1).max() <= 1e-6
+    far = d["p2"] + np.float32(100.0)
+    sep, nxs, xfs, _ = _fwd(dg, d["p1"], far)
+    assert (sep == 0).all() and (nxs == 0).all() and (xfs == 0xFF).all()
+
+
+def test_bad_counts_set_status(dg):
+    import torch
+
+    d = W.convex_pairs_4m(seed=1, n=64, degenerate_frac=0)
+    c1 = d["c1"].copy()
+    c1[5] = 2
+    c1[9] = 9
+    dg.dgal_get_device_status(clear=True)
+    iou, nx, xf, _ = dg.dgal_iou_paired(dev(d["p1"]), dev(d["p2"]), dev(c1), dev(d["c2"]))
+    st = dg.dgal_get_device_status(clear=True)
+    assert st & dg.DGAL_DEV_BAD_COUNT
+    h = host(iou)
+    assert h[5] == 0 and h[9] == 0 and host(nx)[5] == 0
+    # corrupted flags in the backward are detected, gradients zeroed, no fault
+    xf2 = xf.clone()
+    nx2 = nx.clone()
+    xf2[0, 0] = 0xC1  # no such code kind
+    nx2[1] = 17        # more than 2K vertices
+    g1, g2 = dg.dgal_iou_backward(dev(d["p1"]), dev(d["p2"]), torch.ones(64, device="cuda"), nx2, xf2,
+                                  dev(d["c1"]), dev(d["c2"]))
+    st = dg.dgal_get_device_status(clear=True)
+    assert st & dg.DGAL_DEV_BAD_FLAGS
+    assert (host(g1)[0] == 0).all() and (host(g1)[1] == 0).all()
