@@ -65,13 +65,13 @@ k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
         if (COUNTS && (n1 < 3 || n1 > K || n2 < 3 || n2 > K)) {
             o.err = kDevBadCount;
             o.nx = 0;
-            o.ai = o.a1 = o.a2 = 0.f;
+            o.iou = o.ai = o.a1 = o.a2 = 0.f;
             o.degen = 0;
             codes_fill<K>(o.codes, ~0ull);
         } else {
             fwd_pair<K, COUNTS>(p1 + k * 2 * K, p2 + k * 2 * K, n1, n2, flags, g, o);
         }
-        iou[k] = iou_of(o.ai, o.a1, o.a2, o.nx);
+        iou[k] = o.iou;
         if (SAVE) {
             nx[k] = (uint8_t)o.nx;
             store_codes<K>(xflags, k, o.codes);
@@ -96,6 +96,7 @@ k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
         }
         float g1x[K], g1y[K], g2x[K], g2y[K];
         uint32_t err = 0;
+        bool done = false;
         if (COUNTS && (n1 < 3 || n1 > K || n2 < 3 || n2 > K)) {
             err = kDevBadCount;
 #pragma unroll
@@ -118,14 +119,31 @@ k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
                 nx = nxs[k];
                 load_codes<K>(xflags, k, codes);
             }
-            err |= bwd_pair<K, COUNTS>(g, __ldg(grad + k), nx, codes, g1x, g1y, g2x, g2y);
-            if (err & kDevBadFlags) {
+            const float gk = __ldg(grad + k);
+            const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
+            if (nx > 2u * K) {
+                err |= kDevBadFlags;
 #pragma unroll
                 for (int v = 0; v < K; ++v) { g1x[v] = g1y[v] = g2x[v] = g2y[v] = 0.f; }
+            } else {
+                const uint32_t e = bwd_pair<K, COUNTS>(g, gk, nx, codes, refine, g1x, g1y, g2x, g2y);
+                if (e == kNeed64) {
+                    err |= bwd_shoelace<K, double>(p1 + k * 2 * K, p2 + k * 2 * K, g.n1, g.n2, gk, nx, codes,
+                                                   g1 + k * 2 * K, g2 + k * 2 * K);
+                    done = true;
+                } else {
+                    err |= e;
+                    if (e & kDevBadFlags) {
+#pragma unroll
+                        for (int v = 0; v < K; ++v) { g1x[v] = g1y[v] = g2x[v] = g2y[v] = 0.f; }
+                    }
+                }
             }
         }
-        store_poly<K>(g1 + k * 2 * K, g1x, g1y);
-        store_poly<K>(g2 + k * 2 * K, g2x, g2y);
+        if (!done) {
+            store_poly<K>(g1 + k * 2 * K, g1x, g1y);
+            store_poly<K>(g2 + k * 2 * K, g2x, g2y);
+        }
         if (err) atomicOr(status, err);
     }
 }
@@ -150,6 +168,7 @@ static void fwd_dispatch(const float* p1, const uint8_t* c1, const float* p2, co
 dgal_status launch_paired_fwd(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
                               int K, float* iou, uint8_t* nx, uint8_t* xflags, uint8_t* degen, uint32_t flags,
                               cudaStream_t s) {
+    if (!device_status_ptr()) return fail(DGAL_ERR_CUDA, "device status word unavailable");
     const bool counts = c1 || c2;
     if (K == 4) {
         if (counts) fwd_dispatch<4, true>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, s);
@@ -176,6 +195,7 @@ static void bwd_dispatch(const float* p1, const uint8_t* c1, const float* p2, co
 dgal_status launch_paired_bwd(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
                               int K, const float* grad, const uint8_t* nx, const uint8_t* xflags, float* g1,
                               float* g2, uint32_t flags, cudaStream_t s) {
+    if (!device_status_ptr()) return fail(DGAL_ERR_CUDA, "device status word unavailable");
     const bool counts = c1 || c2;
     if (K == 4) {
         if (counts) bwd_dispatch<4, true>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, s);

@@ -54,7 +54,7 @@ __device__ __forceinline__ void pw_entry(const float* __restrict__ pa, const flo
     fwd_loaded<K, COUNTS>(px, py, qx, qy, pa, pb, n1, n2, flags, g, o);
     err |= o.err;
     nxo = o.nx;
-    iou = iou_of(o.ai, o.a1, o.a2, o.nx);
+    iou = o.iou;
 }
 
 template <int K, bool COUNTS>
@@ -201,6 +201,7 @@ static void pairwise_dispatch(const float* a, const uint8_t* ca, int64_t N, cons
 
 dgal_status launch_pairwise(const float* a, const uint8_t* ca, int64_t N, const float* b, const uint8_t* cb,
                             int64_t M, int K, float* iou, uint8_t* nx, uint32_t flags, cudaStream_t s) {
+    if (!device_status_ptr()) return fail(DGAL_ERR_CUDA, "device status word unavailable");
     const bool counts = ca || cb;
     if (K == 4) {
         if (counts) pairwise_dispatch<4, true>(a, ca, N, b, cb, M, iou, nx, flags, s);
@@ -225,6 +226,7 @@ static void batched_dispatch(int S, const int64_t* a_off, const int64_t* b_off, 
 dgal_status launch_batched(int S, const int64_t* a_off, const int64_t* b_off, const int64_t* out_off,
                            const float* a, const uint8_t* ca, const float* b, const uint8_t* cb, int K, float* iou,
                            uint8_t* nx, void* ws, uint32_t flags, const BatchedConfig& cfg, cudaStream_t s) {
+    if (!device_status_ptr()) return fail(DGAL_ERR_CUDA, "device status word unavailable");
     uint32_t* counter = static_cast<uint32_t*>(ws);
     int64_t* tile_start = reinterpret_cast<int64_t*>(static_cast<char*>(ws) + 16);
     k_batched_setup<<<1, kSetupThreads, 0, s>>>(S, a_off, b_off, out_off, (int64_t)cfg.tile, counter, tile_start,
