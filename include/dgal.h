@@ -130,6 +130,28 @@ dgal_status dgal_iou_pairwise_batched(int S, const int64_t* a_off, const int64_t
                                       void* stream);
 
 /*
+ * Allocation-free form of dgal_iou_pairwise_batched (the paper has no
+ * counterpart; this is a convenience of this library).  For callers that
+ * cannot allocate device memory when they call: code running while a stream
+ * is captured into a CUDA graph, latency-critical loops where cudaMalloc would
+ * stall the device, plugins whose host framework owns all device memory.
+ * Arguments and results are those of dgal_iou_pairwise_batched without the
+ * workspace: the scratch (queue counter and per-scene tile prefix) is one
+ * fixed device array inside the library, about 33 KB, held by every GPU that
+ * loads the library until the process exits.  At most 4096 scenes per call;
+ * larger S returns DGAL_ERR_WORKSPACE.  No cudaMalloc or cudaFree is called.
+ * The first call on a device looks up that array's device address once
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  All calls share the array and each call re-initialises
+ * it, so calls whose kernels overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.
+ */
+dgal_status dgal_iou_pairwise_batched_noalloc(int S, const int64_t* a_off, const int64_t* b_off,
+                                              const int64_t* out_off, const float* a, const uint8_t* ca,
+                                              const float* b, const uint8_t* cb, int K, float* iou, uint8_t* nx,
+                                              uint32_t flags, void* stream);
+
+/*
  * The plain form of the ragged batch: one pairwise launch per scene with
  * host-side offsets (a_off_h, b_off_h, out_off_h are HOST int64 [S + 1]).
  */

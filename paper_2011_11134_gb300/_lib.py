@@ -38,6 +38,7 @@ _SIG = {
     "dgal_batched_workspace_bytes": (ctypes.c_size_t, [_I, _I]),
     "dgal_iou_pairwise_batched": (_I, [_I, _P, _P, _P, _P, _P, _P, _P, _I, _P, _P, _P, ctypes.c_size_t, _U32, _P]),
     "dgal_iou_pairwise_per_scene": (_I, [_I, _P, _P, _P, _P, _P, _P, _P, _I, _P, _P, _U32, _P]),
+    "dgal_iou_pairwise_batched_noalloc": (_I, [_I, _P, _P, _P, _P, _P, _P, _P, _I, _P, _P, _U32, _P]),
     "dgal_batched_graph_create": (_I, [ctypes.POINTER(_P), _I, _P, _P, _P, _P, _P, _P, _P, _I, _P, _P, _P,
                                        ctypes.c_size_t, _U32]),
     "dgal_graph_launch": (_I, [_P, _P]),
