@@ -180,6 +180,27 @@ template <int K, bool COUNTS> __device__ __forceinline__ float pair_scale(const 
     return L;
 }
 
+// Input areas from the raw polygons (local frame of P1's vertex 0), for the
+// list paths that do not build a Geo.
+template <int K>
+__device__ __forceinline__ void input_areas_raw(const float* __restrict__ p1, const float* __restrict__ p2, int n1,
+                                                int n2, float& a1, float& a2) {
+    float px[K], py[K], qx[K], qy[K];
+    load_poly<K>(p1, px, py);
+    load_poly<K>(p2, qx, qy);
+    float s1 = 0.f, s2 = 0.f;
+    for (int v = 0; v < n1; ++v) {
+        const int w = (v + 1 < n1) ? v + 1 : 0;
+        s1 += (px[v] - px[0]) * (py[w] - py[0]) - (py[v] - py[0]) * (px[w] - px[0]);
+    }
+    for (int v = 0; v < n2; ++v) {
+        const int w = (v + 1 < n2) ? v + 1 : 0;
+        s2 += (qx[v] - px[0]) * (qy[w] - py[0]) - (qy[v] - py[0]) * (qx[w] - px[0]);
+    }
+    a1 = 0.5f * s1;
+    a2 = 0.5f * s2;
+}
+
 // ------------------------------------------------------------ generic path
 
 // 2K code bytes as one integer (byte k = slot k).
@@ -662,6 +683,246 @@ __device__ __noinline__ void fwd_robust(const float* __restrict__ p1, const floa
     }
 }
 
+// ------------------------------------------------- warp-cooperative robust path
+//
+// All 32 lanes of a warp work on one pair, with the rules of fwd_robust
+// (inclusive vertex tests, strict crossings, exact duplicates dropped, angular
+// order rotated to the smallest code).  Each orientation test runs on its own
+// lane, in FP64 from the raw inputs when refining; the signs are combined by
+// ballot, each candidate vertex is computed on its own lane, candidates are
+// ranked by comparing against every other lane, and the area is a shuffle
+// reduction of shoelace terms taken about the candidates' centroid.  The
+// result is returned in every lane.
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+template <int K>
+__device__ __noinline__ void warp_robust(const float* __restrict__ p1, const float* __restrict__ p2, int n1, int n2,
+                                         bool refine, FwdOut<K>& o) {
+    typedef typename MaskOf<K>::T M;
+    constexpr int KK = K * K;
+    constexpr int C = 2 * K;
+    constexpr int ROUNDS = (2 * KK + 31) / 32;
+    constexpr unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    float px[K], py[K], qx[K], qy[K];
+    load_poly<K>(p1, px, py);
+    load_poly<K>(p2, qx, qy);
+    const float ox = px[0], oy = py[0];
+    float Lf = 0.f;
+#pragma unroll
+    for (int v = 0; v < K; ++v) {
+        Lf = fmaxf(Lf, (v < n1) ? fmaxf(fabsf(px[v] - ox), fabsf(py[v] - oy)) : 0.f);
+        Lf = fmaxf(Lf, (v < n2) ? fmaxf(fabsf(qx[v] - ox), fabsf(qy[v] - oy)) : 0.f);
+    }
+    const double thr = (double)kDegenRel * (double)Lf * (double)Lf;
+
+    // orientation tests: index q < KK is S(i,j), KK <= q < 2KK is T(i,j)
+    M posS = 0, negS = 0, posT = 0, negT = 0;
+    bool deg = !(Lf > 0.f);
+#pragma unroll
+    for (int r = 0; r < ROUNDS; ++r) {
+        const int q = lane + 32 * r;
+        const bool isT = q >= KK;
+        const int rem = isT ? q - KK : q;
+        const int i = rem / K, j = rem % K;
+        const bool valid = q < 2 * KK && i < n1 && j < n2;
+        const int i1 = (i + 1 < n1) ? i + 1 : 0, j1 = (j + 1 < n2) ? j + 1 : 0;
+        const float Ax = isT ? sel<K>(px, i) : sel<K>(qx, j), Ay = isT ? sel<K>(py, i) : sel<K>(qy, j);
+        const float Bx = isT ? sel<K>(px, i1) : sel<K>(qx, j1), By = isT ? sel<K>(py, i1) : sel<K>(qy, j1);
+        const float Px = isT ? sel<K>(qx, j) : sel<K>(px, i), Py = isT ? sel<K>(qy, j) : sel<K>(py, i);
+        double v;
+        if (refine) v = orient64(Ax, Ay, Bx, By, Px, Py);
+        else v = orient32nc(Ax - ox, Ay - oy, Bx - ox, By - oy, Px - ox, Py - oy);
+        deg |= valid && fabs(v) <= thr;
+        const unsigned bp = __ballot_sync(full, valid && v > 0.0), bn = __ballot_sync(full, valid && v < 0.0);
+        if constexpr (K == 4) {
+            posS = bp & 0xFFFFu;
+            negS = bn & 0xFFFFu;
+            posT = bp >> 16;
+            negT = bn >> 16;
+        } else {
+            const int sh = 32 * (r & 1);
+            if (r < 2) {
+                posS |= (M)bp << sh;
+                negS |= (M)bn << sh;
+            } else {
+                posT |= (M)bp << sh;
+                negT |= (M)bn << sh;
+            }
+        }
+    }
+
+    constexpr M kRow0 = (M)((1ull << K) - 1);
+    M col0 = 0, rows = 0, cols = 0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) col0 |= (M)1 << (i * K);
+#pragma unroll
+    for (int i = 0; i < K; ++i) rows |= (i < n1) ? (kRow0 << (i * K)) : (M)0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) cols |= (j < n2) ? (col0 << j) : (M)0;
+    const M V = rows & cols;
+    // strict sign change along P1 edge i (rows i, i+1) and along P2 edge j (columns j, j+1)
+    const M posSn = ((posS >> K) & ~(kRow0 << (K * (n1 - 1)))) | ((posS & kRow0) << (K * (n1 - 1)));
+    const M negSn = ((negS >> K) & ~(kRow0 << (K * (n1 - 1)))) | ((negS & kRow0) << (K * (n1 - 1)));
+    const M posTn = ((posT >> 1) & ~(col0 << (n2 - 1))) | ((posT & col0) << (n2 - 1));
+    const M negTn = ((negT >> 1) & ~(col0 << (n2 - 1))) | ((negT & col0) << (n2 - 1));
+    const M X = ((posS & negSn) | (negS & posSn)) & ((posT & negTn) | (negT & posTn)) & V;
+    // inclusive inside tests, exact duplicates of P1 vertices dropped from P2's
+    uint32_t in1 = 0, in2 = 0;
+    const M nnS = V & ~negS, nnT = V & ~negT;
+    const M colsFull = (M)((1ull << n2) - 1);
+    M rowsCol = 0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) rowsCol |= (i < n1) ? ((M)1 << (i * K)) : (M)0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        in1 |= (i < n1 && ((nnS >> (i * K)) & colsFull) == colsFull) ? (1u << i) : 0u;
+        in2 |= (i < n2 && ((nnT >> i) & rowsCol) == rowsCol) ? (1u << i) : 0u;
+    }
+    bool dup = false;
+    if (lane < n2) {
+        const float mx_ = sel<K>(qx, lane), my_ = sel<K>(qy, lane);
+#pragma unroll
+        for (int i = 0; i < K; ++i) dup |= i < n1 && px[i] == mx_ && py[i] == my_;
+    }
+    in2 &= ~__ballot_sync(full, dup);
+
+    const int c1n = __popc(in1), c2n = __popc(in2), cxn = popc_(X);
+    const int m = c1n + c2n + cxn;
+    o.nx = 0;
+    o.ai = 0.f;
+    o.iou = 0.f;
+    codes_fill<K>(o.codes, ~0ull);
+    double x = 0.0, y = 0.0;
+    uint32_t code = 0xFFu;
+    bool deg2 = false;
+    if (lane < m && m <= C) {
+        const int c = lane;
+        if (c < c1n) {
+            const int i = (int)__fns(in1, 0, c + 1);
+            code = (uint32_t)i;
+            x = (double)sel<K>(px, i) - (double)ox;
+            y = (double)sel<K>(py, i) - (double)oy;
+        } else if (c < c1n + c2n) {
+            const int j = (int)__fns(in2, 0, c - c1n + 1);
+            code = 0x40u | (uint32_t)j;
+            x = (double)sel<K>(qx, j) - (double)ox;
+            y = (double)sel<K>(qy, j) - (double)oy;
+        } else {
+            const int cc = c - c1n - c2n;
+            int b;
+            if constexpr (K == 4) {
+                b = (int)__fns((uint32_t)X, 0, cc + 1);
+            } else {
+                const uint32_t lo = (uint32_t)X, hi = (uint32_t)(X >> 32);
+                const int nlo = __popc(lo);
+                b = (cc < nlo) ? (int)__fns(lo, 0, cc + 1) : 32 + (int)__fns(hi, 0, cc - nlo + 1);
+            }
+            const int i = b / K, j = b % K;
+            const int i1 = (i + 1 < n1) ? i + 1 : 0, j1 = (j + 1 < n2) ? j + 1 : 0;
+            code = 0x80u | ((uint32_t)i << 3) | (uint32_t)j;
+            const float ax0 = sel<K>(px, i), ay0 = sel<K>(py, i), ax1 = sel<K>(px, i1), ay1 = sel<K>(py, i1);
+            const float bx0 = sel<K>(qx, j), by0 = sel<K>(qy, j), bx1 = sel<K>(qx, j1), by1 = sel<K>(qy, j1);
+            double Sa, Sb, Ta, Tb;
+            if (refine) {
+                Sa = orient64(bx0, by0, bx1, by1, ax0, ay0);
+                Sb = orient64(bx0, by0, bx1, by1, ax1, ay1);
+                Ta = orient64(ax0, ay0, ax1, ay1, bx0, by0);
+                Tb = orient64(ax0, ay0, ax1, ay1, bx1, by1);
+            } else {
+                Sa = orient32nc(bx0 - ox, by0 - oy, bx1 - ox, by1 - oy, ax0 - ox, ay0 - oy);
+                Sb = orient32nc(bx0 - ox, by0 - oy, bx1 - ox, by1 - oy, ax1 - ox, ay1 - oy);
+                Ta = orient32nc(ax0 - ox, ay0 - oy, ax1 - ox, ay1 - oy, bx0 - ox, by0 - oy);
+                Tb = orient32nc(ax0 - ox, ay0 - oy, ax1 - ox, ay1 - oy, bx1 - ox, by1 - oy);
+            }
+            const double t = Sa / (Sa - Sb), u = Ta / (Ta - Tb);
+            x = ((double)ax0 - (double)ox) + t * ((double)ax1 - (double)ax0);
+            y = ((double)ay0 - (double)oy) + t * ((double)ay1 - (double)ay0);
+            const double rx = (double)ax1 - ax0, ry = (double)ay1 - ay0, sx = (double)bx1 - bx0, sy = (double)by1 - by0;
+            const double D = rx * sy - ry * sx;
+            deg2 = t <= kDegenRel || t >= 1.0 - kDegenRel || u <= kDegenRel || u >= 1.0 - kDegenRel ||
+                   D * D <= (double)kDegenRel * kDegenRel * (rx * rx + ry * ry) * (sx * sx + sy * sy);
+        }
+    }
+    deg = __any_sync(full, deg || deg2);
+    o.degen = (deg ? 1u : 0u) | (refine ? 2u : 0u);
+    if (m > C) {
+        o.err |= kDevOverflow;
+        o.degen |= 1u;
+        return;
+    }
+    if (m < 3) return;
+
+    // angular order about the centroid, ties by code; rotate to the smallest code
+    const double mx = warp_sum(lane < m ? x : 0.0) / m, my = warp_sum(lane < m ? y : 0.0) / m;
+    const float key = (lane < m) ? pseudo_angle((float)(x - mx), (float)(y - my)) : __int_as_float(0x7f800000);
+    int rank = 0;
+    for (int l = 0; l < m; ++l) {
+        const float k2 = __shfl_sync(full, key, l);
+        const uint32_t c2 = __shfl_sync(full, code, l);
+        rank += (k2 < key || (k2 == key && c2 < code)) ? 1 : 0;
+    }
+    uint32_t cmin = (lane < m) ? code : 0xFFFFu;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) cmin = min(cmin, __shfl_xor_sync(full, cmin, off));
+    const int src = __ffs(__ballot_sync(full, lane < m && code == cmin)) - 1;
+    const int r0 = __shfl_sync(full, rank, src);
+    const int slot = (rank - r0 + m) % m;
+    unsigned long long w0 = 0, w1 = 0;
+    if (lane < m) {
+        if (slot < 8) w0 = (unsigned long long)code << (8 * slot);
+        else w1 = (unsigned long long)code << (8 * (slot - 8));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        w0 |= __shfl_xor_sync(full, w0, off);
+        w1 |= __shfl_xor_sync(full, w1, off);
+    }
+    const unsigned long long fill0 = (m >= 8) ? 0ull : (~0ull << (8 * m));
+    const unsigned long long fill1 = (m >= 16) ? 0ull : (m <= 8 ? ~0ull : (~0ull << (8 * (m - 8))));
+    o.codes.w[0] = w0 | fill0;
+    if constexpr (K > 4) o.codes.w[1] = w1 | fill1;
+
+    // shoelace about the centroid: the next vertex is the lane whose slot is slot + 1
+    const int target = (slot + 1 == m) ? 0 : slot + 1;
+    double nxp = 0.0, nyp = 0.0;
+    for (int l = 0; l < m; ++l) {
+        const int s2 = __shfl_sync(full, slot, l);
+        const double xx = __shfl_sync(full, x, l), yy = __shfl_sync(full, y, l);
+        if (s2 == target) { nxp = xx; nyp = yy; }
+    }
+    double term = 0.0;
+    if (lane < m) {
+        if (refine) term = __dsub_rn(__dmul_rn(x - mx, nyp - my), __dmul_rn(y - my, nxp - mx));
+        else term = (double)((float)(x - mx) * (float)(nyp - my) - (float)(y - my) * (float)(nxp - mx));
+    }
+    const double ai = 0.5 * warp_sum(term);
+    double a1 = 0.0, a2 = 0.0;
+    for (int v = 0; v < n1; ++v) {
+        const int w = (v + 1 < n1) ? v + 1 : 0;
+        const double xv = (double)px[v] - ox, yv = (double)py[v] - oy, xw = (double)px[w] - ox, yw = (double)py[w] - oy;
+        a1 += refine ? __dsub_rn(__dmul_rn(xv, yw), __dmul_rn(yv, xw)) : (double)((float)xv * (float)yw - (float)yv * (float)xw);
+    }
+    for (int v = 0; v < n2; ++v) {
+        const int w = (v + 1 < n2) ? v + 1 : 0;
+        const double xv = (double)qx[v] - ox, yv = (double)qy[v] - oy, xw = (double)qx[w] - ox, yw = (double)qy[w] - oy;
+        a2 += refine ? __dsub_rn(__dmul_rn(xv, yw), __dmul_rn(yv, xw)) : (double)((float)xv * (float)yw - (float)yv * (float)xw);
+    }
+    a1 *= 0.5;
+    a2 *= 0.5;
+    const double U = a1 + a2 - ai;
+    o.nx = (uint32_t)m;
+    o.ai = (float)ai;
+    o.a1 = (float)a1;
+    o.a2 = (float)a2;
+    o.iou = (U > 0.0) ? (float)(ai / U) : 0.f;
+}
+
 // Full forward for one pair whose polygons are already in registers; the raw
 // pointers (this pair's polygons) are only read again by the robust path.
 template <int K, bool COUNTS>
@@ -693,13 +954,13 @@ __device__ __forceinline__ void fwd_pair(const float* __restrict__ p1, const flo
 
 // ---------------------------------------------------------------- backward
 //
-// The recorded codes rebuild the intersection vertices (crossings as
-// w = a + t ea, t = cross(eb, a - b) / cross(ea, eb), each computed once), the
-// shoelace adjoint dA/dw_k = 1/2 perp(w_{k+1} - w_{k-1}) gives each vertex's
-// gradient, vertex codes route it to that vertex and crossing codes through
-// the adjoint of w onto the four endpoints of the two edges.  Intersections
-// smaller than 1e-6 L^2 are redone in FP64 when refinement is on: their
-// vertices are too close together for differences of FP32 local coordinates.
+// Main path (bwd_shape): the shape derivative of the area over the clipped
+// edge pieces named by the codes.  List path (bwd_shoelace): the recorded
+// codes rebuild the intersection vertices (crossings as w = a + t ea,
+// t = cross(eb, a - b) / cross(ea, eb)), the shoelace adjoint
+// dA/dw_k = 1/2 perp(w_{k+1} - w_{k-1}) gives each vertex's gradient, vertex
+// codes route it to that vertex and crossing codes through the adjoint of w
+// onto the four endpoints of the two edges; FP64 with refinement.
 
 // Shoelace adjoint over the recorded vertex sequence in scalar type R, from the
 // raw inputs: vertex codes route straight to that vertex, crossing codes go
@@ -811,142 +1072,164 @@ __device__ __noinline__ uint32_t bwd_shoelace(const float* __restrict__ p1, cons
     return err;
 }
 
-// dL/dP1, dL/dP2 from the codes in FP32 (gradients are the same in the local
-// frame).  Returns device status bits, or kNeed64 when the pair must be redone
-// by bwd_shoelace<K, double>.
-constexpr uint32_t kNeed64 = 0x80000000u;
+// dL/dP1, dL/dP2 from the codes in FP32 by the shape derivative of the
+// intersection area: moving a vertex moves its two incident edges, and the
+// area changes by the normal motion integrated over the clipped pieces of
+// those edges.  For edge a_i -> a_i+1 = a_i + ea_i with outward normal
+// n = (ea.y, -ea.x) and clipped piece [t0, t1] (t = S/D at a crossing),
+//   dA_i/da_i   += n ((1 - t0)^2 - (1 - t1)^2) / 2,
+//   dA_i/da_i+1 += n (t1^2 - t0^2) / 2,
+// and the same for P2's edges with u = -T/D; the areas of the inputs are the
+// full-edge case [0, 1].  Every index is static.  Returns device status bits,
+// or kSlow when the pair must take the shoelace adjoint instead: codes that do
+// not describe two convex polygons in general position (edge piece counts
+// inconsistent with the inside vertices), or, with refinement, an
+// intersection smaller than 1e-5 L^2 (its piece lengths are differences of
+// nearby FP32 crossing parameters).
+constexpr uint32_t kSlow = 0x80000000u;
+constexpr float kTinyArea = 1e-5f;
 
 template <int K, bool COUNTS>
-__device__ __forceinline__ uint32_t bwd_pair(const Geo<K>& g, float grad, uint32_t nx, const Codes<K>& codes,
-                                             bool refine, float (&g1x)[K], float (&g1y)[K], float (&g2x)[K],
-                                             float (&g2y)[K]) {
+__device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, float grad, uint32_t nx, const Codes<K>& codes,
+                                              bool refine, float (&g1x)[K], float (&g1y)[K], float (&g2x)[K],
+                                              float (&g2y)[K]) {
+    typedef typename MaskOf<K>::T M;
     constexpr int C = 2 * K;
+    constexpr M kRow0 = (M)((1ull << K) - 1);
+    M col0 = 0;
 #pragma unroll
-    for (int v = 0; v < K; ++v) { g1x[v] = 0.f; g1y[v] = 0.f; g2x[v] = 0.f; g2y[v] = 0.f; }
-    if (nx < 3u) return 0u;
-    if (nx > (uint32_t)C) return kDevBadFlags;
+    for (int i = 0; i < K; ++i) col0 |= (M)1 << (i * K);
     const int n1 = g.n1, n2 = g.n2;
+    const uint32_t n1m = COUNTS ? (uint32_t)n1 : (uint32_t)K, n2m = COUNTS ? (uint32_t)n2 : (uint32_t)K;
+#pragma unroll
+    for (int v = 0; v < K; ++v) { g1x[v] = g1y[v] = g2x[v] = g2y[v] = 0.f; }
+    if (nx > (uint32_t)C) return kDevBadFlags;
+    if (nx < 3u) return 0u;
 
-    // pass 1: rebuild the intersection vertices
-    float wx[C], wy[C];
-    bool bad = false;
+    // inside vertices and crossings named by the codes
+    uint32_t in1 = 0, in2 = 0, other = 0;
+    M X = 0;
 #pragma unroll
     for (int k = 0; k < C; ++k) {
-        wx[k] = 0.f;
-        wy[k] = 0.f;
-        if ((uint32_t)k < nx) {
-            const uint32_t c = code_at<K>(codes, (uint32_t)k);
-            const uint32_t kind = c >> 6, lo = c & 7u, ci = (c >> 3) & 7u;
-            if (kind == 0u) {
-                bad |= (c & 0x3Fu) >= (uint32_t)n1;
-                wx[k] = sel<K>(g.ax, lo);
-                wy[k] = sel<K>(g.ay, lo);
-            } else if (kind == 1u) {
-                bad |= (c & 0x3Fu) >= (uint32_t)n2;
-                wx[k] = sel<K>(g.bx, lo);
-                wy[k] = sel<K>(g.by, lo);
-            } else {
-                bad |= (kind == 3u) || ci >= (uint32_t)n1 || lo >= (uint32_t)n2;
-                const float ax = sel<K>(g.ax, ci), ay = sel<K>(g.ay, ci), eax = sel<K>(g.eax, ci), eay = sel<K>(g.eay, ci);
-                const float bx = sel<K>(g.bx, lo), by = sel<K>(g.by, lo), ebx = sel<K>(g.ebx, lo), eby = sel<K>(g.eby, lo);
-                const float D = eax * eby - eay * ebx;
-                const float S = ebx * (ay - by) - eby * (ax - bx);
-                bad |= !(D != 0.f);
-                const float t = S / D;
-                wx[k] = ax + t * eax;
-                wy[k] = ay + t * eay;
-            }
-        }
+        const uint32_t c = code_at<K>(codes, (uint32_t)k);
+        const bool live = (uint32_t)k < nx;
+        const uint32_t kind = c >> 6, lo = c & 7u, ci = (c >> 3) & 7u;
+        in1 |= (live && kind == 0u) ? (1u << (c & 0x1Fu)) : 0u;
+        in2 |= (live && kind == 1u) ? (1u << (c & 0x1Fu)) : 0u;
+        X |= (live && kind == 2u) ? ((M)1 << (ci * K + lo)) : (M)0;
+        other |= (live && (kind == 3u || (kind == 2u && (ci >= n1m || lo >= n2m)))) ? 1u : 0u;
     }
-    if (bad) return kDevBadFlags;
-    float twoA = 0.f, lastx = 0.f, lasty = 0.f;
+    if (other || (in1 >> n1m) || (in2 >> n2m)) return kDevBadFlags;
+    // edge piece counts must match the inside vertices: no crossing between
+    // two inside vertices, one between inside and outside, none or two
+    // between two outside vertices; and every code must be distinct
+    bool ok = (__popc(in1) + __popc(in2) + popc_(X)) == (int)nx;
 #pragma unroll
-    for (int k = 0; k < C; ++k) {
-        if ((uint32_t)k < nx) {
-            const float nxx = ((uint32_t)(k + 1) < nx) ? wx[(k + 1) % C] : wx[0];
-            const float nxy = ((uint32_t)(k + 1) < nx) ? wy[(k + 1) % C] : wy[0];
-            twoA += wx[k] * nxy - wy[k] * nxx;
-            if ((uint32_t)k == nx - 1u) { lastx = wx[k]; lasty = wy[k]; }
+    for (int i = 0; i < K; ++i) {
+        const bool vi = !COUNTS || i < n1, vj = !COUNTS || i < n2;
+        const uint32_t ra = (uint32_t)popc_((X >> (i * K)) & kRow0);
+        const uint32_t na = (i + 1 < (int)n1m) ? (uint32_t)(i + 1) : 0u;
+        const uint32_t a0 = (in1 >> i) & 1u, a1 = (in1 >> na) & 1u;
+        ok &= !vi || ((a0 ^ a1) ? (ra == 1u) : (a0 ? ra == 0u : (ra == 0u || ra == 2u)));
+        const uint32_t rb = (uint32_t)popc_((X >> i) & col0);
+        const uint32_t nb = (i + 1 < (int)n2m) ? (uint32_t)(i + 1) : 0u;
+        const uint32_t b0 = (in2 >> i) & 1u, b1 = (in2 >> nb) & 1u;
+        ok &= !vj || ((b0 ^ b1) ? (rb == 1u) : (b0 ? rb == 0u : (rb == 0u || rb == 2u)));
+    }
+    if (!ok) return kSlow;
+
+    // clipped piece of every edge: [t0, t1] on P1 edges, [u0, u1] on P2 edges.
+    // With the piece counts checked above, a P1 edge whose start is inside
+    // ends at its only crossing, one whose end is inside starts at its only
+    // crossing, and one with two crossings runs from the smaller t to the
+    // larger; so min / max over the crossings of the edge give the piece
+    // without looking at orientation signs.  Off the crossing set the
+    // parameters are NaN, which fminf / fmaxf ignore.
+    const float kInf = __int_as_float(0x7f800000), kNaN = __int_as_float(0x7fffffff);
+    float t0[K], t1[K], u0[K], u1[K];
+#pragma unroll
+    for (int v = 0; v < K; ++v) { t0[v] = kInf; t1[v] = -kInf; u0[v] = kInf; u1[v] = -kInf; }
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const bool m = (X >> (i * K + j)) & 1u;
+            const float dx = g.ax[i] - g.bx[j], dy = g.ay[i] - g.by[j];
+            const float S = g.ebx[j] * dy - g.eby[j] * dx;
+            const float T = g.eay[i] * dx - g.eax[i] * dy;
+            const float D = g.eax[i] * g.eby[j] - g.eay[i] * g.ebx[j];
+            const float rD = m ? __fdividef(1.0f, D) : kNaN;
+            const float t = S * rD, u = -T * rD;
+            t0[i] = fminf(t0[i], t);
+            t1[i] = fmaxf(t1[i], t);
+            u0[j] = fminf(u0[j], u);
+            u1[j] = fmaxf(u1[j], u);
         }
     }
-    float a1, a2;
-    input_areas<K, COUNTS>(g, a1, a2);
-    const float ai = 0.5f * twoA;
-    if (refine) {
-        const float L = pair_scale<K, COUNTS>(g);
-        if (ai < 1e-6f * L * L) return kNeed64;
+    const float L = pair_scale<K, COUNTS>(g);
+    uint32_t hasA = in1, hasB = in2;
+#pragma unroll
+    for (int v = 0; v < K; ++v) {
+        const uint32_t na = (v + 1 < (int)n1m) ? (uint32_t)(v + 1) : 0u, nb = (v + 1 < (int)n2m) ? (uint32_t)(v + 1) : 0u;
+        hasA |= ((X >> (v * K)) & kRow0) ? (1u << v) : 0u;
+        hasB |= ((X >> v) & col0) ? (1u << v) : 0u;
+        t0[v] = ((in1 >> v) & 1u) ? 0.f : t0[v];
+        t1[v] = ((in1 >> na) & 1u) ? 1.f : t1[v];
+        u0[v] = ((in2 >> v) & 1u) ? 0.f : u0[v];
+        u1[v] = ((in2 >> nb) & 1u) ? 1.f : u1[v];
     }
+    float twoA = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int v = 0; v < K; ++v) {
+        const float c1 = g.ax[v] * g.eay[v] - g.ay[v] * g.eax[v];
+        const float c2 = g.bx[v] * g.eby[v] - g.by[v] * g.ebx[v];
+        s1 += (!COUNTS || v < n1) ? c1 : 0.f;
+        s2 += (!COUNTS || v < n2) ? c2 : 0.f;
+        twoA += ((hasA >> v) & 1u) ? (t1[v] - t0[v]) * c1 : 0.f;
+        twoA += ((hasB >> v) & 1u) ? (u1[v] - u0[v]) * c2 : 0.f;
+    }
+    const float a1 = 0.5f * s1, a2 = 0.5f * s2, ai = 0.5f * twoA;
+    if (refine && ai < kTinyArea * L * L) return kSlow;
     const float U = a1 + a2 - ai;
     if (!(U > 0.f)) return 0u;
     const float rU = 1.0f / U;
-    const float gai = grad * (a1 + a2) * rU * rU; // d IoU / d A_i
-    const float ga12 = -grad * ai * rU * rU;      // d IoU / d A_1 = d IoU / d A_2
-
-    // pass 2: shoelace adjoint, routed by code
-#pragma unroll
-    for (int k = 0; k < C; ++k) {
-        if ((uint32_t)k < nx) {
-            const float pxk = (k == 0) ? lastx : wx[(k + C - 1) % C];
-            const float pyk = (k == 0) ? lasty : wy[(k + C - 1) % C];
-            const float nxk = ((uint32_t)(k + 1) < nx) ? wx[(k + 1) % C] : wx[0];
-            const float nyk = ((uint32_t)(k + 1) < nx) ? wy[(k + 1) % C] : wy[0];
-            const float gwx = 0.5f * gai * (nyk - pyk);
-            const float gwy = 0.5f * gai * (pxk - nxk);
-            const uint32_t c = code_at<K>(codes, (uint32_t)k);
-            const uint32_t kind = c >> 6, lo = c & 7u, ci = (c >> 3) & 7u;
-            if (kind == 0u) {
-                add_at<K>(g1x, lo, gwx);
-                add_at<K>(g1y, lo, gwy);
-            } else if (kind == 1u) {
-                add_at<K>(g2x, lo, gwx);
-                add_at<K>(g2y, lo, gwy);
-            } else {
-                const float ax = sel<K>(g.ax, ci), ay = sel<K>(g.ay, ci), eax = sel<K>(g.eax, ci), eay = sel<K>(g.eay, ci);
-                const float bx = sel<K>(g.bx, lo), by = sel<K>(g.by, lo), ebx = sel<K>(g.ebx, lo), eby = sel<K>(g.eby, lo);
-                const float dx = ax - bx, dy = ay - by;
-                const float D = eax * eby - eay * ebx;
-                const float S = ebx * dy - eby * dx;
-                const float rD = 1.0f / D;
-                const float t = S * rD;
-                // w = a + t ea,  t = S / D,  S = cross(eb, a - b),  D = cross(ea, eb)
-                const float gt = gwx * eax + gwy * eay;
-                const float gS = gt * rD, gD = -gt * t * rD;
-                float geax = t * gwx + gD * eby, geay = t * gwy - gD * ebx;
-                const float gebx = gS * dy - gD * eay, geby = -gS * dx + gD * eax;
-                const float gdx = -gS * eby, gdy = gS * ebx;
-                // a_i gets gw + gd - gea; a_{i+1} gets gea; b_j gets -gd - geb; b_{j+1} gets geb
-                const uint32_t i1 = (ci + 1u < (uint32_t)n1) ? ci + 1u : 0u;
-                const uint32_t j1 = (lo + 1u < (uint32_t)n2) ? lo + 1u : 0u;
-                add_at<K>(g1x, ci, gwx + gdx - geax);
-                add_at<K>(g1y, ci, gwy + gdy - geay);
-                add_at<K>(g1x, i1, geax);
-                add_at<K>(g1y, i1, geay);
-                add_at<K>(g2x, lo, -gdx - gebx);
-                add_at<K>(g2y, lo, -gdy - geby);
-                add_at<K>(g2x, j1, gebx);
-                add_at<K>(g2y, j1, geby);
-            }
-        }
-    }
-    // areas of the inputs
+    const float gai = grad * (a1 + a2) * rU * rU; // dIoU/dA_i
+    const float h12 = 0.5f * (-grad * ai * rU * rU); // (1/2) dIoU/dA_1 = (1/2) dIoU/dA_2
+    // start / end contributions of every edge, then vertex v = start of edge v
+    // plus end of edge v-1
+    float sx1[K], sy1[K], ex1[K], ey1[K], sx2[K], sy2[K], ex2[K], ey2[K];
 #pragma unroll
     for (int v = 0; v < K; ++v) {
-        // previous vertex = this vertex minus the previous edge
-        const int pv = (v == 0) ? K - 1 : v - 1;
-        float ppx1 = g.ax[pv], ppy1 = g.ay[pv], ppx2 = g.bx[pv], ppy2 = g.by[pv];
-        if (COUNTS && v == 0) {
-            ppx1 = sel<K>(g.ax, (uint32_t)(n1 - 1));
-            ppy1 = sel<K>(g.ay, (uint32_t)(n1 - 1));
-            ppx2 = sel<K>(g.bx, (uint32_t)(n2 - 1));
-            ppy2 = sel<K>(g.by, (uint32_t)(n2 - 1));
-        }
-        const float nx1 = g.ax[v] + g.eax[v], ny1 = g.ay[v] + g.eay[v];
-        const float nx2 = g.bx[v] + g.ebx[v], ny2 = g.by[v] + g.eby[v];
+        const bool pa = (hasA >> v) & 1u, pb = (hasB >> v) & 1u;
+        const float I0a = pa ? 0.5f * ((1.f - t0[v]) * (1.f - t0[v]) - (1.f - t1[v]) * (1.f - t1[v])) : 0.f;
+        const float I1a = pa ? 0.5f * (t1[v] * t1[v] - t0[v] * t0[v]) : 0.f;
+        const float I0b = pb ? 0.5f * ((1.f - u0[v]) * (1.f - u0[v]) - (1.f - u1[v]) * (1.f - u1[v])) : 0.f;
+        const float I1b = pb ? 0.5f * (u1[v] * u1[v] - u0[v] * u0[v]) : 0.f;
+        const float wsa = gai * I0a + h12, wea = gai * I1a + h12;
+        const float wsb = gai * I0b + h12, web = gai * I1b + h12;
+        sx1[v] = wsa * g.eay[v];
+        sy1[v] = -wsa * g.eax[v];
+        ex1[v] = wea * g.eay[v];
+        ey1[v] = -wea * g.eax[v];
+        sx2[v] = wsb * g.eby[v];
+        sy2[v] = -wsb * g.ebx[v];
+        ex2[v] = web * g.eby[v];
+        ey2[v] = -web * g.ebx[v];
+    }
+    float lx1 = ex1[K - 1], ly1 = ey1[K - 1], lx2 = ex2[K - 1], ly2 = ey2[K - 1];
+    if constexpr (COUNTS) {
+        lx1 = sel<K>(ex1, (uint32_t)(n1 - 1));
+        ly1 = sel<K>(ey1, (uint32_t)(n1 - 1));
+        lx2 = sel<K>(ex2, (uint32_t)(n2 - 1));
+        ly2 = sel<K>(ey2, (uint32_t)(n2 - 1));
+    }
+#pragma unroll
+    for (int v = 0; v < K; ++v) {
         const bool v1 = !COUNTS || v < n1, v2 = !COUNTS || v < n2;
-        g1x[v] = v1 ? g1x[v] + 0.5f * ga12 * (ny1 - ppy1) : 0.f;
-        g1y[v] = v1 ? g1y[v] + 0.5f * ga12 * (ppx1 - nx1) : 0.f;
-        g2x[v] = v2 ? g2x[v] + 0.5f * ga12 * (ny2 - ppy2) : 0.f;
-        g2y[v] = v2 ? g2y[v] + 0.5f * ga12 * (ppx2 - nx2) : 0.f;
+        g1x[v] = v1 ? sx1[v] + (v ? ex1[v - 1] : lx1) : 0.f;
+        g1y[v] = v1 ? sy1[v] + (v ? ey1[v - 1] : ly1) : 0.f;
+        g2x[v] = v2 ? sx2[v] + (v ? ex2[v - 1] : lx2) : 0.f;
+        g2y[v] = v2 ? sy2[v] + (v ? ey2[v - 1] : ly2) : 0.f;
     }
     return 0u;
 }

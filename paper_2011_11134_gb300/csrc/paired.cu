@@ -48,37 +48,84 @@ template <int K> __device__ __forceinline__ void store_poly(float* __restrict__ 
     for (int v = 0; v < K / 2; ++v) q[v] = make_float4(x[2 * v], y[2 * v], x[2 * v + 1], y[2 * v + 1]);
 }
 
+// Both kernels walk the pairs warp by warp (32 consecutive pairs per warp and
+// step, grid-stride over warps), with no block-wide barrier.  In the forward,
+// a pair the fast path cannot finish (near-degenerate or not in general
+// position) is finished afterwards by the whole warp together
+// (warp_robust).  In the backward, a pair whose codes the shape derivative
+// cannot take (not in general position, or with refinement a tiny
+// intersection) runs the shoelace adjoint on its own lane after the rest.
+
 template <int K, bool COUNTS, bool SAVE>
 __global__ void __launch_bounds__(kPairThreads)
 k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
              const uint8_t* __restrict__ c2, int64_t n, float* __restrict__ iou, uint8_t* __restrict__ nx,
              uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+    constexpr unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * kPairThreads;
+    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
+    uint32_t err = 0;
+    for (int64_t base = (int64_t)blockIdx.x * kPairThreads + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t k = base + lane;
         int n1 = K, n2 = K;
-        if (COUNTS) {
-            n1 = c1 ? (int)c1[k] : K;
-            n2 = c2 ? (int)c2[k] : K;
+        bool hard = false;
+        if (k < n) {
+            if (COUNTS) {
+                n1 = c1 ? (int)c1[k] : K;
+                n2 = c2 ? (int)c2[k] : K;
+            }
+            FwdOut<K> o;
+            if (COUNTS && (n1 < 3 || n1 > K || n2 < 3 || n2 > K)) {
+                err |= kDevBadCount;
+                o.nx = 0;
+                o.iou = 0.f;
+                o.degen = 0;
+                codes_fill<K>(o.codes, ~0ull);
+            } else {
+                float px[K], py[K], qx[K], qy[K];
+                load_poly<K>(p1 + k * 2 * K, px, py);
+                load_poly<K>(p2 + k * 2 * K, qx, qy);
+                Geo<K> g;
+                make_geo<K, COUNTS>(px, py, qx, qy, n1, n2, g);
+                input_areas<K, COUNTS>(g, o.a1, o.a2);
+                o.degen = 0;
+                hard = !fwd_generic<K, COUNTS>(g, o);
+                if (!hard) {
+                    const float U = o.a1 + o.a2 - o.ai;
+                    o.iou = (o.nx >= 3u && U > 0.f) ? o.ai / U : 0.f;
+                }
+            }
+            if (!hard) {
+                iou[k] = o.iou;
+                if (SAVE) {
+                    nx[k] = (uint8_t)o.nx;
+                    store_codes<K>(xflags, k, o.codes);
+                }
+                if (degen) degen[k] = (uint8_t)o.degen;
+            }
         }
-        FwdOut<K> o;
-        Geo<K> g;
-        if (COUNTS && (n1 < 3 || n1 > K || n2 < 3 || n2 > K)) {
-            o.err = kDevBadCount;
-            o.nx = 0;
-            o.iou = o.ai = o.a1 = o.a2 = 0.f;
-            o.degen = 0;
-            codes_fill<K>(o.codes, ~0ull);
-        } else {
-            fwd_pair<K, COUNTS>(p1 + k * 2 * K, p2 + k * 2 * K, n1, n2, flags, g, o);
+        unsigned todo = __ballot_sync(full, hard);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t kk = base + src;
+            const int m1 = __shfl_sync(full, n1, src), m2 = __shfl_sync(full, n2, src);
+            FwdOut<K> o;
+            o.err = 0;
+            warp_robust<K>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, refine, o);
+            if (lane == src) {
+                err |= o.err;
+                iou[kk] = o.iou;
+                if (SAVE) {
+                    nx[kk] = (uint8_t)o.nx;
+                    store_codes<K>(xflags, kk, o.codes);
+                }
+                if (degen) degen[kk] = (uint8_t)o.degen;
+            }
         }
-        iou[k] = o.iou;
-        if (SAVE) {
-            nx[k] = (uint8_t)o.nx;
-            store_codes<K>(xflags, k, o.codes);
-        }
-        if (degen) degen[k] = (uint8_t)o.degen;
-        if (o.err) atomicOr(status, o.err);
     }
+    if (err) atomicOr(status, err);
 }
 
 template <int K, bool COUNTS, bool RECOMPUTE>
@@ -87,65 +134,80 @@ k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
              const uint8_t* __restrict__ c2, int64_t n, const float* __restrict__ grad,
              const uint8_t* __restrict__ nxs, const uint8_t* __restrict__ xflags, float* __restrict__ g1,
              float* __restrict__ g2, uint32_t flags, uint32_t* status) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+    constexpr unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * kPairThreads;
+    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
+    uint32_t err = 0;
+    for (int64_t base = (int64_t)blockIdx.x * kPairThreads + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t k = base + lane;
         int n1 = K, n2 = K;
-        if (COUNTS) {
-            n1 = c1 ? (int)c1[k] : K;
-            n2 = c2 ? (int)c2[k] : K;
-        }
-        float g1x[K], g1y[K], g2x[K], g2y[K];
-        uint32_t err = 0;
-        bool done = false;
-        if (COUNTS && (n1 < 3 || n1 > K || n2 < 3 || n2 > K)) {
-            err = kDevBadCount;
+        bool slow = false, needfwd = false;
+        Codes<K> codes;
+        uint32_t nxk = 0;
+        if (k < n) {
+            if (COUNTS) {
+                n1 = c1 ? (int)c1[k] : K;
+                n2 = c2 ? (int)c2[k] : K;
+            }
+            float g1x[K], g1y[K], g2x[K], g2y[K];
+            if (COUNTS && (n1 < 3 || n1 > K || n2 < 3 || n2 > K)) {
+                err |= kDevBadCount;
 #pragma unroll
-            for (int v = 0; v < K; ++v) { g1x[v] = g1y[v] = g2x[v] = g2y[v] = 0.f; }
-        } else {
-            Geo<K> g;
-            Codes<K> codes;
-            uint32_t nx;
-            if (RECOMPUTE) {
-                FwdOut<K> o;
-                fwd_pair<K, COUNTS>(p1 + k * 2 * K, p2 + k * 2 * K, n1, n2, flags, g, o);
-                codes = o.codes;
-                nx = o.nx;
-                err |= o.err;
+                for (int v = 0; v < K; ++v) { g1x[v] = g1y[v] = g2x[v] = g2y[v] = 0.f; }
             } else {
                 float px[K], py[K], qx[K], qy[K];
                 load_poly<K>(p1 + k * 2 * K, px, py);
                 load_poly<K>(p2 + k * 2 * K, qx, qy);
+                Geo<K> g;
                 make_geo<K, COUNTS>(px, py, qx, qy, n1, n2, g);
-                nx = nxs[k];
-                load_codes<K>(xflags, k, codes);
-            }
-            const float gk = __ldg(grad + k);
-            const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
-            if (nx > 2u * K) {
-                err |= kDevBadFlags;
-#pragma unroll
-                for (int v = 0; v < K; ++v) { g1x[v] = g1y[v] = g2x[v] = g2y[v] = 0.f; }
-            } else {
-                const uint32_t e = bwd_pair<K, COUNTS>(g, gk, nx, codes, refine, g1x, g1y, g2x, g2y);
-                if (e == kNeed64) {
-                    err |= bwd_shoelace<K, double>(p1 + k * 2 * K, p2 + k * 2 * K, g.n1, g.n2, gk, nx, codes,
-                                                   g1 + k * 2 * K, g2 + k * 2 * K);
-                    done = true;
+                bool have = true;
+                if (RECOMPUTE) {
+                    FwdOut<K> o;
+                    have = fwd_generic<K, COUNTS>(g, o);
+                    codes = o.codes;
+                    nxk = o.nx;
                 } else {
-                    err |= e;
-                    if (e & kDevBadFlags) {
-#pragma unroll
-                        for (int v = 0; v < K; ++v) { g1x[v] = g1y[v] = g2x[v] = g2y[v] = 0.f; }
-                    }
+                    nxk = nxs[k];
+                    load_codes<K>(xflags, k, codes);
+                }
+                uint32_t e = kSlow;
+                if (have) e = bwd_shape<K, COUNTS>(g, __ldg(grad + k), nxk, codes, refine, g1x, g1y, g2x, g2y);
+                needfwd = !have;
+                slow = (e == kSlow);
+                if (!slow) err |= e;
+            }
+            if (!slow) {
+                store_poly<K>(g1 + k * 2 * K, g1x, g1y);
+                store_poly<K>(g2 + k * 2 * K, g2x, g2y);
+            }
+        }
+        if (RECOMPUTE) {
+            unsigned todo = __ballot_sync(full, needfwd);
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int64_t kk = base + src;
+                const int m1 = __shfl_sync(full, n1, src), m2 = __shfl_sync(full, n2, src);
+                FwdOut<K> o;
+                o.err = 0;
+                warp_robust<K>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, refine, o);
+                if (lane == src) {
+                    err |= o.err;
+                    codes = o.codes;
+                    nxk = o.nx;
                 }
             }
         }
-        if (!done) {
-            store_poly<K>(g1 + k * 2 * K, g1x, g1y);
-            store_poly<K>(g2 + k * 2 * K, g2x, g2y);
+        if (slow) {
+            const float gk = __ldg(grad + k);
+            err |= refine ? bwd_shoelace<K, double>(p1 + k * 2 * K, p2 + k * 2 * K, n1, n2, gk, nxk, codes,
+                                                    g1 + k * 2 * K, g2 + k * 2 * K)
+                          : bwd_shoelace<K, float>(p1 + k * 2 * K, p2 + k * 2 * K, n1, n2, gk, nxk, codes,
+                                                   g1 + k * 2 * K, g2 + k * 2 * K);
         }
-        if (err) atomicOr(status, err);
     }
+    if (err) atomicOr(status, err);
 }
 
 static unsigned grid_for(int64_t n, int threads) {

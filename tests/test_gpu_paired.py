@@ -53,8 +53,13 @@ def test_paired_rect_backward_saved_and_recompute(dg, orc):
     gen = (ref["degen"] == 0) & ((host(degen) & 1) == 0)
     rel = grad_rel_err(host(g1), host(g2), o1, o2, gen)
     assert rel.max() <= GRAD_RTOL, f"saved-flag grads: max rel err {rel.max():.3e}"
-    # recompute mode reproduces the saved-flag gradients exactly (same arithmetic)
-    assert torch.equal(g1, r1) and torch.equal(g2, r2)
+    # recompute mode agrees with the saved-flag gradients (identical arithmetic
+    # on generic pairs; near-degenerate pairs may take the shoelace adjoint in
+    # one mode and the shape derivative in the other)
+    scale = max(g1.abs().max().item(), g2.abs().max().item())
+    assert (g1 - r1).abs().max().item() <= 1e-5 * scale and (g2 - r2).abs().max().item() <= 1e-5 * scale
+    same = torch.from_numpy(gen).cuda()
+    assert torch.equal(g1[same], r1[same]) and torch.equal(g2[same], r2[same])
 
 
 def test_loss_pairs_full_size(dg, orc):
@@ -125,7 +130,8 @@ def test_autograd_function(dg):
     p1.grad = None
     p2.grad = None
     (dg.iou(p1, p2, recompute=True) * w).sum().backward()
-    assert torch.equal(a1, p1.grad) and torch.equal(a2, p2.grad)
+    scale = max(a1.abs().max().item(), a2.abs().max().item())
+    assert (a1 - p1.grad).abs().max().item() <= 1e-5 * scale and (a2 - p2.grad).abs().max().item() <= 1e-5 * scale
     _, nx, xf, _ = dg.dgal_iou_paired(p1.detach(), p2.detach())
     b1, b2 = dg.dgal_iou_backward(p1.detach(), p2.detach(), w, nx, xf)
     assert torch.equal(a1, b1) and torch.equal(a2, b2)
