@@ -30,8 +30,15 @@ METRIC = "IoU pairs/s fwd+bwd, batched vs plain on one GB300, ≤1e-5 err vs FP6
 UNIT = "pairs/s"
 WORKLOAD = ("paired rotated-rectangle IoU forward+backward (IoU-loss recipe), 1,000,000 pairs, K=4, FP32, "
             "flags saved in the forward and consumed by the backward")
-FWD_BYTES = 2 * 32 + 4 + 1 + 8          # read both polygons, write IoU, nx, xflags
-BWD_BYTES = 2 * 32 + 4 + 1 + 8 + 2 * 32  # read polygons, dL/dIoU, nx, xflags; write both gradients
+WORKLOADS = {
+    "loss1m": WORKLOAD,
+    "rect4096": "paired rotated-rectangle IoU forward+backward, 4096 pairs, K=4, FP32 (L2-resident, launch-bound)",
+    "convex": "paired general convex polygons (hulls of 3-8 points, counts, K=8) forward+backward, 4,000,000 pairs, "
+              "5% constructed near-degenerate, FP64 refinement on",
+    "pairwise2000": "pairwise IoU matrix, 2000 x 2000 bird's-eye boxes (K=4), forward, IoU + nx",
+    "ragged64": "ragged batch, 64 scenes N_i in [50,3000] x M_i in [5,200] (K=4), forward, one persistent launch "
+                "in a CUDA graph vs one launch per scene",
+}
 
 
 def _peaks():
@@ -136,6 +143,81 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def matrix_workload(args):
+    """Forward-only matrix workloads: the 2000 x 2000 pairwise matrix, and the
+    64-scene ragged batch (persistent launch in a CUDA graph; plain = one
+    launch per scene).  Unit: IoU entries/s."""
+    import torch
+
+    import paper_2011_11134_gb300 as dg
+    from paper_2011_11134_gb300 import workloads as W
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, device=dev, dtype=torch.uint8)
+    if args.workload == "pairwise2000":
+        d = W.pairwise_bev_2000(seed=0)
+        a, b = torch.from_numpy(d["a"]).to(dev), torch.from_numpy(d["b"]).to(dev)
+        N, M = a.shape[0], b.shape[0]
+        out = (torch.empty((N, M), device=dev), torch.empty((N, M), device=dev, dtype=torch.uint8))
+        entries = N * M
+        fast = lambda: dg.dgal_iou_pairwise(a, b, out=out)
+        plain = lambda: dg.dgal_iou_pairwise(a, b, out=out, flags=dg.DGAL_PLAIN)
+        launches = 1
+        out_bytes = 5 * entries
+    else:
+        d = W.ragged_scenes_64(seed=0)
+        a, b = torch.from_numpy(d["a"]).to(dev), torch.from_numpy(d["b"]).to(dev)
+        ao, bo, oo = (torch.from_numpy(d[k]).to(dev) for k in ("a_off", "b_off", "out_off"))
+        entries = int(d["out_off"][-1])
+        g = dg.BatchedGraph(a, b, ao, bo, oo, entries)
+        out = (torch.empty(entries, device=dev), torch.empty(entries, device=dev, dtype=torch.uint8))
+        fast = lambda: g.launch()
+        plain = lambda: dg.dgal_iou_pairwise_per_scene(a, b, d["a_off"], d["b_off"], d["out_off"], out=out,
+                                                       flags=dg.DGAL_PLAIN)
+        launches = 2
+        out_bytes = 5 * entries
+    for _ in range(args.warmup):
+        fast()
+        plain()
+    torch.cuda.synchronize(dev)
+
+    def timed(fn):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for s_ in range(args.steps):
+            flush.fill_(s_ & 0xFF)
+            ev[s_][0].record(stream)
+            fn()
+            ev[s_][1].record(stream)
+        torch.cuda.synchronize(dev)
+        return [e0.elapsed_time(e1) for e0, e1 in ev]
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    t_fast = timed(fast)
+    clocks = sampler.stop()
+    t_plain = timed(plain)
+    ms = statistics.mean(t_fast)
+    value = entries / (ms * 1e-3)
+    peaks = _peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    gbs = out_bytes / (ms * 1e-3) / 1e9
+    line = {
+        "metric": "IoU matrix entries/s, forward", "value": value, "unit": "entries/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "entries": entries,
+                   "l2": "flushed between steps (256 MiB write outside the timed events)"},
+        "plain": {"value": entries / (statistics.mean(t_plain) * 1e-3), "unit": "entries/s",
+                  "ms_per_step": statistics.mean(t_plain)},
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                     "traffic": None, "alg_bytes_per_entry": 5},
+        "gpu_launches": launches * args.steps, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -145,10 +227,15 @@ def main():
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--ref-sample", type=int, default=200_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="loss1m", choices=["loss1m", "rect4096", "convex", "pairwise2000", "ragged64"],
+                    help="loss1m (default) is the headline line; the others measure the remaining workloads")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.workload in ("pairwise2000", "ragged64"):
+        matrix_workload(args)
         return
 
     import torch
@@ -162,14 +249,22 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    n = args.n
-    d = W.loss_pairs_1m(seed=rank, n=n)
+    if args.workload == "rect4096":
+        d = W.paired_rect_4096(seed=rank)
+    elif args.workload == "convex":
+        d = W.convex_pairs_4m(seed=rank, n=args.n if args.n != 1_000_000 else 4_000_000)
+    else:
+        d = W.loss_pairs_1m(seed=rank, n=args.n)
+    n = d["p1"].shape[0]
+    K = d["p1"].shape[1]
     p1 = torch.from_numpy(d["p1"]).to(dev)
     p2 = torch.from_numpy(d["p2"]).to(dev)
+    c1 = torch.from_numpy(d["c1"]).to(dev) if "c1" in d else None
+    c2 = torch.from_numpy(d["c2"]).to(dev) if "c2" in d else None
     grad = torch.ones(n, device=dev)
     iou = torch.empty(n, device=dev)
     nx = torch.empty(n, device=dev, dtype=torch.uint8)
-    xf = torch.empty((n, 8), device=dev, dtype=torch.uint8)
+    xf = torch.empty((n, 2 * K), device=dev, dtype=torch.uint8)
     g1 = torch.empty_like(p1)
     g2 = torch.empty_like(p2)
     flush = torch.empty(256 << 20, device=dev, dtype=torch.uint8)
@@ -180,22 +275,22 @@ def main():
     FLAGS = dg.DGAL_FP64_REFINE
 
     def fwd():
-        st = lib.dgal_iou_paired(L.ptr(p1), None, L.ptr(p2), None, n, 4, L.ptr(iou), L.ptr(nx), L.ptr(xf), None,
+        st = lib.dgal_iou_paired(L.ptr(p1), L.ptr(c1), L.ptr(p2), L.ptr(c2), n, K, L.ptr(iou), L.ptr(nx), L.ptr(xf), None,
                                  FLAGS, sp)
         assert st == 0, dg.dgal_last_error()
 
     def bwd():
-        st = lib.dgal_iou_backward(L.ptr(p1), None, L.ptr(p2), None, n, 4, L.ptr(grad), L.ptr(nx), L.ptr(xf),
+        st = lib.dgal_iou_backward(L.ptr(p1), L.ptr(c1), L.ptr(p2), L.ptr(c2), n, K, L.ptr(grad), L.ptr(nx), L.ptr(xf),
                                    L.ptr(g1), L.ptr(g2), FLAGS, sp)
         assert st == 0, dg.dgal_last_error()
 
     def fwd_plain():
-        st = lib.dgal_iou_paired(L.ptr(p1), None, L.ptr(p2), None, n, 4, L.ptr(iou), None, None, None,
+        st = lib.dgal_iou_paired(L.ptr(p1), L.ptr(c1), L.ptr(p2), L.ptr(c2), n, K, L.ptr(iou), None, None, None,
                                  dg.DGAL_PLAIN, sp)
         assert st == 0, dg.dgal_last_error()
 
     def bwd_plain():
-        st = lib.dgal_iou_backward(L.ptr(p1), None, L.ptr(p2), None, n, 4, L.ptr(grad), None, None, L.ptr(g1),
+        st = lib.dgal_iou_backward(L.ptr(p1), L.ptr(c1), L.ptr(p2), L.ptr(c2), n, K, L.ptr(grad), None, None, L.ptr(g1),
                                    L.ptr(g2), dg.DGAL_PLAIN, sp)
         assert st == 0, dg.dgal_last_error()
 
@@ -247,9 +342,11 @@ def main():
 
         idx = np.random.Generator(np.random.PCG64(7)).choice(n, size=min(n, 20000), replace=False)
         idx.sort()
-        ref = oracle.iou_paired(d["p1"][idx], d["p2"][idx], threads=os.cpu_count() or 1)
+        sc1 = d["c1"][idx] if "c1" in d else None
+        sc2 = d["c2"][idx] if "c2" in d else None
+        ref = oracle.iou_paired(d["p1"][idx], d["p2"][idx], sc1, sc2, threads=os.cpu_count() or 1)
         r1, r2 = oracle.iou_backward_paired(d["p1"][idx], d["p2"][idx], np.ones(len(idx)), ref["nx"],
-                                            ref["xflags"], threads=os.cpu_count() or 1)
+                                            ref["xflags"], sc1, sc2, threads=os.cpu_count() or 1)
         gi = iou.cpu().numpy()[idx].astype(np.float64)
         G = np.concatenate([g1.cpu().numpy()[idx], g2.cpu().numpy()[idx]], 1).astype(np.float64)
         R = np.concatenate([r1, r2], 1)
@@ -269,14 +366,14 @@ def main():
     h_p2 = torch.from_numpy(d["p2"]).pin_memory()
     h_grad = torch.ones(n).pin_memory()
     h_iou = torch.empty(n).pin_memory()
-    h_g1 = torch.empty((n, 4, 2)).pin_memory()
-    h_g2 = torch.empty((n, 4, 2)).pin_memory()
+    h_g1 = torch.empty((n, K, 2)).pin_memory()
+    h_g2 = torch.empty((n, K, 2)).pin_memory()
     for _ in range(2):
         a1 = h_p1.to(dev, non_blocking=True)
         a2 = h_p2.to(dev, non_blocking=True)
         gg = h_grad.to(dev, non_blocking=True)
-        iv, nv, xv, _ = dg.dgal_iou_paired(a1, a2)
-        o1, o2 = dg.dgal_iou_backward(a1, a2, gg, nv, xv)
+        iv, nv, xv, _ = dg.dgal_iou_paired(a1, a2, c1, c2)
+        o1, o2 = dg.dgal_iou_backward(a1, a2, gg, nv, xv, c1, c2)
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -285,8 +382,8 @@ def main():
         a1 = h_p1.to(dev, non_blocking=True)
         a2 = h_p2.to(dev, non_blocking=True)
         gg = h_grad.to(dev, non_blocking=True)
-        iv, nv, xv, _ = dg.dgal_iou_paired(a1, a2)
-        o1, o2 = dg.dgal_iou_backward(a1, a2, gg, nv, xv)
+        iv, nv, xv, _ = dg.dgal_iou_paired(a1, a2, c1, c2)
+        o1, o2 = dg.dgal_iou_backward(a1, a2, gg, nv, xv, c1, c2)
         h_iou.copy_(iv, non_blocking=True)
         h_g1.copy_(o1, non_blocking=True)
         h_g2.copy_(o2, non_blocking=True)
@@ -294,8 +391,8 @@ def main():
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1)
     e2e_value = n * world * args.steps / (e2e_ms / 1e3)
-    h2d = 2 * n * 32 + 4 * n
-    d2h = 4 * n + 2 * n * 32
+    h2d = 2 * n * 8 * K + 4 * n
+    d2h = 4 * n + 2 * n * 8 * K
 
     if rank != 0:
         if world > 1:
@@ -306,17 +403,20 @@ def main():
     peaks = _peaks()
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
     fw_ms, bw_ms = statistics.mean(fw), statistics.mean(bw)
-    fw_gbs = FWD_BYTES * n / (fw_ms * 1e-3) / 1e9
-    bw_gbs = BWD_BYTES * n / (bw_ms * 1e-3) / 1e9
+    cb = 2 if c1 is not None else 0  # count bytes read per pair
+    fwd_bytes = 2 * 8 * K + cb + 4 + 1 + 2 * K
+    bwd_bytes = 2 * 8 * K + cb + 4 + 1 + 2 * K + 2 * 8 * K
+    fw_gbs = fwd_bytes * n / (fw_ms * 1e-3) / 1e9
+    bw_gbs = bwd_bytes * n / (bw_ms * 1e-3) / 1e9
     dom = "forward" if fw_ms >= bw_ms else "backward"
     ach = fw_gbs if dom == "forward" else bw_gbs
-    roofline = {"bound": "hbm", "kernel": f"k_paired_{'fwd' if dom == 'forward' else 'bwd'}<4>", "achieved": ach,
+    roofline = {"bound": "hbm", "kernel": f"k_paired_{'fwd' if dom == 'forward' else 'bwd'}<{K}>", "achieved": ach,
                 "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
-                "per_kernel": {"forward": {"ms": fw_ms, "alg_bytes_per_pair": FWD_BYTES, "GB_s": fw_gbs},
-                               "backward": {"ms": bw_ms, "alg_bytes_per_pair": BWD_BYTES, "GB_s": bw_gbs}}}
+                "per_kernel": {"forward": {"ms": fw_ms, "alg_bytes_per_pair": fwd_bytes, "GB_s": fw_gbs},
+                               "backward": {"ms": bw_ms, "alg_bytes_per_pair": bwd_bytes, "GB_s": bw_gbs}}}
     cpu = None
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and args.workload == "loss1m":
         threads = os.cpu_count() or 1
         sample = min(n, args.ref_sample)
         ds = {k: v[:sample] for k, v in d.items()}
@@ -328,8 +428,9 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "pairs_per_gpu": n, "K": 4, "parallelism": f"replicas x{world}",
-                   "l2": "flushed between steps (256 MiB write outside the timed events); inputs 64 MB"},
+        "config": {"workload": WORKLOADS[args.workload], "pairs_per_gpu": n, "K": K,
+                   "parallelism": f"replicas x{world}",
+                   "l2": f"flushed between steps (256 MiB write outside the timed events); inputs {2 * n * 8 * K / 1e6:.0f} MB"},
         "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": plain_ms / args.steps,
                   "form": "FP32 only, no saved flags, backward recomputes the clip",
                   "batched_over_plain": value / plain_value},
