@@ -161,6 +161,7 @@ def matrix_workload(args):
         N, M = a.shape[0], b.shape[0]
         out = (torch.empty((N, M), device=dev), torch.empty((N, M), device=dev, dtype=torch.uint8))
         entries = N * M
+        tuned = None
         fast = lambda: dg.dgal_iou_pairwise(a, b, out=out)
         plain = lambda: dg.dgal_iou_pairwise(a, b, out=out, flags=dg.DGAL_PLAIN)
         launches = 1
@@ -170,6 +171,7 @@ def matrix_workload(args):
         a, b = torch.from_numpy(d["a"]).to(dev), torch.from_numpy(d["b"]).to(dev)
         ao, bo, oo = (torch.from_numpy(d[k]).to(dev) for k in ("a_off", "b_off", "out_off"))
         entries = int(d["out_off"][-1])
+        tuned = dg.dgal_autotune(4)  # untimed: picks entries per tile, threads per block, blocks per SM
         g = dg.BatchedGraph(a, b, ao, bo, oo, entries)
         out = (torch.empty(entries, device=dev), torch.empty(entries, device=dev, dtype=torch.uint8))
         fast = lambda: g.launch()
@@ -215,6 +217,77 @@ def matrix_workload(args):
                      "traffic": None, "alg_bytes_per_entry": 5},
         "gpu_launches": launches * args.steps, "clocks": clocks,
     }
+    if args.workload == "ragged64":
+        line["config"]["autotuned"] = tuned
+    print(json.dumps(line), flush=True)
+
+
+def fused_workload(args):
+    """The 1M-pair IoU-loss workload through the fused kernel: loss and both
+    gradients in one pass (unit: pairs/s, forward + backward)."""
+    import torch
+
+    import paper_2011_11134_gb300 as dg
+    from paper_2011_11134_gb300 import workloads as W
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    d = W.loss_pairs_1m(seed=0, n=args.n)
+    n = d["p1"].shape[0]
+    p1, p2 = torch.from_numpy(d["p1"]).to(dev), torch.from_numpy(d["p2"]).to(dev)
+    ws = torch.empty(dg.dgal_iou_loss_workspace_bytes(n), device=dev, dtype=torch.uint8)
+    out = (torch.empty(1, device=dev), torch.empty_like(p1), torch.empty_like(p2), None)
+    flush = torch.empty(256 << 20, device=dev, dtype=torch.uint8)
+    run = lambda: dg.dgal_iou_loss(p1, p2, None, 1.0 / n, workspace=ws, out=out)
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    for s_ in range(args.steps):
+        flush.fill_(s_ & 0xFF)
+        ev[s_][0].record(stream)
+        run()
+        ev[s_][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
+    # the same loss through the separate forward and backward calls
+    g_iou = torch.full((n,), -1.0 / n, device=dev)
+
+    def unfused():
+        iv, nx, xf, _ = dg.dgal_iou_paired(p1, p2)
+        dg.dgal_iou_backward(p1, p2, g_iou, nx, xf)
+        return (1.0 - iv).sum() / n
+
+    for _ in range(args.warmup):
+        unfused()
+    torch.cuda.synchronize(dev)
+    for s_ in range(args.steps):
+        flush.fill_(s_ & 0xFF)
+        ev[s_][0].record(stream)
+        unfused()
+        ev[s_][1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms_unfused = statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
+    peaks = _peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    alg = 64 + 64  # read both polygons, write both gradients
+    gbs = alg * n / (ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": n / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "fused IoU loss (mean of 1 - IoU) forward+backward in one kernel, 1,000,000 pairs, K=4",
+                   "l2": "flushed between steps"},
+        "roofline": {"bound": "hbm", "kernel": "k_iou_loss4", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                     "frac": gbs / hbm, "traffic": None, "alg_bytes_per_pair": alg},
+        "unfused": {"value": n / (ms_unfused * 1e-3), "unit": UNIT, "ms_per_step": ms_unfused,
+                    "what": "dgal_iou_paired + torch sum + dgal_iou_backward"},
+        "gpu_launches": 2 * args.steps, "clocks": clocks,
+    }
     print(json.dumps(line), flush=True)
 
 
@@ -227,7 +300,8 @@ def main():
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--ref-sample", type=int, default=200_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="loss1m", choices=["loss1m", "rect4096", "convex", "pairwise2000", "ragged64"],
+    ap.add_argument("--workload", default="loss1m",
+                    choices=["loss1m", "rect4096", "convex", "pairwise2000", "ragged64", "fused1m"],
                     help="loss1m (default) is the headline line; the others measure the remaining workloads")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -237,24 +311,29 @@ def main():
     if args.workload in ("pairwise2000", "ragged64"):
         matrix_workload(args)
         return
+    if args.workload == "fused1m":
+        fused_workload(args)
+        return
 
     import torch
     import torch.distributed as dist
 
     import paper_2011_11134_gb300 as dg
     from paper_2011_11134_gb300 import workloads as W
+    from paper_2011_11134_gb300.replicas import max_over_ranks, replica_seed
 
     rank, world, local = _dist_env()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    seed = replica_seed(rank)  # weak scaling: every replica runs its own seeded workload
     if args.workload == "rect4096":
-        d = W.paired_rect_4096(seed=rank)
+        d = W.paired_rect_4096(seed=seed)
     elif args.workload == "convex":
-        d = W.convex_pairs_4m(seed=rank, n=args.n if args.n != 1_000_000 else 4_000_000)
+        d = W.convex_pairs_4m(seed=seed, n=args.n if args.n != 1_000_000 else 4_000_000)
     else:
-        d = W.loss_pairs_1m(seed=rank, n=args.n)
+        d = W.loss_pairs_1m(seed=seed, n=args.n)
     n = d["p1"].shape[0]
     K = d["p1"].shape[1]
     p1 = torch.from_numpy(d["p1"]).to(dev)
@@ -329,10 +408,7 @@ def main():
     clocks = sampler.stop()
     step_ms = [a + b for a, b in zip(fw, bw)]
     total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dev)
     value = n * world * args.steps / (total_ms / 1e3)
 
     # parity of the timed outputs on a sample (FP64 oracle)
@@ -355,6 +431,12 @@ def main():
         flags_ok = bool(((xf.cpu().numpy()[idx] == ref["xflags"]).all(1) | ~gen).all())
         err = {"iou_max_abs": float(np.abs(gi - ref["iou"]).max()), "grad_max_rel": float(rel[gen].max()),
                "xflags_bit_exact_generic": flags_ok, "sample_pairs": int(len(idx))}
+        if "kind" in d:
+            kd = d["kind"][idx] > 0
+            ie = np.abs(gi - ref["iou"])
+            err["iou_max_abs_constructed_degenerate"] = float(ie[kd].max()) if kd.any() else None
+            err["iou_max_abs_other"] = float(ie[~kd].max())
+            err["constructed_degenerate_in_sample"] = int(kd.sum())
 
     # plain form on the same pairs
     pfw, pbw = timed(args.steps, fwd_plain, bwd_plain)

@@ -104,6 +104,23 @@ dgal_status dgal_iou_backward(const float* p1, const uint8_t* c1, const float* p
                               float* grad_p1, float* grad_p2, uint32_t flags, void* stream);
 
 /*
+ * Fused IoU loss, forward and backward in one pass (the rotated-box IoU-loss
+ * use of the library, paper Sec. IV-A):
+ *   loss[0] = scale * sum_k w_k (1 - IoU(p1[k], p2[k]))      (w = NULL: all 1)
+ *   grad_p1, grad_p2 = d loss / d p1, d p2  (float [n][K][2]; both NULL to skip)
+ *   iou (float [n], optional) receives the IoUs.
+ * K = 4 only.  No flags are stored: each pair's intersection state goes from
+ * the clip straight into the backward.  The loss is reduced per block into
+ * `workspace` (at least dgal_iou_loss_workspace_bytes(n, K) bytes, 16-byte
+ * aligned) and then summed in a fixed order, so it is deterministic.
+ * n = 0 writes loss[0] = 0.
+ */
+size_t dgal_iou_loss_workspace_bytes(int64_t n, int K);
+dgal_status dgal_iou_loss(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n, int K,
+                          const float* weight, float scale, float* loss, float* iou, float* grad_p1, float* grad_p2,
+                          void* workspace, size_t ws_bytes, uint32_t flags, void* stream);
+
+/*
  * Pairwise IoU matrix (the `iou` operation over all N x M pairs):
  *   iou[i*M + j] = IoU(a[i], b[j]), nx[i*M + j] likewise (nx may be NULL).
  * a: float [N][K][2], b: float [M][K][2]; ca, cb counts or NULL.

@@ -191,3 +191,15 @@ def _run_parallel(fn, ranges):
     # ctypes releases the GIL during the foreign call, so threads use all cores.
     with ThreadPoolExecutor(max_workers=len(ranges)) as ex:
         list(ex.map(fn, ranges))
+
+
+def iou_loss(p1, p2, weight=None, scale=1.0, c1=None, c2=None, threads: int = 1):
+    """IoU loss of the paper's case study (Sec. IV-A) in FP64:
+    loss = scale * sum_k w_k (1 - IoU_k), and its gradient, i.e. the pinned
+    backward with dL/dIoU_k = -scale w_k.  Returns (loss, g1, g2, forward dict)."""
+    n = np.asarray(p1).shape[0]
+    w = np.ones(n) if weight is None else np.asarray(weight, dtype=np.float64)
+    f = iou_paired(p1, p2, c1, c2, threads=threads)
+    loss = float(scale * np.sum(w * (1.0 - f["iou"])))
+    g1, g2 = iou_backward_paired(p1, p2, -scale * w, f["nx"], f["xflags"], c1, c2, threads=threads)
+    return loss, g1, g2, f

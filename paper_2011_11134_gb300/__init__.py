@@ -32,6 +32,7 @@ from ._lib import (DGAL_DEV_BAD_COUNT, DGAL_DEV_BAD_FLAGS, DGAL_DEV_BAD_OFFSETS,
 __all__ = [
     "dgal_iou_paired", "dgal_iou_backward", "dgal_iou_pairwise", "dgal_iou_pairwise_batched",
     "dgal_iou_pairwise_per_scene", "dgal_batched_workspace_bytes", "BatchedGraph", "dgal_autotune",
+    "dgal_iou_loss", "dgal_iou_loss_workspace_bytes", "IoULoss", "iou_loss",
     "dgal_get_batched_config", "dgal_get_device_status", "dgal_last_error", "dgal_version", "IoU", "iou",
     "DGAL_FP64_REFINE", "DGAL_PLAIN", "DGAL_DEV_BAD_COUNT", "DGAL_DEV_OVERFLOW", "DGAL_DEV_BAD_FLAGS",
     "DGAL_DEV_BAD_OFFSETS", "DgalError",
@@ -98,6 +99,38 @@ def dgal_iou_backward(p1, p2, grad_iou, nx=None, xflags=None, c1=None, c2=None, 
               _lib.ptr(grad_iou), _lib.ptr(nx), _lib.ptr(xflags), _lib.ptr(g1), _lib.ptr(g2), flags,
               _lib.stream_ptr(stream))
     return g1, g2
+
+
+def dgal_iou_loss_workspace_bytes(n, K=4):
+    return int(_lib.lib().dgal_iou_loss_workspace_bytes(n, K))
+
+
+def dgal_iou_loss(p1, p2, weight=None, scale=1.0, c1=None, c2=None, grads=True, with_iou=False,
+                  flags=DGAL_FP64_REFINE, stream=None, workspace=None, out=None):
+    """Fused IoU loss: returns (loss [1], g1 | None, g2 | None, iou | None) with
+    loss = scale * sum w (1 - IoU) and g = d loss / d p."""
+    _poly(p1, "p1")
+    _poly(p2, "p2")
+    if p1.shape != p2.shape:
+        raise ValueError("p1 and p2 must have the same shape")
+    n, K = p1.shape[0], p1.shape[1]
+    c1 = _counts(c1, n, "c1", p1.device)
+    c2 = _counts(c2, n, "c2", p1.device)
+    if weight is not None and (weight.dtype != torch.float32 or weight.shape != (n,) or not weight.is_contiguous()):
+        raise ValueError("weight must be a contiguous float32 tensor of shape (n,)")
+    if workspace is None:
+        workspace = torch.empty(max(dgal_iou_loss_workspace_bytes(n, K), 16), device=p1.device, dtype=torch.uint8)
+    if out is None:
+        loss = torch.empty(1, device=p1.device, dtype=torch.float32)
+        g1 = torch.empty_like(p1) if grads else None
+        g2 = torch.empty_like(p2) if grads else None
+        iou = torch.empty(n, device=p1.device, dtype=torch.float32) if with_iou else None
+    else:
+        loss, g1, g2, iou = out
+    _lib.call("dgal_iou_loss", _lib.ptr(p1), _lib.ptr(c1), _lib.ptr(p2), _lib.ptr(c2), n, K, _lib.ptr(weight),
+              float(scale), _lib.ptr(loss), _lib.ptr(iou), _lib.ptr(g1), _lib.ptr(g2), _lib.ptr(workspace),
+              workspace.numel(), flags, _lib.stream_ptr(stream))
+    return loss, g1, g2, iou
 
 
 def dgal_iou_pairwise(a, b, ca=None, cb=None, with_nx=True, flags=DGAL_FP64_REFINE, stream=None, out=None):
@@ -268,3 +301,30 @@ class IoU(torch.autograd.Function):
 def iou(p1, p2, c1=None, c2=None, recompute=False, flags=DGAL_FP64_REFINE):
     """Differentiable paired IoU (see ``IoU``)."""
     return IoU.apply(p1, p2, c1, c2, recompute, flags)
+
+
+class IoULoss(torch.autograd.Function):
+    """loss = scale * sum w (1 - IoU) with the fused kernel: the forward pass
+    already computes d loss / d p, and the backward only scales it by the
+    incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, p1, p2, weight=None, scale=1.0, c1=None, c2=None, flags=DGAL_FP64_REFINE):
+        need = p1.requires_grad or p2.requires_grad
+        loss, g1, g2, _ = dgal_iou_loss(p1.contiguous(), p2.contiguous(), weight, scale, c1, c2, grads=need,
+                                        flags=flags)
+        ctx.save_for_backward(g1, g2)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, grad):
+        g1, g2 = ctx.saved_tensors
+        return (None if g1 is None else g1 * grad, None if g2 is None else g2 * grad, None, None, None, None, None)
+
+
+def iou_loss(p1, p2, weight=None, reduction="sum", c1=None, c2=None, flags=DGAL_FP64_REFINE):
+    """Differentiable IoU loss sum_k w_k (1 - IoU_k) (or its mean over pairs)."""
+    if reduction not in ("sum", "mean"):
+        raise ValueError("reduction must be 'sum' or 'mean'")
+    scale = 1.0 / max(p1.shape[0], 1) if reduction == "mean" else 1.0
+    return IoULoss.apply(p1, p2, weight, scale, c1, c2, flags)

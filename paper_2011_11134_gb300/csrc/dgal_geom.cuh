@@ -14,9 +14,10 @@
 //     contributes cross(start, end), its endpoints being polygon vertices or
 //     crossing points a_i + t ea_i (t = S/D, D = cross(ea_i, eb_j)), so no
 //     vertex ordering is needed for it.
-//   Near-degenerate pairs, and pairs whose walk does not close, take a
-//   separate robust path (candidate gathering and an angular sort; with
-//   refinement, FP64 orientation tests, crossing parameters and areas).
+//   Near-degenerate pairs, and pairs whose sign pattern is not that of two
+//   convex polygons in general position, take the warp-cooperative robust
+//   path (candidate gathering and an angular sort; with refinement, FP64
+//   orientation tests, crossing parameters and areas).
 //
 // Backward (paper Sec. II-B `iou_grad`): the recorded codes rebuild the
 // intersection vertices (crossings as a + t ea), the shoelace adjoint gives
@@ -88,11 +89,6 @@ template <int K> __device__ __forceinline__ float sel(const float (&a)[K], uint3
 #pragma unroll
     for (int m = 1; m < K; ++m) r = (idx == (uint32_t)m) ? a[m] : r;
     return r;
-}
-
-template <int K> __device__ __forceinline__ void add_at(float (&a)[K], uint32_t idx, float v) {
-#pragma unroll
-    for (int m = 0; m < K; ++m) a[m] += (idx == (uint32_t)m) ? v : 0.0f;
 }
 
 // Polygon loads: K x (x, y) as K/2 128-bit loads (16-byte aligned rows).
@@ -178,27 +174,6 @@ template <int K, bool COUNTS> __device__ __forceinline__ float pair_scale(const 
         L = fmaxf(L, (!COUNTS || v < g.n2) ? lb : 0.f);
     }
     return L;
-}
-
-// Input areas from the raw polygons (local frame of P1's vertex 0), for the
-// list paths that do not build a Geo.
-template <int K>
-__device__ __forceinline__ void input_areas_raw(const float* __restrict__ p1, const float* __restrict__ p2, int n1,
-                                                int n2, float& a1, float& a2) {
-    float px[K], py[K], qx[K], qy[K];
-    load_poly<K>(p1, px, py);
-    load_poly<K>(p2, qx, qy);
-    float s1 = 0.f, s2 = 0.f;
-    for (int v = 0; v < n1; ++v) {
-        const int w = (v + 1 < n1) ? v + 1 : 0;
-        s1 += (px[v] - px[0]) * (py[w] - py[0]) - (py[v] - py[0]) * (px[w] - px[0]);
-    }
-    for (int v = 0; v < n2; ++v) {
-        const int w = (v + 1 < n2) ? v + 1 : 0;
-        s2 += (qx[v] - px[0]) * (qy[w] - py[0]) - (qy[v] - py[0]) * (qx[w] - px[0]);
-    }
-    a1 = 0.5f * s1;
-    a2 = 0.5f * s2;
 }
 
 // ------------------------------------------------------------ generic path
@@ -469,225 +444,11 @@ __device__ __forceinline__ float pseudo_angle(float dx, float dy) {
     return 2.f - r;
 }
 
-// Shoelace of an ordered point list relative to its first point (double).
-__device__ __forceinline__ double shoelace64(const double* x, const double* y, int m) {
-    double s = 0.0;
-    for (int k = 1; k + 1 < m; ++k)
-        s += __dsub_rn(__dmul_rn(x[k] - x[0], y[k + 1] - y[0]), __dmul_rn(y[k] - y[0], x[k + 1] - x[0]));
-    return 0.5 * s;
-}
-
-// Candidate gathering with the inclusive/strict rules, angular order, shoelace.
-// Reloads the raw float inputs so FP64 tests see the unrounded values.  With
-// refinement on, a near-degenerate pair takes its orientation signs, crossing
-// parameters and shoelace determinants in FP64 (the areas of slivers are
-// ill-conditioned in FP32) and its IoU is formed in FP64.
-template <int K>
-__device__ __noinline__ void fwd_robust(const float* __restrict__ p1, const float* __restrict__ p2, int n1, int n2,
-                                        bool refine, FwdOut<K>& o) {
-    constexpr int C = 2 * K;
-    float px[K], py[K], qx[K], qy[K];
-    load_poly<K>(p1, px, py);
-    load_poly<K>(p2, qx, qy);
-    const float ox = px[0], oy = py[0];
-    float ax[K], ay[K], bx[K], by[K];
-    float L = 0.f;
-    for (int v = 0; v < K; ++v) {
-        ax[v] = px[v] - ox;
-        ay[v] = py[v] - oy;
-        bx[v] = qx[v] - ox;
-        by[v] = qy[v] - oy;
-        if (v < n1) L = fmaxf(L, fmaxf(fabsf(ax[v]), fabsf(ay[v])));
-        if (v < n2) L = fmaxf(L, fmaxf(fabsf(bx[v]), fabsf(by[v])));
-    }
-    const float thr = kDegenRel * L * L;
-
-    // classifier on FP32 local values
-    bool degen = !(L > 0.f);
-    signed char sS[K * K], sT[K * K]; // signs: S(i,j) of a_i vs edge j, T(i,j) of b_j vs edge i
-    float Sf[K * K], Tf[K * K];
-    for (int i = 0; i < n1; ++i) {
-        const int i1 = (i + 1 < n1) ? i + 1 : 0;
-        for (int j = 0; j < n2; ++j) {
-            const int j1 = (j + 1 < n2) ? j + 1 : 0;
-            float s = orient32nc(bx[j], by[j], bx[j1], by[j1], ax[i], ay[i]);
-            float t = orient32nc(ax[i], ay[i], ax[i1], ay[i1], bx[j], by[j]);
-            Sf[i * K + j] = s;
-            Tf[i * K + j] = t;
-            degen |= (fabsf(s) <= thr) || (fabsf(t) <= thr);
-        }
-    }
-    for (int i = 0; i < n1; ++i) {
-        const int i1 = (i + 1 < n1) ? i + 1 : 0;
-        for (int j = 0; j < n2; ++j) {
-            const int j1 = (j + 1 < n2) ? j + 1 : 0;
-            float Sa = Sf[i * K + j], Sb = Sf[i1 * K + j], Ta = Tf[i * K + j], Tb = Tf[i * K + j1];
-            bool cross = ((Sa > 0.f && Sb < 0.f) || (Sa < 0.f && Sb > 0.f)) &&
-                         ((Ta > 0.f && Tb < 0.f) || (Ta < 0.f && Tb > 0.f));
-            if (cross) {
-                float as = fabsf(Sa), bs = fabsf(Sb), at = fabsf(Ta), bt = fabsf(Tb);
-                degen |= fminf(as, bs) <= kDegenRel * (as + bs);
-                degen |= fminf(at, bt) <= kDegenRel * (at + bt);
-                float eax = ax[i1] - ax[i], eay = ay[i1] - ay[i];
-                float ebx = bx[j1] - bx[j], eby = by[j1] - by[j];
-                float D = eax * eby - eay * ebx;
-                float r2 = eax * eax + eay * eay, s2 = ebx * ebx + eby * eby;
-                degen |= D * D <= (kDegenRel * kDegenRel) * r2 * s2;
-            }
-        }
-    }
-    const bool use64 = refine && degen;
-
-    // signs (FP64 from the raw inputs when refining)
-    for (int i = 0; i < n1; ++i) {
-        const int i1 = (i + 1 < n1) ? i + 1 : 0;
-        for (int j = 0; j < n2; ++j) {
-            const int j1 = (j + 1 < n2) ? j + 1 : 0;
-            if (use64) {
-                double s = orient64(qx[j], qy[j], qx[j1], qy[j1], px[i], py[i]);
-                double t = orient64(px[i], py[i], px[i1], py[i1], qx[j], qy[j]);
-                sS[i * K + j] = (s > 0.0) - (s < 0.0);
-                sT[i * K + j] = (t > 0.0) - (t < 0.0);
-            } else {
-                float s = Sf[i * K + j], t = Tf[i * K + j];
-                sS[i * K + j] = (s > 0.f) - (s < 0.f);
-                sT[i * K + j] = (t > 0.f) - (t < 0.f);
-            }
-        }
-    }
-
-    // candidates, relative to P1's vertex 0 (exact in double for float inputs)
-    double cx[C], cy[C];
-    float key[C];
-    uint32_t cc[C];
-    int m = 0;
-    bool overflow = false;
-    // P1 vertices inside-or-on P2
-    for (int i = 0; i < n1; ++i) {
-        bool in = true;
-        for (int j = 0; j < n2; ++j) in &= sS[i * K + j] >= 0;
-        if (in) {
-            if (m < C) {
-                cx[m] = (double)px[i] - (double)ox;
-                cy[m] = (double)py[i] - (double)oy;
-                cc[m] = (uint32_t)i;
-                ++m;
-            } else overflow = true;
-        }
-    }
-    // P2 vertices inside-or-on P1, except exact copies of P1 vertices
-    for (int j = 0; j < n2; ++j) {
-        bool in = true, dup = false;
-        for (int i = 0; i < n1; ++i) {
-            in &= sT[i * K + j] >= 0;
-            dup |= (qx[j] == px[i]) && (qy[j] == py[i]);
-        }
-        if (in && !dup) {
-            if (m < C) {
-                cx[m] = (double)qx[j] - (double)ox;
-                cy[m] = (double)qy[j] - (double)oy;
-                cc[m] = 0x40u | (uint32_t)j;
-                ++m;
-            } else overflow = true;
-        }
-    }
-    // proper crossings
-    for (int i = 0; i < n1; ++i) {
-        const int i1 = (i + 1 < n1) ? i + 1 : 0;
-        for (int j = 0; j < n2; ++j) {
-            const int j1 = (j + 1 < n2) ? j + 1 : 0;
-            int sa = sS[i * K + j], sb = sS[i1 * K + j], ta = sT[i * K + j], tb = sT[i * K + j1];
-            if (sa * sb < 0 && ta * tb < 0) {
-                double x, y;
-                if (use64) {
-                    double Sa = orient64(qx[j], qy[j], qx[j1], qy[j1], px[i], py[i]);
-                    double Sb = orient64(qx[j], qy[j], qx[j1], qy[j1], px[i1], py[i1]);
-                    double t = Sa / (Sa - Sb);
-                    x = ((double)px[i] - (double)ox) + t * ((double)px[i1] - (double)px[i]);
-                    y = ((double)py[i] - (double)oy) + t * ((double)py[i1] - (double)py[i]);
-                } else {
-                    float Sa = Sf[i * K + j], Sb = Sf[i1 * K + j];
-                    float t = Sa / (Sa - Sb);
-                    x = (double)(ax[i] + t * (ax[i1] - ax[i]));
-                    y = (double)(ay[i] + t * (ay[i1] - ay[i]));
-                }
-                if (m < C) {
-                    cx[m] = x;
-                    cy[m] = y;
-                    cc[m] = 0x80u | ((uint32_t)i << 3) | (uint32_t)j;
-                    ++m;
-                } else {
-                    overflow = true;
-                }
-            }
-        }
-    }
-    o.degen = (degen ? 1u : 0u) | (use64 ? 2u : 0u);
-    o.nx = 0;
-    o.ai = 0.f;
-    o.iou = 0.f;
-    codes_fill<K>(o.codes, ~0ull);
-    if (overflow) {
-        o.err |= kDevOverflow;
-        o.degen |= 1u;
-        return;
-    }
-    if (m < 3) return;
-
-    double mx = 0.0, my = 0.0;
-    for (int k = 0; k < m; ++k) { mx += cx[k]; my += cy[k]; }
-    mx /= (double)m;
-    my /= (double)m;
-    for (int k = 0; k < m; ++k) key[k] = pseudo_angle((float)(cx[k] - mx), (float)(cy[k] - my));
-    for (int k = 1; k < m; ++k) {
-        double kx = cx[k], ky = cy[k];
-        float kk = key[k];
-        uint32_t kc = cc[k];
-        int l = k - 1;
-        while (l >= 0 && (key[l] > kk || (key[l] == kk && cc[l] > kc))) {
-            cx[l + 1] = cx[l]; cy[l + 1] = cy[l]; key[l + 1] = key[l]; cc[l + 1] = cc[l];
-            --l;
-        }
-        cx[l + 1] = kx; cy[l + 1] = ky; key[l + 1] = kk; cc[l + 1] = kc;
-    }
-    int s0 = 0;
-    for (int k = 1; k < m; ++k) s0 = (cc[k] < cc[s0]) ? k : s0;
-    double wx[C], wy[C];
-    for (int k = 0; k < m; ++k) {
-        const int a = (s0 + k) % m;
-        code_put<K>(o.codes, (uint32_t)k, cc[a]);
-        wx[k] = cx[a];
-        wy[k] = cy[a];
-    }
-    o.nx = (uint32_t)m;
-    if (use64) {
-        double sx1[K], sy1[K], sx2[K], sy2[K];
-        for (int v = 0; v < n1; ++v) { sx1[v] = px[v]; sy1[v] = py[v]; }
-        for (int v = 0; v < n2; ++v) { sx2[v] = qx[v]; sy2[v] = qy[v]; }
-        const double ai = shoelace64(wx, wy, m);
-        const double a1 = shoelace64(sx1, sy1, n1), a2 = shoelace64(sx2, sy2, n2);
-        const double U = a1 + a2 - ai;
-        o.ai = (float)ai;
-        o.a1 = (float)a1;
-        o.a2 = (float)a2;
-        o.iou = (U > 0.0) ? (float)(ai / U) : 0.f;
-    } else {
-        float twoA = 0.f;
-        for (int k = 0; k < m; ++k) {
-            const int b = (k + 1 < m) ? k + 1 : 0;
-            twoA += (float)wx[k] * (float)wy[b] - (float)wy[k] * (float)wx[b];
-        }
-        o.ai = 0.5f * twoA;
-        const float U = o.a1 + o.a2 - o.ai;
-        o.iou = (U > 0.f) ? o.ai / U : 0.f;
-    }
-}
-
 // ------------------------------------------------- warp-cooperative robust path
 //
-// All 32 lanes of a warp work on one pair, with the rules of fwd_robust
-// (inclusive vertex tests, strict crossings, exact duplicates dropped, angular
-// order rotated to the smallest code).  Each orientation test runs on its own
+// All 32 lanes of a warp work on one pair, with the candidate rules of the
+// definition (inclusive vertex tests, strict crossings, exact duplicates
+// dropped, angular order rotated to the smallest code).  Each orientation test runs on its own
 // lane, in FP64 from the raw inputs when refining; the signs are combined by
 // ballot, each candidate vertex is computed on its own lane, candidates are
 // ranked by comparing against every other lane, and the area is a shuffle
@@ -840,13 +601,15 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
                 Ta = orient32nc(ax0 - ox, ay0 - oy, ax1 - ox, ay1 - oy, bx0 - ox, by0 - oy);
                 Tb = orient32nc(ax0 - ox, ay0 - oy, ax1 - ox, ay1 - oy, bx1 - ox, by1 - oy);
             }
-            const double t = Sa / (Sa - Sb), u = Ta / (Ta - Tb);
-            x = ((double)ax0 - (double)ox) + t * ((double)ax1 - (double)ax0);
-            y = ((double)ay0 - (double)oy) + t * ((double)ay1 - (double)ay0);
-            const double rx = (double)ax1 - ax0, ry = (double)ay1 - ay0, sx = (double)bx1 - bx0, sy = (double)by1 - by0;
-            const double D = rx * sy - ry * sx;
-            deg2 = t <= kDegenRel || t >= 1.0 - kDegenRel || u <= kDegenRel || u >= 1.0 - kDegenRel ||
-                   D * D <= (double)kDegenRel * kDegenRel * (rx * rx + ry * ry) * (sx * sx + sy * sy);
+            // the crossing parameters only place a vertex along its edge, so
+            // they are FP32 quotients of the (FP64) orientation differences
+            const float t = (float)Sa / (float)(Sa - Sb), u = (float)Ta / (float)(Ta - Tb);
+            x = ((double)ax0 - (double)ox) + (double)t * ((double)ax1 - (double)ax0);
+            y = ((double)ay0 - (double)oy) + (double)t * ((double)ay1 - (double)ay0);
+            const float rx = ax1 - ax0, ry = ay1 - ay0, sx = bx1 - bx0, sy = by1 - by0;
+            const float D = rx * sy - ry * sx;
+            deg2 = t <= kDegenRel || t >= 1.0f - kDegenRel || u <= kDegenRel || u >= 1.0f - kDegenRel ||
+                   D * D <= kDegenRel * kDegenRel * (rx * rx + ry * ry) * (sx * sx + sy * sy);
         }
     }
     deg = __any_sync(full, deg || deg2);
@@ -859,7 +622,13 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
     if (m < 3) return;
 
     // angular order about the centroid, ties by code; rotate to the smallest code
-    const double mx = warp_sum(lane < m ? x : 0.0) / m, my = warp_sum(lane < m ? y : 0.0) / m;
+    float cxs = (lane < m) ? (float)x : 0.f, cys = (lane < m) ? (float)y : 0.f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        cxs += __shfl_xor_sync(full, cxs, off);
+        cys += __shfl_xor_sync(full, cys, off);
+    }
+    const double mx = (double)(cxs / (float)m), my = (double)(cys / (float)m);
     const float key = (lane < m) ? pseudo_angle((float)(x - mx), (float)(y - my)) : __int_as_float(0x7f800000);
     int rank = 0;
     for (int l = 0; l < m; ++l) {
@@ -902,16 +671,33 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
         else term = (double)((float)(x - mx) * (float)(nyp - my) - (float)(y - my) * (float)(nxp - mx));
     }
     const double ai = 0.5 * warp_sum(term);
+    // input areas, one shoelace term per lane
     double a1 = 0.0, a2 = 0.0;
-    for (int v = 0; v < n1; ++v) {
-        const int w = (v + 1 < n1) ? v + 1 : 0;
-        const double xv = (double)px[v] - ox, yv = (double)py[v] - oy, xw = (double)px[w] - ox, yw = (double)py[w] - oy;
-        a1 += refine ? __dsub_rn(__dmul_rn(xv, yw), __dmul_rn(yv, xw)) : (double)((float)xv * (float)yw - (float)yv * (float)xw);
-    }
-    for (int v = 0; v < n2; ++v) {
-        const int w = (v + 1 < n2) ? v + 1 : 0;
-        const double xv = (double)qx[v] - ox, yv = (double)qy[v] - oy, xw = (double)qx[w] - ox, yw = (double)qy[w] - oy;
-        a2 += refine ? __dsub_rn(__dmul_rn(xv, yw), __dmul_rn(yv, xw)) : (double)((float)xv * (float)yw - (float)yv * (float)xw);
+    {
+        const int v = lane & 7;
+        const bool second = lane >= 8 && lane < 16;
+        const int n = second ? n2 : n1;
+        const bool on = lane < 16 && v < n;
+        const int w = (v + 1 < n) ? v + 1 : 0;
+        const float* xs = second ? qx : px;
+        const float* ys = second ? qy : py;
+        double term2 = 0.0;
+        if (on) {
+            float xv = 0.f, yv = 0.f, xw = 0.f, yw = 0.f;
+#pragma unroll
+            for (int m2 = 0; m2 < K; ++m2) {
+                xv = (m2 == v) ? xs[m2] : xv;
+                yv = (m2 == v) ? ys[m2] : yv;
+                xw = (m2 == w) ? xs[m2] : xw;
+                yw = (m2 == w) ? ys[m2] : yw;
+            }
+            const double Xv = (double)xv - ox, Yv = (double)yv - oy, Xw = (double)xw - ox, Yw = (double)yw - oy;
+            term2 = refine ? __dsub_rn(__dmul_rn(Xv, Yw), __dmul_rn(Yv, Xw))
+                           : (double)((float)Xv * (float)Yw - (float)Yv * (float)Xw);
+        }
+        const double s1 = warp_sum((lane < 8) ? term2 : 0.0), s2 = warp_sum(second ? term2 : 0.0);
+        a1 = s1;
+        a2 = s2;
     }
     a1 *= 0.5;
     a2 *= 0.5;
@@ -922,35 +708,6 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
     o.a2 = (float)a2;
     o.iou = (U > 0.0) ? (float)(ai / U) : 0.f;
 }
-
-// Full forward for one pair whose polygons are already in registers; the raw
-// pointers (this pair's polygons) are only read again by the robust path.
-template <int K, bool COUNTS>
-__device__ __forceinline__ void fwd_loaded(const float (&px)[K], const float (&py)[K], const float (&qx)[K],
-                                           const float (&qy)[K], const float* __restrict__ p1,
-                                           const float* __restrict__ p2, int n1, int n2, uint32_t flags, Geo<K>& g,
-                                           FwdOut<K>& o) {
-    make_geo<K, COUNTS>(px, py, qx, qy, n1, n2, g);
-    o.err = 0;
-    o.degen = 0;
-    input_areas<K, COUNTS>(g, o.a1, o.a2);
-    if (fwd_generic<K, COUNTS>(g, o)) {
-        const float U = o.a1 + o.a2 - o.ai;
-        o.iou = (o.nx >= 3u && U > 0.f) ? o.ai / U : 0.f;
-    } else {
-        fwd_robust<K>(p1, p2, g.n1, g.n2, (flags & kFlagRefine) && !(flags & kFlagPlain), o);
-    }
-}
-
-template <int K, bool COUNTS>
-__device__ __forceinline__ void fwd_pair(const float* __restrict__ p1, const float* __restrict__ p2, int n1, int n2,
-                                         uint32_t flags, Geo<K>& g, FwdOut<K>& o) {
-    float px[K], py[K], qx[K], qy[K];
-    load_poly<K>(p1, px, py);
-    load_poly<K>(p2, qx, qy);
-    fwd_loaded<K, COUNTS>(px, py, qx, qy, p1, p2, n1, n2, flags, g, o);
-}
-
 
 // ---------------------------------------------------------------- backward
 //

@@ -39,6 +39,10 @@ dgal_status launch_paired_bwd(const float* p1, const uint8_t* c1, const float* p
 dgal_status launch_pairwise(const float* a, const uint8_t* ca, int64_t N, const float* b, const uint8_t* cb,
                             int64_t M, int K, float* iou, uint8_t* nx, uint32_t flags, cudaStream_t s);
 size_t batched_workspace_bytes(int S);
+size_t loss_workspace_bytes(int64_t n);
+dgal_status launch_iou_loss(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n, int K,
+                            const float* weight, float scale, float* loss, float* iou, float* g1, float* g2,
+                            void* ws, uint32_t flags, cudaStream_t s);
 dgal_status launch_batched(int S, const int64_t* a_off, const int64_t* b_off, const int64_t* out_off,
                            const float* a, const uint8_t* ca, const float* b, const uint8_t* cb, int K, float* iou,
                            uint8_t* nx, void* ws, uint32_t flags, const BatchedConfig& cfg, cudaStream_t s);

@@ -1,0 +1,438 @@
+// K = 8 paired kernels: a group of 8 lanes per pair (4 pairs per warp).
+//
+// With K = 8 a thread-per-pair kernel unrolls 64 vertex-edge blocks and its
+// code no longer fits the instruction cache.  Here lane r of a group owns
+// P1's vertex r and edge r (r < n1) and P2's edge r (r < n2), and keeps a copy
+// of P2; every per-lane loop runs over 8, so the code stays small.  All
+// shuffles use the group's own lane mask, and every branch that leads to a
+// shuffle depends only on group-wide values, so groups of a warp may diverge.
+//
+// Forward (paper Sec. II-B `iou`): lane r computes row r of the orientation
+// tables, S(r,j) = orient(b_j, b_j+1, a_r) and T(r,j) = orient(a_r, a_r+1, b_j);
+// the rows are OR-combined into 64-bit sign masks, after which every lane
+// knows the inside vertices and the crossings (as in fwd_generic).  Lane r
+// builds the clipped pieces of P1 edge r and P2 edge r (endpoints are
+// vertices or crossing points; each crossing point comes from cross_point(),
+// whose roundings are spelled out so both lanes that use it get the same
+// bits), and its chunk of the counter-clockwise vertex order: vertex r if
+// inside, the entry crossing of edge r, its exit crossing and the chain of P2
+// vertices that follows an exit.  An exclusive scan of chunk lengths places
+// the chunks; the cycle is rotated to its smallest code.
+//
+// Backward (paper Sec. II-B `iou_grad`): the shape derivative over the
+// clipped pieces (see bwd_shape).  Lane r evaluates P1 edge r and P2 edge r;
+// the contribution of an edge to its end vertex moves to the next lane with
+// one shuffle, and lane r stores vertex r's gradients.
+#pragma once
+
+#include "dgal_geom.cuh"
+
+namespace dgal {
+namespace g8 {
+
+constexpr int G = 8;
+
+__device__ __forceinline__ unsigned gmask() { return 0xFFu << ((threadIdx.x & 31) & ~7); }
+__device__ __forceinline__ int gbase() { return (threadIdx.x & 31) & ~7; }
+
+__device__ __forceinline__ uint64_t gor64(unsigned m, uint64_t v) {
+#pragma unroll
+    for (int off = 1; off < G; off <<= 1) v |= __shfl_xor_sync(m, v, off, G);
+    return v;
+}
+__device__ __forceinline__ uint32_t gor32(unsigned m, uint32_t v) {
+#pragma unroll
+    for (int off = 1; off < G; off <<= 1) v |= __shfl_xor_sync(m, v, off, G);
+    return v;
+}
+__device__ __forceinline__ float gsum(unsigned m, float v) {
+#pragma unroll
+    for (int off = 1; off < G; off <<= 1) v += __shfl_xor_sync(m, v, off, G);
+    return v;
+}
+__device__ __forceinline__ float gmax(unsigned m, float v) {
+#pragma unroll
+    for (int off = 1; off < G; off <<= 1) v = fmaxf(v, __shfl_xor_sync(m, v, off, G));
+    return v;
+}
+__device__ __forceinline__ float gmin(unsigned m, float v) {
+#pragma unroll
+    for (int off = 1; off < G; off <<= 1) v = fminf(v, __shfl_xor_sync(m, v, off, G));
+    return v;
+}
+
+// Crossing point of P1 edge (a, a + ea) with P2 edge (b, b + eb) as a + t ea,
+// t = cross(eb, a - b) / cross(ea, eb), every rounding explicit.
+__device__ __forceinline__ void cross_point(float ax, float ay, float eax, float eay, float bx, float by, float ebx,
+                                            float eby, float& wx, float& wy) {
+    const float dx = __fsub_rn(ax, bx), dy = __fsub_rn(ay, by);
+    const float S = __fsub_rn(__fmul_rn(ebx, dy), __fmul_rn(eby, dx));
+    const float D = __fsub_rn(__fmul_rn(eax, eby), __fmul_rn(eay, ebx));
+    const float t = __fdiv_rn(S, D);
+    wx = __fmaf_rn(t, eax, ax);
+    wy = __fmaf_rn(t, eay, ay);
+}
+
+__device__ __forceinline__ float sel8(const float (&v)[8], uint32_t i) {
+    float r = v[0];
+#pragma unroll
+    for (int m = 1; m < 8; ++m) r = (i == (uint32_t)m) ? v[m] : r;
+    return r;
+}
+
+// Lane view of a pair: own P1 vertex / edge, all of P2, in P1's local frame.
+struct Lane {
+    float ax, ay, eax, eay;
+    float bx[8], by[8], ebx[8], eby[8];
+    int n1, n2, r;
+};
+
+__device__ __forceinline__ void load_lane(const float* __restrict__ p1, const float* __restrict__ p2, int n1, int n2,
+                                          int r, Lane& L) {
+    const float ox = __ldg(p1), oy = __ldg(p1 + 1);
+    const int rr = (r < n1) ? r : 0;
+    const int rn = (rr + 1 < n1) ? rr + 1 : 0;
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p1) + rr);
+    const float2 w = __ldg(reinterpret_cast<const float2*>(p1) + rn);
+    L.ax = v.x - ox;
+    L.ay = v.y - oy;
+    L.eax = (w.x - ox) - L.ax;
+    L.eay = (w.y - oy) - L.ay;
+    float qx[8], qy[8];
+    load_poly<8>(p2, qx, qy);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        L.bx[j] = qx[j] - ox;
+        L.by[j] = qy[j] - oy;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const bool wrap = j + 1 >= n2;
+        L.ebx[j] = (wrap ? L.bx[0] : L.bx[(j + 1) & 7]) - L.bx[j];
+        L.eby[j] = (wrap ? L.by[0] : L.by[(j + 1) & 7]) - L.by[j];
+    }
+    L.n1 = n1;
+    L.n2 = n2;
+    L.r = r;
+}
+
+__device__ __forceinline__ uint64_t col0_mask() {
+    uint64_t c = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) c |= 1ull << (8 * i);
+    return c;
+}
+
+struct FwdG {
+    uint64_t w0, w1; // the 16 code bytes
+    float iou;
+    uint32_t nx;
+};
+
+// Group forward.  Returns false (in every lane of the group) when the pair
+// must take the warp-cooperative robust path.
+__device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
+    const unsigned gm = gmask();
+    const int base = gbase();
+    const int r = L.r, n1 = L.n1, n2 = L.n2;
+    const bool liveA = r < n1, liveB = r < n2;
+    float Lr = liveA ? fmaxf(fabsf(L.ax), fabsf(L.ay)) : 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) Lr = fmaxf(Lr, (j < n2) ? fmaxf(fabsf(L.bx[j]), fabsf(L.by[j])) : 0.f);
+    Lr = gmax(gm, Lr);
+    const float thr = kDegenRel * Lr * Lr;
+
+    // row r of S and T
+    uint32_t sneg = 0, tneg = 0;
+    float mn = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float dx = L.ax - L.bx[j], dy = L.ay - L.by[j];
+        const float s = L.ebx[j] * dy - L.eby[j] * dx;
+        const float t = L.eay * dx - L.eax * dy;
+        mn = fminf(mn, (liveA && j < n2) ? fminf(fabsf(s), fabsf(t)) : __int_as_float(0x7f800000));
+        sneg |= (__float_as_uint(s) >> 31) << j;
+        tneg |= (__float_as_uint(t) >> 31) << j;
+    }
+    mn = gmin(gm, mn);
+    if (!(Lr > 0.f) || !(mn > thr)) return false;
+    const uint32_t colv = (1u << n2) - 1u;
+    const uint64_t sp = gor64(gm, liveA ? (uint64_t)(~sneg & colv) << (8 * r) : 0ull);
+    const uint64_t tp = gor64(gm, liveA ? (uint64_t)(~tneg & colv) << (8 * r) : 0ull);
+    const uint64_t col0 = 0x0101010101010101ull;
+    const uint64_t rows = (n1 >= 8) ? ~0ull : ((1ull << (8 * n1)) - 1ull);
+    const uint64_t cols = col0 * colv;
+    const uint64_t V = rows & cols;
+    const uint64_t sp_next = ((sp >> 8) & ~(0xFFull << (8 * (n1 - 1)))) | ((sp & 0xFFull) << (8 * (n1 - 1)));
+    const uint64_t tp_next = ((tp >> 1) & ~(col0 << (n2 - 1))) | ((tp & col0) << (n2 - 1));
+    const uint64_t X = (sp ^ sp_next) & (tp ^ tp_next) & V;
+    const uint64_t entry1 = X & ~sp, exit1 = X & sp;
+    if ((X & tp) != entry1) return false;
+    // in1: rows of sp equal to all valid columns (exact zero-byte test on sp ^ cols)
+    const uint64_t z = (sp ^ cols) & rows;
+    const uint64_t hi7 = 0x7F7F7F7F7F7F7F7Full;
+    const uint64_t zb = ~(((z & hi7) + hi7) | z | hi7) & rows; // 0x80 in each zero byte of a valid row
+    const uint32_t in1 = (uint32_t)(((zb >> 7) * 0x0102040810204080ull) >> 56);
+    // in2: columns of tp set in every valid row (AND over the rows' bytes)
+    uint64_t a = tp | ~rows;
+    a &= a >> 32;
+    a &= a >> 16;
+    a &= a >> 8;
+    const uint32_t in2 = (uint32_t)(a & 0xFFull) & colv;
+    const uint32_t cnt = (uint32_t)(__popc(in1) + __popc(in2) + __popcll(X));
+    out.nx = 0;
+    out.iou = 0.f;
+    out.w0 = out.w1 = ~0ull;
+    if (cnt == 0u) return true;
+    if (cnt < 3u || cnt > 16u) return false;
+
+    // clipped piece of P1 edge r: from a_r or its entry crossing to a_{r+1} or
+    // its exit crossing
+    const uint32_t rowE = liveA ? (uint32_t)((entry1 >> (8 * r)) & 0xFF) : 0u;
+    const uint32_t rowX = liveA ? (uint32_t)((exit1 >> (8 * r)) & 0xFF) : 0u;
+    bool bad = (rowE & (rowE - 1)) != 0u || (rowX & (rowX - 1)) != 0u;
+    float sAx = L.ax, sAy = L.ay, eAx = L.ax + L.eax, eAy = L.ay + L.eay;
+    if (rowE) {
+        const uint32_t j = (uint32_t)(__ffs(rowE) - 1);
+        cross_point(L.ax, L.ay, L.eax, L.eay, sel8(L.bx, j), sel8(L.by, j), sel8(L.ebx, j), sel8(L.eby, j), sAx, sAy);
+    }
+    if (rowX) {
+        const uint32_t j = (uint32_t)(__ffs(rowX) - 1);
+        cross_point(L.ax, L.ay, L.eax, L.eay, sel8(L.bx, j), sel8(L.by, j), sel8(L.ebx, j), sel8(L.eby, j), eAx, eAy);
+    }
+    const bool hasA = liveA && (((in1 >> r) & 1u) || rowE);
+    // clipped piece of P2 edge r: from b_r or the crossing where P1 leaves
+    // P2 on it, to b_{r+1} or the crossing where P1 enters P2 on it; those
+    // crossings are computed from the P1 edge's data, fetched from its lane
+    const uint64_t cX = liveB ? ((exit1 >> r) & col0) : 0ull, cE = liveB ? ((entry1 >> r) & col0) : 0ull;
+    bad |= (cX & (cX - 1)) != 0ull || (cE & (cE - 1)) != 0ull;
+    const int ix = cX ? (__ffsll((long long)cX) - 1) / 8 : 0;
+    const int ie = cE ? (__ffsll((long long)cE) - 1) / 8 : 0;
+    const float xax = __shfl_sync(gm, L.ax, base + ix), xay = __shfl_sync(gm, L.ay, base + ix);
+    const float xeax = __shfl_sync(gm, L.eax, base + ix), xeay = __shfl_sync(gm, L.eay, base + ix);
+    const float nax = __shfl_sync(gm, L.ax, base + ie), nay = __shfl_sync(gm, L.ay, base + ie);
+    const float neax = __shfl_sync(gm, L.eax, base + ie), neay = __shfl_sync(gm, L.eay, base + ie);
+    const float bxr = sel8(L.bx, (uint32_t)r), byr = sel8(L.by, (uint32_t)r);
+    const float ebxr = sel8(L.ebx, (uint32_t)r), ebyr = sel8(L.eby, (uint32_t)r);
+    float sBx = bxr, sBy = byr, eBx = bxr + ebxr, eBy = byr + ebyr;
+    if (cX) cross_point(xax, xay, xeax, xeay, bxr, byr, ebxr, ebyr, sBx, sBy);
+    if (cE) cross_point(nax, nay, neax, neay, bxr, byr, ebxr, ebyr, eBx, eBy);
+    const bool hasB = liveB && (((in2 >> r) & 1u) || cX);
+    const float twoA = gsum(gm, (hasA ? sAx * eAy - sAy * eAx : 0.f) + (hasB ? sBx * eBy - sBy * eBx : 0.f));
+    const float a1 = 0.5f * gsum(gm, liveA ? L.ax * L.eay - L.ay * L.eax : 0.f);
+    const float a2 = 0.5f * gsum(gm, liveB ? bxr * ebyr - byr * ebxr : 0.f);
+    const float ai = 0.5f * twoA;
+    const float U = a1 + a2 - ai;
+
+    // chunk of the vertex order from P1 edge r
+    uint64_t c_lo = 0, c_hi = 0;
+    uint32_t len = 0, qm = 0;
+    if (liveA) {
+        if ((in1 >> r) & 1u) {
+            c_lo |= (uint64_t)r;
+            ++len;
+        }
+        if (rowE) {
+            c_lo |= (uint64_t)(0x80u | ((uint32_t)r << 3) | (uint32_t)(__ffs(rowE) - 1)) << (8 * len);
+            ++len;
+        }
+        if (rowX) {
+            const uint32_t jx = (uint32_t)(__ffs(rowX) - 1);
+            c_lo |= (uint64_t)(0x80u | ((uint32_t)r << 3) | jx) << (8 * len);
+            ++len;
+            uint32_t j = (jx + 1 < (uint32_t)n2) ? jx + 1 : 0u;
+            for (int m = 0; m < 8 && ((in2 >> j) & 1u) && !((qm >> j) & 1u); ++m) {
+                qm |= 1u << j;
+                const uint64_t code = 0x40u | j;
+                if (len < 8) c_lo |= code << (8 * len);
+                else c_hi |= code << (8 * (len - 8));
+                ++len;
+                j = (j + 1 < (uint32_t)n2) ? j + 1 : 0u;
+            }
+        }
+    }
+    uint32_t off = len;
+#pragma unroll
+    for (int d = 1; d < G; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(gm, off, d, G);
+        if (r >= d) off += v;
+    }
+    const uint32_t total = __shfl_sync(gm, off, base + 7);
+    off -= len;
+    const uint32_t qall = gor32(gm, qm);
+    uint64_t s_lo = 0, s_hi = 0;
+    if (len) {
+        if (off == 0) {
+            s_lo = c_lo;
+            s_hi = c_hi;
+        } else if (off < 8) {
+            s_lo = c_lo << (8 * off);
+            s_hi = (c_hi << (8 * off)) | (c_lo >> (64 - 8 * off));
+        } else {
+            s_hi = c_lo << (8 * (off - 8));
+        }
+    }
+    s_lo = gor64(gm, s_lo);
+    s_hi = gor64(gm, s_hi);
+    const bool q_inside = X == 0 && in1 == 0;
+    if (q_inside) {
+        // P2 inside P1: the intersection is P2
+        bad |= in2 != ((1u << n2) - 1u);
+        s_lo = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s_lo |= (j < n2) ? ((uint64_t)(0x40u | j) << (8 * j)) : 0ull;
+        s_hi = 0;
+    } else {
+        bad |= total != cnt || qall != in2;
+    }
+    if (gor32(gm, bad ? 1u : 0u)) return false;
+    uint32_t start;
+    if (in1) start = (uint32_t)(__ffs(in1) - 1);
+    else if (in2) start = 0x40u | (uint32_t)(__ffs(in2) - 1);
+    else {
+        const int b = __ffsll((long long)X) - 1;
+        start = 0x80u | ((uint32_t)(b / 8) << 3) | (uint32_t)(b % 8);
+    }
+    // slot of the smallest code (lowest byte equal to it), then rotate
+    const uint64_t ones = 0x0101010101010101ull, highs = 0x8080808080808080ull, pat = ones * start;
+    const uint64_t z0 = s_lo ^ pat, z1 = s_hi ^ pat;
+    const uint64_t h0 = (z0 - ones) & ~z0 & highs, h1 = (z1 - ones) & ~z1 & highs;
+    const uint32_t p0 = h0 ? (uint32_t)((__ffsll((long long)h0) - 1) >> 3)
+                           : 8u + (uint32_t)((__ffsll((long long)h1) - 1) >> 3);
+    // rotate the cnt-byte cycle left by p0 bytes
+    typedef unsigned __int128 u128;
+    u128 seq = ((u128)s_hi << 64) | (u128)s_lo;
+    if (p0 && p0 < cnt) {
+        const u128 keep = (cnt >= 16u) ? ~(u128)0 : (((u128)1 << (8u * cnt)) - 1u);
+        seq = ((seq >> (8u * p0)) | (seq << (8u * (cnt - p0)))) & keep;
+    }
+    const uint64_t lo = (uint64_t)seq, hi = (uint64_t)(seq >> 64);
+    out.w0 = lo | ((cnt < 8) ? (~0ull << (8 * cnt)) : 0ull);
+    out.w1 = hi | ((cnt <= 8) ? ~0ull : ((cnt < 16) ? (~0ull << (8 * (cnt - 8))) : 0ull));
+    out.nx = cnt;
+    out.iou = (U > 0.f) ? ai / U : 0.f;
+    return true;
+}
+
+// Group backward (shape derivative).  Returns 0, kDevBadFlags, or kSlow
+// (group-uniform) when the pair must take the shoelace adjoint.  On success
+// lane r holds the gradients of P1 vertex r and P2 vertex r (0 beyond counts).
+__device__ __forceinline__ uint32_t bwd_group(const Lane& L, float grad, uint32_t nx, uint64_t w0, uint64_t w1,
+                                              bool refine, float& g1x, float& g1y, float& g2x, float& g2y) {
+    const unsigned gm = gmask();
+    const int base = gbase();
+    const int r = L.r, n1 = L.n1, n2 = L.n2;
+    const bool liveA = r < n1, liveB = r < n2;
+    g1x = g1y = g2x = g2y = 0.f;
+    if (nx > 16u) return kDevBadFlags;
+    if (nx < 3u) return 0u;
+    // decode slots r and r + 8 on lane r, then OR across the group
+    uint32_t in1 = 0, in2 = 0, other = 0;
+    uint64_t X = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const uint32_t k = (uint32_t)r + 8u * h;
+        const uint32_t c = (uint32_t)(((h ? w1 : w0) >> (8 * r)) & 0xFFull);
+        const bool live = k < nx;
+        const uint32_t kind = c >> 6, lo = c & 7u, ci = (c >> 3) & 7u;
+        in1 |= (live && kind == 0u) ? (1u << (c & 0x1Fu)) : 0u;
+        in2 |= (live && kind == 1u) ? (1u << (c & 0x1Fu)) : 0u;
+        X |= (live && kind == 2u) ? (1ull << (ci * 8 + lo)) : 0ull;
+        other |= (live && (kind == 3u || (kind == 2u && (ci >= (uint32_t)n1 || lo >= (uint32_t)n2)))) ? 1u : 0u;
+    }
+    in1 = gor32(gm, in1);
+    in2 = gor32(gm, in2);
+    X = gor64(gm, X);
+    other = gor32(gm, other);
+    if (other || (in1 >> n1) || (in2 >> n2)) return kDevBadFlags;
+    const uint64_t col0 = col0_mask();
+    const uint32_t rn1 = (r + 1 < n1) ? (uint32_t)(r + 1) : 0u, rn2 = (r + 1 < n2) ? (uint32_t)(r + 1) : 0u;
+    const uint32_t rowX = liveA ? (uint32_t)((X >> (8 * r)) & 0xFF) : 0u;
+    const uint64_t colX = liveB ? ((X >> r) & col0) : 0ull;
+    bool ok = (uint32_t)(__popc(in1) + __popc(in2) + __popcll(X)) == nx;
+    {
+        const uint32_t ra = (uint32_t)__popc(rowX), a0 = (in1 >> r) & 1u, a1 = (in1 >> rn1) & 1u;
+        ok &= !liveA || ((a0 ^ a1) ? ra == 1u : (a0 ? ra == 0u : (ra == 0u || ra == 2u)));
+        const uint32_t rb = (uint32_t)__popcll(colX), b0 = (in2 >> r) & 1u, b1 = (in2 >> rn2) & 1u;
+        ok &= !liveB || ((b0 ^ b1) ? rb == 1u : (b0 ? rb == 0u : (rb == 0u || rb == 2u)));
+    }
+    if (gor32(gm, ok ? 0u : 1u)) return kSlow;
+
+    const float kInf = __int_as_float(0x7f800000);
+    // P1 edge r: parameters of its (at most two) crossings
+    float t0 = kInf, t1 = -kInf;
+    uint32_t rx = rowX;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (rx) {
+            const uint32_t j = (uint32_t)(__ffs(rx) - 1);
+            rx &= rx - 1;
+            const float bx = sel8(L.bx, j), by = sel8(L.by, j), ebx = sel8(L.ebx, j), eby = sel8(L.eby, j);
+            const float dx = L.ax - bx, dy = L.ay - by;
+            const float S = ebx * dy - eby * dx, D = L.eax * eby - L.eay * ebx;
+            const float t = S / D;
+            t0 = fminf(t0, t);
+            t1 = fmaxf(t1, t);
+        }
+    }
+    t0 = ((in1 >> r) & 1u) ? 0.f : t0;
+    t1 = ((in1 >> rn1) & 1u) ? 1.f : t1;
+    // P2 edge r: parameters of its crossings, with the P1 edges' data fetched
+    // from their lanes
+    const float bxr = sel8(L.bx, (uint32_t)r), byr = sel8(L.by, (uint32_t)r);
+    const float ebxr = sel8(L.ebx, (uint32_t)r), ebyr = sel8(L.eby, (uint32_t)r);
+    float u0 = kInf, u1 = -kInf;
+    uint64_t cx = colX;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = cx ? (__ffsll((long long)cx) - 1) / 8 : 0;
+        const bool has = cx != 0ull;
+        cx &= cx ? cx - 1 : 0ull;
+        const float ax = __shfl_sync(gm, L.ax, base + i), ay = __shfl_sync(gm, L.ay, base + i);
+        const float eax = __shfl_sync(gm, L.eax, base + i), eay = __shfl_sync(gm, L.eay, base + i);
+        if (has) {
+            const float dx = ax - bxr, dy = ay - byr;
+            const float T = eay * dx - eax * dy, D = eax * ebyr - eay * ebxr;
+            const float u = -T / D;
+            u0 = fminf(u0, u);
+            u1 = fmaxf(u1, u);
+        }
+    }
+    u0 = ((in2 >> r) & 1u) ? 0.f : u0;
+    u1 = ((in2 >> rn2) & 1u) ? 1.f : u1;
+    const bool hasA = liveA && (((in1 >> r) & 1u) || rowX);
+    const bool hasB = liveB && (((in2 >> r) & 1u) || colX);
+    const float c1 = liveA ? L.ax * L.eay - L.ay * L.eax : 0.f;
+    const float c2 = liveB ? bxr * ebyr - byr * ebxr : 0.f;
+    const float twoA = gsum(gm, (hasA ? (t1 - t0) * c1 : 0.f) + (hasB ? (u1 - u0) * c2 : 0.f));
+    const float a1 = 0.5f * gsum(gm, c1), a2 = 0.5f * gsum(gm, c2);
+    const float ai = 0.5f * twoA;
+    float Lr = liveA ? fmaxf(fabsf(L.ax), fabsf(L.ay)) : 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) Lr = fmaxf(Lr, (j < n2) ? fmaxf(fabsf(L.bx[j]), fabsf(L.by[j])) : 0.f);
+    Lr = gmax(gm, Lr);
+    if (refine && ai < kTinyArea * Lr * Lr) return kSlow;
+    const float U = a1 + a2 - ai;
+    if (!(U > 0.f)) return 0u;
+    const float rU = 1.0f / U;
+    const float gai = grad * (a1 + a2) * rU * rU, h12 = 0.5f * (-grad * ai * rU * rU);
+    const float I0a = hasA ? 0.5f * ((1.f - t0) * (1.f - t0) - (1.f - t1) * (1.f - t1)) : 0.f;
+    const float I1a = hasA ? 0.5f * (t1 * t1 - t0 * t0) : 0.f;
+    const float I0b = hasB ? 0.5f * ((1.f - u0) * (1.f - u0) - (1.f - u1) * (1.f - u1)) : 0.f;
+    const float I1b = hasB ? 0.5f * (u1 * u1 - u0 * u0) : 0.f;
+    const float wsa = liveA ? gai * I0a + h12 : 0.f, wea = liveA ? gai * I1a + h12 : 0.f;
+    const float wsb = liveB ? gai * I0b + h12 : 0.f, web = liveB ? gai * I1b + h12 : 0.f;
+    const float ex1 = wea * L.eay, ey1 = -wea * L.eax, ex2 = web * ebyr, ey2 = -web * ebxr;
+    // vertex r receives the end contribution of edge r - 1 (wrapping at the count)
+    const int pa = base + ((r == 0) ? n1 - 1 : r - 1), pb = base + ((r == 0) ? n2 - 1 : r - 1);
+    const float px1 = __shfl_sync(gm, ex1, pa), py1 = __shfl_sync(gm, ey1, pa);
+    const float px2 = __shfl_sync(gm, ex2, pb), py2 = __shfl_sync(gm, ey2, pb);
+    g1x = liveA ? wsa * L.eay + px1 : 0.f;
+    g1y = liveA ? -wsa * L.eax + py1 : 0.f;
+    g2x = liveB ? wsb * ebyr + px2 : 0.f;
+    g2y = liveB ? -wsb * ebxr + py2 : 0.f;
+    return 0u;
+}
+
+} // namespace g8
+} // namespace dgal

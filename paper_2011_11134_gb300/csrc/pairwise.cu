@@ -22,14 +22,16 @@ namespace dgal {
 
 constexpr int kPwThreads = 128;
 
+// Fast path for one matrix entry.  Returns true when the entry must be
+// finished by the warp-cooperative robust path; otherwise sets iou / nxo.
 template <int K, bool COUNTS>
-__device__ __forceinline__ void pw_entry(const float* __restrict__ pa, const float* __restrict__ pb, int n1, int n2,
-                                         uint32_t flags, float& iou, uint32_t& nxo, uint32_t& err) {
+__device__ __forceinline__ bool pw_fast(const float* __restrict__ pa, const float* __restrict__ pb, int n1, int n2,
+                                        float& iou, uint32_t& nxo, uint32_t& err) {
     iou = 0.f;
     nxo = 0u;
     if (COUNTS && (n1 < 3 || n1 > K || n2 < 3 || n2 > K)) {
         err |= kDevBadCount;
-        return;
+        return false;
     }
     float px[K], py[K], qx[K], qy[K];
     load_poly<K>(pa, px, py);
@@ -48,13 +50,39 @@ __device__ __forceinline__ void pw_entry(const float* __restrict__ pa, const flo
         by0 = vb ? fminf(by0, qy[v]) : by0;
         by1 = vb ? fmaxf(by1, qy[v]) : by1;
     }
-    if (ax1 < bx0 || bx1 < ax0 || ay1 < by0 || by1 < ay0) return;
+    if (ax1 < bx0 || bx1 < ax0 || ay1 < by0 || by1 < ay0) return false;
     Geo<K> g;
     FwdOut<K> o;
-    fwd_loaded<K, COUNTS>(px, py, qx, qy, pa, pb, n1, n2, flags, g, o);
-    err |= o.err;
+    make_geo<K, COUNTS>(px, py, qx, qy, n1, n2, g);
+    input_areas<K, COUNTS>(g, o.a1, o.a2);
+    if (!fwd_generic<K, COUNTS>(g, o)) return true;
+    const float U = o.a1 + o.a2 - o.ai;
     nxo = o.nx;
-    iou = o.iou;
+    iou = (o.nx >= 3u && U > 0.f) ? o.ai / U : 0.f;
+    return false;
+}
+
+// Finishes the entries of this warp step that the fast path handed back, one
+// at a time with the whole warp; the owning lane stores the result.
+template <int K>
+__device__ __forceinline__ void pw_finish(unsigned todo, const float* __restrict__ pa, const float* __restrict__ pb,
+                                          int n1, int n2, bool refine, float& iou, uint32_t& nxo, uint32_t& err) {
+    const int lane = threadIdx.x & 31;
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const float* qa = (const float*)__shfl_sync(0xffffffffu, (unsigned long long)pa, src);
+        const float* qb = (const float*)__shfl_sync(0xffffffffu, (unsigned long long)pb, src);
+        const int m1 = __shfl_sync(0xffffffffu, n1, src), m2 = __shfl_sync(0xffffffffu, n2, src);
+        FwdOut<K> o;
+        o.err = 0;
+        warp_robust<K>(qa, qb, m1, m2, refine, o);
+        if (lane == src) {
+            err |= o.err;
+            iou = o.iou;
+            nxo = o.nx;
+        }
+    }
 }
 
 template <int K, bool COUNTS>
@@ -62,21 +90,31 @@ __global__ void __launch_bounds__(kPwThreads)
 k_pairwise(const float* __restrict__ a, const uint8_t* __restrict__ ca, int64_t N, const float* __restrict__ b,
            const uint8_t* __restrict__ cb, int64_t M, float* __restrict__ iou, uint8_t* __restrict__ nx,
            uint32_t flags, uint32_t* status) {
+    const int lane = threadIdx.x & 31;
     const int64_t total = N * M;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= total) return;
-    int64_t i = e / M, j = e - (e / M) * M;
+    const int64_t stride = (int64_t)gridDim.x * kPwThreads;
+    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
+    int64_t base = (int64_t)blockIdx.x * kPwThreads + (threadIdx.x & ~31);
+    if (base >= total) return;
+    const int64_t e0 = base + lane;
+    int64_t i = e0 / M, j = e0 - (e0 / M) * M;
     const int64_t di = stride / M, dj = stride - di * M;
     uint32_t err = 0;
-    for (; e < total; e += stride) {
-        const int n1 = (COUNTS && ca) ? (int)ca[i] : K;
-        const int n2 = (COUNTS && cb) ? (int)cb[j] : K;
-        float v;
-        uint32_t c;
-        pw_entry<K, COUNTS>(a + i * 2 * K, b + j * 2 * K, n1, n2, flags, v, c, err);
-        iou[e] = v;
-        if (nx) nx[e] = (uint8_t)c;
+    for (; base < total; base += stride) {
+        const int64_t e = base + lane;
+        const bool act = e < total;
+        const int n1 = (COUNTS && ca && act) ? (int)ca[i] : K;
+        const int n2 = (COUNTS && cb && act) ? (int)cb[j] : K;
+        const float* pa = a + (act ? i : 0) * 2 * K;
+        const float* pb = b + (act ? j : 0) * 2 * K;
+        float v = 0.f;
+        uint32_t c = 0;
+        const bool hard = act && pw_fast<K, COUNTS>(pa, pb, n1, n2, v, c, err);
+        pw_finish<K>(__ballot_sync(0xffffffffu, hard), pa, pb, n1, n2, refine, v, c, err);
+        if (act) {
+            iou[e] = v;
+            if (nx) nx[e] = (uint8_t)c;
+        }
         i += di;
         j += dj;
         if (j >= M) {
@@ -143,6 +181,8 @@ __global__ void k_batched(int S, const int64_t* __restrict__ a_off, const int64_
                           const int64_t* __restrict__ tile_start, int64_t tile, uint32_t flags, uint32_t* status) {
     __shared__ int64_t s_tile;
     __shared__ int s_scene;
+    const int lane = threadIdx.x & 31;
+    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
     const int64_t total = tile_start[S];
     uint32_t err = 0;
     for (;;) {
@@ -165,18 +205,26 @@ __global__ void k_batched(int S, const int64_t* __restrict__ a_off, const int64_
         const int64_t Ms = b_off[s + 1] - b0, E = out_off[s + 1] - o0;
         const int64_t e0 = (t - tile_start[s]) * tile;
         const int64_t e1 = min(e0 + tile, E);
-        int64_t e = e0 + threadIdx.x;
-        if (e >= e1) continue;
+        // warp-uniform steps over the tile: lane l takes entry wbase + l
+        int64_t wbase = e0 + (threadIdx.x & ~31);
+        if (wbase >= e1) continue;
+        int64_t e = wbase + lane;
         int64_t i = e / Ms, j = e - (e / Ms) * Ms;
         const int64_t di = (int64_t)blockDim.x / Ms, dj = (int64_t)blockDim.x - di * Ms;
-        for (; e < e1; e += blockDim.x) {
-            const int n1 = (COUNTS && ca) ? (int)ca[a0 + i] : K;
-            const int n2 = (COUNTS && cb) ? (int)cb[b0 + j] : K;
-            float v;
-            uint32_t c;
-            pw_entry<K, COUNTS>(a + (a0 + i) * 2 * K, b + (b0 + j) * 2 * K, n1, n2, flags, v, c, err);
-            iou[o0 + e] = v;
-            if (nx) nx[o0 + e] = (uint8_t)c;
+        for (; wbase < e1; wbase += blockDim.x, e += blockDim.x) {
+            const bool act = e < e1;
+            const int n1 = (COUNTS && ca && act) ? (int)ca[a0 + i] : K;
+            const int n2 = (COUNTS && cb && act) ? (int)cb[b0 + j] : K;
+            const float* pa = a + (act ? a0 + i : 0) * 2 * K;
+            const float* pb = b + (act ? b0 + j : 0) * 2 * K;
+            float v = 0.f;
+            uint32_t c = 0;
+            const bool hard = act && pw_fast<K, COUNTS>(pa, pb, n1, n2, v, c, err);
+            pw_finish<K>(__ballot_sync(0xffffffffu, hard), pa, pb, n1, n2, refine, v, c, err);
+            if (act) {
+                iou[o0 + e] = v;
+                if (nx) nx[o0 + e] = (uint8_t)c;
+            }
             i += di;
             j += dj;
             if (j >= Ms) {
