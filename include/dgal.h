@@ -104,15 +104,18 @@ dgal_status dgal_iou_backward(const float* p1, const uint8_t* c1, const float* p
                               float* grad_p1, float* grad_p2, uint32_t flags, void* stream);
 
 /*
- * Fused IoU loss, forward and backward in one pass (the rotated-box IoU-loss
- * use of the library, paper Sec. IV-A):
+ * IoU loss with its gradient (the rotated-box IoU-loss use of the library,
+ * paper Sec. IV-A):
  *   loss[0] = scale * sum_k w_k (1 - IoU(p1[k], p2[k]))      (w = NULL: all 1)
  *   grad_p1, grad_p2 = d loss / d p1, d p2  (float [n][K][2]; both NULL to skip)
  *   iou (float [n], optional) receives the IoUs.
- * K = 4 only.  No flags are stored: each pair's intersection state goes from
- * the clip straight into the backward.  The loss is reduced per block into
- * `workspace` (at least dgal_iou_loss_workspace_bytes(n, K) bytes, 16-byte
- * aligned) and then summed in a fixed order, so it is deterministic.
+ * K = 4 or 8.  Runs the paired forward with the loss terms summed per warp and
+ * the flags kept in `workspace`, then the paired backward with
+ * dL/dIoU_k = -scale w_k formed in the kernel, then sums the per-warp partials
+ * in a fixed order, so the loss is deterministic.  `workspace`: device memory
+ * of at least dgal_iou_loss_workspace_bytes(n, K) bytes (0 for an invalid K),
+ * 16-byte aligned, caller-owned; calls sharing it must not overlap in time.
+ * DGAL_PLAIN: FP32 only, and the backward recomputes the clip.
  * n = 0 writes loss[0] = 0.
  */
 size_t dgal_iou_loss_workspace_bytes(int64_t n, int K);

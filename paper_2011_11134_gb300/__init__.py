@@ -107,8 +107,10 @@ def dgal_iou_loss_workspace_bytes(n, K=4):
 
 def dgal_iou_loss(p1, p2, weight=None, scale=1.0, c1=None, c2=None, grads=True, with_iou=False,
                   flags=DGAL_FP64_REFINE, stream=None, workspace=None, out=None):
-    """Fused IoU loss: returns (loss [1], g1 | None, g2 | None, iou | None) with
-    loss = scale * sum w (1 - IoU) and g = d loss / d p."""
+    """IoU loss (K = 4 or 8): returns (loss [1], g1 | None, g2 | None, iou | None)
+    with loss = scale * sum w (1 - IoU) and g = d loss / d p.  `workspace`
+    (uint8, dgal_iou_loss_workspace_bytes(n, K) bytes) holds the per-warp
+    partials and the flags passed from the forward to the backward."""
     _poly(p1, "p1")
     _poly(p2, "p2")
     if p1.shape != p2.shape:
@@ -304,7 +306,7 @@ def iou(p1, p2, c1=None, c2=None, recompute=False, flags=DGAL_FP64_REFINE):
 
 
 class IoULoss(torch.autograd.Function):
-    """loss = scale * sum w (1 - IoU) with the fused kernel: the forward pass
+    """loss = scale * sum w (1 - IoU) through dgal_iou_loss: the forward pass
     already computes d loss / d p, and the backward only scales it by the
     incoming gradient."""
 

@@ -170,15 +170,14 @@ dgal_status dgal_iou_pairwise(const float* a, const uint8_t* ca, int64_t N, cons
 }
 
 size_t dgal_iou_loss_workspace_bytes(int64_t n, int K) {
-    (void)K;
-    return n < 0 ? 0 : loss_workspace_bytes(n);
+    return (n < 0 || (K != 4 && K != 8)) ? 0 : loss_workspace_bytes(n, K);
 }
 
 dgal_status dgal_iou_loss(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n, int K,
                           const float* weight, float scale, float* loss, float* iou, float* grad_p1, float* grad_p2,
                           void* workspace, size_t ws_bytes, uint32_t flags, void* stream) {
     t_last_error.clear();
-    if (K != 4) return fail(DGAL_ERR_UNSUPPORTED_K, "dgal_iou_loss supports K = 4 (got %d)", K);
+    if (K != 4 && K != 8) return fail(DGAL_ERR_UNSUPPORTED_K, "K must be 4 or 8 (got %d)", K);
     if (n < 0) return fail(DGAL_ERR_INVALID_ARG, "n = %lld is negative", (long long)n);
     if (!loss) return fail(DGAL_ERR_INVALID_ARG, "loss is NULL");
     if (!aligned(loss, 4)) return fail(DGAL_ERR_ALIGNMENT, "loss is not 4-byte aligned");
@@ -198,8 +197,8 @@ dgal_status dgal_iou_loss(const float* p1, const uint8_t* c1, const float* p2, c
     if (iou && !aligned(iou, 4)) return fail(DGAL_ERR_ALIGNMENT, "iou is not 4-byte aligned");
     if (!workspace) return fail(DGAL_ERR_WORKSPACE, "workspace is NULL");
     if (!aligned(workspace, 16)) return fail(DGAL_ERR_ALIGNMENT, "workspace is not 16-byte aligned");
-    if (ws_bytes < loss_workspace_bytes(n))
-        return fail(DGAL_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", ws_bytes, loss_workspace_bytes(n));
+    if (ws_bytes < loss_workspace_bytes(n, K))
+        return fail(DGAL_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", ws_bytes, loss_workspace_bytes(n, K));
     return launch_iou_loss(p1, c1, p2, c2, n, K, weight, scale, loss, iou, grad_p1, grad_p2, workspace, flags,
                            (cudaStream_t)stream);
 }

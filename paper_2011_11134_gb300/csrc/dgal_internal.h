@@ -39,7 +39,7 @@ dgal_status launch_paired_bwd(const float* p1, const uint8_t* c1, const float* p
 dgal_status launch_pairwise(const float* a, const uint8_t* ca, int64_t N, const float* b, const uint8_t* cb,
                             int64_t M, int K, float* iou, uint8_t* nx, uint32_t flags, cudaStream_t s);
 size_t batched_workspace_bytes(int S);
-size_t loss_workspace_bytes(int64_t n);
+size_t loss_workspace_bytes(int64_t n, int K);
 dgal_status launch_iou_loss(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n, int K,
                             const float* weight, float scale, float* loss, float* iou, float* g1, float* g2,
                             void* ws, uint32_t flags, cudaStream_t s);

@@ -57,21 +57,45 @@ template <int K> __device__ __forceinline__ void store_poly(float* __restrict__ 
 // cannot take (not in general position, or with refinement a tiny
 // intersection) runs the shoelace adjoint on its own lane after the rest.
 
-template <int K, bool COUNTS, bool SAVE>
+// IoU-loss mode of the paired kernels (paper Sec. IV-A, the IoU loss over
+// rotated boxes): the forward adds scale * w_k (1 - IoU_k) into one partial
+// per warp, and the backward takes dL/dIoU_k = -scale * w_k (w = 1 when
+// weight is NULL) instead of reading an upstream gradient.
+struct LossArgs {
+    const float* weight;
+    float scale;
+    float* partials; // one float per warp of the forward grid
+};
+
+__device__ __forceinline__ float loss_weight(const LossArgs& la, int64_t k) {
+    return la.weight ? __ldg(la.weight + k) : 1.f;
+}
+
+__device__ __forceinline__ void put_partial(const LossArgs& la, float acc) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) la.partials[((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5] = acc;
+}
+
+template <int K, bool COUNTS, bool SAVE, bool LOSS>
 __global__ void __launch_bounds__(kPairThreads)
 k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
              const uint8_t* __restrict__ c2, int64_t n, float* __restrict__ iou, uint8_t* __restrict__ nx,
-             uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status) {
+             uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status,
+             LossArgs la) {
     constexpr unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * kPairThreads;
     const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
     uint32_t err = 0;
+    float acc = 0.f;
     for (int64_t base = (int64_t)blockIdx.x * kPairThreads + (threadIdx.x & ~31); base < n; base += stride) {
         const int64_t k = base + lane;
         int n1 = K, n2 = K;
         bool hard = false;
+        float w = 0.f;
         if (k < n) {
+            if (LOSS) w = loss_weight(la, k);
             if (COUNTS) {
                 n1 = c1 ? (int)c1[k] : K;
                 n2 = c2 ? (int)c2[k] : K;
@@ -98,7 +122,8 @@ k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
                 }
             }
             if (!hard) {
-                iou[k] = o.iou;
+                if (LOSS) acc += la.scale * w * (1.f - o.iou);
+                if (!LOSS || iou) iou[k] = o.iou;
                 if (SAVE) {
                     nx[k] = (uint8_t)o.nx;
                     store_codes<K>(xflags, k, o.codes);
@@ -117,7 +142,8 @@ k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
             warp_robust<K>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, refine, o);
             if (lane == src) {
                 err |= o.err;
-                iou[kk] = o.iou;
+                if (LOSS) acc += la.scale * w * (1.f - o.iou);
+                if (!LOSS || iou) iou[kk] = o.iou;
                 if (SAVE) {
                     nx[kk] = (uint8_t)o.nx;
                     store_codes<K>(xflags, kk, o.codes);
@@ -126,15 +152,16 @@ k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
             }
         }
     }
+    if (LOSS) put_partial(la, acc);
     if (err) atomicOr(status, err);
 }
 
-template <int K, bool COUNTS, bool RECOMPUTE>
+template <int K, bool COUNTS, bool RECOMPUTE, bool LOSS>
 __global__ void __launch_bounds__(kPairThreads)
 k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
              const uint8_t* __restrict__ c2, int64_t n, const float* __restrict__ grad,
              const uint8_t* __restrict__ nxs, const uint8_t* __restrict__ xflags, float* __restrict__ g1,
-             float* __restrict__ g2, uint32_t flags, uint32_t* status) {
+             float* __restrict__ g2, uint32_t flags, uint32_t* status, LossArgs la) {
     constexpr unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * kPairThreads;
@@ -173,7 +200,7 @@ k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
                     load_codes<K>(xflags, k, codes);
                 }
                 uint32_t e = kSlow;
-                if (have) e = bwd_shape<K, COUNTS>(g, __ldg(grad + k), nxk, codes, refine, g1x, g1y, g2x, g2y);
+                if (have) e = bwd_shape<K, COUNTS>(g, LOSS ? -la.scale * loss_weight(la, k) : __ldg(grad + k), nxk, codes, refine, g1x, g1y, g2x, g2y);
                 needfwd = !have;
                 slow = (e == kSlow);
                 if (!slow) err |= e;
@@ -201,7 +228,7 @@ k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
             }
         }
         if (slow) {
-            const float gk = __ldg(grad + k);
+            const float gk = LOSS ? -la.scale * loss_weight(la, k) : __ldg(grad + k);
             err |= refine ? bwd_shoelace<K, double>(p1 + k * 2 * K, p2 + k * 2 * K, n1, n2, gk, nxk, codes,
                                                     g1 + k * 2 * K, g2 + k * 2 * K)
                           : bwd_shoelace<K, float>(p1 + k * 2 * K, p2 + k * 2 * K, n1, n2, gk, nxk, codes,
@@ -214,30 +241,34 @@ k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
 // K = 8: one group of 8 lanes per pair (group8.cuh), 4 pairs per warp and
 // step, grid-stride over warps.  Pairs the group cannot finish are done by the
 // whole warp (forward) or by the group's first lane (backward) afterwards.
-template <bool SAVE>
+template <bool SAVE, bool LOSS>
 __global__ void __launch_bounds__(kPairThreads)
 k_paired_fwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
                 const uint8_t* __restrict__ c2, int64_t n, float* __restrict__ iou, uint8_t* __restrict__ nx,
-                uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status) {
+                uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status,
+                LossArgs la) {
     constexpr unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, r = lane & 7;
     const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
     const int64_t warp = ((int64_t)blockIdx.x * kPairThreads + threadIdx.x) >> 5;
     const int64_t stride = (int64_t)gridDim.x * (kPairThreads / 32) * 4;
     uint32_t err = 0;
+    float acc = 0.f;
     for (int64_t base = warp * 4; base < n; base += stride) {
         const int64_t k = base + (lane >> 3);
         const bool act = k < n;
         const int n1 = (act && c1) ? (int)c1[k] : 8, n2 = (act && c2) ? (int)c2[k] : 8;
         const bool good = act && n1 >= 3 && n1 <= 8 && n2 >= 3 && n2 <= 8;
         bool hard = false;
+        const float w = (LOSS && act && r == 0) ? loss_weight(la, k) : 0.f;
         if (good) {
             g8::Lane L;
             g8::load_lane(p1 + k * 16, p2 + k * 16, n1, n2, r, L);
             g8::FwdG o;
             hard = !g8::fwd_group(L, o);
             if (!hard && r == 0) {
-                iou[k] = o.iou;
+                if (LOSS) acc += la.scale * w * (1.f - o.iou);
+                if (!LOSS || iou) iou[k] = o.iou;
                 if (SAVE) {
                     nx[k] = (uint8_t)o.nx;
                     reinterpret_cast<uint4*>(xflags)[k] =
@@ -247,7 +278,8 @@ k_paired_fwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
             }
         } else if (act && r == 0) {
             err |= kDevBadCount;
-            iou[k] = 0.f;
+            if (LOSS) acc += la.scale * w;
+            if (!LOSS || iou) iou[k] = 0.f;
             if (SAVE) {
                 nx[k] = 0;
                 reinterpret_cast<uint4*>(xflags)[k] = make_uint4(~0u, ~0u, ~0u, ~0u);
@@ -265,7 +297,8 @@ k_paired_fwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
             warp_robust<8>(p1 + kk * 16, p2 + kk * 16, m1, m2, refine, o);
             if (lane == src) {
                 err |= o.err;
-                iou[kk] = o.iou;
+                if (LOSS) acc += la.scale * w * (1.f - o.iou);
+                if (!LOSS || iou) iou[kk] = o.iou;
                 if (SAVE) {
                     nx[kk] = (uint8_t)o.nx;
                     store_codes<8>(xflags, kk, o.codes);
@@ -274,15 +307,16 @@ k_paired_fwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
             }
         }
     }
+    if (LOSS) put_partial(la, acc);
     if (err) atomicOr(status, err);
 }
 
-template <bool RECOMPUTE>
+template <bool RECOMPUTE, bool LOSS>
 __global__ void __launch_bounds__(kPairThreads)
 k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
                 const uint8_t* __restrict__ c2, int64_t n, const float* __restrict__ grad,
                 const uint8_t* __restrict__ nxs, const uint8_t* __restrict__ xflags, float* __restrict__ g1,
-                float* __restrict__ g2, uint32_t flags, uint32_t* status) {
+                float* __restrict__ g2, uint32_t flags, uint32_t* status, LossArgs la) {
     constexpr unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, r = lane & 7;
     const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
@@ -314,7 +348,7 @@ k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
                 nxk = nxs[k];
             }
             uint32_t e = kSlow;
-            if (!needfwd) e = g8::bwd_group(L, __ldg(grad + k), nxk, w0, w1, refine, gx1, gy1, gx2, gy2);
+            if (!needfwd) e = g8::bwd_group(L, LOSS ? -la.scale * loss_weight(la, k) : __ldg(grad + k), nxk, w0, w1, refine, gx1, gy1, gx2, gy2);
             slow = e == kSlow;
             if (!slow) {
                 if (r == 0) err |= e;
@@ -348,7 +382,7 @@ k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
             Codes<8> codes;
             codes.w[0] = w0;
             codes.w[1] = w1;
-            const float gk = __ldg(grad + k);
+            const float gk = LOSS ? -la.scale * loss_weight(la, k) : __ldg(grad + k);
             err |= refine ? bwd_shoelace<8, double>(p1 + k * 16, p2 + k * 16, n1, n2, gk, nxk, codes, g1 + k * 16,
                                                     g2 + k * 16)
                           : bwd_shoelace<8, float>(p1 + k * 16, p2 + k * 16, n1, n2, gk, nxk, codes, g1 + k * 16,
@@ -358,14 +392,16 @@ k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
     if (err) atomicOr(status, err);
 }
 
-// ------------------------------------------------------------- fused loss
+// ------------------------------------------------------------- IoU loss
 //
-// loss = scale * sum_k w_k (1 - IoU_k) and its gradient in one pass (the
-// IoU-loss case study, paper Sec. IV-A): each pair is clipped, its IoU and
-// in-register state go straight into the shape-derivative backward with
-// dL/dIoU = -scale w_k, and no flags are stored or read back.  Per-thread
-// loss terms are reduced per block into partials[blockIdx.x]; a second
-// one-block kernel sums the partials in a fixed order (deterministic).
+// loss = scale * sum_k w_k (1 - IoU_k) and its gradient (the IoU-loss case
+// study, paper Sec. IV-A) in three launches on one stream: the paired forward
+// in loss mode (no IoU array needed; flags saved to the workspace), the paired
+// backward in loss mode (dL/dIoU formed in the kernel), and a one-block sum of
+// the per-warp partials in a fixed order, so the loss is deterministic.  A
+// single kernel doing both passes was measured slower: with the forward and
+// backward code resident together it needs about 1.5x the registers and
+// stalls on instruction fetch.
 
 __device__ __forceinline__ float block_sum(float v, float* sh) {
 #pragma unroll
@@ -381,100 +417,6 @@ __device__ __forceinline__ float block_sum(float v, float* sh) {
         for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
     }
     return t;
-}
-
-template <bool COUNTS, bool GRADS>
-__global__ void __launch_bounds__(kPairThreads)
-k_iou_loss4(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
-            const uint8_t* __restrict__ c2, int64_t n, const float* __restrict__ weight, float scale,
-            float* __restrict__ iou, float* __restrict__ g1, float* __restrict__ g2, float* __restrict__ partials,
-            uint32_t flags, uint32_t* status) {
-    constexpr int K = 4;
-    constexpr unsigned full = 0xffffffffu;
-    __shared__ float sh[kPairThreads / 32];
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * kPairThreads;
-    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
-    uint32_t err = 0;
-    float acc = 0.f;
-    for (int64_t base = (int64_t)blockIdx.x * kPairThreads + (threadIdx.x & ~31); base < n; base += stride) {
-        const int64_t k = base + lane;
-        int n1 = K, n2 = K;
-        bool hard = false, slow = false;
-        float w = 0.f, iv = 0.f;
-        Codes<K> codes;
-        codes_fill<K>(codes, ~0ull);
-        uint32_t nxk = 0;
-        if (k < n) {
-            if (COUNTS) {
-                n1 = c1 ? (int)c1[k] : K;
-                n2 = c2 ? (int)c2[k] : K;
-            }
-            w = weight ? __ldg(weight + k) : 1.f;
-            float gx1[K], gy1[K], gx2[K], gy2[K];
-#pragma unroll
-            for (int v = 0; v < K; ++v) { gx1[v] = gy1[v] = gx2[v] = gy2[v] = 0.f; }
-            if (COUNTS && (n1 < 3 || n1 > K || n2 < 3 || n2 > K)) {
-                err |= kDevBadCount;
-            } else {
-                float px[K], py[K], qx[K], qy[K];
-                load_poly<K>(p1 + k * 2 * K, px, py);
-                load_poly<K>(p2 + k * 2 * K, qx, qy);
-                Geo<K> g;
-                make_geo<K, COUNTS>(px, py, qx, qy, n1, n2, g);
-                FwdOut<K> o;
-                input_areas<K, COUNTS>(g, o.a1, o.a2);
-                hard = !fwd_generic<K, COUNTS>(g, o);
-                if (!hard) {
-                    const float U = o.a1 + o.a2 - o.ai;
-                    iv = (o.nx >= 3u && U > 0.f) ? o.ai / U : 0.f;
-                    if (GRADS) {
-                        const uint32_t e = bwd_shape<K, COUNTS>(g, -scale * w, o.nx, o.codes, refine, gx1, gy1, gx2, gy2);
-                        slow = e == kSlow;
-                        if (!slow) err |= e;
-                        codes = o.codes;
-                        nxk = o.nx;
-                    }
-                }
-            }
-            if (!hard) {
-                acc += scale * w * (1.f - iv);
-                if (iou) iou[k] = iv;
-                if (GRADS && !slow) {
-                    store_poly<K>(g1 + k * 2 * K, gx1, gy1);
-                    store_poly<K>(g2 + k * 2 * K, gx2, gy2);
-                }
-            }
-        }
-        unsigned todo = __ballot_sync(full, hard);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int64_t kk = base + src;
-            const int m1 = __shfl_sync(full, n1, src), m2 = __shfl_sync(full, n2, src);
-            FwdOut<K> o;
-            o.err = 0;
-            warp_robust<K>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, refine, o);
-            if (lane == src) {
-                err |= o.err;
-                iv = o.iou;
-                codes = o.codes;
-                nxk = o.nx;
-                acc += scale * w * (1.f - iv);
-                if (iou) iou[kk] = iv;
-                slow = true;
-            }
-        }
-        if (GRADS && slow) {
-            err |= refine ? bwd_shoelace<K, double>(p1 + k * 2 * K, p2 + k * 2 * K, n1, n2, -scale * w, nxk, codes,
-                                                    g1 + k * 2 * K, g2 + k * 2 * K)
-                          : bwd_shoelace<K, float>(p1 + k * 2 * K, p2 + k * 2 * K, n1, n2, -scale * w, nxk, codes,
-                                                   g1 + k * 2 * K, g2 + k * 2 * K);
-        }
-    }
-    const float tot = block_sum(acc, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
-    if (err) atomicOr(status, err);
 }
 
 __global__ void __launch_bounds__(1024) k_sum_partials(const float* __restrict__ partials, int m, float* __restrict__ out) {
@@ -493,88 +435,127 @@ static unsigned grid_for(int64_t n, int threads) {
     return (unsigned)blocks;
 }
 
-template <int K, bool COUNTS>
+// Grid of the paired kernels: one thread per pair for K = 4, one group of 8
+// lanes per pair for K = 8.
+static unsigned paired_grid(int64_t n, int K) {
+    return K == 4 ? grid_for(n, kPairThreads) : grid_for((n + 3) / 4 * 32, kPairThreads);
+}
+
+template <int K, bool COUNTS, bool LOSS>
 static void fwd_dispatch(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
-                         float* iou, uint8_t* nx, uint8_t* xflags, uint8_t* degen, uint32_t flags, cudaStream_t s) {
-    const unsigned grid = grid_for(n, kPairThreads);
+                         float* iou, uint8_t* nx, uint8_t* xflags, uint8_t* degen, uint32_t flags, cudaStream_t s,
+                         const LossArgs& la) {
+    const unsigned grid = paired_grid(n, K);
     uint32_t* st = device_status_ptr();
-    if (nx) k_paired_fwd<K, COUNTS, true><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st);
-    else k_paired_fwd<K, COUNTS, false><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st);
+    if constexpr (K == 4) {
+        if (nx) k_paired_fwd<K, COUNTS, true, LOSS><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st, la);
+        else k_paired_fwd<K, COUNTS, false, LOSS><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st, la);
+    } else {
+        if (nx) k_paired_fwd_g8<true, LOSS><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st, la);
+        else k_paired_fwd_g8<false, LOSS><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st, la);
+    }
+}
+
+template <bool LOSS>
+static void fwd_any(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n, int K,
+                    float* iou, uint8_t* nx, uint8_t* xflags, uint8_t* degen, uint32_t flags, cudaStream_t s,
+                    const LossArgs& la) {
+    if (K == 4) {
+        if (c1 || c2) fwd_dispatch<4, true, LOSS>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, s, la);
+        else fwd_dispatch<4, false, LOSS>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, s, la);
+    } else {
+        fwd_dispatch<8, true, LOSS>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, s, la);
+    }
 }
 
 dgal_status launch_paired_fwd(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
                               int K, float* iou, uint8_t* nx, uint8_t* xflags, uint8_t* degen, uint32_t flags,
                               cudaStream_t s) {
     if (!device_status_ptr()) return fail(DGAL_ERR_CUDA, "device status word unavailable");
-    const bool counts = c1 || c2;
-    if (K == 4) {
-        if (counts) fwd_dispatch<4, true>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, s);
-        else fwd_dispatch<4, false>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, s);
-    } else {
-        const unsigned grid = grid_for((n + 3) / 4 * 32, kPairThreads);
-        uint32_t* st = device_status_ptr();
-        if (nx) k_paired_fwd_g8<true><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st);
-        else k_paired_fwd_g8<false><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st);
-    }
+    fwd_any<false>(p1, c1, p2, c2, n, K, iou, nx, xflags, degen, flags, s, LossArgs{nullptr, 0.f, nullptr});
     return check_launch("paired forward");
 }
 
-template <int K, bool COUNTS>
+template <int K, bool COUNTS, bool LOSS>
 static void bwd_dispatch(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
                          const float* grad, const uint8_t* nx, const uint8_t* xflags, float* g1, float* g2,
-                         uint32_t flags, cudaStream_t s) {
-    const unsigned grid = grid_for(n, kPairThreads);
+                         uint32_t flags, cudaStream_t s, const LossArgs& la) {
+    const unsigned grid = paired_grid(n, K);
     uint32_t* st = device_status_ptr();
-    if (nx && xflags && !(flags & kFlagPlain))
-        k_paired_bwd<K, COUNTS, false><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, st);
-    else
-        k_paired_bwd<K, COUNTS, true><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, st);
+    const bool saved = nx && xflags && !(flags & kFlagPlain);
+    if constexpr (K == 4) {
+        if (saved)
+            k_paired_bwd<K, COUNTS, false, LOSS><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, st, la);
+        else
+            k_paired_bwd<K, COUNTS, true, LOSS><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, st, la);
+    } else {
+        if (saved)
+            k_paired_bwd_g8<false, LOSS><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, st, la);
+        else
+            k_paired_bwd_g8<true, LOSS><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, st, la);
+    }
+}
+
+template <bool LOSS>
+static void bwd_any(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n, int K,
+                    const float* grad, const uint8_t* nx, const uint8_t* xflags, float* g1, float* g2,
+                    uint32_t flags, cudaStream_t s, const LossArgs& la) {
+    if (K == 4) {
+        if (c1 || c2) bwd_dispatch<4, true, LOSS>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, s, la);
+        else bwd_dispatch<4, false, LOSS>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, s, la);
+    } else {
+        bwd_dispatch<8, true, LOSS>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, s, la);
+    }
 }
 
 dgal_status launch_paired_bwd(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
                               int K, const float* grad, const uint8_t* nx, const uint8_t* xflags, float* g1,
                               float* g2, uint32_t flags, cudaStream_t s) {
     if (!device_status_ptr()) return fail(DGAL_ERR_CUDA, "device status word unavailable");
-    const bool counts = c1 || c2;
-    if (K == 4) {
-        if (counts) bwd_dispatch<4, true>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, s);
-        else bwd_dispatch<4, false>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, s);
-    } else {
-        const unsigned grid = grid_for((n + 3) / 4 * 32, kPairThreads);
-        uint32_t* st = device_status_ptr();
-        if (nx && xflags && !(flags & kFlagPlain))
-            k_paired_bwd_g8<false><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, st);
-        else
-            k_paired_bwd_g8<true><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, st);
-    }
+    bwd_any<false>(p1, c1, p2, c2, n, K, grad, nx, xflags, g1, g2, flags, s, LossArgs{nullptr, 0.f, nullptr});
     return check_launch("paired backward");
 }
 
-size_t loss_workspace_bytes(int64_t n) {
-    const int64_t blocks = (int64_t)grid_for(n < 1 ? 1 : n, kPairThreads);
-    return (size_t)(((blocks * 4) + 255) / 256 * 256);
+// Loss workspace: [per-warp partials | nx (n bytes) | xflags (n x 2K bytes)],
+// each part 256-byte aligned.
+struct LossLayout {
+    size_t partials, nx, xflags, total;
+    int64_t warps;
+};
+
+static LossLayout loss_layout(int64_t n, int K) {
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    LossLayout L;
+    L.warps = (int64_t)paired_grid(n < 1 ? 1 : n, K) * (kPairThreads / 32);
+    L.partials = 0;
+    L.nx = up((size_t)L.warps * 4);
+    L.xflags = L.nx + up((size_t)n);
+    L.total = L.xflags + up((size_t)n * 2 * K);
+    return L;
 }
+
+size_t loss_workspace_bytes(int64_t n, int K) { return loss_layout(n, K).total; }
 
 dgal_status launch_iou_loss(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n, int K,
                             const float* weight, float scale, float* loss, float* iou, float* g1, float* g2,
                             void* ws, uint32_t flags, cudaStream_t s) {
     if (!device_status_ptr()) return fail(DGAL_ERR_CUDA, "device status word unavailable");
-    const unsigned grid = grid_for(n, kPairThreads);
-    float* partials = static_cast<float*>(ws);
-    uint32_t* st = device_status_ptr();
-    const bool counts = c1 || c2;
-    if (K != 4) return fail(DGAL_ERR_UNSUPPORTED_K, "the fused loss supports K = 4");
-    if (counts) {
-        if (g1) k_iou_loss4<true, true><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, iou, g1, g2, partials, flags, st);
-        else k_iou_loss4<true, false><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, iou, g1, g2, partials, flags, st);
-    } else {
-        if (g1) k_iou_loss4<false, true><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, iou, g1, g2, partials, flags, st);
-        else k_iou_loss4<false, false><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, iou, g1, g2, partials, flags, st);
-    }
-    dgal_status r = check_launch("fused IoU loss");
+    const LossLayout L = loss_layout(n, K);
+    unsigned char* base = static_cast<unsigned char*>(ws);
+    const LossArgs la{weight, scale, reinterpret_cast<float*>(base + L.partials)};
+    const bool save = g1 && !(flags & kFlagPlain);
+    uint8_t* nx = save ? base + L.nx : nullptr;
+    uint8_t* xflags = save ? base + L.xflags : nullptr;
+    fwd_any<true>(p1, c1, p2, c2, n, K, iou, nx, xflags, nullptr, flags, s, la);
+    dgal_status r = check_launch("IoU loss forward");
     if (r != DGAL_OK) return r;
-    k_sum_partials<<<1, 1024, 0, s>>>(partials, (int)grid, loss);
-    return check_launch("fused IoU loss reduction");
+    if (g1) {
+        bwd_any<true>(p1, c1, p2, c2, n, K, nullptr, nx, xflags, g1, g2, flags, s, la);
+        r = check_launch("IoU loss backward");
+        if (r != DGAL_OK) return r;
+    }
+    k_sum_partials<<<1, 1024, 0, s>>>(la.partials, (int)L.warps, loss);
+    return check_launch("IoU loss reduction");
 }
 
 } // namespace dgal

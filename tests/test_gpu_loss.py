@@ -1,4 +1,5 @@
-"""GPU parity of the fused IoU loss (forward + backward in one pass)."""
+"""GPU parity of the IoU loss call (loss-mode forward, loss-mode backward,
+deterministic partial sum)."""
 import numpy as np
 import pytest
 
@@ -62,5 +63,24 @@ def test_fused_loss_autograd_and_edges(dg):
     lz, _, _, _ = dg.dgal_iou_loss(z, z)
     assert host(lz)[0] == 0.0
     with pytest.raises(dg.DgalError):
-        dg.dgal_iou_loss(dev(W.convex_pairs_4m(seed=1, n=8, degenerate_frac=0)["p1"]),
-                         dev(W.convex_pairs_4m(seed=2, n=8, degenerate_frac=0)["p2"]))
+        dg.dgal_iou_loss(p1.detach(), p2.detach(), workspace=torch.empty(16, device="cuda", dtype=torch.uint8))
+
+
+def test_loss_k8_counts_matches_oracle(dg, orc):
+    import torch
+
+    d = W.convex_pairs_4m(seed=5, n=60_000)
+    n = d["p1"].shape[0]
+    w = np.linspace(0.5, 1.5, n).astype(np.float32)
+    p1, p2, c1, c2 = dev(d["p1"]), dev(d["p2"]), dev(d["c1"]), dev(d["c2"])
+    loss, g1, g2, iou = dg.dgal_iou_loss(p1, p2, dev(w), 2.0, c1=c1, c2=c2, with_iou=True)
+    ref_loss, r1, r2, f = orc.iou_loss(d["p1"], d["p2"], weight=w.astype(np.float64), scale=2.0, c1=d["c1"],
+                                       c2=d["c2"], threads=THREADS)
+    assert abs(host(loss)[0] - ref_loss) <= IOU_ATOL * 2.0 * np.abs(w).sum() + 1e-6 * abs(ref_loss)
+    assert np.abs(host(iou) - f["iou"]).max() <= IOU_ATOL
+    _, nx, xf, degen = dg.dgal_iou_paired(p1, p2, c1, c2, with_degen=True)
+    gen = (f["degen"] == 0) & (host(degen) == 0)
+    rel = grad_rel_err(host(g1), host(g2), r1, r2, gen)
+    assert rel.max() <= GRAD_RTOL, rel.max()
+    b1, b2 = dg.dgal_iou_backward(p1, p2, -2.0 * dev(w), nx, xf, c1=c1, c2=c2)
+    assert torch.equal(b1, g1) and torch.equal(b2, g2)
