@@ -32,6 +32,17 @@ namespace dgal {
 
 constexpr float kDegenRel = 1e-5f; // near-degenerate threshold (relative to L^2, or to t, u in (0, 1))
 
+// Routing threshold of the FP32 fast paths, relative to L^2 (L = largest
+// |local coordinate| of the pair).  An orientation evaluated in the local
+// frame as (c - b) x (a - b) differs from the exact orientation of the input
+// points by at most 48 u L^2 (u = 2^-24) to first order: 16 u L^2 from
+// rounding the three points into the local frame and 32 u L^2 from the four
+// differences, two products and one subtraction (each difference bounded by
+// 2L).  That is 2.9e-6 L^2, so every orientation with |value| > 5e-6 L^2 has
+// its exact sign, and the fast path decides only those pairs.  Pairs with an
+// orientation between this and kDegenRel are still reported near-degenerate.
+constexpr float kRouteRel = 5e-6f;
+
 // device status bits (mirror include/dgal.h)
 constexpr uint32_t kDevBadCount = 0x1u;
 constexpr uint32_t kDevOverflow = 0x2u;
@@ -219,7 +230,7 @@ template <int K, bool COUNTS> __device__ __forceinline__ bool fwd_generic(const 
     const int n1 = g.n1, n2 = g.n2;
 
     const float L = pair_scale<K, COUNTS>(g);
-    const float thr = kDegenRel * L * L;
+    const float thr = kRouteRel * L * L;
 
     // Orientation values: S(i,j) = orient(b_j, b_j+1, a_i), T(i,j) =
     // orient(a_i, a_i+1, b_j).  Kept for K = 4, recomputed for K = 8.
@@ -242,6 +253,7 @@ template <int K, bool COUNTS> __device__ __forceinline__ bool fwd_generic(const 
         }
     }
     if (!(L > 0.f) || !(minabs > thr)) return false;
+    o.degen = (minabs <= kDegenRel * L * L) ? 1u : 0u;
 
     M V = (M)~(M)0;
     if constexpr (KK < 8 * (int)sizeof(M)) V = (M)((1ull << KK) - 1);
@@ -448,18 +460,37 @@ __device__ __forceinline__ float pseudo_angle(float dx, float dy) {
 //
 // All 32 lanes of a warp work on one pair, with the candidate rules of the
 // definition (inclusive vertex tests, strict crossings, exact duplicates
-// dropped, angular order rotated to the smallest code).  Each orientation test runs on its own
-// lane, in FP64 from the raw inputs when refining; the signs are combined by
-// ballot, each candidate vertex is computed on its own lane, candidates are
-// ranked by comparing against every other lane, and the area is a shuffle
-// reduction of shoelace terms taken about the candidates' centroid.  The
-// result is returned in every lane.
+// dropped, angular order rotated to the smallest code).  Each orientation test
+// runs on its own lane, in FP32 in the local frame and, when refining and the
+// FP32 value is too small for its sign to be certain, in FP64 from the raw
+// inputs (exact signs); the signs are combined by ballot, each candidate vertex is computed
+// on its own lane (a crossing's parameters from the orientation values of the
+// lanes that tested its edges), candidates are ranked by comparing against
+// every other lane, and the areas are shuffle reductions of shoelace terms.
+// The areas are taken in FP32 with an estimate of their rounding error; when
+// refining and that estimate is not far below the IoU tolerance (slivers,
+// tiny intersections), they are taken again in FP64 about the candidates'
+// centroid.  GB300's FP64 rate is a small fraction of its FP32 rate, so FP64
+// is kept to the orientation tests and that fallback.  The result is
+// returned in every lane.
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     return v;
 }
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return __shfl_sync(0xffffffffu, v, 0); // one value in every lane
+}
+
+// FP32 area results accepted when 2 u (L P + T) / U, an estimate of the IoU
+// rounding error (P: summed edge lengths of the intersection, T: summed
+// magnitudes of all shoelace products), is below this (the IoU tolerance is
+// 1e-5).
+constexpr float kAreaEstMax = 2e-6f;
 
 template <int K>
 __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const float* __restrict__ p2, int n1, int n2,
@@ -484,6 +515,7 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
 
     // orientation tests: index q < KK is S(i,j), KK <= q < 2KK is T(i,j)
     M posS = 0, negS = 0, posT = 0, negT = 0;
+    float vf[ROUNDS];
     bool deg = !(Lf > 0.f);
 #pragma unroll
     for (int r = 0; r < ROUNDS; ++r) {
@@ -496,9 +528,14 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
         const float Ax = isT ? sel<K>(px, i) : sel<K>(qx, j), Ay = isT ? sel<K>(py, i) : sel<K>(qy, j);
         const float Bx = isT ? sel<K>(px, i1) : sel<K>(qx, j1), By = isT ? sel<K>(py, i1) : sel<K>(qy, j1);
         const float Px = isT ? sel<K>(qx, j) : sel<K>(px, i), Py = isT ? sel<K>(qy, j) : sel<K>(py, i);
-        double v;
-        if (refine) v = orient64(Ax, Ay, Bx, By, Px, Py);
-        else v = orient32nc(Ax - ox, Ay - oy, Bx - ox, By - oy, Px - ox, Py - oy);
+        // FP32 in the local frame first: beyond kRouteRel L^2 its sign is
+        // exact (see kRouteRel); only the lanes below take the FP64 test
+        double v = (double)orient32nc(Ax - ox, Ay - oy, Bx - ox, By - oy, Px - ox, Py - oy);
+        const bool need = refine && valid && !(fabs(v) > (double)kRouteRel * (double)Lf * (double)Lf);
+        if (__any_sync(full, need)) {
+            if (need) v = orient64(Ax, Ay, Bx, By, Px, Py);
+        }
+        vf[r] = (float)v;
         deg |= valid && fabs(v) <= thr;
         const unsigned bp = __ballot_sync(full, valid && v > 0.0), bn = __ballot_sync(full, valid && v < 0.0);
         if constexpr (K == 4) {
@@ -559,23 +596,19 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
     o.ai = 0.f;
     o.iou = 0.f;
     codes_fill<K>(o.codes, ~0ull);
-    double x = 0.0, y = 0.0;
-    uint32_t code = 0xFFu;
-    bool deg2 = false;
-    if (lane < m && m <= C) {
-        const int c = lane;
-        if (c < c1n) {
-            const int i = (int)__fns(in1, 0, c + 1);
-            code = (uint32_t)i;
-            x = (double)sel<K>(px, i) - (double)ox;
-            y = (double)sel<K>(py, i) - (double)oy;
-        } else if (c < c1n + c2n) {
-            const int j = (int)__fns(in2, 0, c - c1n + 1);
-            code = 0x40u | (uint32_t)j;
-            x = (double)sel<K>(qx, j) - (double)ox;
-            y = (double)sel<K>(qy, j) - (double)oy;
+
+    // candidate of this lane: a vertex (t = 0) or a crossing a + t (a1 - a)
+    const bool live = lane < m && m <= C;
+    int ci = 0, cj = 0, kind = 3;
+    if (live) {
+        if (lane < c1n) {
+            kind = 0;
+            ci = (int)__fns(in1, 0, lane + 1);
+        } else if (lane < c1n + c2n) {
+            kind = 1;
+            cj = (int)__fns(in2, 0, lane - c1n + 1);
         } else {
-            const int cc = c - c1n - c2n;
+            const int cc = lane - c1n - c2n;
             int b;
             if constexpr (K == 4) {
                 b = (int)__fns((uint32_t)X, 0, cc + 1);
@@ -584,33 +617,51 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
                 const int nlo = __popc(lo);
                 b = (cc < nlo) ? (int)__fns(lo, 0, cc + 1) : 32 + (int)__fns(hi, 0, cc - nlo + 1);
             }
-            const int i = b / K, j = b % K;
-            const int i1 = (i + 1 < n1) ? i + 1 : 0, j1 = (j + 1 < n2) ? j + 1 : 0;
-            code = 0x80u | ((uint32_t)i << 3) | (uint32_t)j;
-            const float ax0 = sel<K>(px, i), ay0 = sel<K>(py, i), ax1 = sel<K>(px, i1), ay1 = sel<K>(py, i1);
-            const float bx0 = sel<K>(qx, j), by0 = sel<K>(qy, j), bx1 = sel<K>(qx, j1), by1 = sel<K>(qy, j1);
-            double Sa, Sb, Ta, Tb;
-            if (refine) {
-                Sa = orient64(bx0, by0, bx1, by1, ax0, ay0);
-                Sb = orient64(bx0, by0, bx1, by1, ax1, ay1);
-                Ta = orient64(ax0, ay0, ax1, ay1, bx0, by0);
-                Tb = orient64(ax0, ay0, ax1, ay1, bx1, by1);
-            } else {
-                Sa = orient32nc(bx0 - ox, by0 - oy, bx1 - ox, by1 - oy, ax0 - ox, ay0 - oy);
-                Sb = orient32nc(bx0 - ox, by0 - oy, bx1 - ox, by1 - oy, ax1 - ox, ay1 - oy);
-                Ta = orient32nc(ax0 - ox, ay0 - oy, ax1 - ox, ay1 - oy, bx0 - ox, by0 - oy);
-                Tb = orient32nc(ax0 - ox, ay0 - oy, ax1 - ox, ay1 - oy, bx1 - ox, by1 - oy);
-            }
-            // the crossing parameters only place a vertex along its edge, so
-            // they are FP32 quotients of the (FP64) orientation differences
-            const float t = (float)Sa / (float)(Sa - Sb), u = (float)Ta / (float)(Ta - Tb);
-            x = ((double)ax0 - (double)ox) + (double)t * ((double)ax1 - (double)ax0);
-            y = ((double)ay0 - (double)oy) + (double)t * ((double)ay1 - (double)ay0);
-            const float rx = ax1 - ax0, ry = ay1 - ay0, sx = bx1 - bx0, sy = by1 - by0;
-            const float D = rx * sy - ry * sx;
-            deg2 = t <= kDegenRel || t >= 1.0f - kDegenRel || u <= kDegenRel || u >= 1.0f - kDegenRel ||
-                   D * D <= kDegenRel * kDegenRel * (rx * rx + ry * ry) * (sx * sx + sy * sy);
+            kind = 2;
+            ci = b / K;
+            cj = b % K;
         }
+    }
+    const int ci1 = (ci + 1 < n1) ? ci + 1 : 0, cj1 = (cj + 1 < n2) ? cj + 1 : 0;
+    // S(i,j), S(i+1,j) and T(i,j), T(i,j+1) from the lanes that computed them
+    const int qs[4] = {ci * K + cj, ci1 * K + cj, KK + ci * K + cj, KK + ci * K + cj1};
+    float ov[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        ov[f] = 0.f;
+#pragma unroll
+        for (int r = 0; r < ROUNDS; ++r) {
+            const float t = __shfl_sync(full, vf[r], qs[f] & 31);
+            ov[f] = ((qs[f] >> 5) == r) ? t : ov[f];
+        }
+    }
+    uint32_t code = 0xFFu;
+    float fx0 = 0.f, fy0 = 0.f, fx1 = 0.f, fy1 = 0.f, t = 0.f;
+    bool deg2 = false;
+    if (kind == 0) {
+        code = (uint32_t)ci;
+        fx0 = fx1 = sel<K>(px, ci);
+        fy0 = fy1 = sel<K>(py, ci);
+    } else if (kind == 1) {
+        code = 0x40u | (uint32_t)cj;
+        fx0 = fx1 = sel<K>(qx, cj);
+        fy0 = fy1 = sel<K>(qy, cj);
+    } else if (kind == 2) {
+        code = 0x80u | ((uint32_t)ci << 3) | (uint32_t)cj;
+        fx0 = sel<K>(px, ci);
+        fy0 = sel<K>(py, ci);
+        fx1 = sel<K>(px, ci1);
+        fy1 = sel<K>(py, ci1);
+        const float bx0 = sel<K>(qx, cj), by0 = sel<K>(qy, cj), bx1 = sel<K>(qx, cj1), by1 = sel<K>(qy, cj1);
+        // the crossing parameters only place a vertex along its edge, so they
+        // are FP32 quotients of the orientation values (of opposite signs at
+        // a strict crossing, so the differences do not cancel)
+        t = ov[0] / (ov[0] - ov[1]);
+        const float u = ov[2] / (ov[2] - ov[3]);
+        const float rx = fx1 - fx0, ry = fy1 - fy0, sx = bx1 - bx0, sy = by1 - by0;
+        const float D = rx * sy - ry * sx;
+        deg2 = t <= kDegenRel || t >= 1.0f - kDegenRel || u <= kDegenRel || u >= 1.0f - kDegenRel ||
+               D * D <= kDegenRel * kDegenRel * (rx * rx + ry * ry) * (sx * sx + sy * sy);
     }
     deg = __any_sync(full, deg || deg2);
     o.degen = (deg ? 1u : 0u) | (refine ? 2u : 0u);
@@ -620,30 +671,25 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
         return;
     }
     if (m < 3) return;
+    const float x = (fx0 - ox) + t * (fx1 - fx0), y = (fy0 - oy) + t * (fy1 - fy0);
 
     // angular order about the centroid, ties by code; rotate to the smallest code
-    float cxs = (lane < m) ? (float)x : 0.f, cys = (lane < m) ? (float)y : 0.f;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        cxs += __shfl_xor_sync(full, cxs, off);
-        cys += __shfl_xor_sync(full, cys, off);
-    }
-    const double mx = (double)(cxs / (float)m), my = (double)(cys / (float)m);
-    const float key = (lane < m) ? pseudo_angle((float)(x - mx), (float)(y - my)) : __int_as_float(0x7f800000);
+    const float mxf = warp_sum_f(live ? x : 0.f) / (float)m, myf = warp_sum_f(live ? y : 0.f) / (float)m;
+    const float key = live ? pseudo_angle(x - mxf, y - myf) : __int_as_float(0x7f800000);
     int rank = 0;
     for (int l = 0; l < m; ++l) {
         const float k2 = __shfl_sync(full, key, l);
         const uint32_t c2 = __shfl_sync(full, code, l);
         rank += (k2 < key || (k2 == key && c2 < code)) ? 1 : 0;
     }
-    uint32_t cmin = (lane < m) ? code : 0xFFFFu;
+    uint32_t cmin = live ? code : 0xFFFFu;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) cmin = min(cmin, __shfl_xor_sync(full, cmin, off));
-    const int src = __ffs(__ballot_sync(full, lane < m && code == cmin)) - 1;
+    const int src = __ffs(__ballot_sync(full, live && code == cmin)) - 1;
     const int r0 = __shfl_sync(full, rank, src);
     const int slot = (rank - r0 + m) % m;
     unsigned long long w0 = 0, w1 = 0;
-    if (lane < m) {
+    if (live) {
         if (slot < 8) w0 = (unsigned long long)code << (8 * slot);
         else w1 = (unsigned long long)code << (8 * (slot - 8));
     }
@@ -657,56 +703,77 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
     o.codes.w[0] = w0 | fill0;
     if constexpr (K > 4) o.codes.w[1] = w1 | fill1;
 
-    // shoelace about the centroid: the next vertex is the lane whose slot is slot + 1
+    // lane holding the next vertex (slot + 1) of the cycle
     const int target = (slot + 1 == m) ? 0 : slot + 1;
-    double nxp = 0.0, nyp = 0.0;
-    for (int l = 0; l < m; ++l) {
-        const int s2 = __shfl_sync(full, slot, l);
-        const double xx = __shfl_sync(full, x, l), yy = __shfl_sync(full, y, l);
-        if (s2 == target) { nxp = xx; nyp = yy; }
+    int nl = 0;
+    for (int s2 = 0; s2 < m; ++s2) {
+        const unsigned bs = __ballot_sync(full, live && slot == s2);
+        nl = (s2 == target) ? __ffs(bs) - 1 : nl;
     }
-    double term = 0.0;
-    if (lane < m) {
-        if (refine) term = __dsub_rn(__dmul_rn(x - mx, nyp - my), __dmul_rn(y - my, nxp - mx));
-        else term = (double)((float)(x - mx) * (float)(nyp - my) - (float)(y - my) * (float)(nxp - mx));
+    const float xn = __shfl_sync(full, x, nl), yn = __shfl_sync(full, y, nl);
+
+    // FP32 areas: the intersection about its centroid, each input about its
+    // first vertex, with the magnitudes of their products
+    float term = 0.f, mag = 0.f, edge = 0.f;
+    if (live) {
+        const float ux = x - mxf, uy = y - myf, vx = xn - mxf, vy = yn - myf;
+        term = ux * vy - uy * vx;
+        mag = fabsf(ux * vy) + fabsf(uy * vx);
+        edge = fabsf(xn - x) + fabsf(yn - y);
     }
-    const double ai = 0.5 * warp_sum(term);
-    // input areas, one shoelace term per lane
-    double a1 = 0.0, a2 = 0.0;
-    {
-        const int v = lane & 7;
-        const bool second = lane >= 8 && lane < 16;
-        const int n = second ? n2 : n1;
-        const bool on = lane < 16 && v < n;
-        const int w = (v + 1 < n) ? v + 1 : 0;
-        const float* xs = second ? qx : px;
-        const float* ys = second ? qy : py;
-        double term2 = 0.0;
-        if (on) {
-            float xv = 0.f, yv = 0.f, xw = 0.f, yw = 0.f;
+    float term2 = 0.f, mag2 = 0.f;
+    const int v = lane & 7;
+    const bool second = lane >= 8 && lane < 16;
+    const int nv = second ? n2 : n1;
+    const bool on = lane < 16 && v < nv;
+    const int wv = (v + 1 < nv) ? v + 1 : 0;
+    float xv = 0.f, yv = 0.f, xw = 0.f, yw = 0.f;
 #pragma unroll
-            for (int m2 = 0; m2 < K; ++m2) {
-                xv = (m2 == v) ? xs[m2] : xv;
-                yv = (m2 == v) ? ys[m2] : yv;
-                xw = (m2 == w) ? xs[m2] : xw;
-                yw = (m2 == w) ? ys[m2] : yw;
-            }
-            const double Xv = (double)xv - ox, Yv = (double)yv - oy, Xw = (double)xw - ox, Yw = (double)yw - oy;
-            term2 = refine ? __dsub_rn(__dmul_rn(Xv, Yw), __dmul_rn(Yv, Xw))
-                           : (double)((float)Xv * (float)Yw - (float)Yv * (float)Xw);
-        }
-        const double s1 = warp_sum((lane < 8) ? term2 : 0.0), s2 = warp_sum(second ? term2 : 0.0);
-        a1 = s1;
-        a2 = s2;
+    for (int m2 = 0; m2 < K; ++m2) {
+        xv = (m2 == v) ? (second ? qx[m2] : px[m2]) : xv;
+        yv = (m2 == v) ? (second ? qy[m2] : py[m2]) : yv;
+        xw = (m2 == wv) ? (second ? qx[m2] : px[m2]) : xw;
+        yw = (m2 == wv) ? (second ? qy[m2] : py[m2]) : yw;
     }
-    a1 *= 0.5;
-    a2 *= 0.5;
-    const double U = a1 + a2 - ai;
+    const float bx = second ? qx[0] : px[0], by = second ? qy[0] : py[0];
+    if (on) {
+        const float Xv = xv - bx, Yv = yv - by, Xw = xw - bx, Yw = yw - by;
+        term2 = Xv * Yw - Yv * Xw;
+        mag2 = fabsf(Xv * Yw) + fabsf(Yv * Xw);
+    }
+    const float ai = 0.5f * warp_sum_f(term);
+    const float a1 = 0.5f * warp_sum_f(lane < 8 ? term2 : 0.f);
+    const float a2 = 0.5f * warp_sum_f(second ? term2 : 0.f);
+    const float magsum = warp_sum_f(mag + mag2), perim = warp_sum_f(edge);
+    float U = a1 + a2 - ai;
+    const float est = 2.f * 5.9604645e-8f * (Lf * 2.f * perim + magsum);
     o.nx = (uint32_t)m;
-    o.ai = (float)ai;
-    o.a1 = (float)a1;
-    o.a2 = (float)a2;
-    o.iou = (U > 0.0) ? (float)(ai / U) : 0.f;
+    o.ai = ai;
+    o.a1 = a1;
+    o.a2 = a2;
+    if (refine && !(est <= kAreaEstMax * U)) {
+        // FP64 areas: vertices placed on their edges in FP64, the intersection
+        // about the candidates' centroid, the inputs about P1's vertex 0
+        const double X64 = ((double)fx0 - (double)ox) + (double)t * ((double)fx1 - (double)fx0);
+        const double Y64 = ((double)fy0 - (double)oy) + (double)t * ((double)fy1 - (double)fy0);
+        const double mx = warp_sum(live ? X64 : 0.0) / (double)m, my = warp_sum(live ? Y64 : 0.0) / (double)m;
+        const double nxp = __shfl_sync(full, X64, nl), nyp = __shfl_sync(full, Y64, nl);
+        const double tm = live ? __dsub_rn(__dmul_rn(X64 - mx, nyp - my), __dmul_rn(Y64 - my, nxp - mx)) : 0.0;
+        double t2 = 0.0;
+        if (on) {
+            const double Xv = (double)xv - ox, Yv = (double)yv - oy, Xw = (double)xw - ox, Yw = (double)yw - oy;
+            t2 = __dsub_rn(__dmul_rn(Xv, Yw), __dmul_rn(Yv, Xw));
+        }
+        const double ai64 = 0.5 * warp_sum(tm);
+        const double a164 = 0.5 * warp_sum(lane < 8 ? t2 : 0.0), a264 = 0.5 * warp_sum(second ? t2 : 0.0);
+        o.ai = (float)ai64;
+        o.a1 = (float)a164;
+        o.a2 = (float)a264;
+        const double U64 = a164 + a264 - ai64;
+        o.iou = (U64 > 0.0) ? (float)(ai64 / U64) : 0.f;
+        return;
+    }
+    o.iou = (U > 0.f) ? ai / U : 0.f;
 }
 
 // ---------------------------------------------------------------- backward

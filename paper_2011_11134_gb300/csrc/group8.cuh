@@ -127,6 +127,7 @@ struct FwdG {
     uint64_t w0, w1; // the 16 code bytes
     float iou;
     uint32_t nx;
+    uint32_t degen; // near-degenerate (some orientation within kDegenRel L^2)
 };
 
 // Group forward.  Returns false (in every lane of the group) when the pair
@@ -140,7 +141,7 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) Lr = fmaxf(Lr, (j < n2) ? fmaxf(fabsf(L.bx[j]), fabsf(L.by[j])) : 0.f);
     Lr = gmax(gm, Lr);
-    const float thr = kDegenRel * Lr * Lr;
+    const float thr = kRouteRel * Lr * Lr;
 
     // row r of S and T
     uint32_t sneg = 0, tneg = 0;
@@ -156,6 +157,7 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
     }
     mn = gmin(gm, mn);
     if (!(Lr > 0.f) || !(mn > thr)) return false;
+    out.degen = (mn <= kDegenRel * Lr * Lr) ? 1u : 0u;
     const uint32_t colv = (1u << n2) - 1u;
     const uint64_t sp = gor64(gm, liveA ? (uint64_t)(~sneg & colv) << (8 * r) : 0ull);
     const uint64_t tp = gor64(gm, liveA ? (uint64_t)(~tneg & colv) << (8 * r) : 0ull);

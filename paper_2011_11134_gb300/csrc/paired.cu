@@ -52,10 +52,19 @@ template <int K> __device__ __forceinline__ void store_poly(float* __restrict__ 
 // Both kernels walk the pairs warp by warp (32 consecutive pairs per warp and
 // step, grid-stride over warps), with no block-wide barrier.  In the forward,
 // a pair the fast path cannot finish (near-degenerate or not in general
-// position) is finished afterwards by the whole warp together
-// (warp_robust).  In the backward, a pair whose codes the shape derivative
-// cannot take (not in general position, or with refinement a tiny
-// intersection) runs the shoelace adjoint on its own lane after the rest.
+// position) is only marked; a second kernel (k_paired_fix) scans the marks
+// and finishes each marked pair with the whole warp (warp_robust).  Keeping
+// the robust path out of the main kernel keeps its registers and its FP64
+// latency out of the common case.  In the backward, a pair whose codes the
+// shape derivative cannot take (not in general position, or with refinement
+// a tiny intersection) runs the shoelace adjoint on its own lane after the
+// rest.
+
+// Mark of a pair left to k_paired_fix: an IoU of this signalling-NaN bit
+// pattern (arithmetic never produces it: NaN results are the canonical NaN)
+// or, in loss mode, nx = kHardNx.
+constexpr uint32_t kHardIou = 0x7fbadbadu;
+constexpr uint8_t kHardNx = 0xFFu;
 
 // IoU-loss mode of the paired kernels (paper Sec. IV-A, the IoU loss over
 // rotated boxes): the forward adds scale * w_k (1 - IoU_k) into one partial
@@ -83,10 +92,9 @@ k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
              const uint8_t* __restrict__ c2, int64_t n, float* __restrict__ iou, uint8_t* __restrict__ nx,
              uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status,
              LossArgs la) {
-    constexpr unsigned full = 0xffffffffu;
+    (void)flags;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * kPairThreads;
-    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
     uint32_t err = 0;
     float acc = 0.f;
     for (int64_t base = (int64_t)blockIdx.x * kPairThreads + (threadIdx.x & ~31); base < n; base += stride) {
@@ -131,26 +139,87 @@ k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
                 if (degen) degen[k] = (uint8_t)o.degen;
             }
         }
-        unsigned todo = __ballot_sync(full, hard);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int64_t kk = base + src;
-            const int m1 = __shfl_sync(full, n1, src), m2 = __shfl_sync(full, n2, src);
+        if (hard) {
+            if (LOSS) nx[k] = kHardNx;
+            else reinterpret_cast<uint32_t*>(iou)[k] = kHardIou;
+        }
+    }
+    if (LOSS) put_partial(la, acc);
+    if (err) atomicOr(status, err);
+}
+
+// Second forward pass: finishes the pairs the main kernel marked, each with
+// the whole warp (warp_robust), and writes all of their outputs.  Each block
+// owns a contiguous range of segments of kFixSeg pairs (normally one): the
+// block reads the segment's marks (4 B per pair, or 1 B in loss mode,
+// coalesced), queues the marked pairs in shared memory, and its warps then
+// take the queue in turn, so the robust calls of a segment run at once.
+constexpr int kFixThreads = 256;
+constexpr int kFixSeg = 1024;
+
+// One segment per block while that fits the grid: short-lived blocks let each
+// SM overlap many robust calls (a block that meets none exits after its scan).
+static unsigned fix_grid(int64_t n) {
+    const int64_t segs = (n + kFixSeg - 1) / kFixSeg;
+    const int64_t cap = (int64_t)1 << 30;
+    return (unsigned)(segs < 1 ? 1 : (segs < cap ? segs : cap));
+}
+
+template <int K, bool LOSS>
+__global__ void __launch_bounds__(kFixThreads)
+k_paired_fix(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
+             const uint8_t* __restrict__ c2, int64_t n, float* __restrict__ iou, uint8_t* __restrict__ nx,
+             uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status,
+             LossArgs la) {
+    constexpr unsigned full = 0xffffffffu;
+    constexpr int kWarps = kFixThreads / 32;
+    __shared__ int q[kFixSeg];
+    __shared__ int qn;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
+    const int64_t segs = (n + kFixSeg - 1) / kFixSeg;
+    const int64_t per = (segs + gridDim.x - 1) / gridDim.x;
+    const int64_t s0 = (int64_t)blockIdx.x * per, s1 = (s0 + per < segs) ? s0 + per : segs;
+    uint32_t err = 0;
+    float acc = 0.f;
+    if (threadIdx.x == 0) qn = 0;
+    __syncthreads();
+    for (int64_t sg = s0; sg < s1; ++sg) {
+        const int64_t base = sg * kFixSeg;
+#pragma unroll
+        for (int r = 0; r < kFixSeg / kFixThreads; ++r) {
+            const int off = r * kFixThreads + (int)threadIdx.x;
+            const int64_t k = base + off;
+            bool hard = false;
+            if (k < n) hard = LOSS ? (nx[k] == kHardNx) : (__ldg(reinterpret_cast<const uint32_t*>(iou) + k) == kHardIou);
+            const unsigned b = __ballot_sync(full, hard);
+            int pos = 0;
+            if (lane == 0 && b) pos = atomicAdd(&qn, __popc(b));
+            pos = __shfl_sync(full, pos, 0);
+            if (hard) q[pos + __popc(b & ((1u << lane) - 1u))] = off;
+        }
+        __syncthreads();
+        const int m = qn;
+        for (int e = warp; e < m; e += kWarps) {
+            const int64_t kk = base + q[e];
+            const int m1 = c1 ? (int)c1[kk] : K, m2 = c2 ? (int)c2[kk] : K;
             FwdOut<K> o;
             o.err = 0;
             warp_robust<K>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, refine, o);
-            if (lane == src) {
+            if (lane == 0) {
                 err |= o.err;
-                if (LOSS) acc += la.scale * w * (1.f - o.iou);
+                if (LOSS) acc += la.scale * loss_weight(la, kk) * (1.f - o.iou);
                 if (!LOSS || iou) iou[kk] = o.iou;
-                if (SAVE) {
+                if (nx) {
                     nx[kk] = (uint8_t)o.nx;
                     store_codes<K>(xflags, kk, o.codes);
                 }
                 if (degen) degen[kk] = (uint8_t)o.degen;
             }
         }
+        __syncthreads();
+        if (threadIdx.x == 0) qn = 0;
+        __syncthreads();
     }
     if (LOSS) put_partial(la, acc);
     if (err) atomicOr(status, err);
@@ -247,9 +316,8 @@ k_paired_fwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
                 const uint8_t* __restrict__ c2, int64_t n, float* __restrict__ iou, uint8_t* __restrict__ nx,
                 uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status,
                 LossArgs la) {
-    constexpr unsigned full = 0xffffffffu;
+    (void)flags;
     const int lane = threadIdx.x & 31, r = lane & 7;
-    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
     const int64_t warp = ((int64_t)blockIdx.x * kPairThreads + threadIdx.x) >> 5;
     const int64_t stride = (int64_t)gridDim.x * (kPairThreads / 32) * 4;
     uint32_t err = 0;
@@ -274,7 +342,7 @@ k_paired_fwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
                     reinterpret_cast<uint4*>(xflags)[k] =
                         make_uint4((uint32_t)o.w0, (uint32_t)(o.w0 >> 32), (uint32_t)o.w1, (uint32_t)(o.w1 >> 32));
                 }
-                if (degen) degen[k] = 0;
+                if (degen) degen[k] = (uint8_t)o.degen;
             }
         } else if (act && r == 0) {
             err |= kDevBadCount;
@@ -286,25 +354,9 @@ k_paired_fwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
             }
             if (degen) degen[k] = 0;
         }
-        unsigned todo = __ballot_sync(full, hard && r == 0);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int64_t kk = base + (src >> 3);
-            const int m1 = __shfl_sync(full, n1, src), m2 = __shfl_sync(full, n2, src);
-            FwdOut<8> o;
-            o.err = 0;
-            warp_robust<8>(p1 + kk * 16, p2 + kk * 16, m1, m2, refine, o);
-            if (lane == src) {
-                err |= o.err;
-                if (LOSS) acc += la.scale * w * (1.f - o.iou);
-                if (!LOSS || iou) iou[kk] = o.iou;
-                if (SAVE) {
-                    nx[kk] = (uint8_t)o.nx;
-                    store_codes<8>(xflags, kk, o.codes);
-                }
-                if (degen) degen[kk] = (uint8_t)o.degen;
-            }
+        if (hard && r == 0) {
+            if (LOSS) nx[k] = kHardNx;
+            else reinterpret_cast<uint32_t*>(iou)[k] = kHardIou;
         }
     }
     if (LOSS) put_partial(la, acc);
@@ -454,6 +506,9 @@ static void fwd_dispatch(const float* p1, const uint8_t* c1, const float* p2, co
         if (nx) k_paired_fwd_g8<true, LOSS><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st, la);
         else k_paired_fwd_g8<false, LOSS><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st, la);
     }
+    LossArgs lf = la;
+    if (LOSS) lf.partials = la.partials + (size_t)grid * (kPairThreads / 32);
+    k_paired_fix<K, LOSS><<<fix_grid(n), kFixThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st, lf);
 }
 
 template <bool LOSS>
@@ -526,7 +581,9 @@ struct LossLayout {
 static LossLayout loss_layout(int64_t n, int K) {
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     LossLayout L;
-    L.warps = (int64_t)paired_grid(n < 1 ? 1 : n, K) * (kPairThreads / 32);
+    // partials of the main forward, then of the fix pass
+    L.warps = (int64_t)paired_grid(n < 1 ? 1 : n, K) * (kPairThreads / 32) +
+              (int64_t)fix_grid(n < 1 ? 1 : n) * (kFixThreads / 32);
     L.partials = 0;
     L.nx = up((size_t)L.warps * 4);
     L.xflags = L.nx + up((size_t)n);
@@ -543,14 +600,16 @@ dgal_status launch_iou_loss(const float* p1, const uint8_t* c1, const float* p2,
     const LossLayout L = loss_layout(n, K);
     unsigned char* base = static_cast<unsigned char*>(ws);
     const LossArgs la{weight, scale, reinterpret_cast<float*>(base + L.partials)};
+    // the loss-mode forward always keeps nx (it carries the fix-pass marks)
     const bool save = g1 && !(flags & kFlagPlain);
-    uint8_t* nx = save ? base + L.nx : nullptr;
-    uint8_t* xflags = save ? base + L.xflags : nullptr;
+    uint8_t* nx = base + L.nx;
+    uint8_t* xflags = base + L.xflags;
     fwd_any<true>(p1, c1, p2, c2, n, K, iou, nx, xflags, nullptr, flags, s, la);
     dgal_status r = check_launch("IoU loss forward");
     if (r != DGAL_OK) return r;
     if (g1) {
-        bwd_any<true>(p1, c1, p2, c2, n, K, nullptr, nx, xflags, g1, g2, flags, s, la);
+        bwd_any<true>(p1, c1, p2, c2, n, K, nullptr, save ? nx : nullptr, save ? xflags : nullptr, g1, g2, flags, s,
+                      la);
         r = check_launch("IoU loss backward");
         if (r != DGAL_OK) return r;
     }
