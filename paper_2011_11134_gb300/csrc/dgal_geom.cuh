@@ -779,120 +779,146 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
 // ---------------------------------------------------------------- backward
 //
 // Main path (bwd_shape): the shape derivative of the area over the clipped
-// edge pieces named by the codes.  List path (bwd_shoelace): the recorded
-// codes rebuild the intersection vertices (crossings as w = a + t ea,
+// edge pieces named by the codes.  List path (warp_bwd, one warp per pair):
+// the recorded codes rebuild the intersection vertices (crossings as w = a + t ea,
 // t = cross(eb, a - b) / cross(ea, eb)), the shoelace adjoint
 // dA/dw_k = 1/2 perp(w_{k+1} - w_{k-1}) gives each vertex's gradient, vertex
 // codes route it to that vertex and crossing codes through the adjoint of w
 // onto the four endpoints of the two edges; FP64 with refinement.
 
-// Shoelace adjoint over the recorded vertex sequence in scalar type R, from the
-// raw inputs: vertex codes route straight to that vertex, crossing codes go
-// through w = a + t ea, t = cross(eb, a - b) / cross(ea, eb).
+// Warp-cooperative form of the shoelace adjoint, for the pairs the shape
+// derivative cannot take: all 32 lanes work on one pair.  Lane k rebuilds
+// intersection vertex k from its code (crossings as w = a + t ea in R) and
+// takes its neighbours by shuffle; the three areas are shuffle sums; each
+// lane's share dA/dw_k = 1/2 perp(w_{k+1} - w_{k-1}) goes to its vertex, or
+// through the adjoint of w onto the four endpoints of the crossing's edges,
+// by FP32 atomics into the warp's scratch sh[4K] (P1 x, P1 y, P2 x, P2 y);
+// lanes s K + v then add the input-area terms and write the gradients.
+// codes / nx / grad / counts are the pair's (uniform over the warp).  Returns
+// device status bits (the same in every lane).
 template <int K, typename R>
-__device__ __noinline__ uint32_t bwd_shoelace(const float* __restrict__ p1, const float* __restrict__ p2, int n1,
-                                              int n2, float grad, uint32_t nx, Codes<K> codes, float* __restrict__ g1,
-                                              float* __restrict__ g2) {
-    constexpr int C = 2 * K;
+__device__ __noinline__ uint32_t warp_bwd(const float* __restrict__ p1, const float* __restrict__ p2, int n1, int n2,
+                                          float grad, uint32_t nx, Codes<K> codes, float* __restrict__ g1,
+                                          float* __restrict__ g2, float* __restrict__ sh) {
+    constexpr unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     float px[K], py[K], qx[K], qy[K];
     load_poly<K>(p1, px, py);
     load_poly<K>(p2, qx, qy);
-    R ax[K], ay[K], bx[K], by[K], gax[K], gay[K], gbx[K], gby[K];
-    for (int v = 0; v < K; ++v) {
-        ax[v] = (R)px[v] - (R)px[0];
-        ay[v] = (R)py[v] - (R)py[0];
-        bx[v] = (R)qx[v] - (R)px[0];
-        by[v] = (R)qy[v] - (R)py[0];
-        gax[v] = gay[v] = gbx[v] = gby[v] = (R)0;
-    }
-    R wx[C], wy[C];
-    uint32_t err = 0;
-    for (uint32_t k = 0; k < nx; ++k) {
-        const uint32_t c = code_at<K>(codes, k);
-        const uint32_t kind = c >> 6, lo = c & 7u, ci = (c >> 3) & 7u;
-        if (kind == 0u && (c & 0x3Fu) < (uint32_t)n1) {
-            wx[k] = ax[lo];
-            wy[k] = ay[lo];
-        } else if (kind == 1u && (c & 0x3Fu) < (uint32_t)n2) {
-            wx[k] = bx[lo];
-            wy[k] = by[lo];
+    const R ox = (R)px[0], oy = (R)py[0];
+    if (lane < 4 * K) sh[lane] = 0.f;
+    __syncwarp();
+    const bool live = (uint32_t)lane < nx;
+    const uint32_t c = live ? code_at<K>(codes, (uint32_t)lane) : 0xFFu;
+    const uint32_t kind = c >> 6, lo = c & 7u, ci = (c >> 3) & 7u;
+    bool bad = false;
+    R wx = 0, wy = 0;
+    // crossing data kept for the adjoint
+    R eax = 0, eay = 0, ebx = 0, eby = 0, dx = 0, dy = 0, D = 1, t = 0;
+    int i1 = 0, j1 = 0;
+    if (live) {
+        if (kind == 0u) {
+            bad = (c & 0x3Fu) >= (uint32_t)n1;
+            wx = (R)sel<K>(px, lo) - ox;
+            wy = (R)sel<K>(py, lo) - oy;
+        } else if (kind == 1u) {
+            bad = (c & 0x3Fu) >= (uint32_t)n2;
+            wx = (R)sel<K>(qx, lo) - ox;
+            wy = (R)sel<K>(qy, lo) - oy;
         } else if (kind == 2u && ci < (uint32_t)n1 && lo < (uint32_t)n2) {
-            const int i1 = (ci + 1u < (uint32_t)n1) ? ci + 1 : 0, j1 = (lo + 1u < (uint32_t)n2) ? lo + 1 : 0;
-            const R eax = ax[i1] - ax[ci], eay = ay[i1] - ay[ci], ebx = bx[j1] - bx[lo], eby = by[j1] - by[lo];
-            const R D = eax * eby - eay * ebx;
-            const R S = ebx * (ay[ci] - by[lo]) - eby * (ax[ci] - bx[lo]);
-            if (!(D != (R)0)) { err = kDevBadFlags; break; }
-            const R t = S / D;
-            wx[k] = ax[ci] + t * eax;
-            wy[k] = ay[ci] + t * eay;
+            i1 = (ci + 1u < (uint32_t)n1) ? (int)ci + 1 : 0;
+            j1 = (lo + 1u < (uint32_t)n2) ? (int)lo + 1 : 0;
+            const R ax = (R)sel<K>(px, ci) - ox, ay = (R)sel<K>(py, ci) - oy;
+            const R bx = (R)sel<K>(qx, lo) - ox, by = (R)sel<K>(qy, lo) - oy;
+            eax = ((R)sel<K>(px, i1) - ox) - ax;
+            eay = ((R)sel<K>(py, i1) - oy) - ay;
+            ebx = ((R)sel<K>(qx, j1) - ox) - bx;
+            eby = ((R)sel<K>(qy, j1) - oy) - by;
+            dx = ax - bx;
+            dy = ay - by;
+            D = eax * eby - eay * ebx;
+            const R S = ebx * dy - eby * dx;
+            bad = !(D != (R)0);
+            t = bad ? (R)0 : S / D;
+            wx = ax + t * eax;
+            wy = ay + t * eay;
         } else {
-            err = kDevBadFlags;
-            break;
+            bad = true;
         }
     }
-    R a1 = 0, a2 = 0, twoA = 0;
-    for (int v = 0; v < n1; ++v) { const int w = (v + 1 < n1) ? v + 1 : 0; a1 += ax[v] * ay[w] - ay[v] * ax[w]; }
-    for (int v = 0; v < n2; ++v) { const int w = (v + 1 < n2) ? v + 1 : 0; a2 += bx[v] * by[w] - by[v] * bx[w]; }
-    for (uint32_t k = 0; err == 0u && k < nx; ++k) {
-        const uint32_t w = (k + 1 < nx) ? k + 1 : 0;
-        twoA += wx[k] * wy[w] - wy[k] * wx[w];
+    const uint32_t err = __any_sync(full, bad) ? kDevBadFlags : 0u;
+    const int nxt = (lane + 1 < (int)nx) ? lane + 1 : 0, prv = (lane == 0) ? (int)nx - 1 : lane - 1;
+    const R wxn = __shfl_sync(full, wx, nxt), wyn = __shfl_sync(full, wy, nxt);
+    const R wxp = __shfl_sync(full, wx, prv < 0 ? 0 : prv), wyp = __shfl_sync(full, wy, prv < 0 ? 0 : prv);
+    R twoA = live ? wx * wyn - wy * wxn : (R)0;
+    // input areas: lane v (P1) and lane K + v (P2) hold vertex v
+    const int side = (lane >= K && lane < 2 * K) ? 1 : 0;
+    const int v = lane - side * K;
+    const int nv = side ? n2 : n1;
+    const bool onv = lane < 2 * K && v < nv;
+    const int vn = (v + 1 < nv) ? v + 1 : 0, vp = (v == 0) ? nv - 1 : v - 1;
+    R xv = 0, yv = 0, xn = 0, yn = 0, xp = 0, yp = 0;
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+        const float fx = side ? qx[m] : px[m], fy = side ? qy[m] : py[m];
+        xv = (m == v) ? (R)fx - ox : xv;
+        yv = (m == v) ? (R)fy - oy : yv;
+        xn = (m == vn) ? (R)fx - ox : xn;
+        yn = (m == vn) ? (R)fy - oy : yn;
+        xp = (m == vp) ? (R)fx - ox : xp;
+        yp = (m == vp) ? (R)fy - oy : yp;
     }
-    a1 *= (R)0.5;
-    a2 *= (R)0.5;
-    const R ai = (R)0.5 * twoA, U = a1 + a2 - ai;
-    if (err == 0u && U > (R)0) {
-        const R gai = (R)grad * (a1 + a2) / (U * U);
-        const R ga12 = -(R)grad * ai / (U * U);
-        for (uint32_t k = 0; k < nx; ++k) {
-            const uint32_t kp = (k == 0) ? nx - 1 : k - 1, kn = (k + 1 < nx) ? k + 1 : 0;
-            const R gwx = (R)0.5 * gai * (wy[kn] - wy[kp]);
-            const R gwy = (R)0.5 * gai * (wx[kp] - wx[kn]);
-            const uint32_t c = code_at<K>(codes, k);
-            const uint32_t kind = c >> 6, lo = c & 7u, ci = (c >> 3) & 7u;
-            if (kind == 0u) {
-                gax[lo] += gwx;
-                gay[lo] += gwy;
-            } else if (kind == 1u) {
-                gbx[lo] += gwx;
-                gby[lo] += gwy;
-            } else {
-                const int i1 = (ci + 1u < (uint32_t)n1) ? ci + 1 : 0, j1 = (lo + 1u < (uint32_t)n2) ? lo + 1 : 0;
-                const R eax = ax[i1] - ax[ci], eay = ay[i1] - ay[ci], ebx = bx[j1] - bx[lo], eby = by[j1] - by[lo];
-                const R dx = ax[ci] - bx[lo], dy = ay[ci] - by[lo];
-                const R D = eax * eby - eay * ebx, S = ebx * dy - eby * dx, t = S / D;
-                const R gt = gwx * eax + gwy * eay;
-                const R gS = gt / D, gD = -gt * t / D;
-                const R geax = t * gwx + gD * eby, geay = t * gwy - gD * ebx;
-                const R gebx = gS * dy - gD * eay, geby = -gS * dx + gD * eax;
-                const R gdx = -gS * eby, gdy = gS * ebx;
-                gax[ci] += gwx + gdx - geax;
-                gay[ci] += gwy + gdy - geay;
-                gax[i1] += geax;
-                gay[i1] += geay;
-                gbx[lo] += -gdx - gebx;
-                gby[lo] += -gdy - geby;
-                gbx[j1] += gebx;
-                gby[j1] += geby;
-            }
-        }
-        for (int v = 0; v < n1; ++v) {
-            const int vp = (v == 0) ? n1 - 1 : v - 1, vn = (v + 1 < n1) ? v + 1 : 0;
-            gax[v] += (R)0.5 * ga12 * (ay[vn] - ay[vp]);
-            gay[v] += (R)0.5 * ga12 * (ax[vp] - ax[vn]);
-        }
-        for (int v = 0; v < n2; ++v) {
-            const int vp = (v == 0) ? n2 - 1 : v - 1, vn = (v + 1 < n2) ? v + 1 : 0;
-            gbx[v] += (R)0.5 * ga12 * (by[vn] - by[vp]);
-            gby[v] += (R)0.5 * ga12 * (bx[vp] - bx[vn]);
+    R aterm = onv ? xv * yn - yv * xn : (R)0;
+    R s1 = (lane < K) ? aterm : (R)0, s2 = side ? aterm : (R)0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        twoA += __shfl_xor_sync(full, twoA, off);
+        s1 += __shfl_xor_sync(full, s1, off);
+        s2 += __shfl_xor_sync(full, s2, off);
+    }
+    twoA = __shfl_sync(full, twoA, 0);
+    s1 = __shfl_sync(full, s1, 0);
+    s2 = __shfl_sync(full, s2, 0);
+    const R a1 = (R)0.5 * s1, a2 = (R)0.5 * s2, ai = (R)0.5 * twoA, U = a1 + a2 - ai;
+    const bool ok = err == 0u && nx >= 3u && U > (R)0;
+    const R gai = ok ? (R)grad * (a1 + a2) / (U * U) : (R)0;
+    const R ga12 = ok ? -(R)grad * ai / (U * U) : (R)0;
+    if (ok && live) {
+        const R gwx = (R)0.5 * gai * (wyn - wyp), gwy = (R)0.5 * gai * (wxp - wxn);
+        if (kind == 0u) {
+            atomicAdd(sh + lo, (float)gwx);
+            atomicAdd(sh + K + lo, (float)gwy);
+        } else if (kind == 1u) {
+            atomicAdd(sh + 2 * K + lo, (float)gwx);
+            atomicAdd(sh + 3 * K + lo, (float)gwy);
+        } else {
+            // w = a + t ea, t = S / D, S = cross(eb, a - b), D = cross(ea, eb)
+            const R gt = gwx * eax + gwy * eay;
+            const R gS = gt / D, gD = -gt * t / D;
+            const R geax = t * gwx + gD * eby, geay = t * gwy - gD * ebx;
+            const R gebx = gS * dy - gD * eay, geby = -gS * dx + gD * eax;
+            const R gdx = -gS * eby, gdy = gS * ebx;
+            atomicAdd(sh + ci, (float)(gwx + gdx - geax));
+            atomicAdd(sh + K + ci, (float)(gwy + gdy - geay));
+            atomicAdd(sh + i1, (float)geax);
+            atomicAdd(sh + K + i1, (float)geay);
+            atomicAdd(sh + 2 * K + lo, (float)(-gdx - gebx));
+            atomicAdd(sh + 3 * K + lo, (float)(-gdy - geby));
+            atomicAdd(sh + 2 * K + j1, (float)gebx);
+            atomicAdd(sh + 3 * K + j1, (float)geby);
         }
     }
-    for (int v = 0; v < K; ++v) {
-        const bool ok = err == 0u;
-        g1[2 * v] = (ok && v < n1) ? (float)gax[v] : 0.f;
-        g1[2 * v + 1] = (ok && v < n1) ? (float)gay[v] : 0.f;
-        g2[2 * v] = (ok && v < n2) ? (float)gbx[v] : 0.f;
-        g2[2 * v + 1] = (ok && v < n2) ? (float)gby[v] : 0.f;
+    __syncwarp();
+    if (lane < 2 * K) {
+        float gx = 0.f, gy = 0.f;
+        if (ok && onv) {
+            gx = sh[2 * side * K + v] + (float)((R)0.5 * ga12 * (yn - yp));
+            gy = sh[(2 * side + 1) * K + v] + (float)((R)0.5 * ga12 * (xp - xn));
+        }
+        float* g = side ? g2 : g1;
+        reinterpret_cast<float2*>(g)[v] = make_float2(gx, gy);
     }
+    __syncwarp();
     return err;
 }
 

@@ -57,8 +57,8 @@ template <int K> __device__ __forceinline__ void store_poly(float* __restrict__ 
 // the robust path out of the main kernel keeps its registers and its FP64
 // latency out of the common case.  In the backward, a pair whose codes the
 // shape derivative cannot take (not in general position, or with refinement
-// a tiny intersection) runs the shoelace adjoint on its own lane after the
-// rest.
+// a tiny intersection) takes the shoelace adjoint after the rest, with the
+// whole warp on it (warp_bwd).
 
 // Mark of a pair left to k_paired_fix: an IoU of this signalling-NaN bit
 // pattern (arithmetic never produces it: NaN results are the canonical NaN)
@@ -232,6 +232,7 @@ k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
              const uint8_t* __restrict__ nxs, const uint8_t* __restrict__ xflags, float* __restrict__ g1,
              float* __restrict__ g2, uint32_t flags, uint32_t* status, LossArgs la) {
     constexpr unsigned full = 0xffffffffu;
+    __shared__ float s_bwd[kPairThreads / 32][4 * K];
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * kPairThreads;
     const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
@@ -296,12 +297,22 @@ k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
                 }
             }
         }
-        if (slow) {
-            const float gk = LOSS ? -la.scale * loss_weight(la, k) : __ldg(grad + k);
-            err |= refine ? bwd_shoelace<K, double>(p1 + k * 2 * K, p2 + k * 2 * K, n1, n2, gk, nxk, codes,
-                                                    g1 + k * 2 * K, g2 + k * 2 * K)
-                          : bwd_shoelace<K, float>(p1 + k * 2 * K, p2 + k * 2 * K, n1, n2, gk, nxk, codes,
-                                                   g1 + k * 2 * K, g2 + k * 2 * K);
+        unsigned todo = __ballot_sync(full, slow);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t kk = base + src;
+            const int m1 = __shfl_sync(full, n1, src), m2 = __shfl_sync(full, n2, src);
+            const uint32_t mnx = __shfl_sync(full, nxk, src);
+            Codes<K> cs;
+#pragma unroll
+            for (int q = 0; q < (2 * K + 7) / 8; ++q) cs.w[q] = __shfl_sync(full, codes.w[q], src);
+            const float gk = LOSS ? -la.scale * loss_weight(la, kk) : __ldg(grad + kk);
+            const uint32_t e = refine ? warp_bwd<K, double>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, gk, mnx, cs,
+                                                            g1 + kk * 2 * K, g2 + kk * 2 * K, s_bwd[threadIdx.x >> 5])
+                                      : warp_bwd<K, float>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, gk, mnx, cs,
+                                                           g1 + kk * 2 * K, g2 + kk * 2 * K, s_bwd[threadIdx.x >> 5]);
+            if (lane == src) err |= e;
         }
     }
     if (err) atomicOr(status, err);
@@ -370,6 +381,7 @@ k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
                 const uint8_t* __restrict__ nxs, const uint8_t* __restrict__ xflags, float* __restrict__ g1,
                 float* __restrict__ g2, uint32_t flags, uint32_t* status, LossArgs la) {
     constexpr unsigned full = 0xffffffffu;
+    __shared__ float s_bwd[kPairThreads / 32][32];
     const int lane = threadIdx.x & 31, r = lane & 7;
     const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
     const int64_t warp = ((int64_t)blockIdx.x * kPairThreads + threadIdx.x) >> 5;
@@ -430,15 +442,22 @@ k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
                 }
             }
         }
-        if (slow && r == 0) {
-            Codes<8> codes;
-            codes.w[0] = w0;
-            codes.w[1] = w1;
-            const float gk = LOSS ? -la.scale * loss_weight(la, k) : __ldg(grad + k);
-            err |= refine ? bwd_shoelace<8, double>(p1 + k * 16, p2 + k * 16, n1, n2, gk, nxk, codes, g1 + k * 16,
-                                                    g2 + k * 16)
-                          : bwd_shoelace<8, float>(p1 + k * 16, p2 + k * 16, n1, n2, gk, nxk, codes, g1 + k * 16,
-                                                   g2 + k * 16);
+        unsigned todo = __ballot_sync(full, slow && r == 0);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t kk = base + (src >> 3);
+            const int m1 = __shfl_sync(full, n1, src), m2 = __shfl_sync(full, n2, src);
+            const uint32_t mnx = __shfl_sync(full, nxk, src);
+            Codes<8> cs;
+            cs.w[0] = __shfl_sync(full, w0, src);
+            cs.w[1] = __shfl_sync(full, w1, src);
+            const float gk = LOSS ? -la.scale * loss_weight(la, kk) : __ldg(grad + kk);
+            const uint32_t e = refine ? warp_bwd<8, double>(p1 + kk * 16, p2 + kk * 16, m1, m2, gk, mnx, cs, g1 + kk * 16,
+                                                            g2 + kk * 16, s_bwd[threadIdx.x >> 5])
+                                      : warp_bwd<8, float>(p1 + kk * 16, p2 + kk * 16, m1, m2, gk, mnx, cs, g1 + kk * 16,
+                                                           g2 + kk * 16, s_bwd[threadIdx.x >> 5]);
+            if (lane == src) err |= e;
         }
     }
     if (err) atomicOr(status, err);
