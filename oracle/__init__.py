@@ -57,6 +57,8 @@ def _load():
             lib.oracle_iou_paired.restype = ctypes.c_int
             lib.oracle_iou_backward_paired.argtypes = [ctypes.c_int64, ctypes.c_int, P, P, P, P, P, P, P, P, P]
             lib.oracle_iou_backward_paired.restype = ctypes.c_int
+            lib.oracle_area_backward_paired.argtypes = [ctypes.c_int64, ctypes.c_int] + [P] * 11
+            lib.oracle_area_backward_paired.restype = ctypes.c_int
             lib.oracle_iou_pairwise.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, P, P, P, P, P, P]
             lib.oracle_iou_pairwise.restype = ctypes.c_int
             lib.oracle_iou_pair_f64.argtypes = [ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int, P, P, P, P]
@@ -203,3 +205,86 @@ def iou_loss(p1, p2, weight=None, scale=1.0, c1=None, c2=None, threads: int = 1)
     loss = float(scale * np.sum(w * (1.0 - f["iou"])))
     g1, g2 = iou_backward_paired(p1, p2, -scale * w, f["nx"], f["xflags"], c1, c2, threads=threads)
     return loss, g1, g2, f
+
+
+def area_backward_paired(p1, p2, gai, ga1, ga2, nx, xflags, c1=None, c2=None, threads: int = 1):
+    """Area adjoint on paired polygons: dL/dA_i, dL/dA_1, dL/dA_2 [n] -> (g1, g2)
+    float64 [n, K, 2] through the recorded (nx, xflags)."""
+    lib = _load()
+    p1, p2, c1, c2 = _f32(p1), _f32(p2), _u8(c1), _u8(c2)
+    gai, ga1, ga2 = (np.ascontiguousarray(g, dtype=np.float64) for g in (gai, ga1, ga2))
+    nx = np.ascontiguousarray(nx, dtype=np.uint8)
+    xflags = np.ascontiguousarray(xflags, dtype=np.uint8)
+    n, K = p1.shape[0], p1.shape[1]
+    g1 = np.zeros((n, K, 2), np.float64)
+    g2 = np.zeros((n, K, 2), np.float64)
+
+    def run(rng):
+        s, e = rng
+        lib.oracle_area_backward_paired(
+            e - s, K, _ptr(p1[s:e]), _ptr(None if c1 is None else c1[s:e]), _ptr(p2[s:e]),
+            _ptr(None if c2 is None else c2[s:e]), _ptr(gai[s:e]), _ptr(ga1[s:e]), _ptr(ga2[s:e]), _ptr(nx[s:e]),
+            _ptr(xflags[s:e]), _ptr(g1[s:e]), _ptr(g2[s:e]))
+
+    _run_parallel(run, _chunks(n, threads))
+    return g1, g2
+
+
+# ----------------------------------------------------------------- 3D IoU
+#
+# 3D IoU of boxes given as a bird's-eye-view polygon and a vertical extent
+# (z_center, height) (the rotated 3D IoU loss of the paper's Sec. IV-A): the
+# intersection volume is A_i * ov with ov the overlap of the two z-intervals,
+# IoU3 = A_i ov / (A_1 h_1 + A_2 h_2 - A_i ov), 0 when that union is not
+# positive.  At equal interval ends the subgradient takes P1's end.
+
+def _z_terms(z1, z2):
+    z1 = np.asarray(z1, dtype=np.float64)
+    z2 = np.asarray(z2, dtype=np.float64)
+    lo1, hi1 = z1[:, 0] - 0.5 * z1[:, 1], z1[:, 0] + 0.5 * z1[:, 1]
+    lo2, hi2 = z2[:, 0] - 0.5 * z2[:, 1], z2[:, 0] + 0.5 * z2[:, 1]
+    top1 = hi1 <= hi2  # P1's top is the overlap's top
+    bot1 = lo1 >= lo2  # P1's bottom is the overlap's bottom
+    ov = np.minimum(hi1, hi2) - np.maximum(lo1, lo2)
+    return z1[:, 1], z2[:, 1], np.maximum(ov, 0.0), ov > 0.0, top1, bot1
+
+
+def iou3d_paired(p1, p2, z1, z2, c1=None, c2=None, threads: int = 1):
+    """3D IoU of paired boxes; returns the 2D forward's dict with iou replaced
+    by the 3D IoU and the vertical overlap added as "ov"."""
+    f = iou_paired(p1, p2, c1, c2, threads=threads)
+    h1, h2, ov, _, _, _ = _z_terms(z1, z2)
+    ai, a1, a2 = f["areas"][:, 0], f["areas"][:, 1], f["areas"][:, 2]
+    inter = np.where(f["nx"] >= 3, ai, 0.0) * ov
+    union = a1 * h1 + a2 * h2 - inter
+    with np.errstate(divide="ignore", invalid="ignore"):
+        f["iou"] = np.where(union > 0.0, inter / union, 0.0)
+    f["ov"] = ov
+    return f
+
+
+def iou3d_backward_paired(p1, p2, z1, z2, grad, nx, xflags, c1=None, c2=None, threads: int = 1):
+    """dL/dIoU3 [n] -> (g1 [n,K,2], gz1 [n,2], g2 [n,K,2], gz2 [n,2]) in float64,
+    gz = dL/d(z_center, height)."""
+    f = iou_paired(p1, p2, c1, c2, threads=threads)
+    g = np.asarray(grad, dtype=np.float64)
+    h1, h2, ov, pos, top1, bot1 = _z_terms(z1, z2)
+    ai = np.where(np.asarray(nx) >= 3, f["areas"][:, 0], 0.0)
+    a1, a2 = f["areas"][:, 1], f["areas"][:, 2]
+    inter = ai * ov
+    v1, v2 = a1 * h1, a2 * h2
+    union = v1 + v2 - inter
+    ok = union > 0.0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        d_inter = np.where(ok, (v1 + v2) / union ** 2, 0.0)  # dIoU3 / d(A_i ov)
+        d_vol = np.where(ok, -inter / union ** 2, 0.0)  # dIoU3 / dV_k
+    gai = g * d_inter * ov
+    ga1 = g * d_vol * h1
+    ga2 = g * d_vol * h2
+    g1, g2 = area_backward_paired(p1, p2, gai, ga1, ga2, nx, xflags, c1, c2, threads=threads)
+    # ov = min(hi1, hi2) - max(lo1, lo2), hi = z + h/2, lo = z - h/2
+    gov = np.where(pos, g * d_inter * ai, 0.0)
+    t1, b1 = top1.astype(np.float64), bot1.astype(np.float64)
+    gz1 = np.stack([gov * (t1 - b1), gov * 0.5 * (t1 + b1) + g * d_vol * a1], axis=1)
+    gz2 = np.stack([gov * ((1 - t1) - (1 - b1)), gov * 0.5 * ((1 - t1) + (1 - b1)) + g * d_vol * a2], axis=1)
+    return g1, gz1, g2, gz2

@@ -254,23 +254,20 @@ static int point_of_code(uint8_t code, const opt* P, int n1, const opt* Q, int n
     return 0;
 }
 
-/* Backward on one pair (paper Sec. II-B `iou_grad`): dL/dIoU -> dL/dP1,
- * dL/dP2 through the recorded (nx, codes).  Gradients are overwritten. */
-static int backward_pair(const opt* P, int n1, const opt* Q, int n2, double g, int nx, const uint8_t* code,
-                         opt* g1, opt* g2)
+/* Area adjoint on one pair (paper Sec. II-B `iou_grad`, the part below the
+ * IoU): given dL/dA_i (gai) and dL/dA_1, dL/dA_2 (ga1, ga2), the gradients of
+ * L with respect to both polygons' vertices through the recorded (nx, codes).
+ * Gradients are overwritten. */
+static int area_backward_pair(const opt* P, int n1, const opt* Q, int n2, double gai, double ga1, double ga2, int nx,
+                              const uint8_t* code, opt* g1, opt* g2)
 {
     for (int i = 0; i < ORC_MAXK; ++i) { g1[i].x = g1[i].y = 0.0; g2[i].x = g2[i].y = 0.0; }
     if (n1 < 3 || n2 < 3) return ORC_ST_BAD_COUNT;
-    if (nx < 3) return 0;
     opt w[ORC_MAXC];
-    for (int k = 0; k < nx; ++k)
-        if (!point_of_code(code[k], P, n1, Q, n2, &w[k])) return ORC_ST_OVERFLOW;
-    double a1 = shoelace(P, n1), a2 = shoelace(Q, n2), ai = shoelace(w, nx);
-    double U = a1 + a2 - ai;
-    if (!(U > 0.0)) return 0;
-    /* IoU = ai / U, U = a1 + a2 - ai. */
-    double gai = g * (a1 + a2) / (U * U);
-    double ga12 = -g * ai / (U * U);
+    if (nx >= 3)
+        for (int k = 0; k < nx; ++k)
+            if (!point_of_code(code[k], P, n1, Q, n2, &w[k])) return ORC_ST_OVERFLOW;
+    if (nx < 3) nx = 0; /* no intersection polygon: only the input areas */
 
     /* Shoelace adjoint: dA/dw_k = 1/2 (y_{k+1} - y_{k-1}, x_{k-1} - x_{k+1}). */
     for (int k = 0; k < nx; ++k) {
@@ -316,15 +313,35 @@ static int backward_pair(const opt* P, int n1, const opt* Q, int n2, double g, i
     /* Areas of the inputs: same shoelace adjoint on P1 and P2. */
     for (int i = 0; i < n1; ++i) {
         opt pp = P[(i + n1 - 1) % n1], pn = P[(i + 1) % n1];
-        g1[i].x += 0.5 * ga12 * (pn.y - pp.y);
-        g1[i].y += 0.5 * ga12 * (pp.x - pn.x);
+        g1[i].x += 0.5 * ga1 * (pn.y - pp.y);
+        g1[i].y += 0.5 * ga1 * (pp.x - pn.x);
     }
     for (int j = 0; j < n2; ++j) {
         opt qp = Q[(j + n2 - 1) % n2], qn = Q[(j + 1) % n2];
-        g2[j].x += 0.5 * ga12 * (qn.y - qp.y);
-        g2[j].y += 0.5 * ga12 * (qp.x - qn.x);
+        g2[j].x += 0.5 * ga2 * (qn.y - qp.y);
+        g2[j].y += 0.5 * ga2 * (qp.x - qn.x);
     }
     return 0;
+}
+
+/* Backward on one pair: dL/dIoU -> dL/dP1, dL/dP2.  IoU = ai / U with
+ * U = a1 + a2 - ai, so dIoU/dai = (a1 + a2) / U^2 and dIoU/da1 = dIoU/da2 =
+ * -ai / U^2; nx < 3 or U <= 0 give zero gradients. */
+static int backward_pair(const opt* P, int n1, const opt* Q, int n2, double g, int nx, const uint8_t* code,
+                         opt* g1, opt* g2)
+{
+    for (int i = 0; i < ORC_MAXK; ++i) { g1[i].x = g1[i].y = 0.0; g2[i].x = g2[i].y = 0.0; }
+    if (n1 < 3 || n2 < 3) return ORC_ST_BAD_COUNT;
+    if (nx < 3) return 0;
+    opt w[ORC_MAXC];
+    for (int k = 0; k < nx; ++k)
+        if (!point_of_code(code[k], P, n1, Q, n2, &w[k])) return ORC_ST_OVERFLOW;
+    double a1 = shoelace(P, n1), a2 = shoelace(Q, n2), ai = shoelace(w, nx);
+    double U = a1 + a2 - ai;
+    if (!(U > 0.0)) return 0;
+    double gai = g * (a1 + a2) / (U * U);
+    double ga12 = -g * ai / (U * U);
+    return area_backward_pair(P, n1, Q, n2, gai, ga12, ga12, nx, code, g1, g2);
 }
 
 static int load_f32(const float* src, int n, opt* dst)
@@ -385,6 +402,36 @@ int oracle_iou_backward_paired(int64_t n, int K, const float* p1, const uint8_t*
             load_f32(p1 + k * 2 * K, n1, P);
             load_f32(p2 + k * 2 * K, n2, Q);
             st |= backward_pair(P, n1, Q, n2, grad[k], nx[k], xflags + k * 2 * K, G1, G2);
+        }
+        for (int v = 0; v < K; ++v) {
+            g1[(k * K + v) * 2] = G1[v].x;
+            g1[(k * K + v) * 2 + 1] = G1[v].y;
+            g2[(k * K + v) * 2] = G2[v].x;
+            g2[(k * K + v) * 2 + 1] = G2[v].y;
+        }
+    }
+    return st;
+}
+
+/* Batch area adjoint: dL/dA_i, dL/dA_1, dL/dA_2 per pair [n] -> grads
+ * [n][K][2] double through the recorded (nx, xflags). */
+int oracle_area_backward_paired(int64_t n, int K, const float* p1, const uint8_t* c1, const float* p2,
+                                const uint8_t* c2, const double* gai, const double* ga1, const double* ga2,
+                                const uint8_t* nx, const uint8_t* xflags, double* g1, double* g2)
+{
+    if (K < 3 || K > ORC_MAXK) return -1;
+    int st = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        opt P[ORC_MAXK], Q[ORC_MAXK], G1[ORC_MAXK], G2[ORC_MAXK];
+        int n1 = count_of(c1, k, K), n2 = count_of(c2, k, K);
+        memset(G1, 0, sizeof(G1));
+        memset(G2, 0, sizeof(G2));
+        if (n1 < 3 || n1 > K || n2 < 3 || n2 > K) {
+            st |= ORC_ST_BAD_COUNT;
+        } else {
+            load_f32(p1 + k * 2 * K, n1, P);
+            load_f32(p2 + k * 2 * K, n2, Q);
+            st |= area_backward_pair(P, n1, Q, n2, gai[k], ga1[k], ga2[k], nx[k], xflags + k * 2 * K, G1, G2);
         }
         for (int v = 0; v < K; ++v) {
             g1[(k * K + v) * 2] = G1[v].x;
