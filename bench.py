@@ -294,6 +294,84 @@ def fused_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def iou3d_workload(args):
+    """1M paired rotated 3D boxes (bird's-eye-view quadrilateral + vertical
+    extent): dgal_iou3d_paired + dgal_iou3d_backward per step (pairs/s,
+    forward + backward), parity of a sample against the FP64 oracle."""
+    import torch
+
+    import oracle
+    import paper_2011_11134_gb300 as dg
+    from paper_2011_11134_gb300 import workloads as W
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    d = W.loss3d_pairs_1m(seed=0, n=args.n)
+    n = d["p1"].shape[0]
+    p1, p2, z1, z2 = (torch.from_numpy(d[k]).to(dev) for k in ("p1", "p2", "z1", "z2"))
+    grad = torch.ones(n, device=dev)
+    flush = torch.empty(256 << 20, device=dev, dtype=torch.uint8)
+    state = {}
+
+    def fwd():
+        state["f"] = dg.dgal_iou3d_paired(p1, z1, p2, z2)
+
+    def bwd():
+        _, nx, xf, _ = state["f"]
+        state["b"] = dg.dgal_iou3d_backward(p1, z1, p2, z2, grad, nx, xf)
+
+    for _ in range(args.warmup):
+        fwd()
+        bwd()
+    torch.cuda.synchronize(dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    for s_ in range(args.steps):
+        flush.fill_(s_ & 0xFF)
+        ev[s_][0].record(stream)
+        fwd()
+        ev[s_][1].record(stream)
+        bwd()
+        ev[s_][2].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    fw = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    bw = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    ms = fw + bw
+    m = min(n, 20_000)
+    iou = state["f"][0][:m].cpu().numpy()
+    g1, gz1, g2, gz2 = (t[:m].cpu().numpy() for t in state["b"])
+    sub = {k: v[:m] for k, v in d.items()}
+    ref = oracle.iou3d_paired(sub["p1"], sub["p2"], sub["z1"], sub["z2"], threads=os.cpu_count() or 1)
+    r1, rz1, r2, rz2 = oracle.iou3d_backward_paired(sub["p1"], sub["p2"], sub["z1"], sub["z2"], np.ones(m), ref["nx"],
+                                                    ref["xflags"], threads=os.cpu_count() or 1)
+    gen = ref["degen"] == 0
+    G = np.concatenate([g1.reshape(m, -1), g2.reshape(m, -1), gz1, gz2], 1)[gen]
+    R = np.concatenate([r1.reshape(m, -1), r2.reshape(m, -1), rz1, rz2], 1)[gen]
+    grad_rel = float((np.abs(G - R).max(1) / np.maximum(np.abs(R).max(1), 1e-6)).max())
+    peaks = _peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    alg_f, alg_b = 64 + 16 + 13, 64 + 16 + 9 + 4 + 64 + 16
+    line = {
+        "metric": "3D IoU pairs/s fwd+bwd", "value": n / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "paired rotated 3D boxes (bird's-eye-view quadrilateral + (z, h)), 3D IoU "
+                               "forward+backward, 1,000,000 pairs, K=4, FP64 refinement on",
+                   "l2": "flushed between steps (256 MiB write outside the timed events)"},
+        "roofline": {"bound": "hbm", "kernel": "k_paired_fwd<4> (3D)", "achieved": alg_f * n / (fw * 1e-3) / 1e9,
+                     "peak": hbm, "unit": "GB/s", "frac": alg_f * n / (fw * 1e-3) / 1e9 / hbm, "traffic": None,
+                     "per_kernel": {"forward": {"ms": fw, "alg_bytes_per_pair": alg_f},
+                                    "backward": {"ms": bw, "alg_bytes_per_pair": alg_b}}},
+        "parity": {"iou_max_abs": float(np.abs(iou - ref["iou"]).max()), "grad_max_rel": grad_rel,
+                   "sample_pairs": m},
+        "gpu_launches": 3 * args.steps, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,7 +382,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=200_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="loss1m",
-                    choices=["loss1m", "rect4096", "convex", "pairwise2000", "ragged64", "fused1m"],
+                    choices=["loss1m", "rect4096", "convex", "pairwise2000", "ragged64", "fused1m", "iou3d1m"],
                     help="loss1m (default) is the headline line; the others measure the remaining workloads")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -316,6 +394,9 @@ def main():
         return
     if args.workload == "fused1m":
         fused_workload(args)
+        return
+    if args.workload == "iou3d1m":
+        iou3d_workload(args)
         return
 
     import torch

@@ -104,6 +104,31 @@ dgal_status dgal_iou_backward(const float* p1, const uint8_t* c1, const float* p
                               float* grad_p1, float* grad_p2, uint32_t flags, void* stream);
 
 /*
+ * 3D IoU of paired boxes, each given as a bird's-eye-view polygon (as above)
+ * and a vertical extent (the rotated 3D IoU loss use of the library, paper
+ * Sec. IV-A):
+ *   z1, z2   float [n][2] = (z_center, height), height > 0; 8-byte aligned.
+ *   IoU3 = A_i ov / (A_1 h_1 + A_2 h_2 - A_i ov), ov = overlap of the two
+ *   extents [z - h/2, z + h/2] (0 when disjoint); 0 when the union is not
+ *   positive.  nx / xflags / degen record the bird's-eye-view intersection
+ *   exactly as dgal_iou_paired does.
+ */
+dgal_status dgal_iou3d_paired(const float* p1, const uint8_t* c1, const float* z1, const float* p2, const uint8_t* c2,
+                              const float* z2, int64_t n, int K, float* iou, uint8_t* nx, uint8_t* xflags,
+                              uint8_t* degen, uint32_t flags, void* stream);
+
+/*
+ * Backward of dgal_iou3d_paired: grad_iou[k] = dL/dIoU3 -> grad_p1, grad_p2
+ * (float [n][K][2]) and grad_z1, grad_z2 (float [n][2], dL/d(z_center,
+ * height)), all overwritten.  At equal extent ends the subgradient of the
+ * overlap takes P1's end.  nx / xflags: as for dgal_iou_backward.
+ */
+dgal_status dgal_iou3d_backward(const float* p1, const uint8_t* c1, const float* z1, const float* p2,
+                                const uint8_t* c2, const float* z2, int64_t n, int K, const float* grad_iou,
+                                const uint8_t* nx, const uint8_t* xflags, float* grad_p1, float* grad_z1,
+                                float* grad_p2, float* grad_z2, uint32_t flags, void* stream);
+
+/*
  * IoU loss with its gradient (the rotated-box IoU-loss use of the library,
  * paper Sec. IV-A):
  *   loss[0] = scale * sum_k w_k (1 - IoU(p1[k], p2[k]))      (w = NULL: all 1)
@@ -122,6 +147,18 @@ size_t dgal_iou_loss_workspace_bytes(int64_t n, int K);
 dgal_status dgal_iou_loss(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n, int K,
                           const float* weight, float scale, float* loss, float* iou, float* grad_p1, float* grad_p2,
                           void* workspace, size_t ws_bytes, uint32_t flags, void* stream);
+
+/*
+ * 3D IoU loss: dgal_iou_loss with the 3D IoU of dgal_iou3d_paired, i.e.
+ * loss[0] = scale * sum_k w_k (1 - IoU3_k), its gradients grad_p1, grad_p2
+ * (float [n][K][2]) and grad_z1, grad_z2 (float [n][2]); the four gradient
+ * pointers are all NULL (loss only) or all set.  Same workspace as
+ * dgal_iou_loss (dgal_iou_loss_workspace_bytes(n, K)).
+ */
+dgal_status dgal_iou3d_loss(const float* p1, const uint8_t* c1, const float* z1, const float* p2, const uint8_t* c2,
+                            const float* z2, int64_t n, int K, const float* weight, float scale, float* loss,
+                            float* iou, float* grad_p1, float* grad_z1, float* grad_p2, float* grad_z2,
+                            void* workspace, size_t ws_bytes, uint32_t flags, void* stream);
 
 /*
  * Pairwise IoU matrix (the `iou` operation over all N x M pairs):

@@ -35,7 +35,8 @@ __all__ = [
     "dgal_iou_loss", "dgal_iou_loss_workspace_bytes", "IoULoss", "iou_loss",
     "dgal_get_batched_config", "dgal_get_device_status", "dgal_last_error", "dgal_version", "IoU", "iou",
     "DGAL_FP64_REFINE", "DGAL_PLAIN", "DGAL_DEV_BAD_COUNT", "DGAL_DEV_OVERFLOW", "DGAL_DEV_BAD_FLAGS",
-    "DGAL_DEV_BAD_OFFSETS", "DgalError",
+    "DGAL_DEV_BAD_OFFSETS", "DgalError", "dgal_iou3d_paired", "dgal_iou3d_backward", "dgal_iou3d_loss", "IoU3D",
+    "iou3d", "IoU3DLoss", "iou3d_loss",
 ]
 
 
@@ -133,6 +134,86 @@ def dgal_iou_loss(p1, p2, weight=None, scale=1.0, c1=None, c2=None, grads=True, 
               float(scale), _lib.ptr(loss), _lib.ptr(iou), _lib.ptr(g1), _lib.ptr(g2), _lib.ptr(workspace),
               workspace.numel(), flags, _lib.stream_ptr(stream))
     return loss, g1, g2, iou
+
+
+def _zext(z, n, name, device):
+    if not isinstance(z, torch.Tensor) or z.dtype != torch.float32 or z.shape != (n, 2) or not z.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 tensor of shape ({n}, 2) = (z_center, height)")
+    if z.device != device:
+        raise ValueError(f"{name} must be on {device}")
+    return z
+
+
+def dgal_iou3d_paired(p1, z1, p2, z2, c1=None, c2=None, save_flags=True, with_degen=False, flags=DGAL_FP64_REFINE,
+                      stream=None):
+    """3D IoU of paired boxes (bird's-eye-view polygon [n, K, 2] + vertical
+    extent [n, 2] = (z_center, height)); returns (iou [n], nx | None,
+    xflags | None, degen | None) with the bird's-eye-view flags."""
+    _poly(p1, "p1")
+    _poly(p2, "p2")
+    if p1.shape != p2.shape or p1.device != p2.device:
+        raise ValueError("p1 and p2 must have the same shape and device")
+    n, K = p1.shape[0], p1.shape[1]
+    z1, z2 = _zext(z1, n, "z1", p1.device), _zext(z2, n, "z2", p1.device)
+    c1 = _counts(c1, n, "c1", p1.device)
+    c2 = _counts(c2, n, "c2", p1.device)
+    iou = torch.empty(n, device=p1.device, dtype=torch.float32)
+    nx = torch.empty(n, device=p1.device, dtype=torch.uint8) if save_flags else None
+    xflags = torch.empty((n, 2 * K), device=p1.device, dtype=torch.uint8) if save_flags else None
+    degen = torch.empty(n, device=p1.device, dtype=torch.uint8) if with_degen else None
+    _lib.call("dgal_iou3d_paired", _lib.ptr(p1), _lib.ptr(c1), _lib.ptr(z1), _lib.ptr(p2), _lib.ptr(c2), _lib.ptr(z2),
+              n, K, _lib.ptr(iou), _lib.ptr(nx), _lib.ptr(xflags), _lib.ptr(degen), flags, _lib.stream_ptr(stream))
+    return iou, nx, xflags, degen
+
+
+def dgal_iou3d_backward(p1, z1, p2, z2, grad_iou, nx=None, xflags=None, c1=None, c2=None, flags=DGAL_FP64_REFINE,
+                        stream=None):
+    """dL/dIoU3 [n] -> (dL/dp1 [n,K,2], dL/dz1 [n,2], dL/dp2, dL/dz2)."""
+    _poly(p1, "p1")
+    _poly(p2, "p2")
+    n, K = p1.shape[0], p1.shape[1]
+    z1, z2 = _zext(z1, n, "z1", p1.device), _zext(z2, n, "z2", p1.device)
+    if grad_iou.dtype != torch.float32 or grad_iou.shape != (n,) or not grad_iou.is_cuda:
+        raise ValueError("grad_iou must be a CUDA float32 tensor of shape (n,)")
+    grad_iou = grad_iou.contiguous()
+    c1 = _counts(c1, n, "c1", p1.device)
+    c2 = _counts(c2, n, "c2", p1.device)
+    if (nx is None) != (xflags is None):
+        raise ValueError("nx and xflags must be given together")
+    g1, g2 = torch.empty_like(p1), torch.empty_like(p2)
+    gz1, gz2 = torch.empty_like(z1), torch.empty_like(z2)
+    _lib.call("dgal_iou3d_backward", _lib.ptr(p1), _lib.ptr(c1), _lib.ptr(z1), _lib.ptr(p2), _lib.ptr(c2),
+              _lib.ptr(z2), n, K, _lib.ptr(grad_iou), _lib.ptr(nx), _lib.ptr(xflags), _lib.ptr(g1), _lib.ptr(gz1),
+              _lib.ptr(g2), _lib.ptr(gz2), flags, _lib.stream_ptr(stream))
+    return g1, gz1, g2, gz2
+
+
+def dgal_iou3d_loss(p1, z1, p2, z2, weight=None, scale=1.0, c1=None, c2=None, grads=True, with_iou=False,
+                    flags=DGAL_FP64_REFINE, stream=None, workspace=None):
+    """3D IoU loss: returns (loss [1], g1, gz1, g2, gz2, iou) (gradients None
+    when grads is False) with loss = scale * sum w (1 - IoU3)."""
+    _poly(p1, "p1")
+    _poly(p2, "p2")
+    if p1.shape != p2.shape:
+        raise ValueError("p1 and p2 must have the same shape")
+    n, K = p1.shape[0], p1.shape[1]
+    z1, z2 = _zext(z1, n, "z1", p1.device), _zext(z2, n, "z2", p1.device)
+    c1 = _counts(c1, n, "c1", p1.device)
+    c2 = _counts(c2, n, "c2", p1.device)
+    if weight is not None and (weight.dtype != torch.float32 or weight.shape != (n,) or not weight.is_contiguous()):
+        raise ValueError("weight must be a contiguous float32 tensor of shape (n,)")
+    if workspace is None:
+        workspace = torch.empty(max(dgal_iou_loss_workspace_bytes(n, K), 16), device=p1.device, dtype=torch.uint8)
+    loss = torch.empty(1, device=p1.device, dtype=torch.float32)
+    g1 = torch.empty_like(p1) if grads else None
+    g2 = torch.empty_like(p2) if grads else None
+    gz1 = torch.empty_like(z1) if grads else None
+    gz2 = torch.empty_like(z2) if grads else None
+    iou = torch.empty(n, device=p1.device, dtype=torch.float32) if with_iou else None
+    _lib.call("dgal_iou3d_loss", _lib.ptr(p1), _lib.ptr(c1), _lib.ptr(z1), _lib.ptr(p2), _lib.ptr(c2), _lib.ptr(z2),
+              n, K, _lib.ptr(weight), float(scale), _lib.ptr(loss), _lib.ptr(iou), _lib.ptr(g1), _lib.ptr(gz1),
+              _lib.ptr(g2), _lib.ptr(gz2), _lib.ptr(workspace), workspace.numel(), flags, _lib.stream_ptr(stream))
+    return loss, g1, gz1, g2, gz2, iou
 
 
 def dgal_iou_pairwise(a, b, ca=None, cb=None, with_nx=True, flags=DGAL_FP64_REFINE, stream=None, out=None):
@@ -330,3 +411,54 @@ def iou_loss(p1, p2, weight=None, reduction="sum", c1=None, c2=None, flags=DGAL_
         raise ValueError("reduction must be 'sum' or 'mean'")
     scale = 1.0 / max(p1.shape[0], 1) if reduction == "mean" else 1.0
     return IoULoss.apply(p1, p2, weight, scale, c1, c2, flags)
+
+
+class IoU3D(torch.autograd.Function):
+    """3D IoU of paired boxes (bird's-eye-view polygon + (z_center, height))
+    with the hand-written backward; the flags of the forward are saved."""
+
+    @staticmethod
+    def forward(ctx, p1, z1, p2, z2, c1=None, c2=None, flags=DGAL_FP64_REFINE):
+        p1c, p2c, z1c, z2c = p1.contiguous(), p2.contiguous(), z1.contiguous(), z2.contiguous()
+        iou_v, nx, xflags, _ = dgal_iou3d_paired(p1c, z1c, p2c, z2c, c1, c2, flags=flags)
+        ctx.save_for_backward(p1c, z1c, p2c, z2c, nx, xflags, c1, c2)
+        ctx.flags = flags
+        return iou_v
+
+    @staticmethod
+    def backward(ctx, grad):
+        p1, z1, p2, z2, nx, xflags, c1, c2 = ctx.saved_tensors
+        g1, gz1, g2, gz2 = dgal_iou3d_backward(p1, z1, p2, z2, grad.contiguous().float(), nx, xflags, c1, c2,
+                                               flags=ctx.flags)
+        return g1, gz1, g2, gz2, None, None, None
+
+
+def iou3d(p1, z1, p2, z2, c1=None, c2=None, flags=DGAL_FP64_REFINE):
+    """Differentiable paired 3D IoU (see ``IoU3D``)."""
+    return IoU3D.apply(p1, z1, p2, z2, c1, c2, flags)
+
+
+class IoU3DLoss(torch.autograd.Function):
+    """loss = scale * sum w (1 - IoU3) through dgal_iou3d_loss; the forward
+    computes the gradients, the backward scales them."""
+
+    @staticmethod
+    def forward(ctx, p1, z1, p2, z2, weight=None, scale=1.0, c1=None, c2=None, flags=DGAL_FP64_REFINE):
+        need = any(t.requires_grad for t in (p1, z1, p2, z2))
+        loss, g1, gz1, g2, gz2, _ = dgal_iou3d_loss(p1.contiguous(), z1.contiguous(), p2.contiguous(),
+                                                    z2.contiguous(), weight, scale, c1, c2, grads=need, flags=flags)
+        ctx.save_for_backward(g1, gz1, g2, gz2)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, grad):
+        gs = ctx.saved_tensors
+        return tuple(None if g is None else g * grad for g in gs) + (None,) * 5
+
+
+def iou3d_loss(p1, z1, p2, z2, weight=None, reduction="sum", c1=None, c2=None, flags=DGAL_FP64_REFINE):
+    """Differentiable 3D IoU loss sum_k w_k (1 - IoU3_k) (or its mean over pairs)."""
+    if reduction not in ("sum", "mean"):
+        raise ValueError("reduction must be 'sum' or 'mean'")
+    scale = 1.0 / max(p1.shape[0], 1) if reduction == "mean" else 1.0
+    return IoU3DLoss.apply(p1, z1, p2, z2, weight, scale, c1, c2, flags)

@@ -37,6 +37,10 @@ _SIG = {
     "dgal_iou_pairwise": (_I, [_P, _P, _I64, _P, _P, _I64, _I, _P, _P, _U32, _P]),
     "dgal_iou_loss_workspace_bytes": (ctypes.c_size_t, [_I64, _I]),
     "dgal_iou_loss": (_I, [_P, _P, _P, _P, _I64, _I, _P, ctypes.c_float, _P, _P, _P, _P, _P, ctypes.c_size_t, _U32, _P]),
+    "dgal_iou3d_paired": (_I, [_P, _P, _P, _P, _P, _P, _I64, _I, _P, _P, _P, _P, _U32, _P]),
+    "dgal_iou3d_backward": (_I, [_P, _P, _P, _P, _P, _P, _I64, _I, _P, _P, _P, _P, _P, _P, _P, _U32, _P]),
+    "dgal_iou3d_loss": (_I, [_P, _P, _P, _P, _P, _P, _I64, _I, _P, ctypes.c_float, _P, _P, _P, _P, _P, _P, _P,
+                             ctypes.c_size_t, _U32, _P]),
     "dgal_batched_workspace_bytes": (ctypes.c_size_t, [_I, _I]),
     "dgal_iou_pairwise_batched": (_I, [_I, _P, _P, _P, _P, _P, _P, _P, _I, _P, _P, _P, ctypes.c_size_t, _U32, _P]),
     "dgal_iou_pairwise_per_scene": (_I, [_I, _P, _P, _P, _P, _P, _P, _P, _I, _P, _P, _U32, _P]),

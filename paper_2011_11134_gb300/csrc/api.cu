@@ -169,6 +169,60 @@ dgal_status dgal_iou_pairwise(const float* a, const uint8_t* ca, int64_t N, cons
     return launch_pairwise(a, ca, N, b, cb, M, K, iou, nx, flags, (cudaStream_t)stream);
 }
 
+namespace {
+dgal_status check_z_ptr(const void* p, const char* name) {
+    if (!p) return fail(DGAL_ERR_INVALID_ARG, "%s is NULL", name);
+    if (!aligned(p, 8)) return fail(DGAL_ERR_ALIGNMENT, "%s is not 8-byte aligned", name);
+    return DGAL_OK;
+}
+} // namespace
+
+dgal_status dgal_iou3d_paired(const float* p1, const uint8_t* c1, const float* z1, const float* p2, const uint8_t* c2,
+                              const float* z2, int64_t n, int K, float* iou, uint8_t* nx, uint8_t* xflags,
+                              uint8_t* degen, uint32_t flags, void* stream) {
+    t_last_error.clear();
+    DGAL_TRY(check_K(K));
+    if (n < 0) return fail(DGAL_ERR_INVALID_ARG, "n = %lld is negative", (long long)n);
+    if (n == 0) return DGAL_OK;
+    DGAL_TRY(check_poly_ptr(p1, "p1"));
+    DGAL_TRY(check_poly_ptr(p2, "p2"));
+    DGAL_TRY(check_z_ptr(z1, "z1"));
+    DGAL_TRY(check_z_ptr(z2, "z2"));
+    if (!iou) return fail(DGAL_ERR_INVALID_ARG, "iou is NULL");
+    if (!aligned(iou, 4)) return fail(DGAL_ERR_ALIGNMENT, "iou is not 4-byte aligned");
+    if ((nx == nullptr) != (xflags == nullptr))
+        return fail(DGAL_ERR_INVALID_ARG, "nx and xflags must be both NULL or both set");
+    if (xflags && !aligned(xflags, K == 4 ? 8 : 16))
+        return fail(DGAL_ERR_ALIGNMENT, "xflags is not %d-byte aligned", K == 4 ? 8 : 16);
+    return launch_paired3d_fwd(p1, c1, z1, p2, c2, z2, n, K, iou, nx, xflags, degen, flags, (cudaStream_t)stream);
+}
+
+dgal_status dgal_iou3d_backward(const float* p1, const uint8_t* c1, const float* z1, const float* p2,
+                                const uint8_t* c2, const float* z2, int64_t n, int K, const float* grad_iou,
+                                const uint8_t* nx, const uint8_t* xflags, float* grad_p1, float* grad_z1,
+                                float* grad_p2, float* grad_z2, uint32_t flags, void* stream) {
+    t_last_error.clear();
+    DGAL_TRY(check_K(K));
+    if (n < 0) return fail(DGAL_ERR_INVALID_ARG, "n = %lld is negative", (long long)n);
+    if (n == 0) return DGAL_OK;
+    DGAL_TRY(check_poly_ptr(p1, "p1"));
+    DGAL_TRY(check_poly_ptr(p2, "p2"));
+    DGAL_TRY(check_z_ptr(z1, "z1"));
+    DGAL_TRY(check_z_ptr(z2, "z2"));
+    DGAL_TRY(check_poly_ptr(grad_p1, "grad_p1"));
+    DGAL_TRY(check_poly_ptr(grad_p2, "grad_p2"));
+    DGAL_TRY(check_z_ptr(grad_z1, "grad_z1"));
+    DGAL_TRY(check_z_ptr(grad_z2, "grad_z2"));
+    if (!grad_iou) return fail(DGAL_ERR_INVALID_ARG, "grad_iou is NULL");
+    if (!aligned(grad_iou, 4)) return fail(DGAL_ERR_ALIGNMENT, "grad_iou is not 4-byte aligned");
+    if ((nx == nullptr) != (xflags == nullptr))
+        return fail(DGAL_ERR_INVALID_ARG, "nx and xflags must be both NULL or both set");
+    if (xflags && !aligned(xflags, K == 4 ? 8 : 16))
+        return fail(DGAL_ERR_ALIGNMENT, "xflags is not %d-byte aligned", K == 4 ? 8 : 16);
+    return launch_paired3d_bwd(p1, c1, z1, p2, c2, z2, n, K, grad_iou, nx, xflags, grad_p1, grad_z1, grad_p2, grad_z2,
+                               flags, (cudaStream_t)stream);
+}
+
 size_t dgal_iou_loss_workspace_bytes(int64_t n, int K) {
     return (n < 0 || (K != 4 && K != 8)) ? 0 : loss_workspace_bytes(n, K);
 }
@@ -201,6 +255,42 @@ dgal_status dgal_iou_loss(const float* p1, const uint8_t* c1, const float* p2, c
         return fail(DGAL_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", ws_bytes, loss_workspace_bytes(n, K));
     return launch_iou_loss(p1, c1, p2, c2, n, K, weight, scale, loss, iou, grad_p1, grad_p2, workspace, flags,
                            (cudaStream_t)stream);
+}
+
+dgal_status dgal_iou3d_loss(const float* p1, const uint8_t* c1, const float* z1, const float* p2, const uint8_t* c2,
+                            const float* z2, int64_t n, int K, const float* weight, float scale, float* loss,
+                            float* iou, float* grad_p1, float* grad_z1, float* grad_p2, float* grad_z2,
+                            void* workspace, size_t ws_bytes, uint32_t flags, void* stream) {
+    t_last_error.clear();
+    if (K != 4 && K != 8) return fail(DGAL_ERR_UNSUPPORTED_K, "K must be 4 or 8 (got %d)", K);
+    if (n < 0) return fail(DGAL_ERR_INVALID_ARG, "n = %lld is negative", (long long)n);
+    if (!loss) return fail(DGAL_ERR_INVALID_ARG, "loss is NULL");
+    if (!aligned(loss, 4)) return fail(DGAL_ERR_ALIGNMENT, "loss is not 4-byte aligned");
+    if (n == 0) {
+        cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), (cudaStream_t)stream);
+        return e == cudaSuccess ? DGAL_OK : fail(DGAL_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    }
+    DGAL_TRY(check_poly_ptr(p1, "p1"));
+    DGAL_TRY(check_poly_ptr(p2, "p2"));
+    DGAL_TRY(check_z_ptr(z1, "z1"));
+    DGAL_TRY(check_z_ptr(z2, "z2"));
+    const bool any_g = grad_p1 || grad_p2 || grad_z1 || grad_z2;
+    if (any_g && !(grad_p1 && grad_p2 && grad_z1 && grad_z2))
+        return fail(DGAL_ERR_INVALID_ARG, "grad_p1, grad_z1, grad_p2, grad_z2 must be all NULL or all set");
+    if (any_g) {
+        DGAL_TRY(check_poly_ptr(grad_p1, "grad_p1"));
+        DGAL_TRY(check_poly_ptr(grad_p2, "grad_p2"));
+        DGAL_TRY(check_z_ptr(grad_z1, "grad_z1"));
+        DGAL_TRY(check_z_ptr(grad_z2, "grad_z2"));
+    }
+    if (weight && !aligned(weight, 4)) return fail(DGAL_ERR_ALIGNMENT, "weight is not 4-byte aligned");
+    if (iou && !aligned(iou, 4)) return fail(DGAL_ERR_ALIGNMENT, "iou is not 4-byte aligned");
+    if (!workspace) return fail(DGAL_ERR_WORKSPACE, "workspace is NULL");
+    if (!aligned(workspace, 16)) return fail(DGAL_ERR_ALIGNMENT, "workspace is not 16-byte aligned");
+    if (ws_bytes < loss_workspace_bytes(n, K))
+        return fail(DGAL_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", ws_bytes, loss_workspace_bytes(n, K));
+    return launch_iou3d_loss(p1, c1, z1, p2, c2, z2, n, K, weight, scale, loss, iou, grad_p1, grad_z1, grad_p2, grad_z2,
+                             workspace, flags, (cudaStream_t)stream);
 }
 
 size_t dgal_batched_workspace_bytes(int S, int K) {

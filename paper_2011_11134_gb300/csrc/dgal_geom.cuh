@@ -776,6 +776,94 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
     o.iou = (U > 0.f) ? ai / U : 0.f;
 }
 
+// ------------------------------------------------------ metrics of the areas
+//
+// The backward paths take the derivative of the loss with respect to the
+// three areas (A_i, A_1, A_2) from a policy object, so the same clip
+// adjoint serves the 2D IoU and the 3D IoU.
+
+// L = g IoU, IoU = A_i / (A_1 + A_2 - A_i) (paper Sec. II-B `iou`).
+struct AdjIou {
+    float g;
+    template <typename R>
+    __device__ __forceinline__ bool operator()(R ai, R a1, R a2, R& gai, R& ga1, R& ga2) {
+        const R U = a1 + a2 - ai;
+        if (!(U > (R)0)) return false;
+        const R rU = (R)1 / U;
+        gai = (R)g * (a1 + a2) * rU * rU;
+        ga1 = ga2 = -(R)g * ai * rU * rU;
+        return true;
+    }
+};
+
+// Vertical extents of a pair of 3D boxes, (z_center, height) each: the
+// overlap ov = min(hi1, hi2) - max(lo1, lo2) clamped at 0, and which box's
+// ends bound it (P1's at ties).
+struct ZPair {
+    float h1, h2, ov;
+    bool pos, top1, bot1;
+};
+
+__device__ __forceinline__ ZPair z_pair(float2 z1, float2 z2) {
+    ZPair z;
+    const float lo1 = z1.x - 0.5f * z1.y, hi1 = z1.x + 0.5f * z1.y;
+    const float lo2 = z2.x - 0.5f * z2.y, hi2 = z2.x + 0.5f * z2.y;
+    const float ov = fminf(hi1, hi2) - fmaxf(lo1, lo2);
+    z.h1 = z1.y;
+    z.h2 = z2.y;
+    z.pos = ov > 0.f;
+    z.ov = z.pos ? ov : 0.f;
+    z.top1 = hi1 <= hi2;
+    z.bot1 = lo1 >= lo2;
+    return z;
+}
+
+// 3D IoU of boxes given as a bird's-eye-view polygon and a vertical extent
+// (the rotated 3D IoU of the paper's Sec. IV-A): IoU3 = I / U3 with
+// I = A_i ov, U3 = A_1 h_1 + A_2 h_2 - I; 0 when U3 <= 0.
+__device__ __forceinline__ float iou3_value(float ai, float a1, float a2, uint32_t nx, const ZPair& z) {
+    const float I = (nx >= 3u ? ai : 0.f) * z.ov;
+    const float U = a1 * z.h1 + a2 * z.h2 - I;
+    return U > 0.f ? I / U : 0.f;
+}
+
+// L = g IoU3; records the areas it was given, for dL/d(z, h).
+struct AdjIou3 {
+    float g;
+    ZPair z;
+    float ai, a1, a2;
+    bool hit;
+    template <typename R>
+    __device__ __forceinline__ bool operator()(R ai_, R a1_, R a2_, R& gai, R& ga1, R& ga2) {
+        const R I = ai_ * (R)z.ov, V1 = a1_ * (R)z.h1, V2 = a2_ * (R)z.h2, U = V1 + V2 - I;
+        hit = U > (R)0;
+        ai = (float)ai_;
+        a1 = (float)a1_;
+        a2 = (float)a2_;
+        if (!hit) return false;
+        const R rU = (R)1 / U;
+        const R dI = (V1 + V2) * rU * rU, dV = -I * rU * rU; // dIoU3/dI, dIoU3/dV_k
+        gai = (R)g * dI * (R)z.ov;
+        ga1 = (R)g * dV * (R)z.h1;
+        ga2 = (R)g * dV * (R)z.h2;
+        return true;
+    }
+    // dL/d(z_center, height) of both boxes (zero unless the areas were taken
+    // with a positive union): through ov = min(hi1, hi2) - max(lo1, lo2),
+    // hi = z + h/2, lo = z - h/2, and V_k = A_k h_k.
+    __device__ __forceinline__ void z_grads(float2& gz1, float2& gz2) const {
+        gz1 = gz2 = make_float2(0.f, 0.f);
+        if (!hit) return;
+        const float I = ai * z.ov, V1 = a1 * z.h1, V2 = a2 * z.h2, U = V1 + V2 - I;
+        const float rU = 1.f / U;
+        const float dI = (V1 + V2) * rU * rU, dV = -I * rU * rU;
+        const float gov = z.pos ? g * dI * ai : 0.f;
+        const float t1 = z.top1 ? 1.f : 0.f, b1 = z.bot1 ? 1.f : 0.f;
+        gz1 = make_float2(gov * (t1 - b1), gov * 0.5f * (t1 + b1) + g * dV * a1);
+        gz2 = make_float2(gov * ((1.f - t1) - (1.f - b1)), gov * 0.5f * ((1.f - t1) + (1.f - b1)) + g * dV * a2);
+    }
+};
+
 // ---------------------------------------------------------------- backward
 //
 // Main path (bwd_shape): the shape derivative of the area over the clipped
@@ -794,11 +882,12 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
 // through the adjoint of w onto the four endpoints of the crossing's edges,
 // by FP32 atomics into the warp's scratch sh[4K] (P1 x, P1 y, P2 x, P2 y);
 // lanes s K + v then add the input-area terms and write the gradients.
-// codes / nx / grad / counts are the pair's (uniform over the warp).  Returns
-// device status bits (the same in every lane).
-template <int K, typename R>
+// codes / nx / adj / counts are the pair's (uniform over the warp); adj maps
+// the areas to their adjoints.  Returns device status bits (the same in every
+// lane).
+template <int K, typename R, typename Adj>
 __device__ __noinline__ uint32_t warp_bwd(const float* __restrict__ p1, const float* __restrict__ p2, int n1, int n2,
-                                          float grad, uint32_t nx, Codes<K> codes, float* __restrict__ g1,
+                                          Adj& adj, uint32_t nx, Codes<K> codes, float* __restrict__ g1,
                                           float* __restrict__ g2, float* __restrict__ sh) {
     constexpr unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -879,10 +968,10 @@ __device__ __noinline__ uint32_t warp_bwd(const float* __restrict__ p1, const fl
     twoA = __shfl_sync(full, twoA, 0);
     s1 = __shfl_sync(full, s1, 0);
     s2 = __shfl_sync(full, s2, 0);
-    const R a1 = (R)0.5 * s1, a2 = (R)0.5 * s2, ai = (R)0.5 * twoA, U = a1 + a2 - ai;
-    const bool ok = err == 0u && nx >= 3u && U > (R)0;
-    const R gai = ok ? (R)grad * (a1 + a2) / (U * U) : (R)0;
-    const R ga12 = ok ? -(R)grad * ai / (U * U) : (R)0;
+    const R a1 = (R)0.5 * s1, a2 = (R)0.5 * s2, ai = (R)0.5 * twoA;
+    R gai = 0, ga1 = 0, ga2 = 0;
+    const bool ok = err == 0u && nx >= 3u && adj(ai, a1, a2, gai, ga1, ga2);
+    const R gas = side ? ga2 : ga1;
     if (ok && live) {
         const R gwx = (R)0.5 * gai * (wyn - wyp), gwy = (R)0.5 * gai * (wxp - wxn);
         if (kind == 0u) {
@@ -912,8 +1001,8 @@ __device__ __noinline__ uint32_t warp_bwd(const float* __restrict__ p1, const fl
     if (lane < 2 * K) {
         float gx = 0.f, gy = 0.f;
         if (ok && onv) {
-            gx = sh[2 * side * K + v] + (float)((R)0.5 * ga12 * (yn - yp));
-            gy = sh[(2 * side + 1) * K + v] + (float)((R)0.5 * ga12 * (xp - xn));
+            gx = sh[2 * side * K + v] + (float)((R)0.5 * gas * (yn - yp));
+            gy = sh[(2 * side + 1) * K + v] + (float)((R)0.5 * gas * (xp - xn));
         }
         float* g = side ? g2 : g1;
         reinterpret_cast<float2*>(g)[v] = make_float2(gx, gy);
@@ -939,8 +1028,8 @@ __device__ __noinline__ uint32_t warp_bwd(const float* __restrict__ p1, const fl
 constexpr uint32_t kSlow = 0x80000000u;
 constexpr float kTinyArea = 1e-5f;
 
-template <int K, bool COUNTS>
-__device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, float grad, uint32_t nx, const Codes<K>& codes,
+template <int K, bool COUNTS, typename Adj>
+__device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, Adj& adj, uint32_t nx, const Codes<K>& codes,
                                               bool refine, float (&g1x)[K], float (&g1y)[K], float (&g2x)[K],
                                               float (&g2y)[K]) {
     typedef typename MaskOf<K>::T M;
@@ -1040,11 +1129,9 @@ __device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, float grad, uint3
     }
     const float a1 = 0.5f * s1, a2 = 0.5f * s2, ai = 0.5f * twoA;
     if (refine && ai < kTinyArea * L * L) return kSlow;
-    const float U = a1 + a2 - ai;
-    if (!(U > 0.f)) return 0u;
-    const float rU = 1.0f / U;
-    const float gai = grad * (a1 + a2) * rU * rU; // dIoU/dA_i
-    const float h12 = 0.5f * (-grad * ai * rU * rU); // (1/2) dIoU/dA_1 = (1/2) dIoU/dA_2
+    float gai, ga1, ga2;
+    if (!adj(ai, a1, a2, gai, ga1, ga2)) return 0u;
+    const float h1 = 0.5f * ga1, h2 = 0.5f * ga2;
     // start / end contributions of every edge, then vertex v = start of edge v
     // plus end of edge v-1
     float sx1[K], sy1[K], ex1[K], ey1[K], sx2[K], sy2[K], ex2[K], ey2[K];
@@ -1055,8 +1142,8 @@ __device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, float grad, uint3
         const float I1a = pa ? 0.5f * (t1[v] * t1[v] - t0[v] * t0[v]) : 0.f;
         const float I0b = pb ? 0.5f * ((1.f - u0[v]) * (1.f - u0[v]) - (1.f - u1[v]) * (1.f - u1[v])) : 0.f;
         const float I1b = pb ? 0.5f * (u1[v] * u1[v] - u0[v] * u0[v]) : 0.f;
-        const float wsa = gai * I0a + h12, wea = gai * I1a + h12;
-        const float wsb = gai * I0b + h12, web = gai * I1b + h12;
+        const float wsa = gai * I0a + h1, wea = gai * I1a + h1;
+        const float wsb = gai * I0b + h2, web = gai * I1b + h2;
         sx1[v] = wsa * g.eay[v];
         sy1[v] = -wsa * g.eax[v];
         ex1[v] = wea * g.eay[v];

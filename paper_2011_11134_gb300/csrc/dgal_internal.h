@@ -43,6 +43,21 @@ size_t loss_workspace_bytes(int64_t n, int K);
 dgal_status launch_iou_loss(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n, int K,
                             const float* weight, float scale, float* loss, float* iou, float* g1, float* g2,
                             void* ws, uint32_t flags, cudaStream_t s);
+// 3D IoU (z1 / z2: float [n][2] = (z_center, height)) and its backward,
+// paired3d.cu.
+dgal_status launch_paired3d_fwd(const float* p1, const uint8_t* c1, const float* z1, const float* p2,
+                                const uint8_t* c2, const float* z2, int64_t n, int K, float* iou, uint8_t* nx,
+                                uint8_t* xflags, uint8_t* degen, uint32_t flags, cudaStream_t s);
+dgal_status launch_paired3d_bwd(const float* p1, const uint8_t* c1, const float* z1, const float* p2,
+                                const uint8_t* c2, const float* z2, int64_t n, int K, const float* grad,
+                                const uint8_t* nx, const uint8_t* xflags, float* g1, float* gz1, float* g2, float* gz2,
+                                uint32_t flags, cudaStream_t s);
+dgal_status launch_iou3d_loss(const float* p1, const uint8_t* c1, const float* z1, const float* p2, const uint8_t* c2,
+                              const float* z2, int64_t n, int K, const float* weight, float scale, float* loss,
+                              float* iou, float* g1, float* gz1, float* g2, float* gz2, void* ws, uint32_t flags,
+                              cudaStream_t s);
+// One-block fixed-order sum of m per-warp loss partials into *out.
+void launch_sum_partials(const float* partials, int64_t m, float* out, cudaStream_t s);
 dgal_status launch_batched(int S, const int64_t* a_off, const int64_t* b_off, const int64_t* out_off,
                            const float* a, const uint8_t* ca, const float* b, const uint8_t* cb, int K, float* iou,
                            uint8_t* nx, void* ws, uint32_t flags, const BatchedConfig& cfg, cudaStream_t s);

@@ -128,6 +128,7 @@ struct FwdG {
     float iou;
     uint32_t nx;
     uint32_t degen; // near-degenerate (some orientation within kDegenRel L^2)
+    float ai, a1, a2;
 };
 
 // Group forward.  Returns false (in every lane of the group) when the pair
@@ -184,6 +185,7 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
     const uint32_t cnt = (uint32_t)(__popc(in1) + __popc(in2) + __popcll(X));
     out.nx = 0;
     out.iou = 0.f;
+    out.ai = out.a1 = out.a2 = 0.f;
     out.w0 = out.w1 = ~0ull;
     if (cnt == 0u) return true;
     if (cnt < 3u || cnt > 16u) return false;
@@ -313,13 +315,17 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
     out.w1 = hi | ((cnt <= 8) ? ~0ull : ((cnt < 16) ? (~0ull << (8 * (cnt - 8))) : 0ull));
     out.nx = cnt;
     out.iou = (U > 0.f) ? ai / U : 0.f;
+    out.ai = ai;
+    out.a1 = a1;
+    out.a2 = a2;
     return true;
 }
 
 // Group backward (shape derivative).  Returns 0, kDevBadFlags, or kSlow
 // (group-uniform) when the pair must take the shoelace adjoint.  On success
 // lane r holds the gradients of P1 vertex r and P2 vertex r (0 beyond counts).
-__device__ __forceinline__ uint32_t bwd_group(const Lane& L, float grad, uint32_t nx, uint64_t w0, uint64_t w1,
+template <typename Adj>
+__device__ __forceinline__ uint32_t bwd_group(const Lane& L, Adj& adj, uint32_t nx, uint64_t w0, uint64_t w1,
                                               bool refine, float& g1x, float& g1y, float& g2x, float& g2y) {
     const unsigned gm = gmask();
     const int base = gbase();
@@ -414,16 +420,15 @@ __device__ __forceinline__ uint32_t bwd_group(const Lane& L, float grad, uint32_
     for (int j = 0; j < 8; ++j) Lr = fmaxf(Lr, (j < n2) ? fmaxf(fabsf(L.bx[j]), fabsf(L.by[j])) : 0.f);
     Lr = gmax(gm, Lr);
     if (refine && ai < kTinyArea * Lr * Lr) return kSlow;
-    const float U = a1 + a2 - ai;
-    if (!(U > 0.f)) return 0u;
-    const float rU = 1.0f / U;
-    const float gai = grad * (a1 + a2) * rU * rU, h12 = 0.5f * (-grad * ai * rU * rU);
+    float gai, ga1, ga2;
+    if (!adj(ai, a1, a2, gai, ga1, ga2)) return 0u;
+    const float h1 = 0.5f * ga1, h2 = 0.5f * ga2;
     const float I0a = hasA ? 0.5f * ((1.f - t0) * (1.f - t0) - (1.f - t1) * (1.f - t1)) : 0.f;
     const float I1a = hasA ? 0.5f * (t1 * t1 - t0 * t0) : 0.f;
     const float I0b = hasB ? 0.5f * ((1.f - u0) * (1.f - u0) - (1.f - u1) * (1.f - u1)) : 0.f;
     const float I1b = hasB ? 0.5f * (u1 * u1 - u0 * u0) : 0.f;
-    const float wsa = liveA ? gai * I0a + h12 : 0.f, wea = liveA ? gai * I1a + h12 : 0.f;
-    const float wsb = liveB ? gai * I0b + h12 : 0.f, web = liveB ? gai * I1b + h12 : 0.f;
+    const float wsa = liveA ? gai * I0a + h1 : 0.f, wea = liveA ? gai * I1a + h1 : 0.f;
+    const float wsb = liveB ? gai * I0b + h2 : 0.f, web = liveB ? gai * I1b + h2 : 0.f;
     const float ex1 = wea * L.eay, ey1 = -wea * L.eax, ex2 = web * ebyr, ey2 = -web * ebxr;
     // vertex r receives the end contribution of edge r - 1 (wrapping at the count)
     const int pa = base + ((r == 0) ? n1 - 1 : r - 1), pb = base + ((r == 0) ? n2 - 1 : r - 1);

@@ -1,0 +1,658 @@
+// Paired IoU kernels and their launch templates (included by paired.cu for
+// the 2D IoU and by paired3d.cu for the 3D IoU, so each translation unit
+// instantiates its own half).
+//
+// Forward (paper Sec. II-B `iou`): loads both polygons with 128-bit loads,
+// clips in registers (dgal_geom.cuh), stores IoU (4 B), nx (1 B) and the
+// 2K code bytes as one 64/128-bit store, plus an optional degeneracy byte.
+// Backward (paper Sec. II-B `iou_backward`): reads the polygons, dL/dIoU and
+// the recorded (nx, xflags), or recomputes the clip, and writes both
+// gradients with 128-bit stores.
+#pragma once
+
+#include "dgal_geom.cuh"
+#include "dgal_internal.h"
+#include "group8.cuh"
+
+namespace dgal {
+
+constexpr int kPairThreads = 128;
+
+template <int K> __device__ __forceinline__ void store_codes(uint8_t* __restrict__ xf, int64_t k, const Codes<K>& c) {
+    if constexpr (K == 4) {
+        reinterpret_cast<uint64_t*>(xf)[k] = c.w[0];
+    } else {
+        reinterpret_cast<uint4*>(xf)[k] =
+            make_uint4((uint32_t)c.w[0], (uint32_t)(c.w[0] >> 32), (uint32_t)c.w[1], (uint32_t)(c.w[1] >> 32));
+    }
+}
+
+template <int K> __device__ __forceinline__ void load_codes(const uint8_t* __restrict__ xf, int64_t k, Codes<K>& c) {
+    if constexpr (K == 4) {
+        c.w[0] = __ldg(reinterpret_cast<const unsigned long long*>(xf) + k);
+    } else {
+        uint4 u = __ldg(reinterpret_cast<const uint4*>(xf) + k);
+        c.w[0] = (uint64_t)u.x | ((uint64_t)u.y << 32);
+        c.w[1] = (uint64_t)u.z | ((uint64_t)u.w << 32);
+    }
+}
+
+template <int K> __device__ __forceinline__ void store_poly(float* __restrict__ p, const float (&x)[K], const float (&y)[K]) {
+    float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int v = 0; v < K / 2; ++v) q[v] = make_float4(x[2 * v], y[2 * v], x[2 * v + 1], y[2 * v + 1]);
+}
+
+// Both kernels walk the pairs warp by warp (32 consecutive pairs per warp and
+// step, grid-stride over warps), with no block-wide barrier.  In the forward,
+// a pair the fast path cannot finish (near-degenerate or not in general
+// position) is only marked; a second kernel (k_paired_fix) scans the marks
+// and finishes each marked pair with the whole warp (warp_robust).  Keeping
+// the robust path out of the main kernel keeps its registers and its FP64
+// latency out of the common case.  In the backward, a pair whose codes the
+// shape derivative cannot take (not in general position, or with refinement
+// a tiny intersection) takes the shoelace adjoint after the rest, with the
+// whole warp on it (warp_bwd).
+
+// Mark of a pair left to k_paired_fix: an IoU of this signalling-NaN bit
+// pattern (arithmetic never produces it: NaN results are the canonical NaN)
+// or, in loss mode, nx = kHardNx.
+constexpr uint32_t kHardIou = 0x7fbadbadu;
+constexpr uint8_t kHardNx = 0xFFu;
+
+// IoU-loss mode of the paired kernels (paper Sec. IV-A, the IoU loss over
+// rotated boxes): the forward adds scale * w_k (1 - IoU_k) into one partial
+// per warp, and the backward takes dL/dIoU_k = -scale * w_k (w = 1 when
+// weight is NULL) instead of reading an upstream gradient.
+struct LossArgs {
+    const float* weight;
+    float scale;
+    float* partials; // one float per warp of the forward grid
+};
+
+// 3D mode of the paired kernels: each box also has a vertical extent
+// (z_center, height) in z1 / z2 (float [n][2]); the forward gives the 3D IoU
+// and the backward also writes dL/d(z_center, height) into gz1 / gz2.
+struct ZArgs {
+    const float* z1;
+    const float* z2;
+    float* gz1;
+    float* gz2;
+};
+
+__device__ __forceinline__ ZPair z_of(const ZArgs& za, int64_t k) {
+    return z_pair(__ldg(reinterpret_cast<const float2*>(za.z1) + k), __ldg(reinterpret_cast<const float2*>(za.z2) + k));
+}
+
+template <bool Z3> struct AdjOf { typedef AdjIou T; };
+template <> struct AdjOf<true> { typedef AdjIou3 T; };
+
+// The adjoint policy of pair k for dL/dIoU = g.
+template <bool Z3> __device__ __forceinline__ typename AdjOf<Z3>::T adj_of(float g, const ZArgs& za, int64_t k) {
+    typename AdjOf<Z3>::T a;
+    a.g = g;
+    if constexpr (Z3) {
+        a.z = z_of(za, k);
+        a.hit = false;
+        a.ai = a.a1 = a.a2 = 0.f;
+    }
+    return a;
+}
+
+// Writes dL/d(z_center, height) of pair k (3D mode only).
+template <bool Z3> __device__ __forceinline__ void put_zgrad(const ZArgs& za, int64_t k, const typename AdjOf<Z3>::T& a) {
+    if constexpr (Z3) {
+        float2 u, v;
+        a.z_grads(u, v);
+        reinterpret_cast<float2*>(za.gz1)[k] = u;
+        reinterpret_cast<float2*>(za.gz2)[k] = v;
+    }
+}
+
+__device__ __forceinline__ float loss_weight(const LossArgs& la, int64_t k) {
+    return la.weight ? __ldg(la.weight + k) : 1.f;
+}
+
+__device__ __forceinline__ void put_partial(const LossArgs& la, float acc) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) la.partials[((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5] = acc;
+}
+
+template <int K, bool COUNTS, bool SAVE, bool LOSS, bool Z3>
+__global__ void __launch_bounds__(kPairThreads)
+k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
+             const uint8_t* __restrict__ c2, int64_t n, float* __restrict__ iou, uint8_t* __restrict__ nx,
+             uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status,
+             LossArgs la, ZArgs za) {
+    (void)flags;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * kPairThreads;
+    uint32_t err = 0;
+    float acc = 0.f;
+    for (int64_t base = (int64_t)blockIdx.x * kPairThreads + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t k = base + lane;
+        int n1 = K, n2 = K;
+        bool hard = false;
+        float w = 0.f;
+        if (k < n) {
+            if (LOSS) w = loss_weight(la, k);
+            if (COUNTS) {
+                n1 = c1 ? (int)c1[k] : K;
+                n2 = c2 ? (int)c2[k] : K;
+            }
+            FwdOut<K> o;
+            if (COUNTS && (n1 < 3 || n1 > K || n2 < 3 || n2 > K)) {
+                err |= kDevBadCount;
+                o.nx = 0;
+                o.iou = 0.f;
+                o.degen = 0;
+                codes_fill<K>(o.codes, ~0ull);
+            } else {
+                float px[K], py[K], qx[K], qy[K];
+                load_poly<K>(p1 + k * 2 * K, px, py);
+                load_poly<K>(p2 + k * 2 * K, qx, qy);
+                Geo<K> g;
+                make_geo<K, COUNTS>(px, py, qx, qy, n1, n2, g);
+                input_areas<K, COUNTS>(g, o.a1, o.a2);
+                o.degen = 0;
+                hard = !fwd_generic<K, COUNTS>(g, o);
+                if (!hard) {
+                    if constexpr (Z3) {
+                        o.iou = iou3_value(o.ai, o.a1, o.a2, o.nx, z_of(za, k));
+                    } else {
+                        const float U = o.a1 + o.a2 - o.ai;
+                        o.iou = (o.nx >= 3u && U > 0.f) ? o.ai / U : 0.f;
+                    }
+                }
+            }
+            if (!hard) {
+                if (LOSS) acc += la.scale * w * (1.f - o.iou);
+                if (!LOSS || iou) iou[k] = o.iou;
+                if (SAVE) {
+                    nx[k] = (uint8_t)o.nx;
+                    store_codes<K>(xflags, k, o.codes);
+                }
+                if (degen) degen[k] = (uint8_t)o.degen;
+            }
+        }
+        if (hard) {
+            if (LOSS) nx[k] = kHardNx;
+            else reinterpret_cast<uint32_t*>(iou)[k] = kHardIou;
+        }
+    }
+    if (LOSS) put_partial(la, acc);
+    if (err) atomicOr(status, err);
+}
+
+// Second forward pass: finishes the pairs the main kernel marked, each with
+// the whole warp (warp_robust), and writes all of their outputs.  Each block
+// owns a contiguous range of segments of kFixSeg pairs (normally one): the
+// block reads the segment's marks (4 B per pair, or 1 B in loss mode,
+// coalesced), queues the marked pairs in shared memory, and its warps then
+// take the queue in turn, so the robust calls of a segment run at once.
+constexpr int kFixThreads = 256;
+constexpr int kFixSeg = 1024;
+
+// One segment per block while that fits the grid: short-lived blocks let each
+// SM overlap many robust calls (a block that meets none exits after its scan).
+static unsigned fix_grid(int64_t n) {
+    const int64_t segs = (n + kFixSeg - 1) / kFixSeg;
+    const int64_t cap = (int64_t)1 << 30;
+    return (unsigned)(segs < 1 ? 1 : (segs < cap ? segs : cap));
+}
+
+template <int K, bool LOSS, bool Z3>
+__global__ void __launch_bounds__(kFixThreads)
+k_paired_fix(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
+             const uint8_t* __restrict__ c2, int64_t n, float* __restrict__ iou, uint8_t* __restrict__ nx,
+             uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status,
+             LossArgs la, ZArgs za) {
+    constexpr unsigned full = 0xffffffffu;
+    constexpr int kWarps = kFixThreads / 32;
+    __shared__ int q[kFixSeg];
+    __shared__ int qn;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
+    const int64_t segs = (n + kFixSeg - 1) / kFixSeg;
+    const int64_t per = (segs + gridDim.x - 1) / gridDim.x;
+    const int64_t s0 = (int64_t)blockIdx.x * per, s1 = (s0 + per < segs) ? s0 + per : segs;
+    uint32_t err = 0;
+    float acc = 0.f;
+    if (threadIdx.x == 0) qn = 0;
+    __syncthreads();
+    for (int64_t sg = s0; sg < s1; ++sg) {
+        const int64_t base = sg * kFixSeg;
+#pragma unroll
+        for (int r = 0; r < kFixSeg / kFixThreads; ++r) {
+            const int off = r * kFixThreads + (int)threadIdx.x;
+            const int64_t k = base + off;
+            bool hard = false;
+            if (k < n) hard = LOSS ? (nx[k] == kHardNx) : (__ldg(reinterpret_cast<const uint32_t*>(iou) + k) == kHardIou);
+            const unsigned b = __ballot_sync(full, hard);
+            int pos = 0;
+            if (lane == 0 && b) pos = atomicAdd(&qn, __popc(b));
+            pos = __shfl_sync(full, pos, 0);
+            if (hard) q[pos + __popc(b & ((1u << lane) - 1u))] = off;
+        }
+        __syncthreads();
+        const int m = qn;
+        for (int e = warp; e < m; e += kWarps) {
+            const int64_t kk = base + q[e];
+            const int m1 = c1 ? (int)c1[kk] : K, m2 = c2 ? (int)c2[kk] : K;
+            FwdOut<K> o;
+            o.err = 0;
+            warp_robust<K>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, refine, o);
+            if constexpr (Z3) o.iou = iou3_value(o.ai, o.a1, o.a2, o.nx, z_of(za, kk));
+            if (lane == 0) {
+                err |= o.err;
+                if (LOSS) acc += la.scale * loss_weight(la, kk) * (1.f - o.iou);
+                if (!LOSS || iou) iou[kk] = o.iou;
+                if (nx) {
+                    nx[kk] = (uint8_t)o.nx;
+                    store_codes<K>(xflags, kk, o.codes);
+                }
+                if (degen) degen[kk] = (uint8_t)o.degen;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) qn = 0;
+        __syncthreads();
+    }
+    if (LOSS) put_partial(la, acc);
+    if (err) atomicOr(status, err);
+}
+
+template <int K, bool COUNTS, bool RECOMPUTE, bool LOSS, bool Z3>
+__global__ void __launch_bounds__(kPairThreads)
+k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
+             const uint8_t* __restrict__ c2, int64_t n, const float* __restrict__ grad,
+             const uint8_t* __restrict__ nxs, const uint8_t* __restrict__ xflags, float* __restrict__ g1,
+             float* __restrict__ g2, uint32_t flags, uint32_t* status, LossArgs la, ZArgs za) {
+    constexpr unsigned full = 0xffffffffu;
+    __shared__ float s_bwd[kPairThreads / 32][4 * K];
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * kPairThreads;
+    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
+    uint32_t err = 0;
+    for (int64_t base = (int64_t)blockIdx.x * kPairThreads + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t k = base + lane;
+        int n1 = K, n2 = K;
+        bool slow = false, needfwd = false;
+        Codes<K> codes;
+        uint32_t nxk = 0;
+        if (k < n) {
+            if (COUNTS) {
+                n1 = c1 ? (int)c1[k] : K;
+                n2 = c2 ? (int)c2[k] : K;
+            }
+            float g1x[K], g1y[K], g2x[K], g2y[K];
+            auto adj = adj_of<Z3>(LOSS ? -la.scale * loss_weight(la, k) : __ldg(grad + k), za, k);
+            if (COUNTS && (n1 < 3 || n1 > K || n2 < 3 || n2 > K)) {
+                err |= kDevBadCount;
+#pragma unroll
+                for (int v = 0; v < K; ++v) { g1x[v] = g1y[v] = g2x[v] = g2y[v] = 0.f; }
+            } else {
+                float px[K], py[K], qx[K], qy[K];
+                load_poly<K>(p1 + k * 2 * K, px, py);
+                load_poly<K>(p2 + k * 2 * K, qx, qy);
+                Geo<K> g;
+                make_geo<K, COUNTS>(px, py, qx, qy, n1, n2, g);
+                bool have = true;
+                if (RECOMPUTE) {
+                    FwdOut<K> o;
+                    have = fwd_generic<K, COUNTS>(g, o);
+                    codes = o.codes;
+                    nxk = o.nx;
+                } else {
+                    nxk = nxs[k];
+                    load_codes<K>(xflags, k, codes);
+                }
+                uint32_t e = kSlow;
+                if (have) e = bwd_shape<K, COUNTS>(g, adj, nxk, codes, refine, g1x, g1y, g2x, g2y);
+                needfwd = !have;
+                slow = (e == kSlow);
+                if (!slow) err |= e;
+            }
+            if (!slow) {
+                store_poly<K>(g1 + k * 2 * K, g1x, g1y);
+                store_poly<K>(g2 + k * 2 * K, g2x, g2y);
+                put_zgrad<Z3>(za, k, adj);
+            }
+        }
+        if (RECOMPUTE) {
+            unsigned todo = __ballot_sync(full, needfwd);
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int64_t kk = base + src;
+                const int m1 = __shfl_sync(full, n1, src), m2 = __shfl_sync(full, n2, src);
+                FwdOut<K> o;
+                o.err = 0;
+                warp_robust<K>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, refine, o);
+                if (lane == src) {
+                    err |= o.err;
+                    codes = o.codes;
+                    nxk = o.nx;
+                }
+            }
+        }
+        unsigned todo = __ballot_sync(full, slow);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t kk = base + src;
+            const int m1 = __shfl_sync(full, n1, src), m2 = __shfl_sync(full, n2, src);
+            const uint32_t mnx = __shfl_sync(full, nxk, src);
+            Codes<K> cs;
+#pragma unroll
+            for (int q = 0; q < (2 * K + 7) / 8; ++q) cs.w[q] = __shfl_sync(full, codes.w[q], src);
+            auto a = adj_of<Z3>(LOSS ? -la.scale * loss_weight(la, kk) : __ldg(grad + kk), za, kk);
+            const uint32_t e = refine ? warp_bwd<K, double>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, a, mnx, cs,
+                                                            g1 + kk * 2 * K, g2 + kk * 2 * K, s_bwd[threadIdx.x >> 5])
+                                      : warp_bwd<K, float>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, a, mnx, cs,
+                                                           g1 + kk * 2 * K, g2 + kk * 2 * K, s_bwd[threadIdx.x >> 5]);
+            if (lane == src) {
+                err |= e;
+                put_zgrad<Z3>(za, kk, a);
+            }
+        }
+    }
+    if (err) atomicOr(status, err);
+}
+
+// K = 8: one group of 8 lanes per pair (group8.cuh), 4 pairs per warp and
+// step, grid-stride over warps.  Pairs the group cannot finish are done by the
+// whole warp (forward) or by the group's first lane (backward) afterwards.
+template <bool SAVE, bool LOSS, bool Z3>
+__global__ void __launch_bounds__(kPairThreads)
+k_paired_fwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
+                const uint8_t* __restrict__ c2, int64_t n, float* __restrict__ iou, uint8_t* __restrict__ nx,
+                uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status,
+                LossArgs la, ZArgs za) {
+    (void)flags;
+    const int lane = threadIdx.x & 31, r = lane & 7;
+    const int64_t warp = ((int64_t)blockIdx.x * kPairThreads + threadIdx.x) >> 5;
+    const int64_t stride = (int64_t)gridDim.x * (kPairThreads / 32) * 4;
+    uint32_t err = 0;
+    float acc = 0.f;
+    for (int64_t base = warp * 4; base < n; base += stride) {
+        const int64_t k = base + (lane >> 3);
+        const bool act = k < n;
+        const int n1 = (act && c1) ? (int)c1[k] : 8, n2 = (act && c2) ? (int)c2[k] : 8;
+        const bool good = act && n1 >= 3 && n1 <= 8 && n2 >= 3 && n2 <= 8;
+        bool hard = false;
+        const float w = (LOSS && act && r == 0) ? loss_weight(la, k) : 0.f;
+        if (good) {
+            g8::Lane L;
+            g8::load_lane(p1 + k * 16, p2 + k * 16, n1, n2, r, L);
+            g8::FwdG o;
+            hard = !g8::fwd_group(L, o);
+            if constexpr (Z3) {
+                if (!hard && r == 0) o.iou = iou3_value(o.ai, o.a1, o.a2, o.nx, z_of(za, k));
+            }
+            if (!hard && r == 0) {
+                if (LOSS) acc += la.scale * w * (1.f - o.iou);
+                if (!LOSS || iou) iou[k] = o.iou;
+                if (SAVE) {
+                    nx[k] = (uint8_t)o.nx;
+                    reinterpret_cast<uint4*>(xflags)[k] =
+                        make_uint4((uint32_t)o.w0, (uint32_t)(o.w0 >> 32), (uint32_t)o.w1, (uint32_t)(o.w1 >> 32));
+                }
+                if (degen) degen[k] = (uint8_t)o.degen;
+            }
+        } else if (act && r == 0) {
+            err |= kDevBadCount;
+            if (LOSS) acc += la.scale * w;
+            if (!LOSS || iou) iou[k] = 0.f;
+            if (SAVE) {
+                nx[k] = 0;
+                reinterpret_cast<uint4*>(xflags)[k] = make_uint4(~0u, ~0u, ~0u, ~0u);
+            }
+            if (degen) degen[k] = 0;
+        }
+        if (hard && r == 0) {
+            if (LOSS) nx[k] = kHardNx;
+            else reinterpret_cast<uint32_t*>(iou)[k] = kHardIou;
+        }
+    }
+    if (LOSS) put_partial(la, acc);
+    if (err) atomicOr(status, err);
+}
+
+template <bool RECOMPUTE, bool LOSS, bool Z3>
+__global__ void __launch_bounds__(kPairThreads)
+k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
+                const uint8_t* __restrict__ c2, int64_t n, const float* __restrict__ grad,
+                const uint8_t* __restrict__ nxs, const uint8_t* __restrict__ xflags, float* __restrict__ g1,
+                float* __restrict__ g2, uint32_t flags, uint32_t* status, LossArgs la, ZArgs za) {
+    constexpr unsigned full = 0xffffffffu;
+    __shared__ float s_bwd[kPairThreads / 32][32];
+    const int lane = threadIdx.x & 31, r = lane & 7;
+    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
+    const int64_t warp = ((int64_t)blockIdx.x * kPairThreads + threadIdx.x) >> 5;
+    const int64_t stride = (int64_t)gridDim.x * (kPairThreads / 32) * 4;
+    uint32_t err = 0;
+    for (int64_t base = warp * 4; base < n; base += stride) {
+        const int64_t k = base + (lane >> 3);
+        const bool act = k < n;
+        const int n1 = (act && c1) ? (int)c1[k] : 8, n2 = (act && c2) ? (int)c2[k] : 8;
+        const bool good = act && n1 >= 3 && n1 <= 8 && n2 >= 3 && n2 <= 8;
+        bool slow = false, needfwd = false;
+        uint64_t w0 = ~0ull, w1 = ~0ull;
+        uint32_t nxk = 0;
+        float gx1 = 0.f, gy1 = 0.f, gx2 = 0.f, gy2 = 0.f;
+        if (good) {
+            g8::Lane L;
+            g8::load_lane(p1 + k * 16, p2 + k * 16, n1, n2, r, L);
+            if (RECOMPUTE) {
+                g8::FwdG o;
+                needfwd = !g8::fwd_group(L, o);
+                w0 = o.w0;
+                w1 = o.w1;
+                nxk = o.nx;
+            } else {
+                const uint4 u = __ldg(reinterpret_cast<const uint4*>(xflags) + k);
+                w0 = (uint64_t)u.x | ((uint64_t)u.y << 32);
+                w1 = (uint64_t)u.z | ((uint64_t)u.w << 32);
+                nxk = nxs[k];
+            }
+            uint32_t e = kSlow;
+            auto adj = adj_of<Z3>(LOSS ? -la.scale * loss_weight(la, k) : __ldg(grad + k), za, k);
+            if (!needfwd) e = g8::bwd_group(L, adj, nxk, w0, w1, refine, gx1, gy1, gx2, gy2);
+            slow = e == kSlow;
+            if (!slow) {
+                if (r == 0) {
+                    err |= e;
+                    put_zgrad<Z3>(za, k, adj);
+                }
+                reinterpret_cast<float2*>(g1)[k * 8 + r] = make_float2(gx1, gy1);
+                reinterpret_cast<float2*>(g2)[k * 8 + r] = make_float2(gx2, gy2);
+            }
+        } else if (act) {
+            if (r == 0) {
+                err |= kDevBadCount;
+                put_zgrad<Z3>(za, k, adj_of<Z3>(0.f, za, k));
+            }
+            reinterpret_cast<float2*>(g1)[k * 8 + r] = make_float2(0.f, 0.f);
+            reinterpret_cast<float2*>(g2)[k * 8 + r] = make_float2(0.f, 0.f);
+        }
+        if (RECOMPUTE) {
+            unsigned todo = __ballot_sync(full, needfwd && r == 0);
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int64_t kk = base + (src >> 3);
+                const int m1 = __shfl_sync(full, n1, src), m2 = __shfl_sync(full, n2, src);
+                FwdOut<8> o;
+                o.err = 0;
+                warp_robust<8>(p1 + kk * 16, p2 + kk * 16, m1, m2, refine, o);
+                if (lane == src) {
+                    err |= o.err;
+                    w0 = o.codes.w[0];
+                    w1 = o.codes.w[1];
+                    nxk = o.nx;
+                }
+            }
+        }
+        unsigned todo = __ballot_sync(full, slow && r == 0);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t kk = base + (src >> 3);
+            const int m1 = __shfl_sync(full, n1, src), m2 = __shfl_sync(full, n2, src);
+            const uint32_t mnx = __shfl_sync(full, nxk, src);
+            Codes<8> cs;
+            cs.w[0] = __shfl_sync(full, w0, src);
+            cs.w[1] = __shfl_sync(full, w1, src);
+            auto a = adj_of<Z3>(LOSS ? -la.scale * loss_weight(la, kk) : __ldg(grad + kk), za, kk);
+            const uint32_t e = refine ? warp_bwd<8, double>(p1 + kk * 16, p2 + kk * 16, m1, m2, a, mnx, cs, g1 + kk * 16,
+                                                            g2 + kk * 16, s_bwd[threadIdx.x >> 5])
+                                      : warp_bwd<8, float>(p1 + kk * 16, p2 + kk * 16, m1, m2, a, mnx, cs, g1 + kk * 16,
+                                                           g2 + kk * 16, s_bwd[threadIdx.x >> 5]);
+            if (lane == src) {
+                err |= e;
+                put_zgrad<Z3>(za, kk, a);
+            }
+        }
+    }
+    if (err) atomicOr(status, err);
+}
+
+// ------------------------------------------------------------- IoU loss
+//
+// loss = scale * sum_k w_k (1 - IoU_k) and its gradient (the IoU-loss case
+// study, paper Sec. IV-A) in three launches on one stream: the paired forward
+// in loss mode (no IoU array needed; flags saved to the workspace), the paired
+// backward in loss mode (dL/dIoU formed in the kernel), and a one-block sum of
+// the per-warp partials in a fixed order, so the loss is deterministic.  A
+// single kernel doing both passes was measured slower: with the forward and
+// backward code resident together it needs about 1.5x the registers and
+// stalls on instruction fetch.
+
+static unsigned grid_for(int64_t n, int threads) {
+    int64_t blocks = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)sm_count() * 64;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    return (unsigned)blocks;
+}
+
+// Grid of the paired kernels: one thread per pair for K = 4, one group of 8
+// lanes per pair for K = 8.
+static unsigned paired_grid(int64_t n, int K) {
+    return K == 4 ? grid_for(n, kPairThreads) : grid_for((n + 3) / 4 * 32, kPairThreads);
+}
+
+template <int K, bool COUNTS, bool LOSS, bool Z3>
+static void fwd_dispatch(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                         float* iou, uint8_t* nx, uint8_t* xflags, uint8_t* degen, uint32_t flags, cudaStream_t s,
+                         const LossArgs& la, const ZArgs& za) {
+    const unsigned grid = paired_grid(n, K);
+    uint32_t* st = device_status_ptr();
+    if constexpr (K == 4) {
+        if (nx) k_paired_fwd<K, COUNTS, true, LOSS, Z3><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st, la, za);
+        else k_paired_fwd<K, COUNTS, false, LOSS, Z3><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st, la, za);
+    } else {
+        if (nx) k_paired_fwd_g8<true, LOSS, Z3><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st, la, za);
+        else k_paired_fwd_g8<false, LOSS, Z3><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st, la, za);
+    }
+    LossArgs lf = la;
+    if (LOSS) lf.partials = la.partials + (size_t)grid * (kPairThreads / 32);
+    k_paired_fix<K, LOSS, Z3><<<fix_grid(n), kFixThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st, lf, za);
+}
+
+// Forward (main kernel + fix pass) for K = 4 or 8; Z3 selects the 3D IoU.
+template <bool LOSS, bool Z3>
+static void fwd_any(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n, int K,
+                    float* iou, uint8_t* nx, uint8_t* xflags, uint8_t* degen, uint32_t flags, cudaStream_t s,
+                    const LossArgs& la, const ZArgs& za) {
+    if (K == 4) {
+        if (c1 || c2) fwd_dispatch<4, true, LOSS, Z3>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, s, la, za);
+        else fwd_dispatch<4, false, LOSS, Z3>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, s, la, za);
+    } else {
+        fwd_dispatch<8, true, LOSS, Z3>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, s, la, za);
+    }
+}
+
+template <int K, bool COUNTS, bool LOSS, bool Z3>
+static void bwd_dispatch(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                         const float* grad, const uint8_t* nx, const uint8_t* xflags, float* g1, float* g2,
+                         uint32_t flags, cudaStream_t s, const LossArgs& la, const ZArgs& za) {
+    const unsigned grid = paired_grid(n, K);
+    uint32_t* st = device_status_ptr();
+    const bool saved = nx && xflags && !(flags & kFlagPlain);
+    if constexpr (K == 4) {
+        if (saved)
+            k_paired_bwd<K, COUNTS, false, LOSS, Z3><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, st, la, za);
+        else
+            k_paired_bwd<K, COUNTS, true, LOSS, Z3><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, st, la, za);
+    } else {
+        if (saved)
+            k_paired_bwd_g8<false, LOSS, Z3><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, st, la, za);
+        else
+            k_paired_bwd_g8<true, LOSS, Z3><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, st, la, za);
+    }
+}
+
+template <bool LOSS, bool Z3>
+static void bwd_any(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n, int K,
+                    const float* grad, const uint8_t* nx, const uint8_t* xflags, float* g1, float* g2,
+                    uint32_t flags, cudaStream_t s, const LossArgs& la, const ZArgs& za) {
+    if (K == 4) {
+        if (c1 || c2) bwd_dispatch<4, true, LOSS, Z3>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, s, la, za);
+        else bwd_dispatch<4, false, LOSS, Z3>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, s, la, za);
+    } else {
+        bwd_dispatch<8, true, LOSS, Z3>(p1, c1, p2, c2, n, grad, nx, xflags, g1, g2, flags, s, la, za);
+    }
+}
+
+// Loss workspace: [per-warp partials | nx (n bytes) | xflags (n x 2K bytes)],
+// each part 256-byte aligned.
+struct LossLayout {
+    size_t partials, nx, xflags, total;
+    int64_t warps;
+};
+
+static LossLayout loss_layout(int64_t n, int K) {
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    LossLayout L;
+    // partials of the main forward, then of the fix pass
+    L.warps = (int64_t)paired_grid(n < 1 ? 1 : n, K) * (kPairThreads / 32) +
+              (int64_t)fix_grid(n < 1 ? 1 : n) * (kFixThreads / 32);
+    L.partials = 0;
+    L.nx = up((size_t)L.warps * 4);
+    L.xflags = L.nx + up((size_t)n);
+    L.total = L.xflags + up((size_t)n * 2 * K);
+    return L;
+}
+
+// The loss passes (forward and backward in loss mode; the partial sum is
+// launched by the caller).  The loss-mode forward always keeps nx (it carries
+// the fix-pass marks).
+template <bool Z3>
+static dgal_status iou_loss_passes(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                                   int K, const float* weight, float scale, float* iou, float* g1, float* g2,
+                                   const ZArgs& za, void* ws, uint32_t flags, cudaStream_t s, float** partials,
+                                   int64_t* warps) {
+    const LossLayout L = loss_layout(n, K);
+    unsigned char* base = static_cast<unsigned char*>(ws);
+    const LossArgs la{weight, scale, reinterpret_cast<float*>(base + L.partials)};
+    const bool save = g1 && !(flags & kFlagPlain);
+    uint8_t* nx = base + L.nx;
+    uint8_t* xflags = base + L.xflags;
+    fwd_any<true, Z3>(p1, c1, p2, c2, n, K, iou, nx, xflags, nullptr, flags, s, la, za);
+    dgal_status r = check_launch("IoU loss forward");
+    if (r != DGAL_OK) return r;
+    if (g1) {
+        bwd_any<true, Z3>(p1, c1, p2, c2, n, K, nullptr, save ? nx : nullptr, save ? xflags : nullptr, g1, g2, flags,
+                          s, la, za);
+        r = check_launch("IoU loss backward");
+        if (r != DGAL_OK) return r;
+    }
+    *partials = la.partials;
+    *warps = L.warps;
+    return DGAL_OK;
+}
+
+} // namespace dgal

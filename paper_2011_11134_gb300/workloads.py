@@ -121,6 +121,24 @@ def loss_pairs_1m(seed: int = 0, n: int = 1_000_000):
     return dict(p1=pred, p2=target, grad=np.ones(n, np.float32))
 
 
+def loss3d_pairs_1m(seed: int = 0, n: int = 1_000_000):
+    """3D IoU-loss pairs (rotated boxes with a vertical extent), K=4: the
+    bird's-eye view as in the IoU-loss pairs; target extent z ~ U[-1, 1],
+    h ~ U[1.4, 1.8]; prediction z + N(0, 0.2), h * exp(N(0, 0.1)).
+
+    Returns p1, z1 = prediction, p2, z2 = target (z = [n, 2] = (z_center,
+    height)), upstream grad = 1."""
+    d = loss_pairs_1m(seed, n)
+    r = rng_for(seed + 7919)
+    z = r.uniform(-1.0, 1.0, size=n)
+    h = r.uniform(1.4, 1.8, size=n)
+    zp = z + r.normal(0.0, 0.2, size=n)
+    hp = h * np.exp(r.normal(0.0, 0.1, size=n))
+    d["z1"] = np.stack([zp, hp], 1).astype(np.float32)
+    d["z2"] = np.stack([z, h], 1).astype(np.float32)
+    return d
+
+
 # ----------------------------------------------------- general convex polygons
 
 

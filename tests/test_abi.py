@@ -20,7 +20,7 @@ def libdgal():
 def _declared():
     src = open(os.path.join(ROOT, "include", "dgal.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(dgal_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(dgal_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_calls():
