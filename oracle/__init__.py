@@ -288,3 +288,30 @@ def iou3d_backward_paired(p1, p2, z1, z2, grad, nx, xflags, c1=None, c2=None, th
     gz1 = np.stack([gov * (t1 - b1), gov * 0.5 * (t1 + b1) + g * d_vol * a1], axis=1)
     gz2 = np.stack([gov * ((1 - t1) - (1 - b1)), gov * 0.5 * ((1 - t1) + (1 - b1)) + g * d_vol * a2], axis=1)
     return g1, gz1, g2, gz2
+
+
+# ------------------------------------------------------------ rotated NMS
+#
+# Greedy non-maximum suppression over rotated boxes (the consumer of the
+# pairwise IoU matrix named in the paper's Sec. IV, OpenPCDet's rotated NMS):
+# visit the boxes by descending score (equal scores: lower index first); keep
+# a box unless a kept box overlaps it with IoU > threshold.
+
+def nms_rotated(boxes, scores, threshold, counts=None, threads: int = 1):
+    """Kept box indices (int64, in visiting order)."""
+    boxes = np.asarray(boxes)
+    scores = np.asarray(scores, dtype=np.float64)
+    n = boxes.shape[0]
+    if n == 0:
+        return np.zeros(0, np.int64)
+    order = np.array(sorted(range(n), key=lambda i: (-scores[i], i)), dtype=np.int64)
+    cs = None if counts is None else np.asarray(counts)[order]
+    iou, _ = iou_pairwise(boxes[order], boxes[order], cs, cs, threads=threads)
+    removed = np.zeros(n, bool)
+    keep = []
+    for a in range(n):
+        if removed[a]:
+            continue
+        keep.append(order[a])
+        removed[a + 1:] |= iou[a, a + 1:] > threshold
+    return np.array(keep, dtype=np.int64)
