@@ -218,6 +218,31 @@ dgal_status dgal_iou_pairwise_per_scene(int S, const int64_t* a_off_h, const int
                                         void* stream);
 
 /*
+ * Rotated non-maximum suppression (greedy NMS over convex polygons, the use of
+ * the pairwise IoU in rotated-box detection, paper Sec. IV): visit the boxes
+ * by descending score, equal scores by lower index first, NaN scores last (as
+ * -infinity); keep a box unless an already kept box overlaps it with
+ * IoU > threshold.  The IoU is the FP32 IoU of dgal_iou_pairwise, so the
+ * result equals that greedy rule applied to dgal_iou_pairwise's matrix.
+ *   boxes    float [N][K][2] (16-byte aligned), counts uint8 [N] or NULL;
+ *   scores   float [N];
+ *   keep     int64 [N], receives the kept box indices in visiting order in
+ *            keep[0 .. *num_keep); entries beyond are left unchanged;
+ *   num_keep int64 [1] (device), receives the number of kept boxes;
+ *   workspace: device memory of at least dgal_nms_workspace_bytes(N, K)
+ *            bytes (about N^2 / 8 bytes for the suppression bitmap),
+ *            16-byte aligned, caller-owned, contents ignored on entry; calls
+ *            sharing it must not overlap in time.
+ * N <= 131072 (larger N returns DGAL_ERR_INVALID_ARG and
+ * dgal_nms_workspace_bytes returns 0).  N = 0 sets *num_keep = 0.
+ * `flags`: DGAL_FP64_REFINE as for dgal_iou_pairwise.
+ */
+size_t dgal_nms_workspace_bytes(int64_t N, int K);
+dgal_status dgal_nms_rotated(const float* boxes, const uint8_t* counts, const float* scores, int64_t N, int K,
+                             float threshold, int64_t* keep, int64_t* num_keep, void* workspace, size_t ws_bytes,
+                             uint32_t flags, void* stream);
+
+/*
  * CUDA-graph form of dgal_iou_pairwise_batched: captures the call (with these
  * exact pointers and S) into an executable graph; dgal_graph_launch replays
  * it on `stream`.  Inputs may be rewritten in place between replays.

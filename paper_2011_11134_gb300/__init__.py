@@ -7,6 +7,7 @@ Python binding of libdgal's C ABI (include/dgal.h), with the same call names:
     dgal_iou_pairwise          N x M IoU matrix
     dgal_iou_pairwise_batched  ragged scenes in one persistent launch
     dgal_iou_pairwise_per_scene  the plain one-launch-per-scene form
+    dgal_nms_rotated           greedy rotated NMS on the pairwise IoU
     BatchedGraph               the ragged batch captured in a CUDA graph
     dgal_autotune              launch-shape tuner for the ragged batch
     dgal_get_device_status     device-side error bits
@@ -36,7 +37,7 @@ __all__ = [
     "dgal_get_batched_config", "dgal_get_device_status", "dgal_last_error", "dgal_version", "IoU", "iou",
     "DGAL_FP64_REFINE", "DGAL_PLAIN", "DGAL_DEV_BAD_COUNT", "DGAL_DEV_OVERFLOW", "DGAL_DEV_BAD_FLAGS",
     "DGAL_DEV_BAD_OFFSETS", "DgalError", "dgal_iou3d_paired", "dgal_iou3d_backward", "dgal_iou3d_loss", "IoU3D",
-    "iou3d", "IoU3DLoss", "iou3d_loss",
+    "iou3d", "IoU3DLoss", "iou3d_loss", "dgal_nms_rotated", "dgal_nms_workspace_bytes",
 ]
 
 
@@ -233,6 +234,38 @@ def dgal_iou_pairwise(a, b, ca=None, cb=None, with_nx=True, flags=DGAL_FP64_REFI
     _lib.call("dgal_iou_pairwise", _lib.ptr(a), _lib.ptr(ca), N, _lib.ptr(b), _lib.ptr(cb), M, K, _lib.ptr(iou),
               _lib.ptr(nx), flags, _lib.stream_ptr(stream))
     return iou, nx
+
+
+def dgal_nms_workspace_bytes(N, K=4):
+    return int(_lib.lib().dgal_nms_workspace_bytes(N, K))
+
+
+def dgal_nms_rotated(boxes, scores, threshold, counts=None, flags=DGAL_FP64_REFINE, stream=None, workspace=None,
+                     sync=True):
+    """Greedy rotated NMS: boxes visited by descending score (ties: lower
+    index first), a box kept unless a kept box has IoU > threshold with it.
+    sync=True returns the kept indices (int64 [num_keep], visiting order),
+    reading the count back; sync=False returns (keep [N], num_keep [1]) on the
+    device without synchronising."""
+    _poly(boxes, "boxes")
+    N, K = boxes.shape[0], boxes.shape[1]
+    if not isinstance(scores, torch.Tensor) or scores.dtype != torch.float32 or scores.shape != (N,) \
+            or scores.device != boxes.device or not scores.is_contiguous():
+        raise ValueError(f"scores must be a contiguous float32 tensor of shape ({N},) on {boxes.device}")
+    counts = _counts(counts, N, "counts", boxes.device)
+    need = dgal_nms_workspace_bytes(N, K)
+    if need == 0 and N > 0:
+        raise ValueError(f"N = {N} boxes is beyond the NMS limit")
+    if workspace is None:
+        workspace = torch.empty(max(need, 16), device=boxes.device, dtype=torch.uint8)
+    keep = torch.empty(N, device=boxes.device, dtype=torch.int64)
+    num_keep = torch.empty(1, device=boxes.device, dtype=torch.int64)
+    _lib.call("dgal_nms_rotated", _lib.ptr(boxes), _lib.ptr(counts), _lib.ptr(scores), N, K, float(threshold),
+              _lib.ptr(keep), _lib.ptr(num_keep), _lib.ptr(workspace), workspace.numel(), flags,
+              _lib.stream_ptr(stream))
+    if not sync:
+        return keep, num_keep
+    return keep[: int(num_keep.item())]
 
 
 def dgal_batched_workspace_bytes(S, K=4):

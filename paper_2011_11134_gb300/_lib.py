@@ -47,6 +47,8 @@ _SIG = {
     "dgal_iou_pairwise_batched_noalloc": (_I, [_I, _P, _P, _P, _P, _P, _P, _P, _I, _P, _P, _U32, _P]),
     "dgal_batched_graph_create": (_I, [ctypes.POINTER(_P), _I, _P, _P, _P, _P, _P, _P, _P, _I, _P, _P, _P,
                                        ctypes.c_size_t, _U32]),
+    "dgal_nms_workspace_bytes": (ctypes.c_size_t, [_I64, _I]),
+    "dgal_nms_rotated": (_I, [_P, _P, _P, _I64, _I, ctypes.c_float, _P, _P, _P, ctypes.c_size_t, _U32, _P]),
     "dgal_graph_launch": (_I, [_P, _P]),
     "dgal_graph_destroy": (_I, [_P]),
     "dgal_autotune": (_I, [_I, _I, ctypes.c_char_p]),

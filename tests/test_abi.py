@@ -67,3 +67,29 @@ def test_validation_rejects_before_any_launch(libdgal):
     assert f(al, None, al, None, 1, 4, None, None, None, None, 0, None) == 1  # iou NULL
     assert f(al, None, al, None, 1, 4, al, al, None, None, 0, None) == 1  # nx without xflags
     assert b"xflags" in libdgal.dgal_last_error()
+
+
+def test_nms_host_checks(libdgal):
+    """NMS workspace sizing and its limits are host-side."""
+    ws = libdgal.dgal_nms_workspace_bytes
+    ws.restype = ctypes.c_size_t
+    ws.argtypes = [ctypes.c_int64, ctypes.c_int]
+    n = 1000
+    words = (n + 63) // 64
+    assert ws(n, 4) >= n * 4 + n * 32 + n + n * words * 8
+    assert ws(n, 8) > ws(n, 4)
+    assert ws(131072, 4) > 0 and ws(131073, 4) == 0 and ws(10, 5) == 0 and ws(-1, 4) == 0
+    f = libdgal.dgal_nms_rotated
+    P = ctypes.c_void_p
+    f.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int, ctypes.c_float, P, P, P, ctypes.c_size_t, ctypes.c_uint32, P]
+    f.restype = ctypes.c_int
+    buf = (ctypes.c_double * 64)()
+    base = ctypes.addressof(buf)
+    al = base + (-base % 16)
+    assert f(al, None, al, 10, 6, 0.5, al, al, al, 1 << 20, 0, None) == 2  # K unsupported
+    assert f(al, None, al, 200000, 4, 0.5, al, al, al, 1 << 20, 0, None) == 1  # beyond the box limit
+    assert f(al, None, al, 10, 4, 0.5, al, None, al, 1 << 20, 0, None) == 1  # num_keep NULL
+    assert f(al, None, al, 10, 4, 0.5, al, al + 4, al, 1 << 20, 0, None) == 3  # num_keep misaligned
+    assert f(al + 8, None, al, 10, 4, 0.5, al, al, al, 1 << 20, 0, None) == 3  # boxes misaligned
+    assert f(al, None, al, 10, 4, 0.5, al, al, al, 16, 0, None) == 5  # workspace too small
+    assert f(al, None, al, 10, 4, 0.5, al, al, None, 1 << 20, 0, None) == 5  # workspace NULL
