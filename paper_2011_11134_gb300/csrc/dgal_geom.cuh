@@ -189,6 +189,44 @@ template <int K, bool COUNTS> __device__ __forceinline__ float pair_scale(const 
 
 // ------------------------------------------------------------ generic path
 
+// orient(a, b, p) = cross(b - a, p - a) of three input points read from the
+// unrounded FP32 inputs, in IEEE double without contraction and in the same
+// operand order as the FP64 definition, so the value (and its sign) is the
+// FP64 definition's.
+__device__ __forceinline__ double orient_raw(const float* __restrict__ pa, int ia, int ib,
+                                             const float* __restrict__ pp, int ip) {
+    const float2 A = __ldg(reinterpret_cast<const float2*>(pa) + ia);
+    const float2 B = __ldg(reinterpret_cast<const float2*>(pa) + ib);
+    const float2 P = __ldg(reinterpret_cast<const float2*>(pp) + ip);
+    const double bx = __dsub_rn((double)B.x, (double)A.x), by = __dsub_rn((double)B.y, (double)A.y);
+    const double px = __dsub_rn((double)P.x, (double)A.x), py = __dsub_rn((double)P.y, (double)A.y);
+    return __dsub_rn(__dmul_rn(bx, py), __dmul_rn(by, px));
+}
+
+// Sign repair for a pair of quadrilaterals (K = 4): `small` marks the
+// orientations whose FP32 value is too small to trust (bit i*4+j: S(i,j) =
+// orient(b_j, b_j+1, a_i); bit 16+i*4+j: T(i,j) = orient(a_i, a_i+1, b_j)),
+// `neg` holds the FP32 signs in the same layout.  Each marked orientation is
+// re-evaluated by orient_raw and its sign bit replaced.  Returns the repaired
+// signs, or bit 32 set when one is exactly zero (a vertex on the line of an
+// edge: the pair is not in general position).  Not inlined: it runs for well
+// under 0.1% of random pairs, and keeping it out of line keeps the fast
+// path's registers unchanged.
+static __device__ __noinline__ uint64_t exact_signs4(const float* __restrict__ raw1, const float* __restrict__ raw2, int n1,
+                                              int n2, uint32_t small, uint32_t neg) {
+    while (small) {
+        const int b = __ffs(small) - 1;
+        small &= small - 1u;
+        const int q = b & 15, i = q >> 2, j = q & 3;
+        double v;
+        if (b >= 16) v = orient_raw(raw1, i, (i + 1 < n1) ? i + 1 : 0, raw2, j);
+        else v = orient_raw(raw2, j, (j + 1 < n2) ? j + 1 : 0, raw1, i);
+        if (v == 0.0) return 1ull << 32;
+        neg = (v < 0.0) ? (neg | (1u << b)) : (neg & ~(1u << b));
+    }
+    return neg;
+}
+
 // 2K code bytes as one integer (byte k = slot k).
 template <int K> struct SeqOf { typedef uint64_t T; };
 template <> struct SeqOf<8> { typedef unsigned __int128 T; };
@@ -218,7 +256,19 @@ template <int K, bool COUNTS> __device__ __forceinline__ uint64_t q_chain_bytes(
 // local-frame values), every sign is exact, so the inside tests, crossings and
 // the vertex order are exactly those of the FP64 definition.  On success fills
 // o.codes, o.nx and o.ai.
-template <int K, bool COUNTS> __device__ __forceinline__ bool fwd_generic(const Geo<K>& g, FwdOut<K>& o) {
+//
+// raw1, raw2 (optional, K = 4): the pair's unrounded input polygons.  When
+// given, a pair with orientations under the routing threshold is not handed
+// back: those orientations take the FP64 definition's sign (exact_signs4), and
+// only an exact zero (a vertex on the line of an edge) hands the pair back.
+// Their FP32 values still place the crossing points: an FP32 orientation is
+// within 2.9e-6 L^2 of the exact one, which moves a crossing point along its
+// P1 edge and changes the intersection area by at most about 1.5e-6 L^2 per
+// crossing, whatever the crossing angle (the same bound as for any pair of
+// the fast path).  The pair is still reported near-degenerate.
+template <int K, bool COUNTS>
+__device__ __forceinline__ bool fwd_generic(const Geo<K>& g, FwdOut<K>& o, const float* __restrict__ raw1 = nullptr,
+                                            const float* __restrict__ raw2 = nullptr) {
     typedef typename MaskOf<K>::T M;
     typedef typename SeqOf<K>::T Sq;
     constexpr int KK = K * K;
@@ -252,8 +302,39 @@ template <int K, bool COUNTS> __device__ __forceinline__ bool fwd_generic(const 
             neg_t |= (M)(__float_as_uint(t) >> 31) << (i * K + j);
         }
     }
-    if (!(L > 0.f) || !(minabs > thr)) return false;
-    o.degen = (minabs <= kDegenRel * L * L) ? 1u : 0u;
+    if (!(L > 0.f)) return false;
+    uint32_t refined = 0u;
+    if (!(minabs > thr)) {
+        if constexpr (!KEEP) {
+            return false;
+        } else {
+            if (raw1 == nullptr) return false;
+            // Mark every orientation within 3x the threshold (the marks are
+            // taken on a recomputation, which may round differently from the
+            // values above by up to twice the FP32 error bound, so the margin
+            // covers every value that was under the threshold) and take the
+            // FP64 definition's sign for each.
+            const float wide = 3.f * thr;
+            uint32_t small = 0;
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const bool valid = !COUNTS || (i < n1 && j < n2);
+                    const float dx = g.ax[i] - g.bx[j], dy = g.ay[i] - g.by[j];
+                    const float t = g.eay[i] * dx - g.eax[i] * dy;
+                    small |= (valid && !(fabsf(Sv[i * K + j]) > wide)) ? (1u << (i * K + j)) : 0u;
+                    small |= (valid && !(fabsf(t) > wide)) ? (1u << (16 + i * K + j)) : 0u;
+                }
+            }
+            const uint64_t r = exact_signs4(raw1, raw2, n1, n2, small, (uint32_t)neg_s | ((uint32_t)neg_t << 16));
+            if (r >> 32) return false;
+            neg_s = (M)(r & 0xFFFFu);
+            neg_t = (M)((r >> 16) & 0xFFFFu);
+            refined = 2u;
+        }
+    }
+    o.degen = ((minabs <= kDegenRel * L * L) ? 1u : 0u) | refined;
 
     M V = (M)~(M)0;
     if constexpr (KK < 8 * (int)sizeof(M)) V = (M)((1ull << KK) - 1);

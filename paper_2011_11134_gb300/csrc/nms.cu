@@ -104,7 +104,7 @@ k_nms_mask(const float* __restrict__ sboxes, const uint8_t* __restrict__ scounts
         const float* pb = sboxes + (act ? b : 0) * 2 * K;
         float v = 0.f;
         uint32_t nxv = 0;
-        const bool hard = act && pw_fast<K, COUNTS>(pa, pb, n1, n2, v, nxv, err);
+        const bool hard = act && pw_fast<K, COUNTS>(pa, pb, n1, n2, v, nxv, err, refine);
         pw_finish<K>(__ballot_sync(0xffffffffu, hard), pa, pb, n1, n2, refine, v, nxv, err);
         half[h] = __ballot_sync(0xffffffffu, act && v > thr);
     }

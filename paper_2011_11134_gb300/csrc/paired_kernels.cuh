@@ -46,19 +46,13 @@ template <int K> __device__ __forceinline__ void store_poly(float* __restrict__ 
 // Both kernels walk the pairs warp by warp (32 consecutive pairs per warp and
 // step, grid-stride over warps), with no block-wide barrier.  In the forward,
 // a pair the fast path cannot finish (near-degenerate or not in general
-// position) is only marked; a second kernel (k_paired_fix) scans the marks
-// and finishes each marked pair with the whole warp (warp_robust).  Keeping
-// the robust path out of the main kernel keeps its registers and its FP64
-// latency out of the common case.  In the backward, a pair whose codes the
-// shape derivative cannot take (not in general position, or with refinement
-// a tiny intersection) takes the shoelace adjoint after the rest, with the
-// whole warp on it (warp_bwd).
-
-// Mark of a pair left to k_paired_fix: an IoU of this signalling-NaN bit
-// pattern (arithmetic never produces it: NaN results are the canonical NaN)
-// or, in loss mode, nx = kHardNx.
-constexpr uint32_t kHardIou = 0x7fbadbadu;
-constexpr uint8_t kHardNx = 0xFFu;
+// position, well under 0.1% of random boxes) is finished right after the
+// step by the whole warp (warp_robust, a non-inlined call, so its registers
+// and FP64 code stay off the common path); the SM keeps issuing from its other
+// warps meanwhile.  In the backward, a pair whose codes the shape derivative
+// cannot take (not in general position, or with refinement a tiny
+// intersection) takes the shoelace adjoint after the rest, with the whole
+// warp on it (warp_bwd).
 
 // IoU-loss mode of the paired kernels (paper Sec. IV-A, the IoU loss over
 // rotated boxes): the forward adds scale * w_k (1 - IoU_k) into one partial
@@ -119,15 +113,30 @@ __device__ __forceinline__ void put_partial(const LossArgs& la, float acc) {
     if ((threadIdx.x & 31) == 0) la.partials[((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5] = acc;
 }
 
+// Stores the forward results of pair k (and adds its loss term in loss mode).
+template <int K, bool SAVE, bool LOSS>
+__device__ __forceinline__ void put_fwd(const FwdOut<K>& o, int64_t k, float w, const LossArgs& la,
+                                        float* __restrict__ iou, uint8_t* __restrict__ nx,
+                                        uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, float& acc) {
+    if (LOSS) acc += la.scale * w * (1.f - o.iou);
+    if (!LOSS || iou) iou[k] = o.iou;
+    if (SAVE) {
+        nx[k] = (uint8_t)o.nx;
+        store_codes<K>(xflags, k, o.codes);
+    }
+    if (degen) degen[k] = (uint8_t)o.degen;
+}
+
 template <int K, bool COUNTS, bool SAVE, bool LOSS, bool Z3>
 __global__ void __launch_bounds__(kPairThreads)
 k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
              const uint8_t* __restrict__ c2, int64_t n, float* __restrict__ iou, uint8_t* __restrict__ nx,
              uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status,
              LossArgs la, ZArgs za) {
-    (void)flags;
+    constexpr unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * kPairThreads;
+    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
     uint32_t err = 0;
     float acc = 0.f;
     for (int64_t base = (int64_t)blockIdx.x * kPairThreads + (threadIdx.x & ~31); base < n; base += stride) {
@@ -156,7 +165,8 @@ k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
                 make_geo<K, COUNTS>(px, py, qx, qy, n1, n2, g);
                 input_areas<K, COUNTS>(g, o.a1, o.a2);
                 o.degen = 0;
-                hard = !fwd_generic<K, COUNTS>(g, o);
+                hard = refine ? !fwd_generic<K, COUNTS>(g, o, p1 + k * 2 * K, p2 + k * 2 * K)
+                              : !fwd_generic<K, COUNTS>(g, o);
                 if (!hard) {
                     if constexpr (Z3) {
                         o.iou = iou3_value(o.ai, o.a1, o.a2, o.nx, z_of(za, k));
@@ -166,98 +176,25 @@ k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
                     }
                 }
             }
-            if (!hard) {
-                if (LOSS) acc += la.scale * w * (1.f - o.iou);
-                if (!LOSS || iou) iou[k] = o.iou;
-                if (SAVE) {
-                    nx[k] = (uint8_t)o.nx;
-                    store_codes<K>(xflags, k, o.codes);
-                }
-                if (degen) degen[k] = (uint8_t)o.degen;
-            }
+            if (!hard) put_fwd<K, SAVE, LOSS>(o, k, w, la, iou, nx, xflags, degen, acc);
         }
-        if (hard) {
-            if (LOSS) nx[k] = kHardNx;
-            else reinterpret_cast<uint32_t*>(iou)[k] = kHardIou;
-        }
-    }
-    if (LOSS) put_partial(la, acc);
-    if (err) atomicOr(status, err);
-}
-
-// Second forward pass: finishes the pairs the main kernel marked, each with
-// the whole warp (warp_robust), and writes all of their outputs.  Each block
-// owns a contiguous range of segments of kFixSeg pairs (normally one): the
-// block reads the segment's marks (4 B per pair, or 1 B in loss mode,
-// coalesced), queues the marked pairs in shared memory, and its warps then
-// take the queue in turn, so the robust calls of a segment run at once.
-constexpr int kFixThreads = 256;
-constexpr int kFixSeg = 1024;
-
-// One segment per block while that fits the grid: short-lived blocks let each
-// SM overlap many robust calls (a block that meets none exits after its scan).
-static unsigned fix_grid(int64_t n) {
-    const int64_t segs = (n + kFixSeg - 1) / kFixSeg;
-    const int64_t cap = (int64_t)1 << 30;
-    return (unsigned)(segs < 1 ? 1 : (segs < cap ? segs : cap));
-}
-
-template <int K, bool LOSS, bool Z3>
-__global__ void __launch_bounds__(kFixThreads)
-k_paired_fix(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
-             const uint8_t* __restrict__ c2, int64_t n, float* __restrict__ iou, uint8_t* __restrict__ nx,
-             uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status,
-             LossArgs la, ZArgs za) {
-    constexpr unsigned full = 0xffffffffu;
-    constexpr int kWarps = kFixThreads / 32;
-    __shared__ int q[kFixSeg];
-    __shared__ int qn;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
-    const int64_t segs = (n + kFixSeg - 1) / kFixSeg;
-    const int64_t per = (segs + gridDim.x - 1) / gridDim.x;
-    const int64_t s0 = (int64_t)blockIdx.x * per, s1 = (s0 + per < segs) ? s0 + per : segs;
-    uint32_t err = 0;
-    float acc = 0.f;
-    if (threadIdx.x == 0) qn = 0;
-    __syncthreads();
-    for (int64_t sg = s0; sg < s1; ++sg) {
-        const int64_t base = sg * kFixSeg;
-#pragma unroll
-        for (int r = 0; r < kFixSeg / kFixThreads; ++r) {
-            const int off = r * kFixThreads + (int)threadIdx.x;
-            const int64_t k = base + off;
-            bool hard = false;
-            if (k < n) hard = LOSS ? (nx[k] == kHardNx) : (__ldg(reinterpret_cast<const uint32_t*>(iou) + k) == kHardIou);
-            const unsigned b = __ballot_sync(full, hard);
-            int pos = 0;
-            if (lane == 0 && b) pos = atomicAdd(&qn, __popc(b));
-            pos = __shfl_sync(full, pos, 0);
-            if (hard) q[pos + __popc(b & ((1u << lane) - 1u))] = off;
-        }
-        __syncthreads();
-        const int m = qn;
-        for (int e = warp; e < m; e += kWarps) {
-            const int64_t kk = base + q[e];
-            const int m1 = c1 ? (int)c1[kk] : K, m2 = c2 ? (int)c2[kk] : K;
+        // pairs the fast path hands back (near-degenerate or not in general
+        // position): finished here, one at a time, by the whole warp
+        unsigned todo = __ballot_sync(full, hard);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t kk = base + src;
+            const int m1 = __shfl_sync(full, n1, src), m2 = __shfl_sync(full, n2, src);
             FwdOut<K> o;
             o.err = 0;
             warp_robust<K>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, refine, o);
-            if constexpr (Z3) o.iou = iou3_value(o.ai, o.a1, o.a2, o.nx, z_of(za, kk));
-            if (lane == 0) {
+            if (lane == src) {
+                if constexpr (Z3) o.iou = iou3_value(o.ai, o.a1, o.a2, o.nx, z_of(za, kk));
                 err |= o.err;
-                if (LOSS) acc += la.scale * loss_weight(la, kk) * (1.f - o.iou);
-                if (!LOSS || iou) iou[kk] = o.iou;
-                if (nx) {
-                    nx[kk] = (uint8_t)o.nx;
-                    store_codes<K>(xflags, kk, o.codes);
-                }
-                if (degen) degen[kk] = (uint8_t)o.degen;
+                put_fwd<K, SAVE, LOSS>(o, kk, w, la, iou, nx, xflags, degen, acc);
             }
         }
-        __syncthreads();
-        if (threadIdx.x == 0) qn = 0;
-        __syncthreads();
     }
     if (LOSS) put_partial(la, acc);
     if (err) atomicOr(status, err);
@@ -301,7 +238,8 @@ k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
                 bool have = true;
                 if (RECOMPUTE) {
                     FwdOut<K> o;
-                    have = fwd_generic<K, COUNTS>(g, o);
+                    have = refine ? fwd_generic<K, COUNTS>(g, o, p1 + k * 2 * K, p2 + k * 2 * K)
+                                  : fwd_generic<K, COUNTS>(g, o);
                     codes = o.codes;
                     nxk = o.nx;
                 } else {
@@ -370,8 +308,8 @@ k_paired_fwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
                 const uint8_t* __restrict__ c2, int64_t n, float* __restrict__ iou, uint8_t* __restrict__ nx,
                 uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status,
                 LossArgs la, ZArgs za) {
-    (void)flags;
     const int lane = threadIdx.x & 31, r = lane & 7;
+    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
     const int64_t warp = ((int64_t)blockIdx.x * kPairThreads + threadIdx.x) >> 5;
     const int64_t stride = (int64_t)gridDim.x * (kPairThreads / 32) * 4;
     uint32_t err = 0;
@@ -411,9 +349,21 @@ k_paired_fwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
             }
             if (degen) degen[k] = 0;
         }
-        if (hard && r == 0) {
-            if (LOSS) nx[k] = kHardNx;
-            else reinterpret_cast<uint32_t*>(iou)[k] = kHardIou;
+        // pairs the group hands back: finished by the whole warp, one at a time
+        unsigned todo = __ballot_sync(0xffffffffu, hard && r == 0);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t kk = base + (src >> 3);
+            const int m1 = __shfl_sync(0xffffffffu, n1, src), m2 = __shfl_sync(0xffffffffu, n2, src);
+            FwdOut<8> o;
+            o.err = 0;
+            warp_robust<8>(p1 + kk * 16, p2 + kk * 16, m1, m2, refine, o);
+            if (lane == src) {
+                if constexpr (Z3) o.iou = iou3_value(o.ai, o.a1, o.a2, o.nx, z_of(za, kk));
+                err |= o.err;
+                put_fwd<8, SAVE, LOSS>(o, kk, w, la, iou, nx, xflags, degen, acc);
+            }
         }
     }
     if (LOSS) put_partial(la, acc);
@@ -557,12 +507,9 @@ static void fwd_dispatch(const float* p1, const uint8_t* c1, const float* p2, co
         if (nx) k_paired_fwd_g8<true, LOSS, Z3><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st, la, za);
         else k_paired_fwd_g8<false, LOSS, Z3><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st, la, za);
     }
-    LossArgs lf = la;
-    if (LOSS) lf.partials = la.partials + (size_t)grid * (kPairThreads / 32);
-    k_paired_fix<K, LOSS, Z3><<<fix_grid(n), kFixThreads, 0, s>>>(p1, c1, p2, c2, n, iou, nx, xflags, degen, flags, st, lf, za);
 }
 
-// Forward (main kernel + fix pass) for K = 4 or 8; Z3 selects the 3D IoU.
+// Forward for K = 4 or 8; Z3 selects the 3D IoU.
 template <bool LOSS, bool Z3>
 static void fwd_any(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n, int K,
                     float* iou, uint8_t* nx, uint8_t* xflags, uint8_t* degen, uint32_t flags, cudaStream_t s,
@@ -617,9 +564,8 @@ struct LossLayout {
 static LossLayout loss_layout(int64_t n, int K) {
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     LossLayout L;
-    // partials of the main forward, then of the fix pass
-    L.warps = (int64_t)paired_grid(n < 1 ? 1 : n, K) * (kPairThreads / 32) +
-              (int64_t)fix_grid(n < 1 ? 1 : n) * (kFixThreads / 32);
+    // one partial per warp of the forward grid
+    L.warps = (int64_t)paired_grid(n < 1 ? 1 : n, K) * (kPairThreads / 32);
     L.partials = 0;
     L.nx = up((size_t)L.warps * 4);
     L.xflags = L.nx + up((size_t)n);
@@ -628,8 +574,7 @@ static LossLayout loss_layout(int64_t n, int K) {
 }
 
 // The loss passes (forward and backward in loss mode; the partial sum is
-// launched by the caller).  The loss-mode forward always keeps nx (it carries
-// the fix-pass marks).
+// launched by the caller).
 template <bool Z3>
 static dgal_status iou_loss_passes(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
                                    int K, const float* weight, float scale, float* iou, float* g1, float* g2,

@@ -45,7 +45,7 @@ k_pairwise(const float* __restrict__ a, const uint8_t* __restrict__ ca, int64_t 
         const float* pb = b + (act ? j : 0) * 2 * K;
         float v = 0.f;
         uint32_t c = 0;
-        const bool hard = act && pw_fast<K, COUNTS>(pa, pb, n1, n2, v, c, err);
+        const bool hard = act && pw_fast<K, COUNTS>(pa, pb, n1, n2, v, c, err, refine);
         pw_finish<K>(__ballot_sync(0xffffffffu, hard), pa, pb, n1, n2, refine, v, c, err);
         if (act) {
             iou[e] = v;
@@ -155,7 +155,7 @@ __global__ void k_batched(int S, const int64_t* __restrict__ a_off, const int64_
             const float* pb = b + (act ? b0 + j : 0) * 2 * K;
             float v = 0.f;
             uint32_t c = 0;
-            const bool hard = act && pw_fast<K, COUNTS>(pa, pb, n1, n2, v, c, err);
+            const bool hard = act && pw_fast<K, COUNTS>(pa, pb, n1, n2, v, c, err, refine);
             pw_finish<K>(__ballot_sync(0xffffffffu, hard), pa, pb, n1, n2, refine, v, c, err);
             if (act) {
                 iou[o0 + e] = v;

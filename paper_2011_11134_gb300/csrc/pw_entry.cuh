@@ -13,9 +13,10 @@ constexpr int kPwThreads = 128;
 
 // Fast path for one matrix entry.  Returns true when the entry must be
 // finished by the warp-cooperative robust path; otherwise sets iou / nxo.
+// `refine`: FP64 signs for orientations too small for FP32 (fwd_generic).
 template <int K, bool COUNTS>
 __device__ __forceinline__ bool pw_fast(const float* __restrict__ pa, const float* __restrict__ pb, int n1, int n2,
-                                        float& iou, uint32_t& nxo, uint32_t& err) {
+                                        float& iou, uint32_t& nxo, uint32_t& err, bool refine) {
     iou = 0.f;
     nxo = 0u;
     if (COUNTS && (n1 < 3 || n1 > K || n2 < 3 || n2 > K)) {
@@ -44,7 +45,7 @@ __device__ __forceinline__ bool pw_fast(const float* __restrict__ pa, const floa
     FwdOut<K> o;
     make_geo<K, COUNTS>(px, py, qx, qy, n1, n2, g);
     input_areas<K, COUNTS>(g, o.a1, o.a2);
-    if (!fwd_generic<K, COUNTS>(g, o)) return true;
+    if (!(refine ? fwd_generic<K, COUNTS>(g, o, pa, pb) : fwd_generic<K, COUNTS>(g, o))) return true;
     const float U = o.a1 + o.a2 - o.ai;
     nxo = o.nx;
     iou = (o.nx >= 3u && U > 0.f) ? o.ai / U : 0.f;

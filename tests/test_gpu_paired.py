@@ -77,6 +77,12 @@ def test_loss_pairs_full_size(dg, orc):
                                      threads=THREADS)
     rel = grad_rel_err(host(g1), host(g2), o1, o2, gen)
     assert rel.max() <= GRAD_RTOL, f"1M grads: max rel err {rel.max():.3e} at {int(rel.argmax())}"
+    # pairs whose small orientations took the FP64 definition's sign (degen
+    # bit 1) keep the definition's combinatorics: nx and xflags as the oracle's
+    rep = (host(degen) & 2) != 0
+    assert rep.sum() > 100, "the workload has near-degenerate pairs"
+    assert (host(nx)[rep] == ref["nx"][rep]).all()
+    assert (host(xf)[rep] == ref["xflags"][rep]).all()
 
 
 def test_finite_differences_1000(dg, orc):
