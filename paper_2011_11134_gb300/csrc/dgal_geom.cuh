@@ -10,10 +10,12 @@
 //     (P1 vertex -> end of its P1 edge piece, crossing -> continue on the
 //     polygon being entered), not from sorting, and starts at the smallest
 //     code, so nx / xflags come out in the canonical form directly;
-//   * the area is the shoelace sum grouped by edge: each clipped edge piece
-//     contributes cross(start, end), its endpoints being polygon vertices or
-//     crossing points a_i + t ea_i (t = S/D, D = cross(ea_i, eb_j)), so no
-//     vertex ordering is needed for it.
+//   * the area is the shoelace sum grouped by edge pieces, rewritten so that
+//     each inside vertex and each proper crossing adds one term
+//     (fwd_generic); no vertex ordering and no crossing point is needed for
+//     it;
+//   * for quadrilaterals without counts the walk is table-driven: one 64-bit
+//     table entry per edge gives that edge's block of codes.
 //   Near-degenerate pairs, and pairs whose sign pattern is not that of two
 //   convex polygons in general position, take the warp-cooperative robust
 //   path (candidate gathering and an angular sort; with refinement, FP64
@@ -249,6 +251,64 @@ template <int K, bool COUNTS> __device__ __forceinline__ uint64_t q_chain_bytes(
     }
 }
 
+// Table-driven walk for a pair of quadrilaterals without counts.  The block
+// of codes that P1 edge i contributes to the boundary walk (its start vertex
+// if inside P2, its entry crossing, its exit crossing, then the chain of P2
+// vertices inside P1 that follows the exit) depends only on
+//   idx = vI | rowE << 1 | rowX << 5 | in2 << 9
+// (vI: start vertex inside; rowE / rowX: the edge's entry / exit crossings,
+// bit j = P2 edge j; in2: P2 vertices inside P1).  Entry idx holds:
+//   bits 0..39  the block's code bytes with the edge number left out (vertex
+//               byte 0, crossing bytes 0x80 | j, chain bytes 0x40 | j);
+//   bits 40..42 the block's length; bit 43: byte 0 is the start vertex;
+//   bit 44      the pattern is impossible for two convex polygons in general
+//               position (two entries or exits on one edge, an entry after an
+//               inside start, a chain of every P2 vertex);
+//   bits 48..51 the P2 vertices of the chain (to check that no P2 vertex is
+//               emitted twice).
+// The kernel adds the edge number (i to the vertex byte, i << 3 to crossing
+// bytes) and appends the block at the running position.  Generated at
+// compile time; 64 KB, read through L1.
+struct WalkLut4 {
+    unsigned long long e[8192];
+};
+constexpr int lut_ctz4(uint32_t m) { return (m & 1u) ? 0 : (m & 2u) ? 1 : (m & 4u) ? 2 : 3; }
+constexpr int lut_popc4(uint32_t m) {
+    return (int)(m & 1u) + (int)((m >> 1) & 1u) + (int)((m >> 2) & 1u) + (int)((m >> 3) & 1u);
+}
+constexpr unsigned long long walk_entry4(uint32_t idx) {
+    const uint32_t vI = idx & 1u, rowE = (idx >> 1) & 15u, rowX = (idx >> 5) & 15u, in2 = (idx >> 9) & 15u;
+    bool bad = lut_popc4(rowE) > 1 || lut_popc4(rowX) > 1 || (vI && rowE);
+    unsigned long long bytes = 0;
+    uint32_t sz = vI, cm = 0;
+    if (rowE) {
+        bytes |= (unsigned long long)(0x80u | (uint32_t)lut_ctz4(rowE)) << (8 * sz);
+        ++sz;
+    }
+    if (rowX) {
+        const uint32_t jx = (uint32_t)lut_ctz4(rowX);
+        bytes |= (unsigned long long)(0x80u | jx) << (8 * sz);
+        ++sz;
+        uint32_t len = 0;
+        while (len < 4u && ((in2 >> ((jx + 1u + len) & 3u)) & 1u)) {
+            const uint32_t j = (jx + 1u + len) & 3u;
+            bytes |= (unsigned long long)(0x40u | j) << (8 * sz);
+            ++sz;
+            cm |= 1u << j;
+            ++len;
+        }
+        bad = bad || len >= 4u;
+    }
+    if (bad || sz > 5u) return 1ull << 44;
+    return bytes | ((unsigned long long)sz << 40) | ((unsigned long long)vI << 43) | ((unsigned long long)cm << 48);
+}
+constexpr WalkLut4 make_walk_lut4() {
+    WalkLut4 L{};
+    for (uint32_t i = 0; i < 8192u; ++i) L.e[i] = walk_entry4(i);
+    return L;
+}
+static __device__ const WalkLut4 g_walk_lut4 = make_walk_lut4();
+
 // Returns false when the pair must take the robust path: some orientation is
 // within the near-degenerate threshold (|orient| <= 1e-5 L^2), or the sign
 // pattern is not that of two convex polygons in general position.  While every
@@ -384,61 +444,59 @@ __device__ __forceinline__ bool fwd_generic(const Geo<K>& g, FwdOut<K>& o, const
     if (cnt == 0u) return true;
     if (cnt < 3u || cnt > (uint32_t)C) return false;
 
+    const uint32_t n1m = COUNTS ? (uint32_t)n1 : (uint32_t)K;
     const uint32_t n2m = COUNTS ? (uint32_t)n2 : (uint32_t)K;
-    // Area: the shoelace of the intersection grouped by edge, i.e. the sum over
-    // clipped edge pieces of cross(start, end).  A piece of P1 edge i runs from
-    // a_i (if inside) or its entry crossing to a_{i+1} (if inside) or its exit
-    // crossing; likewise for P2.  Each crossing point is computed once, as
-    // a_i + t ea_i with t = S/D, D = cross(ea_i, eb_j), and closes one P1 piece
-    // and one P2 piece, so rounding of t moves a vertex along the boundary and
-    // does not open a gap between the two pieces.
-    float sAx[K], sAy[K], eAx[K], eAy[K], sBx[K], sBy[K], eBx[K], eBy[K];
+    // Area: the shoelace of the intersection grouped by edge pieces.  A piece
+    // of P1 edge i runs between two points s, e of the line a_i + t ea_i, so
+    // cross(s, e) = cross(a_i, e) - cross(a_i, s); likewise a piece of P2 edge
+    // j with b_j.  Summing over pieces, every inside vertex a_i+1 adds
+    // cross(a_i, ea_i) (the end of a piece at t = 1), every inside b_j+1 adds
+    // cross(b_j, eb_j), and every crossing w of P1 edge i and P2 edge j adds
+    // s cross(a_i - b_j, w), s = +1 where P1 leaves P2 (a P1 piece ends and a
+    // P2 piece starts at w) and -1 where it enters.  With w = a_i + (S / D)
+    // ea_i, S = S(i,j), T = T(i,j) = cross(a_i - b_j, ea_i), D = cross(ea_i,
+    // eb_j), and s = sign(D) at a proper crossing, the crossing adds
+    //   (cross(a_i, b_j) D + S T) / |D|.
+    // The crossing point is one point for both of its pieces (no gap opens
+    // between a P1 and a P2 parameter), and since |S| < |D| and |T| < |D| at a
+    // proper crossing, the FP32 error of each term is of order u L^2 however
+    // nearly parallel the two edges are.  No crossing point is formed.
+    float twoA = 0.f;
+    {
+        uint32_t nxt1, nxt2; // bit v: vertex v + 1 (mod count) is inside
+        if constexpr (!COUNTS) {
+            nxt1 = (in1 >> 1) | ((in1 & 1u) << (K - 1));
+            nxt2 = (in2 >> 1) | ((in2 & 1u) << (K - 1));
+        } else {
+            nxt1 = (in1 >> 1) | ((in1 & 1u) << (n1m - 1u));
+            nxt2 = (in2 >> 1) | ((in2 & 1u) << (n2m - 1u));
+        }
 #pragma unroll
-    for (int v = 0; v < K; ++v) {
-        sAx[v] = g.ax[v];
-        sAy[v] = g.ay[v];
-        eAx[v] = g.ax[v] + g.eax[v];
-        eAy[v] = g.ay[v] + g.eay[v];
-        sBx[v] = g.bx[v];
-        sBy[v] = g.by[v];
-        eBx[v] = g.bx[v] + g.ebx[v];
-        eBy[v] = g.by[v] + g.eby[v];
+        for (int v = 0; v < K; ++v) {
+            const float c1 = g.ax[v] * g.eay[v] - g.ay[v] * g.eax[v];
+            const float c2 = g.bx[v] * g.eby[v] - g.by[v] * g.ebx[v];
+            twoA += ((nxt1 >> v) & 1u) ? c1 : 0.f;
+            twoA += ((nxt2 >> v) & 1u) ? c2 : 0.f;
+        }
     }
 #pragma unroll
     for (int i = 0; i < K; ++i) {
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             const int bit = i * K + j;
+            const float dx = g.ax[i] - g.bx[j], dy = g.ay[i] - g.by[j];
             float S;
             if constexpr (KEEP) {
                 S = Sv[bit];
             } else {
-                const float dx = g.ax[i] - g.bx[j], dy = g.ay[i] - g.by[j];
                 S = g.ebx[j] * dy - g.eby[j] * dx;
             }
+            const float T = g.eay[i] * dx - g.eax[i] * dy;
             const float D = g.eax[i] * g.eby[j] - g.eay[i] * g.ebx[j];
-            const float t = __fdividef(S, D);
-            const float wx = g.ax[i] + t * g.eax[i], wy = g.ay[i] + t * g.eay[i];
-            const bool xb = (X >> bit) & 1u;
-            const bool en = xb && ((entry1 >> bit) & 1u);
-            const bool ex = xb && !((entry1 >> bit) & 1u);
-            sAx[i] = en ? wx : sAx[i];
-            sAy[i] = en ? wy : sAy[i];
-            eBx[j] = en ? wx : eBx[j];
-            eBy[j] = en ? wy : eBy[j];
-            eAx[i] = ex ? wx : eAx[i];
-            eAy[i] = ex ? wy : eAy[i];
-            sBx[j] = ex ? wx : sBx[j];
-            sBy[j] = ex ? wy : sBy[j];
+            const float c = g.ax[i] * g.by[j] - g.ay[i] * g.bx[j];
+            const float r = ((X >> bit) & 1u) ? __fdividef(1.0f, fabsf(D)) : 0.f;
+            twoA = fmaf(fmaf(c, D, S * T), r, twoA);
         }
-    }
-    float twoA = 0.f;
-#pragma unroll
-    for (int v = 0; v < K; ++v) {
-        const bool hasA = ((in1 >> v) & 1u) || (((entry1 >> (v * K)) & kRow0) != 0);
-        const bool hasB = ((in2 >> v) & 1u) || (((exit1 >> v) & col0) != 0);
-        twoA += hasA ? sAx[v] * eAy[v] - sAy[v] * eAx[v] : 0.f;
-        twoA += hasB ? sBx[v] * eBy[v] - sBy[v] * eBx[v] : 0.f;
     }
 
     // Vertex order: walk P1's edges in order.  Edge i contributes its start
@@ -453,55 +511,87 @@ __device__ __forceinline__ bool fwd_generic(const Geo<K>& g, FwdOut<K>& o, const
         const int b = ctz_(X);
         start = 0x80u | ((uint32_t)(b / K) << 3) | (uint32_t)(b % K);
     }
-    const uint32_t jmin = (uint32_t)(__ffs(in2 | 0x100u) - 1);
-    const uint32_t fullq = (1u << n2m) - 1u;
     Sq seq = 0;
     uint32_t pos = 0, p0 = 0, qmask = 0;
     bool bad = false;
+    if constexpr (K == 4 && !COUNTS) {
 #pragma unroll
-    for (int i = 0; i < K; ++i) {
-        if (COUNTS && i >= n1) break;
-        if ((in1 >> i) & 1u) {
-            p0 = ((uint32_t)i == start) ? pos : p0;
-            seq |= (Sq)i << (8u * (pos & (C - 1)));
-            ++pos;
-        }
-        const M rowE = (entry1 >> (i * K)) & kRow0;
-        const M rowX = (exit1 >> (i * K)) & kRow0;
-        bad |= ((rowE & (rowE - 1)) | (rowX & (rowX - 1))) != 0;
-        if (rowE) {
-            const uint32_t c = 0x80u | ((uint32_t)i << 3) | (uint32_t)ctz_(rowE);
-            p0 = (c == start) ? pos : p0;
-            seq |= (Sq)c << (8u * (pos & (C - 1)));
-            ++pos;
-        }
-        if (rowX) {
-            const uint32_t jx = (uint32_t)ctz_(rowX);
-            const uint32_t c = 0x80u | ((uint32_t)i << 3) | jx;
-            p0 = (c == start) ? pos : p0;
-            seq |= (Sq)c << (8u * (pos & (C - 1)));
-            ++pos;
-            // P2 vertices jx+1, jx+2, ... (mod n2) while inside P1
-            const uint32_t sh = (jx + 1u >= n2m) ? jx + 1u - n2m : jx + 1u;
-            const uint32_t rot = sh ? (((in2 >> sh) | (in2 << (n2m - sh))) & fullq) : in2;
-            const uint32_t len = (uint32_t)(__ffs(~rot) - 1);
-            bad |= len >= n2m;
-            const uint32_t lm = (1u << len) - 1u;
-            const uint32_t cm = sh ? (((lm << sh) | (lm >> (n2m - sh))) & fullq) : lm;
-            bad |= (qmask & cm) != 0u;
+        for (int i = 0; i < K; ++i) {
+            const uint32_t idx = ((in1 >> i) & 1u) | (((uint32_t)(entry1 >> (i * K)) & 15u) << 1) |
+                                 (((uint32_t)(exit1 >> (i * K)) & 15u) << 5) | (in2 << 9);
+            const unsigned long long e = __ldg(&g_walk_lut4.e[idx]);
+            const uint32_t lo = (uint32_t)e, hi = (uint32_t)(e >> 32);
+            // edge number into the vertex byte (i) and the crossing bytes (i << 3)
+            const uint32_t mult = ((lo >> 4) & 0x080808u) | ((hi >> 11) & 1u);
+            const uint64_t blk = ((uint64_t)(hi & 0xFFu) << 32) | (uint64_t)(lo + (uint32_t)i * mult);
+            const uint32_t cm = (hi >> 16) & 15u;
+            bad |= (((hi >> 12) & 1u) | (qmask & cm)) != 0u;
             qmask |= cm;
-            if ((start >> 6) == 1u && ((cm >> jmin) & 1u)) p0 = pos + ((jmin + n2m - sh) % n2m);
-            if (len) seq |= (Sq)q_chain_bytes<K, COUNTS>(sh, len, n2m) << (8u * (pos & (C - 1)));
-            pos += len;
+            seq |= (Sq)blk << (8u * (pos & 7u));
+            pos += (hi >> 8) & 7u;
         }
-    }
-    if (X == 0 && in1 == 0) {
-        // P2 inside P1: the intersection is P2
-        bad |= in2 != fullq;
-        seq = (Sq)q_chain_bytes<K, COUNTS>(0u, n2m, n2m);
-        pos = n2m;
-        qmask = in2;
-        p0 = 0;
+        if (X == 0 && in1 == 0) {
+            // P2 inside P1: the intersection is P2
+            bad |= in2 != 15u;
+            seq = (Sq)0x43424140u;
+            pos = 4u;
+            qmask = in2;
+        }
+        // position of the smallest code: the zero byte of seq ^ start (codes
+        // are distinct; bytes past the walk are 0, which only matches start
+        // 0, P1 vertex 0, and that one is emitted first)
+        const uint64_t x = (uint64_t)seq ^ (0x0101010101010101ull * (uint64_t)start);
+        const uint64_t z = (x - 0x0101010101010101ull) & ~x & 0x8080808080808080ull;
+        bad |= z == 0ull;
+        p0 = ((uint32_t)__ffsll((long long)z) - 1u) >> 3;
+    } else {
+        const uint32_t jmin = (uint32_t)(__ffs(in2 | 0x100u) - 1);
+        const uint32_t fullq = (1u << n2m) - 1u;
+    #pragma unroll
+        for (int i = 0; i < K; ++i) {
+            if (COUNTS && i >= n1) break;
+            if ((in1 >> i) & 1u) {
+                p0 = ((uint32_t)i == start) ? pos : p0;
+                seq |= (Sq)i << (8u * (pos & (C - 1)));
+                ++pos;
+            }
+            const M rowE = (entry1 >> (i * K)) & kRow0;
+            const M rowX = (exit1 >> (i * K)) & kRow0;
+            bad |= ((rowE & (rowE - 1)) | (rowX & (rowX - 1))) != 0;
+            if (rowE) {
+                const uint32_t c = 0x80u | ((uint32_t)i << 3) | (uint32_t)ctz_(rowE);
+                p0 = (c == start) ? pos : p0;
+                seq |= (Sq)c << (8u * (pos & (C - 1)));
+                ++pos;
+            }
+            if (rowX) {
+                const uint32_t jx = (uint32_t)ctz_(rowX);
+                const uint32_t c = 0x80u | ((uint32_t)i << 3) | jx;
+                p0 = (c == start) ? pos : p0;
+                seq |= (Sq)c << (8u * (pos & (C - 1)));
+                ++pos;
+                // P2 vertices jx+1, jx+2, ... (mod n2) while inside P1
+                const uint32_t sh = (jx + 1u >= n2m) ? jx + 1u - n2m : jx + 1u;
+                const uint32_t rot = sh ? (((in2 >> sh) | (in2 << (n2m - sh))) & fullq) : in2;
+                const uint32_t len = (uint32_t)(__ffs(~rot) - 1);
+                bad |= len >= n2m;
+                const uint32_t lm = (1u << len) - 1u;
+                const uint32_t cm = sh ? (((lm << sh) | (lm >> (n2m - sh))) & fullq) : lm;
+                bad |= (qmask & cm) != 0u;
+                qmask |= cm;
+                if ((start >> 6) == 1u && ((cm >> jmin) & 1u)) p0 = pos + ((jmin + n2m - sh) % n2m);
+                if (len) seq |= (Sq)q_chain_bytes<K, COUNTS>(sh, len, n2m) << (8u * (pos & (C - 1)));
+                pos += len;
+            }
+        }
+        if (X == 0 && in1 == 0) {
+            // P2 inside P1: the intersection is P2
+            bad |= in2 != fullq;
+            seq = (Sq)q_chain_bytes<K, COUNTS>(0u, n2m, n2m);
+            pos = n2m;
+            qmask = in2;
+            p0 = 0;
+        }
     }
     if (bad || pos != cnt || qmask != in2) return false;
     if (p0) seq = (seq >> (8u * p0)) | (seq << (8u * (cnt - p0)));
