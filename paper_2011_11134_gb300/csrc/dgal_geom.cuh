@@ -343,9 +343,11 @@ __device__ __forceinline__ bool fwd_generic(const Geo<K>& g, FwdOut<K>& o, const
     const float thr = kRouteRel * L * L;
 
     // Orientation values: S(i,j) = orient(b_j, b_j+1, a_i), T(i,j) =
-    // orient(a_i, a_i+1, b_j).  Kept for K = 4, recomputed for K = 8.
+    // orient(a_i, a_i+1, b_j).  For K = 4 the loop also forms each pair of
+    // edges' crossing term of the area (used below where (i, j) is a proper
+    // crossing); for K = 8 the terms are formed later.
     constexpr bool KEEP = (K <= 4);
-    float Sv[KEEP ? KK : 1];
+    float Av[KEEP ? KK : 1];
     M neg_s = 0, neg_t = 0;
     float minabs = __int_as_float(0x7f800000);
 #pragma unroll
@@ -355,7 +357,11 @@ __device__ __forceinline__ bool fwd_generic(const Geo<K>& g, FwdOut<K>& o, const
             const float dx = g.ax[i] - g.bx[j], dy = g.ay[i] - g.by[j];
             const float s = g.ebx[j] * dy - g.eby[j] * dx;
             const float t = g.eay[i] * dx - g.eax[i] * dy;
-            if constexpr (KEEP) Sv[i * K + j] = s;
+            if constexpr (KEEP) {
+                const float D = g.eax[i] * g.eby[j] - g.eay[i] * g.ebx[j];
+                const float c = g.ax[i] * g.by[j] - g.ay[i] * g.bx[j];
+                Av[i * K + j] = fmaf(c, D, s * t) * __fdividef(1.0f, fabsf(D));
+            }
             const bool valid = !COUNTS || (i < n1 && j < n2);
             minabs = fminf(minabs, valid ? fminf(fabsf(s), fabsf(t)) : __int_as_float(0x7f800000));
             neg_s |= (M)(__float_as_uint(s) >> 31) << (i * K + j);
@@ -382,8 +388,9 @@ __device__ __forceinline__ bool fwd_generic(const Geo<K>& g, FwdOut<K>& o, const
                 for (int j = 0; j < K; ++j) {
                     const bool valid = !COUNTS || (i < n1 && j < n2);
                     const float dx = g.ax[i] - g.bx[j], dy = g.ay[i] - g.by[j];
+                    const float sv = g.ebx[j] * dy - g.eby[j] * dx;
                     const float t = g.eay[i] * dx - g.eax[i] * dy;
-                    small |= (valid && !(fabsf(Sv[i * K + j]) > wide)) ? (1u << (i * K + j)) : 0u;
+                    small |= (valid && !(fabsf(sv) > wide)) ? (1u << (i * K + j)) : 0u;
                     small |= (valid && !(fabsf(t) > wide)) ? (1u << (16 + i * K + j)) : 0u;
                 }
             }
@@ -484,18 +491,17 @@ __device__ __forceinline__ bool fwd_generic(const Geo<K>& g, FwdOut<K>& o, const
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             const int bit = i * K + j;
-            const float dx = g.ax[i] - g.bx[j], dy = g.ay[i] - g.by[j];
-            float S;
             if constexpr (KEEP) {
-                S = Sv[bit];
+                twoA += ((X >> bit) & 1u) ? Av[bit] : 0.f;
             } else {
-                S = g.ebx[j] * dy - g.eby[j] * dx;
+                const float dx = g.ax[i] - g.bx[j], dy = g.ay[i] - g.by[j];
+                const float S = g.ebx[j] * dy - g.eby[j] * dx;
+                const float T = g.eay[i] * dx - g.eax[i] * dy;
+                const float D = g.eax[i] * g.eby[j] - g.eay[i] * g.ebx[j];
+                const float c = g.ax[i] * g.by[j] - g.ay[i] * g.bx[j];
+                const float r = ((X >> bit) & 1u) ? __fdividef(1.0f, fabsf(D)) : 0.f;
+                twoA = fmaf(fmaf(c, D, S * T), r, twoA);
             }
-            const float T = g.eay[i] * dx - g.eax[i] * dy;
-            const float D = g.eax[i] * g.eby[j] - g.eay[i] * g.ebx[j];
-            const float c = g.ax[i] * g.by[j] - g.ay[i] * g.bx[j];
-            const float r = ((X >> bit) & 1u) ? __fdividef(1.0f, fabsf(D)) : 0.f;
-            twoA = fmaf(fmaf(c, D, S * T), r, twoA);
         }
     }
 
@@ -1199,6 +1205,32 @@ __device__ __noinline__ uint32_t warp_bwd(const float* __restrict__ p1, const fl
 constexpr uint32_t kSlow = 0x80000000u;
 constexpr float kTinyArea = 1e-5f;
 
+// Decoding table for quadrilateral codes (K = 4): entry c is what code byte c
+// contributes to the masks of bwd_shape: bit v (P1 vertex v), bit 4 + v (P2
+// vertex v), bit 8 + 4i + j (crossing of P1 edge i with P2 edge j), bit 24 (a
+// code no quadrilateral pair can have).  0xFF (an unused slot) contributes
+// nothing.  Generated at compile time; 1 KB, read through L1.
+struct CodeLut4 {
+    uint32_t e[256];
+};
+constexpr uint32_t code_entry4(uint32_t c) {
+    if (c == 0xFFu) return 0u;
+    const uint32_t kind = c >> 6;
+    if (kind == 0u) return c < 4u ? (1u << c) : (1u << 24);
+    if (kind == 1u) return (c & 0x3Fu) < 4u ? (1u << (4u + (c & 0x3Fu))) : (1u << 24);
+    if (kind == 2u) {
+        const uint32_t i = (c >> 3) & 7u, j = c & 7u;
+        return (i < 4u && j < 4u) ? (1u << (8u + 4u * i + j)) : (1u << 24);
+    }
+    return 1u << 24;
+}
+constexpr CodeLut4 make_code_lut4() {
+    CodeLut4 L{};
+    for (uint32_t c = 0; c < 256u; ++c) L.e[c] = code_entry4(c);
+    return L;
+}
+static __device__ const CodeLut4 g_code_lut4 = make_code_lut4();
+
 template <int K, bool COUNTS, typename Adj>
 __device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, Adj& adj, uint32_t nx, const Codes<K>& codes,
                                               bool refine, float (&g1x)[K], float (&g1y)[K], float (&g2x)[K],
@@ -1219,15 +1251,41 @@ __device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, Adj& adj, uint32_
     // inside vertices and crossings named by the codes
     uint32_t in1 = 0, in2 = 0, other = 0;
     M X = 0;
+    if constexpr (K == 4) {
+        // slots past nx read as unused (0xFF); one table entry per slot
+        const uint64_t live = (nx >= 8u) ? ~0ull : ((1ull << (8u * nx)) - 1ull);
+        const uint64_t w = codes.w[0] | ~live;
+        const uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
+        uint32_t acc = 0;
 #pragma unroll
-    for (int k = 0; k < C; ++k) {
-        const uint32_t c = code_at<K>(codes, (uint32_t)k);
-        const bool live = (uint32_t)k < nx;
-        const uint32_t kind = c >> 6, lo = c & 7u, ci = (c >> 3) & 7u;
-        in1 |= (live && kind == 0u) ? (1u << (c & 0x1Fu)) : 0u;
-        in2 |= (live && kind == 1u) ? (1u << (c & 0x1Fu)) : 0u;
-        X |= (live && kind == 2u) ? ((M)1 << (ci * K + lo)) : (M)0;
-        other |= (live && (kind == 3u || (kind == 2u && (ci >= n1m || lo >= n2m)))) ? 1u : 0u;
+        for (int k = 0; k < 4; ++k) {
+            acc |= __ldg(&g_code_lut4.e[(lo >> (8 * k)) & 0xFFu]);
+            acc |= __ldg(&g_code_lut4.e[(hi >> (8 * k)) & 0xFFu]);
+        }
+        in1 = acc & 15u;
+        in2 = (acc >> 4) & 15u;
+        X = (M)((acc >> 8) & 0xFFFFu);
+        other = acc >> 24;
+        if constexpr (COUNTS) {
+            // crossings of padded edges
+            M valid = 0;
+#pragma unroll
+            for (int i = 0; i < K; ++i)
+#pragma unroll
+                for (int j = 0; j < K; ++j) valid |= (i < n1 && j < n2) ? ((M)1 << (i * K + j)) : (M)0;
+            other |= (X & ~valid) ? 1u : 0u;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            const uint32_t c = code_at<K>(codes, (uint32_t)k);
+            const bool live = (uint32_t)k < nx;
+            const uint32_t kind = c >> 6, lo = c & 7u, ci = (c >> 3) & 7u;
+            in1 |= (live && kind == 0u) ? (1u << (c & 0x1Fu)) : 0u;
+            in2 |= (live && kind == 1u) ? (1u << (c & 0x1Fu)) : 0u;
+            X |= (live && kind == 2u) ? ((M)1 << (ci * K + lo)) : (M)0;
+            other |= (live && (kind == 3u || (kind == 2u && (ci >= n1m || lo >= n2m)))) ? 1u : 0u;
+        }
     }
     if (other || (in1 >> n1m) || (in2 >> n2m)) return kDevBadFlags;
     // edge piece counts must match the inside vertices: no crossing between

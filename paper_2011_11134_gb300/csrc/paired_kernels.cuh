@@ -127,8 +127,17 @@ __device__ __forceinline__ void put_fwd(const FwdOut<K>& o, int64_t k, float w, 
     if (degen) degen[k] = (uint8_t)o.degen;
 }
 
+// Minimum resident blocks per SM of the K = 4 paired kernels (a register
+// cap).  Both are issue-bound at 14-17 resident warps; 6 blocks (24 warps, 80
+// registers, a few spilled values) measured fastest on the 1M-pair step
+// (forward 44.1 us, backward 49.1 us, against 44.6 / 51.4 at 5 blocks).  The
+// backward that recomputes the clip carries the forward's code as well and
+// keeps 4 blocks (128 registers).
+constexpr int kFwdMinBlocks = 6;
+constexpr int kBwdMinBlocks = 6;
+
 template <int K, bool COUNTS, bool SAVE, bool LOSS, bool Z3>
-__global__ void __launch_bounds__(kPairThreads)
+__global__ void __launch_bounds__(kPairThreads, kFwdMinBlocks)
 k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
              const uint8_t* __restrict__ c2, int64_t n, float* __restrict__ iou, uint8_t* __restrict__ nx,
              uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status,
@@ -201,7 +210,7 @@ k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
 }
 
 template <int K, bool COUNTS, bool RECOMPUTE, bool LOSS, bool Z3>
-__global__ void __launch_bounds__(kPairThreads)
+__global__ void __launch_bounds__(kPairThreads, RECOMPUTE ? 4 : kBwdMinBlocks)
 k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
              const uint8_t* __restrict__ c2, int64_t n, const float* __restrict__ grad,
              const uint8_t* __restrict__ nxs, const uint8_t* __restrict__ xflags, float* __restrict__ g1,
