@@ -59,6 +59,10 @@ def _load():
             lib.oracle_iou_backward_paired.restype = ctypes.c_int
             lib.oracle_area_backward_paired.argtypes = [ctypes.c_int64, ctypes.c_int] + [P] * 11
             lib.oracle_area_backward_paired.restype = ctypes.c_int
+            lib.oracle_intersect_paired.argtypes = [ctypes.c_int64, ctypes.c_int, P, P, P, P, P, P, P]
+            lib.oracle_intersect_paired.restype = ctypes.c_int
+            lib.oracle_area.argtypes = [ctypes.c_int64, ctypes.c_int, P, P, P]
+            lib.oracle_area.restype = ctypes.c_int
             lib.oracle_iou_pairwise.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, P, P, P, P, P, P]
             lib.oracle_iou_pairwise.restype = ctypes.c_int
             lib.oracle_iou_pair_f64.argtypes = [ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int, P, P, P, P]
@@ -113,6 +117,97 @@ def iou_paired(p1, p2, c1=None, c2=None, threads: int = 1):
     _run_parallel(run, _chunks(n, threads))
     out["status"] = status[0]
     return out
+
+
+def intersect_paired(p1, p2, c1=None, c2=None, threads: int = 1):
+    """The intersection polygon of each pair (paper Sec. II-B `intersect`).
+
+    Returns dict(verts=float64[n, 2K, 2] in xflags order, unused slots 0,
+    nx=uint8[n], xflags=uint8[n, 2K], status=int)."""
+    lib = _load()
+    p1, p2, c1, c2 = _f32(p1), _f32(p2), _u8(c1), _u8(c2)
+    n, K = p1.shape[0], p1.shape[1]
+    out = dict(verts=np.zeros((n, 2 * K, 2), np.float64), nx=np.zeros(n, np.uint8),
+               xflags=np.full((n, 2 * K), 0xFF, np.uint8))
+    status = [0]
+
+    def run(rng):
+        s, e = rng
+        st = lib.oracle_intersect_paired(
+            e - s, K, _ptr(p1[s:e]), _ptr(None if c1 is None else c1[s:e]), _ptr(p2[s:e]),
+            _ptr(None if c2 is None else c2[s:e]), _ptr(out["verts"][s:e]), _ptr(out["nx"][s:e]),
+            _ptr(out["xflags"][s:e]))
+        status[0] |= st
+
+    _run_parallel(run, _chunks(n, threads))
+    out["status"] = status[0]
+    return out
+
+
+def area(p, c=None):
+    """Shoelace area of each polygon [n, K, 2] (paper Sec. II-B `area`)."""
+    lib = _load()
+    p, c = _f32(p), _u8(c)
+    n, K = p.shape[0], p.shape[1]
+    out = np.zeros(n, np.float64)
+    lib.oracle_area(n, K, _ptr(p), _ptr(c), _ptr(out))
+    return out
+
+
+# ------------------------------------------------------------------ lines
+#
+# Lines (paper Sec. III, "Lines"): stored as the coefficients (a, b, c) of
+# a x + b y + c = 0 and defined from two points differentiably.  Plain
+# numpy in FP64; the gradients are the hand-derived adjoints of these
+# formulas.
+
+def line_from_points(p, q):
+    """Line through p and q ([n, 2] each): (a, b, c) = (p_y - q_y, q_x - p_x,
+    p_x q_y - q_x p_y), so that a x + b y + c = 0 on both points."""
+    p = np.asarray(p, np.float64)
+    q = np.asarray(q, np.float64)
+    return np.stack([p[:, 1] - q[:, 1], q[:, 0] - p[:, 0], p[:, 0] * q[:, 1] - q[:, 0] * p[:, 1]], 1)
+
+
+def line_from_points_backward(p, q, g):
+    """dL/dp, dL/dq from dL/d(a, b, c) = g [n, 3]."""
+    p = np.asarray(p, np.float64)
+    q = np.asarray(q, np.float64)
+    g = np.asarray(g, np.float64)
+    ga, gb, gc = g[:, 0], g[:, 1], g[:, 2]
+    gp = np.stack([-gb + gc * q[:, 1], ga - gc * q[:, 0]], 1)
+    gq = np.stack([gb - gc * p[:, 1], -ga + gc * p[:, 0]], 1)
+    return gp, gq
+
+
+def line_intersect(l1, l2):
+    """Intersection point of two lines ([n, 3] each): (X / W, Y / W) with
+    X = b1 c2 - b2 c1, Y = c1 a2 - c2 a1, W = a1 b2 - a2 b1 (W = 0: parallel,
+    non-finite result)."""
+    l1 = np.asarray(l1, np.float64)
+    l2 = np.asarray(l2, np.float64)
+    a1, b1, c1 = l1[:, 0], l1[:, 1], l1[:, 2]
+    a2, b2, c2 = l2[:, 0], l2[:, 1], l2[:, 2]
+    W = a1 * b2 - a2 * b1
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.stack([(b1 * c2 - b2 * c1) / W, (c1 * a2 - c2 * a1) / W], 1)
+
+
+def line_intersect_backward(l1, l2, g):
+    """dL/dl1, dL/dl2 from dL/d(x, y) = g [n, 2]."""
+    l1 = np.asarray(l1, np.float64)
+    l2 = np.asarray(l2, np.float64)
+    g = np.asarray(g, np.float64)
+    a1, b1, c1 = l1[:, 0], l1[:, 1], l1[:, 2]
+    a2, b2, c2 = l2[:, 0], l2[:, 1], l2[:, 2]
+    W = a1 * b2 - a2 * b1
+    x = (b1 * c2 - b2 * c1) / W
+    y = (c1 * a2 - c2 * a1) / W
+    gX, gY = g[:, 0] / W, g[:, 1] / W
+    gW = -(g[:, 0] * x + g[:, 1] * y) / W
+    gl1 = np.stack([-gY * c2 + gW * b2, gX * c2 - gW * a2, -gX * b2 + gY * a2], 1)
+    gl2 = np.stack([gY * c1 - gW * b1, -gX * c1 + gW * a1, gX * b1 - gY * a1], 1)
+    return gl1, gl2
 
 
 def iou_backward_paired(p1, p2, grad, nx, xflags, c1=None, c2=None, threads: int = 1):

@@ -64,11 +64,13 @@ typedef struct {
     double ang;
 } ocand;
 
-/* Per-pair forward result. */
+/* Per-pair forward result (w: the intersection polygon's vertices, in the
+ * order of code). */
 typedef struct {
     double iou, ai, a1, a2;
     int nx;
     uint8_t code[ORC_MAXC];
+    opt w[ORC_MAXC];
     int degen;
     int status;
 } ofwd;
@@ -212,13 +214,12 @@ static void forward_pair(const opt* P, int n1, const opt* Q, int n2, int K, ofwd
     int s0 = 0;
     for (int k = 1; k < m; ++k)
         if (cand[k].code < cand[s0].code) s0 = k;
-    opt w[ORC_MAXC];
     for (int k = 0; k < m; ++k) {
         out->code[k] = cand[(s0 + k) % m].code;
-        w[k] = cand[(s0 + k) % m].p;
+        out->w[k] = cand[(s0 + k) % m].p;
     }
     out->nx = m;
-    out->ai = shoelace(w, m);
+    out->ai = shoelace(out->w, m);
     double U = out->a1 + out->a2 - out->ai;
     out->iou = (U > 0.0) ? out->ai / U : 0.0;
 }
@@ -380,6 +381,61 @@ int oracle_iou_paired(int64_t n, int K, const float* p1, const uint8_t* c1, cons
         if (xflags) memcpy(xflags + k * 2 * K, f.code, (size_t)(2 * K));
         if (degen) degen[k] = (uint8_t)f.degen;
         if (areas) { areas[3 * k] = f.ai; areas[3 * k + 1] = f.a1; areas[3 * k + 2] = f.a2; }
+    }
+    return st;
+}
+
+/* Batch `intersect` (paper Sec. II-B: intersect(p1, p2, xflags) returns the
+ * intersection polygon with its vertex count): verts [n][2K][2] receives the
+ * vertices in the order of xflags (counter-clockwise from the smallest code),
+ * unused slots 0; nx, xflags as oracle_iou_paired.  Returns OR of status
+ * bits. */
+int oracle_intersect_paired(int64_t n, int K, const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2,
+                            double* verts, uint8_t* nx, uint8_t* xflags)
+{
+    if (K < 3 || K > ORC_MAXK) return -1;
+    int st = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        opt P[ORC_MAXK], Q[ORC_MAXK];
+        int n1 = count_of(c1, k, K), n2 = count_of(c2, k, K);
+        ofwd f;
+        memset(&f, 0, sizeof(f));
+        memset(f.code, 0xFF, sizeof(f.code));
+        if (n1 < 3 || n1 > K || n2 < 3 || n2 > K) {
+            f.status = ORC_ST_BAD_COUNT;
+        } else {
+            load_f32(p1 + k * 2 * K, n1, P);
+            load_f32(p2 + k * 2 * K, n2, Q);
+            forward_pair(P, n1, Q, n2, K, &f);
+        }
+        st |= f.status;
+        for (int v = 0; v < 2 * K; ++v) {
+            verts[(k * 2 * K + v) * 2] = v < f.nx ? f.w[v].x : 0.0;
+            verts[(k * 2 * K + v) * 2 + 1] = v < f.nx ? f.w[v].y : 0.0;
+        }
+        if (nx) nx[k] = (uint8_t)f.nx;
+        if (xflags) memcpy(xflags + k * 2 * K, f.code, (size_t)(2 * K));
+    }
+    return st;
+}
+
+/* Batch `area` (paper Sec. II-B listing: area(p) of a polygon): the shoelace
+ * area of each polygon [n][K][2] with its count (NULL: K); 0 for a count
+ * outside [3, K]. */
+int oracle_area(int64_t n, int K, const float* p, const uint8_t* c, double* area)
+{
+    if (K < 3 || K > ORC_MAXK) return -1;
+    int st = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        opt P[ORC_MAXK];
+        int m = count_of(c, k, K);
+        if (m < 3 || m > K) {
+            area[k] = 0.0;
+            st |= ORC_ST_BAD_COUNT;
+            continue;
+        }
+        load_f32(p + k * 2 * K, m, P);
+        area[k] = shoelace(P, m);
     }
     return st;
 }
