@@ -161,6 +161,48 @@ dgal_status dgal_iou3d_loss(const float* p1, const uint8_t* c1, const float* z1,
                             void* workspace, size_t ws_bytes, uint32_t flags, void* stream);
 
 /*
+ * The intersection polygon of each pair (paper Sec. II-B, `intersect`, with
+ * `area` of the result): verts float [n][2K][2] receives the nx[k]
+ * intersection vertices in xflags order (counter-clockwise from the smallest
+ * code; input vertices copied, crossings a + t (b - a) of the P1 edge, in
+ * FP32), unused slots 0; area float [n] receives their shoelace area;
+ * nx uint8 [n] and xflags uint8 [n][2K] as dgal_iou_paired (all required).
+ * verts 16-byte aligned.  Runs the paired forward, then one vertex pass.
+ */
+dgal_status dgal_intersect_paired(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                                  int K, float* verts, float* area, uint8_t* nx, uint8_t* xflags, uint32_t flags,
+                                  void* stream);
+
+/*
+ * Area of each polygon (paper Sec. II-B, `area`): area[k] = shoelace area of
+ * p[k] (float [n][K][2], CCW, counts c uint8 [n] or NULL); 0 and
+ * DGAL_DEV_BAD_COUNT for a count outside [3, K].
+ */
+dgal_status dgal_area(const float* p, const uint8_t* c, int64_t n, int K, float* area, void* stream);
+
+/*
+ * Lines (paper Sec. III, "Lines": stored as the coefficients of their
+ * equation, defined by two points in a differentiable manner).  A line is
+ * float [3] = (a, b, c) with a x + b y + c = 0; points are float [2]
+ * (8-byte aligned arrays).
+ *   dgal_line_from_points: line[k] through p[k], q[k]:
+ *     (a, b, c) = (p_y - q_y, q_x - p_x, p_x q_y - q_x p_y).
+ *   dgal_line_from_points_backward: dL/d(a, b, c) [n][3] -> dL/dp, dL/dq
+ *     [n][2] (overwritten).
+ *   dgal_line_intersect: point[k] = (X / W, Y / W), X = b1 c2 - b2 c1,
+ *     Y = c1 a2 - c2 a1, W = a1 b2 - a2 b1; parallel lines (W = 0) give
+ *     non-finite coordinates.
+ *   dgal_line_intersect_backward: dL/d(x, y) [n][2] -> dL/dl1, dL/dl2
+ *     [n][3] (overwritten).
+ */
+dgal_status dgal_line_from_points(const float* p, const float* q, int64_t n, float* line, void* stream);
+dgal_status dgal_line_from_points_backward(const float* p, const float* q, int64_t n, const float* grad_line,
+                                           float* grad_p, float* grad_q, void* stream);
+dgal_status dgal_line_intersect(const float* l1, const float* l2, int64_t n, float* point, void* stream);
+dgal_status dgal_line_intersect_backward(const float* l1, const float* l2, int64_t n, const float* grad_point,
+                                         float* grad_l1, float* grad_l2, void* stream);
+
+/*
  * Pairwise IoU matrix (the `iou` operation over all N x M pairs):
  *   iou[i*M + j] = IoU(a[i], b[j]), nx[i*M + j] likewise (nx may be NULL).
  * a: float [N][K][2], b: float [M][K][2]; ca, cb counts or NULL.

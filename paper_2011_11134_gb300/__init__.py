@@ -8,6 +8,9 @@ Python binding of libdgal's C ABI (include/dgal.h), with the same call names:
     dgal_iou_pairwise_batched  ragged scenes in one persistent launch
     dgal_iou_pairwise_per_scene  the plain one-launch-per-scene form
     dgal_nms_rotated           greedy rotated NMS on the pairwise IoU
+    dgal_intersect_paired      paper Sec. II-B `intersect`: the intersection polygon
+    dgal_area                  paper Sec. II-B `area` of single polygons
+    dgal_line_*                paper Sec. III lines: from two points, intersection (+ backward)
     BatchedGraph               the ragged batch captured in a CUDA graph
     dgal_autotune              launch-shape tuner for the ragged batch
     dgal_get_device_status     device-side error bits
@@ -38,6 +41,9 @@ __all__ = [
     "DGAL_FP64_REFINE", "DGAL_PLAIN", "DGAL_DEV_BAD_COUNT", "DGAL_DEV_OVERFLOW", "DGAL_DEV_BAD_FLAGS",
     "DGAL_DEV_BAD_OFFSETS", "DgalError", "dgal_iou3d_paired", "dgal_iou3d_backward", "dgal_iou3d_loss", "IoU3D",
     "iou3d", "IoU3DLoss", "iou3d_loss", "dgal_nms_rotated", "dgal_nms_workspace_bytes",
+    "dgal_intersect_paired", "dgal_area", "dgal_line_from_points", "dgal_line_from_points_backward",
+    "dgal_line_intersect", "dgal_line_intersect_backward", "LineFromPoints", "LineIntersect",
+    "line_from_points", "line_intersect",
 ]
 
 
@@ -234,6 +240,119 @@ def dgal_iou_pairwise(a, b, ca=None, cb=None, with_nx=True, flags=DGAL_FP64_REFI
     _lib.call("dgal_iou_pairwise", _lib.ptr(a), _lib.ptr(ca), N, _lib.ptr(b), _lib.ptr(cb), M, K, _lib.ptr(iou),
               _lib.ptr(nx), flags, _lib.stream_ptr(stream))
     return iou, nx
+
+
+def dgal_intersect_paired(p1, p2, c1=None, c2=None, flags=DGAL_FP64_REFINE, stream=None):
+    """The intersection polygon of each pair (paper Sec. II-B `intersect`):
+    returns (verts [n, 2K, 2] in xflags order, unused slots 0, area [n],
+    nx [n], xflags [n, 2K])."""
+    _poly(p1, "p1")
+    _poly(p2, "p2")
+    if p1.shape != p2.shape or p1.device != p2.device:
+        raise ValueError("p1 and p2 must have the same shape and device")
+    n, K = p1.shape[0], p1.shape[1]
+    c1 = _counts(c1, n, "c1", p1.device)
+    c2 = _counts(c2, n, "c2", p1.device)
+    verts = torch.empty((n, 2 * K, 2), device=p1.device, dtype=torch.float32)
+    area = torch.empty(n, device=p1.device, dtype=torch.float32)
+    nx = torch.empty(n, device=p1.device, dtype=torch.uint8)
+    xflags = torch.empty((n, 2 * K), device=p1.device, dtype=torch.uint8)
+    _lib.call("dgal_intersect_paired", _lib.ptr(p1), _lib.ptr(c1), _lib.ptr(p2), _lib.ptr(c2), n, K,
+              _lib.ptr(verts), _lib.ptr(area), _lib.ptr(nx), _lib.ptr(xflags), flags, _lib.stream_ptr(stream))
+    return verts, area, nx, xflags
+
+
+def dgal_area(p, c=None, stream=None):
+    """Shoelace area of each polygon [n, K, 2] (paper Sec. II-B `area`)."""
+    _poly(p, "p")
+    n, K = p.shape[0], p.shape[1]
+    c = _counts(c, n, "c", p.device)
+    area = torch.empty(n, device=p.device, dtype=torch.float32)
+    _lib.call("dgal_area", _lib.ptr(p), _lib.ptr(c), n, K, _lib.ptr(area), _lib.stream_ptr(stream))
+    return area
+
+
+def _pts(t, name, width):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or t.dim() != 2 \
+            or t.shape[1] != width or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA float32 tensor [n, {width}]")
+    return t
+
+
+def dgal_line_from_points(p, q, stream=None):
+    """Lines through p[k], q[k] ([n, 2]): (a, b, c) [n, 3] with a x + b y + c = 0."""
+    _pts(p, "p", 2)
+    _pts(q, "q", 2)
+    line = torch.empty((p.shape[0], 3), device=p.device, dtype=torch.float32)
+    _lib.call("dgal_line_from_points", _lib.ptr(p), _lib.ptr(q), p.shape[0], _lib.ptr(line), _lib.stream_ptr(stream))
+    return line
+
+
+def dgal_line_from_points_backward(p, q, grad_line, stream=None):
+    _pts(p, "p", 2)
+    _pts(q, "q", 2)
+    _pts(grad_line, "grad_line", 3)
+    gp, gq = torch.empty_like(p), torch.empty_like(q)
+    _lib.call("dgal_line_from_points_backward", _lib.ptr(p), _lib.ptr(q), p.shape[0], _lib.ptr(grad_line),
+              _lib.ptr(gp), _lib.ptr(gq), _lib.stream_ptr(stream))
+    return gp, gq
+
+
+def dgal_line_intersect(l1, l2, stream=None):
+    """Intersection points [n, 2] of lines l1[k], l2[k] ([n, 3] each)."""
+    _pts(l1, "l1", 3)
+    _pts(l2, "l2", 3)
+    pt = torch.empty((l1.shape[0], 2), device=l1.device, dtype=torch.float32)
+    _lib.call("dgal_line_intersect", _lib.ptr(l1), _lib.ptr(l2), l1.shape[0], _lib.ptr(pt), _lib.stream_ptr(stream))
+    return pt
+
+
+def dgal_line_intersect_backward(l1, l2, grad_point, stream=None):
+    _pts(l1, "l1", 3)
+    _pts(l2, "l2", 3)
+    _pts(grad_point, "grad_point", 2)
+    g1, g2 = torch.empty_like(l1), torch.empty_like(l2)
+    _lib.call("dgal_line_intersect_backward", _lib.ptr(l1), _lib.ptr(l2), l1.shape[0], _lib.ptr(grad_point),
+              _lib.ptr(g1), _lib.ptr(g2), _lib.stream_ptr(stream))
+    return g1, g2
+
+
+class LineFromPoints(torch.autograd.Function):
+    """Differentiable line through two points (paper Sec. III, "Lines")."""
+
+    @staticmethod
+    def forward(ctx, p, q):
+        p, q = p.contiguous(), q.contiguous()
+        ctx.save_for_backward(p, q)
+        return dgal_line_from_points(p, q)
+
+    @staticmethod
+    def backward(ctx, g):
+        p, q = ctx.saved_tensors
+        return dgal_line_from_points_backward(p, q, g.contiguous())
+
+
+class LineIntersect(torch.autograd.Function):
+    """Differentiable intersection point of two lines."""
+
+    @staticmethod
+    def forward(ctx, l1, l2):
+        l1, l2 = l1.contiguous(), l2.contiguous()
+        ctx.save_for_backward(l1, l2)
+        return dgal_line_intersect(l1, l2)
+
+    @staticmethod
+    def backward(ctx, g):
+        l1, l2 = ctx.saved_tensors
+        return dgal_line_intersect_backward(l1, l2, g.contiguous())
+
+
+def line_from_points(p, q):
+    return LineFromPoints.apply(p, q)
+
+
+def line_intersect(l1, l2):
+    return LineIntersect.apply(l1, l2)
 
 
 def dgal_nms_workspace_bytes(N, K=4):

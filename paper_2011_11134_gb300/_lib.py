@@ -49,6 +49,12 @@ _SIG = {
                                        ctypes.c_size_t, _U32]),
     "dgal_nms_workspace_bytes": (ctypes.c_size_t, [_I64, _I]),
     "dgal_nms_rotated": (_I, [_P, _P, _P, _I64, _I, ctypes.c_float, _P, _P, _P, ctypes.c_size_t, _U32, _P]),
+    "dgal_intersect_paired": (_I, [_P, _P, _P, _P, _I64, _I, _P, _P, _P, _P, _U32, _P]),
+    "dgal_area": (_I, [_P, _P, _I64, _I, _P, _P]),
+    "dgal_line_from_points": (_I, [_P, _P, _I64, _P, _P]),
+    "dgal_line_from_points_backward": (_I, [_P, _P, _I64, _P, _P, _P, _P]),
+    "dgal_line_intersect": (_I, [_P, _P, _I64, _P, _P]),
+    "dgal_line_intersect_backward": (_I, [_P, _P, _I64, _P, _P, _P, _P]),
     "dgal_graph_launch": (_I, [_P, _P]),
     "dgal_graph_destroy": (_I, [_P]),
     "dgal_autotune": (_I, [_I, _I, ctypes.c_char_p]),
