@@ -10,13 +10,12 @@
 // Forward (paper Sec. II-B `iou`): lane r computes row r of the orientation
 // tables, S(r,j) = orient(b_j, b_j+1, a_r) and T(r,j) = orient(a_r, a_r+1, b_j);
 // the rows are OR-combined into 64-bit sign masks, after which every lane
-// knows the inside vertices and the crossings (as in fwd_generic).  Lane r
-// builds the clipped pieces of P1 edge r and P2 edge r (endpoints are
-// vertices or crossing points; each crossing point comes from cross_point(),
-// whose roundings are spelled out so both lanes that use it get the same
-// bits), and its chunk of the counter-clockwise vertex order: vertex r if
-// inside, the entry crossing of edge r, its exit crossing and the chain of P2
-// vertices that follows an exit.  An exclusive scan of chunk lengths places
+// knows the inside vertices and the crossings (as in fwd_generic).  The area
+// is fwd_generic's select-free sum: lane r adds P1 edge r's vertex term and
+// its row of crossing terms, a group sum adds them up.  Lane r also builds
+// its chunk of the counter-clockwise vertex order: vertex r if inside, the
+// entry crossing of edge r, its exit crossing and the chain of P2 vertices
+// that follows an exit.  An exclusive scan of chunk lengths places
 // the chunks; the cycle is rotated to its smallest code.
 //
 // Backward (paper Sec. II-B `iou_grad`): the shape derivative over the
@@ -59,18 +58,6 @@ __device__ __forceinline__ float gmin(unsigned m, float v) {
 #pragma unroll
     for (int off = 1; off < G; off <<= 1) v = fminf(v, __shfl_xor_sync(m, v, off, G));
     return v;
-}
-
-// Crossing point of P1 edge (a, a + ea) with P2 edge (b, b + eb) as a + t ea,
-// t = cross(eb, a - b) / cross(ea, eb), every rounding explicit.
-__device__ __forceinline__ void cross_point(float ax, float ay, float eax, float eay, float bx, float by, float ebx,
-                                            float eby, float& wx, float& wy) {
-    const float dx = __fsub_rn(ax, bx), dy = __fsub_rn(ay, by);
-    const float S = __fsub_rn(__fmul_rn(ebx, dy), __fmul_rn(eby, dx));
-    const float D = __fsub_rn(__fmul_rn(eax, eby), __fmul_rn(eay, ebx));
-    const float t = __fdiv_rn(S, D);
-    wx = __fmaf_rn(t, eax, ax);
-    wy = __fmaf_rn(t, eay, ay);
 }
 
 __device__ __forceinline__ float sel8(const float (&v)[8], uint32_t i) {
@@ -144,9 +131,10 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
     Lr = gmax(gm, Lr);
     const float thr = kRouteRel * Lr * Lr;
 
-    // row r of S and T
+    // row r of S and T, and the row's crossing terms of the area (see below)
     uint32_t sneg = 0, tneg = 0;
     float mn = __int_as_float(0x7f800000);
+    float term[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const float dx = L.ax - L.bx[j], dy = L.ay - L.by[j];
@@ -155,6 +143,9 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
         mn = fminf(mn, (liveA && j < n2) ? fminf(fabsf(s), fabsf(t)) : __int_as_float(0x7f800000));
         sneg |= (__float_as_uint(s) >> 31) << j;
         tneg |= (__float_as_uint(t) >> 31) << j;
+        const float D = L.eax * L.eby[j] - L.eay * L.ebx[j];
+        const float c = L.ax * L.by[j] - L.ay * L.bx[j];
+        term[j] = fmaf(c, D, s * t) * __fdividef(1.0f, fabsf(D));
     }
     mn = gmin(gm, mn);
     if (!(Lr > 0.f) || !(mn > thr)) return false;
@@ -190,41 +181,34 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
     if (cnt == 0u) return true;
     if (cnt < 3u || cnt > 16u) return false;
 
-    // clipped piece of P1 edge r: from a_r or its entry crossing to a_{r+1} or
-    // its exit crossing
+    // Area (the select-free shoelace of fwd_generic): every inside vertex
+    // a_i+1 adds cross(a_i, ea_i), every inside b_j+1 adds cross(b_j, eb_j),
+    // and every proper crossing (i, j) adds (cross(a_i, b_j) D + S T) / |D|,
+    // with one crossing point shared by its two pieces and an FP32 error of
+    // order u L^2 at any crossing angle.  Lane r adds P1 edge r's vertex term
+    // and its row of crossing terms; every lane forms the P2 sums itself.
     const uint32_t rowE = liveA ? (uint32_t)((entry1 >> (8 * r)) & 0xFF) : 0u;
     const uint32_t rowX = liveA ? (uint32_t)((exit1 >> (8 * r)) & 0xFF) : 0u;
     bool bad = (rowE & (rowE - 1)) != 0u || (rowX & (rowX - 1)) != 0u;
-    float sAx = L.ax, sAy = L.ay, eAx = L.ax + L.eax, eAy = L.ay + L.eay;
-    if (rowE) {
-        const uint32_t j = (uint32_t)(__ffs(rowE) - 1);
-        cross_point(L.ax, L.ay, L.eax, L.eay, sel8(L.bx, j), sel8(L.by, j), sel8(L.ebx, j), sel8(L.eby, j), sAx, sAy);
-    }
-    if (rowX) {
-        const uint32_t j = (uint32_t)(__ffs(rowX) - 1);
-        cross_point(L.ax, L.ay, L.eax, L.eay, sel8(L.bx, j), sel8(L.by, j), sel8(L.ebx, j), sel8(L.eby, j), eAx, eAy);
-    }
-    const bool hasA = liveA && (((in1 >> r) & 1u) || rowE);
-    // clipped piece of P2 edge r: from b_r or the crossing where P1 leaves
-    // P2 on it, to b_{r+1} or the crossing where P1 enters P2 on it; those
-    // crossings are computed from the P1 edge's data, fetched from its lane
     const uint64_t cX = liveB ? ((exit1 >> r) & col0) : 0ull, cE = liveB ? ((entry1 >> r) & col0) : 0ull;
     bad |= (cX & (cX - 1)) != 0ull || (cE & (cE - 1)) != 0ull;
-    const int ix = cX ? (__ffsll((long long)cX) - 1) / 8 : 0;
-    const int ie = cE ? (__ffsll((long long)cE) - 1) / 8 : 0;
-    const float xax = __shfl_sync(gm, L.ax, base + ix), xay = __shfl_sync(gm, L.ay, base + ix);
-    const float xeax = __shfl_sync(gm, L.eax, base + ix), xeay = __shfl_sync(gm, L.eay, base + ix);
-    const float nax = __shfl_sync(gm, L.ax, base + ie), nay = __shfl_sync(gm, L.ay, base + ie);
-    const float neax = __shfl_sync(gm, L.eax, base + ie), neay = __shfl_sync(gm, L.eay, base + ie);
-    const float bxr = sel8(L.bx, (uint32_t)r), byr = sel8(L.by, (uint32_t)r);
-    const float ebxr = sel8(L.ebx, (uint32_t)r), ebyr = sel8(L.eby, (uint32_t)r);
-    float sBx = bxr, sBy = byr, eBx = bxr + ebxr, eBy = byr + ebyr;
-    if (cX) cross_point(xax, xay, xeax, xeay, bxr, byr, ebxr, ebyr, sBx, sBy);
-    if (cE) cross_point(nax, nay, neax, neay, bxr, byr, ebxr, ebyr, eBx, eBy);
-    const bool hasB = liveB && (((in2 >> r) & 1u) || cX);
-    const float twoA = gsum(gm, (hasA ? sAx * eAy - sAy * eAx : 0.f) + (hasB ? sBx * eBy - sBy * eBx : 0.f));
-    const float a1 = 0.5f * gsum(gm, liveA ? L.ax * L.eay - L.ay * L.eax : 0.f);
-    const float a2 = 0.5f * gsum(gm, liveB ? bxr * ebyr - byr * ebxr : 0.f);
+    const uint32_t nxt1 = (in1 >> 1) | ((in1 & 1u) << (n1 - 1));
+    const uint32_t nxt2 = (in2 >> 1) | ((in2 & 1u) << (n2 - 1));
+    const float c1r = L.ax * L.eay - L.ay * L.eax;
+    const uint32_t xrow = liveA ? (uint32_t)((X >> (8 * r)) & 0xFF) : 0u;
+    float lane2 = ((nxt1 >> r) & 1u && liveA) ? c1r : 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) lane2 += ((xrow >> j) & 1u) ? term[j] : 0.f;
+    float twoB = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float c2 = L.bx[j] * L.eby[j] - L.by[j] * L.ebx[j];
+        twoB += ((nxt2 >> j) & 1u) ? c2 : 0.f;
+        s2 += (j < n2) ? c2 : 0.f;
+    }
+    const float twoA = gsum(gm, lane2) + twoB;
+    const float a1 = 0.5f * gsum(gm, liveA ? c1r : 0.f);
+    const float a2 = 0.5f * s2;
     const float ai = 0.5f * twoA;
     const float U = a1 + a2 - ai;
 
