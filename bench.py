@@ -264,7 +264,18 @@ def fused_workload(args):
     ws = torch.empty(dg.dgal_iou_loss_workspace_bytes(n), device=dev, dtype=torch.uint8)
     out = (torch.empty(1, device=dev), torch.empty_like(p1), torch.empty_like(p2), None)
     flush = torch.empty(256 << 20, device=dev, dtype=torch.uint8)
-    run = lambda: dg.dgal_iou_loss(p1, p2, None, 1.0 / n, workspace=ws, out=out)
+    L = dg._lib
+    lib = L.lib()
+    sp = L.stream_ptr(stream)
+    # direct C-ABI calls with prepared pointers: the timed region holds device
+    # work, not Python argument checks
+    loss_args = (L.ptr(p1), None, L.ptr(p2), None, n, 4, None, 1.0 / n, L.ptr(out[0]), None, L.ptr(out[1]),
+                 L.ptr(out[2]), L.ptr(ws), ws.numel(), dg.DGAL_FP64_REFINE, sp)
+
+    def run():
+        st = lib.dgal_iou_loss(*loss_args)
+        assert st == 0, dg.dgal_last_error()
+
     for _ in range(args.warmup):
         run()
     torch.cuda.synchronize(dev)
@@ -285,10 +296,18 @@ def fused_workload(args):
     ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
     # the same loss through the separate forward and backward calls
     g_iou = torch.full((n,), -1.0 / n, device=dev)
+    iv = torch.empty(n, device=dev)
+    nx_ = torch.empty(n, device=dev, dtype=torch.uint8)
+    xf_ = torch.empty((n, 8), device=dev, dtype=torch.uint8)
+    g1_, g2_ = torch.empty_like(p1), torch.empty_like(p2)
+    fwd_args = (L.ptr(p1), None, L.ptr(p2), None, n, 4, L.ptr(iv), L.ptr(nx_), L.ptr(xf_), None, dg.DGAL_FP64_REFINE,
+                sp)
+    bwd_args = (L.ptr(p1), None, L.ptr(p2), None, n, 4, L.ptr(g_iou), L.ptr(nx_), L.ptr(xf_), L.ptr(g1_), L.ptr(g2_),
+                dg.DGAL_FP64_REFINE, sp)
 
     def unfused():
-        iv, nx, xf, _ = dg.dgal_iou_paired(p1, p2)
-        dg.dgal_iou_backward(p1, p2, g_iou, nx, xf)
+        assert lib.dgal_iou_paired(*fwd_args) == 0
+        assert lib.dgal_iou_backward(*bwd_args) == 0
         return (1.0 - iv).sum() / n
 
     for _ in range(args.warmup):
@@ -317,7 +336,7 @@ def fused_workload(args):
                      "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "alg_bytes_per_pair": alg},
         "unfused": {"value": n / (ms_unfused * 1e-3), "unit": UNIT, "ms_per_step": ms_unfused,
                     "what": "dgal_iou_paired + torch sum + dgal_iou_backward"},
-        "gpu_launches": 4 * args.steps, "clocks": clocks,  # forward, fix pass, backward, partial sum
+        "gpu_launches": 3 * args.steps, "clocks": clocks,  # forward, backward, partial sum
     }
     print(json.dumps(line), flush=True)
 
@@ -339,14 +358,26 @@ def iou3d_workload(args):
     p1, p2, z1, z2 = (torch.from_numpy(d[k]).to(dev) for k in ("p1", "p2", "z1", "z2"))
     grad = torch.ones(n, device=dev)
     flush = torch.empty(256 << 20, device=dev, dtype=torch.uint8)
-    state = {}
+    iou3 = torch.empty(n, device=dev)
+    nx3 = torch.empty(n, device=dev, dtype=torch.uint8)
+    xf3 = torch.empty((n, 8), device=dev, dtype=torch.uint8)
+    g1, g2 = torch.empty_like(p1), torch.empty_like(p2)
+    gz1, gz2 = torch.empty_like(z1), torch.empty_like(z2)
+    state = {"f": (iou3, nx3, xf3, None), "b": (g1, gz1, g2, gz2)}
+    L = dg._lib
+    lib = L.lib()
+    sp = L.stream_ptr(stream)
+    # direct C-ABI calls with prepared pointers (device work only in the timed region)
+    f_args = (L.ptr(p1), None, L.ptr(z1), L.ptr(p2), None, L.ptr(z2), n, 4, L.ptr(iou3), L.ptr(nx3), L.ptr(xf3), None,
+              dg.DGAL_FP64_REFINE, sp)
+    b_args = (L.ptr(p1), None, L.ptr(z1), L.ptr(p2), None, L.ptr(z2), n, 4, L.ptr(grad), L.ptr(nx3), L.ptr(xf3),
+              L.ptr(g1), L.ptr(gz1), L.ptr(g2), L.ptr(gz2), dg.DGAL_FP64_REFINE, sp)
 
     def fwd():
-        state["f"] = dg.dgal_iou3d_paired(p1, z1, p2, z2)
+        assert lib.dgal_iou3d_paired(*f_args) == 0, dg.dgal_last_error()
 
     def bwd():
-        _, nx, xf, _ = state["f"]
-        state["b"] = dg.dgal_iou3d_backward(p1, z1, p2, z2, grad, nx, xf)
+        assert lib.dgal_iou3d_backward(*b_args) == 0, dg.dgal_last_error()
 
     for _ in range(args.warmup):
         fwd()
@@ -393,8 +424,9 @@ def iou3d_workload(args):
         "config": {"workload": "paired rotated 3D boxes (bird's-eye-view quadrilateral + (z, h)), 3D IoU "
                                "forward+backward, 1,000,000 pairs, K=4, FP64 refinement on",
                    "l2": "flushed between steps (256 MiB write outside the timed events)"},
-        "roofline": {"bound": "hbm", "kernel": "k_paired_fwd<4> (3D)", "achieved": alg_f * n / (fw * 1e-3) / 1e9,
-                     "peak": hbm, "unit": "GB/s", "frac": alg_f * n / (fw * 1e-3) / 1e9 / hbm, "traffic": None,
+        "roofline": {"bound": "hbm", "kernel": "k_paired_fwd<4> (3D)" if fw >= bw else "k_paired_bwd<4> (3D)",
+                     "achieved": (alg_f / fw if fw >= bw else alg_b / bw) * n / 1e-3 / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": (alg_f / fw if fw >= bw else alg_b / bw) * n / 1e-3 / 1e9 / hbm, "traffic": None,
                      "per_kernel": {"forward": {"ms": fw, "alg_bytes_per_pair": alg_f},
                                     "backward": {"ms": bw, "alg_bytes_per_pair": alg_b}}},
         "parity": {"iou_max_abs": float(np.abs(iou - ref["iou"]).max()), "grad_max_rel": grad_rel,
@@ -613,8 +645,15 @@ def main():
     bw_gbs = bwd_bytes * n / (bw_ms * 1e-3) / 1e9
     dom = "forward" if fw_ms >= bw_ms else "backward"
     ach = fw_gbs if dom == "forward" else bw_gbs
+    # DRAM bytes per pair of the two K = 4 kernels, dram__bytes_read.sum +
+    # dram__bytes_write.sum of one ncu capture on 4M pairs
+    # (profiles/paired_k4_fwd_bwd_4m_ncu_full.md), scaled to this launch
+    traffic = None
+    if K == 4 and c1 is None and args.workload == "loss1m":
+        traffic = (74.2 if dom == "forward" else 130.8) * n
     roofline = {"bound": "hbm", "kernel": f"k_paired_{'fwd' if dom == 'forward' else 'bwd'}<{K}>", "achieved": ach,
-                "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
+                "traffic_source": "ncu capture of 4M pairs, per pair x pairs" if traffic else None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
                 "per_kernel": {"forward": {"ms": fw_ms, "alg_bytes_per_pair": fwd_bytes, "GB_s": fw_gbs},
                                "backward": {"ms": bw_ms, "alg_bytes_per_pair": bwd_bytes, "GB_s": bw_gbs}}}

@@ -36,16 +36,36 @@ __device__ __forceinline__ float block_sum(float v, float* sh) {
     return t;
 }
 
-__global__ void __launch_bounds__(1024) k_sum_partials(const float* __restrict__ partials, int m, float* __restrict__ out) {
+// One block sums the m per-warp loss partials in a fixed order: thread t
+// takes float4 blocks t, t + 1024, ... (four loads in flight per round, each
+// block's values added in order), then the scalar tail, then a fixed tree.
+// The order does not depend on scheduling, so the loss is deterministic.
+// partials must be 16-byte aligned.
+constexpr int kSumThreads = 1024;
+
+__global__ void __launch_bounds__(kSumThreads) k_sum_partials(const float* __restrict__ partials, int m,
+                                                               float* __restrict__ out) {
     __shared__ float sh[32];
     float v = 0.f;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) v += partials[i];
+    const int m4 = m / 4;
+    const float4* p4 = reinterpret_cast<const float4*>(partials);
+    for (int base = 0; base < m4; base += 4 * kSumThreads) {
+        float4 a[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = base + u * kSumThreads + (int)threadIdx.x;
+            a[u] = (i < m4) ? __ldg(p4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v += (a[u].x + a[u].y) + (a[u].z + a[u].w);
+    }
+    for (int i = 4 * m4 + (int)threadIdx.x; i < m; i += kSumThreads) v += partials[i];
     const float t = block_sum(v, sh);
     if (threadIdx.x == 0) *out = t;
 }
 
 void launch_sum_partials(const float* partials, int64_t m, float* out, cudaStream_t s) {
-    k_sum_partials<<<1, 1024, 0, s>>>(partials, (int)m, out);
+    k_sum_partials<<<1, kSumThreads, 0, s>>>(partials, (int)m, out);
 }
 
 dgal_status launch_paired_fwd(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
