@@ -104,6 +104,28 @@ dgal_status dgal_iou_backward(const float* p1, const uint8_t* c1, const float* p
                               float* grad_p1, float* grad_p2, uint32_t flags, void* stream);
 
 /*
+ * Forward + backward of paired IoU on HOST-resident data (a runtime
+ * convenience; the paper has no counterpart): h_p1, h_p2 float [n][K][2],
+ * h_grad float [n] = dL/dIoU in; h_iou float [n], h_g1, h_g2 float [n][K][2]
+ * out (as dgal_iou_paired then dgal_iou_backward from the saved flags).  The
+ * pairs go through in chunks of `chunk` pairs over three staging slots of
+ * `workspace` (device memory, 256-byte aligned, at least
+ * dgal_iou_host_workspace_bytes(chunk, K) bytes, caller-owned): copies in,
+ * kernels and copies out of different chunks overlap on two copy streams of
+ * the library and the caller's stream.  Results are bit-identical to the
+ * device-memory calls.  The call is asynchronous and ordered on `stream`:
+ * the host buffers must stay valid and unmodified until the stream reaches
+ * that point, and they should be page-locked (pinned) for the copies to
+ * overlap.  The copy streams and their events are created on the first call
+ * on a device (make it outside any stream capture) and reused, so calls from
+ * several host threads must be serialised by the caller.
+ */
+size_t dgal_iou_host_workspace_bytes(int64_t chunk, int K);
+dgal_status dgal_iou_fwd_bwd_host(const float* h_p1, const float* h_p2, const float* h_grad, int64_t n, int K,
+                                  float* h_iou, float* h_g1, float* h_g2, void* workspace, size_t ws_bytes,
+                                  int64_t chunk, uint32_t flags, void* stream);
+
+/*
  * 3D IoU of paired boxes, each given as a bird's-eye-view polygon (as above)
  * and a vertical extent (the rotated 3D IoU loss use of the library, paper
  * Sec. IV-A):

@@ -43,7 +43,7 @@ __all__ = [
     "iou3d", "IoU3DLoss", "iou3d_loss", "dgal_nms_rotated", "dgal_nms_workspace_bytes",
     "dgal_intersect_paired", "dgal_area", "dgal_line_from_points", "dgal_line_from_points_backward",
     "dgal_line_intersect", "dgal_line_intersect_backward", "LineFromPoints", "LineIntersect",
-    "line_from_points", "line_intersect",
+    "line_from_points", "line_intersect", "dgal_iou_fwd_bwd_host", "dgal_iou_host_workspace_bytes",
 ]
 
 
@@ -353,6 +353,39 @@ def line_from_points(p, q):
 
 def line_intersect(l1, l2):
     return LineIntersect.apply(l1, l2)
+
+
+def dgal_iou_host_workspace_bytes(chunk, K=4):
+    return int(_lib.lib().dgal_iou_host_workspace_bytes(chunk, K))
+
+
+def dgal_iou_fwd_bwd_host(p1, p2, grad, out=None, chunk=131072, workspace=None, flags=DGAL_FP64_REFINE,
+                          stream=None, device=None):
+    """Paired IoU forward + backward on host tensors (CPU float32, ideally
+    pinned): p1, p2 [n, K, 2], grad [n] -> (iou [n], g1, g2 [n, K, 2]) on the
+    host, chunked and pipelined (copies overlap the kernels).  Asynchronous on
+    the stream: synchronise before reading the outputs."""
+    for t, name in ((p1, "p1"), (p2, "p2"), (grad, "grad")):
+        if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float32 host tensor")
+    if p1.dim() != 3 or p1.shape[2] != 2 or p1.shape[1] not in (4, 8) or p2.shape != p1.shape:
+        raise ValueError("p1 and p2 must be [n, K, 2] with K in (4, 8)")
+    n, K = p1.shape[0], p1.shape[1]
+    if grad.shape != (n,):
+        raise ValueError("grad must be [n]")
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    if workspace is None:
+        workspace = torch.empty(dgal_iou_host_workspace_bytes(chunk, K) + 256, device=dev, dtype=torch.uint8)
+        off = (-workspace.data_ptr()) % 256
+        workspace = workspace[off:]
+    if out is None:
+        pin = p1.is_pinned()
+        out = (torch.empty(n, pin_memory=pin), torch.empty((n, K, 2), pin_memory=pin),
+               torch.empty((n, K, 2), pin_memory=pin))
+    iou, g1, g2 = out
+    _lib.call("dgal_iou_fwd_bwd_host", _lib.ptr(p1), _lib.ptr(p2), _lib.ptr(grad), n, K, _lib.ptr(iou), _lib.ptr(g1),
+              _lib.ptr(g2), _lib.ptr(workspace), workspace.numel(), chunk, flags, _lib.stream_ptr(stream))
+    return iou, g1, g2
 
 
 def dgal_nms_workspace_bytes(N, K=4):

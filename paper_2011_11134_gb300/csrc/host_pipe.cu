@@ -1,0 +1,173 @@
+// Paired IoU forward + backward on host-resident data, pipelined in chunks.
+//
+// The paired kernels take a few tens of microseconds per million pairs; for
+// data that lives in host memory the copies dominate.  This call splits the
+// pairs into chunks and runs, for chunk c in staging slot c mod 3:
+//   copy-in stream   host -> slot: p1, p2, dL/dIoU         (event in[s])
+//   caller's stream  paired forward (flags kept in the slot) and backward
+//                    from those flags                       (event done[s])
+//   copy-out stream  slot -> host: IoU, dL/dp1, dL/dp2      (event out[s])
+// so the copies in both directions overlap each other and the kernels.  A
+// slot's inputs are rewritten only after its previous kernels finished, and
+// its outputs only after they were copied out.  The copy streams first wait
+// for the work already on the caller's stream, and the caller's stream
+// finally waits for the last copies, so the call is ordered on the caller's
+// stream like any other.  Streams and events are created once per device
+// (the first call on a device) and reused; device memory is the caller's
+// workspace.
+#include <map>
+#include <mutex>
+
+#include "dgal_internal.h"
+
+namespace dgal {
+namespace {
+
+constexpr int kSlots = 3;
+
+struct PipeState {
+    cudaStream_t in = nullptr, out = nullptr;
+    cudaEvent_t entry = nullptr;
+    cudaEvent_t ev_in[kSlots], ev_done[kSlots], ev_out[kSlots];
+};
+
+std::mutex g_pipe_mu;
+std::map<int, PipeState> g_pipe; // device ordinal -> streams and events
+
+dgal_status pipe_state(PipeState** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(DGAL_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    std::lock_guard<std::mutex> lk(g_pipe_mu);
+    auto it = g_pipe.find(dev);
+    if (it != g_pipe.end()) {
+        *out = &it->second;
+        return DGAL_OK;
+    }
+    PipeState st;
+    e = cudaStreamCreateWithFlags(&st.in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st.out, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st.entry, cudaEventDisableTiming);
+    for (int s = 0; s < kSlots && e == cudaSuccess; ++s) {
+        e = cudaEventCreateWithFlags(&st.ev_in[s], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st.ev_done[s], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st.ev_out[s], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return fail(DGAL_ERR_CUDA, "creating the copy streams: %s", cudaGetErrorString(e));
+    auto res = g_pipe.emplace(dev, st);
+    *out = &res.first->second;
+    return DGAL_OK;
+}
+
+size_t up256(size_t b) { return (b + 255) / 256 * 256; }
+
+// One slot: p1 | p2 | grad | iou | nx | xflags | g1 | g2, each 256-byte aligned.
+struct SlotLayout {
+    size_t p1, p2, grad, iou, nx, xflags, g1, g2, bytes;
+};
+
+SlotLayout slot_layout(int64_t chunk, int K) {
+    SlotLayout L;
+    const size_t poly = (size_t)chunk * K * 2 * sizeof(float);
+    size_t o = 0;
+    L.p1 = o;
+    o += up256(poly);
+    L.p2 = o;
+    o += up256(poly);
+    L.grad = o;
+    o += up256((size_t)chunk * 4);
+    L.iou = o;
+    o += up256((size_t)chunk * 4);
+    L.nx = o;
+    o += up256((size_t)chunk);
+    L.xflags = o;
+    o += up256((size_t)chunk * 2 * K);
+    L.g1 = o;
+    o += up256(poly);
+    L.g2 = o;
+    o += up256(poly);
+    L.bytes = o;
+    return L;
+}
+
+#define PIPE_CUDA(expr)                                                                              \
+    do {                                                                                             \
+        cudaError_t _e = (expr);                                                                     \
+        if (_e != cudaSuccess) return fail(DGAL_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(_e)); \
+    } while (0)
+
+} // namespace
+} // namespace dgal
+
+using namespace dgal;
+
+extern "C" size_t dgal_iou_host_workspace_bytes(int64_t chunk, int K) {
+    if ((K != 4 && K != 8) || chunk <= 0) return 0;
+    return kSlots * slot_layout(chunk, K).bytes;
+}
+
+extern "C" dgal_status dgal_iou_fwd_bwd_host(const float* h_p1, const float* h_p2, const float* h_grad, int64_t n,
+                                             int K, float* h_iou, float* h_g1, float* h_g2, void* workspace,
+                                             size_t ws_bytes, int64_t chunk, uint32_t flags, void* stream) {
+    if (K != 4 && K != 8) return fail(DGAL_ERR_UNSUPPORTED_K, "K = %d is not supported (K must be 4 or 8)", K);
+    if (n < 0) return fail(DGAL_ERR_INVALID_ARG, "n = %lld is negative", (long long)n);
+    if (n == 0) return DGAL_OK;
+    if (chunk <= 0) return fail(DGAL_ERR_INVALID_ARG, "chunk = %lld must be positive", (long long)chunk);
+    if (!h_p1 || !h_p2 || !h_grad || !h_iou || !h_g1 || !h_g2)
+        return fail(DGAL_ERR_INVALID_ARG, "a host buffer is NULL");
+    if (!workspace) return fail(DGAL_ERR_WORKSPACE, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(workspace) & 255u)
+        return fail(DGAL_ERR_ALIGNMENT, "workspace is not 256-byte aligned");
+    const SlotLayout L = slot_layout(chunk, K);
+    if (ws_bytes < kSlots * L.bytes)
+        return fail(DGAL_ERR_WORKSPACE, "workspace of %zu bytes is smaller than the %zu bytes needed", ws_bytes,
+                    kSlots * L.bytes);
+    PipeState* P = nullptr;
+    dgal_status st = pipe_state(&P);
+    if (st != DGAL_OK) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    // the copy streams start after the work already queued on the caller's stream
+    PIPE_CUDA(cudaEventRecord(P->entry, cs));
+    PIPE_CUDA(cudaStreamWaitEvent(P->in, P->entry, 0));
+    PIPE_CUDA(cudaStreamWaitEvent(P->out, P->entry, 0));
+    const int64_t nchunks = (n + chunk - 1) / chunk;
+    const size_t pp = (size_t)K * 2 * sizeof(float); // bytes of one polygon
+    for (int64_t c = 0; c < nchunks; ++c) {
+        const int s = (int)(c % kSlots);
+        const int64_t k0 = c * chunk;
+        const int64_t m = (n - k0 < chunk) ? n - k0 : chunk;
+        char* base = static_cast<char*>(workspace) + (size_t)s * L.bytes;
+        float* d_p1 = reinterpret_cast<float*>(base + L.p1);
+        float* d_p2 = reinterpret_cast<float*>(base + L.p2);
+        float* d_grad = reinterpret_cast<float*>(base + L.grad);
+        float* d_iou = reinterpret_cast<float*>(base + L.iou);
+        uint8_t* d_nx = reinterpret_cast<uint8_t*>(base + L.nx);
+        uint8_t* d_xf = reinterpret_cast<uint8_t*>(base + L.xflags);
+        float* d_g1 = reinterpret_cast<float*>(base + L.g1);
+        float* d_g2 = reinterpret_cast<float*>(base + L.g2);
+        // inputs: the slot's previous kernels must be done with them
+        if (c >= kSlots) PIPE_CUDA(cudaStreamWaitEvent(P->in, P->ev_done[s], 0));
+        PIPE_CUDA(cudaMemcpyAsync(d_p1, h_p1 + (size_t)k0 * K * 2, (size_t)m * pp, cudaMemcpyHostToDevice, P->in));
+        PIPE_CUDA(cudaMemcpyAsync(d_p2, h_p2 + (size_t)k0 * K * 2, (size_t)m * pp, cudaMemcpyHostToDevice, P->in));
+        PIPE_CUDA(cudaMemcpyAsync(d_grad, h_grad + k0, (size_t)m * 4, cudaMemcpyHostToDevice, P->in));
+        PIPE_CUDA(cudaEventRecord(P->ev_in[s], P->in));
+        // kernels: inputs arrived, and the slot's previous outputs were copied out
+        PIPE_CUDA(cudaStreamWaitEvent(cs, P->ev_in[s], 0));
+        if (c >= kSlots) PIPE_CUDA(cudaStreamWaitEvent(cs, P->ev_out[s], 0));
+        st = launch_paired_fwd(d_p1, nullptr, d_p2, nullptr, m, K, d_iou, d_nx, d_xf, nullptr, flags, cs);
+        if (st != DGAL_OK) return st;
+        st = launch_paired_bwd(d_p1, nullptr, d_p2, nullptr, m, K, d_grad, d_nx, d_xf, d_g1, d_g2, flags, cs);
+        if (st != DGAL_OK) return st;
+        PIPE_CUDA(cudaEventRecord(P->ev_done[s], cs));
+        // outputs
+        PIPE_CUDA(cudaStreamWaitEvent(P->out, P->ev_done[s], 0));
+        PIPE_CUDA(cudaMemcpyAsync(h_iou + k0, d_iou, (size_t)m * 4, cudaMemcpyDeviceToHost, P->out));
+        PIPE_CUDA(cudaMemcpyAsync(h_g1 + (size_t)k0 * K * 2, d_g1, (size_t)m * pp, cudaMemcpyDeviceToHost, P->out));
+        PIPE_CUDA(cudaMemcpyAsync(h_g2 + (size_t)k0 * K * 2, d_g2, (size_t)m * pp, cudaMemcpyDeviceToHost, P->out));
+        PIPE_CUDA(cudaEventRecord(P->ev_out[s], P->out));
+    }
+    // the caller's stream ends after the last copies out
+    const int64_t first = nchunks > kSlots ? nchunks - kSlots : 0;
+    for (int64_t c = first; c < nchunks; ++c) PIPE_CUDA(cudaStreamWaitEvent(cs, P->ev_out[c % kSlots], 0));
+    return DGAL_OK;
+}
