@@ -45,6 +45,16 @@ constexpr float kDegenRel = 1e-5f; // near-degenerate threshold (relative to L^2
 // orientation between this and kDegenRel are still reported near-degenerate.
 constexpr float kRouteRel = 5e-6f;
 
+// Thin-pair routing of the FP32 fast paths.  Their areas carry an absolute
+// error of order u L^2 (each shoelace term is a difference of products of
+// coordinates up to L), so the IoU error grows as u L^2 / U for a small union
+// U.  An intersecting pair with U below this fraction of L^2 (thin or tiny
+// polygons far apart in the pair's frame) is handed to the warp-cooperative
+// path, whose rounding estimate takes such areas in FP64.  None of the
+// IoU-loss rectangle pairs and about 0.05% of the intersecting convex-hull
+// pairs are below it.
+constexpr float kThinRel = 0.02f;
+
 // device status bits (mirror include/dgal.h)
 constexpr uint32_t kDevBadCount = 0x1u;
 constexpr uint32_t kDevOverflow = 0x2u;
@@ -159,6 +169,7 @@ template <int K> struct FwdOut {
     Codes<K> codes;
     float iou;
     float ai, a1, a2;
+    float L2; // squared coordinate scale of the pair (fast path)
     uint32_t nx;
     uint32_t degen; // bit 0 near-degenerate, bit 1 FP64 orientation tests used
     uint32_t err;   // device status bits
@@ -610,6 +621,7 @@ __device__ __forceinline__ bool fwd_generic(const Geo<K>& g, FwdOut<K>& o, const
     }
     o.nx = cnt;
     o.ai = 0.5f * twoA;
+    o.L2 = L * L;
     return true;
 }
 
@@ -814,6 +826,7 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
     }
     uint32_t code = 0xFFu;
     float fx0 = 0.f, fy0 = 0.f, fx1 = 0.f, fy1 = 0.f, t = 0.f;
+    float gx0 = 0.f, gy0 = 0.f, gx1 = 0.f, gy1 = 0.f; // P2 edge of a crossing
     bool deg2 = false;
     if (kind == 0) {
         code = (uint32_t)ci;
@@ -830,6 +843,10 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
         fx1 = sel<K>(px, ci1);
         fy1 = sel<K>(py, ci1);
         const float bx0 = sel<K>(qx, cj), by0 = sel<K>(qy, cj), bx1 = sel<K>(qx, cj1), by1 = sel<K>(qy, cj1);
+        gx0 = bx0;
+        gy0 = by0;
+        gx1 = bx1;
+        gy1 = by1;
         // the crossing parameters only place a vertex along its edge, so they
         // are FP32 quotients of the orientation values (of opposite signs at
         // a strict crossing, so the differences do not cancel)
@@ -929,10 +946,18 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
     o.a1 = a1;
     o.a2 = a2;
     if (refine && !(est <= kAreaEstMax * U)) {
-        // FP64 areas: vertices placed on their edges in FP64, the intersection
-        // about the candidates' centroid, the inputs about P1's vertex 0
-        const double X64 = ((double)fx0 - (double)ox) + (double)t * ((double)fx1 - (double)fx0);
-        const double Y64 = ((double)fy0 - (double)oy) + (double)t * ((double)fy1 - (double)fy0);
+        // FP64 areas: vertices placed on their edges in FP64 (a crossing's
+        // parameter from its two orientations in FP64, which have opposite
+        // signs at a proper crossing, so the quotient does not cancel), the
+        // intersection about the candidates' centroid, the inputs about P1's
+        // vertex 0
+        double t64 = (double)t;
+        if (kind == 2) {
+            const double s0 = orient64(gx0, gy0, gx1, gy1, fx0, fy0), s1 = orient64(gx0, gy0, gx1, gy1, fx1, fy1);
+            t64 = s0 / (s0 - s1);
+        }
+        const double X64 = ((double)fx0 - (double)ox) + t64 * ((double)fx1 - (double)fx0);
+        const double Y64 = ((double)fy0 - (double)oy) + t64 * ((double)fy1 - (double)fy0);
         const double mx = warp_sum(live ? X64 : 0.0) / (double)m, my = warp_sum(live ? Y64 : 0.0) / (double)m;
         const double nxp = __shfl_sync(full, X64, nl), nyp = __shfl_sync(full, Y64, nl);
         const double tm = live ? __dsub_rn(__dmul_rn(X64 - mx, nyp - my), __dmul_rn(Y64 - my, nxp - mx)) : 0.0;

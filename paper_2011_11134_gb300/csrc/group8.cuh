@@ -211,6 +211,7 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
     const float a2 = 0.5f * s2;
     const float ai = 0.5f * twoA;
     const float U = a1 + a2 - ai;
+    if (U < kThinRel * Lr * Lr) return false; // thin pair: FP64 areas on the warp path
 
     // chunk of the vertex order from P1 edge r
     uint64_t c_lo = 0, c_hi = 0;

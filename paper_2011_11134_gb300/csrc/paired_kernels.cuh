@@ -176,6 +176,8 @@ k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
                 o.degen = 0;
                 hard = refine ? !fwd_generic<K, COUNTS>(g, o, p1 + k * 2 * K, p2 + k * 2 * K)
                               : !fwd_generic<K, COUNTS>(g, o);
+                // thin pairs: FP64 areas on the warp path (kThinRel)
+                hard = hard || (o.nx >= 3u && o.a1 + o.a2 - o.ai < kThinRel * o.L2);
                 if (!hard) {
                     if constexpr (Z3) {
                         o.iou = iou3_value(o.ai, o.a1, o.a2, o.nx, z_of(za, k));

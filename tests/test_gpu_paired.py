@@ -4,7 +4,7 @@ import pytest
 
 from paper_2011_11134_gb300 import workloads as W
 
-from .gpu_helpers import GRAD_RTOL, THREADS, check_forward, dev, grad_rel_err, host
+from .gpu_helpers import GRAD_RTOL, IOU_ATOL, THREADS, check_forward, dev, grad_rel_err, host
 
 pytestmark = pytest.mark.gpu
 
@@ -221,3 +221,32 @@ def test_bad_counts_set_status(dg):
     st = dg.dgal_get_device_status(clear=True)
     assert st & dg.DGAL_DEV_BAD_FLAGS
     assert (host(g1)[0] == 0).all() and (host(g1)[1] == 0).all()
+
+
+def test_thin_pairs_within_tolerance(dg, orc):
+    """Thin rectangles (aspect up to 800) with slightly shifted partners:
+    their union is a small fraction of the pair's squared coordinate scale,
+    where FP32 shoelace sums lose digits; the IoU stays within 1e-5 of the
+    FP64 oracle on every pair, K = 4 paired and pairwise, and K = 8."""
+    r = np.random.default_rng(61)
+    n = 20000
+    c = r.uniform(0, 10, (n, 2))
+    w, h = r.uniform(2.0, 4.0, n), r.uniform(0.005, 0.02, n)
+    th = r.uniform(-np.pi, np.pi, n)
+    p1 = W.boxes_to_polygons(c[:, 0], c[:, 1], w, h, th)
+    shift = r.normal(0, 0.004, (n, 2))
+    p2 = W.boxes_to_polygons(c[:, 0] + shift[:, 0], c[:, 1] + shift[:, 1], w * r.uniform(0.98, 1.02, n),
+                             h * r.uniform(0.8, 1.2, n), th + r.normal(0, 1e-3, n))
+    ref = orc.iou_paired(p1, p2, threads=THREADS)
+    assert (ref["nx"] >= 3).mean() > 0.5
+    iou, _, _, _ = dg.dgal_iou_paired(dev(p1), dev(p2))
+    assert np.abs(host(iou).astype(np.float64) - ref["iou"]).max() <= IOU_ATOL
+    m, _ = dg.dgal_iou_pairwise(dev(p1[:300]), dev(p2[:300]), with_nx=False)
+    rm, _ = orc.iou_pairwise(p1[:300], p2[:300], threads=THREADS)
+    assert np.abs(host(m).astype(np.float64) - rm).max() <= IOU_ATOL
+    # K = 8: the same rectangles padded with counts
+    q1 = np.concatenate([p1, np.repeat(p1[:, :1], 4, 1)], 1).astype(np.float32)
+    q2 = np.concatenate([p2, np.repeat(p2[:, :1], 4, 1)], 1).astype(np.float32)
+    cnt = np.full(n, 4, np.uint8)
+    i8, _, _, _ = dg.dgal_iou_paired(dev(q1), dev(q2), dev(cnt), dev(cnt))
+    assert np.abs(host(i8).astype(np.float64) - ref["iou"]).max() <= IOU_ATOL
