@@ -250,3 +250,33 @@ def test_thin_pairs_within_tolerance(dg, orc):
     cnt = np.full(n, 4, np.uint8)
     i8, _, _, _ = dg.dgal_iou_paired(dev(q1), dev(q2), dev(cnt), dev(cnt))
     assert np.abs(host(i8).astype(np.float64) - ref["iou"]).max() <= IOU_ATOL
+
+
+def test_k4_with_counts(dg, orc):
+    """Triangles and quadrilaterals in K = 4 storage (counts 3 or 4): the
+    K = 4 kernels' count-aware instantiations, forward, backward from saved
+    flags and recomputed, and the pairwise matrix."""
+    import torch
+
+    d = W.convex_pairs_4m(seed=17, n=30_000, K=4, degenerate_frac=0.0)
+    assert (d["c1"] == 3).any() and (d["c1"] == 4).any()
+    p1, p2, c1, c2 = d["p1"], d["p2"], d["c1"], d["c2"]
+    iou, nx, xf, degen = _fwd(dg, p1, p2, c1, c2)
+    ref = orc.iou_paired(p1, p2, c1, c2, threads=THREADS)
+    gen = check_forward(iou, nx, xf, degen, ref, "K=4 counts")
+    g = np.ones(p1.shape[0], np.float32)
+    r1, r2 = orc.iou_backward_paired(p1, p2, np.ones(p1.shape[0]), ref["nx"], ref["xflags"], c1, c2,
+                                     threads=THREADS)
+    P1, P2, C1, C2 = dev(p1), dev(p2), dev(c1), dev(c2)
+    for saved in (True, False):
+        a, b = (dev(nx), dev(xf)) if saved else (None, None)
+        g1, g2 = dg.dgal_iou_backward(P1, P2, dev(g), a, b, c1=C1, c2=C2)
+        torch.cuda.synchronize()
+        rel = grad_rel_err(host(g1), host(g2), r1, r2, gen)
+        assert rel.max() <= GRAD_RTOL, (saved, rel.max())
+        pad = np.arange(4)[None, :] >= c1.astype(int)[:, None]
+        assert (host(g1)[pad] == 0).all()
+    m, mnx = dg.dgal_iou_pairwise(P1[:400], P2[:300], C1[:400], C2[:300])
+    rm, rnx = orc.iou_pairwise(p1[:400], p2[:300], c1[:400], c2[:300], threads=THREADS)
+    assert np.abs(host(m).astype(np.float64) - rm).max() <= IOU_ATOL
+    assert dg.dgal_get_device_status() == 0
