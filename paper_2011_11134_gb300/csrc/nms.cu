@@ -16,10 +16,12 @@
 //                    two 32-lane ballots;
 //   3. k_nms_greedy  one block walks the words of 64 rows at a time: thread 0
 //                    resolves the suppression inside the 64-row block from
-//                    its diagonal word, then all threads OR the kept rows'
-//                    words into the removal bitmap held in shared memory.  The
-//                    next diagonal is fetched while the current rows are
-//                    applied.  Only kept rows are ever read.
+//                    its diagonal word, then every (kept row, later word)
+//                    pair goes to its own thread, which ORs the word into the
+//                    removal bitmap held in shared memory, so the block's
+//                    loads are in flight together.  The next diagonal is
+//                    fetched while the current rows are applied.  Only kept
+//                    rows are ever read.
 #include <cmath>
 
 #include "dgal_geom.cuh"
@@ -115,9 +117,10 @@ k_nms_mask(const float* __restrict__ sboxes, const uint8_t* __restrict__ scounts
 __global__ void __launch_bounds__(kNmsGreedyThreads)
 k_nms_greedy(const int32_t* __restrict__ order, const uint64_t* __restrict__ mask, int64_t N, int64_t W,
              int64_t* __restrict__ keep, int64_t* __restrict__ num_keep) {
-    extern __shared__ uint64_t removed[]; // W words: bit b of word w = row 64 w + b is suppressed
+    extern __shared__ unsigned long long removed[]; // W words: bit b of word w = row 64 w + b is suppressed
     __shared__ uint64_t diag[2][64];
     __shared__ uint64_t s_kept;
+    __shared__ int s_rows[64]; // the kept rows of the current block, in order
     const int t = threadIdx.x;
     for (int64_t w = t; w < W; w += blockDim.x) removed[w] = 0ull;
     if (t < 64) diag[0][t] = (t < N) ? mask[(int64_t)t * W] : 0ull;
@@ -145,17 +148,21 @@ k_nms_greedy(const int32_t* __restrict__ order, const uint64_t* __restrict__ mas
         }
         __syncthreads();
         const uint64_t kept = s_kept;
-        if (t < 64 && ((kept >> t) & 1ull))
-            keep[count + __popcll(kept & ((1ull << t) - 1ull))] = (int64_t)order[c * 64 + t];
-        count += __popcll(kept);
-        for (int64_t w = c + 1 + t; w < W; w += blockDim.x) {
-            uint64_t acc = 0ull, m = kept;
-            while (m) {
-                const int r = __ffsll((long long)m) - 1;
-                m &= m - 1ull;
-                acc |= mask[(c * 64 + r) * W + w];
-            }
-            removed[w] |= acc;
+        if (t < 64 && ((kept >> t) & 1ull)) {
+            const int slot = __popcll(kept & ((1ull << t) - 1ull));
+            keep[count + slot] = (int64_t)order[c * 64 + t];
+            s_rows[slot] = t;
+        }
+        const int nk = __popcll(kept);
+        count += nk;
+        __syncthreads();
+        // every (kept row, later word) pair on its own thread, so all the
+        // block's loads are in flight together; shared-memory OR to combine
+        const int nw = (int)(W - c - 1), pairs = nk * nw; // W <= 2048: 32-bit indices
+        for (int idx = t; idx < pairs; idx += blockDim.x) {
+            const int k = idx / nw, w = (int)c + 1 + (idx - k * nw);
+            const uint64_t v = mask[(c * 64 + s_rows[k]) * W + w];
+            if (v) atomicOr(&removed[w], (unsigned long long)v);
         }
         if (t < 64) diag[buf ^ 1][t] = nd;
         __syncthreads();
