@@ -1,13 +1,12 @@
 // Pairwise IoU matrices: one N x M matrix, or a ragged batch of S matrices
 // in one persistent launch.
 //
-// Each thread owns one (i, j) entry of a row-major matrix, so consecutive
-// lanes write consecutive IoU floats and nx bytes (coalesced).  Row polygon
-// a_i is the same for most lanes of a warp (a broadcast load), column polygons
-// b_j are consecutive 32/64-byte rows; both sets are small and stay in L1/L2.
-// An exact axis-aligned bounding-box test (comparisons on the float inputs,
-// no rounding) rejects disjoint pairs before the clip: they have IoU 0 and
-// nx 0 by definition (no vertex inside, no crossing).
+// One matrix: tiles of 32 rows x 128 columns; an exact axis-aligned
+// bounding-box test (comparisons on the float inputs, no rounding) on every
+// entry first, since disjoint pairs have IoU 0 and nx 0 by definition (no
+// vertex inside, no crossing), then the clip on the queued entries whose
+// boxes meet, densely (see k_pairwise).  Consecutive lanes write consecutive
+// IoU floats and nx bytes.
 //
 // Ragged batch: a setup kernel turns the device-side offsets into a tile
 // prefix (tiles of `tile` consecutive entries of one scene's matrix) and
@@ -21,42 +20,111 @@
 
 namespace dgal {
 
+// Tiles of the N x M matrix: kTileRows rows x kPwThreads columns (32 rows
+// measured fastest on the 2000 x 2000 bird's-eye matrix: 26.6 us, against
+// 29.4 at 16 rows and 33.5 at 8; more rows give each tile more queued
+// entries, so more of its warps clip at once).
+constexpr int kTileRows = 32;
+
+// Axis-aligned bounding box (min x, min y, max x, max y) of a polygon's first
+// n vertices; a count outside [3, K] gives a box that meets every box, so the
+// entry reaches pw_fast, which reports the count.
+template <int K, bool COUNTS> __device__ __forceinline__ float4 poly_box(const float* __restrict__ p, int n) {
+    if (COUNTS && (n < 3 || n > K)) {
+        const float inf = __int_as_float(0x7f800000);
+        return make_float4(-inf, -inf, inf, inf);
+    }
+    float x[K], y[K];
+    load_poly<K>(p, x, y);
+    float4 r = make_float4(x[0], y[0], x[0], y[0]);
+#pragma unroll
+    for (int v = 1; v < K; ++v) {
+        const bool on = !COUNTS || v < n;
+        r.x = on ? fminf(r.x, x[v]) : r.x;
+        r.y = on ? fminf(r.y, y[v]) : r.y;
+        r.z = on ? fmaxf(r.z, x[v]) : r.z;
+        r.w = on ? fmaxf(r.w, y[v]) : r.w;
+    }
+    return r;
+}
+
+// One N x M matrix.  Blocks take tiles of kTileRows x 128 entries in turn:
+//   1. thread c computes the bounding box of column j0 + c, threads < 8 those
+//      of the tile's rows (shared memory);
+//   2. every entry is tested on the boxes (exact comparisons of the float
+//      inputs); a disjoint pair has IoU 0 and nx 0 by definition and is
+//      written at once (consecutive threads, consecutive columns), the others
+//      are queued in shared memory;
+//   3. the block's warps clip the queued entries densely (pw_fast, with the
+//      warp-cooperative finish for the ones it hands back).
+// In bird's-eye scenes about 2% of the entries have meeting boxes; without the
+// queue a warp runs the clip whenever one of its 32 entries needs it.
 template <int K, bool COUNTS>
 __global__ void __launch_bounds__(kPwThreads)
 k_pairwise(const float* __restrict__ a, const uint8_t* __restrict__ ca, int64_t N, const float* __restrict__ b,
            const uint8_t* __restrict__ cb, int64_t M, float* __restrict__ iou, uint8_t* __restrict__ nx,
            uint32_t flags, uint32_t* status) {
-    const int lane = threadIdx.x & 31;
-    const int64_t total = N * M;
-    const int64_t stride = (int64_t)gridDim.x * kPwThreads;
+    constexpr unsigned full = 0xffffffffu;
+    __shared__ float4 s_rbox[kTileRows];
+    __shared__ uint16_t s_q[kTileRows * kPwThreads];
+    __shared__ int s_nq;
+    const int t = threadIdx.x, lane = t & 31;
     const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
-    int64_t base = (int64_t)blockIdx.x * kPwThreads + (threadIdx.x & ~31);
-    if (base >= total) return;
-    const int64_t e0 = base + lane;
-    int64_t i = e0 / M, j = e0 - (e0 / M) * M;
-    const int64_t di = stride / M, dj = stride - di * M;
+    const int64_t cblocks = (M + kPwThreads - 1) / kPwThreads;
+    const int64_t tiles = ((N + kTileRows - 1) / kTileRows) * cblocks;
+    const float inf = __int_as_float(0x7f800000);
     uint32_t err = 0;
-    for (; base < total; base += stride) {
-        const int64_t e = base + lane;
-        const bool act = e < total;
-        const int n1 = (COUNTS && ca && act) ? (int)ca[i] : K;
-        const int n2 = (COUNTS && cb && act) ? (int)cb[j] : K;
-        const float* pa = a + (act ? i : 0) * 2 * K;
-        const float* pb = b + (act ? j : 0) * 2 * K;
-        float v = 0.f;
-        uint32_t c = 0;
-        const bool hard = act && pw_fast<K, COUNTS>(pa, pb, n1, n2, v, c, err, refine);
-        pw_finish<K>(__ballot_sync(0xffffffffu, hard), pa, pb, n1, n2, refine, v, c, err);
-        if (act) {
-            iou[e] = v;
-            if (nx) nx[e] = (uint8_t)c;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t rb = tile / cblocks;
+        const int64_t i0 = rb * kTileRows, j0 = (tile - rb * cblocks) * kPwThreads;
+        const int64_t j = j0 + t;
+        const bool jv = j < M;
+        const float4 cbx = jv ? poly_box<K, COUNTS>(b + j * 2 * K, (COUNTS && cb) ? (int)cb[j] : K)
+                              : make_float4(inf, inf, -inf, -inf);
+        if (t < kTileRows) {
+            const int64_t i = i0 + t;
+            s_rbox[t] = (i < N) ? poly_box<K, COUNTS>(a + i * 2 * K, (COUNTS && ca) ? (int)ca[i] : K)
+                                : make_float4(inf, inf, -inf, -inf);
         }
-        i += di;
-        j += dj;
-        if (j >= M) {
-            j -= M;
-            ++i;
+        if (t == 0) s_nq = 0;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kTileRows; ++r) {
+            const int64_t i = i0 + r;
+            const bool v = jv && i < N;
+            const float4 rbx = s_rbox[r];
+            const bool meet = v && !(rbx.z < cbx.x || cbx.z < rbx.x || rbx.w < cbx.y || cbx.w < rbx.y);
+            if (v && !meet) {
+                iou[i * M + j] = 0.f;
+                if (nx) nx[i * M + j] = 0;
+            }
+            const unsigned bal = __ballot_sync(full, meet);
+            int pos = 0;
+            if (lane == 0 && bal) pos = atomicAdd(&s_nq, __popc(bal));
+            pos = __shfl_sync(full, pos, 0);
+            if (meet) s_q[pos + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)((r << 8) | t);
         }
+        __syncthreads();
+        const int nq = s_nq;
+        for (int qb = t & ~31; qb < nq; qb += kPwThreads) {
+            const int q = qb + lane;
+            const bool act = q < nq;
+            const int code = act ? (int)s_q[q] : 0;
+            const int64_t i = i0 + (code >> 8), jj = j0 + (code & 0xFF);
+            const int n1 = (COUNTS && ca && act) ? (int)ca[i] : K;
+            const int n2 = (COUNTS && cb && act) ? (int)cb[jj] : K;
+            const float* pa = a + (act ? i : 0) * 2 * K;
+            const float* pb = b + (act ? jj : 0) * 2 * K;
+            float v = 0.f;
+            uint32_t c = 0;
+            const bool hard = act && pw_fast<K, COUNTS>(pa, pb, n1, n2, v, c, err, refine);
+            pw_finish<K>(__ballot_sync(full, hard), pa, pb, n1, n2, refine, v, c, err);
+            if (act) {
+                iou[i * M + jj] = v;
+                if (nx) nx[i * M + jj] = (uint8_t)c;
+            }
+        }
+        __syncthreads(); // the next tile reuses the boxes and the queue
     }
     if (err) atomicOr(status, err);
 }
@@ -175,9 +243,9 @@ __global__ void k_batched(int S, const int64_t* __restrict__ a_off, const int64_
 template <int K, bool COUNTS>
 static void pairwise_dispatch(const float* a, const uint8_t* ca, int64_t N, const float* b, const uint8_t* cb,
                               int64_t M, float* iou, uint8_t* nx, uint32_t flags, cudaStream_t s) {
-    const int64_t total = N * M;
-    int64_t blocks = (total + kPwThreads - 1) / kPwThreads;
-    const int64_t cap = (int64_t)sm_count() * 32;
+    const int64_t tiles = ((N + kTileRows - 1) / kTileRows) * ((M + kPwThreads - 1) / kPwThreads);
+    int64_t blocks = tiles;
+    const int64_t cap = (int64_t)sm_count() * 8;
     if (blocks > cap) blocks = cap;
     k_pairwise<K, COUNTS><<<(unsigned)blocks, kPwThreads, 0, s>>>(a, ca, N, b, cb, M, iou, nx, flags,
                                                                    device_status_ptr());
