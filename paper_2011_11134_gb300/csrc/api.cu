@@ -74,7 +74,7 @@ BatchedConfig batched_config(int K) {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_cfg.find({d, K});
     if (it != g_cfg.end()) return it->second;
-    return BatchedConfig{1024, 128, 8};
+    return BatchedConfig{4096, 128, 4}; // 32 x 128 tiles, four blocks per SM
 }
 
 void set_batched_config(int K, BatchedConfig c) {
@@ -595,7 +595,7 @@ extern "C" dgal_status dgal_autotune(int K, int config_class, const char* cache_
         cleanup();
         return fail(DGAL_ERR_CUDA, "autotune: synthetic input generation failed");
     }
-    const int tiles[] = {256, 512, 1024, 2048, 4096};
+    const int tiles[] = {1024, 2048, 4096}; // entries per tile: rows x threads
     const int threads[] = {128, 256};
     const int bps[] = {2, 4, 8, 12};
     BatchedConfig best{1024, 128, 8};

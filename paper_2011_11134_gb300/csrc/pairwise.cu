@@ -9,9 +9,9 @@
 // IoU floats and nx bytes.
 //
 // Ragged batch: a setup kernel turns the device-side offsets into a tile
-// prefix (tiles of `tile` consecutive entries of one scene's matrix) and
-// resets a queue counter; persistent blocks (SMs x blocks_sm) pop tile
-// numbers with one atomicAdd each until the queue is empty.  The queue only
+// prefix (tiles of rows x threads entries of one scene's matrix) and resets a
+// queue counter; persistent blocks (SMs x blocks_sm) pop tile numbers with
+// one atomicAdd each until the queue is empty and run pw_tile on each.  The queue only
 // grows, nothing waits on it, so the launch cannot hang; everything it reads
 // lives on the device, so the pair of launches can be captured in a graph.
 #include "dgal_geom.cuh"
@@ -19,6 +19,14 @@
 #include "pw_entry.cuh"
 
 namespace dgal {
+
+// Single matrices narrower than this, or with fewer than two tiles per SM,
+// take the one-thread-per-entry kernel (the tiled one would leave most of a
+// tile's columns, or most SMs, idle).
+constexpr int64_t kFlatMaxCols = 96;
+
+// Rows of a ragged-batch tile: entries per tile / threads, at most this.
+constexpr int kMaxTileRows = 32;
 
 // Tiles of the N x M matrix: kTileRows rows x kPwThreads columns (32 rows
 // measured fastest on the 2000 x 2000 bird's-eye matrix: 26.6 us, against
@@ -48,83 +56,138 @@ template <int K, bool COUNTS> __device__ __forceinline__ float4 poly_box(const f
     return r;
 }
 
-// One N x M matrix.  Blocks take tiles of kTileRows x 128 entries in turn:
-//   1. thread c computes the bounding box of column j0 + c, threads < 8 those
+// One tile of rows [i0, i0 + R) x columns [j0, j0 + blockDim.x) of an N x M
+// matrix (a, b: the matrix's row and column polygons; iou, nx: its outputs):
+//   1. thread c computes the bounding box of column j0 + c, threads < R those
 //      of the tile's rows (shared memory);
 //   2. every entry is tested on the boxes (exact comparisons of the float
 //      inputs); a disjoint pair has IoU 0 and nx 0 by definition and is
 //      written at once (consecutive threads, consecutive columns), the others
-//      are queued in shared memory;
+//      are queued in shared memory (s_q, codes r << 8 | c);
 //   3. the block's warps clip the queued entries densely (pw_fast, with the
 //      warp-cooperative finish for the ones it hands back).
 // In bird's-eye scenes about 2% of the entries have meeting boxes; without the
-// queue a warp runs the clip whenever one of its 32 entries needs it.
+// queue a warp runs the clip whenever one of its 32 entries needs it.  Every
+// thread of the block calls this (it has block barriers).
+template <int K, bool COUNTS>
+__device__ __forceinline__ void pw_tile(const float* __restrict__ a, const uint8_t* __restrict__ ca, int64_t N,
+                                        const float* __restrict__ b, const uint8_t* __restrict__ cb, int64_t M,
+                                        float* __restrict__ iou, uint8_t* __restrict__ nx, int64_t i0, int64_t j0,
+                                        int R, float4* s_rbox, uint16_t* s_q, int* s_nq, bool refine,
+                                        uint32_t& err) {
+    constexpr unsigned full = 0xffffffffu;
+    const int t = threadIdx.x, lane = t & 31, C = blockDim.x;
+    const float inf = __int_as_float(0x7f800000);
+    const int64_t j = j0 + t;
+    const bool jv = j < M;
+    const float4 cbx = jv ? poly_box<K, COUNTS>(b + j * 2 * K, (COUNTS && cb) ? (int)cb[j] : K)
+                          : make_float4(inf, inf, -inf, -inf);
+    if (t < R) {
+        const int64_t i = i0 + t;
+        s_rbox[t] = (i < N) ? poly_box<K, COUNTS>(a + i * 2 * K, (COUNTS && ca) ? (int)ca[i] : K)
+                            : make_float4(inf, inf, -inf, -inf);
+    }
+    if (t == 0) *s_nq = 0;
+    __syncthreads();
+#pragma unroll 4
+    for (int r = 0; r < R; ++r) {
+        const int64_t i = i0 + r;
+        const bool v = jv && i < N;
+        const float4 rbx = s_rbox[r];
+        const bool meet = v && !(rbx.z < cbx.x || cbx.z < rbx.x || rbx.w < cbx.y || cbx.w < rbx.y);
+        if (v && !meet) {
+            iou[i * M + j] = 0.f;
+            if (nx) nx[i * M + j] = 0;
+        }
+        const unsigned bal = __ballot_sync(full, meet);
+        int pos = 0;
+        if (lane == 0 && bal) pos = atomicAdd(s_nq, __popc(bal));
+        pos = __shfl_sync(full, pos, 0);
+        if (meet) s_q[pos + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)((r << 8) | t);
+    }
+    __syncthreads();
+    const int nq = *s_nq;
+    for (int qb = t & ~31; qb < nq; qb += C) {
+        const int q = qb + lane;
+        const bool act = q < nq;
+        const int code = act ? (int)s_q[q] : 0;
+        const int64_t i = i0 + (code >> 8), jj = j0 + (code & 0xFF);
+        const int n1 = (COUNTS && ca && act) ? (int)ca[i] : K;
+        const int n2 = (COUNTS && cb && act) ? (int)cb[jj] : K;
+        const float* pa = a + (act ? i : 0) * 2 * K;
+        const float* pb = b + (act ? jj : 0) * 2 * K;
+        float v = 0.f;
+        uint32_t c = 0;
+        const bool hard = act && pw_fast<K, COUNTS>(pa, pb, n1, n2, v, c, err, refine);
+        pw_finish<K>(__ballot_sync(full, hard), pa, pb, n1, n2, refine, v, c, err);
+        if (act) {
+            iou[i * M + jj] = v;
+            if (nx) nx[i * M + jj] = (uint8_t)c;
+        }
+    }
+    __syncthreads(); // the next tile reuses the boxes and the queue
+}
+
+// One N x M matrix: blocks take tiles of kTileRows x kPwThreads entries in
+// turn (pw_tile).
 template <int K, bool COUNTS>
 __global__ void __launch_bounds__(kPwThreads)
 k_pairwise(const float* __restrict__ a, const uint8_t* __restrict__ ca, int64_t N, const float* __restrict__ b,
            const uint8_t* __restrict__ cb, int64_t M, float* __restrict__ iou, uint8_t* __restrict__ nx,
            uint32_t flags, uint32_t* status) {
-    constexpr unsigned full = 0xffffffffu;
     __shared__ float4 s_rbox[kTileRows];
     __shared__ uint16_t s_q[kTileRows * kPwThreads];
     __shared__ int s_nq;
-    const int t = threadIdx.x, lane = t & 31;
     const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
     const int64_t cblocks = (M + kPwThreads - 1) / kPwThreads;
     const int64_t tiles = ((N + kTileRows - 1) / kTileRows) * cblocks;
-    const float inf = __int_as_float(0x7f800000);
     uint32_t err = 0;
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int64_t rb = tile / cblocks;
-        const int64_t i0 = rb * kTileRows, j0 = (tile - rb * cblocks) * kPwThreads;
-        const int64_t j = j0 + t;
-        const bool jv = j < M;
-        const float4 cbx = jv ? poly_box<K, COUNTS>(b + j * 2 * K, (COUNTS && cb) ? (int)cb[j] : K)
-                              : make_float4(inf, inf, -inf, -inf);
-        if (t < kTileRows) {
-            const int64_t i = i0 + t;
-            s_rbox[t] = (i < N) ? poly_box<K, COUNTS>(a + i * 2 * K, (COUNTS && ca) ? (int)ca[i] : K)
-                                : make_float4(inf, inf, -inf, -inf);
+        pw_tile<K, COUNTS>(a, ca, N, b, cb, M, iou, nx, rb * kTileRows, (tile - rb * cblocks) * kPwThreads,
+                           kTileRows, s_rbox, s_q, &s_nq, refine, err);
+    }
+    if (err) atomicOr(status, err);
+}
+
+// Small or narrow matrices: one thread per entry, row-major (no tiles, so a
+// small matrix still spreads over many blocks).
+template <int K, bool COUNTS>
+__global__ void __launch_bounds__(kPwThreads)
+k_pairwise_flat(const float* __restrict__ a, const uint8_t* __restrict__ ca, int64_t N, const float* __restrict__ b,
+           const uint8_t* __restrict__ cb, int64_t M, float* __restrict__ iou, uint8_t* __restrict__ nx,
+           uint32_t flags, uint32_t* status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = N * M;
+    const int64_t stride = (int64_t)gridDim.x * kPwThreads;
+    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
+    int64_t base = (int64_t)blockIdx.x * kPwThreads + (threadIdx.x & ~31);
+    if (base >= total) return;
+    const int64_t e0 = base + lane;
+    int64_t i = e0 / M, j = e0 - (e0 / M) * M;
+    const int64_t di = stride / M, dj = stride - di * M;
+    uint32_t err = 0;
+    for (; base < total; base += stride) {
+        const int64_t e = base + lane;
+        const bool act = e < total;
+        const int n1 = (COUNTS && ca && act) ? (int)ca[i] : K;
+        const int n2 = (COUNTS && cb && act) ? (int)cb[j] : K;
+        const float* pa = a + (act ? i : 0) * 2 * K;
+        const float* pb = b + (act ? j : 0) * 2 * K;
+        float v = 0.f;
+        uint32_t c = 0;
+        const bool hard = act && pw_fast<K, COUNTS>(pa, pb, n1, n2, v, c, err, refine);
+        pw_finish<K>(__ballot_sync(0xffffffffu, hard), pa, pb, n1, n2, refine, v, c, err);
+        if (act) {
+            iou[e] = v;
+            if (nx) nx[e] = (uint8_t)c;
         }
-        if (t == 0) s_nq = 0;
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < kTileRows; ++r) {
-            const int64_t i = i0 + r;
-            const bool v = jv && i < N;
-            const float4 rbx = s_rbox[r];
-            const bool meet = v && !(rbx.z < cbx.x || cbx.z < rbx.x || rbx.w < cbx.y || cbx.w < rbx.y);
-            if (v && !meet) {
-                iou[i * M + j] = 0.f;
-                if (nx) nx[i * M + j] = 0;
-            }
-            const unsigned bal = __ballot_sync(full, meet);
-            int pos = 0;
-            if (lane == 0 && bal) pos = atomicAdd(&s_nq, __popc(bal));
-            pos = __shfl_sync(full, pos, 0);
-            if (meet) s_q[pos + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)((r << 8) | t);
+        i += di;
+        j += dj;
+        if (j >= M) {
+            j -= M;
+            ++i;
         }
-        __syncthreads();
-        const int nq = s_nq;
-        for (int qb = t & ~31; qb < nq; qb += kPwThreads) {
-            const int q = qb + lane;
-            const bool act = q < nq;
-            const int code = act ? (int)s_q[q] : 0;
-            const int64_t i = i0 + (code >> 8), jj = j0 + (code & 0xFF);
-            const int n1 = (COUNTS && ca && act) ? (int)ca[i] : K;
-            const int n2 = (COUNTS && cb && act) ? (int)cb[jj] : K;
-            const float* pa = a + (act ? i : 0) * 2 * K;
-            const float* pb = b + (act ? jj : 0) * 2 * K;
-            float v = 0.f;
-            uint32_t c = 0;
-            const bool hard = act && pw_fast<K, COUNTS>(pa, pb, n1, n2, v, c, err, refine);
-            pw_finish<K>(__ballot_sync(full, hard), pa, pb, n1, n2, refine, v, c, err);
-            if (act) {
-                iou[i * M + jj] = v;
-                if (nx) nx[i * M + jj] = (uint8_t)c;
-            }
-        }
-        __syncthreads(); // the next tile reuses the boxes and the queue
     }
     if (err) atomicOr(status, err);
 }
@@ -138,7 +201,7 @@ constexpr int kSetupThreads = 1024;
 
 __global__ void __launch_bounds__(kSetupThreads)
 k_batched_setup(int S, const int64_t* __restrict__ a_off, const int64_t* __restrict__ b_off,
-                const int64_t* __restrict__ out_off, int64_t tile, uint32_t* __restrict__ counter,
+                const int64_t* __restrict__ out_off, int64_t rows, int64_t cols, uint32_t* __restrict__ counter,
                 int64_t* __restrict__ tile_start, uint32_t* status) {
     __shared__ int64_t part[kSetupThreads];
     const int t = threadIdx.x;
@@ -151,7 +214,7 @@ k_batched_setup(int S, const int64_t* __restrict__ a_off, const int64_t* __restr
         const int64_t E = out_off[s + 1] - out_off[s];
         const bool ok = Ns >= 0 && Ms >= 0 && E == Ns * Ms && a_off[0] == 0 && b_off[0] == 0 && out_off[0] == 0;
         err |= ok ? 0u : kDevBadOffsets;
-        sum += ok ? (E + tile - 1) / tile : 0;
+        sum += ok ? ((Ns + rows - 1) / rows) * ((Ms + cols - 1) / cols) : 0;
     }
     part[t] = sum;
     __syncthreads();
@@ -168,7 +231,7 @@ k_batched_setup(int S, const int64_t* __restrict__ a_off, const int64_t* __restr
         const int64_t Ns = a_off[s + 1] - a_off[s], Ms = b_off[s + 1] - b_off[s];
         const int64_t E = out_off[s + 1] - out_off[s];
         const bool ok = Ns >= 0 && Ms >= 0 && E == Ns * Ms && a_off[0] == 0 && b_off[0] == 0 && out_off[0] == 0;
-        run += ok ? (E + tile - 1) / tile : 0;
+        run += ok ? ((Ns + rows - 1) / rows) * ((Ms + cols - 1) / cols) : 0;
     }
     if (t == kSetupThreads - 1) {
         tile_start[S] = part[t];
@@ -182,12 +245,15 @@ __global__ void k_batched(int S, const int64_t* __restrict__ a_off, const int64_
                           const int64_t* __restrict__ out_off, const float* __restrict__ a,
                           const uint8_t* __restrict__ ca, const float* __restrict__ b, const uint8_t* __restrict__ cb,
                           float* __restrict__ iou, uint8_t* __restrict__ nx, uint32_t* __restrict__ counter,
-                          const int64_t* __restrict__ tile_start, int64_t tile, uint32_t flags, uint32_t* status) {
+                          const int64_t* __restrict__ tile_start, int rows, uint32_t flags, uint32_t* status) {
+    extern __shared__ uint16_t s_q[]; // rows x blockDim.x queue codes
+    __shared__ float4 s_rbox[kMaxTileRows];
     __shared__ int64_t s_tile;
     __shared__ int s_scene;
-    const int lane = threadIdx.x & 31;
+    __shared__ int s_nq;
     const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
     const int64_t total = tile_start[S];
+    const int64_t cols = blockDim.x;
     uint32_t err = 0;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -206,36 +272,13 @@ __global__ void k_batched(int S, const int64_t* __restrict__ a_off, const int64_
         __syncthreads();
         if (t >= total) break;
         const int64_t a0 = a_off[s], b0 = b_off[s], o0 = out_off[s];
-        const int64_t Ms = b_off[s + 1] - b0, E = out_off[s + 1] - o0;
-        const int64_t e0 = (t - tile_start[s]) * tile;
-        const int64_t e1 = min(e0 + tile, E);
-        // warp-uniform steps over the tile: lane l takes entry wbase + l
-        int64_t wbase = e0 + (threadIdx.x & ~31);
-        if (wbase >= e1) continue;
-        int64_t e = wbase + lane;
-        int64_t i = e / Ms, j = e - (e / Ms) * Ms;
-        const int64_t di = (int64_t)blockDim.x / Ms, dj = (int64_t)blockDim.x - di * Ms;
-        for (; wbase < e1; wbase += blockDim.x, e += blockDim.x) {
-            const bool act = e < e1;
-            const int n1 = (COUNTS && ca && act) ? (int)ca[a0 + i] : K;
-            const int n2 = (COUNTS && cb && act) ? (int)cb[b0 + j] : K;
-            const float* pa = a + (act ? a0 + i : 0) * 2 * K;
-            const float* pb = b + (act ? b0 + j : 0) * 2 * K;
-            float v = 0.f;
-            uint32_t c = 0;
-            const bool hard = act && pw_fast<K, COUNTS>(pa, pb, n1, n2, v, c, err, refine);
-            pw_finish<K>(__ballot_sync(0xffffffffu, hard), pa, pb, n1, n2, refine, v, c, err);
-            if (act) {
-                iou[o0 + e] = v;
-                if (nx) nx[o0 + e] = (uint8_t)c;
-            }
-            i += di;
-            j += dj;
-            if (j >= Ms) {
-                j -= Ms;
-                ++i;
-            }
-        }
+        const int64_t Ns = a_off[s + 1] - a0, Ms = b_off[s + 1] - b0;
+        const int64_t cblocks = (Ms + cols - 1) / cols;
+        const int64_t lt = t - tile_start[s];
+        const int64_t rb = lt / cblocks;
+        pw_tile<K, COUNTS>(a + a0 * 2 * K, COUNTS && ca ? ca + a0 : nullptr, Ns, b + b0 * 2 * K,
+                           COUNTS && cb ? cb + b0 : nullptr, Ms, iou + o0, nx ? nx + o0 : nullptr, rb * rows,
+                           (lt - rb * cblocks) * cols, rows, s_rbox, s_q, &s_nq, refine, err);
     }
     if (err) atomicOr(status, err);
 }
@@ -244,6 +287,15 @@ template <int K, bool COUNTS>
 static void pairwise_dispatch(const float* a, const uint8_t* ca, int64_t N, const float* b, const uint8_t* cb,
                               int64_t M, float* iou, uint8_t* nx, uint32_t flags, cudaStream_t s) {
     const int64_t tiles = ((N + kTileRows - 1) / kTileRows) * ((M + kPwThreads - 1) / kPwThreads);
+    if (M < kFlatMaxCols || tiles < (int64_t)sm_count() * 2) {
+        // narrow or small: one thread per entry spreads over more blocks
+        int64_t blocks = (N * M + kPwThreads - 1) / kPwThreads;
+        const int64_t cap = (int64_t)sm_count() * 32;
+        if (blocks > cap) blocks = cap;
+        k_pairwise_flat<K, COUNTS><<<(unsigned)blocks, kPwThreads, 0, s>>>(a, ca, N, b, cb, M, iou, nx, flags,
+                                                                            device_status_ptr());
+        return;
+    }
     int64_t blocks = tiles;
     const int64_t cap = (int64_t)sm_count() * 8;
     if (blocks > cap) blocks = cap;
@@ -265,14 +317,22 @@ dgal_status launch_pairwise(const float* a, const uint8_t* ca, int64_t N, const 
     return check_launch("pairwise");
 }
 
+// Tile shape of the ragged batch: cfg.threads columns x (cfg.tile /
+// cfg.threads) rows, 1 to kMaxTileRows.
+static int batched_rows(const BatchedConfig& cfg) {
+    int r = cfg.tile / (cfg.threads > 0 ? cfg.threads : 1);
+    return r < 1 ? 1 : (r > kMaxTileRows ? kMaxTileRows : r);
+}
+
 template <int K, bool COUNTS>
 static void batched_dispatch(int S, const int64_t* a_off, const int64_t* b_off, const int64_t* out_off,
                              const float* a, const uint8_t* ca, const float* b, const uint8_t* cb, float* iou,
                              uint8_t* nx, uint32_t* counter, const int64_t* tile_start, uint32_t flags,
                              const BatchedConfig& cfg, cudaStream_t s) {
     const unsigned grid = (unsigned)(sm_count() * cfg.blocks_sm);
-    k_batched<K, COUNTS><<<grid, cfg.threads, 0, s>>>(S, a_off, b_off, out_off, a, ca, b, cb, iou, nx, counter,
-                                                       tile_start, (int64_t)cfg.tile, flags, device_status_ptr());
+    const int rows = batched_rows(cfg);
+    k_batched<K, COUNTS><<<grid, cfg.threads, (size_t)rows * cfg.threads * sizeof(uint16_t), s>>>(
+        S, a_off, b_off, out_off, a, ca, b, cb, iou, nx, counter, tile_start, rows, flags, device_status_ptr());
 }
 
 dgal_status launch_batched(int S, const int64_t* a_off, const int64_t* b_off, const int64_t* out_off,
@@ -281,8 +341,8 @@ dgal_status launch_batched(int S, const int64_t* a_off, const int64_t* b_off, co
     if (!device_status_ptr()) return fail(DGAL_ERR_CUDA, "device status word unavailable");
     uint32_t* counter = static_cast<uint32_t*>(ws);
     int64_t* tile_start = reinterpret_cast<int64_t*>(static_cast<char*>(ws) + 16);
-    k_batched_setup<<<1, kSetupThreads, 0, s>>>(S, a_off, b_off, out_off, (int64_t)cfg.tile, counter, tile_start,
-                                                device_status_ptr());
+    k_batched_setup<<<1, kSetupThreads, 0, s>>>(S, a_off, b_off, out_off, (int64_t)batched_rows(cfg),
+                                                (int64_t)cfg.threads, counter, tile_start, device_status_ptr());
     dgal_status st = check_launch("batched setup");
     if (st != DGAL_OK) return st;
     const bool counts = ca || cb;
