@@ -676,8 +676,11 @@ def main():
         ds = {k: v[:sample] for k, v in d.items()}
         cpu_oracle_run(ds, threads)
         secs = cpu_oracle_run(ds, threads)
+        one = min(sample, 20_000)  # single-thread rate on a smaller sample (about a second)
+        secs1 = cpu_oracle_run({k: v[:one] for k, v in d.items()}, 1)
         cpu = {"value": sample / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"first {sample} pairs of the workload, fwd+bwd, FP64 C oracle on all host cores"}
+               "sample": f"first {sample} pairs of the workload, fwd+bwd, FP64 C oracle on all host cores",
+               "single_thread": {"value": one / secs1, "unit": UNIT, "cores": 1, "sample": f"first {one} pairs"}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
