@@ -700,7 +700,7 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
         Lf = fmaxf(Lf, (v < n1) ? fmaxf(fabsf(px[v] - ox), fabsf(py[v] - oy)) : 0.f);
         Lf = fmaxf(Lf, (v < n2) ? fmaxf(fabsf(qx[v] - ox), fabsf(qy[v] - oy)) : 0.f);
     }
-    const double thr = (double)kDegenRel * (double)Lf * (double)Lf;
+    const float thr32 = kDegenRel * Lf * Lf, route32 = kRouteRel * Lf * Lf;
 
     // orientation tests: index q < KK is S(i,j), KK <= q < 2KK is T(i,j)
     M posS = 0, negS = 0, posT = 0, negT = 0;
@@ -718,15 +718,23 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
         const float Bx = isT ? sel<K>(px, i1) : sel<K>(qx, j1), By = isT ? sel<K>(py, i1) : sel<K>(qy, j1);
         const float Px = isT ? sel<K>(qx, j) : sel<K>(px, i), Py = isT ? sel<K>(qy, j) : sel<K>(py, i);
         // FP32 in the local frame first: beyond kRouteRel L^2 its sign is
-        // exact (see kRouteRel); only the lanes below take the FP64 test
-        double v = (double)orient32nc(Ax - ox, Ay - oy, Bx - ox, By - oy, Px - ox, Py - oy);
-        const bool need = refine && valid && !(fabs(v) > (double)kRouteRel * (double)Lf * (double)Lf);
+        // exact (see kRouteRel); only the lanes below take the FP64 test.
+        // Everything else stays in FP32 (GB300's FP64 rate is a small
+        // fraction of its FP32 rate, and many warps run this at once).
+        float v = orient32nc(Ax - ox, Ay - oy, Bx - ox, By - oy, Px - ox, Py - oy);
+        bool pos = v > 0.f, neg = v < 0.f;
+        const bool need = refine && valid && !(fabsf(v) > route32);
         if (__any_sync(full, need)) {
-            if (need) v = orient64(Ax, Ay, Bx, By, Px, Py);
+            if (need) {
+                const double v64 = orient64(Ax, Ay, Bx, By, Px, Py);
+                pos = v64 > 0.0;
+                neg = v64 < 0.0;
+                v = (float)v64;
+            }
         }
-        vf[r] = (float)v;
-        deg |= valid && fabs(v) <= thr;
-        const unsigned bp = __ballot_sync(full, valid && v > 0.0), bn = __ballot_sync(full, valid && v < 0.0);
+        vf[r] = v;
+        deg |= valid && !(fabsf(v) > thr32);
+        const unsigned bp = __ballot_sync(full, valid && pos), bn = __ballot_sync(full, valid && neg);
         if constexpr (K == 4) {
             posS = bp & 0xFFFFu;
             negS = bn & 0xFFFFu;
@@ -958,7 +966,9 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
         }
         const double X64 = ((double)fx0 - (double)ox) + t64 * ((double)fx1 - (double)fx0);
         const double Y64 = ((double)fy0 - (double)oy) + t64 * ((double)fy1 - (double)fy0);
-        const double mx = warp_sum(live ? X64 : 0.0) / (double)m, my = warp_sum(live ? Y64 : 0.0) / (double)m;
+        // about the FP32 centroid: any origin gives the same area, and one
+        // within the polygon keeps the products small
+        const double mx = (double)mxf, my = (double)myf;
         const double nxp = __shfl_sync(full, X64, nl), nyp = __shfl_sync(full, Y64, nl);
         const double tm = live ? __dsub_rn(__dmul_rn(X64 - mx, nyp - my), __dmul_rn(Y64 - my, nxp - mx)) : 0.0;
         double t2 = 0.0;
