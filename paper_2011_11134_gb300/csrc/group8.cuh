@@ -71,6 +71,7 @@ __device__ __forceinline__ float sel8(const float (&v)[8], uint32_t i) {
 struct Lane {
     float ax, ay, eax, eay;
     float bx[8], by[8], ebx[8], eby[8];
+    float bxr, byr, ebxr, ebyr; // the lane's own P2 vertex r and edge r (= bx[r], ..., loaded directly)
     int n1, n2, r;
 };
 
@@ -97,6 +98,18 @@ __device__ __forceinline__ void load_lane(const float* __restrict__ p1, const fl
         const bool wrap = j + 1 >= n2;
         L.ebx[j] = (wrap ? L.bx[0] : L.bx[(j + 1) & 7]) - L.bx[j];
         L.eby[j] = (wrap ? L.by[0] : L.by[(j + 1) & 7]) - L.by[j];
+    }
+    {
+        // the lane's own P2 vertex and edge, with the arithmetic of the loop
+        // above (so the values equal bx[r], by[r], ebx[r], eby[r])
+        const int rr2 = (r < n2) ? r : 0;
+        const int rn2 = (rr2 + 1 < n2) ? rr2 + 1 : 0;
+        const float2 q0 = __ldg(reinterpret_cast<const float2*>(p2) + rr2);
+        const float2 q1 = __ldg(reinterpret_cast<const float2*>(p2) + rn2);
+        L.bxr = q0.x - ox;
+        L.byr = q0.y - oy;
+        L.ebxr = (q1.x - ox) - L.bxr;
+        L.ebyr = (q1.y - oy) - L.byr;
     }
     L.n1 = n1;
     L.n2 = n2;
@@ -363,7 +376,7 @@ __device__ __forceinline__ uint32_t bwd_group(const Lane& L, Adj& adj, uint32_t 
             const float bx = sel8(L.bx, j), by = sel8(L.by, j), ebx = sel8(L.ebx, j), eby = sel8(L.eby, j);
             const float dx = L.ax - bx, dy = L.ay - by;
             const float S = ebx * dy - eby * dx, D = L.eax * eby - L.eay * ebx;
-            const float t = S / D;
+            const float t = S * __fdividef(1.0f, D);
             t0 = fminf(t0, t);
             t1 = fmaxf(t1, t);
         }
@@ -372,8 +385,7 @@ __device__ __forceinline__ uint32_t bwd_group(const Lane& L, Adj& adj, uint32_t 
     t1 = ((in1 >> rn1) & 1u) ? 1.f : t1;
     // P2 edge r: parameters of its crossings, with the P1 edges' data fetched
     // from their lanes
-    const float bxr = sel8(L.bx, (uint32_t)r), byr = sel8(L.by, (uint32_t)r);
-    const float ebxr = sel8(L.ebx, (uint32_t)r), ebyr = sel8(L.eby, (uint32_t)r);
+    const float bxr = L.bxr, byr = L.byr, ebxr = L.ebxr, ebyr = L.ebyr;
     float u0 = kInf, u1 = -kInf;
     uint64_t cx = colX;
 #pragma unroll
@@ -386,7 +398,7 @@ __device__ __forceinline__ uint32_t bwd_group(const Lane& L, Adj& adj, uint32_t 
         if (has) {
             const float dx = ax - bxr, dy = ay - byr;
             const float T = eay * dx - eax * dy, D = eax * ebyr - eay * ebxr;
-            const float u = -T / D;
+            const float u = -T * __fdividef(1.0f, D);
             u0 = fminf(u0, u);
             u1 = fmaxf(u1, u);
         }
