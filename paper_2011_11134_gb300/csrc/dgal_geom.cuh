@@ -723,7 +723,10 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
         // fraction of its FP32 rate, and many warps run this at once).
         float v = orient32nc(Ax - ox, Ay - oy, Bx - ox, By - oy, Px - ox, Py - oy);
         bool pos = v > 0.f, neg = v < 0.f;
-        const bool need = refine && valid && !(fabsf(v) > route32);
+        // a point equal to an endpoint of the edge has orientation exactly 0,
+        // and the uncontracted FP32 form above gives exactly 0 there too
+        const bool coinc = (Px == Ax && Py == Ay) || (Px == Bx && Py == By);
+        const bool need = refine && valid && !coinc && !(fabsf(v) > route32);
         if (__any_sync(full, need)) {
             if (need) {
                 const double v64 = orient64(Ax, Ay, Bx, By, Px, Py);
