@@ -485,6 +485,9 @@ def main():
         d = W.loss_pairs_1m(seed=seed, n=args.n)
     n = d["p1"].shape[0]
     K = d["p1"].shape[1]
+    workload_name = WORKLOADS[args.workload]
+    if args.workload in ("loss1m", "convex") and n != (1_000_000 if args.workload == "loss1m" else 4_000_000):
+        workload_name += f" (resized by --n to {n:,} pairs)"
     p1 = torch.from_numpy(d["p1"]).to(dev)
     p2 = torch.from_numpy(d["p2"]).to(dev)
     c1 = torch.from_numpy(d["c1"]).to(dev) if "c1" in d else None
@@ -662,7 +665,7 @@ def main():
     # (profiles/paired_k4_fwd_bwd_4m_ncu_full.md), scaled to this launch
     traffic = None
     if K == 4 and c1 is None and args.workload == "loss1m":
-        traffic = (74.2 if dom == "forward" else 130.8) * n
+        traffic = (74.3 if dom == "forward" else 130.8) * n
     roofline = {"bound": "hbm", "kernel": f"k_paired_{'fwd' if dom == 'forward' else 'bwd'}<{K}>", "achieved": ach,
                 "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
                 "traffic_source": "ncu capture of 4M pairs, per pair x pairs" if traffic else None,
@@ -685,7 +688,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "pairs_per_gpu": n, "K": K,
+        "config": {"workload": workload_name, "pairs_per_gpu": n, "K": K,
                    "parallelism": f"replicas x{world}",
                    "l2": f"flushed between steps (256 MiB write outside the timed events); inputs {2 * n * 8 * K / 1e6:.0f} MB"},
         "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": plain_ms / args.steps,
