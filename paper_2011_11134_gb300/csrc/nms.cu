@@ -9,19 +9,28 @@
 //                    (its rank in the visiting order) and copies the polygon
 //                    to that slot, so no sort is needed and the order is
 //                    deterministic;
-//   2. k_nms_mask    one warp per (row a, 64-column word c >= a / 64) of the
-//                    visiting-order matrix computes IoU(a, b) for b > a in the
-//                    word's 64 columns (pw_entry.cuh, the same FP32 IoU as
-//                    dgal_iou_pairwise) and stores the word of bits IoU > thr,
-//                    two 32-lane ballots;
-//   3. k_nms_greedy  one block walks the words of 64 rows at a time: thread 0
-//                    resolves the suppression inside the 64-row block from
-//                    its diagonal word, then every (kept row, later word)
-//                    pair goes to its own thread, which ORs the word into the
-//                    removal bitmap held in shared memory, so the block's
-//                    loads are in flight together.  The next diagonal is
-//                    fetched while the current rows are applied.  Only kept
-//                    rows are ever read.
+//   2. k_nms_mask    one block per tile of 32 rows x 128 columns (two 64-bit
+//                    words per row) of the visiting-order matrix, on or right
+//                    of the rows' diagonal word: the pairwise tile
+//                    (pw_entry.cuh: exact box test on every entry b > a, the
+//                    same FP32 IoU as dgal_iou_pairwise on the queued ones)
+//                    sets bit b of row a's word when IoU(a, b) > thr.  The
+//                    tile stores its words and, for the diagonal 64 x 64
+//                    block, also its transpose: for each row b, the rows a < b
+//                    of its 64-row block that suppress it;
+//   3. k_nms_greedy  one block walks the rows 64 at a time.  Warp 0 decides
+//                    the block's rows from the transposed diagonal in a few
+//                    ballot rounds (a row is kept once none of its
+//                    suppressors is kept or undecided, suppressed once one of
+//                    them is kept; every round decides at least the lowest
+//                    undecided row), then the kept rows' later words are ORed
+//                    into the removal bitmap held in shared memory.  What a
+//                    64-row block reads (transposed diagonal, visiting order,
+//                    the rows' next 32 words) does not depend on the outcome,
+//                    so asynchronous copies (cp.async) bring it into a ring of
+//                    shared-memory stages kNmsStages - 1 blocks ahead, and the
+//                    walk does not wait on memory; words further right are
+//                    loaded for kept rows only.
 #include <cmath>
 
 #include "dgal_geom.cuh"
@@ -30,19 +39,22 @@
 
 namespace dgal {
 
-constexpr int64_t kNmsMaxBoxes = 131072; // removal bitmap: 2048 words = 16 KB of shared memory
-constexpr int kNmsThreads = 128;         // rank and mask kernels: 4 warps, one box / row each
+constexpr int64_t kNmsMaxBoxes = 131072; // removal bitmap: 2048 words = 16 KB of shared memory (+ 67 KB of stages)
+constexpr int kNmsThreads = 128;         // rank kernel: 4 warps, one box each
 constexpr int kNmsRowsPerBlock = kNmsThreads / 32;
-constexpr int kNmsGreedyThreads = 1024;
+constexpr int kNmsGreedyThreads = 1024;  // 32 warps: warp k holds rows k and k + 32 of a 64-row block
 
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct NmsLayout {
-    size_t order, boxes, counts, mask, total;
+    size_t order, boxes, counts, mask, sup, total;
 };
 
 // Workspace: order int32 [N] | polygons in visiting order float [N][K][2] |
-// their counts uint8 [N] | suppression words uint64 [N][W], W = ceil(N / 64).
+// their counts uint8 [N] | suppression words uint64 [N][W], W = ceil(N / 64) |
+// transposed diagonal uint32 [N][2] (word of row b, bit a mod 64: a < b in
+// the same 64-row block suppresses b; half h written by the tile of rows
+// 64 (b / 64) + 32 h).
 static NmsLayout nms_layout(int64_t N, int K) {
     const int64_t W = (N + 63) / 64;
     NmsLayout L;
@@ -55,6 +67,8 @@ static NmsLayout nms_layout(int64_t N, int K) {
     off += align256((size_t)N);
     L.mask = off;
     off += align256((size_t)N * (size_t)W * 8);
+    L.sup = off;
+    off += align256((size_t)N * 8);
     L.total = off;
     return L;
 }
@@ -85,96 +99,170 @@ k_nms_rank(const float* __restrict__ boxes, const uint8_t* __restrict__ counts, 
     if (counts && lane == 0) scounts[r] = counts[i];
 }
 
-template <int K, bool COUNTS>
-__global__ void __launch_bounds__(kNmsThreads)
-k_nms_mask(const float* __restrict__ sboxes, const uint8_t* __restrict__ scounts, int64_t N, int64_t W, float thr,
-           uint64_t* __restrict__ mask, uint32_t flags, uint32_t* status) {
-    const int lane = threadIdx.x & 31;
-    const int64_t a = (int64_t)blockIdx.x * kNmsRowsPerBlock + (threadIdx.x >> 5);
-    const int64_t c = blockIdx.y;
-    if (a >= N || (a >> 6) > c) return; // warp-uniform: words left of the diagonal are never read
-    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
-    const int n1 = COUNTS ? (int)scounts[a] : K;
-    const float* pa = sboxes + a * 2 * K;
-    uint32_t err = 0;
-    uint32_t half[2];
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-        const int64_t b = c * 64 + h * 32 + lane;
-        const bool act = b > a && b < N;
-        const int n2 = (COUNTS && act) ? (int)scounts[b] : K;
-        const float* pb = sboxes + (act ? b : 0) * 2 * K;
-        float v = 0.f;
-        uint32_t nxv = 0;
-        const bool hard = act && pw_fast<K, COUNTS>(pa, pb, n1, n2, v, nxv, err, refine);
-        pw_finish<K>(__ballot_sync(0xffffffffu, hard), pa, pb, n1, n2, refine, v, nxv, err);
-        half[h] = __ballot_sync(0xffffffffu, act && v > thr);
+// Tile output of the suppression mask: bit (b - j0) of the tile's two words
+// of row a is set when IoU(a, b) > thr, and for a, b in the same 64-row block
+// bit a mod 32 of column b's transposed word.  Only entries right of the
+// diagonal are wanted (row a is suppressed by earlier rows only).  Disjoint
+// pairs have IoU 0, which exceeds only a negative threshold.
+struct NmsBitsOut {
+    unsigned long long* bits; // shared memory: 2 words per tile row
+    unsigned* tbits;          // shared memory: 1 transposed half-word per tile column
+    int64_t i0, j0;
+    float thr;
+    __device__ __forceinline__ bool wanted(int64_t i, int64_t j) const { return j > i; }
+    __device__ __forceinline__ void set(int64_t i, int64_t j) const {
+        atomicOr(&bits[(i - i0) * 2 + ((j - j0) >> 6)], 1ull << ((j - j0) & 63));
+        if ((i >> 6) == (j >> 6)) atomicOr(&tbits[j - j0], 1u << (i & 31));
     }
-    if (lane == 0) mask[a * W + c] = (uint64_t)half[0] | ((uint64_t)half[1] << 32);
+    __device__ __forceinline__ void disjoint(int64_t i, int64_t j) const {
+        if (0.f > thr) set(i, j);
+    }
+    __device__ __forceinline__ void put(int64_t i, int64_t j, float v, uint32_t) const {
+        if (v > thr) set(i, j);
+    }
+};
+
+constexpr int kNmsTileRows = 32; // rows of a mask tile; its kPwThreads = 128 columns are two words
+
+template <int K, bool COUNTS>
+__global__ void __launch_bounds__(kPwThreads)
+k_nms_mask(const float* __restrict__ sboxes, const uint8_t* __restrict__ scounts, int64_t N, int64_t W, float thr,
+           uint64_t* __restrict__ mask, uint32_t* __restrict__ sup, uint32_t flags, uint32_t* status) {
+    __shared__ float4 s_rbox[kNmsTileRows];
+    __shared__ uint16_t s_q[kNmsTileRows * kPwThreads];
+    __shared__ int s_nq;
+    __shared__ unsigned long long s_bits[kNmsTileRows * 2];
+    __shared__ unsigned s_tbits[kPwThreads];
+    const int t = threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.y * kNmsTileRows, w0 = 2 * (int64_t)blockIdx.x, j0 = w0 * 64;
+    // all the tile's rows share the diagonal word i0 / 64 (tiles are 32-row
+    // aligned); words left of it are never read
+    const int64_t c0 = i0 >> 6;
+    if (w0 + 1 < c0) return; // block-uniform
+    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
+    // ordered before any put by pw_tile's first barrier
+    if (t < kNmsTileRows * 2) s_bits[t] = 0ull;
+    s_tbits[t] = 0u;
+    uint32_t err = 0;
+    const NmsBitsOut out{s_bits, s_tbits, i0, j0, thr};
+    pw_tile<K, COUNTS>(sboxes, scounts, N, sboxes, scounts, N, i0, j0, kNmsTileRows, s_rbox, s_q, &s_nq, refine, err,
+                       out);
+    // pw_tile ends with a barrier: the bits are final
+    if (t < kNmsTileRows * 2) {
+        const int64_t a = i0 + (t >> 1), w = w0 + (t & 1);
+        if (a < N && w < W && w >= c0) mask[a * W + w] = s_bits[t];
+    }
+    const int64_t j = j0 + t;
+    if (j < N && (j >> 6) == c0) sup[j * 2 + ((i0 >> 5) & 1)] = s_tbits[t];
     if (err) atomicOr(status, err);
 }
 
+// What the greedy pass reads for one 64-row block: the rows' words
+// c + 1 .. c + 32, their transposed diagonal words and their box indices.
+struct NmsStage {
+    uint64_t near[64][32];
+    uint64_t sup[64];
+    int32_t ord[64];
+};
+constexpr int kNmsStages = 4;
+
+__device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes, bool pred) {
+    // src-size 0 copies nothing and fills the destination with zeros
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(pred ? 8 : 0) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(pred ? 4 : 0) : "memory");
+}
+
 __global__ void __launch_bounds__(kNmsGreedyThreads)
-k_nms_greedy(const int32_t* __restrict__ order, const uint64_t* __restrict__ mask, int64_t N, int64_t W,
-             int64_t* __restrict__ keep, int64_t* __restrict__ num_keep) {
-    extern __shared__ unsigned long long removed[]; // W words: bit b of word w = row 64 w + b is suppressed
-    __shared__ uint64_t diag[2][64];
+k_nms_greedy(const int32_t* __restrict__ order, const uint64_t* __restrict__ mask, const uint64_t* __restrict__ sup,
+             int64_t N, int64_t W, int64_t* __restrict__ keep, int64_t* __restrict__ num_keep) {
+    extern __shared__ __align__(16) unsigned char g_smem[];
+    NmsStage* stage = reinterpret_cast<NmsStage*>(g_smem);
+    // W words: bit b of word w = row 64 w + b is suppressed
+    unsigned long long* removed = reinterpret_cast<unsigned long long*>(g_smem + kNmsStages * sizeof(NmsStage));
     __shared__ uint64_t s_kept;
     __shared__ int s_rows[64]; // the kept rows of the current block, in order
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
     for (int64_t w = t; w < W; w += blockDim.x) removed[w] = 0ull;
-    if (t < 64) diag[0][t] = (t < N) ? mask[(int64_t)t * W] : 0ull;
-    __syncthreads();
+    // copies of block c into its stage (none past the last block), one group per block
+    auto issue = [&](int64_t c) {
+        if (c < W) {
+            NmsStage& st = stage[c % kNmsStages];
+            const int64_t r0 = c * 64 + wp, r1 = r0 + 32, w = c + 1 + lane;
+            cp_async(&st.near[wp][lane], (r0 < N && w < W) ? mask + r0 * W + w : mask, 8, r0 < N && w < W);
+            cp_async(&st.near[wp + 32][lane], (r1 < N && w < W) ? mask + r1 * W + w : mask, 8, r1 < N && w < W);
+            const int64_t r = c * 64 + (t & 63);
+            if (t < 64) cp_async(&st.sup[t], r < N ? sup + r : sup, 8, r < N);
+            else if (t < 128) cp_async(&st.ord[t - 64], r < N ? order + r : order, 4, r < N);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    for (int c = 0; c < kNmsStages - 1; ++c) issue(c);
     int64_t count = 0;
     for (int64_t c = 0; c < W; ++c) {
-        const int buf = (int)(c & 1);
-        // the next block's diagonal words do not depend on this block's outcome
-        uint64_t nd = 0ull;
-        const int64_t rn = (c + 1) * 64 + t;
-        if (t < 64 && c + 1 < W && rn < N) nd = mask[rn * W + c + 1];
-        if (t == 0) {
+        // block c's group is the oldest of the kNmsStages - 1 in flight
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kNmsStages - 2) : "memory");
+        __syncthreads(); // every thread's copies of block c, the removal words, the previous block done
+        issue(c + kNmsStages - 1); // into the stage the previous block used
+        const NmsStage& st = stage[c % kNmsStages];
+        if (wp == 0) {
             const int64_t rows = N - c * 64;
             const uint64_t valid = rows >= 64 ? ~0ull : ((1ull << rows) - 1ull);
-            uint64_t cur = removed[c] | ~valid;
-            uint64_t kept = 0ull;
-            uint64_t avail = ~cur;
-            while (avail) {
-                const int r = __ffsll((long long)avail) - 1;
-                kept |= 1ull << r;
-                cur |= diag[buf][r]; // rows of this block that row r suppresses (all above r)
-                avail = (r == 63) ? 0ull : (~cur & (~0ull << (r + 1)));
+            // suppressors of rows 64 c + lane and 64 c + 32 + lane: only bits below the row count
+            const uint64_t sb0 = st.sup[lane] & ((1ull << lane) - 1ull);
+            const uint64_t sb1 = st.sup[lane + 32] & ((1ull << (lane + 32)) - 1ull);
+            uint64_t und = ~removed[c] & valid, kept = 0ull; // warp-uniform
+            while (und) {
+                const bool u0 = (und >> lane) & 1ull, u1 = (und >> (lane + 32)) & 1ull;
+                const uint64_t live = und | kept;
+                const uint64_t k = (uint64_t)__ballot_sync(0xffffffffu, u0 && !(sb0 & live)) |
+                                   ((uint64_t)__ballot_sync(0xffffffffu, u1 && !(sb1 & live)) << 32);
+                const uint64_t x = (uint64_t)__ballot_sync(0xffffffffu, u0 && (sb0 & kept)) |
+                                   ((uint64_t)__ballot_sync(0xffffffffu, u1 && (sb1 & kept)) << 32);
+                kept |= k;
+                und &= ~(k | x);
             }
-            s_kept = kept;
+            if (lane == 0) s_kept = kept;
         }
         __syncthreads();
         const uint64_t kept = s_kept;
         if (t < 64 && ((kept >> t) & 1ull)) {
             const int slot = __popcll(kept & ((1ull << t) - 1ull));
-            keep[count + slot] = (int64_t)order[c * 64 + t];
+            keep[count + slot] = (int64_t)st.ord[t];
             s_rows[slot] = t;
         }
         const int nk = __popcll(kept);
         count += nk;
-        __syncthreads();
-        // every (kept row, later word) pair on its own thread, so all the
-        // block's loads are in flight together; shared-memory OR to combine
-        const int nw = (int)(W - c - 1), pairs = nk * nw; // W <= 2048: 32-bit indices
-        for (int idx = t; idx < pairs; idx += blockDim.x) {
-            const int k = idx / nw, w = (int)c + 1 + (idx - k * nw);
-            const uint64_t v = mask[(c * 64 + s_rows[k]) * W + w];
-            if (v) atomicOr(&removed[w], (unsigned long long)v);
+        // near words of the kept rows (zero past the last word)
+        const uint64_t v = (((kept >> wp) & 1ull) ? st.near[wp][lane] : 0ull) |
+                           (((kept >> (wp + 32)) & 1ull) ? st.near[wp + 32][lane] : 0ull);
+        if (v) atomicOr(&removed[c + 1 + lane], (unsigned long long)v);
+        // words c + 33 .. W - 1: every (kept row, word) pair on its own thread
+        const int nfar = (int)(W - c - 33); // W <= 2048: 32-bit indices
+        if (nfar > 0) {
+            __syncthreads(); // s_rows
+            for (int idx = t; idx < nk * nfar; idx += blockDim.x) {
+                const int kk = idx / nfar, w = (int)c + 33 + (idx - kk * nfar);
+                const uint64_t f = mask[(c * 64 + s_rows[kk]) * W + w];
+                if (f) atomicOr(&removed[w], (unsigned long long)f);
+            }
         }
-        if (t < 64) diag[buf ^ 1][t] = nd;
-        __syncthreads();
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (t == 0) *num_keep = count;
 }
 
+static size_t nms_greedy_smem(int64_t W) { return kNmsStages * sizeof(NmsStage) + (size_t)W * 8; }
+
 template <int K, bool COUNTS>
 static void nms_mask_dispatch(const float* sboxes, const uint8_t* scounts, int64_t N, int64_t W, float thr,
-                              uint64_t* mask, uint32_t flags, cudaStream_t s) {
-    const dim3 grid((unsigned)((N + kNmsRowsPerBlock - 1) / kNmsRowsPerBlock), (unsigned)W);
-    k_nms_mask<K, COUNTS><<<grid, kNmsThreads, 0, s>>>(sboxes, scounts, N, W, thr, mask, flags, device_status_ptr());
+                              uint64_t* mask, uint32_t* sup, uint32_t flags, cudaStream_t s) {
+    // x: pairs of words (128 columns), y: 32-row tiles; N <= kNmsMaxBoxes keeps y <= 4096
+    const dim3 grid((unsigned)((N + kPwThreads - 1) / kPwThreads), (unsigned)((N + kNmsTileRows - 1) / kNmsTileRows));
+    k_nms_mask<K, COUNTS><<<grid, kPwThreads, 0, s>>>(sboxes, scounts, N, W, thr, mask, sup, flags,
+                                                       device_status_ptr());
 }
 
 static dgal_status launch_nms(const float* boxes, const uint8_t* counts, const float* scores, int64_t N, int K,
@@ -187,6 +275,7 @@ static dgal_status launch_nms(const float* boxes, const uint8_t* counts, const f
     float* sboxes = reinterpret_cast<float*>(base + L.boxes);
     uint8_t* scounts = reinterpret_cast<uint8_t*>(base + L.counts);
     uint64_t* mask = reinterpret_cast<uint64_t*>(base + L.mask);
+    uint32_t* sup = reinterpret_cast<uint32_t*>(base + L.sup);
     const int64_t W = (N + 63) / 64;
     const unsigned rank_grid = (unsigned)((N + kNmsRowsPerBlock - 1) / kNmsRowsPerBlock);
     if (K == 4) k_nms_rank<4><<<rank_grid, kNmsThreads, 0, s>>>(boxes, counts, scores, N, order, sboxes, scounts);
@@ -194,15 +283,19 @@ static dgal_status launch_nms(const float* boxes, const uint8_t* counts, const f
     dgal_status st = check_launch("nms rank");
     if (st != DGAL_OK) return st;
     if (K == 4) {
-        if (counts) nms_mask_dispatch<4, true>(sboxes, scounts, N, W, thr, mask, flags, s);
-        else nms_mask_dispatch<4, false>(sboxes, scounts, N, W, thr, mask, flags, s);
+        if (counts) nms_mask_dispatch<4, true>(sboxes, scounts, N, W, thr, mask, sup, flags, s);
+        else nms_mask_dispatch<4, false>(sboxes, scounts, N, W, thr, mask, sup, flags, s);
     } else {
-        if (counts) nms_mask_dispatch<8, true>(sboxes, scounts, N, W, thr, mask, flags, s);
-        else nms_mask_dispatch<8, false>(sboxes, scounts, N, W, thr, mask, flags, s);
+        if (counts) nms_mask_dispatch<8, true>(sboxes, scounts, N, W, thr, mask, sup, flags, s);
+        else nms_mask_dispatch<8, false>(sboxes, scounts, N, W, thr, mask, sup, flags, s);
     }
     st = check_launch("nms mask");
     if (st != DGAL_OK) return st;
-    k_nms_greedy<<<1, kNmsGreedyThreads, (size_t)W * 8, s>>>(order, mask, N, W, keep, num_keep);
+    const size_t smem = nms_greedy_smem(W);
+    cudaError_t e = cudaFuncSetAttribute(k_nms_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return fail(DGAL_ERR_CUDA, "nms greedy shared memory (%zu bytes): %s", smem, cudaGetErrorString(e));
+    k_nms_greedy<<<1, kNmsGreedyThreads, smem, s>>>(order, mask, reinterpret_cast<const uint64_t*>(sup), N, W, keep,
+                                                    num_keep);
     return check_launch("nms greedy");
 }
 

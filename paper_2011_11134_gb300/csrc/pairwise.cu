@@ -34,104 +34,16 @@ constexpr int kMaxTileRows = 32;
 // entries, so more of its warps clip at once).
 constexpr int kTileRows = 32;
 
-// Axis-aligned bounding box (min x, min y, max x, max y) of a polygon's first
-// n vertices; a count outside [3, K] gives a box that meets every box, so the
-// entry reaches pw_fast, which reports the count.
-template <int K, bool COUNTS> __device__ __forceinline__ float4 poly_box(const float* __restrict__ p, int n) {
-    if (COUNTS && (n < 3 || n > K)) {
-        const float inf = __int_as_float(0x7f800000);
-        return make_float4(-inf, -inf, inf, inf);
-    }
-    float x[K], y[K];
-    load_poly<K>(p, x, y);
-    float4 r = make_float4(x[0], y[0], x[0], y[0]);
-#pragma unroll
-    for (int v = 1; v < K; ++v) {
-        const bool on = !COUNTS || v < n;
-        r.x = on ? fminf(r.x, x[v]) : r.x;
-        r.y = on ? fminf(r.y, y[v]) : r.y;
-        r.z = on ? fmaxf(r.z, x[v]) : r.z;
-        r.w = on ? fmaxf(r.w, y[v]) : r.w;
-    }
-    return r;
-}
+// Blocks per SM the K = 4 tile kernel is compiled for (registers <= 65536 /
+// (128 x this)); K = 8 holds its polygons in registers and takes 1.
+constexpr int kPwMinBlocks = 5;
 
-// One tile of rows [i0, i0 + R) x columns [j0, j0 + blockDim.x) of an N x M
-// matrix (a, b: the matrix's row and column polygons; iou, nx: its outputs):
-//   1. thread c computes the bounding box of column j0 + c, threads < R those
-//      of the tile's rows (shared memory);
-//   2. every entry is tested on the boxes (exact comparisons of the float
-//      inputs); a disjoint pair has IoU 0 and nx 0 by definition and is
-//      written at once (consecutive threads, consecutive columns), the others
-//      are queued in shared memory (s_q, codes r << 8 | c);
-//   3. the block's warps clip the queued entries densely (pw_fast, with the
-//      warp-cooperative finish for the ones it hands back).
-// In bird's-eye scenes about 2% of the entries have meeting boxes; without the
-// queue a warp runs the clip whenever one of its 32 entries needs it.  Every
-// thread of the block calls this (it has block barriers).
+// One N x M matrix: one block per tile of kTileRows x kPwThreads entries
+// (pw_tile).  Without a loop over tiles the kernel holds fewer registers, so
+// more blocks share an SM; the tile count fits a 1-D grid for any matrix whose
+// outputs fit in memory.
 template <int K, bool COUNTS>
-__device__ __forceinline__ void pw_tile(const float* __restrict__ a, const uint8_t* __restrict__ ca, int64_t N,
-                                        const float* __restrict__ b, const uint8_t* __restrict__ cb, int64_t M,
-                                        float* __restrict__ iou, uint8_t* __restrict__ nx, int64_t i0, int64_t j0,
-                                        int R, float4* s_rbox, uint16_t* s_q, int* s_nq, bool refine,
-                                        uint32_t& err) {
-    constexpr unsigned full = 0xffffffffu;
-    const int t = threadIdx.x, lane = t & 31, C = blockDim.x;
-    const float inf = __int_as_float(0x7f800000);
-    const int64_t j = j0 + t;
-    const bool jv = j < M;
-    const float4 cbx = jv ? poly_box<K, COUNTS>(b + j * 2 * K, (COUNTS && cb) ? (int)cb[j] : K)
-                          : make_float4(inf, inf, -inf, -inf);
-    if (t < R) {
-        const int64_t i = i0 + t;
-        s_rbox[t] = (i < N) ? poly_box<K, COUNTS>(a + i * 2 * K, (COUNTS && ca) ? (int)ca[i] : K)
-                            : make_float4(inf, inf, -inf, -inf);
-    }
-    if (t == 0) *s_nq = 0;
-    __syncthreads();
-#pragma unroll 4
-    for (int r = 0; r < R; ++r) {
-        const int64_t i = i0 + r;
-        const bool v = jv && i < N;
-        const float4 rbx = s_rbox[r];
-        const bool meet = v && !(rbx.z < cbx.x || cbx.z < rbx.x || rbx.w < cbx.y || cbx.w < rbx.y);
-        if (v && !meet) {
-            iou[i * M + j] = 0.f;
-            if (nx) nx[i * M + j] = 0;
-        }
-        const unsigned bal = __ballot_sync(full, meet);
-        int pos = 0;
-        if (lane == 0 && bal) pos = atomicAdd(s_nq, __popc(bal));
-        pos = __shfl_sync(full, pos, 0);
-        if (meet) s_q[pos + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)((r << 8) | t);
-    }
-    __syncthreads();
-    const int nq = *s_nq;
-    for (int qb = t & ~31; qb < nq; qb += C) {
-        const int q = qb + lane;
-        const bool act = q < nq;
-        const int code = act ? (int)s_q[q] : 0;
-        const int64_t i = i0 + (code >> 8), jj = j0 + (code & 0xFF);
-        const int n1 = (COUNTS && ca && act) ? (int)ca[i] : K;
-        const int n2 = (COUNTS && cb && act) ? (int)cb[jj] : K;
-        const float* pa = a + (act ? i : 0) * 2 * K;
-        const float* pb = b + (act ? jj : 0) * 2 * K;
-        float v = 0.f;
-        uint32_t c = 0;
-        const bool hard = act && pw_fast<K, COUNTS>(pa, pb, n1, n2, v, c, err, refine);
-        pw_finish<K>(__ballot_sync(full, hard), pa, pb, n1, n2, refine, v, c, err);
-        if (act) {
-            iou[i * M + jj] = v;
-            if (nx) nx[i * M + jj] = (uint8_t)c;
-        }
-    }
-    __syncthreads(); // the next tile reuses the boxes and the queue
-}
-
-// One N x M matrix: blocks take tiles of kTileRows x kPwThreads entries in
-// turn (pw_tile).
-template <int K, bool COUNTS>
-__global__ void __launch_bounds__(kPwThreads)
+__global__ void __launch_bounds__(kPwThreads, K == 4 ? kPwMinBlocks : 1)
 k_pairwise(const float* __restrict__ a, const uint8_t* __restrict__ ca, int64_t N, const float* __restrict__ b,
            const uint8_t* __restrict__ cb, int64_t M, float* __restrict__ iou, uint8_t* __restrict__ nx,
            uint32_t flags, uint32_t* status) {
@@ -140,13 +52,10 @@ k_pairwise(const float* __restrict__ a, const uint8_t* __restrict__ ca, int64_t 
     __shared__ int s_nq;
     const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
     const int64_t cblocks = (M + kPwThreads - 1) / kPwThreads;
-    const int64_t tiles = ((N + kTileRows - 1) / kTileRows) * cblocks;
+    const int64_t rb = blockIdx.x / cblocks;
     uint32_t err = 0;
-    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int64_t rb = tile / cblocks;
-        pw_tile<K, COUNTS>(a, ca, N, b, cb, M, iou, nx, rb * kTileRows, (tile - rb * cblocks) * kPwThreads,
-                           kTileRows, s_rbox, s_q, &s_nq, refine, err);
-    }
+    pw_tile<K, COUNTS>(a, ca, N, b, cb, M, rb * kTileRows, ((int64_t)blockIdx.x - rb * cblocks) * kPwThreads,
+                       kTileRows, s_rbox, s_q, &s_nq, refine, err, PwMatrixOut{iou, nx, M});
     if (err) atomicOr(status, err);
 }
 
@@ -276,9 +185,10 @@ __global__ void k_batched(int S, const int64_t* __restrict__ a_off, const int64_
         const int64_t cblocks = (Ms + cols - 1) / cols;
         const int64_t lt = t - tile_start[s];
         const int64_t rb = lt / cblocks;
+        const PwMatrixOut out{iou + o0, nx ? nx + o0 : nullptr, Ms};
         pw_tile<K, COUNTS>(a + a0 * 2 * K, COUNTS && ca ? ca + a0 : nullptr, Ns, b + b0 * 2 * K,
-                           COUNTS && cb ? cb + b0 : nullptr, Ms, iou + o0, nx ? nx + o0 : nullptr, rb * rows,
-                           (lt - rb * cblocks) * cols, rows, s_rbox, s_q, &s_nq, refine, err);
+                           COUNTS && cb ? cb + b0 : nullptr, Ms, rb * rows, (lt - rb * cblocks) * cols, rows, s_rbox,
+                           s_q, &s_nq, refine, err, out);
     }
     if (err) atomicOr(status, err);
 }
@@ -296,11 +206,9 @@ static void pairwise_dispatch(const float* a, const uint8_t* ca, int64_t N, cons
                                                                             device_status_ptr());
         return;
     }
-    int64_t blocks = tiles;
-    const int64_t cap = (int64_t)sm_count() * 8;
-    if (blocks > cap) blocks = cap;
-    k_pairwise<K, COUNTS><<<(unsigned)blocks, kPwThreads, 0, s>>>(a, ca, N, b, cb, M, iou, nx, flags,
-                                                                   device_status_ptr());
+    // tiles <= N * M / kPwThreads; an output of 2^31 * 128 entries would not fit in memory
+    k_pairwise<K, COUNTS><<<(unsigned)tiles, kPwThreads, 0, s>>>(a, ca, N, b, cb, M, iou, nx, flags,
+                                                                  device_status_ptr());
 }
 
 dgal_status launch_pairwise(const float* a, const uint8_t* ca, int64_t N, const float* b, const uint8_t* cb,

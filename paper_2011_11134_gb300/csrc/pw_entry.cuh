@@ -1,8 +1,9 @@
-// One entry of a pairwise IoU matrix: an exact bounding-box rejection, the
-// one-thread fast path (dgal_geom.cuh), and the warp-cooperative robust path
-// for the entries the fast path hands back.  Shared by the pairwise matrix
-// kernels and the rotated-NMS suppression mask, so both see the same FP32 IoU
-// for the same pair of polygons.
+// Entries and tiles of a pairwise IoU matrix: an exact bounding-box
+// rejection, the one-thread fast path (dgal_geom.cuh), the warp-cooperative
+// robust path for the entries the fast path hands back, and the tile that
+// queues the entries whose boxes meet so the clip runs densely.  Shared by the
+// pairwise matrix kernels and the rotated-NMS suppression mask, so both see
+// the same FP32 IoU for the same pair of polygons.
 #pragma once
 
 #include "dgal_geom.cuh"
@@ -74,6 +75,112 @@ __device__ __forceinline__ void pw_finish(unsigned todo, const float* __restrict
             nxo = o.nx;
         }
     }
+}
+
+// Axis-aligned bounding box (min x, min y, max x, max y) of a polygon's first
+// n vertices; a count outside [3, K] gives a box that meets every box, so the
+// entry reaches pw_fast, which reports the count.
+template <int K, bool COUNTS> __device__ __forceinline__ float4 poly_box(const float* __restrict__ p, int n) {
+    if (COUNTS && (n < 3 || n > K)) {
+        const float inf = __int_as_float(0x7f800000);
+        return make_float4(-inf, -inf, inf, inf);
+    }
+    float x[K], y[K];
+    load_poly<K>(p, x, y);
+    float4 r = make_float4(x[0], y[0], x[0], y[0]);
+#pragma unroll
+    for (int v = 1; v < K; ++v) {
+        const bool on = !COUNTS || v < n;
+        r.x = on ? fminf(r.x, x[v]) : r.x;
+        r.y = on ? fminf(r.y, y[v]) : r.y;
+        r.z = on ? fmaxf(r.z, x[v]) : r.z;
+        r.w = on ? fmaxf(r.w, y[v]) : r.w;
+    }
+    return r;
+}
+
+// Where a tile's results go: the IoU matrix (and nx) of one N x M matrix.
+// wanted(i, j): the entry is computed at all; disjoint(i, j): its boxes do
+// not meet (IoU 0, nx 0 by definition); put(i, j, iou, nx): the clip's result.
+struct PwMatrixOut {
+    float* __restrict__ iou;
+    uint8_t* __restrict__ nx; // nullable
+    int64_t M;
+    __device__ __forceinline__ bool wanted(int64_t, int64_t) const { return true; }
+    __device__ __forceinline__ void disjoint(int64_t i, int64_t j) const {
+        iou[i * M + j] = 0.f;
+        if (nx) nx[i * M + j] = 0;
+    }
+    __device__ __forceinline__ void put(int64_t i, int64_t j, float v, uint32_t c) const {
+        iou[i * M + j] = v;
+        if (nx) nx[i * M + j] = (uint8_t)c;
+    }
+};
+
+// One tile of rows [i0, i0 + R) x columns [j0, j0 + blockDim.x) of an N x M
+// matrix (a, b: the matrix's row and column polygons; out: where results go):
+//   1. thread c computes the bounding box of column j0 + c, threads < R those
+//      of the tile's rows (shared memory);
+//   2. every wanted entry is tested on the boxes (exact comparisons of the
+//      float inputs); a disjoint pair has IoU 0 and nx 0 by definition and is
+//      reported at once (consecutive threads, consecutive columns), the others
+//      are queued in shared memory (s_q, codes r << 8 | c);
+//   3. the block's warps clip the queued entries densely (pw_fast, with the
+//      warp-cooperative finish for the ones it hands back).
+// In bird's-eye scenes about 2% of the entries have meeting boxes; without the
+// queue a warp runs the clip whenever one of its 32 entries needs it.  Every
+// thread of the block calls this (it has block barriers); blockDim.x <= 256
+// and R <= 256 (8-bit fields of the queue codes).
+template <int K, bool COUNTS, class Out>
+__device__ __forceinline__ void pw_tile(const float* __restrict__ a, const uint8_t* __restrict__ ca, int64_t N,
+                                        const float* __restrict__ b, const uint8_t* __restrict__ cb, int64_t M,
+                                        int64_t i0, int64_t j0, int R, float4* s_rbox, uint16_t* s_q, int* s_nq,
+                                        bool refine, uint32_t& err, const Out& out) {
+    constexpr unsigned full = 0xffffffffu;
+    const int t = threadIdx.x, lane = t & 31, C = blockDim.x;
+    const float inf = __int_as_float(0x7f800000);
+    const int64_t j = j0 + t;
+    const bool jv = j < M;
+    const float4 cbx = jv ? poly_box<K, COUNTS>(b + j * 2 * K, (COUNTS && cb) ? (int)cb[j] : K)
+                          : make_float4(inf, inf, -inf, -inf);
+    if (t < R) {
+        const int64_t i = i0 + t;
+        s_rbox[t] = (i < N) ? poly_box<K, COUNTS>(a + i * 2 * K, (COUNTS && ca) ? (int)ca[i] : K)
+                            : make_float4(inf, inf, -inf, -inf);
+    }
+    if (t == 0) *s_nq = 0;
+    __syncthreads();
+#pragma unroll 4
+    for (int r = 0; r < R; ++r) {
+        const int64_t i = i0 + r;
+        const bool v = jv && i < N && out.wanted(i, j);
+        const float4 rbx = s_rbox[r];
+        const bool meet = v && !(rbx.z < cbx.x || cbx.z < rbx.x || rbx.w < cbx.y || cbx.w < rbx.y);
+        if (v && !meet) out.disjoint(i, j);
+        const unsigned bal = __ballot_sync(full, meet);
+        int pos = 0;
+        if (lane == 0 && bal) pos = atomicAdd(s_nq, __popc(bal));
+        pos = __shfl_sync(full, pos, 0);
+        if (meet) s_q[pos + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)((r << 8) | t);
+    }
+    __syncthreads();
+    const int nq = *s_nq;
+    for (int qb = t & ~31; qb < nq; qb += C) {
+        const int q = qb + lane;
+        const bool act = q < nq;
+        const int code = act ? (int)s_q[q] : 0;
+        const int64_t i = i0 + (code >> 8), jj = j0 + (code & 0xFF);
+        const int n1 = (COUNTS && ca && act) ? (int)ca[i] : K;
+        const int n2 = (COUNTS && cb && act) ? (int)cb[jj] : K;
+        const float* pa = a + (act ? i : 0) * 2 * K;
+        const float* pb = b + (act ? jj : 0) * 2 * K;
+        float v = 0.f;
+        uint32_t c = 0;
+        const bool hard = act && pw_fast<K, COUNTS>(pa, pb, n1, n2, v, c, err, refine);
+        pw_finish<K>(__ballot_sync(full, hard), pa, pb, n1, n2, refine, v, c, err);
+        if (act) out.put(i, jj, v, c);
+    }
+    __syncthreads(); // the next tile reuses the boxes and the queue
 }
 
 } // namespace dgal

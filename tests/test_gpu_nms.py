@@ -88,6 +88,16 @@ def test_nms_k8_counts(dg, orc):
     assert 0 < len(keep) < 700
 
 
+def test_nms_wide_2600(dg, orc):
+    """2600 boxes: 41 words per row, so the greedy pass also ORs words beyond
+    the 32 it holds in registers for each 64-row block."""
+    d = W.pairwise_bev_2000(seed=13, N=2600, M=1)
+    r = np.random.default_rng(73)
+    scores = r.uniform(0, 1, 2600).astype(np.float32)
+    keep = _check(dg, orc, d["a"], scores, 0.3, label="2600 boxes")
+    assert 0 < len(keep) < 2600
+
+
 @pytest.mark.parametrize("n", [1, 2, 63, 64, 65, 129, 200])
 def test_nms_ragged_sizes(dg, orc, n):
     d = W.pairwise_bev_2000(seed=100 + n, N=n, M=1)
