@@ -80,6 +80,8 @@ typedef enum {
 #define DGAL_DEV_BAD_COUNT 0x1u /* a vertex count outside [3, K] (pair treated as empty) */
 #define DGAL_DEV_OVERFLOW 0x2u  /* more than 2K intersection candidates (pair treated as empty) */
 #define DGAL_DEV_BAD_FLAGS 0x4u /* backward: nx > 2K or a code naming a missing vertex/edge */
+#define DGAL_DEV_BAD_OFFSETS 0x8u /* ragged batch: offsets not starting at 0 or not N_s x M_s (scene skipped) */
+#define DGAL_DEV_TIMEOUT 0x10u    /* a bounded wait on an asynchronous copy ran out (results incomplete) */
 
 /*
  * Paired IoU forward (paper Sec. II-B, `iou`): for k < n,

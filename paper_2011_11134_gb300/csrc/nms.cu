@@ -27,11 +27,17 @@
 //                    into the removal bitmap held in shared memory.  What a
 //                    64-row block reads (transposed diagonal, visiting order,
 //                    the rows' next 32 words) does not depend on the outcome,
-//                    so asynchronous copies (cp.async) bring it into a ring of
-//                    shared-memory stages kNmsStages - 1 blocks ahead, and the
-//                    walk does not wait on memory; words further right are
+//                    so the tensor-memory-access engine brings it into a ring
+//                    of shared-memory stages kNmsStages - 1 blocks ahead (one
+//                    2-D tiled load of 64 rows x 34 words, two 1-D bulk
+//                    copies, completion counted on an mbarrier per stage), and
+//                    the walk does not wait on memory; words further right are
 //                    loaded for kept rows only.
 #include <cmath>
+#include <mutex>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "dgal_geom.cuh"
 #include "dgal_internal.h"
@@ -39,10 +45,12 @@
 
 namespace dgal {
 
-constexpr int64_t kNmsMaxBoxes = 131072; // removal bitmap: 2048 words = 16 KB of shared memory (+ 67 KB of stages)
+constexpr int64_t kNmsMaxBoxes = 131072; // removal bitmap: 2048 words = 16 KB of shared memory (+ 71 KB of stages)
 constexpr int kNmsThreads = 128;         // rank kernel: 4 warps, one box each
 constexpr int kNmsRowsPerBlock = kNmsThreads / 32;
-constexpr int kNmsGreedyThreads = 1024;  // 32 warps: warp k holds rows k and k + 32 of a 64-row block
+constexpr int kNmsGreedyThreads = 512;   // warp k handles rows k, k + warps, ... of a 64-row block
+constexpr int kNmsGreedyWarps = kNmsGreedyThreads / 32;
+static_assert(kNmsGreedyThreads >= 128 && 64 % kNmsGreedyWarps == 0, "greedy block shape");
 
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -50,13 +58,20 @@ struct NmsLayout {
     size_t order, boxes, counts, mask, sup, total;
 };
 
+// Words per row of the suppression matrix, padded to even so that rows and
+// even word offsets are 16-byte aligned (bulk copies).
+static int64_t nms_row_words(int64_t N) {
+    const int64_t W = (N + 63) / 64;
+    return W + (W & 1);
+}
+
 // Workspace: order int32 [N] | polygons in visiting order float [N][K][2] |
-// their counts uint8 [N] | suppression words uint64 [N][W], W = ceil(N / 64) |
+// their counts uint8 [N] | suppression words uint64 [N][Wp], Wp = row words
+// (the first ceil(N / 64) used) |
 // transposed diagonal uint32 [N][2] (word of row b, bit a mod 64: a < b in
 // the same 64-row block suppresses b; half h written by the tile of rows
 // 64 (b / 64) + 32 h).
 static NmsLayout nms_layout(int64_t N, int K) {
-    const int64_t W = (N + 63) / 64;
     NmsLayout L;
     size_t off = 0;
     L.order = off;
@@ -66,7 +81,7 @@ static NmsLayout nms_layout(int64_t N, int K) {
     L.counts = off;
     off += align256((size_t)N);
     L.mask = off;
-    off += align256((size_t)N * (size_t)W * 8);
+    off += align256((size_t)N * (size_t)nms_row_words(N) * 8);
     L.sup = off;
     off += align256((size_t)N * 8);
     L.total = off;
@@ -126,8 +141,8 @@ constexpr int kNmsTileRows = 32; // rows of a mask tile; its kPwThreads = 128 co
 
 template <int K, bool COUNTS>
 __global__ void __launch_bounds__(kPwThreads)
-k_nms_mask(const float* __restrict__ sboxes, const uint8_t* __restrict__ scounts, int64_t N, int64_t W, float thr,
-           uint64_t* __restrict__ mask, uint32_t* __restrict__ sup, uint32_t flags, uint32_t* status) {
+k_nms_mask(const float* __restrict__ sboxes, const uint8_t* __restrict__ scounts, int64_t N, int64_t W, int64_t Wp,
+           float thr, uint64_t* __restrict__ mask, uint32_t* __restrict__ sup, uint32_t flags, uint32_t* status) {
     __shared__ float4 s_rbox[kNmsTileRows];
     __shared__ uint16_t s_q[kNmsTileRows * kPwThreads];
     __shared__ int s_nq;
@@ -150,61 +165,115 @@ k_nms_mask(const float* __restrict__ sboxes, const uint8_t* __restrict__ scounts
     // pw_tile ends with a barrier: the bits are final
     if (t < kNmsTileRows * 2) {
         const int64_t a = i0 + (t >> 1), w = w0 + (t & 1);
-        if (a < N && w < W && w >= c0) mask[a * W + w] = s_bits[t];
+        if (a < N && w < W && w >= c0) mask[a * Wp + w] = s_bits[t];
     }
     const int64_t j = j0 + t;
     if (j < N && (j >> 6) == c0) sup[j * 2 + ((i0 >> 5) & 1)] = s_tbits[t];
     if (err) atomicOr(status, err);
 }
 
-// What the greedy pass reads for one 64-row block: the rows' words
-// c + 1 .. c + 32, their transposed diagonal words and their box indices.
+// What the greedy pass reads for one 64-row block c: the rows' words
+// s .. s + nb - 1 (s = c + 1 rounded down to even, nb = min(34, Wp), so the
+// words c + 1 .. c + 32), packed [row][nb] as the tiled load writes them,
+// their transposed diagonal words and their box indices.
+constexpr int kNmsNear = 34;
 struct NmsStage {
-    uint64_t near[64][32];
+    uint64_t near[64 * kNmsNear];
     uint64_t sup[64];
     int32_t ord[64];
 };
+static_assert(sizeof(NmsStage) % 128 == 0 && (kNmsNear * 8) % 16 == 0, "tiled-load alignment");
 constexpr int kNmsStages = 4;
+constexpr int kNmsWaitSpins = 1 << 20; // bound on an mbarrier wait (then DGAL_DEV_TIMEOUT)
 
-__device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes, bool pred) {
-    // src-size 0 copies nothing and fills the destination with zeros
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    if (bytes == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(pred ? 8 : 0) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(pred ? 4 : 0) : "memory");
+// Box of the tiled load: words per row (even, >= 2: 16-byte rows) and rows.
+__host__ __device__ __forceinline__ int nms_box_words(int64_t Wp) { return Wp < kNmsNear ? (int)Wp : kNmsNear; }
+__host__ __device__ __forceinline__ int nms_box_rows(int64_t N) { return N < 64 ? (int)N : 64; }
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// One bulk copy (global -> this CTA's shared memory) that signals its bytes on `bar`.
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// One 2-D tiled load of the box at (x = word, y = row) that signals its bytes on `bar`.
+__device__ __forceinline__ void tiled_load(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::
+            "r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Waits for the phase of `bar` with the given parity; false after kNmsWaitSpins polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    const unsigned a = smem_addr(bar);
+    for (int i = 0; i < kNmsWaitSpins; ++i) {
+        unsigned done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
 }
 
 __global__ void __launch_bounds__(kNmsGreedyThreads)
-k_nms_greedy(const int32_t* __restrict__ order, const uint64_t* __restrict__ mask, const uint64_t* __restrict__ sup,
-             int64_t N, int64_t W, int64_t* __restrict__ keep, int64_t* __restrict__ num_keep) {
-    extern __shared__ __align__(16) unsigned char g_smem[];
-    NmsStage* stage = reinterpret_cast<NmsStage*>(g_smem);
+k_nms_greedy(const __grid_constant__ CUtensorMap mask_map, const int32_t* __restrict__ order,
+             const uint64_t* __restrict__ mask, const uint64_t* __restrict__ sup, int64_t N, int64_t W, int64_t Wp,
+             int64_t* __restrict__ keep, int64_t* __restrict__ num_keep, uint32_t* status) {
+    extern __shared__ unsigned char g_smem[];
+    // stages on a 128-byte boundary (tiled loads); the launch adds 128 bytes for this
+    unsigned char* base = g_smem + ((128u - (smem_addr(g_smem) & 127u)) & 127u);
+    NmsStage* stage = reinterpret_cast<NmsStage*>(base);
     // W words: bit b of word w = row 64 w + b is suppressed
-    unsigned long long* removed = reinterpret_cast<unsigned long long*>(g_smem + kNmsStages * sizeof(NmsStage));
+    unsigned long long* removed = reinterpret_cast<unsigned long long*>(base + kNmsStages * sizeof(NmsStage));
+    __shared__ __align__(8) uint64_t s_bar[kNmsStages]; // one transaction barrier per stage
     __shared__ uint64_t s_kept;
     __shared__ int s_rows[64]; // the kept rows of the current block, in order
     const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
     for (int64_t w = t; w < W; w += blockDim.x) removed[w] = 0ull;
-    // copies of block c into its stage (none past the last block), one group per block
+    if (t == 0) {
+        for (int i = 0; i < kNmsStages; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&s_bar[i])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    // thread 32 (warp 1) loads block c into its stage: the rows' word window
+    // (tiled load; rows past N and words past Wp read as zero), the
+    // transposed diagonal words and the box indices (bulk copies, sizes
+    // rounded up to 16 bytes into the workspace padding), after arming the
+    // stage's barrier with the byte count.
+    const int nb = nms_box_words(Wp), br = nms_box_rows(N);
     auto issue = [&](int64_t c) {
-        if (c < W) {
-            NmsStage& st = stage[c % kNmsStages];
-            const int64_t r0 = c * 64 + wp, r1 = r0 + 32, w = c + 1 + lane;
-            cp_async(&st.near[wp][lane], (r0 < N && w < W) ? mask + r0 * W + w : mask, 8, r0 < N && w < W);
-            cp_async(&st.near[wp + 32][lane], (r1 < N && w < W) ? mask + r1 * W + w : mask, 8, r1 < N && w < W);
-            const int64_t r = c * 64 + (t & 63);
-            if (t < 64) cp_async(&st.sup[t], r < N ? sup + r : sup, 8, r < N);
-            else if (t < 128) cp_async(&st.ord[t - 64], r < N ? order + r : order, 4, r < N);
-        }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        if (t != 32 || c >= W) return;
+        NmsStage& st = stage[c % kNmsStages];
+        uint64_t* bar = &s_bar[c % kNmsStages];
+        const int rows = N - c * 64 < 64 ? (int)(N - c * 64) : 64;
+        const unsigned sup_bytes = (unsigned)((rows * 8 + 15) & ~15), ord_bytes = (unsigned)((rows * 4 + 15) & ~15);
+        const unsigned total = (unsigned)(nb * br * 8) + sup_bytes + ord_bytes;
+        // the stage's previous (generic) reads, ordered by the block barrier, come before these async writes
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(total)
+                     : "memory");
+        tiled_load(st.near, &mask_map, (int)((c + 1) & ~1ll), (int)(c * 64), bar);
+        bulk_copy(st.sup, sup + c * 64, sup_bytes, bar);
+        bulk_copy(st.ord, order + c * 64, ord_bytes, bar);
     };
     for (int c = 0; c < kNmsStages - 1; ++c) issue(c);
     int64_t count = 0;
     for (int64_t c = 0; c < W; ++c) {
-        // block c's group is the oldest of the kNmsStages - 1 in flight
-        asm volatile("cp.async.wait_group %0;\n" ::"n"(kNmsStages - 2) : "memory");
-        __syncthreads(); // every thread's copies of block c, the removal words, the previous block done
+        // block c's copies landed; every thread waits so that it sees them
+        const bool ok = mbar_wait(&s_bar[c % kNmsStages], (unsigned)((c / kNmsStages) & 1));
+        if (__syncthreads_or(!ok)) { // also: the removal words and the previous block are done
+            if (t == 0) atomicOr(status, kDevTimeout);
+            break;
+        }
         issue(c + kNmsStages - 1); // into the stage the previous block used
         const NmsStage& st = stage[c % kNmsStages];
         if (wp == 0) {
@@ -235,33 +304,64 @@ k_nms_greedy(const int32_t* __restrict__ order, const uint64_t* __restrict__ mas
         }
         const int nk = __popcll(kept);
         count += nk;
-        // near words of the kept rows (zero past the last word)
-        const uint64_t v = (((kept >> wp) & 1ull) ? st.near[wp][lane] : 0ull) |
-                           (((kept >> (wp + 32)) & 1ull) ? st.near[wp + 32][lane] : 0ull);
-        if (v) atomicOr(&removed[c + 1 + lane], (unsigned long long)v);
+        // near words of the kept rows (word c + 1 + lane is window slot c + 1 + lane - s)
+        const int64_t wn = c + 1 + lane;
+        if (wn < W) {
+            const int slot = (int)(wn - ((c + 1) & ~1ll));
+            uint64_t v = 0ull;
+#pragma unroll
+            for (int q = wp; q < 64; q += kNmsGreedyWarps) v |= ((kept >> q) & 1ull) ? st.near[q * nb + slot] : 0ull;
+            if (v) atomicOr(&removed[wn], (unsigned long long)v);
+        }
         // words c + 33 .. W - 1: every (kept row, word) pair on its own thread
         const int nfar = (int)(W - c - 33); // W <= 2048: 32-bit indices
         if (nfar > 0) {
             __syncthreads(); // s_rows
             for (int idx = t; idx < nk * nfar; idx += blockDim.x) {
                 const int kk = idx / nfar, w = (int)c + 33 + (idx - kk * nfar);
-                const uint64_t f = mask[(c * 64 + s_rows[kk]) * W + w];
+                const uint64_t f = mask[(c * 64 + s_rows[kk]) * Wp + w];
                 if (f) atomicOr(&removed[w], (unsigned long long)f);
             }
         }
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (t == 0) *num_keep = count;
 }
 
-static size_t nms_greedy_smem(int64_t W) { return kNmsStages * sizeof(NmsStage) + (size_t)W * 8; }
+static size_t nms_greedy_smem(int64_t W) { return 128 + kNmsStages * sizeof(NmsStage) + (size_t)W * 8; }
+
+// Tensor map of the suppression matrix for the greedy pass's tiled loads:
+// uint64 [N][Wp], box nms_box_words(Wp) x nms_box_rows(N), no swizzle,
+// out-of-range elements read as zero.  The encoder is the driver's, found
+// through the runtime once.
+static dgal_status nms_mask_map(CUtensorMap* map, const uint64_t* mask, int64_t N, int64_t Wp) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!encode) return fail(DGAL_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    const cuuint64_t dims[2] = {(cuuint64_t)Wp, (cuuint64_t)N};
+    const cuuint64_t strides[1] = {(cuuint64_t)Wp * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)nms_box_words(Wp), (cuuint32_t)nms_box_rows(N)};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<uint64_t*>(mask), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(DGAL_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return DGAL_OK;
+}
 
 template <int K, bool COUNTS>
-static void nms_mask_dispatch(const float* sboxes, const uint8_t* scounts, int64_t N, int64_t W, float thr,
-                              uint64_t* mask, uint32_t* sup, uint32_t flags, cudaStream_t s) {
+static void nms_mask_dispatch(const float* sboxes, const uint8_t* scounts, int64_t N, int64_t W, int64_t Wp,
+                              float thr, uint64_t* mask, uint32_t* sup, uint32_t flags, cudaStream_t s) {
     // x: pairs of words (128 columns), y: 32-row tiles; N <= kNmsMaxBoxes keeps y <= 4096
     const dim3 grid((unsigned)((N + kPwThreads - 1) / kPwThreads), (unsigned)((N + kNmsTileRows - 1) / kNmsTileRows));
-    k_nms_mask<K, COUNTS><<<grid, kPwThreads, 0, s>>>(sboxes, scounts, N, W, thr, mask, sup, flags,
+    k_nms_mask<K, COUNTS><<<grid, kPwThreads, 0, s>>>(sboxes, scounts, N, W, Wp, thr, mask, sup, flags,
                                                        device_status_ptr());
 }
 
@@ -276,26 +376,29 @@ static dgal_status launch_nms(const float* boxes, const uint8_t* counts, const f
     uint8_t* scounts = reinterpret_cast<uint8_t*>(base + L.counts);
     uint64_t* mask = reinterpret_cast<uint64_t*>(base + L.mask);
     uint32_t* sup = reinterpret_cast<uint32_t*>(base + L.sup);
-    const int64_t W = (N + 63) / 64;
+    const int64_t W = (N + 63) / 64, Wp = nms_row_words(N);
     const unsigned rank_grid = (unsigned)((N + kNmsRowsPerBlock - 1) / kNmsRowsPerBlock);
     if (K == 4) k_nms_rank<4><<<rank_grid, kNmsThreads, 0, s>>>(boxes, counts, scores, N, order, sboxes, scounts);
     else k_nms_rank<8><<<rank_grid, kNmsThreads, 0, s>>>(boxes, counts, scores, N, order, sboxes, scounts);
     dgal_status st = check_launch("nms rank");
     if (st != DGAL_OK) return st;
     if (K == 4) {
-        if (counts) nms_mask_dispatch<4, true>(sboxes, scounts, N, W, thr, mask, sup, flags, s);
-        else nms_mask_dispatch<4, false>(sboxes, scounts, N, W, thr, mask, sup, flags, s);
+        if (counts) nms_mask_dispatch<4, true>(sboxes, scounts, N, W, Wp, thr, mask, sup, flags, s);
+        else nms_mask_dispatch<4, false>(sboxes, scounts, N, W, Wp, thr, mask, sup, flags, s);
     } else {
-        if (counts) nms_mask_dispatch<8, true>(sboxes, scounts, N, W, thr, mask, sup, flags, s);
-        else nms_mask_dispatch<8, false>(sboxes, scounts, N, W, thr, mask, sup, flags, s);
+        if (counts) nms_mask_dispatch<8, true>(sboxes, scounts, N, W, Wp, thr, mask, sup, flags, s);
+        else nms_mask_dispatch<8, false>(sboxes, scounts, N, W, Wp, thr, mask, sup, flags, s);
     }
     st = check_launch("nms mask");
     if (st != DGAL_OK) return st;
     const size_t smem = nms_greedy_smem(W);
     cudaError_t e = cudaFuncSetAttribute(k_nms_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail(DGAL_ERR_CUDA, "nms greedy shared memory (%zu bytes): %s", smem, cudaGetErrorString(e));
-    k_nms_greedy<<<1, kNmsGreedyThreads, smem, s>>>(order, mask, reinterpret_cast<const uint64_t*>(sup), N, W, keep,
-                                                    num_keep);
+    CUtensorMap map;
+    st = nms_mask_map(&map, mask, N, Wp);
+    if (st != DGAL_OK) return st;
+    k_nms_greedy<<<1, kNmsGreedyThreads, smem, s>>>(map, order, mask, reinterpret_cast<const uint64_t*>(sup), N, W,
+                                                    Wp, keep, num_keep, device_status_ptr());
     return check_launch("nms greedy");
 }
 
