@@ -235,7 +235,8 @@ k_nms_greedy(const __grid_constant__ CUtensorMap mask_map, const int32_t* __rest
     unsigned long long* removed = reinterpret_cast<unsigned long long*>(base + kNmsStages * sizeof(NmsStage));
     __shared__ __align__(8) uint64_t s_bar[kNmsStages]; // one transaction barrier per stage
     __shared__ uint64_t s_kept;
-    __shared__ int s_rows[64]; // the kept rows of the current block, in order
+    __shared__ int s_rows[64];                             // the kept rows of the current block, in order
+    __shared__ uint64_t s_part[kNmsGreedyWarps][32];       // per warp: OR of its kept rows' words c + 1 + lane
     const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
     for (int64_t w = t; w < W; w += blockDim.x) removed[w] = 0ull;
     if (t == 0) {
@@ -277,6 +278,15 @@ k_nms_greedy(const __grid_constant__ CUtensorMap mask_map, const int32_t* __rest
         issue(c + kNmsStages - 1); // into the stage the previous block used
         const NmsStage& st = stage[c % kNmsStages];
         if (wp == 0) {
+            // the previous block's near words: word c + lane gathers the warps' parts
+            // (far words of earlier blocks, ORed atomically, are all >= c + 32)
+            if (c > 0 && c + lane < W) {
+                uint64_t v = 0ull;
+#pragma unroll
+                for (int k = 0; k < kNmsGreedyWarps; ++k) v |= s_part[k][lane];
+                removed[c + lane] |= v;
+            }
+            __syncwarp();
             const int64_t rows = N - c * 64;
             const uint64_t valid = rows >= 64 ? ~0ull : ((1ull << rows) - 1ull);
             // suppressors of rows 64 c + lane and 64 c + 32 + lane: only bits below the row count
@@ -304,14 +314,15 @@ k_nms_greedy(const __grid_constant__ CUtensorMap mask_map, const int32_t* __rest
         }
         const int nk = __popcll(kept);
         count += nk;
-        // near words of the kept rows (word c + 1 + lane is window slot c + 1 + lane - s)
+        // near words of the kept rows (word c + 1 + lane is window slot c + 1 + lane - s),
+        // per warp; warp 0 ORs the parts into the removal words at the next block
         const int64_t wn = c + 1 + lane;
         if (wn < W) {
             const int slot = (int)(wn - ((c + 1) & ~1ll));
             uint64_t v = 0ull;
 #pragma unroll
             for (int q = wp; q < 64; q += kNmsGreedyWarps) v |= ((kept >> q) & 1ull) ? st.near[q * nb + slot] : 0ull;
-            if (v) atomicOr(&removed[wn], (unsigned long long)v);
+            s_part[wp][lane] = v;
         }
         // words c + 33 .. W - 1: every (kept row, word) pair on its own thread
         const int nfar = (int)(W - c - 33); // W <= 2048: 32-bit indices
