@@ -109,18 +109,24 @@ dgal_status dgal_iou_backward(const float* p1, const uint8_t* c1, const float* p
  * Forward + backward of paired IoU on HOST-resident data (a runtime
  * convenience; the paper has no counterpart): h_p1, h_p2 float [n][K][2],
  * h_grad float [n] = dL/dIoU in; h_iou float [n], h_g1, h_g2 float [n][K][2]
- * out (as dgal_iou_paired then dgal_iou_backward from the saved flags).  The
- * pairs go through in chunks of `chunk` pairs over three staging slots of
- * `workspace` (device memory, 256-byte aligned, at least
- * dgal_iou_host_workspace_bytes(chunk, K) bytes, caller-owned): copies in,
- * kernels and copies out of different chunks overlap on two copy streams of
- * the library and the caller's stream.  Results are bit-identical to the
- * device-memory calls.  The call is asynchronous and ordered on `stream`:
- * the host buffers must stay valid and unmodified until the stream reaches
- * that point, and they should be page-locked (pinned) for the copies to
- * overlap.  The copy streams and their events are created on the first call
- * on a device (make it outside any stream capture) and reused, so calls from
- * several host threads must be serialised by the caller.
+ * out (as dgal_iou_paired then dgal_iou_backward from the saved flags).
+ * Results are bit-identical to the device-memory calls.  Two forms:
+ *   direct: K = 4 with all six buffers page-locked and mapped into the
+ *     device's address space (cudaHostAlloc / pinned torch tensors; the
+ *     polygon and gradient buffers 16-byte aligned): one kernel reads and
+ *     writes the host buffers in place; `workspace` and `chunk` are not used
+ *     (workspace may be NULL, chunk must still be positive);
+ *   staged (otherwise): the pairs go through in chunks of `chunk` pairs over
+ *     three staging slots of `workspace` (device memory, 256-byte aligned, at
+ *     least dgal_iou_host_workspace_bytes(chunk, K) bytes, caller-owned):
+ *     copies in, kernels and copies out of different chunks overlap on two
+ *     copy streams of the library and the caller's stream.  The buffers
+ *     should be pinned for the copies to overlap.  The copy streams and their
+ *     events are created on the first staged call on a device (make it
+ *     outside any stream capture) and reused, so staged calls from several
+ *     host threads must be serialised by the caller.
+ * The call is asynchronous and ordered on `stream`: the host buffers must
+ * stay valid and unmodified until the stream reaches that point.
  */
 size_t dgal_iou_host_workspace_bytes(int64_t chunk, int K);
 dgal_status dgal_iou_fwd_bwd_host(const float* h_p1, const float* h_p2, const float* h_grad, int64_t n, int K,

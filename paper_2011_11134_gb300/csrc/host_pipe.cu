@@ -1,8 +1,16 @@
-// Paired IoU forward + backward on host-resident data, pipelined in chunks.
+// Paired IoU forward + backward on host-resident data.
 //
 // The paired kernels take a few tens of microseconds per million pairs; for
-// data that lives in host memory the copies dominate.  This call splits the
-// pairs into chunks and runs, for chunk c in staging slot c mod 3:
+// data that lives in host memory the host link dominates.  Two forms:
+//
+// Direct (K = 4, every buffer pinned and mapped into the device's address
+// space): one kernel reads the polygons and dL/dIoU from host memory and
+// writes IoU and both gradients back, the clip state staying in registers
+// between the forward and the backward (k_paired_fused).  Loads from both
+// directions are in flight together, and nothing is staged.
+//
+// Staged (otherwise): the pairs go in chunks; for chunk c in staging slot
+// c mod 3:
 //   copy-in stream   host -> slot: p1, p2, dL/dIoU         (event in[s])
 //   caller's stream  paired forward (flags kept in the slot) and backward
 //                    from those flags                       (event done[s])
@@ -96,6 +104,17 @@ SlotLayout slot_layout(int64_t chunk, int K) {
         if (_e != cudaSuccess) return fail(DGAL_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(_e)); \
     } while (0)
 
+// Device address of a host buffer the device can load and store directly
+// (pinned and mapped), else NULL.
+void* mapped(const void* h) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError(); // not a CUDA pointer: clear the error
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 } // namespace
 } // namespace dgal
 
@@ -115,6 +134,22 @@ extern "C" dgal_status dgal_iou_fwd_bwd_host(const float* h_p1, const float* h_p
     if (chunk <= 0) return fail(DGAL_ERR_INVALID_ARG, "chunk = %lld must be positive", (long long)chunk);
     if (!h_p1 || !h_p2 || !h_grad || !h_iou || !h_g1 || !h_g2)
         return fail(DGAL_ERR_INVALID_ARG, "a host buffer is NULL");
+    if (K == 4) {
+        void* d_p1 = mapped(h_p1);
+        void* d_p2 = mapped(h_p2);
+        void* d_grad = mapped(h_grad);
+        void* d_iou = mapped(h_iou);
+        void* d_g1 = mapped(h_g1);
+        void* d_g2 = mapped(h_g2);
+        // 16-byte vertex loads and stores
+        const bool aligned = ((reinterpret_cast<uintptr_t>(d_p1) | reinterpret_cast<uintptr_t>(d_p2) |
+                               reinterpret_cast<uintptr_t>(d_g1) | reinterpret_cast<uintptr_t>(d_g2)) & 15u) == 0;
+        if (d_p1 && d_p2 && d_grad && d_iou && d_g1 && d_g2 && aligned)
+            return launch_paired_fused(static_cast<const float*>(d_p1), static_cast<const float*>(d_p2), n,
+                                       static_cast<const float*>(d_grad), static_cast<float*>(d_iou),
+                                       static_cast<float*>(d_g1), static_cast<float*>(d_g2), flags,
+                                       (cudaStream_t)stream);
+    }
     if (!workspace) return fail(DGAL_ERR_WORKSPACE, "workspace is NULL");
     if (reinterpret_cast<uintptr_t>(workspace) & 255u)
         return fail(DGAL_ERR_ALIGNMENT, "workspace is not 256-byte aligned");

@@ -86,6 +86,14 @@ dgal_status launch_paired_bwd(const float* p1, const uint8_t* c1, const float* p
     return check_launch("paired backward");
 }
 
+dgal_status launch_paired_fused(const float* p1, const float* p2, int64_t n, const float* grad, float* iou, float* g1,
+                                float* g2, uint32_t flags, cudaStream_t s) {
+    if (!device_status_ptr()) return fail(DGAL_ERR_CUDA, "device status word unavailable");
+    k_paired_fused<4><<<paired_grid(n, 4), kPairThreads, 0, s>>>(p1, p2, n, grad, iou, g1, g2, flags,
+                                                                 device_status_ptr());
+    return check_launch("paired forward + backward");
+}
+
 size_t loss_workspace_bytes(int64_t n, int K) { return loss_layout(n, K).total; }
 
 dgal_status launch_iou_loss(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n, int K,

@@ -310,6 +310,94 @@ k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
     if (err) atomicOr(status, err);
 }
 
+// Forward and backward in one pass, for pairs that live in pinned host
+// memory the kernel reads and writes in place (K = 4, no counts): the step is
+// then bound by the host link, and the clip state stays in registers between
+// the two halves instead of making a round trip as flags.  Every value is the
+// one the separate kernels give: the forward is k_paired_fwd's (with its
+// hand-back of hard pairs to warp_robust), and the backward is k_paired_bwd's
+// from the codes the forward just produced.
+template <int K>
+__global__ void __launch_bounds__(kPairThreads, 4)
+k_paired_fused(const float* __restrict__ p1, const float* __restrict__ p2, int64_t n, const float* __restrict__ grad,
+               float* __restrict__ iou, float* __restrict__ g1, float* __restrict__ g2, uint32_t flags,
+               uint32_t* status) {
+    constexpr unsigned full = 0xffffffffu;
+    __shared__ float s_bwd[kPairThreads / 32][4 * K];
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * kPairThreads;
+    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
+    const ZArgs za{nullptr, nullptr, nullptr, nullptr};
+    uint32_t err = 0;
+    for (int64_t base = (int64_t)blockIdx.x * kPairThreads + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t k = base + lane;
+        const bool live = k < n;
+        float px[K], py[K], qx[K], qy[K];
+        FwdOut<K> o;
+        bool hard = false;
+        if (live) {
+            load_poly<K>(p1 + k * 2 * K, px, py);
+            load_poly<K>(p2 + k * 2 * K, qx, qy);
+            Geo<K> g;
+            make_geo<K, false>(px, py, qx, qy, K, K, g);
+            input_areas<K, false>(g, o.a1, o.a2);
+            hard = refine ? !fwd_generic<K, false>(g, o, p1 + k * 2 * K, p2 + k * 2 * K) : !fwd_generic<K, false>(g, o);
+            hard = hard || (o.nx >= 3u && o.a1 + o.a2 - o.ai < kThinRel * o.L2);
+            if (!hard) {
+                const float U = o.a1 + o.a2 - o.ai;
+                o.iou = (o.nx >= 3u && U > 0.f) ? o.ai / U : 0.f;
+            }
+        }
+        unsigned todo = __ballot_sync(full, hard);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t kk = base + src;
+            FwdOut<K> r;
+            r.err = 0;
+            warp_robust<K>(p1 + kk * 2 * K, p2 + kk * 2 * K, K, K, refine, r);
+            if (lane == src) {
+                err |= r.err;
+                o.iou = r.iou;
+                o.nx = r.nx;
+                o.codes = r.codes;
+            }
+        }
+        bool slow = false;
+        if (live) {
+            iou[k] = o.iou;
+            Geo<K> g;
+            make_geo<K, false>(px, py, qx, qy, K, K, g);
+            float g1x[K], g1y[K], g2x[K], g2y[K];
+            auto adj = adj_of<false>(grad[k], za, k);
+            const uint32_t e = bwd_shape<K, false>(g, adj, o.nx, o.codes, refine, g1x, g1y, g2x, g2y);
+            slow = e == kSlow;
+            if (!slow) {
+                err |= e;
+                store_poly<K>(g1 + k * 2 * K, g1x, g1y);
+                store_poly<K>(g2 + k * 2 * K, g2x, g2y);
+            }
+        }
+        todo = __ballot_sync(full, slow);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t kk = base + src;
+            const uint32_t mnx = __shfl_sync(full, o.nx, src);
+            Codes<K> cs;
+#pragma unroll
+            for (int q = 0; q < (2 * K + 7) / 8; ++q) cs.w[q] = __shfl_sync(full, o.codes.w[q], src);
+            auto a = adj_of<false>(grad[kk], za, kk);
+            const uint32_t e = refine ? warp_bwd<K, double>(p1 + kk * 2 * K, p2 + kk * 2 * K, K, K, a, mnx, cs,
+                                                            g1 + kk * 2 * K, g2 + kk * 2 * K, s_bwd[threadIdx.x >> 5])
+                                      : warp_bwd<K, float>(p1 + kk * 2 * K, p2 + kk * 2 * K, K, K, a, mnx, cs,
+                                                           g1 + kk * 2 * K, g2 + kk * 2 * K, s_bwd[threadIdx.x >> 5]);
+            if (lane == src) err |= e;
+        }
+    }
+    if (err) atomicOr(status, err);
+}
+
 // K = 8: one group of 8 lanes per pair (group8.cuh), 4 pairs per warp and
 // step, grid-stride over warps.  Pairs the group cannot finish are done by the
 // whole warp (forward) or by the group's first lane (backward) afterwards.

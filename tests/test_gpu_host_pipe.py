@@ -1,6 +1,7 @@
-"""dgal_iou_fwd_bwd_host (paired forward + backward on host buffers, chunked
-and pipelined) gives bit-identical results to the device-memory calls, for
-ragged chunk tails, one chunk, tiny and empty inputs; and a sample agrees
+"""dgal_iou_fwd_bwd_host (paired forward + backward on host buffers) gives
+bit-identical results to the device-memory calls in both of its forms: the
+direct kernel on pinned buffers, and the chunked pipeline (pageable buffers),
+for ragged chunk tails, one chunk, tiny and empty inputs; and a sample agrees
 with the FP64 oracle."""
 import numpy as np
 import pytest
@@ -24,16 +25,19 @@ def dg():
     return m
 
 
+@pytest.mark.parametrize("pinned", [True, False])
 @pytest.mark.parametrize("n,chunk", [(300_007, 65_536), (50_000, 131_072), (1, 1000), (7, 3)])
-def test_host_pipeline_matches_device_path(dg, n, chunk):
+def test_host_pipeline_matches_device_path(dg, n, chunk, pinned):
     import torch
 
     d = W.loss_pairs_1m(seed=40, n=n)
     r = np.random.default_rng(41)
     grad = r.normal(size=n).astype(np.float32)
-    hp1 = torch.from_numpy(d["p1"]).pin_memory()
-    hp2 = torch.from_numpy(d["p2"]).pin_memory()
-    hg = torch.from_numpy(grad).pin_memory()
+    hp1 = torch.from_numpy(d["p1"])
+    hp2 = torch.from_numpy(d["p2"])
+    hg = torch.from_numpy(grad)
+    if pinned:  # the direct form
+        hp1, hp2, hg = hp1.pin_memory(), hp2.pin_memory(), hg.pin_memory()
     iou, g1, g2 = dg.dgal_iou_fwd_bwd_host(hp1, hp2, hg, chunk=chunk)
     torch.cuda.synchronize()
     p1, p2, gd = dev(d["p1"]), dev(d["p2"]), dev(grad)
@@ -64,7 +68,8 @@ def test_host_pipeline_oracle_sample_and_edges(dg, orc):
     z = torch.empty((0, 4, 2)).pin_memory()
     out = dg.dgal_iou_fwd_bwd_host(z, z, torch.empty(0).pin_memory())
     assert out[0].numel() == 0
-    # a workspace too small is rejected on the host
+    # the staged form (pageable buffers) rejects a workspace too small on the host
     ws = torch.empty(1024, device="cuda", dtype=torch.uint8)
     with pytest.raises(dg.DgalError):
-        dg.dgal_iou_fwd_bwd_host(hp1, hp2, hg, chunk=4096, workspace=ws)
+        dg.dgal_iou_fwd_bwd_host(torch.from_numpy(d["p1"]), torch.from_numpy(d["p2"]), torch.ones(n), chunk=4096,
+                                 workspace=ws)
