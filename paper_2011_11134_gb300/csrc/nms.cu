@@ -101,6 +101,7 @@ k_nms_rank(const float* __restrict__ boxes, const uint8_t* __restrict__ counts, 
     if (i >= N) return; // warp-uniform
     const float si = nms_key(__ldg(scores + i));
     int r = 0;
+#pragma unroll 4
     for (int64_t j = lane; j < N; j += 32) {
         const float sj = nms_key(__ldg(scores + j));
         r += (sj > si || (sj == si && j < i)) ? 1 : 0;
