@@ -600,34 +600,29 @@ def main():
     plain_value = n * world * args.steps / (plain_ms / 1e3)
 
     # end to end through the C ABI on pinned host buffers: dgal_iou_fwd_bwd_host
-    # reads the polygons and dL/dIoU from host memory and writes IoU and the
-    # gradients back (K = 4: one kernel on the pinned buffers in place; all
-    # inside the timed region)
+    # reads the polygons (and counts) and dL/dIoU from host memory and writes
+    # IoU and the gradients back, all inside the timed region: K = 4 without
+    # counts in its direct form (one kernel on the pinned buffers in place),
+    # otherwise staged (chunks copied in and out, overlapping the kernels)
     h_p1 = torch.from_numpy(d["p1"]).pin_memory()
     h_p2 = torch.from_numpy(d["p2"]).pin_memory()
+    h_c1 = torch.from_numpy(d["c1"]).pin_memory() if "c1" in d else None
+    h_c2 = torch.from_numpy(d["c2"]).pin_memory() if "c2" in d else None
     h_grad = torch.ones(n).pin_memory()
     h_iou = torch.empty(n).pin_memory()
     h_g1 = torch.empty((n, K, 2)).pin_memory()
     h_g2 = torch.empty((n, K, 2)).pin_memory()
     chunk = 262144
-    ws_e2e = torch.empty(dg.dgal_iou_host_workspace_bytes(chunk, K) + 256, device=dev, dtype=torch.uint8)
-    ws_e2e = ws_e2e[(-ws_e2e.data_ptr()) % 256:]
-    use_host_call = c1 is None
-    host_args = (L.ptr(h_p1), L.ptr(h_p2), L.ptr(h_grad), n, K, L.ptr(h_iou), L.ptr(h_g1), L.ptr(h_g2), L.ptr(ws_e2e),
-                 ws_e2e.numel(), chunk, FLAGS, sp)
+    direct = K == 4 and h_c1 is None
+    ws_e2e = None
+    if not direct:
+        ws_e2e = torch.empty(dg.dgal_iou_host_workspace_bytes(chunk, K) + 256, device=dev, dtype=torch.uint8)
+        ws_e2e = ws_e2e[(-ws_e2e.data_ptr()) % 256:]
+    host_args = (L.ptr(h_p1), L.ptr(h_c1), L.ptr(h_p2), L.ptr(h_c2), L.ptr(h_grad), n, K, L.ptr(h_iou), L.ptr(h_g1),
+                 L.ptr(h_g2), L.ptr(ws_e2e), ws_e2e.numel() if ws_e2e is not None else 0, chunk, FLAGS, sp)
 
     def e2e_step():
-        if use_host_call:
-            assert lib.dgal_iou_fwd_bwd_host(*host_args) == 0, dg.dgal_last_error()
-        else:
-            a1 = h_p1.to(dev, non_blocking=True)
-            a2 = h_p2.to(dev, non_blocking=True)
-            gg = h_grad.to(dev, non_blocking=True)
-            iv, nv, xv, _ = dg.dgal_iou_paired(a1, a2, c1, c2)
-            o1, o2 = dg.dgal_iou_backward(a1, a2, gg, nv, xv, c1, c2)
-            h_iou.copy_(iv, non_blocking=True)
-            h_g1.copy_(o1, non_blocking=True)
-            h_g2.copy_(o2, non_blocking=True)
+        assert lib.dgal_iou_fwd_bwd_host(*host_args) == 0, dg.dgal_last_error()
 
     for _ in range(2):
         e2e_step()
@@ -641,7 +636,7 @@ def main():
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1)
     e2e_value = n * world * args.steps / (e2e_ms / 1e3)
-    h2d = 2 * n * 8 * K + 4 * n
+    h2d = 2 * n * 8 * K + 4 * n + (2 * n if h_c1 is not None else 0)
     d2h = 4 * n + 2 * n * 8 * K
 
     if rank != 0:
@@ -697,9 +692,9 @@ def main():
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "path": "dgal_iou_fwd_bwd_host on pinned host buffers (direct form: one kernel reads and writes "
-                        "them in place over the host link)" if use_host_call
-                        else "torch copies + dgal_iou_paired + dgal_iou_backward"},
+                "path": "dgal_iou_fwd_bwd_host on pinned host buffers, " + (
+                    "direct form: one kernel reads and writes them in place over the host link" if direct else
+                    f"staged form: {chunk}-pair chunks copied in and out, overlapping the kernels")},
         "gpu_launches": 2 * args.steps,  # forward (saves the flags), backward (reads them)
         "clocks": clocks,
         "parity": err,

@@ -108,10 +108,11 @@ dgal_status dgal_iou_backward(const float* p1, const uint8_t* c1, const float* p
 /*
  * Forward + backward of paired IoU on HOST-resident data (a runtime
  * convenience; the paper has no counterpart): h_p1, h_p2 float [n][K][2],
+ * h_c1, h_c2 uint8 [n] vertex counts or NULL (as for dgal_iou_paired),
  * h_grad float [n] = dL/dIoU in; h_iou float [n], h_g1, h_g2 float [n][K][2]
  * out (as dgal_iou_paired then dgal_iou_backward from the saved flags).
  * Results are bit-identical to the device-memory calls.  Two forms:
- *   direct: K = 4 with all six buffers page-locked and mapped into the
+ *   direct: K = 4 without counts, all six buffers page-locked and mapped into the
  *     device's address space (cudaHostAlloc / pinned torch tensors; the
  *     polygon and gradient buffers 16-byte aligned): one kernel reads and
  *     writes the host buffers in place; `workspace` and `chunk` are not used
@@ -129,9 +130,9 @@ dgal_status dgal_iou_backward(const float* p1, const uint8_t* c1, const float* p
  * stay valid and unmodified until the stream reaches that point.
  */
 size_t dgal_iou_host_workspace_bytes(int64_t chunk, int K);
-dgal_status dgal_iou_fwd_bwd_host(const float* h_p1, const float* h_p2, const float* h_grad, int64_t n, int K,
-                                  float* h_iou, float* h_g1, float* h_g2, void* workspace, size_t ws_bytes,
-                                  int64_t chunk, uint32_t flags, void* stream);
+dgal_status dgal_iou_fwd_bwd_host(const float* h_p1, const uint8_t* h_c1, const float* h_p2, const uint8_t* h_c2,
+                                  const float* h_grad, int64_t n, int K, float* h_iou, float* h_g1, float* h_g2,
+                                  void* workspace, size_t ws_bytes, int64_t chunk, uint32_t flags, void* stream);
 
 /*
  * 3D IoU of paired boxes, each given as a bird's-eye-view polygon (as above)

@@ -359,13 +359,13 @@ def dgal_iou_host_workspace_bytes(chunk, K=4):
     return int(_lib.lib().dgal_iou_host_workspace_bytes(chunk, K))
 
 
-def dgal_iou_fwd_bwd_host(p1, p2, grad, out=None, chunk=131072, workspace=None, flags=DGAL_FP64_REFINE,
-                          stream=None, device=None):
+def dgal_iou_fwd_bwd_host(p1, p2, grad, c1=None, c2=None, out=None, chunk=131072, workspace=None,
+                          flags=DGAL_FP64_REFINE, stream=None, device=None):
     """Paired IoU forward + backward on host tensors (CPU float32, ideally
-    pinned): p1, p2 [n, K, 2], grad [n] -> (iou [n], g1, g2 [n, K, 2]) on the
-    host.  K = 4 with every tensor pinned runs one kernel on the host memory in
-    place (no workspace); otherwise chunked and pipelined (copies overlap the
-    kernels).  Asynchronous on the stream: synchronise before reading the
+    pinned): p1, p2 [n, K, 2], optional uint8 vertex counts c1, c2 [n],
+    grad [n] -> (iou [n], g1, g2 [n, K, 2]) on the host.  K = 4 without counts
+    and every tensor pinned runs one kernel on the host memory in place (no
+    workspace); otherwise chunked and pipelined (copies overlap the kernels).  Asynchronous on the stream: synchronise before reading the
     outputs."""
     for t, name in ((p1, "p1"), (p2, "p2"), (grad, "grad")):
         if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
@@ -375,21 +375,25 @@ def dgal_iou_fwd_bwd_host(p1, p2, grad, out=None, chunk=131072, workspace=None, 
     n, K = p1.shape[0], p1.shape[1]
     if grad.shape != (n,):
         raise ValueError("grad must be [n]")
+    for t, name in ((c1, "c1"), (c2, "c2")):
+        if t is not None and (not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.uint8
+                              or t.shape != (n,) or not t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous uint8 host tensor of shape [n]")
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
     if out is None:
         pin = p1.is_pinned()
         out = (torch.empty(n, pin_memory=pin), torch.empty((n, K, 2), pin_memory=pin),
                torch.empty((n, K, 2), pin_memory=pin))
     iou, g1, g2 = out
-    direct = (K == 4 and all(t.is_pinned() for t in (p1, p2, grad, iou, g1, g2))
+    direct = (K == 4 and c1 is None and c2 is None and all(t.is_pinned() for t in (p1, p2, grad, iou, g1, g2))
               and all(t.data_ptr() % 16 == 0 for t in (p1, p2, g1, g2)))
     if workspace is None and not direct:
         workspace = torch.empty(dgal_iou_host_workspace_bytes(chunk, K) + 256, device=dev, dtype=torch.uint8)
         off = (-workspace.data_ptr()) % 256
         workspace = workspace[off:]
     ws_ptr, ws_bytes = (_lib.ptr(workspace), workspace.numel()) if workspace is not None else (None, 0)
-    _lib.call("dgal_iou_fwd_bwd_host", _lib.ptr(p1), _lib.ptr(p2), _lib.ptr(grad), n, K, _lib.ptr(iou), _lib.ptr(g1),
-              _lib.ptr(g2), ws_ptr, ws_bytes, chunk, flags, _lib.stream_ptr(stream))
+    _lib.call("dgal_iou_fwd_bwd_host", _lib.ptr(p1), _lib.ptr(c1), _lib.ptr(p2), _lib.ptr(c2), _lib.ptr(grad), n, K,
+              _lib.ptr(iou), _lib.ptr(g1), _lib.ptr(g2), ws_ptr, ws_bytes, chunk, flags, _lib.stream_ptr(stream))
     return iou, g1, g2
 
 

@@ -56,7 +56,7 @@ _SIG = {
     "dgal_line_intersect": (_I, [_P, _P, _I64, _P, _P]),
     "dgal_line_intersect_backward": (_I, [_P, _P, _I64, _P, _P, _P, _P]),
     "dgal_iou_host_workspace_bytes": (ctypes.c_size_t, [_I64, _I]),
-    "dgal_iou_fwd_bwd_host": (_I, [_P, _P, _P, _I64, _I, _P, _P, _P, _P, ctypes.c_size_t, _I64, _U32, _P]),
+    "dgal_iou_fwd_bwd_host": (_I, [_P, _P, _P, _P, _P, _I64, _I, _P, _P, _P, _P, ctypes.c_size_t, _I64, _U32, _P]),
     "dgal_graph_launch": (_I, [_P, _P]),
     "dgal_graph_destroy": (_I, [_P]),
     "dgal_autotune": (_I, [_I, _I, ctypes.c_char_p]),

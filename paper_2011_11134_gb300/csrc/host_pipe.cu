@@ -3,14 +3,14 @@
 // The paired kernels take a few tens of microseconds per million pairs; for
 // data that lives in host memory the host link dominates.  Two forms:
 //
-// Direct (K = 4, every buffer pinned and mapped into the device's address
-// space): one kernel reads the polygons and dL/dIoU from host memory and
+// Direct (K = 4 without counts, every buffer pinned and mapped into the
+// device's address space): one kernel reads the polygons and dL/dIoU from host memory and
 // writes IoU and both gradients back, the clip state staying in registers
 // between the forward and the backward (k_paired_fused).  Loads from both
 // directions are in flight together, and nothing is staged.
 //
 // Staged (otherwise): the pairs go in chunks; for chunk c in staging slot
-// c mod 3:
+// c mod 3 (the counts, when given, travel with the polygons):
 //   copy-in stream   host -> slot: p1, p2, dL/dIoU         (event in[s])
 //   caller's stream  paired forward (flags kept in the slot) and backward
 //                    from those flags                       (event done[s])
@@ -69,9 +69,10 @@ dgal_status pipe_state(PipeState** out) {
 
 size_t up256(size_t b) { return (b + 255) / 256 * 256; }
 
-// One slot: p1 | p2 | grad | iou | nx | xflags | g1 | g2, each 256-byte aligned.
+// One slot: p1 | p2 | grad | iou | nx | xflags | g1 | g2 | c1 | c2, each
+// 256-byte aligned.
 struct SlotLayout {
-    size_t p1, p2, grad, iou, nx, xflags, g1, g2, bytes;
+    size_t p1, p2, grad, iou, nx, xflags, g1, g2, c1, c2, bytes;
 };
 
 SlotLayout slot_layout(int64_t chunk, int K) {
@@ -94,6 +95,10 @@ SlotLayout slot_layout(int64_t chunk, int K) {
     o += up256(poly);
     L.g2 = o;
     o += up256(poly);
+    L.c1 = o;
+    o += up256((size_t)chunk);
+    L.c2 = o;
+    o += up256((size_t)chunk);
     L.bytes = o;
     return L;
 }
@@ -125,16 +130,17 @@ extern "C" size_t dgal_iou_host_workspace_bytes(int64_t chunk, int K) {
     return kSlots * slot_layout(chunk, K).bytes;
 }
 
-extern "C" dgal_status dgal_iou_fwd_bwd_host(const float* h_p1, const float* h_p2, const float* h_grad, int64_t n,
-                                             int K, float* h_iou, float* h_g1, float* h_g2, void* workspace,
-                                             size_t ws_bytes, int64_t chunk, uint32_t flags, void* stream) {
+extern "C" dgal_status dgal_iou_fwd_bwd_host(const float* h_p1, const uint8_t* h_c1, const float* h_p2,
+                                             const uint8_t* h_c2, const float* h_grad, int64_t n, int K, float* h_iou,
+                                             float* h_g1, float* h_g2, void* workspace, size_t ws_bytes, int64_t chunk,
+                                             uint32_t flags, void* stream) {
     if (K != 4 && K != 8) return fail(DGAL_ERR_UNSUPPORTED_K, "K = %d is not supported (K must be 4 or 8)", K);
     if (n < 0) return fail(DGAL_ERR_INVALID_ARG, "n = %lld is negative", (long long)n);
     if (n == 0) return DGAL_OK;
     if (chunk <= 0) return fail(DGAL_ERR_INVALID_ARG, "chunk = %lld must be positive", (long long)chunk);
     if (!h_p1 || !h_p2 || !h_grad || !h_iou || !h_g1 || !h_g2)
         return fail(DGAL_ERR_INVALID_ARG, "a host buffer is NULL");
-    if (K == 4) {
+    if (K == 4 && !h_c1 && !h_c2) {
         void* d_p1 = mapped(h_p1);
         void* d_p2 = mapped(h_p2);
         void* d_grad = mapped(h_grad);
@@ -180,18 +186,22 @@ extern "C" dgal_status dgal_iou_fwd_bwd_host(const float* h_p1, const float* h_p
         uint8_t* d_xf = reinterpret_cast<uint8_t*>(base + L.xflags);
         float* d_g1 = reinterpret_cast<float*>(base + L.g1);
         float* d_g2 = reinterpret_cast<float*>(base + L.g2);
+        uint8_t* d_c1 = h_c1 ? reinterpret_cast<uint8_t*>(base + L.c1) : nullptr;
+        uint8_t* d_c2 = h_c2 ? reinterpret_cast<uint8_t*>(base + L.c2) : nullptr;
         // inputs: the slot's previous kernels must be done with them
         if (c >= kSlots) PIPE_CUDA(cudaStreamWaitEvent(P->in, P->ev_done[s], 0));
         PIPE_CUDA(cudaMemcpyAsync(d_p1, h_p1 + (size_t)k0 * K * 2, (size_t)m * pp, cudaMemcpyHostToDevice, P->in));
         PIPE_CUDA(cudaMemcpyAsync(d_p2, h_p2 + (size_t)k0 * K * 2, (size_t)m * pp, cudaMemcpyHostToDevice, P->in));
         PIPE_CUDA(cudaMemcpyAsync(d_grad, h_grad + k0, (size_t)m * 4, cudaMemcpyHostToDevice, P->in));
+        if (h_c1) PIPE_CUDA(cudaMemcpyAsync(d_c1, h_c1 + k0, (size_t)m, cudaMemcpyHostToDevice, P->in));
+        if (h_c2) PIPE_CUDA(cudaMemcpyAsync(d_c2, h_c2 + k0, (size_t)m, cudaMemcpyHostToDevice, P->in));
         PIPE_CUDA(cudaEventRecord(P->ev_in[s], P->in));
         // kernels: inputs arrived, and the slot's previous outputs were copied out
         PIPE_CUDA(cudaStreamWaitEvent(cs, P->ev_in[s], 0));
         if (c >= kSlots) PIPE_CUDA(cudaStreamWaitEvent(cs, P->ev_out[s], 0));
-        st = launch_paired_fwd(d_p1, nullptr, d_p2, nullptr, m, K, d_iou, d_nx, d_xf, nullptr, flags, cs);
+        st = launch_paired_fwd(d_p1, d_c1, d_p2, d_c2, m, K, d_iou, d_nx, d_xf, nullptr, flags, cs);
         if (st != DGAL_OK) return st;
-        st = launch_paired_bwd(d_p1, nullptr, d_p2, nullptr, m, K, d_grad, d_nx, d_xf, d_g1, d_g2, flags, cs);
+        st = launch_paired_bwd(d_p1, d_c1, d_p2, d_c2, m, K, d_grad, d_nx, d_xf, d_g1, d_g2, flags, cs);
         if (st != DGAL_OK) return st;
         PIPE_CUDA(cudaEventRecord(P->ev_done[s], cs));
         // outputs

@@ -49,6 +49,29 @@ def test_host_pipeline_matches_device_path(dg, n, chunk, pinned):
     assert dg.dgal_get_device_status() == 0
 
 
+@pytest.mark.parametrize("n,chunk", [(100_003, 32_768), (5, 2)])
+def test_host_pipeline_k8_counts_matches_device_path(dg, n, chunk):
+    """General convex polygons (K = 8, vertex counts, constructed degenerate
+    pairs included) through the staged form."""
+    import torch
+
+    d = W.convex_pairs_4m(seed=43, n=n)
+    r = np.random.default_rng(44)
+    grad = r.normal(size=n).astype(np.float32)
+    hp1, hp2 = torch.from_numpy(d["p1"]).pin_memory(), torch.from_numpy(d["p2"]).pin_memory()
+    hc1, hc2 = torch.from_numpy(d["c1"]).pin_memory(), torch.from_numpy(d["c2"]).pin_memory()
+    hg = torch.from_numpy(grad).pin_memory()
+    iou, g1, g2 = dg.dgal_iou_fwd_bwd_host(hp1, hp2, hg, c1=hc1, c2=hc2, chunk=chunk)
+    torch.cuda.synchronize()
+    p1, p2, c1, c2, gd = dev(d["p1"]), dev(d["p2"]), dev(d["c1"]), dev(d["c2"]), dev(grad)
+    ri, rnx, rxf, _ = dg.dgal_iou_paired(p1, p2, c1, c2)
+    r1, r2 = dg.dgal_iou_backward(p1, p2, gd, rnx, rxf, c1, c2)
+    torch.cuda.synchronize()
+    assert np.array_equal(iou.numpy(), host(ri))
+    assert np.array_equal(g1.numpy(), host(r1)) and np.array_equal(g2.numpy(), host(r2))
+    assert dg.dgal_get_device_status() == 0
+
+
 def test_host_pipeline_oracle_sample_and_edges(dg, orc):
     import torch
 
