@@ -185,7 +185,9 @@ struct NmsStage {
 };
 static_assert(sizeof(NmsStage) % 128 == 0 && (kNmsNear * 8) % 16 == 0, "tiled-load alignment");
 constexpr int kNmsStages = 4;
-constexpr int kNmsWaitSpins = 1 << 20; // bound on an mbarrier wait (then DGAL_DEV_TIMEOUT)
+// Bound on an mbarrier wait, in non-blocking polls (tens of cycles each, so
+// well under a second at GB300 clocks); then DGAL_DEV_TIMEOUT.
+constexpr int kNmsWaitSpins = 1 << 24;
 
 // Box of the tiled load: words per row (even, >= 2: 16-byte rows) and rows.
 __host__ __device__ __forceinline__ int nms_box_words(int64_t Wp) { return Wp < kNmsNear ? (int)Wp : kNmsNear; }
@@ -210,12 +212,14 @@ __device__ __forceinline__ void tiled_load(void* dst, const CUtensorMap* map, in
         : "memory");
 }
 
-// Waits for the phase of `bar` with the given parity; false after kNmsWaitSpins polls.
+// Waits for the phase of `bar` with the given parity; false after kNmsWaitSpins
+// polls.  test_wait never suspends the thread, so the bound is a number of
+// polls rather than a number of system-dependent suspend intervals.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
     const unsigned a = smem_addr(bar);
     for (int i = 0; i < kNmsWaitSpins; ++i) {
         unsigned done;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(done)
                      : "r"(a), "r"(parity)
                      : "memory");
