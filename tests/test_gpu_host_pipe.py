@@ -72,6 +72,32 @@ def test_host_pipeline_k8_counts_matches_device_path(dg, n, chunk):
     assert dg.dgal_get_device_status() == 0
 
 
+def test_host_pipeline_unaligned_pinned_views_take_the_staged_form(dg):
+    """Pinned buffers whose polygon views start 4 bytes into an allocation
+    cannot take the direct form's 16-byte vertex loads: the call stages them,
+    with the same results."""
+    import torch
+
+    n = 10_001
+    d = W.loss_pairs_1m(seed=45, n=n)
+    flat1 = torch.empty(n * 8 + 1).pin_memory()
+    flat2 = torch.empty(n * 8 + 1).pin_memory()
+    hp1 = flat1[1:].view(n, 4, 2)
+    hp2 = flat2[1:].view(n, 4, 2)
+    hp1.copy_(torch.from_numpy(d["p1"]))
+    hp2.copy_(torch.from_numpy(d["p2"]))
+    assert hp1.data_ptr() % 16 != 0
+    hg = torch.ones(n).pin_memory()
+    iou, g1, g2 = dg.dgal_iou_fwd_bwd_host(hp1, hp2, hg, chunk=4096)
+    torch.cuda.synchronize()
+    p1, p2 = dev(d["p1"]), dev(d["p2"])
+    ri, rnx, rxf, _ = dg.dgal_iou_paired(p1, p2)
+    r1, r2 = dg.dgal_iou_backward(p1, p2, dev(np.ones(n, np.float32)), rnx, rxf)
+    torch.cuda.synchronize()
+    assert np.array_equal(iou.numpy(), host(ri))
+    assert np.array_equal(g1.numpy(), host(r1)) and np.array_equal(g2.numpy(), host(r2))
+
+
 def test_host_pipeline_oracle_sample_and_edges(dg, orc):
     import torch
 
