@@ -167,8 +167,9 @@ dgal_status dgal_iou3d_backward(const float* p1, const uint8_t* c1, const float*
  *   iou (float [n], optional) receives the IoUs.
  * K = 4 or 8.  Runs the paired forward with the loss terms summed per warp and
  * the flags kept in `workspace`, then the paired backward with
- * dL/dIoU_k = -scale w_k formed in the kernel, then sums the per-warp partials
- * in a fixed order, so the loss is deterministic.  `workspace`: device memory
+ * dL/dIoU_k = -scale w_k formed in the kernel; one block of the backward sums
+ * the per-warp partials in a fixed order (a separate one-block launch does
+ * when no gradient is wanted), so the loss is deterministic.  `workspace`: device memory
  * of at least dgal_iou_loss_workspace_bytes(n, K) bytes (0 for an invalid K),
  * 16-byte aligned, caller-owned; calls sharing it must not overlap in time.
  * DGAL_PLAIN: FP32 only, and the backward recomputes the clip.

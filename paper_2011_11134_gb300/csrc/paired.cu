@@ -100,14 +100,8 @@ dgal_status launch_iou_loss(const float* p1, const uint8_t* c1, const float* p2,
                             const float* weight, float scale, float* loss, float* iou, float* g1, float* g2,
                             void* ws, uint32_t flags, cudaStream_t s) {
     if (!device_status_ptr()) return fail(DGAL_ERR_CUDA, "device status word unavailable");
-    float* partials = nullptr;
-    int64_t warps = 0;
-    const dgal_status r = iou_loss_passes<false>(p1, c1, p2, c2, n, K, weight, scale, iou, g1, g2,
-                                                 ZArgs{nullptr, nullptr, nullptr, nullptr}, ws, flags, s, &partials,
-                                                 &warps);
-    if (r != DGAL_OK) return r;
-    launch_sum_partials(partials, warps, loss, s);
-    return check_launch("IoU loss reduction");
+    return iou_loss_passes<false>(p1, c1, p2, c2, n, K, weight, scale, loss, iou, g1, g2,
+                                  ZArgs{nullptr, nullptr, nullptr, nullptr}, ws, flags, s);
 }
 
 } // namespace dgal

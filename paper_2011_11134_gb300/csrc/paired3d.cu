@@ -35,13 +35,8 @@ dgal_status launch_iou3d_loss(const float* p1, const uint8_t* c1, const float* z
                               float* iou, float* g1, float* gz1, float* g2, float* gz2, void* ws, uint32_t flags,
                               cudaStream_t s) {
     if (!device_status_ptr()) return fail(DGAL_ERR_CUDA, "device status word unavailable");
-    float* partials = nullptr;
-    int64_t warps = 0;
-    const dgal_status r = iou_loss_passes<true>(p1, c1, p2, c2, n, K, weight, scale, iou, g1, g2,
-                                                ZArgs{z1, z2, gz1, gz2}, ws, flags, s, &partials, &warps);
-    if (r != DGAL_OK) return r;
-    launch_sum_partials(partials, warps, loss, s);
-    return check_launch("3D IoU loss reduction");
+    return iou_loss_passes<true>(p1, c1, p2, c2, n, K, weight, scale, loss, iou, g1, g2, ZArgs{z1, z2, gz1, gz2}, ws,
+                                 flags, s);
 }
 
 } // namespace dgal

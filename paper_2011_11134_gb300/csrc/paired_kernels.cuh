@@ -62,6 +62,8 @@ struct LossArgs {
     const float* weight;
     float scale;
     float* partials; // one float per warp of the forward grid
+    float* loss;     // backward: block 0 writes the sum of the partials here (NULL: not in this launch)
+    int64_t nparts;  // number of partials
 };
 
 // 3D mode of the paired kernels: each box also has a vertical extent
@@ -111,6 +113,43 @@ __device__ __forceinline__ void put_partial(const LossArgs& la, float acc) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     if ((threadIdx.x & 31) == 0) la.partials[((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5] = acc;
+}
+
+// Block 0 of the loss-mode backward sums the forward's per-warp partials in a
+// fixed order before taking its pairs: thread t adds float4 blocks t,
+// t + blockDim, ... (four loads in flight per round, each block's values in
+// order), then the scalar tail, then a fixed tree over the warps.  The order
+// does not depend on scheduling, so the loss is deterministic, and the sum
+// needs no launch of its own: the other blocks go straight to their pairs.
+// partials must be 16-byte aligned.  Block-uniform (it has block barriers).
+__device__ __forceinline__ void loss_fold(const LossArgs& la) {
+    if (!la.loss || blockIdx.x != 0) return;
+    __shared__ float sh[32];
+    const int64_t m = la.nparts, m4 = m / 4, step = blockDim.x;
+    const float4* p4 = reinterpret_cast<const float4*>(la.partials);
+    float v = 0.f;
+    for (int64_t base = 0; base < m4; base += 4 * step) {
+        float4 a[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = base + u * step + threadIdx.x;
+            a[u] = (i < m4) ? __ldg(p4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v += (a[u].x + a[u].y) + (a[u].z + a[u].w);
+    }
+    for (int64_t i = 4 * m4 + threadIdx.x; i < m; i += step) v += la.partials[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float t = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (l == 0) *la.loss = t;
+    }
 }
 
 // Stores the forward results of pair k (and adds its loss term in loss mode).
@@ -222,6 +261,7 @@ k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * kPairThreads;
     const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
+    if constexpr (LOSS) loss_fold(la);
     uint32_t err = 0;
     for (int64_t base = (int64_t)blockIdx.x * kPairThreads + (threadIdx.x & ~31); base < n; base += stride) {
         const int64_t k = base + lane;
@@ -479,6 +519,7 @@ k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
     __shared__ float s_bwd[kPairThreads / 32][32];
     const int lane = threadIdx.x & 31, r = lane & 7;
     const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
+    if constexpr (LOSS) loss_fold(la);
     const int64_t warp = ((int64_t)blockIdx.x * kPairThreads + threadIdx.x) >> 5;
     const int64_t stride = (int64_t)gridDim.x * (kPairThreads / 32) * 4;
     uint32_t err = 0;
@@ -571,13 +612,13 @@ k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
 // ------------------------------------------------------------- IoU loss
 //
 // loss = scale * sum_k w_k (1 - IoU_k) and its gradient (the IoU-loss case
-// study, paper Sec. IV-A) in three launches on one stream: the paired forward
-// in loss mode (no IoU array needed; flags saved to the workspace), the paired
-// backward in loss mode (dL/dIoU formed in the kernel), and a one-block sum of
-// the per-warp partials in a fixed order, so the loss is deterministic.  A
-// single kernel doing both passes was measured slower: with the forward and
-// backward code resident together it needs about 1.5x the registers and
-// stalls on instruction fetch.
+// study, paper Sec. IV-A) in two launches on one stream: the paired forward
+// in loss mode (no IoU array needed; flags saved to the workspace) and the
+// paired backward in loss mode (dL/dIoU formed in the kernel), whose block 0
+// also sums the per-warp partials in a fixed order (loss_fold), so the loss
+// is deterministic.  A single kernel doing both passes was measured slower:
+// with the forward and backward code resident together it needs about 1.5x
+// the registers and stalls on instruction fetch.
 
 static unsigned grid_for(int64_t n, int threads) {
     int64_t blocks = (n + threads - 1) / threads;
@@ -672,16 +713,16 @@ static LossLayout loss_layout(int64_t n, int K) {
     return L;
 }
 
-// The loss passes (forward and backward in loss mode; the partial sum is
-// launched by the caller).
+// The loss passes: the forward in loss mode, then the backward in loss mode
+// with the partial sum folded into its block 0, or (no gradients wanted) the
+// one-block partial sum on its own.
 template <bool Z3>
 static dgal_status iou_loss_passes(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
-                                   int K, const float* weight, float scale, float* iou, float* g1, float* g2,
-                                   const ZArgs& za, void* ws, uint32_t flags, cudaStream_t s, float** partials,
-                                   int64_t* warps) {
+                                   int K, const float* weight, float scale, float* loss, float* iou, float* g1,
+                                   float* g2, const ZArgs& za, void* ws, uint32_t flags, cudaStream_t s) {
     const LossLayout L = loss_layout(n, K);
     unsigned char* base = static_cast<unsigned char*>(ws);
-    const LossArgs la{weight, scale, reinterpret_cast<float*>(base + L.partials)};
+    const LossArgs la{weight, scale, reinterpret_cast<float*>(base + L.partials), nullptr, 0};
     const bool save = g1 && !(flags & kFlagPlain);
     uint8_t* nx = base + L.nx;
     uint8_t* xflags = base + L.xflags;
@@ -689,14 +730,13 @@ static dgal_status iou_loss_passes(const float* p1, const uint8_t* c1, const flo
     dgal_status r = check_launch("IoU loss forward");
     if (r != DGAL_OK) return r;
     if (g1) {
+        const LossArgs lb{weight, scale, la.partials, loss, L.warps};
         bwd_any<true, Z3>(p1, c1, p2, c2, n, K, nullptr, save ? nx : nullptr, save ? xflags : nullptr, g1, g2, flags,
-                          s, la, za);
-        r = check_launch("IoU loss backward");
-        if (r != DGAL_OK) return r;
+                          s, lb, za);
+        return check_launch("IoU loss backward");
     }
-    *partials = la.partials;
-    *warps = L.warps;
-    return DGAL_OK;
+    launch_sum_partials(la.partials, L.warps, loss, s);
+    return check_launch("IoU loss reduction");
 }
 
 } // namespace dgal
