@@ -98,6 +98,17 @@ def test_nms_wide_2600(dg, orc):
     assert 0 < len(keep) < 2600
 
 
+def test_nms_4500_far_words(dg, orc):
+    """4500 boxes: 71 words per row, most of them beyond the 32 the greedy
+    pass stages for each 64-row block."""
+    d = W.pairwise_bev_2000(seed=20, N=4500, M=1)
+    r = np.random.default_rng(74)
+    scores = r.uniform(0, 1, 4500).astype(np.float32)
+    scores[::7] = scores[5]  # ties: lower index first
+    keep = _check(dg, orc, d["a"], scores, 0.45, label="4500 boxes")
+    assert 0 < len(keep) < 4500
+
+
 @pytest.mark.parametrize("n", [1, 2, 63, 64, 65, 129, 200])
 def test_nms_ragged_sizes(dg, orc, n):
     d = W.pairwise_bev_2000(seed=100 + n, N=n, M=1)
