@@ -112,7 +112,7 @@ dgal_status dgal_iou_backward(const float* p1, const uint8_t* c1, const float* p
  * h_grad float [n] = dL/dIoU in; h_iou float [n], h_g1, h_g2 float [n][K][2]
  * out (as dgal_iou_paired then dgal_iou_backward from the saved flags).
  * Results are bit-identical to the device-memory calls.  Two forms:
- *   direct: K = 4 without counts, all six buffers page-locked and mapped into the
+ *   direct: K = 4, all buffers (counts included) page-locked and mapped into the
  *     device's address space (cudaHostAlloc / pinned torch tensors; the
  *     polygon and gradient buffers 16-byte aligned): one kernel reads and
  *     writes the host buffers in place; `workspace` and `chunk` are not used

@@ -363,10 +363,10 @@ def dgal_iou_fwd_bwd_host(p1, p2, grad, c1=None, c2=None, out=None, chunk=131072
                           flags=DGAL_FP64_REFINE, stream=None, device=None):
     """Paired IoU forward + backward on host tensors (CPU float32, ideally
     pinned): p1, p2 [n, K, 2], optional uint8 vertex counts c1, c2 [n],
-    grad [n] -> (iou [n], g1, g2 [n, K, 2]) on the host.  K = 4 without counts
-    and every tensor pinned runs one kernel on the host memory in place (no
-    workspace); otherwise chunked and pipelined (copies overlap the kernels).  Asynchronous on the stream: synchronise before reading the
-    outputs."""
+    grad [n] -> (iou [n], g1, g2 [n, K, 2]) on the host.  K = 4 with every
+    tensor pinned runs one kernel on the host memory in place (no workspace);
+    otherwise chunked and pipelined (copies overlap the kernels).
+    Asynchronous on the stream: synchronise before reading the outputs."""
     for t, name in ((p1, "p1"), (p2, "p2"), (grad, "grad")):
         if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
             raise ValueError(f"{name} must be a contiguous float32 host tensor")
@@ -385,7 +385,7 @@ def dgal_iou_fwd_bwd_host(p1, p2, grad, c1=None, c2=None, out=None, chunk=131072
         out = (torch.empty(n, pin_memory=pin), torch.empty((n, K, 2), pin_memory=pin),
                torch.empty((n, K, 2), pin_memory=pin))
     iou, g1, g2 = out
-    direct = (K == 4 and c1 is None and c2 is None and all(t.is_pinned() for t in (p1, p2, grad, iou, g1, g2))
+    direct = (K == 4 and all(t.is_pinned() for t in (p1, p2, grad, iou, g1, g2, c1, c2) if t is not None)
               and all(t.data_ptr() % 16 == 0 for t in (p1, p2, g1, g2)))
     if workspace is None and not direct:
         workspace = torch.empty(dgal_iou_host_workspace_bytes(chunk, K) + 256, device=dev, dtype=torch.uint8)

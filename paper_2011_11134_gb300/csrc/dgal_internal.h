@@ -36,9 +36,10 @@ dgal_status launch_paired_fwd(const float* p1, const uint8_t* c1, const float* p
 dgal_status launch_paired_bwd(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
                               int K, const float* grad, const uint8_t* nx, const uint8_t* xflags, float* g1,
                               float* g2, uint32_t flags, cudaStream_t s);
-// K = 4, no counts: forward + backward in one pass (pointers may be device-mapped host memory).
-dgal_status launch_paired_fused(const float* p1, const float* p2, int64_t n, const float* grad, float* iou, float* g1,
-                                float* g2, uint32_t flags, cudaStream_t s);
+// K = 4: forward + backward in one pass (pointers may be device-mapped host memory).
+dgal_status launch_paired_fused(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                                int K, const float* grad, float* iou, float* g1, float* g2, uint32_t flags,
+                                cudaStream_t s);
 dgal_status launch_pairwise(const float* a, const uint8_t* ca, int64_t N, const float* b, const uint8_t* cb,
                             int64_t M, int K, float* iou, uint8_t* nx, uint32_t flags, cudaStream_t s);
 size_t batched_workspace_bytes(int S);

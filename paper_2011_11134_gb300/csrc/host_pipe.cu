@@ -3,11 +3,13 @@
 // The paired kernels take a few tens of microseconds per million pairs; for
 // data that lives in host memory the host link dominates.  Two forms:
 //
-// Direct (K = 4 without counts, every buffer pinned and mapped into the
-// device's address space): one kernel reads the polygons and dL/dIoU from host memory and
-// writes IoU and both gradients back, the clip state staying in registers
-// between the forward and the backward (k_paired_fused).  Loads from both
-// directions are in flight together, and nothing is staged.
+// Direct (K = 4, every buffer pinned and mapped into the device's address
+// space): one kernel reads the polygons (and counts) and dL/dIoU from host
+// memory and writes IoU and both gradients back, the clip state staying in
+// registers between the forward and the backward (k_paired_fused).  Loads
+// from both directions are in flight together, and nothing is staged.  (A
+// K = 8 one-pass kernel measured slower than the staged form: it needs 168
+// registers, and its warp path reads the polygons again over the link.)
 //
 // Staged (otherwise): the pairs go in chunks; for chunk c in staging slot
 // c mod 3 (the counts, when given, travel with the polygons):
@@ -140,18 +142,22 @@ extern "C" dgal_status dgal_iou_fwd_bwd_host(const float* h_p1, const uint8_t* h
     if (chunk <= 0) return fail(DGAL_ERR_INVALID_ARG, "chunk = %lld must be positive", (long long)chunk);
     if (!h_p1 || !h_p2 || !h_grad || !h_iou || !h_g1 || !h_g2)
         return fail(DGAL_ERR_INVALID_ARG, "a host buffer is NULL");
-    if (K == 4 && !h_c1 && !h_c2) {
+    if (K == 4) {
         void* d_p1 = mapped(h_p1);
         void* d_p2 = mapped(h_p2);
         void* d_grad = mapped(h_grad);
         void* d_iou = mapped(h_iou);
         void* d_g1 = mapped(h_g1);
         void* d_g2 = mapped(h_g2);
+        void* d_c1 = h_c1 ? mapped(h_c1) : nullptr;
+        void* d_c2 = h_c2 ? mapped(h_c2) : nullptr;
         // 16-byte vertex loads and stores
         const bool aligned = ((reinterpret_cast<uintptr_t>(d_p1) | reinterpret_cast<uintptr_t>(d_p2) |
                                reinterpret_cast<uintptr_t>(d_g1) | reinterpret_cast<uintptr_t>(d_g2)) & 15u) == 0;
-        if (d_p1 && d_p2 && d_grad && d_iou && d_g1 && d_g2 && aligned)
-            return launch_paired_fused(static_cast<const float*>(d_p1), static_cast<const float*>(d_p2), n,
+        const bool counts_ok = (!h_c1 || d_c1) && (!h_c2 || d_c2);
+        if (d_p1 && d_p2 && d_grad && d_iou && d_g1 && d_g2 && counts_ok && aligned)
+            return launch_paired_fused(static_cast<const float*>(d_p1), static_cast<const uint8_t*>(d_c1),
+                                       static_cast<const float*>(d_p2), static_cast<const uint8_t*>(d_c2), n, K,
                                        static_cast<const float*>(d_grad), static_cast<float*>(d_iou),
                                        static_cast<float*>(d_g1), static_cast<float*>(d_g2), flags,
                                        (cudaStream_t)stream);

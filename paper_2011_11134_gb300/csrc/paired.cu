@@ -86,11 +86,17 @@ dgal_status launch_paired_bwd(const float* p1, const uint8_t* c1, const float* p
     return check_launch("paired backward");
 }
 
-dgal_status launch_paired_fused(const float* p1, const float* p2, int64_t n, const float* grad, float* iou, float* g1,
-                                float* g2, uint32_t flags, cudaStream_t s) {
-    if (!device_status_ptr()) return fail(DGAL_ERR_CUDA, "device status word unavailable");
-    k_paired_fused<4><<<paired_grid(n, 4), kPairThreads, 0, s>>>(p1, p2, n, grad, iou, g1, g2, flags,
-                                                                 device_status_ptr());
+dgal_status launch_paired_fused(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                                int K, const float* grad, float* iou, float* g1, float* g2, uint32_t flags,
+                                cudaStream_t s) {
+    uint32_t* st = device_status_ptr();
+    if (!st) return fail(DGAL_ERR_CUDA, "device status word unavailable");
+    if (K != 4) return fail(DGAL_ERR_UNSUPPORTED_K, "the one-pass form takes K = 4");
+    const unsigned grid = paired_grid(n, K);
+    if (c1 || c2)
+        k_paired_fused<4, true><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, grad, iou, g1, g2, flags, st);
+    else
+        k_paired_fused<4, false><<<grid, kPairThreads, 0, s>>>(p1, c1, p2, c2, n, grad, iou, g1, g2, flags, st);
     return check_launch("paired forward + backward");
 }
 

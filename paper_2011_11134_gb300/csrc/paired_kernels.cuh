@@ -351,17 +351,17 @@ k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
 }
 
 // Forward and backward in one pass, for pairs that live in pinned host
-// memory the kernel reads and writes in place (K = 4, no counts): the step is
-// then bound by the host link, and the clip state stays in registers between
-// the two halves instead of making a round trip as flags.  Every value is the
-// one the separate kernels give: the forward is k_paired_fwd's (with its
-// hand-back of hard pairs to warp_robust), and the backward is k_paired_bwd's
-// from the codes the forward just produced.
-template <int K>
+// memory the kernel reads and writes in place: the step is then bound by the
+// host link, and the clip state stays in registers between the two halves
+// instead of making a round trip as flags.  Every value is the one the
+// separate kernels give: the forward is k_paired_fwd's (with its hand-back of
+// hard pairs to warp_robust), and the backward is k_paired_bwd's from the
+// codes the forward just produced.
+template <int K, bool COUNTS>
 __global__ void __launch_bounds__(kPairThreads, 4)
-k_paired_fused(const float* __restrict__ p1, const float* __restrict__ p2, int64_t n, const float* __restrict__ grad,
-               float* __restrict__ iou, float* __restrict__ g1, float* __restrict__ g2, uint32_t flags,
-               uint32_t* status) {
+k_paired_fused(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
+               const uint8_t* __restrict__ c2, int64_t n, const float* __restrict__ grad, float* __restrict__ iou,
+               float* __restrict__ g1, float* __restrict__ g2, uint32_t flags, uint32_t* status) {
     constexpr unsigned full = 0xffffffffu;
     __shared__ float s_bwd[kPairThreads / 32][4 * K];
     const int lane = threadIdx.x & 31;
@@ -372,30 +372,41 @@ k_paired_fused(const float* __restrict__ p1, const float* __restrict__ p2, int64
     for (int64_t base = (int64_t)blockIdx.x * kPairThreads + (threadIdx.x & ~31); base < n; base += stride) {
         const int64_t k = base + lane;
         const bool live = k < n;
+        int n1 = K, n2 = K;
+        if (COUNTS && live) {
+            n1 = c1 ? (int)c1[k] : K;
+            n2 = c2 ? (int)c2[k] : K;
+        }
+        const bool good = live && (!COUNTS || (n1 >= 3 && n1 <= K && n2 >= 3 && n2 <= K));
         float px[K], py[K], qx[K], qy[K];
         FwdOut<K> o;
+        o.iou = 0.f;
         bool hard = false;
-        if (live) {
+        if (good) {
             load_poly<K>(p1 + k * 2 * K, px, py);
             load_poly<K>(p2 + k * 2 * K, qx, qy);
             Geo<K> g;
-            make_geo<K, false>(px, py, qx, qy, K, K, g);
-            input_areas<K, false>(g, o.a1, o.a2);
-            hard = refine ? !fwd_generic<K, false>(g, o, p1 + k * 2 * K, p2 + k * 2 * K) : !fwd_generic<K, false>(g, o);
+            make_geo<K, COUNTS>(px, py, qx, qy, n1, n2, g);
+            input_areas<K, COUNTS>(g, o.a1, o.a2);
+            hard = refine ? !fwd_generic<K, COUNTS>(g, o, p1 + k * 2 * K, p2 + k * 2 * K)
+                          : !fwd_generic<K, COUNTS>(g, o);
             hard = hard || (o.nx >= 3u && o.a1 + o.a2 - o.ai < kThinRel * o.L2);
             if (!hard) {
                 const float U = o.a1 + o.a2 - o.ai;
                 o.iou = (o.nx >= 3u && U > 0.f) ? o.ai / U : 0.f;
             }
+        } else if (live) {
+            err |= kDevBadCount;
         }
         unsigned todo = __ballot_sync(full, hard);
         while (todo) {
             const int src = __ffs(todo) - 1;
             todo &= todo - 1;
             const int64_t kk = base + src;
+            const int m1 = __shfl_sync(full, n1, src), m2 = __shfl_sync(full, n2, src);
             FwdOut<K> r;
             r.err = 0;
-            warp_robust<K>(p1 + kk * 2 * K, p2 + kk * 2 * K, K, K, refine, r);
+            warp_robust<K>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, refine, r);
             if (lane == src) {
                 err |= r.err;
                 o.iou = r.iou;
@@ -406,14 +417,19 @@ k_paired_fused(const float* __restrict__ p1, const float* __restrict__ p2, int64
         bool slow = false;
         if (live) {
             iou[k] = o.iou;
-            Geo<K> g;
-            make_geo<K, false>(px, py, qx, qy, K, K, g);
             float g1x[K], g1y[K], g2x[K], g2y[K];
-            auto adj = adj_of<false>(grad[k], za, k);
-            const uint32_t e = bwd_shape<K, false>(g, adj, o.nx, o.codes, refine, g1x, g1y, g2x, g2y);
-            slow = e == kSlow;
+            if (good) {
+                Geo<K> g;
+                make_geo<K, COUNTS>(px, py, qx, qy, n1, n2, g);
+                auto adj = adj_of<false>(grad[k], za, k);
+                const uint32_t e = bwd_shape<K, COUNTS>(g, adj, o.nx, o.codes, refine, g1x, g1y, g2x, g2y);
+                slow = e == kSlow;
+                if (!slow) err |= e;
+            } else {
+#pragma unroll
+                for (int v = 0; v < K; ++v) { g1x[v] = g1y[v] = g2x[v] = g2y[v] = 0.f; }
+            }
             if (!slow) {
-                err |= e;
                 store_poly<K>(g1 + k * 2 * K, g1x, g1y);
                 store_poly<K>(g2 + k * 2 * K, g2x, g2y);
             }
@@ -423,14 +439,15 @@ k_paired_fused(const float* __restrict__ p1, const float* __restrict__ p2, int64
             const int src = __ffs(todo) - 1;
             todo &= todo - 1;
             const int64_t kk = base + src;
+            const int m1 = __shfl_sync(full, n1, src), m2 = __shfl_sync(full, n2, src);
             const uint32_t mnx = __shfl_sync(full, o.nx, src);
             Codes<K> cs;
 #pragma unroll
             for (int q = 0; q < (2 * K + 7) / 8; ++q) cs.w[q] = __shfl_sync(full, o.codes.w[q], src);
             auto a = adj_of<false>(grad[kk], za, kk);
-            const uint32_t e = refine ? warp_bwd<K, double>(p1 + kk * 2 * K, p2 + kk * 2 * K, K, K, a, mnx, cs,
+            const uint32_t e = refine ? warp_bwd<K, double>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, a, mnx, cs,
                                                             g1 + kk * 2 * K, g2 + kk * 2 * K, s_bwd[threadIdx.x >> 5])
-                                      : warp_bwd<K, float>(p1 + kk * 2 * K, p2 + kk * 2 * K, K, K, a, mnx, cs,
+                                      : warp_bwd<K, float>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, a, mnx, cs,
                                                            g1 + kk * 2 * K, g2 + kk * 2 * K, s_bwd[threadIdx.x >> 5]);
             if (lane == src) err |= e;
         }

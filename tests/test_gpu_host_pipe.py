@@ -49,18 +49,22 @@ def test_host_pipeline_matches_device_path(dg, n, chunk, pinned):
     assert dg.dgal_get_device_status() == 0
 
 
-@pytest.mark.parametrize("n,chunk", [(100_003, 32_768), (5, 2)])
-def test_host_pipeline_k8_counts_matches_device_path(dg, n, chunk):
-    """General convex polygons (K = 8, vertex counts, constructed degenerate
-    pairs included) through the staged form."""
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("K,n,chunk", [(8, 100_003, 32_768), (8, 5, 2), (4, 30_001, 8_192)])
+def test_host_pipeline_counts_matches_device_path(dg, K, n, chunk, pinned):
+    """General convex polygons with vertex counts (K = 8: constructed
+    degenerate pairs included, always staged; K = 4: triangles and
+    quadrilaterals, the direct form when pinned) through the host call."""
     import torch
 
-    d = W.convex_pairs_4m(seed=43, n=n)
+    d = W.convex_pairs_4m(seed=43, n=n, K=K, degenerate_frac=0.05 if K == 8 else 0.0)
     r = np.random.default_rng(44)
     grad = r.normal(size=n).astype(np.float32)
-    hp1, hp2 = torch.from_numpy(d["p1"]).pin_memory(), torch.from_numpy(d["p2"]).pin_memory()
-    hc1, hc2 = torch.from_numpy(d["c1"]).pin_memory(), torch.from_numpy(d["c2"]).pin_memory()
-    hg = torch.from_numpy(grad).pin_memory()
+    hp1, hp2 = torch.from_numpy(d["p1"]), torch.from_numpy(d["p2"])
+    hc1, hc2 = torch.from_numpy(d["c1"]), torch.from_numpy(d["c2"])
+    hg = torch.from_numpy(grad)
+    if pinned:
+        hp1, hp2, hc1, hc2, hg = (t.pin_memory() for t in (hp1, hp2, hc1, hc2, hg))
     iou, g1, g2 = dg.dgal_iou_fwd_bwd_host(hp1, hp2, hg, c1=hc1, c2=hc2, chunk=chunk)
     torch.cuda.synchronize()
     p1, p2, c1, c2, gd = dev(d["p1"]), dev(d["p2"]), dev(d["c1"]), dev(d["c2"]), dev(grad)
