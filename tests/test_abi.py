@@ -93,3 +93,27 @@ def test_nms_host_checks(libdgal):
     assert f(al + 8, None, al, 10, 4, 0.5, al, al, al, 1 << 20, 0, None) == 3  # boxes misaligned
     assert f(al, None, al, 10, 4, 0.5, al, al, al, 16, 0, None) == 5  # workspace too small
     assert f(al, None, al, 10, 4, 0.5, al, al, None, 1 << 20, 0, None) == 5  # workspace NULL
+
+
+def test_host_call_checks(libdgal):
+    """dgal_iou_fwd_bwd_host validates its arguments on the host, before any
+    device work; its workspace sizing is host arithmetic."""
+    wsb = libdgal.dgal_iou_host_workspace_bytes
+    wsb.restype = ctypes.c_size_t
+    wsb.argtypes = [ctypes.c_int64, ctypes.c_int]
+    assert wsb(1000, 4) >= 3 * 1000 * (2 * 32 + 4 + 4 + 1 + 8 + 2 * 32 + 2)
+    assert wsb(1000, 8) > wsb(1000, 4) and wsb(1000, 5) == 0 and wsb(0, 4) == 0
+    f = libdgal.dgal_iou_fwd_bwd_host
+    P = ctypes.c_void_p
+    f.argtypes = [P, P, P, P, P, ctypes.c_int64, ctypes.c_int, P, P, P, P, ctypes.c_size_t, ctypes.c_int64,
+                  ctypes.c_uint32, P]
+    f.restype = ctypes.c_int
+    buf = (ctypes.c_float * 64)()
+    a = ctypes.addressof(buf)
+    assert f(a, None, a, None, a, 4, 5, a, a, a, None, 0, 16, 0, None) == 2  # K unsupported
+    assert f(a, None, a, None, a, -1, 4, a, a, a, None, 0, 16, 0, None) == 1  # negative n
+    assert f(a, None, a, None, a, 0, 4, a, a, a, None, 0, 16, 0, None) == 0  # n = 0: nothing to do
+    assert f(a, None, a, None, a, 4, 4, a, a, a, None, 0, 0, 0, None) == 1  # chunk not positive
+    assert f(a, None, a, None, None, 4, 4, a, a, a, None, 0, 16, 0, None) == 1  # grad NULL
+    # pageable buffers take the staged form, which needs a workspace
+    assert f(a, None, a, None, a, 4, 8, a, a, a, None, 0, 16, 0, None) == 5
