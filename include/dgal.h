@@ -336,7 +336,9 @@ dgal_status dgal_graph_destroy(dgal_graph graph);
  * problem generated on the current device and keeps the fastest per (device,
  * K).  cache_path (or, when NULL, the environment variable DGAL_TUNE_CACHE)
  * names a JSON file that is read first and rewritten with the result; NULL and
- * no variable means an in-memory cache only.  config_class is reserved (0).
+ * no variable means an in-memory cache only.  A cached shape outside what the
+ * kernel accepts (threads a multiple of 32 up to 256, 1 to 64 blocks per SM,
+ * a positive tile) is ignored and the shape tuned again.  config_class is reserved (0).
  * This call allocates device memory and synchronises: call it before timing
  * or capturing, never inside a capture.
  */

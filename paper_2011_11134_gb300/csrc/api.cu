@@ -496,6 +496,14 @@ std::string device_key(int K) {
     return buf;
 }
 
+// A launch shape the ragged-batch kernel accepts: whole warps, at most 256
+// threads (the tile's queue codes hold the column in 8 bits), 1 to 64
+// resident blocks per SM, a positive tile.  Cache entries outside this are
+// ignored.
+bool valid_config(int t, int th, int b) {
+    return t > 0 && th >= 32 && th <= 256 && th % 32 == 0 && b >= 1 && b <= 64;
+}
+
 // Tiny JSON map {"key": [tile, threads, blocks_sm], ...} (one line per entry).
 std::map<std::string, BatchedConfig> read_cache(const std::string& path) {
     std::map<std::string, BatchedConfig> m;
@@ -510,7 +518,7 @@ std::map<std::string, BatchedConfig> read_cache(const std::string& path) {
         std::string key(q1 + 1, q2);
         int t = 0, th = 0, b = 0;
         char* br = strchr(q2, '[');
-        if (br && sscanf(br, "[%d, %d, %d]", &t, &th, &b) == 3 && t > 0 && th > 0 && b > 0) m[key] = BatchedConfig{t, th, b};
+        if (br && sscanf(br, "[%d, %d, %d]", &t, &th, &b) == 3 && valid_config(t, th, b)) m[key] = BatchedConfig{t, th, b};
     }
     fclose(f);
     return m;

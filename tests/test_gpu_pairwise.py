@@ -143,3 +143,17 @@ def test_autotune_cache(dg, tmp_path):
     assert "K=4" in text
     # a second call reads the cache
     assert dg.dgal_autotune(4, cache_path=path) == cfg
+
+
+def test_autotune_cache_rejects_invalid_shapes(dg, tmp_path):
+    """A cached shape the ragged kernel cannot take (512 threads: the queue
+    codes hold the column in 8 bits) is ignored and the shape tuned again."""
+    path = tmp_path / "tune.json"
+    cfg = dg.dgal_autotune(4, cache_path=path)
+    text = path.read_text()
+    key = text.split('"')[1]
+    path.write_text('{\n  "%s": [4096, 512, 4]\n}\n' % key)
+    again = dg.dgal_autotune(4, cache_path=path)
+    assert again["threads"] in (128, 256) and again["threads"] * again["blocks_per_sm"] <= 2048
+    assert ", 512," not in path.read_text()
+    assert dg.dgal_get_device_status() == 0
