@@ -224,7 +224,8 @@ dgal_status dgal_iou3d_backward(const float* p1, const uint8_t* c1, const float*
 }
 
 size_t dgal_iou_loss_workspace_bytes(int64_t n, int K) {
-    return (n < 0 || (K != 4 && K != 8)) ? 0 : loss_workspace_bytes(n, K);
+    // beyond 2^40 pairs (64 TB of polygons) the size would overflow; no such input fits in memory
+    return (n < 0 || n > (int64_t(1) << 40) || (K != 4 && K != 8)) ? 0 : loss_workspace_bytes(n, K);
 }
 
 dgal_status dgal_iou_loss(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n, int K,

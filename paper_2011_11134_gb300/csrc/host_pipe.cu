@@ -128,7 +128,8 @@ void* mapped(const void* h) {
 using namespace dgal;
 
 extern "C" size_t dgal_iou_host_workspace_bytes(int64_t chunk, int K) {
-    if ((K != 4 && K != 8) || chunk <= 0) return 0;
+    // beyond 2^40 pairs per chunk the size would overflow; no such slot fits in memory
+    if ((K != 4 && K != 8) || chunk <= 0 || chunk > (int64_t(1) << 40)) return 0;
     return kSlots * slot_layout(chunk, K).bytes;
 }
 
@@ -162,6 +163,7 @@ extern "C" dgal_status dgal_iou_fwd_bwd_host(const float* h_p1, const uint8_t* h
                                        static_cast<float*>(d_g1), static_cast<float*>(d_g2), flags,
                                        (cudaStream_t)stream);
     }
+    if (chunk > n) chunk = n; // a slot never needs more than the pairs there are
     if (!workspace) return fail(DGAL_ERR_WORKSPACE, "workspace is NULL");
     if (reinterpret_cast<uintptr_t>(workspace) & 255u)
         return fail(DGAL_ERR_ALIGNMENT, "workspace is not 256-byte aligned");

@@ -117,3 +117,13 @@ def test_host_call_checks(libdgal):
     assert f(a, None, a, None, None, 4, 4, a, a, a, None, 0, 16, 0, None) == 1  # grad NULL
     # pageable buffers take the staged form, which needs a workspace
     assert f(a, None, a, None, a, 4, 8, a, a, a, None, 0, 16, 0, None) == 5
+
+
+def test_workspace_sizes_refuse_overflowing_counts(libdgal):
+    """Sizing calls return 0 for pair counts whose workspace size would
+    overflow (no such input fits in memory)."""
+    for name in ("dgal_iou_host_workspace_bytes", "dgal_iou_loss_workspace_bytes"):
+        f = getattr(libdgal, name)
+        f.restype = ctypes.c_size_t
+        f.argtypes = [ctypes.c_int64, ctypes.c_int]
+        assert f(1 << 62, 4) == 0 and f(-5, 4) == 0
