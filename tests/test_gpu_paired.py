@@ -172,6 +172,32 @@ def test_convex_k8_with_degenerate(dg, orc):
     assert dg.dgal_get_device_status() == 0
 
 
+def test_convex_k8_full_size_sampled(dg, orc):
+    """The 4M-pair convex workload at full size, in the bench's launch
+    configuration (forward saving flags, backward from them), checked on a
+    sample the oracle computes pair by pair: 20,000 random pairs plus 2,000
+    constructed near-degenerate ones."""
+    import torch
+
+    d = W.convex_pairs_4m(seed=0)
+    n = d["p1"].shape[0]
+    p1, p2, c1, c2 = dev(d["p1"]), dev(d["p2"]), dev(d["c1"]), dev(d["c2"])
+    iou, nx, xf, degen = dg.dgal_iou_paired(p1, p2, c1, c2, with_degen=True)
+    g1, g2 = dg.dgal_iou_backward(p1, p2, torch.ones(n, device="cuda"), nx, xf, c1, c2)
+    torch.cuda.synchronize()
+    assert dg.dgal_get_device_status() == 0
+    rng = np.random.default_rng(11)
+    idx = np.union1d(rng.choice(n, 20_000, replace=False), rng.choice(np.flatnonzero(d["kind"] > 0), 2_000,
+                                                                      replace=False))
+    s1, s2, sc1, sc2 = d["p1"][idx], d["p2"][idx], d["c1"][idx], d["c2"][idx]
+    ref = orc.iou_paired(s1, s2, sc1, sc2, threads=THREADS)
+    gen = check_forward(host(iou)[idx], host(nx)[idx], host(xf)[idx], host(degen)[idx], ref, "convex 4M sample")
+    o1, o2 = orc.iou_backward_paired(s1, s2, np.ones(len(idx)), ref["nx"], ref["xflags"], sc1, sc2,
+                                     threads=THREADS)
+    rel = grad_rel_err(host(g1)[idx], host(g2)[idx], o1, o2, gen)
+    assert rel.max() <= GRAD_RTOL, f"convex 4M sample grads: max rel err {rel.max():.3e}"
+
+
 def test_plain_form_generic_parity(dg, orc):
     """DGAL_PLAIN (FP32 only, recompute backward) matches on generic pairs."""
     d = W.paired_rect_4096(seed=4)
