@@ -28,10 +28,11 @@ constexpr int64_t kFlatMaxCols = 96;
 // Rows of a ragged-batch tile: entries per tile / threads, at most this.
 constexpr int kMaxTileRows = 32;
 
-// Tiles of the N x M matrix: kTileRows rows x kPwThreads columns (32 rows
-// measured fastest on the 2000 x 2000 bird's-eye matrix: 26.6 us, against
-// 29.4 at 16 rows and 33.5 at 8; more rows give each tile more queued
-// entries, so more of its warps clip at once).
+// Tiles of the N x M matrix: kTileRows rows x kPwThreads columns.  On the
+// 2000 x 2000 bird's-eye matrix, 32 rows measured 26.6 us against 29.4 at 16
+// rows and 33.5 at 8 while blocks looped over tiles; with one tile per block,
+// 16, 32 and 64 rows measured within 24.6-25.4 us.  More rows give each tile
+// more queued entries, so more of its warps clip at once.
 constexpr int kTileRows = 32;
 
 // Blocks per SM the K = 4 tile kernel is compiled for (registers <= 65536 /
