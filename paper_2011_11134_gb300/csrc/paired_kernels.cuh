@@ -7,7 +7,9 @@
 // 2K code bytes as one 64/128-bit store, plus an optional degeneracy byte.
 // Backward (paper Sec. II-B `iou_backward`): reads the polygons, dL/dIoU and
 // the recorded (nx, xflags), or recomputes the clip, and writes both
-// gradients with 128-bit stores.
+// gradients with 128-bit stores.  One-pass form (k_paired_fused, K = 4): both
+// halves in one kernel for pairs in pinned host memory, the codes kept in
+// registers between them.
 #pragma once
 
 #include "dgal_geom.cuh"
