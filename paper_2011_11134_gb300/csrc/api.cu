@@ -299,8 +299,13 @@ size_t dgal_batched_workspace_bytes(int S, int K) {
     return S < 0 ? 0 : batched_workspace_bytes(S);
 }
 
-static dgal_status check_batched(int S, const int64_t* a_off, const int64_t* b_off, const int64_t* out_off,
-                                 const float* a, const float* b, int K, float* iou, void* ws, size_t ws_bytes) {
+} // extern "C"
+
+namespace dgal {
+void clear_last_error() { t_last_error.clear(); }
+
+dgal_status check_batched_args(int S, const int64_t* a_off, const int64_t* b_off, const int64_t* out_off,
+                               const float* a, const float* b, int K, const float* iou) {
     DGAL_TRY(check_K(K));
     if (S < 0) return fail(DGAL_ERR_INVALID_ARG, "S = %d is negative", S);
     if (!a_off || !b_off || !out_off) return fail(DGAL_ERR_INVALID_ARG, "offset arrays must not be NULL");
@@ -310,6 +315,15 @@ static dgal_status check_batched(int S, const int64_t* a_off, const int64_t* b_o
     DGAL_TRY(check_poly_ptr(b, "b"));
     if (!iou) return fail(DGAL_ERR_INVALID_ARG, "iou is NULL");
     if (!aligned(iou, 4)) return fail(DGAL_ERR_ALIGNMENT, "iou is not 4-byte aligned");
+    return DGAL_OK;
+}
+} // namespace dgal
+
+extern "C" {
+
+static dgal_status check_batched(int S, const int64_t* a_off, const int64_t* b_off, const int64_t* out_off,
+                                 const float* a, const float* b, int K, float* iou, void* ws, size_t ws_bytes) {
+    DGAL_TRY(check_batched_args(S, a_off, b_off, out_off, a, b, K, iou));
     if (!ws) return fail(DGAL_ERR_WORKSPACE, "workspace is NULL");
     if (!aligned(ws, 16)) return fail(DGAL_ERR_ALIGNMENT, "workspace is not 16-byte aligned");
     if (ws_bytes < batched_workspace_bytes(S))

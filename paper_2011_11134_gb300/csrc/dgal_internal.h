@@ -11,6 +11,12 @@ namespace dgal {
 
 // Records a message for dgal_last_error() and returns `st`.
 dgal_status fail(dgal_status st, const char* fmt, ...);
+// Clears the calling host thread's dgal_last_error() message.
+void clear_last_error();
+// Argument checks of the ragged batch that do not involve its workspace (K,
+// S, offset / polygon / output pointers and their alignment).
+dgal_status check_batched_args(int S, const int64_t* a_off, const int64_t* b_off, const int64_t* out_off,
+                               const float* a, const float* b, int K, const float* iou);
 // Checks cudaGetLastError after a launch.
 dgal_status check_launch(const char* what);
 // Number of SMs of the current device (cached per device).

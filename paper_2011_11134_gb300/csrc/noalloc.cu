@@ -57,8 +57,11 @@ extern "C" dgal_status dgal_iou_pairwise_batched_noalloc(int S, const int64_t* a
                                                          const int64_t* out_off, const float* a, const uint8_t* ca,
                                                          const float* b, const uint8_t* cb, int K, float* iou,
                                                          uint8_t* nx, uint32_t flags, void* stream) {
+    clear_last_error();
     if (S == 0) return DGAL_OK;
-    if (S < 0) return fail(DGAL_ERR_INVALID_ARG, "S = %d is negative", S);
+    // the arguments are checked first, so a bad K or pointer is reported as
+    // such whatever S is
+    if (dgal_status st = check_batched_args(S, a_off, b_off, out_off, a, b, K, iou); st != DGAL_OK) return st;
     if (S > kNoAllocMaxScenes)
         return fail(DGAL_ERR_WORKSPACE,
                     "S = %d scenes exceeds the fixed scratch of dgal_iou_pairwise_batched_noalloc (at most %d); "

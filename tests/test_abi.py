@@ -127,3 +127,23 @@ def test_workspace_sizes_refuse_overflowing_counts(libdgal):
         f.restype = ctypes.c_size_t
         f.argtypes = [ctypes.c_int64, ctypes.c_int]
         assert f(1 << 62, 4) == 0 and f(-5, 4) == 0
+
+
+def test_noalloc_host_checks(libdgal):
+    """The allocation-free ragged batch checks its arguments before its scene
+    limit, and a call that succeeds clears the previous call's message."""
+    f = libdgal.dgal_iou_pairwise_batched_noalloc
+    P = ctypes.c_void_p
+    f.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, ctypes.c_int, P, P, ctypes.c_uint32, P]
+    f.restype = ctypes.c_int
+    libdgal.dgal_last_error.restype = ctypes.c_char_p
+    buf = (ctypes.c_double * 64)()
+    base = ctypes.addressof(buf)
+    al = base + (-base % 16)
+    assert f(5000, al, al, al, al, None, al, None, 5, al, None, 0, None) == 2  # K before the limit
+    assert f(5000, None, al, al, al, None, al, None, 4, al, None, 0, None) == 1  # NULL offsets before the limit
+    assert f(5000, al, al, al, al + 4, None, al, None, 4, al, None, 0, None) == 3  # misaligned polygons
+    assert f(5000, al, al, al, al, None, al, None, 4, al, None, 0, None) == 5  # beyond 4096 scenes
+    assert b"4096" in libdgal.dgal_last_error()
+    assert f(0, None, None, None, None, None, None, None, 4, None, None, 0, None) == 0  # S = 0: no launch
+    assert libdgal.dgal_last_error() == b""

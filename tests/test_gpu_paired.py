@@ -4,7 +4,7 @@ import pytest
 
 from paper_2011_11134_gb300 import workloads as W
 
-from .gpu_helpers import GRAD_RTOL, IOU_ATOL, THREADS, check_forward, dev, grad_rel_err, host
+from .gpu_helpers import GRAD_RTOL, IOU_ATOL, THREADS, check_flagged_grads, check_forward, dev, grad_rel_err, host
 
 pytestmark = pytest.mark.gpu
 
@@ -77,6 +77,7 @@ def test_loss_pairs_full_size(dg, orc):
                                      threads=THREADS)
     rel = grad_rel_err(host(g1), host(g2), o1, o2, gen)
     assert rel.max() <= GRAD_RTOL, f"1M grads: max rel err {rel.max():.3e} at {int(rel.argmax())}"
+    check_flagged_grads(host(g1), host(g2), d["p1"], d["p2"], None, None, ref, ~gen, label="loss 1M")
     # pairs whose small orientations took the FP64 definition's sign (degen
     # bit 1) keep the definition's combinatorics: nx and xflags as the oracle's
     rep = (host(degen) & 2) != 0
@@ -165,6 +166,7 @@ def test_convex_k8_with_degenerate(dg, orc):
                                      d["c2"], threads=THREADS)
     rel = grad_rel_err(host(g1), host(g2), o1, o2, gen)
     assert rel.max() <= GRAD_RTOL, f"K=8 grads: max rel err {rel.max():.3e} at {int(np.nonzero(gen)[0][rel.argmax()])}"
+    check_flagged_grads(host(g1), host(g2), d["p1"], d["p2"], d["c1"], d["c2"], ref, ~gen, label="convex K=8")
     # padded slots get exactly zero gradient
     cnt1 = d["c1"].astype(int)
     pad = np.arange(8)[None, :] >= cnt1[:, None]
@@ -196,6 +198,7 @@ def test_convex_k8_full_size_sampled(dg, orc):
                                      threads=THREADS)
     rel = grad_rel_err(host(g1)[idx], host(g2)[idx], o1, o2, gen)
     assert rel.max() <= GRAD_RTOL, f"convex 4M sample grads: max rel err {rel.max():.3e}"
+    check_flagged_grads(host(g1)[idx], host(g2)[idx], s1, s2, sc1, sc2, ref, ~gen, label="convex 4M sample")
 
 
 def test_plain_form_generic_parity(dg, orc):

@@ -30,15 +30,23 @@ def _check_matrix(iou, nx, ref_iou, ref_nx, label):
     return np.nonzero(nx != ref_nx)
 
 
+def _assert_flagged(orc, a, b, rows, cols, ca=None, cb=None, label=""):
+    """Every (row, col) entry whose nx differs from the oracle's must be a pair
+    the oracle classifies near-degenerate."""
+    if len(rows) == 0:
+        return
+    o = orc.iou_paired(a[rows], b[cols], None if ca is None else ca[rows], None if cb is None else cb[cols])
+    bad = np.nonzero(o["degen"] == 0)[0]
+    assert bad.size == 0, f"{label}: nx differs on {bad.size} pairs the oracle does not flag, first {bad[:5]}"
+
+
 def test_pairwise_bev_full(dg, orc):
     """The 2000 x 2000 bird's-eye matrix, every entry."""
     d = W.pairwise_bev_2000(seed=0)
     iou, nx = dg.dgal_iou_pairwise(dev(d["a"]), dev(d["b"]))
     ref_iou, ref_nx = orc.iou_pairwise(d["a"], d["b"], threads=THREADS)
     bad = _check_matrix(host(iou), host(nx), ref_iou, ref_nx, "pairwise 2000x2000")
-    if bad[0].size:
-        o = orc.iou_paired(d["a"][bad[0]], d["b"][bad[1]])
-        assert o["degen"].all(), "nx differs on a pair the oracle does not flag"
+    _assert_flagged(orc, d["a"], d["b"], bad[0], bad[1], label="pairwise 2000x2000")
     assert (ref_iou > 0).mean() > 0.001  # the workload has overlaps
 
 
@@ -47,7 +55,8 @@ def test_pairwise_ragged_shapes(dg, orc, N, M):
     d = W.pairwise_bev_2000(seed=N + M, N=N, M=M)
     iou, nx = dg.dgal_iou_pairwise(dev(d["a"]), dev(d["b"]))
     ref_iou, ref_nx = orc.iou_pairwise(d["a"], d["b"])
-    _check_matrix(host(iou), host(nx), ref_iou, ref_nx, f"pairwise {N}x{M}")
+    bad = _check_matrix(host(iou), host(nx), ref_iou, ref_nx, f"pairwise {N}x{M}")
+    _assert_flagged(orc, d["a"], d["b"], bad[0], bad[1], label=f"pairwise {N}x{M}")
 
 
 def test_pairwise_k8_counts(dg, orc):
@@ -55,7 +64,8 @@ def test_pairwise_k8_counts(dg, orc):
     a, b, ca, cb = d["p1"][:300], d["p2"][300:], d["c1"][:300], d["c2"][300:]
     iou, nx = dg.dgal_iou_pairwise(dev(a), dev(b), dev(ca), dev(cb))
     ref_iou, ref_nx = orc.iou_pairwise(a, b, ca, cb)
-    _check_matrix(host(iou), host(nx), ref_iou, ref_nx, "pairwise K=8")
+    bad = _check_matrix(host(iou), host(nx), ref_iou, ref_nx, "pairwise K=8")
+    _assert_flagged(orc, a, b, bad[0], bad[1], ca, cb, label="pairwise K=8")
 
 
 def _batched_inputs(seed=0, S=64):
@@ -84,8 +94,13 @@ def test_batched_ragged_full(dg, orc):
     ref_iou, ref_nx = _oracle_batched(orc, d)
     err = np.abs(host(iou).astype(np.float64) - ref_iou)
     assert err.max() <= IOU_ATOL
-    mism = (host(nx) != ref_nx).mean()
-    assert mism < 1e-4
+    # every nx mismatch is an entry whose pair the oracle flags near-degenerate
+    ent = np.nonzero(host(nx) != ref_nx)[0]
+    scene = np.searchsorted(d["out_off"], ent, side="right") - 1
+    loc = ent - d["out_off"][scene]
+    rows = d["a_off"][scene] + loc // d["M"][scene]
+    cols = d["b_off"][scene] + loc % d["M"][scene]
+    _assert_flagged(orc, d["a"], d["b"], rows, cols, label="ragged batch")
     # the plain per-scene form and the CUDA-graph form give identical bytes
     iou2, nx2 = dg.dgal_iou_pairwise_per_scene(a, b, d["a_off"], d["b_off"], d["out_off"],
                                                flags=dg.DGAL_FP64_REFINE)

@@ -30,6 +30,15 @@ MUTATIONS = [
     ("gs term dropped", "opt gs = {gN * (-q.y) + gD * (-r.y), gN * q.x + gD * r.x};",
      "opt gs = {gN * (-q.y), gN * q.x + gD * r.x};"),
     ("P2 gradient index shifted", "g2[j1].x += gs.x;", "g2[j].x += gs.x;"),
+    # the near-degenerate classifier, which decides where bit-exactness is waived
+    ("orientation threshold x10", "double thr = ORC_DEGEN_REL * L * L;", "double thr = 10.0 * ORC_DEGEN_REL * L * L;"),
+    ("crossing-parameter threshold x10", "if (t <= ORC_DEGEN_REL || t >= 1.0 - ORC_DEGEN_REL) return 1;",
+     "if (t <= 10.0 * ORC_DEGEN_REL || t >= 1.0 - 10.0 * ORC_DEGEN_REL) return 1;"),
+    ("parallel-edge threshold x10", "if (fabs(cross2(r, s)) <= ORC_DEGEN_REL * nr * ns && bbox_overlap",
+     "if (fabs(cross2(r, s)) <= 10.0 * ORC_DEGEN_REL * nr * ns && bbox_overlap"),
+    ("parallel-edge bbox guard dropped", "ORC_DEGEN_REL * nr * ns && bbox_overlap(a, b, c, d)) return 1;",
+     "ORC_DEGEN_REL * nr * ns) return 1;"),
+    ("classifier scale L about the origin", "opt o = P[0];", "opt o = {0.0, 0.0};"),
 ]
 
 

@@ -368,3 +368,119 @@ def test_constructed_degenerate_kinds(orc):
         inter = exact_clip.clip(P, Q)
         ai = float(exact_clip.area(inter)) if len(inter) >= 3 else 0.0
         assert abs(o["areas"][k, 0] - ai) <= 1e-12 * max(1.0, ai)
+
+
+# ------------------------------------------- near-degenerate classifier
+#
+# The classifier decides where bit-exact nx / xflags are waived, so it is
+# pinned on both sides: each family below places one quantity of the
+# definition (with L the largest |coordinate| about P1's vertex 0) at a chosen
+# multiple of its threshold by construction, with every other quantity of the
+# pair far from its own threshold.  At 0.7 of the threshold the pair must be
+# flagged and at 1.4 it must not be; a threshold taken 10 times too large, an
+# L taken about the origin (the 70 m offset) or a criterion missing its
+# guard flags a pair it must not, and a criterion left out misses one.
+
+
+def _orient_family(ratio, off=0.0):
+    """(i): the bottom vertex of a diamond sits 2 delta above the line of the
+    square's top edge (length 2), so its orientation is 2 delta; L = 3.4 +
+    delta.  delta solves 2 delta = ratio * 1e-5 L^2."""
+    delta = 0.0
+    for _ in range(4):
+        delta = ratio * 1e-5 * (3.4 + delta) ** 2 / 2
+    P = np.array([(0, 0), (2, 0), (2, 2), (0, 2)], np.float64) + off
+    Q = np.array([(1, 2 + delta), (1.7, 2.7 + delta), (1, 3.4 + delta), (0.3, 2.7 + delta)], np.float64) + off
+    P, Q = P.astype(np.float32), Q.astype(np.float32)
+    # the construction's quantity from the rounded inputs: the orientation of
+    # Q[0] against the top edge (2,2) -> (0,2) is 2 (y(Q[0]) - y(P[2]))
+    d = 2.0 * (float(Q[0, 1]) - float(P[2, 1]))
+    L = float(np.abs(np.concatenate([P, Q]).astype(np.float64) - P[0].astype(np.float64)).max())
+    return P, Q, d / (1e-5 * L * L)
+
+
+def _crossing_family(ratio):
+    """(ii): an edge of Q (direction (1, 2), 8 long times the sine) crosses the
+    square's bottom edge at x = 2 eps, i.e. at t = eps; the orientation of the
+    square's vertex 0 against that edge is 7.2 eps, above 1e-5 L^2 = 4e-5 for
+    eps >= 0.6e-5.  eps = ratio * 1e-5."""
+    eps = ratio * 1e-5
+    P = np.array([(0, 0), (2, 0), (2, 2), (0, 2)], np.float32)
+    Q = np.array([(2 * eps - 0.9, -1.8), (2 * eps + 0.9, 1.8), (-1.2, 1.9), (-1.9, -0.5)], np.float32)
+    c0, c1 = Q[0].astype(np.float64), Q[1].astype(np.float64)
+    x = c0[0] + (0.0 - c0[1]) / (c1[1] - c0[1]) * (c1[0] - c0[0])  # where Q's edge 0 meets y = 0
+    return P, Q, (x / 2.0) / 1e-5
+
+
+def _parallel_family(ratio, apart=False):
+    """(iii): Q's edge 0 runs from (3, 1.5 + eta) to (1.5, 0), against P's edge
+    0 from (0, 0) to (2, 2): |cross(r, s)| = 2 eta with |r||s| = 6 (about), so
+    eta = ratio * 3e-5.  The two lines are 1.06 apart, so no orientation is
+    small.  apart=True moves Q by (1.5, -1.5): the edges' bounding boxes no
+    longer overlap."""
+    eta = ratio * 3e-5
+    P = np.array([(0, 0), (2, 2), (0.9, 2.6), (-0.6, 1.5)], np.float32)
+    Q = np.array([(3, 1.5 + eta), (1.5, 0), (2.5, -1), (3.5, 0.5)], np.float64)
+    if apart:
+        Q = Q + np.array([1.5, -1.5])
+    Q = Q.astype(np.float32)
+    r = (P[1] - P[0]).astype(np.float64)
+    s = (Q[1] - Q[0]).astype(np.float64)
+    return P, Q, abs(r[0] * s[1] - r[1] * s[0]) / (1e-5 * np.hypot(*r) * np.hypot(*s))
+
+
+def _degen_flag(orc, P, Q):
+    return int(orc.iou_paired(P[None], Q[None])["degen"][0])
+
+
+@pytest.mark.parametrize("off", [0.0, 70.0], ids=["local", "offset70m"])
+def test_degenerate_orientation_threshold(orc, off):
+    lo, hi = _orient_family(0.7, off), _orient_family(1.4, off)
+    assert 0.5 < lo[2] < 0.9 and 1.2 < hi[2] < 1.7, (lo[2], hi[2])
+    assert _degen_flag(orc, lo[0], lo[1]) == 1
+    assert _degen_flag(orc, hi[0], hi[1]) == 0
+
+
+def test_degenerate_crossing_parameter_threshold(orc):
+    lo, hi = _crossing_family(0.7), _crossing_family(1.4)
+    assert 0.6 < lo[2] < 0.8 and 1.3 < hi[2] < 1.5, (lo[2], hi[2])
+    o = orc.iou_paired(np.stack([lo[0], hi[0]]), np.stack([lo[1], hi[1]]))
+    assert list(o["degen"]) == [1, 0]
+    # the crossing is a real one: the intersection has a crossing code on
+    # P's edge 0 with Q's edge 0
+    assert 0x80 in list(o["xflags"][1])
+
+
+def test_degenerate_parallel_threshold(orc):
+    lo, hi = _parallel_family(0.7), _parallel_family(1.4)
+    assert 0.6 < lo[2] < 0.8 and 1.3 < hi[2] < 1.5, (lo[2], hi[2])
+    assert _degen_flag(orc, lo[0], lo[1]) == 1
+    assert _degen_flag(orc, hi[0], hi[1]) == 0
+    # exactly parallel edges whose bounding boxes do not overlap are not a
+    # near-degenerate configuration
+    P, Q, ratio = _parallel_family(0.0, apart=True)
+    assert ratio == 0.0
+    assert _degen_flag(orc, P, Q) == 0
+
+
+def test_degenerate_rate_on_loss_workload(orc):
+    """The IoU-loss pairs are generic: the classifier flags a small fraction
+    (0.13% measured), so the waiver of bit-exactness stays rare."""
+    d = W.loss_pairs_1m(seed=0, n=200_000)
+    o = orc.iou_paired(d["p1"], d["p2"], threads=8)
+    assert o["degen"].mean() < 0.005
+
+
+def test_gradient_magnitude_bound(orc):
+    """|dIoU/dv| <= 3 * 2 sqrt(2) L / U for every vertex (the IoU's derivative
+    through the three areas, each moved by at most the pair's diameter per
+    unit of vertex motion): holds on every pair, near-degenerate ones
+    included, and is the bound the GPU tests apply to pairs the parity bar
+    waives."""
+    from .gpu_helpers import check_flagged_grads
+
+    d = W.convex_pairs_4m(seed=5, n=20_000, degenerate_frac=0.2)
+    ref = orc.iou_paired(d["p1"], d["p2"], d["c1"], d["c2"], threads=8)
+    g1, g2 = orc.iou_backward_paired(d["p1"], d["p2"], np.ones(20_000), ref["nx"], ref["xflags"], d["c1"], d["c2"],
+                                     threads=8)
+    check_flagged_grads(g1, g2, d["p1"], d["p2"], d["c1"], d["c2"], ref, np.ones(20_000, bool), label="oracle")

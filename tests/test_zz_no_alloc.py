@@ -58,6 +58,29 @@ def test_noalloc_matches_workspace_form_twice():
         assert err <= IOU_ATOL, f"call {call}: max |dIoU| {err}"
         assert torch.equal(nx, ref_nx), f"call {call}: nx differs"
 
+    # the largest batch the fixed scratch holds (4096 scenes, most of them
+    # empty), which pins the scratch size arithmetic
+    d = W.ragged_scenes_64(seed=13, S=4096, n_range=(0, 3), m_range=(0, 2))
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    a, b = dev(d["a"]), dev(d["b"])
+    ao, bo, oo = dev(d["a_off"]), dev(d["b_off"]), dev(d["out_off"])
+    total = int(d["out_off"][-1])
+    assert len(d["N"]) == 4096 and total > 0
+    iou = torch.full((total,), -1.0, device="cuda")
+    nx = torch.full((total,), 0xEE, dtype=torch.uint8, device="cuda")
+    ref_iou = torch.empty(total, device="cuda")
+    ref_nx = torch.empty(total, dtype=torch.uint8, device="cuda")
+    ws = torch.empty(lib.dgal_batched_workspace_bytes(4096, 4), dtype=torch.uint8, device="cuda")
+    s = _lib.stream_ptr()
+    assert ref_fn(4096, _lib.ptr(ao), _lib.ptr(bo), _lib.ptr(oo), _lib.ptr(a), None, _lib.ptr(b), None, 4,
+                  _lib.ptr(ref_iou), _lib.ptr(ref_nx), _lib.ptr(ws), ws.numel(), _lib.DGAL_FP64_REFINE, s) == 0
+    st = fn(4096, _lib.ptr(ao), _lib.ptr(bo), _lib.ptr(oo), _lib.ptr(a), None, _lib.ptr(b), None, 4, _lib.ptr(iou),
+            _lib.ptr(nx), _lib.DGAL_FP64_REFINE, s)
+    assert st == 0, lib.dgal_last_error()
+    torch.cuda.synchronize()
+    assert (iou - ref_iou).abs().max().item() <= IOU_ATOL
+    assert torch.equal(nx, ref_nx)
+
     # more scenes than the fixed scratch holds: a clear error, no launch
     big = torch.zeros(4098, dtype=torch.int64, device="cuda")
     st = fn(4097, _lib.ptr(big), _lib.ptr(big), _lib.ptr(big), _lib.ptr(a), None, _lib.ptr(b), None, 4,
