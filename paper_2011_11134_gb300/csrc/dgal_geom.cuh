@@ -107,6 +107,24 @@ template <typename T> __device__ __forceinline__ int popc_(T m) {
     else return __popc(m);
 }
 
+// Three-operand minimum / maximum (one instruction on sm_100 and later).
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// Shifts acc left by one and moves the sign bit of v into bit 0 (one funnel
+// shift), so that sign masks are built without a shift and an OR per bit.
+__device__ __forceinline__ uint32_t push_sign(uint32_t acc, float v) {
+    return __funnelshift_l(__float_as_uint(v), acc, 1);
+}
+
 // Value at dynamic index idx of a register array (select chain, no local memory).
 template <int K> __device__ __forceinline__ float sel(const float (&a)[K], uint32_t idx) {
     float r = a[0];
@@ -141,8 +159,10 @@ __device__ __forceinline__ void make_geo(const float (&px)[K], const float (&py)
     const float ox = px[0], oy = py[0];
 #pragma unroll
     for (int v = 0; v < K; ++v) {
-        g.ax[v] = px[v] - ox;
-        g.ay[v] = py[v] - oy;
+        // P1's vertex 0 is the origin: exactly 0 for finite inputs, and
+        // written as 0 so that the terms it would multiply drop out
+        g.ax[v] = v ? px[v] - ox : 0.f;
+        g.ay[v] = v ? py[v] - oy : 0.f;
         g.bx[v] = qx[v] - ox;
         g.by[v] = qy[v] - oy;
     }
@@ -191,12 +211,20 @@ template <int K, bool COUNTS> __device__ __forceinline__ void input_areas(const 
 
 template <int K, bool COUNTS> __device__ __forceinline__ float pair_scale(const Geo<K>& g) {
     float L = 0.f;
+    if constexpr (!COUNTS) {
 #pragma unroll
-    for (int v = 0; v < K; ++v) {
-        float la = fmaxf(fabsf(g.ax[v]), fabsf(g.ay[v]));
-        float lb = fmaxf(fabsf(g.bx[v]), fabsf(g.by[v]));
-        L = fmaxf(L, (!COUNTS || v < g.n1) ? la : 0.f);
-        L = fmaxf(L, (!COUNTS || v < g.n2) ? lb : 0.f);
+        for (int v = 0; v < K; ++v) {
+            L = fmax3(L, fabsf(g.ax[v]), fabsf(g.ay[v]));
+            L = fmax3(L, fabsf(g.bx[v]), fabsf(g.by[v]));
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < K; ++v) {
+            float la = fmaxf(fabsf(g.ax[v]), fabsf(g.ay[v]));
+            float lb = fmaxf(fabsf(g.bx[v]), fabsf(g.by[v]));
+            L = fmaxf(L, v < g.n1 ? la : 0.f);
+            L = fmaxf(L, v < g.n2 ? lb : 0.f);
+        }
     }
     return L;
 }
@@ -239,6 +267,59 @@ static __device__ __noinline__ uint64_t exact_signs4(const float* __restrict__ r
         neg = (v < 0.0) ? (neg | (1u << b)) : (neg & ~(1u << b));
     }
     return neg;
+}
+
+// The sign repair of fwd_finish (K = 4): the pair's local frame is rebuilt
+// from the raw inputs (so the caller need not keep its geometry live), every
+// orientation within 3x the routing threshold thr is marked (the marks are
+// taken on this recomputation, which may round differently from the caller's
+// values by up to twice the FP32 error bound, so the margin covers every
+// value that was under the threshold), and exact_signs4 takes the FP64
+// definition's sign for each.  neg: the caller's sign bits (S at bit 4i + j,
+// T at bit 16 + 4i + j).  Not inlined: it runs for well under 0.1% of pairs.
+static __device__ __noinline__ uint64_t refine_signs4(const float* __restrict__ raw1, const float* __restrict__ raw2,
+                                                      int n1, int n2, float thr, uint32_t neg) {
+    float px[4], py[4], qx[4], qy[4];
+    const float4* a = reinterpret_cast<const float4*>(raw1);
+    const float4* b = reinterpret_cast<const float4*>(raw2);
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+        const float4 f = __ldg(a + v), h = __ldg(b + v);
+        px[2 * v] = f.x; py[2 * v] = f.y; px[2 * v + 1] = f.z; py[2 * v + 1] = f.w;
+        qx[2 * v] = h.x; qy[2 * v] = h.y; qx[2 * v + 1] = h.z; qy[2 * v + 1] = h.w;
+    }
+    const float ox = px[0], oy = py[0];
+    float ax[4], ay[4], bx[4], by[4], eax[4], eay[4], ebx[4], eby[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        ax[v] = v ? px[v] - ox : 0.f;
+        ay[v] = v ? py[v] - oy : 0.f;
+        bx[v] = qx[v] - ox;
+        by[v] = qy[v] - oy;
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int w1 = (v + 1 < n1) ? v + 1 : 0, w2 = (v + 1 < n2) ? v + 1 : 0;
+        eax[v] = (w1 ? px[w1] - ox : 0.f) - ax[v];
+        eay[v] = (w1 ? py[w1] - oy : 0.f) - ay[v];
+        ebx[v] = (qx[w2] - ox) - bx[v];
+        eby[v] = (qy[w2] - oy) - by[v];
+    }
+    const float wide = 3.f * thr;
+    uint32_t small = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool valid = i < n1 && j < n2;
+            const float dx = ax[i] - bx[j], dy = ay[i] - by[j];
+            const float sv = ebx[j] * dy - eby[j] * dx;
+            const float t = eay[i] * dx - eax[i] * dy;
+            small |= (valid && !(fabsf(sv) > wide)) ? (1u << (i * 4 + j)) : 0u;
+            small |= (valid && !(fabsf(t) > wide)) ? (1u << (16 + i * 4 + j)) : 0u;
+        }
+    }
+    return exact_signs4(raw1, raw2, n1, n2, small, neg);
 }
 
 // 2K code bytes as one integer (byte k = slot k).
@@ -321,6 +402,12 @@ constexpr WalkLut4 make_walk_lut4() {
 }
 static __device__ const WalkLut4 g_walk_lut4 = make_walk_lut4();
 
+template <int K, bool COUNTS>
+__device__ __forceinline__ bool fwd_finish(const Geo<K>& g, float L, typename MaskOf<K>::T neg_s,
+                                           typename MaskOf<K>::T neg_t, float minabs, const float (&Av)[K <= 4 ? K * K : 1],
+                                           const float (&cv)[2][K], FwdOut<K>& o, const float* __restrict__ raw1,
+                                           const float* __restrict__ raw2);
+
 // Returns false when the pair must take the robust path: some orientation is
 // within the near-degenerate threshold (|orient| <= 1e-5 L^2), or the sign
 // pattern is not that of two convex polygons in general position.  While every
@@ -342,17 +429,9 @@ template <int K, bool COUNTS>
 __device__ __forceinline__ bool fwd_generic(const Geo<K>& g, FwdOut<K>& o, const float* __restrict__ raw1 = nullptr,
                                             const float* __restrict__ raw2 = nullptr) {
     typedef typename MaskOf<K>::T M;
-    typedef typename SeqOf<K>::T Sq;
     constexpr int KK = K * K;
-    constexpr int C = 2 * K;
-    constexpr M kRow0 = (M)((1ull << K) - 1);
-    M col0 = 0;
-#pragma unroll
-    for (int i = 0; i < K; ++i) col0 |= (M)1 << (i * K);
     const int n1 = g.n1, n2 = g.n2;
-
     const float L = pair_scale<K, COUNTS>(g);
-    const float thr = kRouteRel * L * L;
 
     // Orientation values: S(i,j) = orient(b_j, b_j+1, a_i), T(i,j) =
     // orient(a_i, a_i+1, b_j).  For K = 4 the loop also forms each pair of
@@ -362,24 +441,68 @@ __device__ __forceinline__ bool fwd_generic(const Geo<K>& g, FwdOut<K>& o, const
     float Av[KEEP ? KK : 1];
     M neg_s = 0, neg_t = 0;
     float minabs = __int_as_float(0x7f800000);
+    if constexpr (K == 4) {
+        // highest (i, j) first, so that push_sign leaves S(i,j)'s sign in
+        // bit i * 4 + j
 #pragma unroll
-    for (int i = 0; i < K; ++i) {
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
+        for (int q = KK - 1; q >= 0; --q) {
+            const int i = q / K, j = q % K;
             const float dx = g.ax[i] - g.bx[j], dy = g.ay[i] - g.by[j];
             const float s = g.ebx[j] * dy - g.eby[j] * dx;
             const float t = g.eay[i] * dx - g.eax[i] * dy;
-            if constexpr (KEEP) {
-                const float D = g.eax[i] * g.eby[j] - g.eay[i] * g.ebx[j];
-                const float c = g.ax[i] * g.by[j] - g.ay[i] * g.bx[j];
-                Av[i * K + j] = fmaf(c, D, s * t) * __fdividef(1.0f, fabsf(D));
-            }
+            const float D = g.eax[i] * g.eby[j] - g.eay[i] * g.ebx[j];
+            const float c = g.ax[i] * g.by[j] - g.ay[i] * g.bx[j];
+            Av[q] = fmaf(c, D, s * t) * __fdividef(1.0f, fabsf(D));
             const bool valid = !COUNTS || (i < n1 && j < n2);
-            minabs = fminf(minabs, valid ? fminf(fabsf(s), fabsf(t)) : __int_as_float(0x7f800000));
-            neg_s |= (M)(__float_as_uint(s) >> 31) << (i * K + j);
-            neg_t |= (M)(__float_as_uint(t) >> 31) << (i * K + j);
+            minabs = valid ? fmin3(minabs, fabsf(s), fabsf(t)) : minabs;
+            neg_s = (M)push_sign((uint32_t)neg_s, s);
+            neg_t = (M)push_sign((uint32_t)neg_t, t);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const float dx = g.ax[i] - g.bx[j], dy = g.ay[i] - g.by[j];
+                const float s = g.ebx[j] * dy - g.eby[j] * dx;
+                const float t = g.eay[i] * dx - g.eax[i] * dy;
+                const bool valid = !COUNTS || (i < n1 && j < n2);
+                minabs = fminf(minabs, valid ? fminf(fabsf(s), fabsf(t)) : __int_as_float(0x7f800000));
+                neg_s |= (M)(__float_as_uint(s) >> 31) << (i * K + j);
+                neg_t |= (M)(__float_as_uint(t) >> 31) << (i * K + j);
+            }
         }
     }
+    float cv[2][K]; // cross(a_v, ea_v), cross(b_v, eb_v): the vertex terms of the area
+#pragma unroll
+    for (int v = 0; v < K; ++v) {
+        cv[0][v] = g.ax[v] * g.eay[v] - g.ay[v] * g.eax[v];
+        cv[1][v] = g.bx[v] * g.eby[v] - g.by[v] * g.ebx[v];
+    }
+    return fwd_finish<K, COUNTS>(g, L, neg_s, neg_t, minabs, Av, cv, o, raw1, raw2);
+}
+
+// The part of fwd_generic after the orientation values: the sign repair (with
+// raw1, raw2), the masks, the inside tests, the area and the vertex order.
+// L: the pair's scale; neg_s, neg_t: sign bits of S(i,j), T(i,j) at bit
+// i K + j; minabs: the smallest |S|, |T| of the valid entries; Av: the
+// crossing terms of the area (K = 4; unused for K = 8); cv: the vertex terms.
+template <int K, bool COUNTS>
+__device__ __forceinline__ bool fwd_finish(const Geo<K>& g, float L, typename MaskOf<K>::T neg_s,
+                                           typename MaskOf<K>::T neg_t, float minabs, const float (&Av)[K <= 4 ? K * K : 1],
+                                           const float (&cv)[2][K], FwdOut<K>& o, const float* __restrict__ raw1,
+                                           const float* __restrict__ raw2) {
+    typedef typename MaskOf<K>::T M;
+    typedef typename SeqOf<K>::T Sq;
+    constexpr int KK = K * K;
+    constexpr int C = 2 * K;
+    constexpr M kRow0 = (M)((1ull << K) - 1);
+    constexpr bool KEEP = (K <= 4);
+    M col0 = 0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) col0 |= (M)1 << (i * K);
+    const int n1 = g.n1, n2 = g.n2;
+    const float thr = kRouteRel * L * L;
     if (!(L > 0.f)) return false;
     uint32_t refined = 0u;
     if (!(minabs > thr)) {
@@ -387,26 +510,7 @@ __device__ __forceinline__ bool fwd_generic(const Geo<K>& g, FwdOut<K>& o, const
             return false;
         } else {
             if (raw1 == nullptr) return false;
-            // Mark every orientation within 3x the threshold (the marks are
-            // taken on a recomputation, which may round differently from the
-            // values above by up to twice the FP32 error bound, so the margin
-            // covers every value that was under the threshold) and take the
-            // FP64 definition's sign for each.
-            const float wide = 3.f * thr;
-            uint32_t small = 0;
-#pragma unroll
-            for (int i = 0; i < K; ++i) {
-#pragma unroll
-                for (int j = 0; j < K; ++j) {
-                    const bool valid = !COUNTS || (i < n1 && j < n2);
-                    const float dx = g.ax[i] - g.bx[j], dy = g.ay[i] - g.by[j];
-                    const float sv = g.ebx[j] * dy - g.eby[j] * dx;
-                    const float t = g.eay[i] * dx - g.eax[i] * dy;
-                    small |= (valid && !(fabsf(sv) > wide)) ? (1u << (i * K + j)) : 0u;
-                    small |= (valid && !(fabsf(t) > wide)) ? (1u << (16 + i * K + j)) : 0u;
-                }
-            }
-            const uint64_t r = exact_signs4(raw1, raw2, n1, n2, small, (uint32_t)neg_s | ((uint32_t)neg_t << 16));
+            const uint64_t r = refine_signs4(raw1, raw2, n1, n2, thr, (uint32_t)neg_s | ((uint32_t)neg_t << 16));
             if (r >> 32) return false;
             neg_s = (M)(r & 0xFFFFu);
             neg_t = (M)((r >> 16) & 0xFFFFu);
@@ -442,7 +546,15 @@ __device__ __forceinline__ bool fwd_generic(const Geo<K>& g, FwdOut<K>& o, const
 
     // inside tests
     uint32_t in1 = 0, in2 = 0;
-    {
+    if constexpr (K == 4 && !COUNTS) {
+        // in1 bit i: row i of sp all set; in2 bit j: column j of tp all set
+        uint32_t r = (uint32_t)sp & ((uint32_t)sp >> 1);
+        r &= r >> 2;                                        // bit 4i: row i full
+        in1 = (((r & 0x1111u) * 0x1248u) >> 12) & 15u;      // bits 0, 4, 8, 12 -> 0..3
+        uint32_t c = (uint32_t)tp & ((uint32_t)tp >> 8);
+        c &= c >> 4;                                        // bit j: column j full
+        in2 = c & 15u;
+    } else {
         const M colsFull = COUNTS ? (M)((1ull << n2) - 1) : kRow0;
         M rowsCol = 0;
 #pragma unroll
@@ -492,10 +604,8 @@ __device__ __forceinline__ bool fwd_generic(const Geo<K>& g, FwdOut<K>& o, const
         }
 #pragma unroll
         for (int v = 0; v < K; ++v) {
-            const float c1 = g.ax[v] * g.eay[v] - g.ay[v] * g.eax[v];
-            const float c2 = g.bx[v] * g.eby[v] - g.by[v] * g.ebx[v];
-            twoA += ((nxt1 >> v) & 1u) ? c1 : 0.f;
-            twoA += ((nxt2 >> v) & 1u) ? c2 : 0.f;
+            twoA += ((nxt1 >> v) & 1u) ? cv[0][v] : 0.f;
+            twoA += ((nxt2 >> v) & 1u) ? cv[1][v] : 0.f;
         }
     }
 #pragma unroll

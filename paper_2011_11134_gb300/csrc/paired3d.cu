@@ -7,7 +7,7 @@
 // Backward (paper Sec. II-B `iou_backward`): reads the polygons, dL/dIoU and
 // the recorded (nx, xflags), or recomputes the clip, and writes both
 // gradients with 128-bit stores.
-#include "paired_kernels.cuh"
+#include "paired_launch.cuh"
 
 namespace dgal {
 
