@@ -14,6 +14,8 @@ polygons also carry uint8 vertex counts.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 
@@ -144,7 +146,17 @@ def loss3d_pairs_1m(seed: int = 0, n: int = 1_000_000):
 
 def _strictly_convex_ccw(poly: np.ndarray, cnt: np.ndarray) -> np.ndarray:
     """True where every consecutive vertex triple (in float64 on the stored
-    float32 values) turns strictly left, i.e. a valid convex CCW input."""
+    float32 values) turns strictly left, i.e. a valid convex CCW input (row
+    chunks on a thread pool for large inputs)."""
+    n = poly.shape[0]
+    chunk = 1 << 16
+    if n > chunk:
+        from concurrent.futures import ThreadPoolExecutor
+
+        spans = [(s, min(n, s + chunk)) for s in range(0, n, chunk)]
+        with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+            return np.concatenate(list(ex.map(lambda se: _strictly_convex_ccw(poly[se[0]:se[1]], cnt[se[0]:se[1]]),
+                                              spans)))
     n, K, _ = poly.shape
     p = poly.astype(np.float64)
     ok = np.ones(n, bool)
@@ -162,15 +174,10 @@ def _strictly_convex_ccw(poly: np.ndarray, cnt: np.ndarray) -> np.ndarray:
     return ok
 
 
-def _hulls(r: np.random.Generator, centers: np.ndarray, K: int):
-    """Convex hull of 3..K points uniform in a disc (radius ~ U[0.5,3]) around
-    each center; returns float32 [n, K, 2] padded with vertex 0 and counts."""
-    n = centers.shape[0]
-    m = r.integers(3, K + 1, size=n)
-    rad = r.uniform(0.5, 3.0, size=n)
-    ang = r.uniform(-np.pi, np.pi, size=(n, K))
-    rr = rad[:, None] * np.sqrt(r.uniform(0.0, 1.0, size=(n, K)))
-    pts = np.stack([rr * np.cos(ang), rr * np.sin(ang)], axis=-1)  # relative to center
+def _hull_points(pts: np.ndarray, m: np.ndarray, centers: np.ndarray, K: int):
+    """Convex hull (counter-clockwise, padded with vertex 0) of the first m
+    points of each row of pts (relative to the row's center)."""
+    n = pts.shape[0]
     valid = np.arange(K)[None, :] < m[:, None]
     # sort valid points by angle about their mean (an interior point)
     mean = (pts * valid[..., None]).sum(1) / m[:, None]
@@ -184,17 +191,18 @@ def _hulls(r: np.random.Generator, centers: np.ndarray, K: int):
     # the triangle mean-prev-next, hence inside the hull, so dropping all of
     # them in one sweep is safe)
     cols = np.arange(K)[None, :]
-    rows = np.arange(n)[:, None]
+    X, Y = np.ascontiguousarray(pts[..., 0]), np.ascontiguousarray(pts[..., 1])
     for _ in range(K):
-        nxt = np.full((n, K), -1)
-        prv = np.full((n, K), -1)
-        for off in range(K - 1, 0, -1):
-            nxt = np.where(np.roll(alive, -off, axis=1), (cols + off) % K, nxt)
-            prv = np.where(np.roll(alive, off, axis=1), (cols - off) % K, prv)
-        P = pts
-        Pp = P[rows, np.maximum(prv, 0)]
-        Pn = P[rows, np.maximum(nxt, 0)]
-        t = (P[..., 0] - Pp[..., 0]) * (Pn[..., 1] - P[..., 1]) - (P[..., 1] - Pp[..., 1]) * (Pn[..., 0] - P[..., 0])
+        # cyclic previous / next alive point of every position
+        pm = np.maximum.accumulate(np.where(alive, cols, -1), axis=1)  # last alive at or before i
+        prv = np.concatenate([np.full((n, 1), -1), pm[:, :-1]], 1)
+        prv = np.where(prv < 0, pm[:, -1:], prv)
+        nm = np.minimum.accumulate(np.where(alive, cols, K)[:, ::-1], axis=1)[:, ::-1]  # first alive at or after i
+        nxt = np.concatenate([nm[:, 1:], np.full((n, 1), K)], 1)
+        nxt = np.where(nxt >= K, nm[:, :1], nxt)
+        Xp, Yp = np.take_along_axis(X, prv, 1), np.take_along_axis(Y, prv, 1)
+        Xn, Yn = np.take_along_axis(X, nxt, 1), np.take_along_axis(Y, nxt, 1)
+        t = (X - Xp) * (Yn - Y) - (Y - Yp) * (Xn - X)
         drop = alive & (t <= 0)
         if not drop.any():
             break
@@ -207,6 +215,29 @@ def _hulls(r: np.random.Generator, centers: np.ndarray, K: int):
     pad = np.arange(K)[None, :, None] >= cnt[:, None, None]
     pts = np.where(pad, first, pts)
     return pts.astype(np.float32), cnt.astype(np.uint8)
+
+
+def _hulls(r: np.random.Generator, centers: np.ndarray, K: int):
+    """Convex hull of 3..K points uniform in a disc (radius ~ U[0.5,3]) around
+    each center; returns float32 [n, K, 2] padded with vertex 0 and counts.
+    The random draws come first, in one sequence; the hulls are then built in
+    row chunks on a thread pool (the result does not depend on the chunks)."""
+    n = centers.shape[0]
+    m = r.integers(3, K + 1, size=n)
+    rad = r.uniform(0.5, 3.0, size=n)
+    ang = r.uniform(-np.pi, np.pi, size=(n, K))
+    rr = rad[:, None] * np.sqrt(r.uniform(0.0, 1.0, size=(n, K)))
+    pts = np.stack([rr * np.cos(ang), rr * np.sin(ang)], axis=-1)  # relative to center
+    chunk = 1 << 16
+    if n <= chunk:
+        return _hull_points(pts, m, centers, K)
+    from concurrent.futures import ThreadPoolExecutor
+
+    spans = [(s, min(n, s + chunk)) for s in range(0, n, chunk)]
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        parts = list(ex.map(lambda se: _hull_points(pts[se[0]:se[1]], m[se[0]:se[1]], centers[se[0]:se[1]], K),
+                            spans))
+    return np.concatenate([p for p, _ in parts]), np.concatenate([c for _, c in parts])
 
 
 def convex_pairs_4m(seed: int = 0, n: int = 4_000_000, K: int = 8, degenerate_frac: float = 0.05):
@@ -249,38 +280,36 @@ def convex_pairs_4m(seed: int = 0, n: int = 4_000_000, K: int = 8, degenerate_fr
         sel_v = r.integers(0, 1 << 30, size=nd)
         shift = r.uniform(-0.25, 0.25, size=nd)
         sign = np.where(r.uniform(size=nd) < 0.5, -1.0, 1.0)
-        for t in range(nd):
-            k = idx[t]
-            m = int(c1[k])
-            P = p1[k, :m].astype(np.float64)
-            e = int(sel_v[t] % m)
-            if kinds[t] == 1:
-                q = p1[k].copy()
-            elif kinds[t] == 2:
-                a, b = P[e], P[(e + 1) % m]
-                d = (b - a) / np.linalg.norm(b - a)
-                rel = P - a
-                refl = a + 2 * (rel @ d)[:, None] * d[None, :] - rel
-                Q = refl.astype(np.float32)
-                Q[e] = p1[k, e]
-                Q[(e + 1) % m] = p1[k, (e + 1) % m]
-                Q = Q[::-1]
-                q = np.repeat(Q[:1], K, axis=0)
-                q[:m] = Q
-            elif kinds[t] == 3:
-                v = P[e]
-                Q = (2 * v - P).astype(np.float32)
-                Q[e] = p1[k, e]
-                q = np.repeat(Q[:1], K, axis=0)
-                q[:m] = Q
-            else:
-                a, b = P[e], P[(e + 1) % m]
-                L = np.linalg.norm(b - a)
-                d = (b - a) / L
-                nrm = np.array([-d[1], d[0]])
-                Q = (P + shift[t] * L * d + sign[t] * 1e-6 * nrm).astype(np.float32)
-                q = np.repeat(Q[:1], K, axis=0)
-                q[:m] = Q
-            p2[k] = q
-            c2[k] = c1[k]
+        m = c1[idx].astype(np.int64)
+        e = sel_v % m
+        e1 = (e + 1) % m
+        rows = np.arange(nd)
+        P = p1[idx].astype(np.float64)  # [nd, K, 2]; slots >= m repeat vertex 0
+        live = np.arange(K)[None, :] < m[:, None]
+        a, b = P[rows, e], P[rows, e1]
+        q = np.empty((nd, K, 2), np.float32)
+        # 1 identical
+        q1 = p1[idx]
+        # 2 reflection across edge e, its endpoints copied exactly, order reversed
+        d = (b - a) / np.linalg.norm(b - a, axis=1, keepdims=True)
+        rel = P - a[:, None, :]
+        proj = rel[..., 0] * d[:, None, 0] + rel[..., 1] * d[:, None, 1]
+        Q2 = (a[:, None, :] + 2 * proj[..., None] * d[:, None, :] - rel).astype(np.float32)
+        Q2[rows, e] = p1[idx][rows, e]
+        Q2[rows, e1] = p1[idx][rows, e1]
+        rev = np.where(live, m[:, None] - 1 - np.arange(K)[None, :], 0)  # reversed order of the m live slots
+        Q2 = np.take_along_axis(Q2, rev[..., None], axis=1)
+        # 3 point reflection through vertex e, which is kept exactly
+        Q3 = (2 * a[:, None, :] - P).astype(np.float32)
+        Q3[rows, e] = p1[idx][rows, e]
+        # 4 shifted along edge e by U[-1/4, 1/4] of its length and 1e-6 along its normal
+        Le = np.linalg.norm(b - a, axis=1)
+        nrm = np.stack([-d[:, 1], d[:, 0]], 1)
+        Q4 = (P + (shift * Le)[:, None, None] * d[:, None, :] + (sign * 1e-6)[:, None, None] * nrm[:, None, :]).astype(
+            np.float32)
+        kk = kinds[:, None, None]
+        q = np.where(kk == 1, q1, np.where(kk == 2, Q2, np.where(kk == 3, Q3, Q4)))
+        q = np.where(live[..., None], q, q[:, :1, :])  # pad with vertex 0
+        p2[idx] = q
+        c2[idx] = c1[idx]
     return dict(p1=p1, c1=c1, p2=p2, c2=c2, kind=kind)
