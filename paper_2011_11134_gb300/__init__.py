@@ -26,6 +26,7 @@ marshals arguments.  ``workloads`` (seeded inputs) imports without CUDA.
 from __future__ import annotations
 
 import ctypes
+import os
 
 import torch
 
@@ -553,16 +554,45 @@ def dgal_version():
     return int(_lib.lib().dgal_version())
 
 
+# Memory budget of the saved flags of ``IoU`` (bytes): above it the forward
+# keeps no flags and the backward re-runs the clip.  The flags take 1 + 2K
+# bytes per pair (9 for quadrilaterals: 90 MB for 10^7 pairs, 170 MB for
+# K = 8).  Overridden by the environment variable DGAL_FLAG_BUDGET_BYTES or
+# by IoU's ``flag_budget`` argument.
+DEFAULT_FLAG_BUDGET_BYTES = 64 << 20
+
+
+def flag_budget_bytes(budget=None):
+    """The flag budget in bytes: ``budget`` if given, else
+    DGAL_FLAG_BUDGET_BYTES from the environment, else the default (64 MiB)."""
+    if budget is not None:
+        return int(budget)
+    env = os.environ.get("DGAL_FLAG_BUDGET_BYTES")
+    return int(env) if env else DEFAULT_FLAG_BUDGET_BYTES
+
+
+def choose_recompute(n, K, recompute=None, budget=None):
+    """Recompute mode for n pairs of capacity K: ``recompute`` when given,
+    else True exactly when the saved flags (n (1 + 2K) bytes) would exceed the
+    flag budget."""
+    if recompute is not None:
+        return bool(recompute)
+    return n * (1 + 2 * K) > flag_budget_bytes(budget)
+
+
 class IoU(torch.autograd.Function):
     """IoU of paired convex polygons with the library's hand-written backward.
 
-    Saved-flag mode records (nx, xflags) in the forward (K + 1... 2K + 1 bytes
-    per pair) and the backward reads them; recompute mode stores nothing and
-    the backward re-runs the clip."""
+    Saved-flag mode records (nx, xflags) in the forward (1 + 2K bytes per
+    pair) and the backward reads them; recompute mode stores nothing and the
+    backward re-runs the clip.  ``recompute=None`` picks recompute mode when
+    the flags would exceed the flag budget (``choose_recompute``)."""
 
     @staticmethod
-    def forward(ctx, p1, p2, c1=None, c2=None, recompute=False, flags=DGAL_FP64_REFINE):
+    def forward(ctx, p1, p2, c1=None, c2=None, recompute=None, flags=DGAL_FP64_REFINE, flag_budget=None):
         p1c, p2c = p1.contiguous(), p2.contiguous()
+        recompute = choose_recompute(p1c.shape[0], p1c.shape[1], recompute, flag_budget)
+        ctx.recompute = recompute
         iou_v, nx, xflags, _ = dgal_iou_paired(p1c, p2c, c1, c2, save_flags=not recompute, flags=flags)
         ctx.save_for_backward(p1c, p2c, nx, xflags, c1, c2)
         ctx.flags = flags
@@ -572,12 +602,12 @@ class IoU(torch.autograd.Function):
     def backward(ctx, grad):
         p1, p2, nx, xflags, c1, c2 = ctx.saved_tensors
         g1, g2 = dgal_iou_backward(p1, p2, grad.contiguous().float(), nx, xflags, c1, c2, flags=ctx.flags)
-        return g1, g2, None, None, None, None
+        return g1, g2, None, None, None, None, None
 
 
-def iou(p1, p2, c1=None, c2=None, recompute=False, flags=DGAL_FP64_REFINE):
+def iou(p1, p2, c1=None, c2=None, recompute=None, flags=DGAL_FP64_REFINE, flag_budget=None):
     """Differentiable paired IoU (see ``IoU``)."""
-    return IoU.apply(p1, p2, c1, c2, recompute, flags)
+    return IoU.apply(p1, p2, c1, c2, recompute, flags, flag_budget)
 
 
 class IoULoss(torch.autograd.Function):

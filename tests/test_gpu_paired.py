@@ -309,3 +309,27 @@ def test_k4_with_counts(dg, orc):
     rm, rnx = orc.iou_pairwise(p1[:400], p2[:300], c1[:400], c2[:300], threads=THREADS)
     assert np.abs(host(m).astype(np.float64) - rm).max() <= IOU_ATOL
     assert dg.dgal_get_device_status() == 0
+
+
+def test_recompute_chosen_by_flag_budget(dg, monkeypatch):
+    """Above the flag budget IoU keeps no flags and its backward re-runs the
+    clip; the gradients equal those of the saved-flag mode."""
+    import torch
+
+    n = 1000
+    d = W.paired_rect_4096(seed=3, n=n)
+    w = torch.rand(n, device="cuda")
+    grads = []
+    for budget, want in ((n * 9 - 1, True), (n * 9, False)):
+        p1 = dev(d["p1"]).requires_grad_(True)
+        p2 = dev(d["p2"]).requires_grad_(True)
+        y = dg.iou(p1, p2, flag_budget=budget)
+        assert y.grad_fn.recompute is want
+        (y * w).sum().backward()
+        grads.append((p1.grad, p2.grad))
+    (a1, a2), (b1, b2) = grads
+    scale = max(b1.abs().max().item(), b2.abs().max().item())
+    assert (a1 - b1).abs().max().item() <= 1e-5 * scale and (a2 - b2).abs().max().item() <= 1e-5 * scale
+    # the environment variable sets the default budget
+    monkeypatch.setenv("DGAL_FLAG_BUDGET_BYTES", "1")
+    assert dg.iou(dev(d["p1"]).requires_grad_(True), dev(d["p2"])).grad_fn.recompute is True
