@@ -70,6 +70,12 @@ def _load():
             lib.oracle_iou_backward_pair_f64.argtypes = [ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int,
                                                          ctypes.c_double, ctypes.c_int, P, P, P]
             lib.oracle_iou_backward_pair_f64.restype = ctypes.c_int
+            lib.oracle_loss_variant_paired.argtypes = [ctypes.c_int64, ctypes.c_int, P, P, P, P, ctypes.c_int, P, P,
+                                                       P, P, P]
+            lib.oracle_loss_variant_paired.restype = ctypes.c_int
+            lib.oracle_loss_variant_pair_f64.argtypes = [ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int,
+                                                         ctypes.c_int, ctypes.c_double, P, P, P]
+            lib.oracle_loss_variant_pair_f64.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -410,3 +416,49 @@ def nms_rotated(boxes, scores, threshold, counts=None, threads: int = 1):
         keep.append(order[a])
         removed[a + 1:] |= iou[a, a + 1:] > threshold
     return np.array(keep, dtype=np.int64)
+
+
+GIOU = 1
+DIOU = 2
+
+
+def loss_variant_paired(p1, p2, variant, weight=None, c1=None, c2=None, threads: int = 1):
+    """Per-pair loss terms of the GIoU (variant 1) or DIoU (variant 2) loss and
+    their gradients (dgal_oracle.c, "GIoU / DIoU terms of the loss").
+
+    Returns dict(lk=float64[n] = w (1 - GIoU) or w (1 - DIoU),
+    terms=float64[n, 4] = (IoU, hull area, rho2, c2), g1, g2 = float64[n, K, 2]
+    = d lk / d p1, d p2, status=int)."""
+    lib = _load()
+    p1, p2, c1, c2 = _f32(p1), _f32(p2), _u8(c1), _u8(c2)
+    n, K = p1.shape[0], p1.shape[1]
+    w = None if weight is None else np.ascontiguousarray(weight, dtype=np.float64)
+    out = dict(lk=np.zeros(n), terms=np.zeros((n, 4)), g1=np.zeros((n, K, 2)), g2=np.zeros((n, K, 2)))
+    status = [0]
+
+    def run(rng):
+        s, e = rng
+        st = lib.oracle_loss_variant_paired(
+            e - s, K, _ptr(p1[s:e]), _ptr(None if c1 is None else c1[s:e]), _ptr(p2[s:e]),
+            _ptr(None if c2 is None else c2[s:e]), int(variant), _ptr(None if w is None else w[s:e]),
+            _ptr(out["lk"][s:e]), _ptr(out["terms"][s:e]), _ptr(out["g1"][s:e]), _ptr(out["g2"][s:e]))
+        status[0] |= st
+
+    _run_parallel(run, _chunks(n, threads))
+    out["status"] = status[0]
+    return out
+
+
+def loss_variant_pair_f64(p1, p2, variant, w=1.0, K=None):
+    """Single pair in double: returns (lk, g1 [n1, 2], g2 [n2, 2])."""
+    lib = _load()
+    p1 = np.ascontiguousarray(p1, dtype=np.float64)
+    p2 = np.ascontiguousarray(p2, dtype=np.float64)
+    n1, n2 = p1.shape[0], p2.shape[0]
+    K = K or max(n1, n2)
+    lk = ctypes.c_double(0.0)
+    g1 = np.zeros((K, 2), np.float64)
+    g2 = np.zeros((K, 2), np.float64)
+    lib.oracle_loss_variant_pair_f64(K, _ptr(p1), n1, _ptr(p2), n2, int(variant), float(w), ctypes.byref(lk),
+                                     _ptr(g1), _ptr(g2))
+    return lk.value, g1[:n1], g2[:n2]

@@ -566,3 +566,200 @@ int oracle_iou_backward_pair_f64(int K, const double* p1, int n1, const double* 
     }
     return st;
 }
+
+
+/* ------------------------------------------- GIoU / DIoU terms of the loss
+ *
+ * The IoU-loss case study (paper Sec. IV-A) trains rotated boxes with
+ * 1 - IoU.  Its generalized and distance-penalised variants (the paper names
+ * the IoU loss only; these are the standard extensions) add, per pair:
+ *   GIoU = IoU - (A_h - U) / A_h,  A_h = area of the convex hull of both
+ *          polygons' vertices, U = A_1 + A_2 - A_i;
+ *   DIoU = IoU - rho2 / c2,  rho2 = squared distance between the two
+ *          polygons' vertex means, c2 = squared diameter of that hull (the
+ *          largest squared distance between any two of the vertices).
+ * The loss term of a pair is w (1 - GIoU) or w (1 - DIoU).  The hull is
+ * Andrew's monotone chain over the n1 + n2 points in double (points sorted by
+ * x, then y; collinear points dropped); its gradient is the shoelace adjoint
+ * over the hull's vertices, each routed to the input vertex it came from.
+ * The diameter takes the first largest pair in index order (P1's vertices,
+ * then P2's), and its gradient goes to that pair. */
+
+typedef struct {
+    opt p;
+    int src; /* 0..n1-1: P1 vertex, n1..: P2 vertex */
+} hpt;
+
+/* Convex hull (counter-clockwise, no collinear points) of m points; returns
+ * the number of hull vertices written to hull[]. */
+static int monotone_chain(hpt* pts, int m, hpt* hull)
+{
+    for (int k = 1; k < m; ++k) {
+        hpt v = pts[k];
+        int l = k - 1;
+        while (l >= 0 && (pts[l].p.x > v.p.x || (pts[l].p.x == v.p.x && pts[l].p.y > v.p.y))) {
+            pts[l + 1] = pts[l];
+            --l;
+        }
+        pts[l + 1] = v;
+    }
+    int h = 0;
+    for (int k = 0; k < m; ++k) { /* lower chain */
+        while (h >= 2 && orient(hull[h - 2].p, hull[h - 1].p, pts[k].p) <= 0.0) --h;
+        hull[h++] = pts[k];
+    }
+    for (int k = m - 2, lo = h + 1; k >= 0; --k) { /* upper chain */
+        while (h >= lo && orient(hull[h - 2].p, hull[h - 1].p, pts[k].p) <= 0.0) --h;
+        hull[h++] = pts[k];
+    }
+    return h > 1 ? h - 1 : h; /* the last point repeats the first */
+}
+
+typedef struct {
+    double ah, rho2, c2;
+    int h;
+    hpt hull[4 * ORC_MAXK + 1]; /* the chains hold up to 2 m points while they are built */
+    int da, db; /* the diameter's pair (indices into P1 ++ P2) */
+} ohull;
+
+static void hull_terms(const opt* P, int n1, const opt* Q, int n2, ohull* o)
+{
+    hpt pts[2 * ORC_MAXK];
+    int m = 0;
+    for (int i = 0; i < n1; ++i) { pts[m].p = P[i]; pts[m].src = i; ++m; }
+    for (int j = 0; j < n2; ++j) { pts[m].p = Q[j]; pts[m].src = n1 + j; ++m; }
+    o->h = monotone_chain(pts, m, o->hull);
+    opt hv[4 * ORC_MAXK];
+    for (int k = 0; k < o->h; ++k) hv[k] = o->hull[k].p;
+    o->ah = o->h >= 3 ? shoelace(hv, o->h) : 0.0;
+    opt m1 = {0.0, 0.0}, m2 = {0.0, 0.0};
+    for (int i = 0; i < n1; ++i) { m1.x += P[i].x; m1.y += P[i].y; }
+    for (int j = 0; j < n2; ++j) { m2.x += Q[j].x; m2.y += Q[j].y; }
+    m1.x /= n1; m1.y /= n1; m2.x /= n2; m2.y /= n2;
+    o->rho2 = (m1.x - m2.x) * (m1.x - m2.x) + (m1.y - m2.y) * (m1.y - m2.y);
+    opt all[2 * ORC_MAXK];
+    for (int i = 0; i < n1; ++i) all[i] = P[i];
+    for (int j = 0; j < n2; ++j) all[n1 + j] = Q[j];
+    o->c2 = -1.0;
+    o->da = o->db = 0;
+    for (int a = 0; a < n1 + n2; ++a)
+        for (int b = a + 1; b < n1 + n2; ++b) {
+            double d = (all[a].x - all[b].x) * (all[a].x - all[b].x) + (all[a].y - all[b].y) * (all[a].y - all[b].y);
+            if (d > o->c2) { o->c2 = d; o->da = a; o->db = b; }
+        }
+}
+
+static void add_to(opt* g1, opt* g2, int n1, int src, double gx, double gy)
+{
+    if (src < n1) { g1[src].x += gx; g1[src].y += gy; }
+    else { g2[src - n1].x += gx; g2[src - n1].y += gy; }
+}
+
+/* Loss term and its gradient on one pair (variant 1: GIoU, 2: DIoU):
+ * *lk = w (1 - GIoU) or w (1 - DIoU); g1, g2 = d lk / d P, d Q.
+ * Zero (and *lk = w) for U <= 0 or a degenerate hull / diameter. */
+static int loss_variant_pair(const opt* P, int n1, const opt* Q, int n2, int K, int variant, double w, double* lk,
+                             double* terms, opt* g1, opt* g2)
+{
+    ofwd f;
+    forward_pair(P, n1, Q, n2, K, &f);
+    ohull hq;
+    hull_terms(P, n1, Q, n2, &hq);
+    double U = f.a1 + f.a2 - f.ai;
+    double iou = f.iou;
+    terms[0] = iou;
+    terms[1] = hq.ah;
+    terms[2] = hq.rho2;
+    terms[3] = hq.c2;
+    for (int i = 0; i < ORC_MAXK; ++i) { g1[i].x = g1[i].y = 0.0; g2[i].x = g2[i].y = 0.0; }
+    if (!(U > 0.0)) { *lk = w; return f.status; }
+    int nx = f.nx >= 3 ? f.nx : 0;
+    /* d IoU / d(A_i, A_1, A_2) (zero without an intersection polygon) */
+    double di = nx ? (f.a1 + f.a2) / (U * U) : 0.0, d12 = nx ? -f.ai / (U * U) : 0.0;
+    double gai, ga1, ga2;
+    if (variant == 1) {
+        if (!(hq.ah > 0.0)) { *lk = w * (1.0 - iou); return f.status; }
+        *lk = w * (1.0 - iou + (hq.ah - U) / hq.ah);
+        /* lk = w (2 - IoU - U / A_h) */
+        gai = w * (-di + 1.0 / hq.ah);
+        ga1 = ga2 = w * (-d12 - 1.0 / hq.ah);
+    } else {
+        if (!(hq.c2 > 0.0)) { *lk = w * (1.0 - iou); return f.status; }
+        *lk = w * (1.0 - iou + hq.rho2 / hq.c2);
+        gai = -w * di;
+        ga1 = ga2 = -w * d12;
+    }
+    int st = area_backward_pair(P, n1, Q, n2, gai, ga1, ga2, nx, f.code, g1, g2);
+    if (variant == 1) {
+        /* hull area: shoelace adjoint over the hull's vertices */
+        double gh = w * U / (hq.ah * hq.ah);
+        for (int k = 0; k < hq.h; ++k) {
+            opt hp = hq.hull[(k + hq.h - 1) % hq.h].p, hn = hq.hull[(k + 1) % hq.h].p;
+            add_to(g1, g2, n1, hq.hull[k].src, 0.5 * gh * (hn.y - hp.y), 0.5 * gh * (hp.x - hn.x));
+        }
+    } else {
+        /* rho2 / c2 */
+        opt m1 = {0.0, 0.0}, m2 = {0.0, 0.0};
+        for (int i = 0; i < n1; ++i) { m1.x += P[i].x; m1.y += P[i].y; }
+        for (int j = 0; j < n2; ++j) { m2.x += Q[j].x; m2.y += Q[j].y; }
+        m1.x /= n1; m1.y /= n1; m2.x /= n2; m2.y /= n2;
+        double gr = w / hq.c2, gc = -w * hq.rho2 / (hq.c2 * hq.c2);
+        for (int i = 0; i < n1; ++i) { g1[i].x += gr * 2.0 * (m1.x - m2.x) / n1; g1[i].y += gr * 2.0 * (m1.y - m2.y) / n1; }
+        for (int j = 0; j < n2; ++j) { g2[j].x -= gr * 2.0 * (m1.x - m2.x) / n2; g2[j].y -= gr * 2.0 * (m1.y - m2.y) / n2; }
+        opt pa = hq.da < n1 ? P[hq.da] : Q[hq.da - n1], pb = hq.db < n1 ? P[hq.db] : Q[hq.db - n1];
+        add_to(g1, g2, n1, hq.da, gc * 2.0 * (pa.x - pb.x), gc * 2.0 * (pa.y - pb.y));
+        add_to(g1, g2, n1, hq.db, -gc * 2.0 * (pa.x - pb.x), -gc * 2.0 * (pa.y - pb.y));
+    }
+    return f.status | st;
+}
+
+/* Batch loss terms of the GIoU (variant 1) or DIoU (variant 2) loss:
+ * lk [n] = w_k (1 - GIoU_k) or w_k (1 - DIoU_k) (w = NULL: 1); terms [n][4] =
+ * (IoU, A_h, rho2, c2) or NULL; g1, g2 [n][K][2] = d lk / d p1, d p2 (or
+ * NULL).  Returns OR of status bits. */
+int oracle_loss_variant_paired(int64_t n, int K, const float* p1, const uint8_t* c1, const float* p2,
+                               const uint8_t* c2, int variant, const double* w, double* lk, double* terms, double* g1,
+                               double* g2)
+{
+    if (K < 3 || K > ORC_MAXK || (variant != 1 && variant != 2)) return -1;
+    int st = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        opt P[ORC_MAXK], Q[ORC_MAXK], G1[ORC_MAXK], G2[ORC_MAXK];
+        double tm[4] = {0.0, 0.0, 0.0, 0.0};
+        int n1 = count_of(c1, k, K), n2 = count_of(c2, k, K);
+        double wk = w ? w[k] : 1.0;
+        memset(G1, 0, sizeof(G1));
+        memset(G2, 0, sizeof(G2));
+        if (n1 < 3 || n1 > K || n2 < 3 || n2 > K) {
+            st |= ORC_ST_BAD_COUNT;
+            lk[k] = wk;
+        } else {
+            load_f32(p1 + k * 2 * K, n1, P);
+            load_f32(p2 + k * 2 * K, n2, Q);
+            st |= loss_variant_pair(P, n1, Q, n2, K, variant, wk, &lk[k], tm, G1, G2);
+        }
+        if (terms) memcpy(terms + 4 * k, tm, sizeof(tm));
+        for (int v = 0; v < K; ++v) {
+            if (g1) { g1[(k * K + v) * 2] = G1[v].x; g1[(k * K + v) * 2 + 1] = G1[v].y; }
+            if (g2) { g2[(k * K + v) * 2] = G2[v].x; g2[(k * K + v) * 2 + 1] = G2[v].y; }
+        }
+    }
+    return st;
+}
+
+/* Double-precision single-pair loss term (for finite differences). */
+int oracle_loss_variant_pair_f64(int K, const double* p1, int n1, const double* p2, int n2, int variant, double w,
+                                 double* lk, double* g1, double* g2)
+{
+    if (K < 3 || K > ORC_MAXK || (variant != 1 && variant != 2)) return -1;
+    opt P[ORC_MAXK], Q[ORC_MAXK], G1[ORC_MAXK], G2[ORC_MAXK];
+    for (int v = 0; v < n1 && v < ORC_MAXK; ++v) { P[v].x = p1[2 * v]; P[v].y = p1[2 * v + 1]; }
+    for (int v = 0; v < n2 && v < ORC_MAXK; ++v) { Q[v].x = p2[2 * v]; Q[v].y = p2[2 * v + 1]; }
+    double tm[4];
+    int st = loss_variant_pair(P, n1, Q, n2, K, variant, w, lk, tm, G1, G2);
+    for (int v = 0; v < K; ++v) {
+        if (g1) { g1[2 * v] = G1[v].x; g1[2 * v + 1] = G1[v].y; }
+        if (g2) { g2[2 * v] = G2[v].x; g2[2 * v + 1] = G2[v].y; }
+    }
+    return st;
+}

@@ -39,12 +39,24 @@ MUTATIONS = [
     ("parallel-edge bbox guard dropped", "ORC_DEGEN_REL * nr * ns && bbox_overlap(a, b, c, d)) return 1;",
      "ORC_DEGEN_REL * nr * ns) return 1;"),
     ("classifier scale L about the origin", "opt o = P[0];", "opt o = {0.0, 0.0};"),
+    # the GIoU / DIoU loss terms
+    ("hull keeps right turns", "while (h >= 2 && orient(hull[h - 2].p, hull[h - 1].p, pts[k].p) <= 0.0) --h;",
+     "while (h >= 2 && orient(hull[h - 2].p, hull[h - 1].p, pts[k].p) >= 0.0) --h;"),
+    ("GIoU hull-area gradient sign", "double gh = w * U / (hq.ah * hq.ah);", "double gh = -w * U / (hq.ah * hq.ah);"),
+    ("GIoU 1 / A_h term dropped from dL/dA_i", "gai = w * (-di + 1.0 / hq.ah);", "gai = w * (-di);"),
+    ("DIoU centre gradient to the wrong polygon",
+     "g2[j].x -= gr * 2.0 * (m1.x - m2.x) / n2;", "g2[j].x += gr * 2.0 * (m1.x - m2.x) / n2;"),
+    ("DIoU diameter from the wrong pair", "if (d > o->c2) { o->c2 = d; o->da = a; o->db = b; }",
+     "if (d > o->c2) { o->c2 = d; o->da = a; o->db = a; }"),
+    ("DIoU centre as the first vertex", "m1.x /= n1; m1.y /= n1; m2.x /= n2; m2.y /= n2;\n    o->rho2",
+     "m1 = P[0]; m2 = Q[0];\n    o->rho2"),
 ]
 
 
 @pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
 def test_pins_catch_mutation(tmp_path, name, old, new):
     src = open(SRC).read()
+    old, new = old.replace("\\n", "\n"), new.replace("\\n", "\n")
     assert src.count(old) == 1, f"mutation anchor not found: {name}"
     mut = tmp_path / "oracle_mut.c"
     mut.write_text(src.replace(old, new))
@@ -53,6 +65,7 @@ def test_pins_catch_mutation(tmp_path, name, old, new):
                    check=True)
     env = dict(os.environ, DGAL_ORACLE_SO=str(so))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")], cwd=ROOT, env=env,
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_loss_variants.py")], cwd=ROOT, env=env,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
