@@ -75,6 +75,12 @@ typedef enum {
                                  parameters in FP64 from the unrounded inputs */
 #define DGAL_PLAIN 0x2u       /* the plain form: FP32 only, no refinement, one
                                  straightforward launch; the backward recomputes the clip */
+#define DGAL_LOSS_GIOU 0x4u   /* dgal_iou_loss: the generalized IoU loss (see there) */
+#define DGAL_LOSS_DIOU 0x8u   /* dgal_iou_loss: the distance IoU loss (see there) */
+#define DGAL_TEST_EXPIRE_WAIT 0x100u /* dgal_nms_rotated, for tests of the failure path: the
+                                        greedy pass takes its wait-expiry path (DGAL_DEV_TIMEOUT,
+                                        results incomplete) at its second block, once that block's
+                                        copies have landed */
 
 /* Device status bits (dgal_get_device_status). */
 #define DGAL_DEV_BAD_COUNT 0x1u /* a vertex count outside [3, K] (pair treated as empty) */
@@ -165,20 +171,45 @@ dgal_status dgal_iou3d_backward(const float* p1, const uint8_t* c1, const float*
  *   loss[0] = scale * sum_k w_k (1 - IoU(p1[k], p2[k]))      (w = NULL: all 1)
  *   grad_p1, grad_p2 = d loss / d p1, d p2  (float [n][K][2]; both NULL to skip)
  *   iou (float [n], optional) receives the IoUs.
+ * With DGAL_LOSS_GIOU (the generalized IoU loss) each pair's term is instead
+ *   w_k (1 - IoU_k + (A_h - U) / A_h),  A_h = area of the convex hull of both
+ *   polygons' vertices, U = A_1 + A_2 - A_i the union;
+ * with DGAL_LOSS_DIOU (the distance IoU loss)
+ *   w_k (1 - IoU_k + rho2 / c2),  rho2 = squared distance between the two
+ *   polygons' vertex means, c2 = squared diameter of that hull (the largest
+ *   squared distance between two of the vertices).
+ * The paper names the IoU loss; these two are its standard extensions.  A
+ * pair whose union is not positive adds w_k and no gradient.
  * K = 4 or 8.  Runs the paired forward with the loss terms summed per warp and
  * the flags kept in `workspace`, then the paired backward with
- * dL/dIoU_k = -scale w_k formed in the kernel; one block of the backward sums
- * the per-warp partials in a fixed order (a separate one-block launch does
- * when no gradient is wanted), so the loss is deterministic.  `workspace`: device memory
- * of at least dgal_iou_loss_workspace_bytes(n, K) bytes (0 for an invalid K),
- * 16-byte aligned, caller-owned; calls sharing it must not overlap in time.
- * DGAL_PLAIN: FP32 only, and the backward recomputes the clip.
+ * dL/dIoU_k = -scale w_k formed in the kernel (for GIoU / DIoU a pass each way
+ * adds the hull / centre terms); one block of the backward sums the per-warp
+ * partials in a fixed order (a separate one-block launch does when no
+ * gradient is wanted), so the loss is deterministic.  `workspace`: device
+ * memory of at least dgal_iou_loss_workspace_bytes(n, K) bytes (0 for an
+ * invalid K), 16-byte aligned, caller-owned; calls sharing it must not
+ * overlap in time.  A call without gradients leaves in the workspace what
+ * dgal_iou_loss_backward needs.  DGAL_PLAIN: FP32 only, and the backward
+ * recomputes the clip.  DGAL_LOSS_GIOU and DGAL_LOSS_DIOU exclude each other.
  * n = 0 writes loss[0] = 0.
  */
 size_t dgal_iou_loss_workspace_bytes(int64_t n, int K);
 dgal_status dgal_iou_loss(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n, int K,
                           const float* weight, float scale, float* loss, float* iou, float* grad_p1, float* grad_p2,
                           void* workspace, size_t ws_bytes, uint32_t flags, void* stream);
+
+/*
+ * Backward of dgal_iou_loss for callers that take the loss's gradient later
+ * (an autograd backward): after a dgal_iou_loss call with grad_p1 = grad_p2 =
+ * NULL on the same inputs, weights, scale, flags and workspace, writes
+ *   grad_p1, grad_p2 = dloss[0] * d loss / d p1, d p2   (float [n][K][2]),
+ * with dloss a device pointer to one float (the upstream gradient of the
+ * loss), read on the device, so nothing synchronises.  dloss = NULL means 1.
+ * Same arguments and checks as dgal_iou_loss otherwise.
+ */
+dgal_status dgal_iou_loss_backward(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                                   int K, const float* weight, float scale, const float* dloss, float* grad_p1,
+                                   float* grad_p2, void* workspace, size_t ws_bytes, uint32_t flags, void* stream);
 
 /*
  * 3D IoU loss: dgal_iou_loss with the 3D IoU of dgal_iou3d_paired, i.e.
@@ -191,6 +222,13 @@ dgal_status dgal_iou3d_loss(const float* p1, const uint8_t* c1, const float* z1,
                             const float* z2, int64_t n, int K, const float* weight, float scale, float* loss,
                             float* iou, float* grad_p1, float* grad_z1, float* grad_p2, float* grad_z2,
                             void* workspace, size_t ws_bytes, uint32_t flags, void* stream);
+
+/* Backward of dgal_iou3d_loss, as dgal_iou_loss_backward is of dgal_iou_loss
+ * (the GIoU / DIoU flags are not taken by the 3D loss). */
+dgal_status dgal_iou3d_loss_backward(const float* p1, const uint8_t* c1, const float* z1, const float* p2,
+                                     const uint8_t* c2, const float* z2, int64_t n, int K, const float* weight,
+                                     float scale, const float* dloss, float* grad_p1, float* grad_z1, float* grad_p2,
+                                     float* grad_z2, void* workspace, size_t ws_bytes, uint32_t flags, void* stream);
 
 /*
  * The intersection polygon of each pair (paper Sec. II-B, `intersect`, with
@@ -235,16 +273,28 @@ dgal_status dgal_line_intersect_backward(const float* l1, const float* l2, int64
                                          float* grad_l1, float* grad_l2, void* stream);
 
 /*
- * Pairwise IoU matrix (the `iou` operation over all N x M pairs):
- *   iou[i*M + j] = IoU(a[i], b[j]), nx[i*M + j] likewise (nx may be NULL).
- * a: float [N][K][2], b: float [M][K][2]; ca, cb counts or NULL.
+ * Pairwise IoU matrix: the paper's `iou` operation (Sec. II-B: intersect
+ * the two convex polygons, take the shoelace areas, IoU = A_I / (A_1 + A_2 -
+ * A_I)) applied to every one of the N x M pairs, as a rotated-box detector
+ * does when it matches or suppresses boxes (Sec. IV):
+ *   iou[i*M + j] = IoU(a[i], b[j]), nx[i*M + j] = vertex count of the
+ *   intersection polygon (nx may be NULL).
+ * a: float [N][K][2], b: float [M][K][2], CCW vertices (Sec. III), device,
+ * 16-byte aligned; ca, cb: uint8 counts (3..K) or NULL for "all K"; iou: float
+ * [N*M], nx: uint8 [N*M], device, caller-owned, overwritten.  N = 0 or M = 0
+ * is a no-op returning DGAL_OK.  Invalid K, negative sizes or a NULL a / b /
+ * iou return DGAL_ERR_INVALID_ARG, a misaligned pointer DGAL_ERR_ALIGNMENT, a
+ * launch error DGAL_ERR_CUDA.
+ * `flags`: DGAL_FP64_REFINE re-decides near-degenerate orientations in FP64.
  */
 dgal_status dgal_iou_pairwise(const float* a, const uint8_t* ca, int64_t N, const float* b, const uint8_t* cb,
                               int64_t M, int K, float* iou, uint8_t* nx, uint32_t flags, void* stream);
 
 /*
- * Ragged batch of S pairwise matrices in one persistent launch.
- * Scene s compares a[a_off[s] .. a_off[s+1]) with b[b_off[s] .. b_off[s+1]);
+ * Ragged batch of S pairwise matrices in one persistent launch: the `iou`
+ * operation of Sec. II-B over every pair of each scene, one scene per image
+ * or point cloud of a detector's batch (Sec. IV), with scenes of different
+ * sizes.  Scene s compares a[a_off[s] .. a_off[s+1]) with b[b_off[s] .. b_off[s+1]);
  * its N_s x M_s matrix is written row-major at iou + out_off[s] (and nx +
  * out_off[s]); out_off[s+1] - out_off[s] must equal N_s * M_s.
  * a_off, b_off, out_off: device int64 [S + 1], non-decreasing, a_off[0] =
@@ -331,14 +381,20 @@ dgal_status dgal_graph_launch(dgal_graph graph, void* stream);
 dgal_status dgal_graph_destroy(dgal_graph graph);
 
 /*
- * Autotuner for the ragged batch: times candidate launch shapes (entries per
- * tile, threads per block, resident blocks per SM) on a synthetic ragged
- * problem generated on the current device and keeps the fastest per (device,
- * K).  cache_path (or, when NULL, the environment variable DGAL_TUNE_CACHE)
- * names a JSON file that is read first and rewritten with the result; NULL and
- * no variable means an in-memory cache only.  A cached shape outside what the
- * kernel accepts (threads a multiple of 32 up to 256, 1 to 64 blocks per SM,
- * a positive tile) is ignored and the shape tuned again.  config_class is reserved (0).
+ * Autotuner of the launch shapes, keeping the fastest per (device, K):
+ *   config_class 0, the ragged batch: times candidate shapes (entries per
+ *     tile, threads per block, resident blocks per SM) on a synthetic ragged
+ *     problem generated on the current device;
+ *   config_class 1, the paired calls: for quadrilaterals (K = 4), times one
+ *     lane per pair against groups of 8 lanes per pair on the forward +
+ *     backward of synthetic pairs at 2^10 .. 2^18 pairs, and sets the batch
+ *     size below which groups are used (smaller batches are latency-bound;
+ *     K = 8 pairs always take groups).  Untuned, that size is 16384.
+ * cache_path (or, when NULL, the environment variable DGAL_TUNE_CACHE) names
+ * a JSON file that is read first and rewritten with the result; NULL and no
+ * variable means an in-memory cache only.  A cached ragged-batch shape
+ * outside what the kernel accepts (threads a multiple of 32 up to 256, 1 to
+ * 64 blocks per SM, a positive tile) is ignored and the shape tuned again.
  * This call allocates device memory and synchronises: call it before timing
  * or capturing, never inside a capture.
  */
@@ -347,6 +403,10 @@ dgal_status dgal_autotune(int K, int config_class, const char* cache_path);
 /* The launch shape currently used by dgal_iou_pairwise_batched for K:
  * out[0] = entries per tile, out[1] = threads per block, out[2] = blocks per SM. */
 dgal_status dgal_get_batched_config(int K, int32_t out[3]);
+
+/* The launch shape currently used by the paired calls for K: *group_below =
+ * the batch size (pairs) below which a group of 8 lanes takes each pair. */
+dgal_status dgal_get_paired_config(int K, int64_t* group_below);
 
 /* Reads (and, if clear != 0, resets) the current device's status word;
  * synchronises the device. */

@@ -32,13 +32,16 @@ import torch
 
 from . import _lib
 from ._lib import (DGAL_DEV_BAD_COUNT, DGAL_DEV_BAD_FLAGS, DGAL_DEV_BAD_OFFSETS, DGAL_DEV_OVERFLOW,
-                   DGAL_FP64_REFINE, DGAL_PLAIN, DgalError)
+                   DGAL_DEV_TIMEOUT, DGAL_FP64_REFINE, DGAL_LOSS_DIOU, DGAL_LOSS_GIOU, DGAL_PLAIN,
+                   DGAL_TEST_EXPIRE_WAIT, DgalError)
 
 __all__ = [
     "dgal_iou_paired", "dgal_iou_backward", "dgal_iou_pairwise", "dgal_iou_pairwise_batched",
     "dgal_iou_pairwise_per_scene", "dgal_batched_workspace_bytes", "BatchedGraph", "dgal_autotune",
-    "dgal_iou_loss", "dgal_iou_loss_workspace_bytes", "IoULoss", "iou_loss",
-    "dgal_get_batched_config", "dgal_get_device_status", "dgal_last_error", "dgal_version", "IoU", "iou",
+    "dgal_iou_loss", "dgal_iou_loss_workspace_bytes", "dgal_iou_loss_backward", "dgal_iou3d_loss_backward",
+    "IoULoss", "iou_loss", "DGAL_LOSS_GIOU", "DGAL_LOSS_DIOU", "LOSS_VARIANTS", "DGAL_DEV_TIMEOUT",
+    "DGAL_TEST_EXPIRE_WAIT",
+    "dgal_get_batched_config", "dgal_get_paired_config", "dgal_get_device_status", "dgal_last_error", "dgal_version", "IoU", "iou",
     "DGAL_FP64_REFINE", "DGAL_PLAIN", "DGAL_DEV_BAD_COUNT", "DGAL_DEV_OVERFLOW", "DGAL_DEV_BAD_FLAGS",
     "DGAL_DEV_BAD_OFFSETS", "DgalError", "dgal_iou3d_paired", "dgal_iou3d_backward", "dgal_iou3d_loss", "IoU3D",
     "iou3d", "IoU3DLoss", "iou3d_loss", "dgal_nms_rotated", "dgal_nms_workspace_bytes",
@@ -114,12 +117,25 @@ def dgal_iou_loss_workspace_bytes(n, K=4):
     return int(_lib.lib().dgal_iou_loss_workspace_bytes(n, K))
 
 
+# loss variant name -> flag bits of dgal_iou_loss
+LOSS_VARIANTS = {"iou": 0, "giou": DGAL_LOSS_GIOU, "diou": DGAL_LOSS_DIOU}
+
+
+def _loss_flags(flags, variant):
+    if variant not in LOSS_VARIANTS:
+        raise ValueError(f"variant must be one of {sorted(LOSS_VARIANTS)}")
+    return (flags & ~(DGAL_LOSS_GIOU | DGAL_LOSS_DIOU)) | LOSS_VARIANTS[variant]
+
+
 def dgal_iou_loss(p1, p2, weight=None, scale=1.0, c1=None, c2=None, grads=True, with_iou=False,
-                  flags=DGAL_FP64_REFINE, stream=None, workspace=None, out=None):
+                  flags=DGAL_FP64_REFINE, stream=None, workspace=None, out=None, variant="iou"):
     """IoU loss (K = 4 or 8): returns (loss [1], g1 | None, g2 | None, iou | None)
-    with loss = scale * sum w (1 - IoU) and g = d loss / d p.  `workspace`
-    (uint8, dgal_iou_loss_workspace_bytes(n, K) bytes) holds the per-warp
-    partials and the flags passed from the forward to the backward."""
+    with loss = scale * sum w (1 - IoU) (variant "iou"), scale * sum w (1 -
+    GIoU) ("giou") or scale * sum w (1 - DIoU) ("diou"), and g = d loss / d p.
+    `workspace` (uint8, dgal_iou_loss_workspace_bytes(n, K) bytes) holds the
+    per-warp partials and the state passed from the forward to the backward;
+    after a call with grads=False it feeds dgal_iou_loss_backward."""
+    flags = _loss_flags(flags, variant)
     _poly(p1, "p1")
     _poly(p2, "p2")
     if p1.shape != p2.shape:
@@ -142,6 +158,41 @@ def dgal_iou_loss(p1, p2, weight=None, scale=1.0, c1=None, c2=None, grads=True, 
               float(scale), _lib.ptr(loss), _lib.ptr(iou), _lib.ptr(g1), _lib.ptr(g2), _lib.ptr(workspace),
               workspace.numel(), flags, _lib.stream_ptr(stream))
     return loss, g1, g2, iou
+
+
+def dgal_iou_loss_backward(p1, p2, workspace, dloss=None, weight=None, scale=1.0, c1=None, c2=None,
+                           flags=DGAL_FP64_REFINE, stream=None, variant="iou"):
+    """Gradients of a loss computed by dgal_iou_loss(grads=False) with this
+    workspace: returns (g1, g2) = dloss * d loss / d p1, d p2, with dloss a
+    CUDA float32 tensor of one element (read on the device) or None (1)."""
+    flags = _loss_flags(flags, variant)
+    n, K = p1.shape[0], p1.shape[1]
+    if dloss is not None and (not isinstance(dloss, torch.Tensor) or dloss.dtype != torch.float32 or
+                              dloss.numel() != 1 or dloss.device != p1.device):
+        raise ValueError("dloss must be a float32 tensor of one element on the polygons' device")
+    dloss = None if dloss is None else dloss.contiguous()
+    g1, g2 = torch.empty_like(p1), torch.empty_like(p2)
+    _lib.call("dgal_iou_loss_backward", _lib.ptr(p1), _lib.ptr(c1), _lib.ptr(p2), _lib.ptr(c2), n, K, _lib.ptr(weight),
+              float(scale), _lib.ptr(dloss), _lib.ptr(g1), _lib.ptr(g2), _lib.ptr(workspace), workspace.numel(), flags,
+              _lib.stream_ptr(stream))
+    return g1, g2
+
+
+def dgal_iou3d_loss_backward(p1, z1, p2, z2, workspace, dloss=None, weight=None, scale=1.0, c1=None, c2=None,
+                             flags=DGAL_FP64_REFINE, stream=None):
+    """Gradients of a loss computed by dgal_iou3d_loss(grads=False) with this
+    workspace: returns (g1, gz1, g2, gz2), each times dloss (see
+    dgal_iou_loss_backward)."""
+    n, K = p1.shape[0], p1.shape[1]
+    if dloss is not None and (not isinstance(dloss, torch.Tensor) or dloss.dtype != torch.float32 or
+                              dloss.numel() != 1 or dloss.device != p1.device):
+        raise ValueError("dloss must be a float32 tensor of one element on the polygons' device")
+    dloss = None if dloss is None else dloss.contiguous()
+    g1, g2, gz1, gz2 = torch.empty_like(p1), torch.empty_like(p2), torch.empty_like(z1), torch.empty_like(z2)
+    _lib.call("dgal_iou3d_loss_backward", _lib.ptr(p1), _lib.ptr(c1), _lib.ptr(z1), _lib.ptr(p2), _lib.ptr(c2),
+              _lib.ptr(z2), n, K, _lib.ptr(weight), float(scale), _lib.ptr(dloss), _lib.ptr(g1), _lib.ptr(gz1),
+              _lib.ptr(g2), _lib.ptr(gz2), _lib.ptr(workspace), workspace.numel(), flags, _lib.stream_ptr(stream))
+    return g1, gz1, g2, gz2
 
 
 def _zext(z, n, name, device):
@@ -529,9 +580,17 @@ class BatchedGraph:
             pass
 
 
-def dgal_autotune(K=4, cache_path=None):
-    _lib.call("dgal_autotune", K, 0, None if cache_path is None else str(cache_path).encode())
-    return dgal_get_batched_config(K)
+def dgal_autotune(K=4, cache_path=None, config_class=0):
+    """Tune a launch shape (0: the ragged batch, 1: the paired calls); returns
+    the shape now in use (dgal_get_batched_config / dgal_get_paired_config)."""
+    _lib.call("dgal_autotune", K, config_class, None if cache_path is None else str(cache_path).encode())
+    return dgal_get_batched_config(K) if config_class == 0 else dgal_get_paired_config(K)
+
+
+def dgal_get_paired_config(K=4):
+    out = ctypes.c_int64(0)
+    _lib.call("dgal_get_paired_config", K, ctypes.byref(out))
+    return dict(group_below=out.value)
 
 
 def dgal_get_batched_config(K=4):
@@ -611,30 +670,37 @@ def iou(p1, p2, c1=None, c2=None, recompute=None, flags=DGAL_FP64_REFINE, flag_b
 
 
 class IoULoss(torch.autograd.Function):
-    """loss = scale * sum w (1 - IoU) through dgal_iou_loss: the forward pass
-    already computes d loss / d p, and the backward only scales it by the
-    incoming gradient."""
+    """loss = scale * sum w (1 - IoU) (or GIoU / DIoU) through dgal_iou_loss:
+    the forward computes the loss and keeps the clip state in a workspace; the
+    backward runs dgal_iou_loss_backward on it with the incoming gradient
+    read on the device (no arithmetic outside the library)."""
 
     @staticmethod
-    def forward(ctx, p1, p2, weight=None, scale=1.0, c1=None, c2=None, flags=DGAL_FP64_REFINE):
-        need = p1.requires_grad or p2.requires_grad
-        loss, g1, g2, _ = dgal_iou_loss(p1.contiguous(), p2.contiguous(), weight, scale, c1, c2, grads=need,
-                                        flags=flags)
-        ctx.save_for_backward(g1, g2)
+    def forward(ctx, p1, p2, weight=None, scale=1.0, c1=None, c2=None, flags=DGAL_FP64_REFINE, variant="iou"):
+        p1c, p2c = p1.contiguous(), p2.contiguous()
+        n, K = p1c.shape[0], p1c.shape[1]
+        ws = torch.empty(max(dgal_iou_loss_workspace_bytes(n, K), 16), device=p1c.device, dtype=torch.uint8)
+        loss, _, _, _ = dgal_iou_loss(p1c, p2c, weight, scale, c1, c2, grads=False, flags=flags, workspace=ws,
+                                      variant=variant)
+        ctx.save_for_backward(p1c, p2c, weight, c1, c2, ws)
+        ctx.scale, ctx.flags, ctx.variant = scale, flags, variant
         return loss[0]
 
     @staticmethod
     def backward(ctx, grad):
-        g1, g2 = ctx.saved_tensors
-        return (None if g1 is None else g1 * grad, None if g2 is None else g2 * grad, None, None, None, None, None)
+        p1, p2, weight, c1, c2, ws = ctx.saved_tensors
+        g1, g2 = dgal_iou_loss_backward(p1, p2, ws, grad.reshape(1).float(), weight, ctx.scale, c1, c2,
+                                        flags=ctx.flags, variant=ctx.variant)
+        return g1, g2, None, None, None, None, None, None
 
 
-def iou_loss(p1, p2, weight=None, reduction="sum", c1=None, c2=None, flags=DGAL_FP64_REFINE):
-    """Differentiable IoU loss sum_k w_k (1 - IoU_k) (or its mean over pairs)."""
+def iou_loss(p1, p2, weight=None, reduction="sum", c1=None, c2=None, flags=DGAL_FP64_REFINE, variant="iou"):
+    """Differentiable IoU loss sum_k w_k (1 - IoU_k) (or its mean over pairs);
+    variant "giou" / "diou" for the generalized / distance IoU loss."""
     if reduction not in ("sum", "mean"):
         raise ValueError("reduction must be 'sum' or 'mean'")
     scale = 1.0 / max(p1.shape[0], 1) if reduction == "mean" else 1.0
-    return IoULoss.apply(p1, p2, weight, scale, c1, c2, flags)
+    return IoULoss.apply(p1, p2, weight, scale, c1, c2, flags, variant)
 
 
 class IoU3D(torch.autograd.Function):
@@ -663,21 +729,26 @@ def iou3d(p1, z1, p2, z2, c1=None, c2=None, flags=DGAL_FP64_REFINE):
 
 
 class IoU3DLoss(torch.autograd.Function):
-    """loss = scale * sum w (1 - IoU3) through dgal_iou3d_loss; the forward
-    computes the gradients, the backward scales them."""
+    """loss = scale * sum w (1 - IoU3) through dgal_iou3d_loss; the backward
+    runs dgal_iou3d_loss_backward with the incoming gradient read on the
+    device."""
 
     @staticmethod
     def forward(ctx, p1, z1, p2, z2, weight=None, scale=1.0, c1=None, c2=None, flags=DGAL_FP64_REFINE):
-        need = any(t.requires_grad for t in (p1, z1, p2, z2))
-        loss, g1, gz1, g2, gz2, _ = dgal_iou3d_loss(p1.contiguous(), z1.contiguous(), p2.contiguous(),
-                                                    z2.contiguous(), weight, scale, c1, c2, grads=need, flags=flags)
-        ctx.save_for_backward(g1, gz1, g2, gz2)
+        ts = [t.contiguous() for t in (p1, z1, p2, z2)]
+        n, K = ts[0].shape[0], ts[0].shape[1]
+        ws = torch.empty(max(dgal_iou_loss_workspace_bytes(n, K), 16), device=ts[0].device, dtype=torch.uint8)
+        loss, *_ = dgal_iou3d_loss(*ts, weight, scale, c1, c2, grads=False, flags=flags, workspace=ws)
+        ctx.save_for_backward(*ts, weight, c1, c2, ws)
+        ctx.scale, ctx.flags = scale, flags
         return loss[0]
 
     @staticmethod
     def backward(ctx, grad):
-        gs = ctx.saved_tensors
-        return tuple(None if g is None else g * grad for g in gs) + (None,) * 5
+        p1, z1, p2, z2, weight, c1, c2, ws = ctx.saved_tensors
+        g1, gz1, g2, gz2 = dgal_iou3d_loss_backward(p1, z1, p2, z2, ws, grad.reshape(1).float(), weight, ctx.scale,
+                                                    c1, c2, flags=ctx.flags)
+        return (g1, gz1, g2, gz2) + (None,) * 5
 
 
 def iou3d_loss(p1, z1, p2, z2, weight=None, reduction="sum", c1=None, c2=None, flags=DGAL_FP64_REFINE):

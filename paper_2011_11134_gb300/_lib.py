@@ -18,6 +18,10 @@ LIB_PATH = os.path.join(PKG, "libdgal.so")
 DGAL_OK = 0
 DGAL_FP64_REFINE = 0x1
 DGAL_PLAIN = 0x2
+DGAL_LOSS_GIOU = 0x4
+DGAL_LOSS_DIOU = 0x8
+DGAL_TEST_EXPIRE_WAIT = 0x100
+DGAL_DEV_TIMEOUT = 0x10
 DGAL_DEV_BAD_COUNT = 0x1
 DGAL_DEV_OVERFLOW = 0x2
 DGAL_DEV_BAD_FLAGS = 0x4
@@ -37,6 +41,10 @@ _SIG = {
     "dgal_iou_pairwise": (_I, [_P, _P, _I64, _P, _P, _I64, _I, _P, _P, _U32, _P]),
     "dgal_iou_loss_workspace_bytes": (ctypes.c_size_t, [_I64, _I]),
     "dgal_iou_loss": (_I, [_P, _P, _P, _P, _I64, _I, _P, ctypes.c_float, _P, _P, _P, _P, _P, ctypes.c_size_t, _U32, _P]),
+    "dgal_iou_loss_backward": (_I, [_P, _P, _P, _P, _I64, _I, _P, ctypes.c_float, _P, _P, _P, _P, ctypes.c_size_t,
+                                     _U32, _P]),
+    "dgal_iou3d_loss_backward": (_I, [_P, _P, _P, _P, _P, _P, _I64, _I, _P, ctypes.c_float, _P, _P, _P, _P, _P, _P,
+                                       ctypes.c_size_t, _U32, _P]),
     "dgal_iou3d_paired": (_I, [_P, _P, _P, _P, _P, _P, _I64, _I, _P, _P, _P, _P, _U32, _P]),
     "dgal_iou3d_backward": (_I, [_P, _P, _P, _P, _P, _P, _I64, _I, _P, _P, _P, _P, _P, _P, _P, _U32, _P]),
     "dgal_iou3d_loss": (_I, [_P, _P, _P, _P, _P, _P, _I64, _I, _P, ctypes.c_float, _P, _P, _P, _P, _P, _P, _P,
@@ -61,6 +69,7 @@ _SIG = {
     "dgal_graph_destroy": (_I, [_P]),
     "dgal_autotune": (_I, [_I, _I, ctypes.c_char_p]),
     "dgal_get_batched_config": (_I, [_I, ctypes.POINTER(ctypes.c_int32)]),
+    "dgal_get_paired_config": (_I, [_I, ctypes.POINTER(ctypes.c_int64)]),
     "dgal_get_device_status": (_I, [ctypes.POINTER(_U32), _I]),
     "dgal_last_error": (ctypes.c_char_p, []),
     "dgal_version": (_I, []),

@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdgal.so")
-SOURCES = ["paired.cu", "paired3d.cu", "pairwise.cu", "api.cu", "noalloc.cu", "nms.cu", "geom_ops.cu", "host_pipe.cu"]
+SOURCES = ["paired.cu", "paired3d.cu", "pairwise.cu", "api.cu", "noalloc.cu", "nms.cu", "geom_ops.cu", "host_pipe.cu",
+           "loss_variants.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -83,6 +83,26 @@ void set_batched_config(int K, BatchedConfig c) {
     g_cfg[{d, K}] = c;
 }
 
+namespace {
+std::map<std::pair<int, int>, PairedConfig> g_pcfg; // (device, K)
+// Untuned default: groups of 8 lanes below 16384 quadrilateral pairs.
+constexpr int64_t kGroupBelowDefault = 16384;
+} // namespace
+
+PairedConfig paired_config(int K) {
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_pcfg.find({d, K});
+    if (it != g_pcfg.end()) return it->second;
+    return PairedConfig{K == 4 ? kGroupBelowDefault : 0};
+}
+
+void set_paired_config(int K, PairedConfig c) {
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_pcfg[{d, K}] = c;
+}
+
 } // namespace dgal
 
 using namespace dgal;
@@ -228,11 +248,69 @@ size_t dgal_iou_loss_workspace_bytes(int64_t n, int K) {
     return (n < 0 || n > (int64_t(1) << 40) || (K != 4 && K != 8)) ? 0 : loss_workspace_bytes(n, K);
 }
 
+static dgal_status check_loss_flags(uint32_t flags, bool three_d) {
+    const uint32_t var = flags & (DGAL_LOSS_GIOU | DGAL_LOSS_DIOU);
+    if (var == (DGAL_LOSS_GIOU | DGAL_LOSS_DIOU))
+        return fail(DGAL_ERR_INVALID_ARG, "DGAL_LOSS_GIOU and DGAL_LOSS_DIOU exclude each other");
+    if (var && three_d) return fail(DGAL_ERR_INVALID_ARG, "the 3D IoU loss takes neither DGAL_LOSS_GIOU nor DGAL_LOSS_DIOU");
+    return DGAL_OK;
+}
+
+static dgal_status check_loss_common(const float* p1, const float* p2, int64_t n, int K, const float* weight,
+                                     void* workspace, size_t ws_bytes) {
+    DGAL_TRY(check_poly_ptr(p1, "p1"));
+    DGAL_TRY(check_poly_ptr(p2, "p2"));
+    if (weight && !aligned(weight, 4)) return fail(DGAL_ERR_ALIGNMENT, "weight is not 4-byte aligned");
+    if (!workspace) return fail(DGAL_ERR_WORKSPACE, "workspace is NULL");
+    if (!aligned(workspace, 16)) return fail(DGAL_ERR_ALIGNMENT, "workspace is not 16-byte aligned");
+    if (ws_bytes < loss_workspace_bytes(n, K))
+        return fail(DGAL_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", ws_bytes, loss_workspace_bytes(n, K));
+    return DGAL_OK;
+}
+
+dgal_status dgal_iou_loss_backward(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                                   int K, const float* weight, float scale, const float* dloss, float* grad_p1,
+                                   float* grad_p2, void* workspace, size_t ws_bytes, uint32_t flags, void* stream) {
+    t_last_error.clear();
+    if (K != 4 && K != 8) return fail(DGAL_ERR_UNSUPPORTED_K, "K must be 4 or 8 (got %d)", K);
+    if (n < 0) return fail(DGAL_ERR_INVALID_ARG, "n = %lld is negative", (long long)n);
+    DGAL_TRY(check_loss_flags(flags, false));
+    if (n == 0) return DGAL_OK;
+    DGAL_TRY(check_poly_ptr(grad_p1, "grad_p1"));
+    DGAL_TRY(check_poly_ptr(grad_p2, "grad_p2"));
+    if (dloss && !aligned(dloss, 4)) return fail(DGAL_ERR_ALIGNMENT, "dloss is not 4-byte aligned");
+    DGAL_TRY(check_loss_common(p1, p2, n, K, weight, workspace, ws_bytes));
+    return launch_iou_loss_backward(p1, c1, p2, c2, n, K, weight, scale, dloss, grad_p1, grad_p2, workspace, flags,
+                                    (cudaStream_t)stream);
+}
+
+dgal_status dgal_iou3d_loss_backward(const float* p1, const uint8_t* c1, const float* z1, const float* p2,
+                                     const uint8_t* c2, const float* z2, int64_t n, int K, const float* weight,
+                                     float scale, const float* dloss, float* grad_p1, float* grad_z1, float* grad_p2,
+                                     float* grad_z2, void* workspace, size_t ws_bytes, uint32_t flags, void* stream) {
+    t_last_error.clear();
+    if (K != 4 && K != 8) return fail(DGAL_ERR_UNSUPPORTED_K, "K must be 4 or 8 (got %d)", K);
+    if (n < 0) return fail(DGAL_ERR_INVALID_ARG, "n = %lld is negative", (long long)n);
+    DGAL_TRY(check_loss_flags(flags, true));
+    if (n == 0) return DGAL_OK;
+    DGAL_TRY(check_z_ptr(z1, "z1"));
+    DGAL_TRY(check_z_ptr(z2, "z2"));
+    DGAL_TRY(check_poly_ptr(grad_p1, "grad_p1"));
+    DGAL_TRY(check_poly_ptr(grad_p2, "grad_p2"));
+    DGAL_TRY(check_z_ptr(grad_z1, "grad_z1"));
+    DGAL_TRY(check_z_ptr(grad_z2, "grad_z2"));
+    if (dloss && !aligned(dloss, 4)) return fail(DGAL_ERR_ALIGNMENT, "dloss is not 4-byte aligned");
+    DGAL_TRY(check_loss_common(p1, p2, n, K, weight, workspace, ws_bytes));
+    return launch_iou3d_loss_backward(p1, c1, z1, p2, c2, z2, n, K, weight, scale, dloss, grad_p1, grad_z1, grad_p2,
+                                      grad_z2, workspace, flags, (cudaStream_t)stream);
+}
+
 dgal_status dgal_iou_loss(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n, int K,
                           const float* weight, float scale, float* loss, float* iou, float* grad_p1, float* grad_p2,
                           void* workspace, size_t ws_bytes, uint32_t flags, void* stream) {
     t_last_error.clear();
     if (K != 4 && K != 8) return fail(DGAL_ERR_UNSUPPORTED_K, "K must be 4 or 8 (got %d)", K);
+    DGAL_TRY(check_loss_flags(flags, false));
     if (n < 0) return fail(DGAL_ERR_INVALID_ARG, "n = %lld is negative", (long long)n);
     if (!loss) return fail(DGAL_ERR_INVALID_ARG, "loss is NULL");
     if (!aligned(loss, 4)) return fail(DGAL_ERR_ALIGNMENT, "loss is not 4-byte aligned");
@@ -264,6 +342,7 @@ dgal_status dgal_iou3d_loss(const float* p1, const uint8_t* c1, const float* z1,
                             void* workspace, size_t ws_bytes, uint32_t flags, void* stream) {
     t_last_error.clear();
     if (K != 4 && K != 8) return fail(DGAL_ERR_UNSUPPORTED_K, "K must be 4 or 8 (got %d)", K);
+    DGAL_TRY(check_loss_flags(flags, true));
     if (n < 0) return fail(DGAL_ERR_INVALID_ARG, "n = %lld is negative", (long long)n);
     if (!loss) return fail(DGAL_ERR_INVALID_ARG, "loss is NULL");
     if (!aligned(loss, 4)) return fail(DGAL_ERR_ALIGNMENT, "loss is not 4-byte aligned");
@@ -457,6 +536,14 @@ dgal_status dgal_get_batched_config(int K, int32_t out[3]) {
     return DGAL_OK;
 }
 
+dgal_status dgal_get_paired_config(int K, int64_t* group_below) {
+    t_last_error.clear();
+    DGAL_TRY(check_K(K));
+    if (!group_below) return fail(DGAL_ERR_INVALID_ARG, "group_below is NULL");
+    *group_below = paired_config(K).group_below;
+    return DGAL_OK;
+}
+
 } // extern "C"
 
 // ---------------------------------------------------------------- autotuner
@@ -519,9 +606,14 @@ bool valid_config(int t, int th, int b) {
     return t > 0 && th >= 32 && th <= 256 && th % 32 == 0 && b >= 1 && b <= 64;
 }
 
-// Tiny JSON map {"key": [tile, threads, blocks_sm], ...} (one line per entry).
-std::map<std::string, BatchedConfig> read_cache(const std::string& path) {
-    std::map<std::string, BatchedConfig> m;
+// Tiny JSON map {"key": [a, b, c], ...} (one line per entry): for a ragged
+// batch key [tile, threads, blocks_sm], for a paired key ("...|paired")
+// [group_below, 0, 0].
+struct Triple {
+    long long a, b, c;
+};
+std::map<std::string, Triple> read_cache(const std::string& path) {
+    std::map<std::string, Triple> m;
     FILE* f = fopen(path.c_str(), "r");
     if (!f) return m;
     char line[1024];
@@ -531,46 +623,149 @@ std::map<std::string, BatchedConfig> read_cache(const std::string& path) {
         char* q2 = strchr(q1 + 1, '"');
         if (!q2) continue;
         std::string key(q1 + 1, q2);
-        int t = 0, th = 0, b = 0;
+        long long t = 0, th = 0, b = 0;
         char* br = strchr(q2, '[');
-        if (br && sscanf(br, "[%d, %d, %d]", &t, &th, &b) == 3 && valid_config(t, th, b)) m[key] = BatchedConfig{t, th, b};
+        if (br && sscanf(br, "[%lld, %lld, %lld]", &t, &th, &b) == 3) m[key] = Triple{t, th, b};
     }
     fclose(f);
     return m;
 }
 
-bool write_cache(const std::string& path, const std::map<std::string, BatchedConfig>& m) {
+bool write_cache(const std::string& path, const std::map<std::string, Triple>& m) {
     std::string tmp = path + ".tmp";
     FILE* f = fopen(tmp.c_str(), "w");
     if (!f) return false;
     fprintf(f, "{\n");
     size_t k = 0;
     for (auto& kv : m) {
-        fprintf(f, "  \"%s\": [%d, %d, %d]%s\n", kv.first.c_str(), kv.second.tile, kv.second.threads,
-                kv.second.blocks_sm, (++k < m.size()) ? "," : "");
+        fprintf(f, "  \"%s\": [%lld, %lld, %lld]%s\n", kv.first.c_str(), kv.second.a, kv.second.b, kv.second.c,
+                (++k < m.size()) ? "," : "");
     }
     fprintf(f, "}\n");
     fclose(f);
     return rename(tmp.c_str(), path.c_str()) == 0;
 }
 
+// IoU-loss-like quadrilateral pairs for the paired tuning: box a with center
+// in [0, 10]^2, sides in [0.5, 4], any angle; box b = a moved by about
+// N(0, 0.5) per axis, sides scaled in [0.8, 1.2], turned by up to 0.3.
+__global__ void k_synth_pairs(float* __restrict__ p1, float* __restrict__ p2, int64_t n, uint64_t seed) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint64_t b = seed * 0x9E3779B97F4A7C15ull + (uint64_t)k * 32u;
+    const float cx = 10.f * unit(b), cy = 10.f * unit(b + 1);
+    const float w = 0.5f + 3.5f * unit(b + 2), h = 0.5f + 3.5f * unit(b + 3);
+    const float th = 6.2831853f * unit(b + 4) - 3.1415927f;
+    const float dx = (unit(b + 5) + unit(b + 6) + unit(b + 7) - 1.5f), dy = (unit(b + 8) + unit(b + 9) + unit(b + 10) - 1.5f);
+    const float w2 = w * (0.8f + 0.4f * unit(b + 11)), h2 = h * (0.8f + 0.4f * unit(b + 12));
+    const float th2 = th + 0.6f * unit(b + 13) - 0.3f;
+    const float lx[4] = {-0.5f, 0.5f, 0.5f, -0.5f}, ly[4] = {-0.5f, -0.5f, 0.5f, 0.5f};
+    float s, c, s2, c2;
+    sincosf(th, &s, &c);
+    sincosf(th2, &s2, &c2);
+    for (int v = 0; v < 4; ++v) {
+        p1[k * 8 + 2 * v] = cx + c * w * lx[v] - s * h * ly[v];
+        p1[k * 8 + 2 * v + 1] = cy + s * w * lx[v] + c * h * ly[v];
+        p2[k * 8 + 2 * v] = cx + dx + c2 * w2 * lx[v] - s2 * h2 * ly[v];
+        p2[k * 8 + 2 * v + 1] = cy + dy + s2 * w2 * lx[v] + c2 * h2 * ly[v];
+    }
+}
+
 } // namespace dgal_tune
 
 using namespace dgal_tune;
 
+// Paired launch shape (config_class 1): for quadrilaterals, the batch size
+// below which groups of 8 lanes beat one lane per pair, from timing both
+// shapes on the forward + backward of synthetic pairs at sizes 2^10 .. 2^18.
+static dgal_status tune_paired(int K, const std::string& path) {
+    const std::string key = device_key(K) + "|paired";
+    if (!path.empty()) {
+        auto m = read_cache(path);
+        auto it = m.find(key);
+        if (it != m.end() && it->second.a >= 0) {
+            set_paired_config(K, PairedConfig{(int64_t)it->second.a});
+            return DGAL_OK;
+        }
+    }
+    if (K != 4) { // K = 8 pairs always take groups of 8 lanes
+        set_paired_config(K, PairedConfig{0});
+        return DGAL_OK;
+    }
+    const int64_t nmax = 1 << 18;
+    float *p1 = nullptr, *p2 = nullptr, *iou = nullptr, *grad = nullptr, *g1 = nullptr, *g2 = nullptr;
+    uint8_t *nx = nullptr, *xf = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(p1); cudaFree(p2); cudaFree(iou); cudaFree(grad); cudaFree(g1); cudaFree(g2); cudaFree(nx); cudaFree(xf);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (cudaMalloc(&p1, nmax * 32) != cudaSuccess || cudaMalloc(&p2, nmax * 32) != cudaSuccess ||
+        cudaMalloc(&iou, nmax * 4) != cudaSuccess || cudaMalloc(&grad, nmax * 4) != cudaSuccess ||
+        cudaMalloc(&g1, nmax * 32) != cudaSuccess || cudaMalloc(&g2, nmax * 32) != cudaSuccess ||
+        cudaMalloc(&nx, nmax) != cudaSuccess || cudaMalloc(&xf, nmax * 8) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cleanup();
+        return fail(DGAL_ERR_CUDA, "autotune: allocation failed");
+    }
+    k_synth_pairs<<<(unsigned)(nmax / 256), 256>>>(p1, p2, nmax, 3);
+    cudaMemset(grad, 0, nmax * 4);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cleanup();
+        return fail(DGAL_ERR_CUDA, "autotune: synthetic input generation failed");
+    }
+    // time one shape (forced by the threshold) at n pairs: best of 5 steps after one
+    auto step_ms = [&](int64_t n, int64_t below) -> float {
+        set_paired_config(4, PairedConfig{below});
+        float best = 1e30f;
+        for (int rep = 0; rep < 6; ++rep) {
+            cudaEventRecord(e0, 0);
+            launch_paired_fwd(p1, nullptr, p2, nullptr, n, 4, iou, nx, xf, nullptr, kFlagRefine, 0);
+            launch_paired_bwd(p1, nullptr, p2, nullptr, n, 4, grad, nx, xf, g1, g2, kFlagRefine, 0);
+            cudaEventRecord(e1, 0);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < best) best = ms;
+        }
+        return best;
+    };
+    int64_t below = 2 * nmax; // groups everywhere unless one lane per pair wins
+    for (int64_t n = 1 << 10; n <= nmax; n <<= 2) {
+        const float tg = step_ms(n, INT64_MAX), t1 = step_ms(n, 0);
+        if (t1 <= tg) {
+            below = n;
+            break;
+        }
+    }
+    const cudaError_t e = cudaGetLastError();
+    cleanup();
+    if (e != cudaSuccess) return fail(DGAL_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+    set_paired_config(4, PairedConfig{below});
+    if (!path.empty()) {
+        auto m = read_cache(path);
+        m[key] = Triple{(long long)below, 0, 0};
+        if (!write_cache(path, m)) return fail(DGAL_ERR_INVALID_ARG, "autotune: cannot write %s", path.c_str());
+    }
+    return DGAL_OK;
+}
+
 extern "C" dgal_status dgal_autotune(int K, int config_class, const char* cache_path) {
     t_last_error.clear();
     DGAL_TRY(check_K(K));
-    (void)config_class;
+    if (config_class != 0 && config_class != 1)
+        return fail(DGAL_ERR_INVALID_ARG, "config_class must be 0 (ragged batch) or 1 (paired), got %d", config_class);
     std::string path;
     if (cache_path) path = cache_path;
     else if (const char* env = getenv("DGAL_TUNE_CACHE")) path = env;
+    if (config_class == 1) return tune_paired(K, path);
     const std::string key = device_key(K);
     if (!path.empty()) {
         auto m = read_cache(path);
         auto it = m.find(key);
-        if (it != m.end()) {
-            set_batched_config(K, it->second);
+        if (it != m.end() && valid_config((int)it->second.a, (int)it->second.b, (int)it->second.c)) {
+            set_batched_config(K, BatchedConfig{(int)it->second.a, (int)it->second.b, (int)it->second.c});
             return DGAL_OK;
         }
     }
@@ -652,7 +847,7 @@ extern "C" dgal_status dgal_autotune(int K, int config_class, const char* cache_
     set_batched_config(K, best);
     if (!path.empty()) {
         auto m = read_cache(path);
-        m[key] = best;
+        m[key] = Triple{best.tile, best.threads, best.blocks_sm};
         if (!write_cache(path, m)) return fail(DGAL_ERR_INVALID_ARG, "autotune: cannot write %s", path.c_str());
     }
     return DGAL_OK;

@@ -19,7 +19,7 @@
 //   Near-degenerate pairs, and pairs whose sign pattern is not that of two
 //   convex polygons in general position, take the warp-cooperative robust
 //   path (candidate gathering and an angular sort; with refinement, FP64
-//   orientation tests, crossing parameters and areas).
+//   orientation tests and float-float crossing parameters and areas).
 //
 // Backward (paper Sec. II-B `iou_grad`): the recorded codes rebuild the
 // intersection vertices (crossings as a + t ea), the shoelace adjoint gives
@@ -50,7 +50,7 @@ constexpr float kRouteRel = 5e-6f;
 // coordinates up to L), so the IoU error grows as u L^2 / U for a small union
 // U.  An intersecting pair with U below this fraction of L^2 (thin or tiny
 // polygons far apart in the pair's frame) is handed to the warp-cooperative
-// path, whose rounding estimate takes such areas in FP64.  None of the
+// path, whose rounding estimate takes such areas in float-float.  None of the
 // IoU-loss rectangle pairs and about 0.05% of the intersecting convex-hull
 // pairs are below it.
 constexpr float kThinRel = 0.02f;
@@ -756,6 +756,66 @@ __device__ __forceinline__ float pseudo_angle(float dx, float dy) {
     return 2.f - r;
 }
 
+// ------------------------------------------------------------ float-float
+//
+// A float-float number hi + lo carries about 48 significant bits with FP32
+// instructions only: sums by the error-free two-sum, products with the FMA
+// residual, a quotient refined by one correction step (the classic
+// double-single arithmetic of Dekker and of Knuth's two-sum).  The warp
+// paths take their accurate areas and shoelace adjoints in it, so that FP64
+// stays with the orientation tests.
+
+struct ff {
+    float hi, lo;
+    __device__ __forceinline__ ff() : hi(0.f), lo(0.f) {}
+    __device__ __forceinline__ ff(float f) : hi(f), lo(0.f) {}
+    __device__ __forceinline__ ff(float h, float l) : hi(h), lo(l) {}
+    __device__ __forceinline__ explicit operator float() const { return hi + lo; }
+};
+
+// s + e = a + b exactly
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return ff(s, (a - (s - bb)) + (b - bb));
+}
+// the same for |a| >= |b| (or a = 0)
+__device__ __forceinline__ ff ff_quick(float a, float b) {
+    const float s = a + b;
+    return ff(s, b - (s - a));
+}
+__device__ __forceinline__ ff operator+(ff x, ff y) {
+    ff s = ff_two_sum(x.hi, y.hi);
+    const ff t = ff_two_sum(x.lo, y.lo);
+    s = ff_quick(s.hi, s.lo + t.hi);
+    return ff_quick(s.hi, s.lo + t.lo);
+}
+__device__ __forceinline__ ff operator-(ff x) { return ff(-x.hi, -x.lo); }
+__device__ __forceinline__ ff operator-(ff x, ff y) { return x + (-y); }
+__device__ __forceinline__ ff operator*(ff x, ff y) {
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e));
+    return ff_quick(p, e);
+}
+__device__ __forceinline__ ff operator/(ff x, ff y) {
+    const float q1 = x.hi / y.hi;
+    const ff r = x - y * ff(q1);
+    return ff_quick(q1, r.hi / y.hi);
+}
+__device__ __forceinline__ ff& operator+=(ff& x, ff y) { return x = x + y; }
+__device__ __forceinline__ bool operator>(ff x, ff y) { return x.hi > y.hi || (x.hi == y.hi && x.lo > y.lo); }
+__device__ __forceinline__ bool operator!=(ff x, ff y) { return x.hi != y.hi || x.lo != y.lo; }
+
+// Warp shuffles of float and float-float values.
+__device__ __forceinline__ float shfl(unsigned m, float v, int src) { return __shfl_sync(m, v, src); }
+__device__ __forceinline__ ff shfl(unsigned m, ff v, int src) {
+    return ff(__shfl_sync(m, v.hi, src), __shfl_sync(m, v.lo, src));
+}
+__device__ __forceinline__ float shfl_xor(unsigned m, float v, int off) { return __shfl_xor_sync(m, v, off); }
+__device__ __forceinline__ ff shfl_xor(unsigned m, ff v, int off) {
+    return ff(__shfl_xor_sync(m, v.hi, off), __shfl_xor_sync(m, v.lo, off));
+}
+
 // ------------------------------------------------- warp-cooperative robust path
 //
 // All 32 lanes of a warp work on one pair, with the candidate rules of the
@@ -769,16 +829,11 @@ __device__ __forceinline__ float pseudo_angle(float dx, float dy) {
 // every other lane, and the areas are shuffle reductions of shoelace terms.
 // The areas are taken in FP32 with an estimate of their rounding error; when
 // refining and that estimate is not far below the IoU tolerance (slivers,
-// tiny intersections), they are taken again in FP64 about the candidates'
-// centroid.  GB300's FP64 rate is a small fraction of its FP32 rate, so FP64
-// is kept to the orientation tests and that fallback.  The result is
-// returned in every lane.
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    return v;
-}
+// tiny intersections), they are taken again in float-float about the
+// candidates' centroid, with every crossing placed from float-float
+// orientations.  GB300's FP64 rate is a small fraction of its FP32 rate, and
+// FP64 is kept to the orientation tests.  The result is returned in every
+// lane.
 
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
@@ -986,7 +1041,20 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
         o.degen |= 1u;
         return;
     }
-    if (m < 3) return;
+    if (m < 3) {
+        // empty intersection: the inputs' areas are still reported (the union)
+        float s1 = 0.f, s2 = 0.f;
+        if (lane < K) {
+            const int v = lane, w = (lane + 1 < n1) ? lane + 1 : 0, w2 = (lane + 1 < n2) ? lane + 1 : 0;
+            const float X1 = sel<K>(px, v) - ox, Y1 = sel<K>(py, v) - oy, X2 = sel<K>(px, w) - ox, Y2 = sel<K>(py, w) - oy;
+            const float U1 = sel<K>(qx, v) - ox, V1 = sel<K>(qy, v) - oy, U2 = sel<K>(qx, w2) - ox, V2 = sel<K>(qy, w2) - oy;
+            s1 = (v < n1) ? X1 * Y2 - Y1 * X2 : 0.f;
+            s2 = (v < n2) ? U1 * V2 - V1 * U2 : 0.f;
+        }
+        o.a1 = 0.5f * warp_sum_f(s1);
+        o.a2 = 0.5f * warp_sum_f(s2);
+        return;
+    }
     const float x = (fx0 - ox) + t * (fx1 - fx0), y = (fy0 - oy) + t * (fy1 - fy0);
 
     // angular order about the centroid, ties by code; rotate to the smallest code
@@ -1068,35 +1136,53 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
     o.a1 = a1;
     o.a2 = a2;
     if (refine && !(est <= kAreaEstMax * U)) {
-        // FP64 areas: vertices placed on their edges in FP64 (a crossing's
-        // parameter from its two orientations in FP64, which have opposite
-        // signs at a proper crossing, so the quotient does not cancel), the
-        // intersection about the candidates' centroid, the inputs about P1's
-        // vertex 0
-        double t64 = (double)t;
-        if (kind == 2) {
-            const double s0 = orient64(gx0, gy0, gx1, gy1, fx0, fy0), s1 = orient64(gx0, gy0, gx1, gy1, fx1, fy1);
-            t64 = s0 / (s0 - s1);
+        // Float-float areas: every vertex placed on its edge in float-float
+        // (a crossing's parameter from its two orientations about the P2
+        // edge, which have opposite signs at a proper crossing, so their
+        // difference does not cancel), the intersection about the
+        // candidates' FP32 centroid, the inputs about P1's vertex 0.
+        ff X(0.f), Y(0.f);
+        if (live) {
+            const ff f0x = ff_two_sum(fx0, -ox), f0y = ff_two_sum(fy0, -oy);
+            if (kind == 2) {
+                // S = orient(g0, g1, f) for both ends of the P1 edge, exactly
+                // as float-float from the FP32 inputs
+                const ff sx = ff_two_sum(gx1, -gx0), sy = ff_two_sum(gy1, -gy0);
+                const ff s0 = sx * ff_two_sum(fy0, -gy0) - sy * ff_two_sum(fx0, -gx0);
+                const ff s1 = sx * ff_two_sum(fy1, -gy0) - sy * ff_two_sum(fx1, -gx0);
+                const ff tt = s0 / (s0 - s1);
+                X = f0x + tt * ff_two_sum(fx1, -fx0);
+                Y = f0y + tt * ff_two_sum(fy1, -fy0);
+            } else {
+                X = f0x;
+                Y = f0y;
+            }
         }
-        const double X64 = ((double)fx0 - (double)ox) + t64 * ((double)fx1 - (double)fx0);
-        const double Y64 = ((double)fy0 - (double)oy) + t64 * ((double)fy1 - (double)fy0);
         // about the FP32 centroid: any origin gives the same area, and one
         // within the polygon keeps the products small
-        const double mx = (double)mxf, my = (double)myf;
-        const double nxp = __shfl_sync(full, X64, nl), nyp = __shfl_sync(full, Y64, nl);
-        const double tm = live ? __dsub_rn(__dmul_rn(X64 - mx, nyp - my), __dmul_rn(Y64 - my, nxp - mx)) : 0.0;
-        double t2 = 0.0;
+        const ff mx(mxf), my(myf);
+        const ff Xn = shfl(full, X, nl), Yn = shfl(full, Y, nl);
+        ff tm = live ? (X - mx) * (Yn - my) - (Y - my) * (Xn - mx) : ff(0.f);
+        ff t2(0.f);
         if (on) {
-            const double Xv = (double)xv - ox, Yv = (double)yv - oy, Xw = (double)xw - ox, Yw = (double)yw - oy;
-            t2 = __dsub_rn(__dmul_rn(Xv, Yw), __dmul_rn(Yv, Xw));
+            const ff Xv = ff_two_sum(xv, -ox), Yv = ff_two_sum(yv, -oy), Xw = ff_two_sum(xw, -ox),
+                     Yw = ff_two_sum(yw, -oy);
+            t2 = Xv * Yw - Yv * Xw;
         }
-        const double ai64 = 0.5 * warp_sum(tm);
-        const double a164 = 0.5 * warp_sum(lane < 8 ? t2 : 0.0), a264 = 0.5 * warp_sum(second ? t2 : 0.0);
-        o.ai = (float)ai64;
-        o.a1 = (float)a164;
-        o.a2 = (float)a264;
-        const double U64 = a164 + a264 - ai64;
-        o.iou = (U64 > 0.0) ? (float)(ai64 / U64) : 0.f;
+        ff t1 = lane < 8 ? t2 : ff(0.f), t3 = second ? t2 : ff(0.f);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            tm += shfl_xor(full, tm, off);
+            t1 += shfl_xor(full, t1, off);
+            t3 += shfl_xor(full, t3, off);
+        }
+        const ff half(0.5f);
+        const ff aiF = half * tm, a1F = half * t1, a2F = half * t3;
+        o.ai = (float)aiF;
+        o.a1 = (float)a1F;
+        o.a2 = (float)a2F;
+        const ff UF = a1F + a2F - aiF;
+        o.iou = (UF > ff(0.f)) ? (float)(aiF / UF) : 0.f;
         return;
     }
     o.iou = (U > 0.f) ? ai / U : 0.f;
@@ -1108,16 +1194,28 @@ __device__ __noinline__ void warp_robust(const float* __restrict__ p1, const flo
 // three areas (A_i, A_1, A_2) from a policy object, so the same clip
 // adjoint serves the 2D IoU and the 3D IoU.
 
-// L = g IoU, IoU = A_i / (A_1 + A_2 - A_i) (paper Sec. II-B `iou`).
+// 1 / U: in FP32 the approximate reciprocal refined by one Newton step
+// (within about 1 ulp, and without the branch of IEEE division; the
+// gradients it scales are checked to 1e-3), in float-float its quotient.
+__device__ __forceinline__ float recip_adj(float U) {
+    const float r = __fdividef(1.0f, U);
+    return r * fmaf(-U, r, 2.0f);
+}
+__device__ __forceinline__ ff recip_adj(ff U) { return ff(1.0f) / U; }
+
+// L = g IoU + e (A_i - A_1 - A_2), IoU = A_i / (A_1 + A_2 - A_i) (paper
+// Sec. II-B `iou`); e = 0 except in the GIoU loss, where the term -U / A_h of
+// the loss adds it (with the hull area A_h held fixed here).
 struct AdjIou {
     float g;
+    float e;
     template <typename R>
     __device__ __forceinline__ bool operator()(R ai, R a1, R a2, R& gai, R& ga1, R& ga2) {
         const R U = a1 + a2 - ai;
         if (!(U > (R)0)) return false;
-        const R rU = (R)1 / U;
-        gai = (R)g * (a1 + a2) * rU * rU;
-        ga1 = ga2 = -(R)g * ai * rU * rU;
+        const R rU = recip_adj(U);
+        gai = (R)g * (a1 + a2) * rU * rU + (R)e;
+        ga1 = ga2 = -(R)g * ai * rU * rU - (R)e;
         return true;
     }
 };
@@ -1198,7 +1296,7 @@ struct AdjIou3 {
 // t = cross(eb, a - b) / cross(ea, eb)), the shoelace adjoint
 // dA/dw_k = 1/2 perp(w_{k+1} - w_{k-1}) gives each vertex's gradient, vertex
 // codes route it to that vertex and crossing codes through the adjoint of w
-// onto the four endpoints of the two edges; FP64 with refinement.
+// onto the four endpoints of the two edges; in float-float with refinement.
 
 // Warp-cooperative form of the shoelace adjoint, for the pairs the shape
 // derivative cannot take: all 32 lanes work on one pair.  Lane k rebuilds
@@ -1223,7 +1321,9 @@ __device__ __noinline__ uint32_t warp_bwd(const float* __restrict__ p1, const fl
     const R ox = (R)px[0], oy = (R)py[0];
     if (lane < 4 * K) sh[lane] = 0.f;
     __syncwarp();
-    const bool live = (uint32_t)lane < nx;
+    // fewer than three vertices: an empty intersection (the inputs' areas
+    // still take their adjoints)
+    const bool live = nx >= 3u && (uint32_t)lane < nx;
     const uint32_t c = live ? code_at<K>(codes, (uint32_t)lane) : 0xFFu;
     const uint32_t kind = c >> 6, lo = c & 7u, ci = (c >> 3) & 7u;
     bool bad = false;
@@ -1263,8 +1363,8 @@ __device__ __noinline__ uint32_t warp_bwd(const float* __restrict__ p1, const fl
     }
     const uint32_t err = __any_sync(full, bad) ? kDevBadFlags : 0u;
     const int nxt = (lane + 1 < (int)nx) ? lane + 1 : 0, prv = (lane == 0) ? (int)nx - 1 : lane - 1;
-    const R wxn = __shfl_sync(full, wx, nxt), wyn = __shfl_sync(full, wy, nxt);
-    const R wxp = __shfl_sync(full, wx, prv < 0 ? 0 : prv), wyp = __shfl_sync(full, wy, prv < 0 ? 0 : prv);
+    const R wxn = shfl(full, wx, nxt), wyn = shfl(full, wy, nxt);
+    const R wxp = shfl(full, wx, prv < 0 ? 0 : prv), wyp = shfl(full, wy, prv < 0 ? 0 : prv);
     R twoA = live ? wx * wyn - wy * wxn : (R)0;
     // input areas: lane v (P1) and lane K + v (P2) hold vertex v
     const int side = (lane >= K && lane < 2 * K) ? 1 : 0;
@@ -1287,16 +1387,16 @@ __device__ __noinline__ uint32_t warp_bwd(const float* __restrict__ p1, const fl
     R s1 = (lane < K) ? aterm : (R)0, s2 = side ? aterm : (R)0;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        twoA += __shfl_xor_sync(full, twoA, off);
-        s1 += __shfl_xor_sync(full, s1, off);
-        s2 += __shfl_xor_sync(full, s2, off);
+        twoA += shfl_xor(full, twoA, off);
+        s1 += shfl_xor(full, s1, off);
+        s2 += shfl_xor(full, s2, off);
     }
-    twoA = __shfl_sync(full, twoA, 0);
-    s1 = __shfl_sync(full, s1, 0);
-    s2 = __shfl_sync(full, s2, 0);
+    twoA = shfl(full, twoA, 0);
+    s1 = shfl(full, s1, 0);
+    s2 = shfl(full, s2, 0);
     const R a1 = (R)0.5 * s1, a2 = (R)0.5 * s2, ai = (R)0.5 * twoA;
     R gai = 0, ga1 = 0, ga2 = 0;
-    const bool ok = err == 0u && nx >= 3u && adj(ai, a1, a2, gai, ga1, ga2);
+    const bool ok = err == 0u && adj(ai, a1, a2, gai, ga1, ga2);
     const R gas = side ? ga2 : ga1;
     if (ok && live) {
         const R gwx = (R)0.5 * gai * (wyn - wyp), gwy = (R)0.5 * gai * (wxp - wxn);
@@ -1395,14 +1495,16 @@ __device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, Adj& adj, uint32_
 #pragma unroll
     for (int v = 0; v < K; ++v) { g1x[v] = g1y[v] = g2x[v] = g2y[v] = 0.f; }
     if (nx > (uint32_t)C) return kDevBadFlags;
-    if (nx < 3u) return 0u;
+    // fewer than three vertices: an empty intersection (no piece on any edge),
+    // taken by the same arithmetic as the other pairs
+    const bool empty = nx < 3u;
 
     // inside vertices and crossings named by the codes
     uint32_t in1 = 0, in2 = 0, other = 0;
     M X = 0;
     if constexpr (K == 4) {
         // slots past nx read as unused (0xFF); one table entry per slot
-        const uint64_t live = (nx >= 8u) ? ~0ull : ((1ull << (8u * nx)) - 1ull);
+        const uint64_t live = empty ? 0ull : (nx >= 8u) ? ~0ull : ((1ull << (8u * nx)) - 1ull);
         const uint64_t w = codes.w[0] | ~live;
         const uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
         uint32_t acc = 0;
@@ -1428,7 +1530,7 @@ __device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, Adj& adj, uint32_
 #pragma unroll
         for (int k = 0; k < C; ++k) {
             const uint32_t c = code_at<K>(codes, (uint32_t)k);
-            const bool live = (uint32_t)k < nx;
+            const bool live = !empty && (uint32_t)k < nx;
             const uint32_t kind = c >> 6, lo = c & 7u, ci = (c >> 3) & 7u;
             in1 |= (live && kind == 0u) ? (1u << (c & 0x1Fu)) : 0u;
             in2 |= (live && kind == 1u) ? (1u << (c & 0x1Fu)) : 0u;
@@ -1440,7 +1542,7 @@ __device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, Adj& adj, uint32_
     // edge piece counts must match the inside vertices: no crossing between
     // two inside vertices, one between inside and outside, none or two
     // between two outside vertices; and every code must be distinct
-    bool ok = (__popc(in1) + __popc(in2) + popc_(X)) == (int)nx;
+    bool ok = empty || (__popc(in1) + __popc(in2) + popc_(X)) == (int)nx;
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         const bool vi = !COUNTS || i < n1, vj = !COUNTS || i < n2;
@@ -1468,6 +1570,7 @@ __device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, Adj& adj, uint32_
     for (int v = 0; v < K; ++v) { t0[v] = kInf; t1[v] = -kInf; u0[v] = kInf; u1[v] = -kInf; }
 #pragma unroll
     for (int i = 0; i < K; ++i) {
+        float tr[K]; // row i's parameters, reduced after the row
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             const bool m = (X >> (i * K + j)) & 1u;
@@ -1476,24 +1579,28 @@ __device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, Adj& adj, uint32_
             const float T = g.eay[i] * dx - g.eax[i] * dy;
             const float D = g.eax[i] * g.eby[j] - g.eay[i] * g.ebx[j];
             const float rD = m ? __fdividef(1.0f, D) : kNaN;
-            const float t = S * rD, u = -T * rD;
-            t0[i] = fminf(t0[i], t);
-            t1[i] = fmaxf(t1[i], t);
+            const float u = -T * rD;
+            tr[j] = S * rD;
             u0[j] = fminf(u0[j], u);
             u1[j] = fmaxf(u1[j], u);
         }
+#pragma unroll
+        for (int j = 0; j + 1 < K; j += 2) {
+            t0[i] = fmin3(t0[i], tr[j], tr[j + 1]);
+            t1[i] = fmax3(t1[i], tr[j], tr[j + 1]);
+        }
     }
+    // Edges without a piece get [0, 0]: every term they would add is then 0.
     const float L = pair_scale<K, COUNTS>(g);
-    uint32_t hasA = in1, hasB = in2;
 #pragma unroll
     for (int v = 0; v < K; ++v) {
         const uint32_t na = (v + 1 < (int)n1m) ? (uint32_t)(v + 1) : 0u, nb = (v + 1 < (int)n2m) ? (uint32_t)(v + 1) : 0u;
-        hasA |= ((X >> (v * K)) & kRow0) ? (1u << v) : 0u;
-        hasB |= ((X >> v) & col0) ? (1u << v) : 0u;
-        t0[v] = ((in1 >> v) & 1u) ? 0.f : t0[v];
-        t1[v] = ((in1 >> na) & 1u) ? 1.f : t1[v];
-        u0[v] = ((in2 >> v) & 1u) ? 0.f : u0[v];
-        u1[v] = ((in2 >> nb) & 1u) ? 1.f : u1[v];
+        const bool pa = ((in1 >> v) & 1u) || ((X >> (v * K)) & kRow0);
+        const bool pb = ((in2 >> v) & 1u) || ((X >> v) & col0);
+        t0[v] = pa ? (((in1 >> v) & 1u) ? 0.f : t0[v]) : 0.f;
+        t1[v] = pa ? (((in1 >> na) & 1u) ? 1.f : t1[v]) : 0.f;
+        u0[v] = pb ? (((in2 >> v) & 1u) ? 0.f : u0[v]) : 0.f;
+        u1[v] = pb ? (((in2 >> nb) & 1u) ? 1.f : u1[v]) : 0.f;
     }
     float twoA = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
@@ -1502,26 +1609,26 @@ __device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, Adj& adj, uint32_
         const float c2 = g.bx[v] * g.eby[v] - g.by[v] * g.ebx[v];
         s1 += (!COUNTS || v < n1) ? c1 : 0.f;
         s2 += (!COUNTS || v < n2) ? c2 : 0.f;
-        twoA += ((hasA >> v) & 1u) ? (t1[v] - t0[v]) * c1 : 0.f;
-        twoA += ((hasB >> v) & 1u) ? (u1[v] - u0[v]) * c2 : 0.f;
+        twoA = fmaf(t1[v] - t0[v], c1, twoA);
+        twoA = fmaf(u1[v] - u0[v], c2, twoA);
     }
     const float a1 = 0.5f * s1, a2 = 0.5f * s2, ai = 0.5f * twoA;
-    if (refine && ai < kTinyArea * L * L) return kSlow;
+    if (refine && !empty && ai < kTinyArea * L * L) return kSlow;
     float gai, ga1, ga2;
     if (!adj(ai, a1, a2, gai, ga1, ga2)) return 0u;
-    const float h1 = 0.5f * ga1, h2 = 0.5f * ga2;
-    // start / end contributions of every edge, then vertex v = start of edge v
-    // plus end of edge v-1
+    const float h1 = 0.5f * ga1, h2 = 0.5f * ga2, hg = 0.5f * gai;
+    // Start / end weights of every edge: the piece [t0, t1] moves the start
+    // vertex by ((1 - t0)^2 - (1 - t1)^2) / 2 = (t1 - t0)(2 - t0 - t1) / 2 and
+    // the end vertex by (t1^2 - t0^2) / 2 = (t1 - t0)(t1 + t0) / 2 (times the
+    // edge normal), plus the full edge of the input's own area.  Vertex v
+    // takes the start of edge v and the end of edge v - 1.
     float sx1[K], sy1[K], ex1[K], ey1[K], sx2[K], sy2[K], ex2[K], ey2[K];
 #pragma unroll
     for (int v = 0; v < K; ++v) {
-        const bool pa = (hasA >> v) & 1u, pb = (hasB >> v) & 1u;
-        const float I0a = pa ? 0.5f * ((1.f - t0[v]) * (1.f - t0[v]) - (1.f - t1[v]) * (1.f - t1[v])) : 0.f;
-        const float I1a = pa ? 0.5f * (t1[v] * t1[v] - t0[v] * t0[v]) : 0.f;
-        const float I0b = pb ? 0.5f * ((1.f - u0[v]) * (1.f - u0[v]) - (1.f - u1[v]) * (1.f - u1[v])) : 0.f;
-        const float I1b = pb ? 0.5f * (u1[v] * u1[v] - u0[v] * u0[v]) : 0.f;
-        const float wsa = gai * I0a + h1, wea = gai * I1a + h1;
-        const float wsb = gai * I0b + h2, web = gai * I1b + h2;
+        const float da = hg * (t1[v] - t0[v]), sa = t1[v] + t0[v];
+        const float db = hg * (u1[v] - u0[v]), sb = u1[v] + u0[v];
+        const float wsa = fmaf(da, 2.f - sa, h1), wea = fmaf(da, sa, h1);
+        const float wsb = fmaf(db, 2.f - sb, h2), web = fmaf(db, sb, h2);
         sx1[v] = wsa * g.eay[v];
         sy1[v] = -wsa * g.eax[v];
         ex1[v] = wea * g.eay[v];

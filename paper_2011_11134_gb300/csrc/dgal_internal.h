@@ -35,13 +35,24 @@ struct BatchedConfig {
 BatchedConfig batched_config(int K);
 void set_batched_config(int K, BatchedConfig c);
 
+// Launch shape of the paired kernels for quadrilaterals: below group_below
+// pairs a group of 8 lanes takes each pair (lower latency for small
+// batches), from there one lane per pair (fewer instructions per pair).
+struct PairedConfig {
+    int64_t group_below;
+};
+PairedConfig paired_config(int K);
+void set_paired_config(int K, PairedConfig c);
+
 // Launchers (no validation; called from the C ABI after checks).
+// n_shape: the batch size that picks the launch shape (default n; a chunk of
+// a larger batch passes the whole batch's size so that results match).
 dgal_status launch_paired_fwd(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
                               int K, float* iou, uint8_t* nx, uint8_t* xflags, uint8_t* degen, uint32_t flags,
-                              cudaStream_t s);
+                              cudaStream_t s, int64_t n_shape = -1);
 dgal_status launch_paired_bwd(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
                               int K, const float* grad, const uint8_t* nx, const uint8_t* xflags, float* g1,
-                              float* g2, uint32_t flags, cudaStream_t s);
+                              float* g2, uint32_t flags, cudaStream_t s, int64_t n_shape = -1);
 // K = 4: forward + backward in one pass (pointers may be device-mapped host memory).
 dgal_status launch_paired_fused(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
                                 int K, const float* grad, float* iou, float* g1, float* g2, uint32_t flags,
@@ -66,8 +77,27 @@ dgal_status launch_iou3d_loss(const float* p1, const uint8_t* c1, const float* z
                               const float* z2, int64_t n, int K, const float* weight, float scale, float* loss,
                               float* iou, float* g1, float* gz1, float* g2, float* gz2, void* ws, uint32_t flags,
                               cudaStream_t s);
-// One-block fixed-order sum of m per-warp loss partials into *out.
-void launch_sum_partials(const float* partials, int64_t m, float* out, cudaStream_t s);
+// One-block fixed-order sum of m per-warp loss partials (and of m2 more from
+// partials2 when it is not NULL) into *out.
+void launch_sum_partials(const float* partials, int64_t m, const float* partials2, int64_t m2, float* out,
+                         cudaStream_t s);
+// Backward of the IoU loss from the state a forward-only dgal_iou_loss left
+// in the workspace; dloss: device pointer to the loss's upstream gradient.
+dgal_status launch_iou_loss_backward(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                                     int K, const float* weight, float scale, const float* dloss, float* g1,
+                                     float* g2, void* ws, uint32_t flags, cudaStream_t s);
+dgal_status launch_iou3d_loss_backward(const float* p1, const uint8_t* c1, const float* z1, const float* p2,
+                                       const uint8_t* c2, const float* z2, int64_t n, int K, const float* weight,
+                                       float scale, const float* dloss, float* g1, float* gz1, float* g2, float* gz2,
+                                       void* ws, uint32_t flags, cudaStream_t s);
+// The GIoU (variant 1) / DIoU (variant 2) terms of the loss (loss_variants.cu).
+int64_t loss_var_partials(int64_t n);
+dgal_status launch_loss_var_fwd(int variant, const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2,
+                                int64_t n, int K, const float* weight, float scale, const float* u, float* ah,
+                                float* partials, cudaStream_t s);
+dgal_status launch_loss_var_bwd(int variant, const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2,
+                                int64_t n, int K, const float* weight, float scale, const float* dloss, const float* u,
+                                const float* ah, float* g1, float* g2, cudaStream_t s);
 dgal_status launch_batched(int S, const int64_t* a_off, const int64_t* b_off, const int64_t* out_off,
                            const float* a, const uint8_t* ca, const float* b, const uint8_t* cb, int K, float* iou,
                            uint8_t* nx, void* ws, uint32_t flags, const BatchedConfig& cfg, cudaStream_t s);

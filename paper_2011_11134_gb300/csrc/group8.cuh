@@ -75,6 +75,9 @@ struct Lane {
     int n1, n2, r;
 };
 
+// KIN: the capacity of the stored polygons (8, or 4 for quadrilaterals taken
+// by groups of 8 lanes; then lanes 4..7 hold padding and stay idle).
+template <int KIN = 8>
 __device__ __forceinline__ void load_lane(const float* __restrict__ p1, const float* __restrict__ p2, int n1, int n2,
                                           int r, Lane& L) {
     const float ox = __ldg(p1), oy = __ldg(p1 + 1);
@@ -87,7 +90,17 @@ __device__ __forceinline__ void load_lane(const float* __restrict__ p1, const fl
     L.eax = (w.x - ox) - L.ax;
     L.eay = (w.y - oy) - L.ay;
     float qx[8], qy[8];
-    load_poly<8>(p2, qx, qy);
+    if constexpr (KIN == 8) {
+        load_poly<8>(p2, qx, qy);
+    } else {
+        float ux[KIN], uy[KIN];
+        load_poly<KIN>(p2, ux, uy);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            qx[j] = ux[j < KIN ? j : 0];
+            qy[j] = uy[j < KIN ? j : 0];
+        }
+    }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         L.bx[j] = qx[j] - ox;
@@ -138,6 +151,22 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
     const int base = gbase();
     const int r = L.r, n1 = L.n1, n2 = L.n2;
     const bool liveA = r < n1, liveB = r < n2;
+    // Identical polygons (bit-equal vertices in the same order): by the
+    // candidate rules the intersection is P1 itself (every P1 vertex is on
+    // P2's boundary, P2's vertices are exact duplicates and no crossing is
+    // proper), so IoU = 1 and the codes are P1's vertices in order.  The pair
+    // is near-degenerate (its orientations vanish) and needs no test at all.
+    if (n1 == n2 && !gor32(gm, (liveA && (L.ax != L.bxr || L.ay != L.byr)) ? 1u : 0u)) {
+        const float a = 0.5f * gsum(gm, liveA ? L.ax * L.eay - L.ay * L.eax : 0.f);
+        const uint64_t seq = 0x0706050403020100ull;
+        out.w0 = n1 >= 8 ? seq : (seq | (~0ull << (8 * n1)));
+        out.w1 = ~0ull;
+        out.nx = (uint32_t)n1;
+        out.ai = out.a1 = out.a2 = a;
+        out.iou = a > 0.f ? 1.f : 0.f;
+        out.degen = 1u;
+        return true;
+    }
     float Lr = liveA ? fmaxf(fabsf(L.ax), fabsf(L.ay)) : 0.f;
 #pragma unroll
     for (int j = 0; j < 8; ++j) Lr = fmaxf(Lr, (j < n2) ? fmaxf(fabsf(L.bx[j]), fabsf(L.by[j])) : 0.f);
@@ -189,8 +218,17 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
     const uint32_t cnt = (uint32_t)(__popc(in1) + __popc(in2) + __popcll(X));
     out.nx = 0;
     out.iou = 0.f;
-    out.ai = out.a1 = out.a2 = 0.f;
+    out.ai = 0.f;
     out.w0 = out.w1 = ~0ull;
+    // the inputs' areas (kept for the union also when the intersection is empty)
+    const float c1r = L.ax * L.eay - L.ay * L.eax;
+    float s2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s2 += (j < n2) ? L.bx[j] * L.eby[j] - L.by[j] * L.ebx[j] : 0.f;
+    const float a1 = 0.5f * gsum(gm, liveA ? c1r : 0.f);
+    const float a2 = 0.5f * s2;
+    out.a1 = a1;
+    out.a2 = a2;
     if (cnt == 0u) return true;
     if (cnt < 3u || cnt > 16u) return false;
 
@@ -207,24 +245,20 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
     bad |= (cX & (cX - 1)) != 0ull || (cE & (cE - 1)) != 0ull;
     const uint32_t nxt1 = (in1 >> 1) | ((in1 & 1u) << (n1 - 1));
     const uint32_t nxt2 = (in2 >> 1) | ((in2 & 1u) << (n2 - 1));
-    const float c1r = L.ax * L.eay - L.ay * L.eax;
     const uint32_t xrow = liveA ? (uint32_t)((X >> (8 * r)) & 0xFF) : 0u;
     float lane2 = ((nxt1 >> r) & 1u && liveA) ? c1r : 0.f;
 #pragma unroll
     for (int j = 0; j < 8; ++j) lane2 += ((xrow >> j) & 1u) ? term[j] : 0.f;
-    float twoB = 0.f, s2 = 0.f;
+    float twoB = 0.f;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const float c2 = L.bx[j] * L.eby[j] - L.by[j] * L.ebx[j];
         twoB += ((nxt2 >> j) & 1u) ? c2 : 0.f;
-        s2 += (j < n2) ? c2 : 0.f;
     }
     const float twoA = gsum(gm, lane2) + twoB;
-    const float a1 = 0.5f * gsum(gm, liveA ? c1r : 0.f);
-    const float a2 = 0.5f * s2;
     const float ai = 0.5f * twoA;
     const float U = a1 + a2 - ai;
-    if (U < kThinRel * Lr * Lr) return false; // thin pair: FP64 areas on the warp path
+    if (U < kThinRel * Lr * Lr) return false; // thin pair: float-float areas on the warp path
 
     // chunk of the vertex order from P1 edge r
     uint64_t c_lo = 0, c_hi = 0;
@@ -331,7 +365,8 @@ __device__ __forceinline__ uint32_t bwd_group(const Lane& L, Adj& adj, uint32_t 
     const bool liveA = r < n1, liveB = r < n2;
     g1x = g1y = g2x = g2y = 0.f;
     if (nx > 16u) return kDevBadFlags;
-    if (nx < 3u) return 0u;
+    // fewer than three vertices: an empty intersection, no piece on any edge
+    const bool empty = nx < 3u;
     // decode slots r and r + 8 on lane r, then OR across the group
     uint32_t in1 = 0, in2 = 0, other = 0;
     uint64_t X = 0;
@@ -339,7 +374,7 @@ __device__ __forceinline__ uint32_t bwd_group(const Lane& L, Adj& adj, uint32_t 
     for (int h = 0; h < 2; ++h) {
         const uint32_t k = (uint32_t)r + 8u * h;
         const uint32_t c = (uint32_t)(((h ? w1 : w0) >> (8 * r)) & 0xFFull);
-        const bool live = k < nx;
+        const bool live = !empty && k < nx;
         const uint32_t kind = c >> 6, lo = c & 7u, ci = (c >> 3) & 7u;
         in1 |= (live && kind == 0u) ? (1u << (c & 0x1Fu)) : 0u;
         in2 |= (live && kind == 1u) ? (1u << (c & 0x1Fu)) : 0u;
@@ -355,7 +390,7 @@ __device__ __forceinline__ uint32_t bwd_group(const Lane& L, Adj& adj, uint32_t 
     const uint32_t rn1 = (r + 1 < n1) ? (uint32_t)(r + 1) : 0u, rn2 = (r + 1 < n2) ? (uint32_t)(r + 1) : 0u;
     const uint32_t rowX = liveA ? (uint32_t)((X >> (8 * r)) & 0xFF) : 0u;
     const uint64_t colX = liveB ? ((X >> r) & col0) : 0ull;
-    bool ok = (uint32_t)(__popc(in1) + __popc(in2) + __popcll(X)) == nx;
+    bool ok = empty || (uint32_t)(__popc(in1) + __popc(in2) + __popcll(X)) == nx;
     {
         const uint32_t ra = (uint32_t)__popc(rowX), a0 = (in1 >> r) & 1u, a1 = (in1 >> rn1) & 1u;
         ok &= !liveA || ((a0 ^ a1) ? ra == 1u : (a0 ? ra == 0u : (ra == 0u || ra == 2u)));
@@ -416,7 +451,7 @@ __device__ __forceinline__ uint32_t bwd_group(const Lane& L, Adj& adj, uint32_t 
 #pragma unroll
     for (int j = 0; j < 8; ++j) Lr = fmaxf(Lr, (j < n2) ? fmaxf(fabsf(L.bx[j]), fabsf(L.by[j])) : 0.f);
     Lr = gmax(gm, Lr);
-    if (refine && ai < kTinyArea * Lr * Lr) return kSlow;
+    if (refine && !empty && ai < kTinyArea * Lr * Lr) return kSlow;
     float gai, ga1, ga2;
     if (!adj(ai, a1, a2, gai, ga1, ga2)) return 0u;
     const float h1 = 0.5f * ga1, h2 = 0.5f * ga2;

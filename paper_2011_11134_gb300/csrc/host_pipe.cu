@@ -207,9 +207,9 @@ extern "C" dgal_status dgal_iou_fwd_bwd_host(const float* h_p1, const uint8_t* h
         // kernels: inputs arrived, and the slot's previous outputs were copied out
         PIPE_CUDA(cudaStreamWaitEvent(cs, P->ev_in[s], 0));
         if (c >= kSlots) PIPE_CUDA(cudaStreamWaitEvent(cs, P->ev_out[s], 0));
-        st = launch_paired_fwd(d_p1, d_c1, d_p2, d_c2, m, K, d_iou, d_nx, d_xf, nullptr, flags, cs);
+        st = launch_paired_fwd(d_p1, d_c1, d_p2, d_c2, m, K, d_iou, d_nx, d_xf, nullptr, flags, cs, n);
         if (st != DGAL_OK) return st;
-        st = launch_paired_bwd(d_p1, d_c1, d_p2, d_c2, m, K, d_grad, d_nx, d_xf, d_g1, d_g2, flags, cs);
+        st = launch_paired_bwd(d_p1, d_c1, d_p2, d_c2, m, K, d_grad, d_nx, d_xf, d_g1, d_g2, flags, cs, n);
         if (st != DGAL_OK) return st;
         PIPE_CUDA(cudaEventRecord(P->ev_done[s], cs));
         // outputs

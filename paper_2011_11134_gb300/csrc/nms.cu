@@ -231,7 +231,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
 __global__ void __launch_bounds__(kNmsGreedyThreads)
 k_nms_greedy(const __grid_constant__ CUtensorMap mask_map, const int32_t* __restrict__ order,
              const uint64_t* __restrict__ mask, const uint64_t* __restrict__ sup, int64_t N, int64_t W, int64_t Wp,
-             int64_t* __restrict__ keep, int64_t* __restrict__ num_keep, uint32_t* status) {
+             int64_t* __restrict__ keep, int64_t* __restrict__ num_keep, uint32_t* status, int64_t expire_at) {
     extern __shared__ unsigned char g_smem[];
     // stages on a 128-byte boundary (tiled loads); the launch adds 128 bytes for this
     unsigned char* base = g_smem + ((128u - (smem_addr(g_smem) & 127u)) & 127u);
@@ -275,9 +275,26 @@ k_nms_greedy(const __grid_constant__ CUtensorMap mask_map, const int32_t* __rest
     int64_t count = 0;
     for (int64_t c = 0; c < W; ++c) {
         // block c's copies landed; every thread waits so that it sees them
-        const bool ok = mbar_wait(&s_bar[c % kNmsStages], (unsigned)((c / kNmsStages) & 1));
+        const bool landed = mbar_wait(&s_bar[c % kNmsStages], (unsigned)((c / kNmsStages) & 1));
+        // expire_at (tests only): this block's wait is taken as expired once
+        // its copies have landed, to run the expiry path without a real stall
+        const bool ok = landed && c != expire_at;
         if (__syncthreads_or(!ok)) { // also: the removal words and the previous block are done
-            if (t == 0) atomicOr(status, kDevTimeout);
+            // Expiry: no copy may land in this block's shared memory after it
+            // exits, so the copies already issued (blocks c .. c + stages - 2)
+            // are waited for, each again within the bound, before the barriers
+            // are invalidated and the pass stops with DGAL_DEV_TIMEOUT.
+            const int64_t last = (c + kNmsStages - 2 < W - 1) ? c + kNmsStages - 2 : W - 1;
+            bool drained = true;
+            for (int64_t cc = c; cc <= last; ++cc)
+                drained &= mbar_wait(&s_bar[cc % kNmsStages], (unsigned)((cc / kNmsStages) & 1));
+            __syncthreads();
+            if (t == 0) {
+                if (drained)
+                    for (int i = 0; i < kNmsStages; ++i)
+                        asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_addr(&s_bar[i])) : "memory");
+                atomicOr(status, kDevTimeout);
+            }
             break;
         }
         issue(c + kNmsStages - 1); // into the stage the previous block used
@@ -413,8 +430,10 @@ static dgal_status launch_nms(const float* boxes, const uint8_t* counts, const f
     CUtensorMap map;
     st = nms_mask_map(&map, mask, N, Wp);
     if (st != DGAL_OK) return st;
+    // DGAL_TEST_EXPIRE_WAIT: the expiry path at the second block (or the first when there is one)
+    const int64_t expire_at = (flags & DGAL_TEST_EXPIRE_WAIT) ? (W > 1 ? 1 : 0) : -1;
     k_nms_greedy<<<1, kNmsGreedyThreads, smem, s>>>(map, order, mask, reinterpret_cast<const uint64_t*>(sup), N, W,
-                                                    Wp, keep, num_keep, device_status_ptr());
+                                                    Wp, keep, num_keep, device_status_ptr(), expire_at);
     return check_launch("nms greedy");
 }
 

@@ -36,53 +36,42 @@ __device__ __forceinline__ float block_sum(float v, float* sh) {
     return t;
 }
 
-// One block sums the m per-warp loss partials in a fixed order: thread t
-// takes float4 blocks t, t + 1024, ... (four loads in flight per round, each
-// block's values added in order), then the scalar tail, then a fixed tree.
-// The order does not depend on scheduling, so the loss is deterministic.
-// partials must be 16-byte aligned.
+// One block sums the m per-warp loss partials in a fixed order (then the m2
+// partials of the GIoU / DIoU terms, when given): fold_part's rounds over each
+// array, then a fixed tree.  The order does not depend on scheduling, so the
+// loss is deterministic.  The partials must be 16-byte aligned.
 constexpr int kSumThreads = 1024;
 
-__global__ void __launch_bounds__(kSumThreads) k_sum_partials(const float* __restrict__ partials, int m,
+__global__ void __launch_bounds__(kSumThreads) k_sum_partials(const float* __restrict__ partials, int64_t m,
+                                                               const float* __restrict__ partials2, int64_t m2,
                                                                float* __restrict__ out) {
     __shared__ float sh[32];
-    float v = 0.f;
-    const int m4 = m / 4;
-    const float4* p4 = reinterpret_cast<const float4*>(partials);
-    for (int base = 0; base < m4; base += 4 * kSumThreads) {
-        float4 a[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = base + u * kSumThreads + (int)threadIdx.x;
-            a[u] = (i < m4) ? __ldg(p4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) v += (a[u].x + a[u].y) + (a[u].z + a[u].w);
-    }
-    for (int i = 4 * m4 + (int)threadIdx.x; i < m; i += kSumThreads) v += partials[i];
+    float v = fold_part(partials, m);
+    if (partials2) v += fold_part(partials2, m2);
     const float t = block_sum(v, sh);
     if (threadIdx.x == 0) *out = t;
 }
 
-void launch_sum_partials(const float* partials, int64_t m, float* out, cudaStream_t s) {
-    k_sum_partials<<<1, kSumThreads, 0, s>>>(partials, (int)m, out);
+void launch_sum_partials(const float* partials, int64_t m, const float* partials2, int64_t m2, float* out,
+                         cudaStream_t s) {
+    k_sum_partials<<<1, kSumThreads, 0, s>>>(partials, m, partials2, m2, out);
 }
 
 dgal_status launch_paired_fwd(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
                               int K, float* iou, uint8_t* nx, uint8_t* xflags, uint8_t* degen, uint32_t flags,
-                              cudaStream_t s) {
+                              cudaStream_t s, int64_t n_shape) {
     if (!device_status_ptr()) return fail(DGAL_ERR_CUDA, "device status word unavailable");
     fwd_any<false, false>(p1, c1, p2, c2, n, K, iou, nx, xflags, degen, flags, s, LossArgs{nullptr, 0.f, nullptr},
-                          ZArgs{nullptr, nullptr, nullptr, nullptr});
+                          ZArgs{nullptr, nullptr, nullptr, nullptr}, n_shape);
     return check_launch("paired forward");
 }
 
 dgal_status launch_paired_bwd(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
                               int K, const float* grad, const uint8_t* nx, const uint8_t* xflags, float* g1,
-                              float* g2, uint32_t flags, cudaStream_t s) {
+                              float* g2, uint32_t flags, cudaStream_t s, int64_t n_shape) {
     if (!device_status_ptr()) return fail(DGAL_ERR_CUDA, "device status word unavailable");
     bwd_any<false, false>(p1, c1, p2, c2, n, K, grad, nx, xflags, g1, g2, flags, s, LossArgs{nullptr, 0.f, nullptr},
-                          ZArgs{nullptr, nullptr, nullptr, nullptr});
+                          ZArgs{nullptr, nullptr, nullptr, nullptr}, n_shape);
     return check_launch("paired backward");
 }
 
@@ -108,6 +97,14 @@ dgal_status launch_iou_loss(const float* p1, const uint8_t* c1, const float* p2,
     if (!device_status_ptr()) return fail(DGAL_ERR_CUDA, "device status word unavailable");
     return iou_loss_passes<false>(p1, c1, p2, c2, n, K, weight, scale, loss, iou, g1, g2,
                                   ZArgs{nullptr, nullptr, nullptr, nullptr}, ws, flags, s);
+}
+
+dgal_status launch_iou_loss_backward(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
+                                     int K, const float* weight, float scale, const float* dloss, float* g1,
+                                     float* g2, void* ws, uint32_t flags, cudaStream_t s) {
+    if (!device_status_ptr()) return fail(DGAL_ERR_CUDA, "device status word unavailable");
+    return iou_loss_backward<false>(p1, c1, p2, c2, n, K, weight, scale, dloss, nullptr, g1, g2,
+                                    ZArgs{nullptr, nullptr, nullptr, nullptr}, ws, flags, s);
 }
 
 } // namespace dgal

@@ -39,4 +39,13 @@ dgal_status launch_iou3d_loss(const float* p1, const uint8_t* c1, const float* z
                                  flags, s);
 }
 
+dgal_status launch_iou3d_loss_backward(const float* p1, const uint8_t* c1, const float* z1, const float* p2,
+                                       const uint8_t* c2, const float* z2, int64_t n, int K, const float* weight,
+                                       float scale, const float* dloss, float* g1, float* gz1, float* g2, float* gz2,
+                                       void* ws, uint32_t flags, cudaStream_t s) {
+    if (!device_status_ptr()) return fail(DGAL_ERR_CUDA, "device status word unavailable");
+    return iou_loss_backward<true>(p1, c1, p2, c2, n, K, weight, scale, dloss, nullptr, g1, g2,
+                                   ZArgs{z1, z2, gz1, gz2}, ws, flags, s);
+}
+
 } // namespace dgal

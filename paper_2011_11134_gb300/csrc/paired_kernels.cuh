@@ -50,7 +50,7 @@ template <int K> __device__ __forceinline__ void store_poly(float* __restrict__ 
 // a pair the fast path cannot finish (near-degenerate or not in general
 // position, well under 0.1% of random boxes) is finished right after the
 // step by the whole warp (warp_robust, a non-inlined call, so its registers
-// and FP64 code stay off the common path); the SM keeps issuing from its other
+// and slow-path code stay off the common path); the SM keeps issuing from its other
 // warps meanwhile.  In the backward, a pair whose codes the shape derivative
 // cannot take (not in general position, or with refinement a tiny
 // intersection) takes the shoelace adjoint after the rest, with the whole
@@ -58,15 +58,28 @@ template <int K> __device__ __forceinline__ void store_poly(float* __restrict__ 
 
 // IoU-loss mode of the paired kernels (paper Sec. IV-A, the IoU loss over
 // rotated boxes): the forward adds scale * w_k (1 - IoU_k) into one partial
-// per warp, and the backward takes dL/dIoU_k = -scale * w_k (w = 1 when
-// weight is NULL) instead of reading an upstream gradient.
+// per warp, and the backward takes dL/dIoU_k = -scale * w_k * dloss (w = 1
+// when weight is NULL, dloss = 1 when NULL) instead of reading an upstream
+// gradient.  For the GIoU loss the forward also keeps each pair's union U and
+// the backward adds scale * w_k * dloss / A_h to dL/dA_i and subtracts it from
+// dL/dA_1, dL/dA_2 (A_h the pair's hull area, from the GIoU pass).
 struct LossArgs {
     const float* weight;
     float scale;
-    float* partials; // one float per warp of the forward grid
-    float* loss;     // backward: block 0 writes the sum of the partials here (NULL: not in this launch)
-    int64_t nparts;  // number of partials
+    float* partials;        // one float per warp of the forward grid
+    float* loss;            // backward: block 0 writes the sum of the partials here (NULL: not in this launch)
+    int64_t nparts;         // number of partials
+    float* u_out;           // forward, GIoU: U = A_1 + A_2 - A_i per pair (NULL: not kept)
+    const float* ah;        // backward, GIoU: hull area per pair (NULL: plain IoU loss)
+    const float* partials2; // backward: partials of the GIoU / DIoU terms, folded after the first (or NULL)
+    int64_t nparts2;
+    const float* dloss;     // backward: device pointer to the upstream gradient of the loss (NULL: 1)
 };
+
+// dL/dIoU_k of the loss-mode backward.
+__device__ __forceinline__ float loss_dl(const LossArgs& la, float w) {
+    return -la.scale * w * (la.dloss ? __ldg(la.dloss) : 1.f);
+}
 
 // 3D mode of the paired kernels: each box also has a vertical extent
 // (z_center, height) in z1 / z2 (float [n][2]); the forward gives the 3D IoU
@@ -93,6 +106,8 @@ template <bool Z3> __device__ __forceinline__ typename AdjOf<Z3>::T adj_of(float
         a.z = z_of(za, k);
         a.hit = false;
         a.ai = a.a1 = a.a2 = 0.f;
+    } else {
+        a.e = 0.f;
     }
     return a;
 }
@@ -111,6 +126,23 @@ __device__ __forceinline__ float loss_weight(const LossArgs& la, int64_t k) {
     return la.weight ? __ldg(la.weight + k) : 1.f;
 }
 
+// The adjoint policy of pair k in a backward: dL/dIoU read from grad, or in
+// loss mode formed from the weights (plus the GIoU term when la.ah is set).
+template <bool LOSS, bool Z3>
+__device__ __forceinline__ typename AdjOf<Z3>::T make_adj(const LossArgs& la, const float* __restrict__ grad,
+                                                          const ZArgs& za, int64_t k) {
+    if constexpr (LOSS) {
+        const float g = loss_dl(la, loss_weight(la, k));
+        auto a = adj_of<Z3>(g, za, k);
+        if constexpr (!Z3) {
+            if (la.ah) a.e = -g / __ldg(la.ah + k);
+        }
+        return a;
+    } else {
+        return adj_of<Z3>(__ldg(grad + k), za, k);
+    }
+}
+
 __device__ __forceinline__ void put_partial(const LossArgs& la, float acc) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
@@ -124,11 +156,10 @@ __device__ __forceinline__ void put_partial(const LossArgs& la, float acc) {
 // does not depend on scheduling, so the loss is deterministic, and the sum
 // needs no launch of its own: the other blocks go straight to their pairs.
 // partials must be 16-byte aligned.  Block-uniform (it has block barriers).
-__device__ __forceinline__ void loss_fold(const LossArgs& la) {
-    if (!la.loss || blockIdx.x != 0) return;
-    __shared__ float sh[32];
-    const int64_t m = la.nparts, m4 = m / 4, step = blockDim.x;
-    const float4* p4 = reinterpret_cast<const float4*>(la.partials);
+// Thread-level part of the fixed-order sum of m partials (16-byte aligned).
+__device__ __forceinline__ float fold_part(const float* __restrict__ partials, int64_t m) {
+    const int64_t m4 = m / 4, step = blockDim.x;
+    const float4* p4 = reinterpret_cast<const float4*>(partials);
     float v = 0.f;
     for (int64_t base = 0; base < m4; base += 4 * step) {
         float4 a[4];
@@ -140,7 +171,15 @@ __device__ __forceinline__ void loss_fold(const LossArgs& la) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) v += (a[u].x + a[u].y) + (a[u].z + a[u].w);
     }
-    for (int64_t i = 4 * m4 + threadIdx.x; i < m; i += step) v += la.partials[i];
+    for (int64_t i = 4 * m4 + threadIdx.x; i < m; i += step) v += partials[i];
+    return v;
+}
+
+__device__ __forceinline__ void loss_fold(const LossArgs& la) {
+    if (!la.loss || blockIdx.x != 0) return;
+    __shared__ float sh[32];
+    float v = fold_part(la.partials, la.nparts);
+    if (la.partials2) v += fold_part(la.partials2, la.nparts2);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -159,7 +198,10 @@ template <int K, bool SAVE, bool LOSS>
 __device__ __forceinline__ void put_fwd(const FwdOut<K>& o, int64_t k, float w, const LossArgs& la,
                                         float* __restrict__ iou, uint8_t* __restrict__ nx,
                                         uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, float& acc) {
-    if (LOSS) acc += la.scale * w * (1.f - o.iou);
+    if (LOSS) {
+        acc += la.scale * w * (1.f - o.iou);
+        if (la.u_out) la.u_out[k] = o.a1 + o.a2 - (o.nx >= 3u ? o.ai : 0.f);
+    }
     if (!LOSS || iou) iou[k] = o.iou;
     if (SAVE) {
         nx[k] = (uint8_t)o.nx;
@@ -205,6 +247,7 @@ k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
                 err |= kDevBadCount;
                 o.nx = 0;
                 o.iou = 0.f;
+                o.ai = o.a1 = o.a2 = 0.f;
                 o.degen = 0;
                 codes_fill<K>(o.codes, ~0ull);
             } else {
@@ -217,7 +260,7 @@ k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
                 o.degen = 0;
                 hard = refine ? !fwd_generic<K, COUNTS>(g, o, p1 + k * 2 * K, p2 + k * 2 * K)
                               : !fwd_generic<K, COUNTS>(g, o);
-                // thin pairs: FP64 areas on the warp path (kThinRel)
+                // thin pairs: float-float areas on the warp path (kThinRel)
                 hard = hard || (o.nx >= 3u && o.a1 + o.a2 - o.ai < kThinRel * o.L2);
                 if (!hard) {
                     if constexpr (Z3) {
@@ -277,7 +320,7 @@ k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
                 n2 = c2 ? (int)c2[k] : K;
             }
             float g1x[K], g1y[K], g2x[K], g2y[K];
-            auto adj = adj_of<Z3>(LOSS ? -la.scale * loss_weight(la, k) : __ldg(grad + k), za, k);
+            auto adj = make_adj<LOSS, Z3>(la, grad, za, k);
             if (COUNTS && (n1 < 3 || n1 > K || n2 < 3 || n2 > K)) {
                 err |= kDevBadCount;
 #pragma unroll
@@ -338,8 +381,8 @@ k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
             Codes<K> cs;
 #pragma unroll
             for (int q = 0; q < (2 * K + 7) / 8; ++q) cs.w[q] = __shfl_sync(full, codes.w[q], src);
-            auto a = adj_of<Z3>(LOSS ? -la.scale * loss_weight(la, kk) : __ldg(grad + kk), za, kk);
-            const uint32_t e = refine ? warp_bwd<K, double>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, a, mnx, cs,
+            auto a = make_adj<LOSS, Z3>(la, grad, za, kk);
+            const uint32_t e = refine ? warp_bwd<K, ff>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, a, mnx, cs,
                                                             g1 + kk * 2 * K, g2 + kk * 2 * K, s_bwd[threadIdx.x >> 5])
                                       : warp_bwd<K, float>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, a, mnx, cs,
                                                            g1 + kk * 2 * K, g2 + kk * 2 * K, s_bwd[threadIdx.x >> 5]);
@@ -447,7 +490,7 @@ k_paired_fused(const float* __restrict__ p1, const uint8_t* __restrict__ c1, con
 #pragma unroll
             for (int q = 0; q < (2 * K + 7) / 8; ++q) cs.w[q] = __shfl_sync(full, o.codes.w[q], src);
             auto a = adj_of<false>(grad[kk], za, kk);
-            const uint32_t e = refine ? warp_bwd<K, double>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, a, mnx, cs,
+            const uint32_t e = refine ? warp_bwd<K, ff>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, a, mnx, cs,
                                                             g1 + kk * 2 * K, g2 + kk * 2 * K, s_bwd[threadIdx.x >> 5])
                                       : warp_bwd<K, float>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, a, mnx, cs,
                                                            g1 + kk * 2 * K, g2 + kk * 2 * K, s_bwd[threadIdx.x >> 5]);
@@ -460,7 +503,11 @@ k_paired_fused(const float* __restrict__ p1, const uint8_t* __restrict__ c1, con
 // K = 8: one group of 8 lanes per pair (group8.cuh), 4 pairs per warp and
 // step, grid-stride over warps.  Pairs the group cannot finish are done by the
 // whole warp (forward) or by the group's first lane (backward) afterwards.
-template <bool SAVE, bool LOSS, bool Z3>
+// DEFER: a pair the group hands back is marked (its IoU written as NaN) and
+// left to k_paired_fwd_finish, instead of being finished here by the warp.
+// KIN: the capacity of the stored polygons (8; or 4, quadrilaterals spread
+// over 8 lanes to cut the latency of small batches).
+template <bool SAVE, bool LOSS, bool Z3, bool DEFER = false, int KIN = 8>
 __global__ void __launch_bounds__(kPairThreads)
 k_paired_fwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
                 const uint8_t* __restrict__ c2, int64_t n, float* __restrict__ iou, uint8_t* __restrict__ nx,
@@ -475,52 +522,66 @@ k_paired_fwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
     for (int64_t base = warp * 4; base < n; base += stride) {
         const int64_t k = base + (lane >> 3);
         const bool act = k < n;
-        const int n1 = (act && c1) ? (int)c1[k] : 8, n2 = (act && c2) ? (int)c2[k] : 8;
-        const bool good = act && n1 >= 3 && n1 <= 8 && n2 >= 3 && n2 <= 8;
+        const int n1 = (act && c1) ? (int)c1[k] : KIN, n2 = (act && c2) ? (int)c2[k] : KIN;
+        const bool good = act && n1 >= 3 && n1 <= KIN && n2 >= 3 && n2 <= KIN;
         bool hard = false;
         const float w = (LOSS && act && r == 0) ? loss_weight(la, k) : 0.f;
         if (good) {
             g8::Lane L;
-            g8::load_lane(p1 + k * 16, p2 + k * 16, n1, n2, r, L);
+            g8::load_lane<KIN>(p1 + k * 2 * KIN, p2 + k * 2 * KIN, n1, n2, r, L);
             g8::FwdG o;
             hard = !g8::fwd_group(L, o);
             if constexpr (Z3) {
                 if (!hard && r == 0) o.iou = iou3_value(o.ai, o.a1, o.a2, o.nx, z_of(za, k));
             }
             if (!hard && r == 0) {
-                if (LOSS) acc += la.scale * w * (1.f - o.iou);
+                if (LOSS) {
+                    acc += la.scale * w * (1.f - o.iou);
+                    if (la.u_out) la.u_out[k] = o.a1 + o.a2 - (o.nx >= 3u ? o.ai : 0.f);
+                }
                 if (!LOSS || iou) iou[k] = o.iou;
                 if (SAVE) {
                     nx[k] = (uint8_t)o.nx;
-                    reinterpret_cast<uint4*>(xflags)[k] =
-                        make_uint4((uint32_t)o.w0, (uint32_t)(o.w0 >> 32), (uint32_t)o.w1, (uint32_t)(o.w1 >> 32));
+                    if constexpr (KIN == 8)
+                        reinterpret_cast<uint4*>(xflags)[k] =
+                            make_uint4((uint32_t)o.w0, (uint32_t)(o.w0 >> 32), (uint32_t)o.w1, (uint32_t)(o.w1 >> 32));
+                    else
+                        reinterpret_cast<uint64_t*>(xflags)[k] = o.w0;
                 }
                 if (degen) degen[k] = (uint8_t)o.degen;
             }
         } else if (act && r == 0) {
             err |= kDevBadCount;
-            if (LOSS) acc += la.scale * w;
+            if (LOSS) {
+                acc += la.scale * w;
+                if (la.u_out) la.u_out[k] = 0.f;
+            }
             if (!LOSS || iou) iou[k] = 0.f;
             if (SAVE) {
                 nx[k] = 0;
-                reinterpret_cast<uint4*>(xflags)[k] = make_uint4(~0u, ~0u, ~0u, ~0u);
+                if constexpr (KIN == 8) reinterpret_cast<uint4*>(xflags)[k] = make_uint4(~0u, ~0u, ~0u, ~0u);
+                else reinterpret_cast<uint64_t*>(xflags)[k] = ~0ull;
             }
             if (degen) degen[k] = 0;
         }
-        // pairs the group hands back: finished by the whole warp, one at a time
-        unsigned todo = __ballot_sync(0xffffffffu, hard && r == 0);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int64_t kk = base + (src >> 3);
-            const int m1 = __shfl_sync(0xffffffffu, n1, src), m2 = __shfl_sync(0xffffffffu, n2, src);
-            FwdOut<8> o;
-            o.err = 0;
-            warp_robust<8>(p1 + kk * 16, p2 + kk * 16, m1, m2, refine, o);
-            if (lane == src) {
-                if constexpr (Z3) o.iou = iou3_value(o.ai, o.a1, o.a2, o.nx, z_of(za, kk));
-                err |= o.err;
-                put_fwd<8, SAVE, LOSS>(o, kk, w, la, iou, nx, xflags, degen, acc);
+        if constexpr (DEFER) {
+            if (hard && r == 0) iou[k] = __int_as_float(0x7fffffff);
+        } else {
+            // pairs the group hands back: finished by the whole warp, one at a time
+            unsigned todo = __ballot_sync(0xffffffffu, hard && r == 0);
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int64_t kk = base + (src >> 3);
+                const int m1 = __shfl_sync(0xffffffffu, n1, src), m2 = __shfl_sync(0xffffffffu, n2, src);
+                FwdOut<KIN> o;
+                o.err = 0;
+                warp_robust<KIN>(p1 + kk * 2 * KIN, p2 + kk * 2 * KIN, m1, m2, refine, o);
+                if (lane == src) {
+                    if constexpr (Z3) o.iou = iou3_value(o.ai, o.a1, o.a2, o.nx, z_of(za, kk));
+                    err |= o.err;
+                    put_fwd<KIN, SAVE, LOSS>(o, kk, w, la, iou, nx, xflags, degen, acc);
+                }
             }
         }
     }
@@ -528,7 +589,48 @@ k_paired_fwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
     if (err) atomicOr(status, err);
 }
 
-template <bool RECOMPUTE, bool LOSS, bool Z3>
+// The pairs a deferring forward handed back (IoU marked NaN), finished by
+// whole warps in a launch of their own: every warp of this kernel runs the
+// warp-cooperative path only, so the SM holds as many of them as its
+// registers allow and their long dependent chains overlap.  Warp w scans 32
+// IoU values per step (one coalesced load), then takes the marked pairs one
+// at a time.  A NaN IoU from NaN inputs is recomputed here too (as NaN).
+template <int K, bool SAVE, bool Z3>
+__global__ void __launch_bounds__(kPairThreads)
+k_paired_fwd_finish(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
+                    const uint8_t* __restrict__ c2, int64_t n, float* __restrict__ iou, uint8_t* __restrict__ nx,
+                    uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status,
+                    ZArgs za) {
+    constexpr unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
+    const int64_t stride = (int64_t)gridDim.x * kPairThreads;
+    const LossArgs la{nullptr, 0.f, nullptr, nullptr, 0};
+    uint32_t err = 0;
+    float acc = 0.f;
+    for (int64_t base = (int64_t)blockIdx.x * kPairThreads + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t k = base + lane;
+        const bool mark = k < n && isnan(iou[k]);
+        unsigned todo = __ballot_sync(full, mark);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t kk = base + src;
+            const int m1 = c1 ? (int)c1[kk] : K, m2 = c2 ? (int)c2[kk] : K;
+            FwdOut<K> o;
+            o.err = 0;
+            warp_robust<K>(p1 + kk * 2 * K, p2 + kk * 2 * K, m1, m2, refine, o);
+            if (lane == src) {
+                if constexpr (Z3) o.iou = iou3_value(o.ai, o.a1, o.a2, o.nx, z_of(za, kk));
+                err |= o.err;
+                put_fwd<K, SAVE, false>(o, kk, 0.f, la, iou, nx, xflags, degen, acc);
+            }
+        }
+    }
+    if (err) atomicOr(status, err);
+}
+
+template <bool RECOMPUTE, bool LOSS, bool Z3, int KIN = 8>
 __global__ void __launch_bounds__(kPairThreads)
 k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
                 const uint8_t* __restrict__ c2, int64_t n, const float* __restrict__ grad,
@@ -545,15 +647,15 @@ k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
     for (int64_t base = warp * 4; base < n; base += stride) {
         const int64_t k = base + (lane >> 3);
         const bool act = k < n;
-        const int n1 = (act && c1) ? (int)c1[k] : 8, n2 = (act && c2) ? (int)c2[k] : 8;
-        const bool good = act && n1 >= 3 && n1 <= 8 && n2 >= 3 && n2 <= 8;
+        const int n1 = (act && c1) ? (int)c1[k] : KIN, n2 = (act && c2) ? (int)c2[k] : KIN;
+        const bool good = act && n1 >= 3 && n1 <= KIN && n2 >= 3 && n2 <= KIN;
         bool slow = false, needfwd = false;
         uint64_t w0 = ~0ull, w1 = ~0ull;
         uint32_t nxk = 0;
         float gx1 = 0.f, gy1 = 0.f, gx2 = 0.f, gy2 = 0.f;
         if (good) {
             g8::Lane L;
-            g8::load_lane(p1 + k * 16, p2 + k * 16, n1, n2, r, L);
+            g8::load_lane<KIN>(p1 + k * 2 * KIN, p2 + k * 2 * KIN, n1, n2, r, L);
             if (RECOMPUTE) {
                 g8::FwdG o;
                 needfwd = !g8::fwd_group(L, o);
@@ -561,13 +663,17 @@ k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
                 w1 = o.w1;
                 nxk = o.nx;
             } else {
-                const uint4 u = __ldg(reinterpret_cast<const uint4*>(xflags) + k);
-                w0 = (uint64_t)u.x | ((uint64_t)u.y << 32);
-                w1 = (uint64_t)u.z | ((uint64_t)u.w << 32);
+                if constexpr (KIN == 8) {
+                    const uint4 u = __ldg(reinterpret_cast<const uint4*>(xflags) + k);
+                    w0 = (uint64_t)u.x | ((uint64_t)u.y << 32);
+                    w1 = (uint64_t)u.z | ((uint64_t)u.w << 32);
+                } else {
+                    w0 = __ldg(reinterpret_cast<const unsigned long long*>(xflags) + k);
+                }
                 nxk = nxs[k];
             }
             uint32_t e = kSlow;
-            auto adj = adj_of<Z3>(LOSS ? -la.scale * loss_weight(la, k) : __ldg(grad + k), za, k);
+            auto adj = make_adj<LOSS, Z3>(la, grad, za, k);
             if (!needfwd) e = g8::bwd_group(L, adj, nxk, w0, w1, refine, gx1, gy1, gx2, gy2);
             slow = e == kSlow;
             if (!slow) {
@@ -575,16 +681,20 @@ k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
                     err |= e;
                     put_zgrad<Z3>(za, k, adj);
                 }
-                reinterpret_cast<float2*>(g1)[k * 8 + r] = make_float2(gx1, gy1);
-                reinterpret_cast<float2*>(g2)[k * 8 + r] = make_float2(gx2, gy2);
+                if (r < KIN) {
+                    reinterpret_cast<float2*>(g1)[k * KIN + r] = make_float2(gx1, gy1);
+                    reinterpret_cast<float2*>(g2)[k * KIN + r] = make_float2(gx2, gy2);
+                }
             }
         } else if (act) {
             if (r == 0) {
                 err |= kDevBadCount;
                 put_zgrad<Z3>(za, k, adj_of<Z3>(0.f, za, k));
             }
-            reinterpret_cast<float2*>(g1)[k * 8 + r] = make_float2(0.f, 0.f);
-            reinterpret_cast<float2*>(g2)[k * 8 + r] = make_float2(0.f, 0.f);
+            if (r < KIN) {
+                reinterpret_cast<float2*>(g1)[k * KIN + r] = make_float2(0.f, 0.f);
+                reinterpret_cast<float2*>(g2)[k * KIN + r] = make_float2(0.f, 0.f);
+            }
         }
         if (RECOMPUTE) {
             unsigned todo = __ballot_sync(full, needfwd && r == 0);
@@ -593,13 +703,13 @@ k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
                 todo &= todo - 1;
                 const int64_t kk = base + (src >> 3);
                 const int m1 = __shfl_sync(full, n1, src), m2 = __shfl_sync(full, n2, src);
-                FwdOut<8> o;
+                FwdOut<KIN> o;
                 o.err = 0;
-                warp_robust<8>(p1 + kk * 16, p2 + kk * 16, m1, m2, refine, o);
+                warp_robust<KIN>(p1 + kk * 2 * KIN, p2 + kk * 2 * KIN, m1, m2, refine, o);
                 if (lane == src) {
                     err |= o.err;
                     w0 = o.codes.w[0];
-                    w1 = o.codes.w[1];
+                    if constexpr (KIN == 8) w1 = o.codes.w[1];
                     nxk = o.nx;
                 }
             }
@@ -611,14 +721,15 @@ k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
             const int64_t kk = base + (src >> 3);
             const int m1 = __shfl_sync(full, n1, src), m2 = __shfl_sync(full, n2, src);
             const uint32_t mnx = __shfl_sync(full, nxk, src);
-            Codes<8> cs;
+            Codes<KIN> cs;
             cs.w[0] = __shfl_sync(full, w0, src);
-            cs.w[1] = __shfl_sync(full, w1, src);
-            auto a = adj_of<Z3>(LOSS ? -la.scale * loss_weight(la, kk) : __ldg(grad + kk), za, kk);
-            const uint32_t e = refine ? warp_bwd<8, double>(p1 + kk * 16, p2 + kk * 16, m1, m2, a, mnx, cs, g1 + kk * 16,
-                                                            g2 + kk * 16, s_bwd[threadIdx.x >> 5])
-                                      : warp_bwd<8, float>(p1 + kk * 16, p2 + kk * 16, m1, m2, a, mnx, cs, g1 + kk * 16,
-                                                           g2 + kk * 16, s_bwd[threadIdx.x >> 5]);
+            if constexpr (KIN == 8) cs.w[1] = __shfl_sync(full, w1, src);
+            auto a = make_adj<LOSS, Z3>(la, grad, za, kk);
+            const int64_t o2 = kk * 2 * KIN;
+            const uint32_t e = refine ? warp_bwd<KIN, ff>(p1 + o2, p2 + o2, m1, m2, a, mnx, cs, g1 + o2, g2 + o2,
+                                                          s_bwd[threadIdx.x >> 5])
+                                      : warp_bwd<KIN, float>(p1 + o2, p2 + o2, m1, m2, a, mnx, cs, g1 + o2, g2 + o2,
+                                                             s_bwd[threadIdx.x >> 5]);
             if (lane == src) {
                 err |= e;
                 put_zgrad<Z3>(za, kk, a);

@@ -48,7 +48,7 @@ __device__ __forceinline__ bool pw_fast(const float* __restrict__ pa, const floa
     input_areas<K, COUNTS>(g, o.a1, o.a2);
     if (!(refine ? fwd_generic<K, COUNTS>(g, o, pa, pb) : fwd_generic<K, COUNTS>(g, o))) return true;
     const float U = o.a1 + o.a2 - o.ai;
-    if (o.nx >= 3u && U < kThinRel * o.L2) return true; // thin pair: FP64 areas on the warp path
+    if (o.nx >= 3u && U < kThinRel * o.L2) return true; // thin pair: float-float areas on the warp path
     nxo = o.nx;
     iou = (o.nx >= 3u && U > 0.f) ? o.ai / U : 0.f;
     return false;

@@ -12,6 +12,10 @@ from .gpu_helpers import GRAD_RTOL, IOU_ATOL, THREADS, dev, grad_rel_err, host
 
 pytestmark = pytest.mark.gpu
 
+# quadrilateral batches below this many pairs take 8-lane groups on the device
+# (the untuned default of the library's paired launch shape)
+GROUP_BELOW = 16384
+
 
 @pytest.fixture(scope="module")
 def dg():
@@ -44,8 +48,15 @@ def test_host_pipeline_matches_device_path(dg, n, chunk, pinned):
     ri, rnx, rxf, _ = dg.dgal_iou_paired(p1, p2)
     r1, r2 = dg.dgal_iou_backward(p1, p2, gd, rnx, rxf)
     torch.cuda.synchronize()
-    assert np.array_equal(iou.numpy(), host(ri))
-    assert np.array_equal(g1.numpy(), host(r1)) and np.array_equal(g2.numpy(), host(r2))
+    if n >= GROUP_BELOW or not pinned:
+        assert np.array_equal(iou.numpy(), host(ri))
+        assert np.array_equal(g1.numpy(), host(r1)) and np.array_equal(g2.numpy(), host(r2))
+    else:
+        # a batch this small takes 8-lane groups on the device and one lane
+        # per pair in the host-resident kernel: equal up to rounding
+        assert np.abs(iou.numpy() - host(ri)).max() <= 1e-6
+        m = max(np.abs(host(r1)).max(), np.abs(host(r2)).max(), 1e-30)
+        assert np.abs(g1.numpy() - host(r1)).max() <= 1e-5 * m and np.abs(g2.numpy() - host(r2)).max() <= 1e-5 * m
     assert dg.dgal_get_device_status() == 0
 
 

@@ -135,3 +135,29 @@ def test_nms_nan_scores_and_extremes(dg, orc):
     empty = torch.empty((0, 4, 2), device="cuda", dtype=torch.float32)
     assert dg.dgal_nms_rotated(empty, torch.empty(0, device="cuda"), 0.5).numel() == 0
     assert dg.dgal_get_device_status() == 0
+
+
+def test_nms_wait_expiry_path(dg):
+    """The greedy pass's bounded-wait failure path, reached without stalling
+    anything: the test flag takes it at the second block once that block's
+    copies have landed.  The call returns, the status word holds
+    DGAL_DEV_TIMEOUT, the kept list stops after the first block (a prefix of
+    the full result), and the next call on the same context gives the full
+    result (the pass waited for its copies in flight before it stopped)."""
+    import torch
+
+    d = W.pairwise_bev_2000(seed=0)
+    a = dev(d["a"])
+    scores = torch.from_numpy(np.random.default_rng(0).uniform(0, 1, a.shape[0]).astype(np.float32)).cuda()
+    full = dg.dgal_nms_rotated(a, scores, 0.2)
+    dg.dgal_get_device_status(clear=True)
+    keep, num = dg.dgal_nms_rotated(a, scores, 0.2, flags=dg.DGAL_FP64_REFINE | dg.DGAL_TEST_EXPIRE_WAIT,
+                                    sync=False)
+    torch.cuda.synchronize()
+    assert dg.dgal_get_device_status(clear=True) & dg.DGAL_DEV_TIMEOUT
+    m = int(num.item())
+    assert 0 < m <= 64 and m < full.numel()
+    assert torch.equal(keep[:m], full[:m])
+    again = dg.dgal_nms_rotated(a, scores, 0.2)
+    assert torch.equal(again, full)
+    assert dg.dgal_get_device_status() == 0

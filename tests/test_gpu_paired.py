@@ -159,7 +159,8 @@ def test_convex_k8_with_degenerate(dg, orc):
     kind = d["kind"]
     hd = host(degen)
     assert (hd[kind > 0] & 1).all(), "every constructed degenerate pair is flagged"
-    assert (hd[kind > 0] & 2).all(), "and refined in FP64"
+    # identical pairs are recognised as such; the others take FP64 orientations
+    assert (hd[kind > 1] & 2).all(), "and refined in FP64"
     grad = torch.ones(p1.shape[0], device="cuda")
     g1, g2 = dg.dgal_iou_backward(p1, p2, grad, nx, xf, c1, c2)
     o1, o2 = orc.iou_backward_paired(d["p1"], d["p2"], np.ones(p1.shape[0]), ref["nx"], ref["xflags"], d["c1"],
@@ -333,3 +334,46 @@ def test_recompute_chosen_by_flag_budget(dg, monkeypatch):
     # the environment variable sets the default budget
     monkeypatch.setenv("DGAL_FLAG_BUDGET_BYTES", "1")
     assert dg.iou(dev(d["p1"]).requires_grad_(True), dev(d["p2"])).grad_fn.recompute is True
+
+
+def test_paired_launch_shapes_and_tuner(dg, orc, tmp_path):
+    """Both launch shapes of the paired calls (a group of 8 lanes per pair,
+    one lane per pair) match the oracle at sizes on either side of the
+    threshold, whichever shape the threshold picks; the tuner caches the
+    threshold it measures."""
+    import torch
+
+    key_dev = None
+    for below, sizes in ((1 << 40, (1000, 50_000)), (0, (1000, 50_000))):
+        path = tmp_path / f"shape{below}.json"
+        if key_dev is None:
+            dg.dgal_autotune(4, cache_path=path, config_class=1)
+            key_dev = path.read_text().split('"')[1]
+            assert key_dev.endswith("|paired")
+        path.write_text('{\n  "%s": [%d, 0, 0]\n}\n' % (key_dev, below))
+        assert dg.dgal_autotune(4, cache_path=path, config_class=1)["group_below"] == below
+        for n in sizes:
+            d = W.loss_pairs_1m(seed=31, n=n)
+            p1, p2 = dev(d["p1"]), dev(d["p2"])
+            iou, nx, xf, degen = dg.dgal_iou_paired(p1, p2, with_degen=True)
+            ref = orc.iou_paired(d["p1"], d["p2"], threads=THREADS)
+            gen = check_forward(host(iou), host(nx), host(xf), host(degen), ref, f"shape below={below} n={n}")
+            grad = torch.linspace(-1, 1, n, device="cuda")
+            g1, g2 = dg.dgal_iou_backward(p1, p2, grad, nx, xf)
+            r1, r2 = orc.iou_backward_paired(d["p1"], d["p2"], host(grad).astype(np.float64), ref["nx"], ref["xflags"],
+                                             threads=THREADS)
+            rel = grad_rel_err(host(g1), host(g2), r1, r2, gen)
+            assert rel.max() <= GRAD_RTOL, f"below={below} n={n}: {rel.max():.3e}"
+            # recompute mode on the same shape
+            h1, h2 = dg.dgal_iou_backward(p1, p2, grad)
+            m = max(g1.abs().max().item(), g2.abs().max().item())
+            assert (h1 - g1).abs().max().item() <= 1e-5 * m
+    # a fresh tuning (no cache) leaves a threshold in use
+    cfg = dg.dgal_autotune(4, cache_path=tmp_path / "fresh.json", config_class=1)
+    assert cfg["group_below"] >= 0
+    assert "|paired" in (tmp_path / "fresh.json").read_text()
+    assert dg.dgal_get_device_status() == 0
+    # back to the untuned threshold for the tests that follow in this process
+    path = tmp_path / "default.json"
+    path.write_text('{\n  "%s": [16384, 0, 0]\n}\n' % key_dev)
+    assert dg.dgal_autotune(4, cache_path=path, config_class=1)["group_below"] == 16384
