@@ -8,7 +8,11 @@ saved flags, i.e. every step of the hot path.  "Plain" = the same pairs
 through the plain form (FP32 only, no flags saved, backward recomputes).
 
 Prints one JSON line (rank 0).  Options: --gpus N --steps K --warmup W
-[--impl reference] [--n PAIRS].
+[--impl reference] [--n PAIRS] [--workload NAME] [--no-configs].  The default
+line also carries, under "configs", the other workloads measured in the same
+run: 4096 rectangle pairs, the 2000 x 2000 pairwise matrix, the 64-scene
+ragged batch and the 4M convex pairs (each with its plain form, a parity
+sample against the FP64 oracle and the oracle's own rate).
 """
 from __future__ import annotations
 
@@ -109,10 +113,11 @@ def cpu_oracle_run(d, threads):
     """One fwd+bwd pass of the FP64 oracle over the arrays in d; returns seconds."""
     import oracle
 
+    c1, c2 = d.get("c1"), d.get("c2")
+    grad = d["grad"].astype(np.float64) if "grad" in d else np.ones(d["p1"].shape[0])
     t0 = time.perf_counter()
-    o = oracle.iou_paired(d["p1"], d["p2"], threads=threads)
-    oracle.iou_backward_paired(d["p1"], d["p2"], d["grad"].astype(np.float64), o["nx"], o["xflags"],
-                               threads=threads)
+    o = oracle.iou_paired(d["p1"], d["p2"], c1, c2, threads=threads)
+    oracle.iou_backward_paired(d["p1"], d["p2"], grad, o["nx"], o["xflags"], c1, c2, threads=threads)
     return time.perf_counter() - t0
 
 
@@ -146,9 +151,15 @@ def reference_arm(args):
 
 
 def matrix_workload(args):
+    print(json.dumps(matrix_measure(args, args.workload)), flush=True)
+
+
+def matrix_measure(args, workload, parity=False):
     """Forward-only matrix workloads: the 2000 x 2000 pairwise matrix, and the
     64-scene ragged batch (persistent launch in a CUDA graph; plain = one
-    launch per scene).  Unit: IoU entries/s."""
+    launch per scene).  Unit: IoU entries/s.  Returns the JSON line; with
+    parity, also checks sampled rows / scenes against the FP64 oracle and times
+    the oracle on them (its cpu_baseline)."""
     import torch
 
     import paper_2011_11134_gb300 as dg
@@ -157,7 +168,7 @@ def matrix_workload(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, device=dev, dtype=torch.uint8)
-    if args.workload == "pairwise2000":
+    if workload == "pairwise2000":
         d = W.pairwise_bev_2000(seed=0)
         a, b = torch.from_numpy(d["a"]).to(dev), torch.from_numpy(d["b"]).to(dev)
         N, M = a.shape[0], b.shape[0]
@@ -168,7 +179,7 @@ def matrix_workload(args):
         plain = lambda: dg.dgal_iou_pairwise(a, b, out=out, flags=dg.DGAL_PLAIN)
         launches = 1
         out_bytes = 5 * entries
-    elif args.workload == "ragged64":
+    elif workload == "ragged64":
         d = W.ragged_scenes_64(seed=0)
         a, b = torch.from_numpy(d["a"]).to(dev), torch.from_numpy(d["b"]).to(dev)
         ao, bo, oo = (torch.from_numpy(d[k]).to(dev) for k in ("a_off", "b_off", "out_off"))
@@ -181,7 +192,7 @@ def matrix_workload(args):
                                                        flags=dg.DGAL_PLAIN)
         launches = 2
         out_bytes = 5 * entries
-    elif args.workload == "nms2000":
+    elif workload == "nms2000":
         d = W.pairwise_bev_2000(seed=0)
         a = torch.from_numpy(d["a"]).to(dev)
         N = a.shape[0]
@@ -227,7 +238,7 @@ def matrix_workload(args):
         "metric": "IoU matrix entries/s, forward", "value": value, "unit": "entries/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "entries": entries,
+        "config": {"workload": WORKLOADS[workload], "entries": entries,
                    "l2": "flushed between steps (256 MiB write outside the timed events)"},
         "plain": {"value": entries / (statistics.mean(t_plain) * 1e-3), "unit": "entries/s",
                   "ms_per_step": statistics.mean(t_plain)} if t_plain else None,
@@ -235,16 +246,54 @@ def matrix_workload(args):
                      "traffic": None, "alg_bytes_per_entry": 5},
         "gpu_launches": launches * args.steps, "clocks": clocks,
     }
-    if args.workload == "ragged64":
+    if workload == "ragged64":
         line["config"]["autotuned"] = tuned
-    if args.workload == "nms2000":
+    if parity and workload in ("pairwise2000", "ragged64"):
+        line.update(_matrix_parity(workload, d, out, entries))
+    if workload == "nms2000":
         line["metric"] = "NMS pair tests/s (IoU > threshold decisions, upper triangle)"
         line["unit"] = "pairs/s"
         line["config"]["boxes"] = N
         line["config"]["kept"] = int(dg.dgal_nms_rotated(a, scores, 0.2, workspace=ws).numel())
         line["roofline"]["alg_bytes_per_entry"] = 1 / 8
         line["roofline"]["note"] = "latency-bound (one sequential greedy block); not an HBM-bound size"
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def _matrix_parity(workload, d, out, entries):
+    """Sampled parity of a matrix workload against the FP64 oracle (the first
+    200 rows of the 2000 x 2000 matrix; 4 of the 64 scenes), and the oracle's
+    rate on that sample (all host cores)."""
+    import oracle
+
+    threads = os.cpu_count() or 1
+    iou = out[0].cpu().numpy().ravel()
+    nx = out[1].cpu().numpy().ravel()
+    t0 = time.perf_counter()
+    if workload == "pairwise2000":
+        rows = 200
+        ref_iou, ref_nx = oracle.iou_pairwise(d["a"][:rows], d["b"], threads=threads)
+        got_iou = iou[: rows * d["b"].shape[0]]
+        got_nx = nx[: rows * d["b"].shape[0]]
+        sample = f"first {rows} rows ({rows * d['b'].shape[0]:,} entries)"
+        ref_iou, ref_nx = ref_iou.ravel(), ref_nx.ravel()
+    else:
+        got, gnx, ri, rn = [], [], [], []
+        for s_ in (0, 21, 42, 63):
+            a = d["a"][d["a_off"][s_]:d["a_off"][s_ + 1]]
+            b = d["b"][d["b_off"][s_]:d["b_off"][s_ + 1]]
+            r_iou, r_nx = oracle.iou_pairwise(a, b, threads=threads)
+            ri.append(r_iou.ravel())
+            rn.append(r_nx.ravel())
+            got.append(iou[d["out_off"][s_]:d["out_off"][s_ + 1]])
+            gnx.append(nx[d["out_off"][s_]:d["out_off"][s_ + 1]])
+        ref_iou, ref_nx, got_iou, got_nx = map(np.concatenate, (ri, rn, got, gnx))
+        sample = f"scenes 0, 21, 42, 63 ({ref_iou.size:,} entries)"
+    secs = time.perf_counter() - t0
+    return {"parity": {"iou_max_abs": float(np.abs(got_iou.astype(np.float64) - ref_iou).max()),
+                       "nx_mismatch_entries": int((got_nx != ref_nx).sum()), "sample": sample},
+            "cpu_baseline": {"value": ref_iou.size / secs, "unit": "entries/s", "cores": threads, "kind": "oracle",
+                             "sample": sample + ", forward"}}
 
 
 def fused_workload(args):
@@ -442,9 +491,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--n", type=int, default=0, help="pairs of a paired workload (default: its own size)")
     ap.add_argument("--ref-sample", type=int, default=200_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="headline line only (skip the other configurations' measurements)")
     ap.add_argument("--workload", default="loss1m",
                     choices=["loss1m", "rect4096", "convex", "pairwise2000", "ragged64", "fused1m", "iou3d1m",
                              "nms2000"],
@@ -458,12 +509,38 @@ def main():
         matrix_workload(args)
         return
     if args.workload == "fused1m":
+        args.n = args.n or 1_000_000
         fused_workload(args)
         return
     if args.workload == "iou3d1m":
+        args.n = args.n or 1_000_000
         iou3d_workload(args)
         return
 
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    line = paired_measure(args, args.workload, args.n, with_e2e=True,
+                          with_cpu=(not args.no_cpu_baseline and world == 1))
+    if rank == 0:
+        if args.workload == "loss1m" and world == 1 and not args.no_configs and not args.n:
+            line["configs"] = other_configs(args)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def paired_measure(args, workload, n_pairs, with_e2e, with_cpu):
+    """One paired workload (loss1m, rect4096 or convex): forward (saving the
+    flags) + backward (reading them) timed over args.steps steps, the plain
+    form timed on the same pairs, parity of a sample against the FP64 oracle,
+    and optionally the host-resident call (e2e) and the oracle's own rate
+    (cpu_baseline).  Returns the JSON line on rank 0, None on the others."""
     import torch
     import torch.distributed as dist
 
@@ -472,21 +549,18 @@ def main():
     from paper_2011_11134_gb300.replicas import max_over_ranks, replica_seed
 
     rank, world, local = _dist_env()
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     seed = replica_seed(rank)  # weak scaling: every replica runs its own seeded workload
-    if args.workload == "rect4096":
+    if workload == "rect4096":
         d = W.paired_rect_4096(seed=seed)
-    elif args.workload == "convex":
-        d = W.convex_pairs_4m(seed=seed, n=args.n if args.n != 1_000_000 else 4_000_000)
+    elif workload == "convex":
+        d = W.convex_pairs_4m(seed=seed, n=n_pairs or 4_000_000)
     else:
-        d = W.loss_pairs_1m(seed=seed, n=args.n)
+        d = W.loss_pairs_1m(seed=seed, n=n_pairs or 1_000_000)
     n = d["p1"].shape[0]
     K = d["p1"].shape[1]
-    workload_name = WORKLOADS[args.workload]
-    if args.workload in ("loss1m", "convex") and n != (1_000_000 if args.workload == "loss1m" else 4_000_000):
+    workload_name = WORKLOADS[workload]
+    if n_pairs and workload in ("loss1m", "convex"):
         workload_name += f" (resized by --n to {n:,} pairs)"
     p1 = torch.from_numpy(d["p1"]).to(dev)
     p2 = torch.from_numpy(d["p2"]).to(dev)
@@ -567,12 +641,17 @@ def main():
     total_ms = max_over_ranks(total_ms, dev)
     value = n * world * args.steps / (total_ms / 1e3)
 
-    # parity of the timed outputs on a sample (FP64 oracle)
+    # parity of the timed outputs on a sample (FP64 oracle): 20,000 random
+    # pairs, plus 2,000 constructed near-degenerate ones where the workload has them
     err = None
     if rank == 0:
         import oracle
 
-        idx = np.random.Generator(np.random.PCG64(7)).choice(n, size=min(n, 20000), replace=False)
+        rng = np.random.Generator(np.random.PCG64(7))
+        idx = rng.choice(n, size=min(n, 20000), replace=False)
+        if "kind" in d and (d["kind"] > 0).any():
+            deg = np.flatnonzero(d["kind"] > 0)
+            idx = np.union1d(idx, rng.choice(deg, size=min(2000, deg.size), replace=False))
         idx.sort()
         sc1 = d["c1"][idx] if "c1" in d else None
         sc2 = d["c2"][idx] if "c2" in d else None
@@ -592,6 +671,7 @@ def main():
             ie = np.abs(gi - ref["iou"])
             err["iou_max_abs_constructed_degenerate"] = float(ie[kd].max()) if kd.any() else None
             err["iou_max_abs_other"] = float(ie[~kd].max())
+            err["grad_max_rel_generic"] = float(rel[gen].max())
             err["constructed_degenerate_in_sample"] = int(kd.sum())
 
     # plain form on the same pairs
@@ -599,11 +679,91 @@ def main():
     plain_ms = sum(pfw) + sum(pbw)
     plain_value = n * world * args.steps / (plain_ms / 1e3)
 
-    # end to end through the C ABI on pinned host buffers: dgal_iou_fwd_bwd_host
-    # reads the polygons (and counts) and dL/dIoU from host memory and writes
-    # IoU and the gradients back, all inside the timed region: K = 4 in its
-    # direct form (one kernel on the pinned buffers in place), K = 8 staged
-    # (chunks copied in and out, overlapping the kernels)
+    e2e = _paired_e2e(args, dg, d, n, K, world, dev, stream) if with_e2e else None
+    if rank != 0:
+        return None
+
+    peaks = _peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    fw_ms, bw_ms = statistics.mean(fw), statistics.mean(bw)
+    cb = 2 if c1 is not None else 0  # count bytes read per pair
+    fwd_bytes = 2 * 8 * K + cb + 4 + 1 + 2 * K
+    bwd_bytes = 2 * 8 * K + cb + 4 + 1 + 2 * K + 2 * 8 * K
+    fw_gbs = fwd_bytes * n / (fw_ms * 1e-3) / 1e9
+    bw_gbs = bwd_bytes * n / (bw_ms * 1e-3) / 1e9
+    dom = "forward" if fw_ms >= bw_ms else "backward"
+    ach = fw_gbs if dom == "forward" else bw_gbs
+    roofline = {"bound": "hbm", "kernel": f"k_paired_{'fwd' if dom == 'forward' else 'bwd'}<{K}>", "achieved": ach,
+                "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                "traffic_note": "the kernels changed since the last DRAM capture: per-launch DRAM bytes are in "
+                                "the profile summaries, not re-measured in this line",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
+                "per_kernel": {"forward": {"ms": fw_ms, "alg_bytes_per_pair": fwd_bytes, "GB_s": fw_gbs},
+                               "backward": {"ms": bw_ms, "alg_bytes_per_pair": bwd_bytes, "GB_s": bw_gbs}},
+                "step": {"ms": total_ms / args.steps, "alg_bytes_per_pair": fwd_bytes + bwd_bytes,
+                         "frac": (fwd_bytes + bwd_bytes) * n / (total_ms / args.steps * 1e-3) / 1e9 / hbm}}
+    if K == 8:
+        # 2.7 kflop per pair (the FP32 model of the survey) against the derived FP32 peak
+        roofline["fp32"] = {"achieved_tflops": 2.7e3 * n / (total_ms / args.steps * 1e-3) / 1e12,
+                            "peak_tflops": FP32_PEAK_TFLOPS,
+                            "frac": 2.7e3 * n / (total_ms / args.steps * 1e-3) / 1e12 / FP32_PEAK_TFLOPS}
+    cpu = None
+    if with_cpu:
+        threads = os.cpu_count() or 1
+        if "kind" in d:
+            # every constructed near-degenerate pair of the first 2M, plus the first 100,000 pairs
+            deg = np.flatnonzero(d["kind"][: min(n, 2_000_000)] > 0)
+            sidx = np.union1d(np.arange(min(n, 100_000)), deg)
+            ds = {k: v[sidx] for k, v in d.items()}
+            desc = f"{sidx.size:,} pairs: the first 100,000 and all {deg.size:,} constructed near-degenerate " \
+                   f"pairs of the first 2M, fwd+bwd, FP64 C oracle on all host cores"
+        else:
+            sample = min(n, args.ref_sample)
+            ds = {k: v[:sample] for k, v in d.items()}
+            desc = f"first {sample} pairs of the workload, fwd+bwd, FP64 C oracle on all host cores"
+        m = ds["p1"].shape[0]
+        cpu_oracle_run(ds, threads)
+        secs = cpu_oracle_run(ds, threads)
+        one = min(m, 20_000)  # single-thread rate on a smaller sample (about a second)
+        secs1 = cpu_oracle_run({k: v[:one] for k, v in ds.items()}, 1)
+        cpu = {"value": m / secs, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
+               "single_thread": {"value": one / secs1, "unit": UNIT, "cores": 1, "sample": f"first {one} pairs"}}
+    launches = 3 if K == 8 else 2  # K = 8: forward, its hard-pair finish, backward
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name, "pairs_per_gpu": n, "K": K,
+                   "parallelism": f"replicas x{world}",
+                   "l2": f"flushed between steps (256 MiB write outside the timed events); inputs {2 * n * 8 * K / 1e6:.0f} MB"},
+        "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": plain_ms / args.steps,
+                  "form": "FP32 only, no saved flags, backward recomputes the clip",
+                  "batched_over_plain": value / plain_value},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches * args.steps,  # forward (saves the flags), backward (reads them)
+        "clocks": clocks,
+        "parity": err,
+    }
+    return line
+
+
+# FP32 non-tensor peak of GB300, derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def _paired_e2e(args, dg, d, n, K, world, dev, stream):
+    """End to end through the C ABI on pinned host buffers:
+    dgal_iou_fwd_bwd_host reads the polygons (and counts) and dL/dIoU from
+    host memory and writes IoU and the gradients back, all inside the timed
+    region: K = 4 in its direct form (one kernel on the pinned buffers in
+    place), K = 8 staged (chunks copied in and out, overlapping the kernels)."""
+    import torch
+
+    L = dg._lib
+    lib = L.lib()
+    sp = L.stream_ptr(stream)
     h_p1 = torch.from_numpy(d["p1"]).pin_memory()
     h_p2 = torch.from_numpy(d["p2"]).pin_memory()
     h_c1 = torch.from_numpy(d["c1"]).pin_memory() if "c1" in d else None
@@ -619,7 +779,8 @@ def main():
         ws_e2e = torch.empty(dg.dgal_iou_host_workspace_bytes(chunk, K) + 256, device=dev, dtype=torch.uint8)
         ws_e2e = ws_e2e[(-ws_e2e.data_ptr()) % 256:]
     host_args = (L.ptr(h_p1), L.ptr(h_c1), L.ptr(h_p2), L.ptr(h_c2), L.ptr(h_grad), n, K, L.ptr(h_iou), L.ptr(h_g1),
-                 L.ptr(h_g2), L.ptr(ws_e2e), ws_e2e.numel() if ws_e2e is not None else 0, chunk, FLAGS, sp)
+                 L.ptr(h_g2), L.ptr(ws_e2e), ws_e2e.numel() if ws_e2e is not None else 0, chunk,
+                 dg.DGAL_FP64_REFINE, sp)
 
     def e2e_step():
         assert lib.dgal_iou_fwd_bwd_host(*host_args) == 0, dg.dgal_last_error()
@@ -635,74 +796,44 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1)
-    e2e_value = n * world * args.steps / (e2e_ms / 1e3)
     h2d = 2 * n * 8 * K + 4 * n + (2 * n if h_c1 is not None else 0)
     d2h = 4 * n + 2 * n * 8 * K
+    return {"value": n * world * args.steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h,
+            "path": "dgal_iou_fwd_bwd_host on pinned host buffers, " + (
+                "direct form: one kernel reads and writes them in place over the host link" if direct else
+                f"staged form: {chunk}-pair chunks copied in and out, overlapping the kernels")}
 
-    if rank != 0:
-        if world > 1:
-            dist.barrier()
-            dist.destroy_process_group()
-        return
 
-    peaks = _peaks()
-    hbm = peaks["hbm_gbs"] if peaks else 6800.0
-    fw_ms, bw_ms = statistics.mean(fw), statistics.mean(bw)
-    cb = 2 if c1 is not None else 0  # count bytes read per pair
-    fwd_bytes = 2 * 8 * K + cb + 4 + 1 + 2 * K
-    bwd_bytes = 2 * 8 * K + cb + 4 + 1 + 2 * K + 2 * 8 * K
-    fw_gbs = fwd_bytes * n / (fw_ms * 1e-3) / 1e9
-    bw_gbs = bwd_bytes * n / (bw_ms * 1e-3) / 1e9
-    dom = "forward" if fw_ms >= bw_ms else "backward"
-    ach = fw_gbs if dom == "forward" else bw_gbs
-    # DRAM bytes per pair of the two K = 4 kernels, dram__bytes_read.sum +
-    # dram__bytes_write.sum of one ncu capture on 4M pairs
-    # (profiles/paired_k4_fwd_bwd_4m_ncu_full.md), scaled to this launch
-    traffic = None
-    if K == 4 and c1 is None and args.workload == "loss1m":
-        traffic = (74.3 if dom == "forward" else 130.8) * n
-    roofline = {"bound": "hbm", "kernel": f"k_paired_{'fwd' if dom == 'forward' else 'bwd'}<{K}>", "achieved": ach,
-                "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
-                "traffic_source": "ncu capture of 4M pairs, per pair x pairs" if traffic else None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
-                "per_kernel": {"forward": {"ms": fw_ms, "alg_bytes_per_pair": fwd_bytes, "GB_s": fw_gbs},
-                               "backward": {"ms": bw_ms, "alg_bytes_per_pair": bwd_bytes, "GB_s": bw_gbs}}}
-    cpu = None
-    if not args.no_cpu_baseline and world == 1 and args.workload == "loss1m":
-        threads = os.cpu_count() or 1
-        sample = min(n, args.ref_sample)
-        ds = {k: v[:sample] for k, v in d.items()}
-        cpu_oracle_run(ds, threads)
-        secs = cpu_oracle_run(ds, threads)
-        one = min(sample, 20_000)  # single-thread rate on a smaller sample (about a second)
-        secs1 = cpu_oracle_run({k: v[:one] for k, v in d.items()}, 1)
-        cpu = {"value": sample / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"first {sample} pairs of the workload, fwd+bwd, FP64 C oracle on all host cores",
-               "single_thread": {"value": one / secs1, "unit": UNIT, "cores": 1, "sample": f"first {one} pairs"}}
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name, "pairs_per_gpu": n, "K": K,
-                   "parallelism": f"replicas x{world}",
-                   "l2": f"flushed between steps (256 MiB write outside the timed events); inputs {2 * n * 8 * K / 1e6:.0f} MB"},
-        "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": plain_ms / args.steps,
-                  "form": "FP32 only, no saved flags, backward recomputes the clip",
-                  "batched_over_plain": value / plain_value},
-        "roofline": roofline,
-        "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "path": "dgal_iou_fwd_bwd_host on pinned host buffers, " + (
-                    "direct form: one kernel reads and writes them in place over the host link" if direct else
-                    f"staged form: {chunk}-pair chunks copied in and out, overlapping the kernels")},
-        "gpu_launches": 2 * args.steps,  # forward (saves the flags), backward (reads them)
-        "clocks": clocks,
-        "parity": err,
-    }
-    print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
+def _summary(line, keys=("value", "unit", "ms_per_step", "plain", "roofline", "parity", "cpu_baseline", "clocks",
+                         "gpu_launches")):
+    out = {"workload": line["config"]["workload"]}
+    out.update({k: line.get(k) for k in keys})
+    if isinstance(out.get("roofline"), dict):
+        out["roofline"] = {k: v for k, v in out["roofline"].items() if k != "per_kernel"} | {
+            "per_kernel": line["roofline"].get("per_kernel")}
+    return out
+
+
+def other_configs(args):
+    """The configurations other than the headline, measured in the same run
+    (each with its own timing, plain form, parity sample and oracle rate):
+    1 the 4096 rotated-rectangle pairs, 2 the 2000 x 2000 pairwise matrix,
+    3 the 64-scene ragged batch in a CUDA graph, 5 the 4M convex pairs with 5%
+    constructed near-degenerate ones."""
+    import paper_2011_11134_gb300 as dg
+
+    out = {}
+    dg.dgal_autotune(4, config_class=1)  # the paired launch shape (untimed)
+    c1 = paired_measure(args, "rect4096", 0, with_e2e=False, with_cpu=True)
+    c1["roofline"]["note"] = "0.9 MB per step stays in L2: launch/latency-bound, the HBM fraction is not meaningful"
+    c1["config"]["paired_shape"] = dg.dgal_get_paired_config(4)
+    out["1_rect4096_fwd_bwd"] = _summary(c1) | {"paired_shape": c1["config"]["paired_shape"]}
+    out["2_pairwise2000_fwd"] = _summary(matrix_measure(args, "pairwise2000", parity=True))
+    out["3_ragged64_fwd_graph"] = _summary(matrix_measure(args, "ragged64", parity=True))
+    c5 = paired_measure(args, "convex", 0, with_e2e=False, with_cpu=True)
+    out["5_convex4m_fwd_bwd"] = _summary(c5)
+    return out
 
 
 if __name__ == "__main__":
