@@ -496,6 +496,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true",
                     help="headline line only (skip the other configurations' measurements)")
+    ap.add_argument("--launch-only", action="store_true",
+                    help="paired workloads: run the batched forward + backward warmup + steps times and exit, "
+                         "with no timing, oracle or host-memory pass (a short program to run under a profiler)")
     ap.add_argument("--workload", default="loss1m",
                     choices=["loss1m", "rect4096", "convex", "pairwise2000", "ragged64", "fused1m", "iou3d1m",
                              "nms2000"],
@@ -526,7 +529,7 @@ def main():
     torch.cuda.set_device(local)
     line = paired_measure(args, args.workload, args.n, with_e2e=True,
                           with_cpu=(not args.no_cpu_baseline and world == 1))
-    if rank == 0:
+    if rank == 0 and not args.launch_only:
         if args.workload == "loss1m" and world == 1 and not args.no_configs and not args.n:
             line["configs"] = other_configs(args)
         print(json.dumps(line), flush=True)
@@ -535,12 +538,15 @@ def main():
         dist.destroy_process_group()
 
 
-def paired_measure(args, workload, n_pairs, with_e2e, with_cpu):
+def paired_measure(args, workload, n_pairs, with_e2e, with_cpu, use_graph=False):
     """One paired workload (loss1m, rect4096 or convex): forward (saving the
     flags) + backward (reading them) timed over args.steps steps, the plain
     form timed on the same pairs, parity of a sample against the FP64 oracle,
     and optionally the host-resident call (e2e) and the oracle's own rate
-    (cpu_baseline).  Returns the JSON line on rank 0, None on the others."""
+    (cpu_baseline).  With use_graph the batched step is also captured in a
+    CUDA graph (forward + backward, replayed once per step) and the line's
+    value is the graph's; the eager calls' rate is kept beside it.  Returns
+    the JSON line on rank 0, None on the others."""
     import torch
     import torch.distributed as dist
 
@@ -579,14 +585,14 @@ def paired_measure(args, workload, n_pairs, with_e2e, with_cpu):
     sp = L.stream_ptr(stream)
     FLAGS = dg.DGAL_FP64_REFINE
 
-    def fwd():
+    def fwd(s=None):
         st = lib.dgal_iou_paired(L.ptr(p1), L.ptr(c1), L.ptr(p2), L.ptr(c2), n, K, L.ptr(iou), L.ptr(nx), L.ptr(xf), None,
-                                 FLAGS, sp)
+                                 FLAGS, s or sp)
         assert st == 0, dg.dgal_last_error()
 
-    def bwd():
+    def bwd(s=None):
         st = lib.dgal_iou_backward(L.ptr(p1), L.ptr(c1), L.ptr(p2), L.ptr(c2), n, K, L.ptr(grad), L.ptr(nx), L.ptr(xf),
-                                   L.ptr(g1), L.ptr(g2), FLAGS, sp)
+                                   L.ptr(g1), L.ptr(g2), FLAGS, s or sp)
         assert st == 0, dg.dgal_last_error()
 
     def fwd_plain():
@@ -617,6 +623,14 @@ def paired_measure(args, workload, n_pairs, with_e2e, with_cpu):
         bw = [ev[s][1].elapsed_time(ev[s][2]) for s in range(steps)]
         return fw, bw
 
+    if args.launch_only:
+        for _ in range(args.warmup + args.steps):
+            fwd()
+            bwd()
+        torch.cuda.synchronize(dev)
+        assert dg.dgal_get_device_status() == 0
+        return None
+
     # warm-up (untimed)
     for _ in range(args.warmup):
         fwd()
@@ -625,6 +639,36 @@ def paired_measure(args, workload, n_pairs, with_e2e, with_cpu):
         bwd_plain()
     torch.cuda.synchronize(dev)
 
+    graph = None
+    if use_graph:
+        # the batched forward + backward captured once, on a side stream
+        cs = torch.cuda.Stream(dev)
+        cs.wait_stream(stream)
+        with torch.cuda.stream(cs):
+            csp = L.stream_ptr(cs)
+            fwd(csp)
+            bwd(csp)
+            torch.cuda.synchronize(dev)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=cs):
+                fwd(csp)
+                bwd(csp)
+        stream.wait_stream(cs)
+        torch.cuda.synchronize(dev)
+
+    def timed_graph(steps):
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+        for _ in range(max(3, args.warmup)):
+            flush.fill_(0)
+            graph.replay()
+        for s in range(steps):
+            flush.fill_(s & 0xFF)
+            ev[s][0].record(stream)
+            graph.replay()
+            ev[s][1].record(stream)
+        torch.cuda.synchronize(dev)
+        return [ev[s][0].elapsed_time(ev[s][1]) for s in range(steps)]
+
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
@@ -632,13 +676,15 @@ def paired_measure(args, workload, n_pairs, with_e2e, with_cpu):
         dist.barrier()
     torch.cuda.synchronize(dev)
     fw, bw = timed(args.steps, fwd, bwd)
+    gsteps = timed_graph(args.steps) if graph is not None else None
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
     step_ms = [a + b for a, b in zip(fw, bw)]
-    total_ms = sum(step_ms)
-    total_ms = max_over_ranks(total_ms, dev)
+    eager_ms = max_over_ranks(sum(step_ms), dev)
+    eager_value = n * world * args.steps / (eager_ms / 1e3)
+    total_ms = max_over_ranks(sum(gsteps), dev) if gsteps is not None else eager_ms
     value = n * world * args.steps / (total_ms / 1e3)
 
     # parity of the timed outputs on a sample (FP64 oracle): 20,000 random
@@ -693,10 +739,16 @@ def paired_measure(args, workload, n_pairs, with_e2e, with_cpu):
     bw_gbs = bwd_bytes * n / (bw_ms * 1e-3) / 1e9
     dom = "forward" if fw_ms >= bw_ms else "backward"
     ach = fw_gbs if dom == "forward" else bw_gbs
+    # DRAM bytes per pair (dram__bytes_read.sum + dram__bytes_write.sum) of the
+    # K = 4 forward and backward from one ncu capture of 4,000,000 IoU-loss
+    # pairs (the current kernels), scaled to this launch by its pairs
+    traffic = None
+    if K == 4 and c1 is None and workload == "loss1m":
+        traffic = (DRAM_BYTES_PER_PAIR_K4["forward" if dom == "forward" else "backward"]) * n
     roofline = {"bound": "hbm", "kernel": f"k_paired_{'fwd' if dom == 'forward' else 'bwd'}<{K}>", "achieved": ach,
-                "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
-                "traffic_note": "the kernels changed since the last DRAM capture: per-launch DRAM bytes are in "
-                                "the profile summaries, not re-measured in this line",
+                "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
+                "traffic_source": ("ncu DRAM bytes per pair of a 4M-pair capture of the same kernel, x pairs per "
+                                   "launch") if traffic else None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
                 "per_kernel": {"forward": {"ms": fw_ms, "alg_bytes_per_pair": fwd_bytes, "GB_s": fw_gbs},
                                "backward": {"ms": bw_ms, "alg_bytes_per_pair": bwd_bytes, "GB_s": bw_gbs}},
@@ -746,8 +798,18 @@ def paired_measure(args, workload, n_pairs, with_e2e, with_cpu):
         "clocks": clocks,
         "parity": err,
     }
+    if graph is not None:
+        line["form"] = "batched forward + backward captured in one CUDA graph, replayed once per step"
+        line["eager"] = {"value": eager_value, "unit": UNIT, "ms_per_step": eager_ms / args.steps,
+                         "form": "the same two calls launched eagerly"}
+        line["plain"]["batched_over_plain"] = value / plain_value
+        line["plain"]["eager_batched_over_plain"] = eager_value / plain_value
     return line
 
+
+# DRAM bytes per pair of the K = 4 paired kernels (forward saving the flags,
+# backward reading them), measured by ncu on 4,000,000 IoU-loss pairs
+DRAM_BYTES_PER_PAIR_K4 = {"forward": 73.86, "backward": 129.93}
 
 # FP32 non-tensor peak of GB300, derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -825,10 +887,11 @@ def other_configs(args):
 
     out = {}
     dg.dgal_autotune(4, config_class=1)  # the paired launch shape (untimed)
-    c1 = paired_measure(args, "rect4096", 0, with_e2e=False, with_cpu=True)
+    c1 = paired_measure(args, "rect4096", 0, with_e2e=False, with_cpu=True, use_graph=True)
     c1["roofline"]["note"] = "0.9 MB per step stays in L2: launch/latency-bound, the HBM fraction is not meaningful"
     c1["config"]["paired_shape"] = dg.dgal_get_paired_config(4)
-    out["1_rect4096_fwd_bwd"] = _summary(c1) | {"paired_shape": c1["config"]["paired_shape"]}
+    out["1_rect4096_fwd_bwd"] = _summary(c1) | {"paired_shape": c1["config"]["paired_shape"], "form": c1["form"],
+                                                "eager": c1["eager"]}
     out["2_pairwise2000_fwd"] = _summary(matrix_measure(args, "pairwise2000", parity=True))
     out["3_ragged64_fwd_graph"] = _summary(matrix_measure(args, "ragged64", parity=True))
     c5 = paired_measure(args, "convex", 0, with_e2e=False, with_cpu=True)

@@ -389,7 +389,7 @@ dgal_status dgal_graph_destroy(dgal_graph graph);
  *     lane per pair against groups of 8 lanes per pair on the forward +
  *     backward of synthetic pairs at 2^10 .. 2^18 pairs, and sets the batch
  *     size below which groups are used (smaller batches are latency-bound;
- *     K = 8 pairs always take groups).  Untuned, that size is 16384.
+ *     K = 8 pairs always take groups).  Untuned, that size is 1024.
  * cache_path (or, when NULL, the environment variable DGAL_TUNE_CACHE) names
  * a JSON file that is read first and rewritten with the result; NULL and no
  * variable means an in-memory cache only.  A cached ragged-batch shape

@@ -85,8 +85,9 @@ void set_batched_config(int K, BatchedConfig c) {
 
 namespace {
 std::map<std::pair<int, int>, PairedConfig> g_pcfg; // (device, K)
-// Untuned default: groups of 8 lanes below 16384 quadrilateral pairs.
-constexpr int64_t kGroupBelowDefault = 16384;
+// Untuned default: groups of 8 lanes below 1024 quadrilateral pairs (where
+// both shapes are within a few microseconds of the launch floor).
+constexpr int64_t kGroupBelowDefault = 1024;
 } // namespace
 
 PairedConfig paired_config(int K) {

@@ -1543,17 +1543,39 @@ __device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, Adj& adj, uint32_
     // two inside vertices, one between inside and outside, none or two
     // between two outside vertices; and every code must be distinct
     bool ok = empty || (__popc(in1) + __popc(in2) + popc_(X)) == (int)nx;
+    if constexpr (K == 4 && !COUNTS) {
+        // The same rule on all eight edges at once, in 4-bit fields: field i
+        // of R counts the crossings of P1 edge i (row i of X), field j of C
+        // those of P2 edge j (row j of X transposed).  An edge whose ends are
+        // inside and outside needs count 1 (s = 1), both inside count 0, both
+        // outside count 0 or 2 (n = 1 masks bit 1 of the field).
+        const uint32_t x = (uint32_t)X;
+        uint32_t xt = x, t = (xt ^ (xt >> 3)) & 0x0A0Au;
+        xt ^= t ^ (t << 3);
+        t = (xt ^ (xt >> 6)) & 0x00CCu;
+        xt ^= t ^ (t << 6);
+        auto nib_pop = [](uint32_t v) {
+            v = (v & 0x5555u) + ((v >> 1) & 0x5555u);
+            return (v & 0x3333u) + ((v >> 2) & 0x3333u);
+        };
+        auto spread = [](uint32_t m) { return (m | (m << 3) | (m << 6) | (m << 9)) & 0x1111u; };
+        const uint32_t in1n = ((in1 >> 1) | (in1 << 3)) & 15u, in2n = ((in2 >> 1) | (in2 << 3)) & 15u;
+        const uint32_t da = (nib_pop(x) ^ spread(in1 ^ in1n)) & ~(spread(~(in1 | in1n) & 15u) << 1);
+        const uint32_t db = (nib_pop(xt) ^ spread(in2 ^ in2n)) & ~(spread(~(in2 | in2n) & 15u) << 1);
+        ok &= (da | db) == 0u;
+    } else {
 #pragma unroll
-    for (int i = 0; i < K; ++i) {
-        const bool vi = !COUNTS || i < n1, vj = !COUNTS || i < n2;
-        const uint32_t ra = (uint32_t)popc_((X >> (i * K)) & kRow0);
-        const uint32_t na = (i + 1 < (int)n1m) ? (uint32_t)(i + 1) : 0u;
-        const uint32_t a0 = (in1 >> i) & 1u, a1 = (in1 >> na) & 1u;
-        ok &= !vi || ((a0 ^ a1) ? (ra == 1u) : (a0 ? ra == 0u : (ra == 0u || ra == 2u)));
-        const uint32_t rb = (uint32_t)popc_((X >> i) & col0);
-        const uint32_t nb = (i + 1 < (int)n2m) ? (uint32_t)(i + 1) : 0u;
-        const uint32_t b0 = (in2 >> i) & 1u, b1 = (in2 >> nb) & 1u;
-        ok &= !vj || ((b0 ^ b1) ? (rb == 1u) : (b0 ? rb == 0u : (rb == 0u || rb == 2u)));
+        for (int i = 0; i < K; ++i) {
+            const bool vi = !COUNTS || i < n1, vj = !COUNTS || i < n2;
+            const uint32_t ra = (uint32_t)popc_((X >> (i * K)) & kRow0);
+            const uint32_t na = (i + 1 < (int)n1m) ? (uint32_t)(i + 1) : 0u;
+            const uint32_t a0 = (in1 >> i) & 1u, a1 = (in1 >> na) & 1u;
+            ok &= !vi || ((a0 ^ a1) ? (ra == 1u) : (a0 ? ra == 0u : (ra == 0u || ra == 2u)));
+            const uint32_t rb = (uint32_t)popc_((X >> i) & col0);
+            const uint32_t nb = (i + 1 < (int)n2m) ? (uint32_t)(i + 1) : 0u;
+            const uint32_t b0 = (in2 >> i) & 1u, b1 = (in2 >> nb) & 1u;
+            ok &= !vj || ((b0 ^ b1) ? (rb == 1u) : (b0 ? rb == 0u : (rb == 0u || rb == 2u)));
+        }
     }
     if (!ok) return kSlow;
 

@@ -129,6 +129,40 @@ __device__ __forceinline__ void load_lane(const float* __restrict__ p1, const fl
     L.r = r;
 }
 
+// The backward's lane view: only the lane's own P1 vertex / edge and P2
+// vertex / edge; the other lanes' come by shuffle.  The values equal those of
+// load_lane (same arithmetic).
+struct LaneS {
+    float ax, ay, eax, eay;
+    float bxr, byr, ebxr, ebyr;
+    int n1, n2, r;
+};
+
+template <int KIN = 8>
+__device__ __forceinline__ void load_lane_slim(const float* __restrict__ p1, const float* __restrict__ p2, int n1,
+                                               int n2, int r, LaneS& L) {
+    const float ox = __ldg(p1), oy = __ldg(p1 + 1);
+    const int rr = (r < n1) ? r : 0;
+    const int rn = (rr + 1 < n1) ? rr + 1 : 0;
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p1) + rr);
+    const float2 w = __ldg(reinterpret_cast<const float2*>(p1) + rn);
+    L.ax = v.x - ox;
+    L.ay = v.y - oy;
+    L.eax = (w.x - ox) - L.ax;
+    L.eay = (w.y - oy) - L.ay;
+    const int rr2 = (r < n2) ? r : 0;
+    const int rn2 = (rr2 + 1 < n2) ? rr2 + 1 : 0;
+    const float2 q0 = __ldg(reinterpret_cast<const float2*>(p2) + rr2);
+    const float2 q1 = __ldg(reinterpret_cast<const float2*>(p2) + rn2);
+    L.bxr = q0.x - ox;
+    L.byr = q0.y - oy;
+    L.ebxr = (q1.x - ox) - L.bxr;
+    L.ebyr = (q1.y - oy) - L.byr;
+    L.n1 = n1;
+    L.n2 = n2;
+    L.r = r;
+}
+
 __device__ __forceinline__ uint64_t col0_mask() {
     uint64_t c = 0;
 #pragma unroll
@@ -167,24 +201,26 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
         out.degen = 1u;
         return true;
     }
-    float Lr = liveA ? fmaxf(fabsf(L.ax), fabsf(L.ay)) : 0.f;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) Lr = fmaxf(Lr, (j < n2) ? fmaxf(fabsf(L.bx[j]), fabsf(L.by[j])) : 0.f);
-    Lr = gmax(gm, Lr);
+    // L: the largest |coordinate| over both polygons (lane r contributes its
+    // own P1 and P2 vertex)
+    const float Lr = gmax(gm, fmaxf(liveA ? fmaxf(fabsf(L.ax), fabsf(L.ay)) : 0.f,
+                                    liveB ? fmaxf(fabsf(L.bxr), fabsf(L.byr)) : 0.f));
     const float thr = kRouteRel * Lr * Lr;
 
-    // row r of S and T, and the row's crossing terms of the area (see below)
+    // row r of S and T, and the row's crossing terms of the area (see below);
+    // j runs downwards so that the funnel shifts leave the sign of column j
+    // in bit j
     uint32_t sneg = 0, tneg = 0;
     float mn = __int_as_float(0x7f800000);
     float term[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 7; j >= 0; --j) {
         const float dx = L.ax - L.bx[j], dy = L.ay - L.by[j];
         const float s = L.ebx[j] * dy - L.eby[j] * dx;
         const float t = L.eay * dx - L.eax * dy;
         mn = fminf(mn, (liveA && j < n2) ? fminf(fabsf(s), fabsf(t)) : __int_as_float(0x7f800000));
-        sneg |= (__float_as_uint(s) >> 31) << j;
-        tneg |= (__float_as_uint(t) >> 31) << j;
+        sneg = push_sign(sneg, s);
+        tneg = push_sign(tneg, t);
         const float D = L.eax * L.eby[j] - L.eay * L.ebx[j];
         const float c = L.ax * L.by[j] - L.ay * L.bx[j];
         term[j] = fmaf(c, D, s * t) * __fdividef(1.0f, fabsf(D));
@@ -222,11 +258,9 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
     out.w0 = out.w1 = ~0ull;
     // the inputs' areas (kept for the union also when the intersection is empty)
     const float c1r = L.ax * L.eay - L.ay * L.eax;
-    float s2 = 0.f;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) s2 += (j < n2) ? L.bx[j] * L.eby[j] - L.by[j] * L.ebx[j] : 0.f;
+    const float c2r = L.bxr * L.ebyr - L.byr * L.ebxr;
     const float a1 = 0.5f * gsum(gm, liveA ? c1r : 0.f);
-    const float a2 = 0.5f * s2;
+    const float a2 = 0.5f * gsum(gm, liveB ? c2r : 0.f);
     out.a1 = a1;
     out.a2 = a2;
     if (cnt == 0u) return true;
@@ -237,7 +271,7 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
     // and every proper crossing (i, j) adds (cross(a_i, b_j) D + S T) / |D|,
     // with one crossing point shared by its two pieces and an FP32 error of
     // order u L^2 at any crossing angle.  Lane r adds P1 edge r's vertex term
-    // and its row of crossing terms; every lane forms the P2 sums itself.
+    // and its row of crossing terms, and P2 edge r's vertex term.
     const uint32_t rowE = liveA ? (uint32_t)((entry1 >> (8 * r)) & 0xFF) : 0u;
     const uint32_t rowX = liveA ? (uint32_t)((exit1 >> (8 * r)) & 0xFF) : 0u;
     bool bad = (rowE & (rowE - 1)) != 0u || (rowX & (rowX - 1)) != 0u;
@@ -247,15 +281,10 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
     const uint32_t nxt2 = (in2 >> 1) | ((in2 & 1u) << (n2 - 1));
     const uint32_t xrow = liveA ? (uint32_t)((X >> (8 * r)) & 0xFF) : 0u;
     float lane2 = ((nxt1 >> r) & 1u && liveA) ? c1r : 0.f;
+    lane2 += ((nxt2 >> r) & 1u && liveB) ? c2r : 0.f;
 #pragma unroll
     for (int j = 0; j < 8; ++j) lane2 += ((xrow >> j) & 1u) ? term[j] : 0.f;
-    float twoB = 0.f;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const float c2 = L.bx[j] * L.eby[j] - L.by[j] * L.ebx[j];
-        twoB += ((nxt2 >> j) & 1u) ? c2 : 0.f;
-    }
-    const float twoA = gsum(gm, lane2) + twoB;
+    const float twoA = gsum(gm, lane2);
     const float ai = 0.5f * twoA;
     const float U = a1 + a2 - ai;
     if (U < kThinRel * Lr * Lr) return false; // thin pair: float-float areas on the warp path
@@ -356,8 +385,8 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
 // Group backward (shape derivative).  Returns 0, kDevBadFlags, or kSlow
 // (group-uniform) when the pair must take the shoelace adjoint.  On success
 // lane r holds the gradients of P1 vertex r and P2 vertex r (0 beyond counts).
-template <typename Adj>
-__device__ __forceinline__ uint32_t bwd_group(const Lane& L, Adj& adj, uint32_t nx, uint64_t w0, uint64_t w1,
+template <typename LaneT, typename Adj>
+__device__ __forceinline__ uint32_t bwd_group(const LaneT& L, Adj& adj, uint32_t nx, uint64_t w0, uint64_t w1,
                                               bool refine, float& g1x, float& g1y, float& g2x, float& g2y) {
     const unsigned gm = gmask();
     const int base = gbase();
@@ -400,15 +429,18 @@ __device__ __forceinline__ uint32_t bwd_group(const Lane& L, Adj& adj, uint32_t 
     if (gor32(gm, ok ? 0u : 1u)) return kSlow;
 
     const float kInf = __int_as_float(0x7f800000);
-    // P1 edge r: parameters of its (at most two) crossings
+    // P1 edge r: parameters of its (at most two) crossings, with the P2
+    // edges' data fetched from their lanes
     float t0 = kInf, t1 = -kInf;
     uint32_t rx = rowX;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        if (rx) {
-            const uint32_t j = (uint32_t)(__ffs(rx) - 1);
-            rx &= rx - 1;
-            const float bx = sel8(L.bx, j), by = sel8(L.by, j), ebx = sel8(L.ebx, j), eby = sel8(L.eby, j);
+        const int j = rx ? __ffs(rx) - 1 : 0;
+        const bool has = rx != 0u;
+        rx &= rx ? rx - 1u : 0u;
+        const float bx = __shfl_sync(gm, L.bxr, base + j), by = __shfl_sync(gm, L.byr, base + j);
+        const float ebx = __shfl_sync(gm, L.ebxr, base + j), eby = __shfl_sync(gm, L.ebyr, base + j);
+        if (has) {
             const float dx = L.ax - bx, dy = L.ay - by;
             const float S = ebx * dy - eby * dx, D = L.eax * eby - L.eay * ebx;
             const float t = S * __fdividef(1.0f, D);
@@ -447,10 +479,8 @@ __device__ __forceinline__ uint32_t bwd_group(const Lane& L, Adj& adj, uint32_t 
     const float twoA = gsum(gm, (hasA ? (t1 - t0) * c1 : 0.f) + (hasB ? (u1 - u0) * c2 : 0.f));
     const float a1 = 0.5f * gsum(gm, c1), a2 = 0.5f * gsum(gm, c2);
     const float ai = 0.5f * twoA;
-    float Lr = liveA ? fmaxf(fabsf(L.ax), fabsf(L.ay)) : 0.f;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) Lr = fmaxf(Lr, (j < n2) ? fmaxf(fabsf(L.bx[j]), fabsf(L.by[j])) : 0.f);
-    Lr = gmax(gm, Lr);
+    const float Lr = gmax(gm, fmaxf(liveA ? fmaxf(fabsf(L.ax), fabsf(L.ay)) : 0.f,
+                                    liveB ? fmaxf(fabsf(bxr), fabsf(byr)) : 0.f));
     if (refine && !empty && ai < kTinyArea * Lr * Lr) return kSlow;
     float gai, ga1, ga2;
     if (!adj(ai, a1, a2, gai, ga1, ga2)) return 0u;

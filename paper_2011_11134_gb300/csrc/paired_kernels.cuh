@@ -16,6 +16,8 @@
 #include "dgal_internal.h"
 #include "group8.cuh"
 
+#include <type_traits>
+
 namespace dgal {
 
 constexpr int kPairThreads = 128;
@@ -631,7 +633,7 @@ k_paired_fwd_finish(const float* __restrict__ p1, const uint8_t* __restrict__ c1
 }
 
 template <bool RECOMPUTE, bool LOSS, bool Z3, int KIN = 8>
-__global__ void __launch_bounds__(kPairThreads)
+__global__ void __launch_bounds__(kPairThreads, RECOMPUTE ? 1 : kBwdMinBlocks)
 k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
                 const uint8_t* __restrict__ c2, int64_t n, const float* __restrict__ grad,
                 const uint8_t* __restrict__ nxs, const uint8_t* __restrict__ xflags, float* __restrict__ g1,
@@ -654,9 +656,12 @@ k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
         uint32_t nxk = 0;
         float gx1 = 0.f, gy1 = 0.f, gx2 = 0.f, gy2 = 0.f;
         if (good) {
-            g8::Lane L;
-            g8::load_lane<KIN>(p1 + k * 2 * KIN, p2 + k * 2 * KIN, n1, n2, r, L);
-            if (RECOMPUTE) {
+            // the recomputing form needs all of P2 in every lane (the forward's
+            // rows); the other takes the lane's own vertices only
+            typename std::conditional<RECOMPUTE, g8::Lane, g8::LaneS>::type L;
+            if constexpr (RECOMPUTE) g8::load_lane<KIN>(p1 + k * 2 * KIN, p2 + k * 2 * KIN, n1, n2, r, L);
+            else g8::load_lane_slim<KIN>(p1 + k * 2 * KIN, p2 + k * 2 * KIN, n1, n2, r, L);
+            if constexpr (RECOMPUTE) {
                 g8::FwdG o;
                 needfwd = !g8::fwd_group(L, o);
                 w0 = o.w0;

@@ -12,11 +12,6 @@ from .gpu_helpers import GRAD_RTOL, IOU_ATOL, THREADS, dev, grad_rel_err, host
 
 pytestmark = pytest.mark.gpu
 
-# quadrilateral batches below this many pairs take 8-lane groups on the device
-# (the untuned default of the library's paired launch shape)
-GROUP_BELOW = 16384
-
-
 @pytest.fixture(scope="module")
 def dg():
     import torch
@@ -48,7 +43,7 @@ def test_host_pipeline_matches_device_path(dg, n, chunk, pinned):
     ri, rnx, rxf, _ = dg.dgal_iou_paired(p1, p2)
     r1, r2 = dg.dgal_iou_backward(p1, p2, gd, rnx, rxf)
     torch.cuda.synchronize()
-    if n >= GROUP_BELOW or not pinned:
+    if n >= dg.dgal_get_paired_config(4)["group_below"] or not pinned:
         assert np.array_equal(iou.numpy(), host(ri))
         assert np.array_equal(g1.numpy(), host(r1)) and np.array_equal(g2.numpy(), host(r2))
     else:

@@ -375,5 +375,5 @@ def test_paired_launch_shapes_and_tuner(dg, orc, tmp_path):
     assert dg.dgal_get_device_status() == 0
     # back to the untuned threshold for the tests that follow in this process
     path = tmp_path / "default.json"
-    path.write_text('{\n  "%s": [16384, 0, 0]\n}\n' % key_dev)
-    assert dg.dgal_autotune(4, cache_path=path, config_class=1)["group_below"] == 16384
+    path.write_text('{\n  "%s": [1024, 0, 0]\n}\n' % key_dev)
+    assert dg.dgal_autotune(4, cache_path=path, config_class=1)["group_below"] == 1024
