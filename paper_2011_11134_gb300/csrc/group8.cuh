@@ -170,6 +170,40 @@ __device__ __forceinline__ uint64_t col0_mask() {
     return c;
 }
 
+// FP64 sign repair of lane r's row (refinement on, r < n1): every orientation
+// of the row within 3x the routing threshold thr takes the FP64 definition's
+// sign (orient_raw, the definition's operand order, from the raw inputs).
+// The row's FP32 values are formed again from the lane's data; the margin
+// covers a different rounding (contraction) of that second evaluation.
+// sneg, tneg: the row's FP32 sign bits (bit j: column j).  Returns the
+// repaired bits (S in bits 0-7, T in bits 8-15), or bit 32 set when one
+// orientation is exactly zero (a vertex on the line of an edge).  It runs only
+// for pairs with an orientation under the threshold.
+__device__ __forceinline__ uint64_t refine_row8(const Lane& L, const float* __restrict__ raw1,
+                                                const float* __restrict__ raw2, int n1, int n2, int r, float thr,
+                                                uint32_t sneg, uint32_t tneg) {
+    const float wide = 3.f * thr;
+    const int rn = (r + 1 < n1) ? r + 1 : 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (j >= n2) break;
+        const float dx = L.ax - L.bx[j], dy = L.ay - L.by[j];
+        const float sv = L.ebx[j] * dy - L.eby[j] * dx;
+        const float tv = L.eay * dx - L.eax * dy;
+        if (!(fabsf(sv) > wide)) {
+            const double v = orient_raw(raw2, j, (j + 1 < n2) ? j + 1 : 0, raw1, r);
+            if (v == 0.0) return 1ull << 32;
+            sneg = (v < 0.0) ? (sneg | (1u << j)) : (sneg & ~(1u << j));
+        }
+        if (!(fabsf(tv) > wide)) {
+            const double v = orient_raw(raw1, r, rn, raw2, j);
+            if (v == 0.0) return 1ull << 32;
+            tneg = (v < 0.0) ? (tneg | (1u << j)) : (tneg & ~(1u << j));
+        }
+    }
+    return (uint64_t)(sneg & 0xFFu) | ((uint64_t)(tneg & 0xFFu) << 8);
+}
+
 struct FwdG {
     uint64_t w0, w1; // the 16 code bytes
     float iou;
@@ -179,8 +213,14 @@ struct FwdG {
 };
 
 // Group forward.  Returns false (in every lane of the group) when the pair
-// must take the warp-cooperative robust path.
-__device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
+// must take the warp-cooperative robust path.  raw1, raw2 (refinement on):
+// the pair's input polygons; orientations under the routing threshold then
+// take the FP64 definition's sign (refine_row8), and only an exact zero hands
+// the pair back.  Their FP32 values still place the crossing points, as in
+// the quadrilateral forward.
+template <int KIN = 8>
+__device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out, const float* __restrict__ raw1 = nullptr,
+                                          const float* __restrict__ raw2 = nullptr) {
     const unsigned gm = gmask();
     const int base = gbase();
     const int r = L.r, n1 = L.n1, n2 = L.n2;
@@ -226,8 +266,19 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out) {
         term[j] = fmaf(c, D, s * t) * __fdividef(1.0f, fabsf(D));
     }
     mn = gmin(gm, mn);
-    if (!(Lr > 0.f) || !(mn > thr)) return false;
-    out.degen = (mn <= kDegenRel * Lr * Lr) ? 1u : 0u;
+    if (!(Lr > 0.f)) return false;
+    uint32_t refined = 0u;
+    if (!(mn > thr)) {
+        if (raw1 == nullptr) return false;
+        const uint64_t rr = liveA ? refine_row8(L, raw1, raw2, n1, n2, r, thr, sneg, tneg) : 0ull;
+        if (gor32(gm, (uint32_t)(rr >> 32))) return false;
+        if (liveA) {
+            sneg = (uint32_t)rr & 0xFFu;
+            tneg = (uint32_t)(rr >> 8) & 0xFFu;
+        }
+        refined = 2u;
+    }
+    out.degen = ((mn <= kDegenRel * Lr * Lr) ? 1u : 0u) | refined;
     const uint32_t colv = (1u << n2) - 1u;
     const uint64_t sp = gor64(gm, liveA ? (uint64_t)(~sneg & colv) << (8 * r) : 0ull);
     const uint64_t tp = gor64(gm, liveA ? (uint64_t)(~tneg & colv) << (8 * r) : 0ull);

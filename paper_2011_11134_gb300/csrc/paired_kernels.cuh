@@ -510,7 +510,7 @@ k_paired_fused(const float* __restrict__ p1, const uint8_t* __restrict__ c1, con
 // KIN: the capacity of the stored polygons (8; or 4, quadrilaterals spread
 // over 8 lanes to cut the latency of small batches).
 template <bool SAVE, bool LOSS, bool Z3, bool DEFER = false, int KIN = 8>
-__global__ void __launch_bounds__(kPairThreads)
+__global__ void __launch_bounds__(kPairThreads, 7)
 k_paired_fwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
                 const uint8_t* __restrict__ c2, int64_t n, float* __restrict__ iou, uint8_t* __restrict__ nx,
                 uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status,
@@ -532,7 +532,7 @@ k_paired_fwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
             g8::Lane L;
             g8::load_lane<KIN>(p1 + k * 2 * KIN, p2 + k * 2 * KIN, n1, n2, r, L);
             g8::FwdG o;
-            hard = !g8::fwd_group(L, o);
+            hard = refine ? !g8::fwd_group<KIN>(L, o, p1 + k * 2 * KIN, p2 + k * 2 * KIN) : !g8::fwd_group<KIN>(L, o);
             if constexpr (Z3) {
                 if (!hard && r == 0) o.iou = iou3_value(o.ai, o.a1, o.a2, o.nx, z_of(za, k));
             }
@@ -663,7 +663,8 @@ k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, co
             else g8::load_lane_slim<KIN>(p1 + k * 2 * KIN, p2 + k * 2 * KIN, n1, n2, r, L);
             if constexpr (RECOMPUTE) {
                 g8::FwdG o;
-                needfwd = !g8::fwd_group(L, o);
+                needfwd = refine ? !g8::fwd_group<KIN>(L, o, p1 + k * 2 * KIN, p2 + k * 2 * KIN)
+                                 : !g8::fwd_group<KIN>(L, o);
                 w0 = o.w0;
                 w1 = o.w1;
                 nxk = o.nx;
