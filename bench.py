@@ -543,10 +543,12 @@ def paired_measure(args, workload, n_pairs, with_e2e, with_cpu, use_graph=False)
     flags) + backward (reading them) timed over args.steps steps, the plain
     form timed on the same pairs, parity of a sample against the FP64 oracle,
     and optionally the host-resident call (e2e) and the oracle's own rate
-    (cpu_baseline).  With use_graph the batched step is also captured in a
-    CUDA graph (forward + backward, replayed once per step) and the line's
-    value is the graph's; the eager calls' rate is kept beside it.  Returns
-    the JSON line on rank 0, None on the others."""
+    (cpu_baseline).  With use_graph (small batches) the batched step is also
+    timed captured in a CUDA graph (forward + backward, replayed once per
+    step) and as one dgal_iou_fwd_bwd call (dL/dIoU given up front: one
+    kernel for K = 4); the line's value is the one-call form's, and the
+    graph's and the eager calls' rates are kept beside it.  Returns the JSON
+    line on rank 0, None on the others."""
     import torch
     import torch.distributed as dist
 
@@ -656,6 +658,24 @@ def paired_measure(args, workload, n_pairs, with_e2e, with_cpu, use_graph=False)
         stream.wait_stream(cs)
         torch.cuda.synchronize(dev)
 
+    def onecall():
+        st = lib.dgal_iou_fwd_bwd(L.ptr(p1), L.ptr(c1), L.ptr(p2), L.ptr(c2), L.ptr(grad), n, K, L.ptr(iou), L.ptr(g1),
+                                  L.ptr(g2), L.ptr(nx), L.ptr(xf), FLAGS, sp)
+        assert st == 0, dg.dgal_last_error()
+
+    def timed_one(steps, f):
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+        for _ in range(max(3, args.warmup)):
+            flush.fill_(0)
+            f()
+        for s in range(steps):
+            flush.fill_(s & 0xFF)
+            ev[s][0].record(stream)
+            f()
+            ev[s][1].record(stream)
+        torch.cuda.synchronize(dev)
+        return [ev[s][0].elapsed_time(ev[s][1]) for s in range(steps)]
+
     def timed_graph(steps):
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
         for _ in range(max(3, args.warmup)):
@@ -677,6 +697,7 @@ def paired_measure(args, workload, n_pairs, with_e2e, with_cpu, use_graph=False)
     torch.cuda.synchronize(dev)
     fw, bw = timed(args.steps, fwd, bwd)
     gsteps = timed_graph(args.steps) if graph is not None else None
+    osteps = timed_one(args.steps, onecall) if graph is not None else None  # last: parity reads its outputs
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -684,7 +705,8 @@ def paired_measure(args, workload, n_pairs, with_e2e, with_cpu, use_graph=False)
     step_ms = [a + b for a, b in zip(fw, bw)]
     eager_ms = max_over_ranks(sum(step_ms), dev)
     eager_value = n * world * args.steps / (eager_ms / 1e3)
-    total_ms = max_over_ranks(sum(gsteps), dev) if gsteps is not None else eager_ms
+    graph_ms = max_over_ranks(sum(gsteps), dev) if gsteps is not None else None
+    total_ms = max_over_ranks(sum(osteps), dev) if osteps is not None else eager_ms
     value = n * world * args.steps / (total_ms / 1e3)
 
     # parity of the timed outputs on a sample (FP64 oracle): 20,000 random
@@ -799,11 +821,18 @@ def paired_measure(args, workload, n_pairs, with_e2e, with_cpu, use_graph=False)
         "parity": err,
     }
     if graph is not None:
-        line["form"] = "batched forward + backward captured in one CUDA graph, replayed once per step"
+        graph_value = n * world * args.steps / (graph_ms / 1e3)
+        line["form"] = ("one dgal_iou_fwd_bwd call per step (dL/dIoU = 1 given up front): forward and backward in one "
+                        "kernel, the clip state kept in registers between them")
+        line["graph"] = {"value": graph_value, "unit": UNIT, "ms_per_step": graph_ms / args.steps,
+                         "form": "dgal_iou_paired (flags saved) + dgal_iou_backward (flags read) captured in one CUDA "
+                                 "graph, replayed once per step"}
         line["eager"] = {"value": eager_value, "unit": UNIT, "ms_per_step": eager_ms / args.steps,
                          "form": "the same two calls launched eagerly"}
+        line["gpu_launches"] = args.steps  # the one-call form: one kernel per step
         line["plain"]["batched_over_plain"] = value / plain_value
-        line["plain"]["eager_batched_over_plain"] = eager_value / plain_value
+        line["plain"]["graph_over_plain"] = graph_value / plain_value
+        line["plain"]["eager_over_plain"] = eager_value / plain_value
     return line
 
 
@@ -891,7 +920,7 @@ def other_configs(args):
     c1["roofline"]["note"] = "0.9 MB per step stays in L2: launch/latency-bound, the HBM fraction is not meaningful"
     c1["config"]["paired_shape"] = dg.dgal_get_paired_config(4)
     out["1_rect4096_fwd_bwd"] = _summary(c1) | {"paired_shape": c1["config"]["paired_shape"], "form": c1["form"],
-                                                "eager": c1["eager"]}
+                                                "graph": c1["graph"], "eager": c1["eager"]}
     out["2_pairwise2000_fwd"] = _summary(matrix_measure(args, "pairwise2000", parity=True))
     out["3_ragged64_fwd_graph"] = _summary(matrix_measure(args, "ragged64", parity=True))
     c5 = paired_measure(args, "convex", 0, with_e2e=False, with_cpu=True)

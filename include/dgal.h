@@ -273,6 +273,26 @@ dgal_status dgal_line_intersect_backward(const float* l1, const float* l2, int64
                                          float* grad_l1, float* grad_l2, void* stream);
 
 /*
+ * Forward and backward of the paired IoU in one call, for callers that know
+ * dL/dIoU before the forward (a loss linear in the IoU, or a fixed upstream
+ * gradient): the paper's `iou` and `iou_backward` (Sec. II-B) on the same
+ * pairs.  Arguments as for dgal_iou_paired and dgal_iou_backward, all device
+ * memory: grad_iou float [n] in, iou float [n] and grad_p1, grad_p2 float
+ * [n][K][2] out (overwritten).
+ *   K = 4: one kernel computes both halves, the clip state kept in registers
+ *     between them (no flags are written; nx and xflags may be NULL).  The
+ *     values are those of the two separate calls at one lane per pair (from
+ *     the batch size where those calls take one lane per pair, see
+ *     dgal_autotune class 1, they are bit-identical).
+ *   K = 8: the forward and the backward kernels, with the flags in the
+ *     caller's scratch nx uint8 [n], xflags uint8 [n][16] (16-byte aligned).
+ * Errors as for dgal_iou_paired.
+ */
+dgal_status dgal_iou_fwd_bwd(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2,
+                             const float* grad_iou, int64_t n, int K, float* iou, float* grad_p1, float* grad_p2,
+                             uint8_t* nx, uint8_t* xflags, uint32_t flags, void* stream);
+
+/*
  * Pairwise IoU matrix: the paper's `iou` operation (Sec. II-B: intersect
  * the two convex polygons, take the shoelace areas, IoU = A_I / (A_1 + A_2 -
  * A_I)) applied to every one of the N x M pairs, as a rotated-box detector

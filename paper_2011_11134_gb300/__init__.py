@@ -36,7 +36,7 @@ from ._lib import (DGAL_DEV_BAD_COUNT, DGAL_DEV_BAD_FLAGS, DGAL_DEV_BAD_OFFSETS,
                    DGAL_TEST_EXPIRE_WAIT, DgalError)
 
 __all__ = [
-    "dgal_iou_paired", "dgal_iou_backward", "dgal_iou_pairwise", "dgal_iou_pairwise_batched",
+    "dgal_iou_paired", "dgal_iou_backward", "dgal_iou_fwd_bwd", "dgal_iou_pairwise", "dgal_iou_pairwise_batched",
     "dgal_iou_pairwise_per_scene", "dgal_batched_workspace_bytes", "BatchedGraph", "dgal_autotune",
     "dgal_iou_loss", "dgal_iou_loss_workspace_bytes", "dgal_iou_loss_backward", "dgal_iou3d_loss_backward",
     "IoULoss", "iou_loss", "DGAL_LOSS_GIOU", "DGAL_LOSS_DIOU", "LOSS_VARIANTS", "DGAL_DEV_TIMEOUT",
@@ -111,6 +111,30 @@ def dgal_iou_backward(p1, p2, grad_iou, nx=None, xflags=None, c1=None, c2=None, 
               _lib.ptr(grad_iou), _lib.ptr(nx), _lib.ptr(xflags), _lib.ptr(g1), _lib.ptr(g2), flags,
               _lib.stream_ptr(stream))
     return g1, g2
+
+
+def dgal_iou_fwd_bwd(p1, p2, grad_iou, c1=None, c2=None, flags=DGAL_FP64_REFINE, stream=None):
+    """Forward and backward in one call when dL/dIoU is known up front:
+    returns (iou [n], dL/dp1, dL/dp2 [n, K, 2]).  K = 4 runs one kernel (no
+    flags are stored); K = 8 saves the flags in scratch this call allocates."""
+    _poly(p1, "p1")
+    _poly(p2, "p2")
+    n, K = p1.shape[0], p1.shape[1]
+    if grad_iou.dtype != torch.float32 or grad_iou.shape != (n,) or not grad_iou.is_cuda:
+        raise ValueError("grad_iou must be a CUDA float32 tensor of shape (n,)")
+    grad_iou = grad_iou.contiguous()
+    c1 = _counts(c1, n, "c1", p1.device)
+    c2 = _counts(c2, n, "c2", p1.device)
+    iou = torch.empty(n, device=p1.device, dtype=torch.float32)
+    g1 = torch.empty_like(p1)
+    g2 = torch.empty_like(p2)
+    nx = xf = None
+    if K != 4:
+        nx = torch.empty(n, device=p1.device, dtype=torch.uint8)
+        xf = torch.empty((n, 2 * K), device=p1.device, dtype=torch.uint8)
+    _lib.call("dgal_iou_fwd_bwd", _lib.ptr(p1), _lib.ptr(c1), _lib.ptr(p2), _lib.ptr(c2), _lib.ptr(grad_iou), n, K,
+              _lib.ptr(iou), _lib.ptr(g1), _lib.ptr(g2), _lib.ptr(nx), _lib.ptr(xf), flags, _lib.stream_ptr(stream))
+    return iou, g1, g2
 
 
 def dgal_iou_loss_workspace_bytes(n, K=4):

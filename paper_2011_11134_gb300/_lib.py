@@ -38,6 +38,7 @@ _U32 = ctypes.c_uint32
 _SIG = {
     "dgal_iou_paired": (_I, [_P, _P, _P, _P, _I64, _I, _P, _P, _P, _P, _U32, _P]),
     "dgal_iou_backward": (_I, [_P, _P, _P, _P, _I64, _I, _P, _P, _P, _P, _P, _U32, _P]),
+    "dgal_iou_fwd_bwd": (_I, [_P, _P, _P, _P, _P, _I64, _I, _P, _P, _P, _P, _P, _U32, _P]),
     "dgal_iou_pairwise": (_I, [_P, _P, _I64, _P, _P, _I64, _I, _P, _P, _U32, _P]),
     "dgal_iou_loss_workspace_bytes": (ctypes.c_size_t, [_I64, _I]),
     "dgal_iou_loss": (_I, [_P, _P, _P, _P, _I64, _I, _P, ctypes.c_float, _P, _P, _P, _P, _P, ctypes.c_size_t, _U32, _P]),

@@ -176,6 +176,29 @@ dgal_status dgal_iou_backward(const float* p1, const uint8_t* c1, const float* p
                              (cudaStream_t)stream);
 }
 
+dgal_status dgal_iou_fwd_bwd(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2,
+                             const float* grad_iou, int64_t n, int K, float* iou, float* grad_p1, float* grad_p2,
+                             uint8_t* nx, uint8_t* xflags, uint32_t flags, void* stream) {
+    t_last_error.clear();
+    DGAL_TRY(check_K(K));
+    if (n < 0) return fail(DGAL_ERR_INVALID_ARG, "n = %lld is negative", (long long)n);
+    if (n == 0) return DGAL_OK;
+    DGAL_TRY(check_poly_ptr(p1, "p1"));
+    DGAL_TRY(check_poly_ptr(p2, "p2"));
+    DGAL_TRY(check_poly_ptr(grad_p1, "grad_p1"));
+    DGAL_TRY(check_poly_ptr(grad_p2, "grad_p2"));
+    if (!grad_iou || !iou) return fail(DGAL_ERR_INVALID_ARG, "grad_iou or iou is NULL");
+    if (!aligned(grad_iou, 4) || !aligned(iou, 4)) return fail(DGAL_ERR_ALIGNMENT, "grad_iou or iou is not 4-byte aligned");
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (K == 4) return launch_paired_fused(p1, c1, p2, c2, n, K, grad_iou, iou, grad_p1, grad_p2, flags, s);
+    // K = 8: the forward saves the flags in the caller's scratch, the backward reads them
+    if (!nx || !xflags) return fail(DGAL_ERR_INVALID_ARG, "K = 8 needs nx and xflags scratch");
+    if (!aligned(xflags, 16)) return fail(DGAL_ERR_ALIGNMENT, "xflags is not 16-byte aligned");
+    const dgal_status r = launch_paired_fwd(p1, c1, p2, c2, n, K, iou, nx, xflags, nullptr, flags, s);
+    if (r != DGAL_OK) return r;
+    return launch_paired_bwd(p1, c1, p2, c2, n, K, grad_iou, nx, xflags, grad_p1, grad_p2, flags, s);
+}
+
 dgal_status dgal_iou_pairwise(const float* a, const uint8_t* ca, int64_t N, const float* b, const uint8_t* cb,
                               int64_t M, int K, float* iou, uint8_t* nx, uint32_t flags, void* stream) {
     t_last_error.clear();

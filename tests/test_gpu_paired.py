@@ -377,3 +377,49 @@ def test_paired_launch_shapes_and_tuner(dg, orc, tmp_path):
     path = tmp_path / "default.json"
     path.write_text('{\n  "%s": [1024, 0, 0]\n}\n' % key_dev)
     assert dg.dgal_autotune(4, cache_path=path, config_class=1)["group_below"] == 1024
+
+
+@pytest.mark.parametrize("K,n", [(4, 4096 + 37), (4, 300), (8, 5003)])
+def test_fwd_bwd_one_call(dg, orc, K, n):
+    """dgal_iou_fwd_bwd (dL/dIoU given up front): K = 4 in one kernel, K = 8
+    through the two kernels with caller scratch; the same values as the two
+    separate calls (bit for bit where those take one lane per pair), and the
+    oracle's IoU."""
+    import ctypes
+
+    import torch
+
+    from paper_2011_11134_gb300 import _lib
+
+    if K == 4:
+        d = W.paired_rect_4096(seed=11, n=n)
+        c1 = c2 = None
+    else:
+        d = W.convex_pairs_4m(seed=11, n=n)
+        c1, c2 = dev(d["c1"]), dev(d["c2"])
+    p1, p2 = dev(d["p1"]), dev(d["p2"])
+    grad = torch.linspace(-1.0, 2.0, n, device="cuda")
+    iou, g1, g2 = dg.dgal_iou_fwd_bwd(p1, p2, grad, c1, c2)
+    ri, rnx, rxf, _ = dg.dgal_iou_paired(p1, p2, c1, c2)
+    r1, r2 = dg.dgal_iou_backward(p1, p2, grad, rnx, rxf, c1, c2)
+    torch.cuda.synchronize()
+    if K == 8 or n >= dg.dgal_get_paired_config(4)["group_below"]:
+        assert torch.equal(iou, ri) and torch.equal(g1, r1) and torch.equal(g2, r2)
+    else:
+        m = max(r1.abs().max().item(), r2.abs().max().item())
+        assert (iou - ri).abs().max().item() <= 1e-6
+        assert (g1 - r1).abs().max().item() <= 1e-5 * m and (g2 - r2).abs().max().item() <= 1e-5 * m
+    f = orc.iou_paired(d["p1"], d["p2"], d.get("c1"), d.get("c2"), threads=THREADS)
+    assert np.abs(host(iou) - f["iou"]).max() <= IOU_ATOL
+    assert dg.dgal_get_device_status() == 0
+    # K = 8 without flag scratch is refused before any launch
+    if K == 8:
+        lib = _lib.lib()
+        st = lib.dgal_iou_fwd_bwd(_lib.ptr(p1), _lib.ptr(c1), _lib.ptr(p2), _lib.ptr(c2), _lib.ptr(grad), n, K,
+                                  _lib.ptr(iou), _lib.ptr(g1), _lib.ptr(g2), None, None, dg.DGAL_FP64_REFINE,
+                                  _lib.stream_ptr(None))
+        assert st != 0 and "scratch" in dg.dgal_last_error()
+    # nothing to do
+    z = torch.zeros((0, K, 2), device="cuda")
+    e = dg.dgal_iou_fwd_bwd(z, z, torch.zeros(0, device="cuda"))
+    assert e[0].numel() == 0
