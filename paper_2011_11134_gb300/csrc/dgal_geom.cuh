@@ -1585,11 +1585,15 @@ __device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, Adj& adj, uint32_
     // crossing, and one with two crossings runs from the smaller t to the
     // larger; so min / max over the crossings of the edge give the piece
     // without looking at orientation signs.  Off the crossing set the
-    // parameters are NaN, which fminf / fmaxf ignore.
-    const float kInf = __int_as_float(0x7f800000), kNaN = __int_as_float(0x7fffffff);
+    // parameters are NaN, which fminf / fmaxf ignore.  The reductions start at
+    // t0 = 1, t1 = 0: a crossing's parameter lies in (0, 1), so the start
+    // values do not change the min / max over crossings, and an edge with no
+    // piece (no crossing, neither end inside) keeps an empty interval whose
+    // length max(t1 - t0, 0) is 0, so every term it would add is 0.
+    const float kNaN = __int_as_float(0x7fffffff);
     float t0[K], t1[K], u0[K], u1[K];
 #pragma unroll
-    for (int v = 0; v < K; ++v) { t0[v] = kInf; t1[v] = -kInf; u0[v] = kInf; u1[v] = -kInf; }
+    for (int v = 0; v < K; ++v) { t0[v] = 1.f; t1[v] = 0.f; u0[v] = 1.f; u1[v] = 0.f; }
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         float tr[K]; // row i's parameters, reduced after the row
@@ -1612,17 +1616,19 @@ __device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, Adj& adj, uint32_
             t1[i] = fmax3(t1[i], tr[j], tr[j + 1]);
         }
     }
-    // Edges without a piece get [0, 0]: every term they would add is then 0.
+    // an inside start vertex opens its edge's piece at 0, an inside end
+    // vertex closes it at 1
     const float L = pair_scale<K, COUNTS>(g);
+    float dta[K], dtb[K]; // piece lengths
 #pragma unroll
     for (int v = 0; v < K; ++v) {
         const uint32_t na = (v + 1 < (int)n1m) ? (uint32_t)(v + 1) : 0u, nb = (v + 1 < (int)n2m) ? (uint32_t)(v + 1) : 0u;
-        const bool pa = ((in1 >> v) & 1u) || ((X >> (v * K)) & kRow0);
-        const bool pb = ((in2 >> v) & 1u) || ((X >> v) & col0);
-        t0[v] = pa ? (((in1 >> v) & 1u) ? 0.f : t0[v]) : 0.f;
-        t1[v] = pa ? (((in1 >> na) & 1u) ? 1.f : t1[v]) : 0.f;
-        u0[v] = pb ? (((in2 >> v) & 1u) ? 0.f : u0[v]) : 0.f;
-        u1[v] = pb ? (((in2 >> nb) & 1u) ? 1.f : u1[v]) : 0.f;
+        t0[v] = ((in1 >> v) & 1u) ? 0.f : t0[v];
+        t1[v] = ((in1 >> na) & 1u) ? 1.f : t1[v];
+        u0[v] = ((in2 >> v) & 1u) ? 0.f : u0[v];
+        u1[v] = ((in2 >> nb) & 1u) ? 1.f : u1[v];
+        dta[v] = fmaxf(t1[v] - t0[v], 0.f);
+        dtb[v] = fmaxf(u1[v] - u0[v], 0.f);
     }
     float twoA = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
@@ -1631,8 +1637,8 @@ __device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, Adj& adj, uint32_
         const float c2 = g.bx[v] * g.eby[v] - g.by[v] * g.ebx[v];
         s1 += (!COUNTS || v < n1) ? c1 : 0.f;
         s2 += (!COUNTS || v < n2) ? c2 : 0.f;
-        twoA = fmaf(t1[v] - t0[v], c1, twoA);
-        twoA = fmaf(u1[v] - u0[v], c2, twoA);
+        twoA = fmaf(dta[v], c1, twoA);
+        twoA = fmaf(dtb[v], c2, twoA);
     }
     const float a1 = 0.5f * s1, a2 = 0.5f * s2, ai = 0.5f * twoA;
     if (refine && !empty && ai < kTinyArea * L * L) return kSlow;
@@ -1647,8 +1653,8 @@ __device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, Adj& adj, uint32_
     float sx1[K], sy1[K], ex1[K], ey1[K], sx2[K], sy2[K], ex2[K], ey2[K];
 #pragma unroll
     for (int v = 0; v < K; ++v) {
-        const float da = hg * (t1[v] - t0[v]), sa = t1[v] + t0[v];
-        const float db = hg * (u1[v] - u0[v]), sb = u1[v] + u0[v];
+        const float da = hg * dta[v], sa = t1[v] + t0[v];
+        const float db = hg * dtb[v], sb = u1[v] + u0[v];
         const float wsa = fmaf(da, 2.f - sa, h1), wea = fmaf(da, sa, h1);
         const float wsb = fmaf(db, 2.f - sb, h2), web = fmaf(db, sb, h2);
         sx1[v] = wsa * g.eay[v];
