@@ -1594,6 +1594,10 @@ __device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, Adj& adj, uint32_
     float t0[K], t1[K], u0[K], u1[K];
 #pragma unroll
     for (int v = 0; v < K; ++v) { t0[v] = 1.f; t1[v] = 0.f; u0[v] = 1.f; u1[v] = 0.f; }
+    // rows are taken two at a time, so that each column's min / max folds
+    // two rows per three-operand instruction
+    static_assert(K % 2 == 0, "an even capacity");
+    float up[K]; // the previous (even) row's u parameters
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         float tr[K]; // row i's parameters, reduced after the row
@@ -1607,8 +1611,12 @@ __device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, Adj& adj, uint32_
             const float rD = m ? __fdividef(1.0f, D) : kNaN;
             const float u = -T * rD;
             tr[j] = S * rD;
-            u0[j] = fminf(u0[j], u);
-            u1[j] = fmaxf(u1[j], u);
+            if (i & 1) {
+                u0[j] = fmin3(u0[j], up[j], u);
+                u1[j] = fmax3(u1[j], up[j], u);
+            } else {
+                up[j] = u;
+            }
         }
 #pragma unroll
         for (int j = 0; j + 1 < K; j += 2) {
