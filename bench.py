@@ -369,6 +369,28 @@ def fused_workload(args):
         ev[s_][1].record(stream)
     torch.cuda.synchronize(dev)
     ms_unfused = statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
+    # the GIoU and DIoU forms of the same loss (one more kernel in each pass:
+    # the hull / centre / diameter terms)
+    variants = {}
+    for name, bit in (("giou", dg.DGAL_LOSS_GIOU), ("diou", dg.DGAL_LOSS_DIOU)):
+        vargs = loss_args[:-2] + (dg.DGAL_FP64_REFINE | bit, sp)
+
+        def vrun():
+            st = lib.dgal_iou_loss(*vargs)
+            assert st == 0, dg.dgal_last_error()
+
+        for _ in range(args.warmup):
+            vrun()
+        torch.cuda.synchronize(dev)
+        for s_ in range(args.steps):
+            flush.fill_(s_ & 0xFF)
+            ev[s_][0].record(stream)
+            vrun()
+            ev[s_][1].record(stream)
+        torch.cuda.synchronize(dev)
+        vms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
+        variants[name] = {"value": n / (vms * 1e-3), "unit": UNIT, "ms_per_step": vms,
+                          "loss": float(out[0].item()), "gpu_launches_per_step": 4}
     peaks = _peaks()
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
     # forward: polygons 64 B + flags 9 B out; backward: polygons 64 B + flags
@@ -385,6 +407,7 @@ def fused_workload(args):
                      "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "alg_bytes_per_pair": alg},
         "unfused": {"value": n / (ms_unfused * 1e-3), "unit": UNIT, "ms_per_step": ms_unfused,
                     "what": "dgal_iou_paired + torch sum + dgal_iou_backward"},
+        "variants": variants,
         "gpu_launches": 2 * args.steps, "clocks": clocks,  # forward, backward (with the partial sum in its block 0)
     }
     print(json.dumps(line), flush=True)
@@ -838,7 +861,7 @@ def paired_measure(args, workload, n_pairs, with_e2e, with_cpu, use_graph=False)
 
 # DRAM bytes per pair of the K = 4 paired kernels (forward saving the flags,
 # backward reading them), measured by ncu on 4,000,000 IoU-loss pairs
-DRAM_BYTES_PER_PAIR_K4 = {"forward": 73.86, "backward": 129.93}
+DRAM_BYTES_PER_PAIR_K4 = {"forward": 73.89, "backward": 129.64}
 
 # FP32 non-tensor peak of GB300, derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
