@@ -60,13 +60,6 @@ __device__ __forceinline__ float gmin(unsigned m, float v) {
     return v;
 }
 
-__device__ __forceinline__ float sel8(const float (&v)[8], uint32_t i) {
-    float r = v[0];
-#pragma unroll
-    for (int m = 1; m < 8; ++m) r = (i == (uint32_t)m) ? v[m] : r;
-    return r;
-}
-
 // Lane view of a pair: own P1 vertex / edge, all of P2, in P1's local frame.
 struct Lane {
     float ax, ay, eax, eay;
@@ -375,7 +368,10 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out, const float*
     }
     const uint32_t total = __shfl_sync(gm, off, base + 7);
     off -= len;
-    const uint32_t qall = gor32(gm, qm);
+    // one group OR for the P2 chain marks (8 bits) and the lane's own checks
+    const uint32_t qb = gor32(gm, qm | (bad ? 0x100u : 0u));
+    const uint32_t qall = qb & 0xFFu;
+    bool bad_g = (qb >> 8) != 0u; // group-uniform from here on
     uint64_t s_lo = 0, s_hi = 0;
     if (len) {
         if (off == 0) {
@@ -393,15 +389,15 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out, const float*
     const bool q_inside = X == 0 && in1 == 0;
     if (q_inside) {
         // P2 inside P1: the intersection is P2
-        bad |= in2 != ((1u << n2) - 1u);
+        bad_g |= in2 != ((1u << n2) - 1u);
         s_lo = 0;
 #pragma unroll
         for (int j = 0; j < 8; ++j) s_lo |= (j < n2) ? ((uint64_t)(0x40u | j) << (8 * j)) : 0ull;
         s_hi = 0;
     } else {
-        bad |= total != cnt || qall != in2;
+        bad_g |= total != cnt || qall != in2;
     }
-    if (gor32(gm, bad ? 1u : 0u)) return false;
+    if (bad_g) return false;
     uint32_t start;
     if (in1) start = (uint32_t)(__ffs(in1) - 1);
     else if (in2) start = 0x40u | (uint32_t)(__ffs(in2) - 1);
@@ -455,16 +451,19 @@ __device__ __forceinline__ uint32_t bwd_group(const LaneT& L, Adj& adj, uint32_t
         const uint32_t k = (uint32_t)r + 8u * h;
         const uint32_t c = (uint32_t)(((h ? w1 : w0) >> (8 * r)) & 0xFFull);
         const bool live = !empty && k < nx;
-        const uint32_t kind = c >> 6, lo = c & 7u, ci = (c >> 3) & 7u;
-        in1 |= (live && kind == 0u) ? (1u << (c & 0x1Fu)) : 0u;
-        in2 |= (live && kind == 1u) ? (1u << (c & 0x1Fu)) : 0u;
+        const uint32_t kind = c >> 6, lo = c & 7u, ci = (c >> 3) & 7u, v = c & 0x3Fu;
+        in1 |= (live && kind == 0u && v < 8u) ? (1u << v) : 0u;
+        in2 |= (live && kind == 1u && v < 8u) ? (1u << v) : 0u;
         X |= (live && kind == 2u) ? (1ull << (ci * 8 + lo)) : 0ull;
-        other |= (live && (kind == 3u || (kind == 2u && (ci >= (uint32_t)n1 || lo >= (uint32_t)n2)))) ? 1u : 0u;
+        other |= (live && (kind == 3u || (kind < 2u && v >= 8u) ||
+                           (kind == 2u && (ci >= (uint32_t)n1 || lo >= (uint32_t)n2)))) ? 1u : 0u;
     }
-    in1 = gor32(gm, in1);
-    in2 = gor32(gm, in2);
+    // one group OR for the three small masks (8 + 8 + 1 bits)
+    const uint32_t pk = gor32(gm, in1 | (in2 << 8) | (other << 16));
+    in1 = pk & 0xFFu;
+    in2 = (pk >> 8) & 0xFFu;
+    other = pk >> 16;
     X = gor64(gm, X);
-    other = gor32(gm, other);
     if (other || (in1 >> n1) || (in2 >> n2)) return kDevBadFlags;
     const uint64_t col0 = col0_mask();
     const uint32_t rn1 = (r + 1 < n1) ? (uint32_t)(r + 1) : 0u, rn2 = (r + 1 < n2) ? (uint32_t)(r + 1) : 0u;
