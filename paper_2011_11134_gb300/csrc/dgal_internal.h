@@ -94,10 +94,11 @@ dgal_status launch_iou3d_loss_backward(const float* p1, const uint8_t* c1, const
 int64_t loss_var_partials(int64_t n);
 dgal_status launch_loss_var_fwd(int variant, const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2,
                                 int64_t n, int K, const float* weight, float scale, const float* u, float* ah,
-                                float* partials, cudaStream_t s);
+                                uint64_t* aux, float* partials, cudaStream_t s);
 dgal_status launch_loss_var_bwd(int variant, const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2,
                                 int64_t n, int K, const float* weight, float scale, const float* dloss, const float* u,
-                                const float* ah, float* g1, float* g2, cudaStream_t s);
+                                const float* ah, const uint64_t* aux, float* g1, float* g2,
+                                cudaStream_t s);
 dgal_status launch_batched(int S, const int64_t* a_off, const int64_t* b_off, const int64_t* out_off,
                            const float* a, const uint8_t* ca, const float* b, const uint8_t* cb, int K, float* iou,
                            uint8_t* nx, void* ws, uint32_t flags, const BatchedConfig& cfg, cudaStream_t s);

@@ -14,7 +14,8 @@
 // dependence of -U / A_h on the three areas).  The backward pass here adds
 // the remaining terms to the gradients: for GIoU the hull area's shoelace
 // adjoint times scale w dloss U / A_h^2, for DIoU the adjoints of rho2 and
-// c2.  A pair with U <= 0 has no extra term (and no gradient), as its IoU.
+// c2.  The forward keeps the hull's vertex order per pair (GIoU), so the
+// backward does not wrap the points again.  A pair with U <= 0 has no extra term (and no gradient), as its IoU.
 //
 // One thread per pair.  The n1 + n2 points sit in shared memory (point v of
 // thread t at v * blockDim + t, so a warp's reads of one point index are
@@ -97,9 +98,13 @@ __device__ __forceinline__ float hull(const VarPts<K>& s, int m, uint64_t& order
                 continue;
             }
             const float o = (nx_ - xc) * (yr - yc) - (ny_ - yc) * (xr - xc);
-            const float dr = (xr - xc) * (xr - xc) + (yr - yc) * (yr - yc);
-            const float dn = (nx_ - xc) * (nx_ - xc) + (ny_ - yc) * (ny_ - yc);
-            if (o < 0.f || (o == 0.f && dr > dn)) {
+            bool take = o < 0.f;
+            if (o == 0.f) { // collinear with the candidate: the farther one
+                const float dr = (xr - xc) * (xr - xc) + (yr - yc) * (yr - yc);
+                const float dn = (nx_ - xc) * (nx_ - xc) + (ny_ - yc) * (ny_ - yc);
+                take = dr > dn;
+            }
+            if (take) {
                 nxt = r;
                 nx_ = xr;
                 ny_ = yr;
@@ -116,11 +121,10 @@ __device__ __forceinline__ float hull(const VarPts<K>& s, int m, uint64_t& order
     return area2;
 }
 
-// Vertex means' squared distance and the squared diameter (first largest pair).
+// Vertex means' difference (dmx, dmy) and its squared length rho2.
 template <int K>
-__device__ __forceinline__ void centre_diameter(const VarPts<K>& s, int n1, int n2, float& rho2, float& dmx,
-                                                float& dmy, float& c2, int& da, int& db) {
-    const int t = threadIdx.x, m = n1 + n2;
+__device__ __forceinline__ void centre(const VarPts<K>& s, int n1, int n2, float& rho2, float& dmx, float& dmy) {
+    const int t = threadIdx.x;
     float sx1 = 0.f, sy1 = 0.f, sx2 = 0.f, sy2 = 0.f;
     for (int v = 0; v < n1; ++v) {
         sx1 += s.x[v][t];
@@ -133,13 +137,22 @@ __device__ __forceinline__ void centre_diameter(const VarPts<K>& s, int n1, int 
     dmx = sx1 / (float)n1 - sx2 / (float)n2;
     dmy = sy1 / (float)n1 - sy2 / (float)n2;
     rho2 = dmx * dmx + dmy * dmy;
+}
+
+// Squared distance of points a and b.
+template <int K> __device__ __forceinline__ float dist2(const VarPts<K>& s, int a, int b) {
+    const int t = threadIdx.x;
+    const float dx = s.x[a][t] - s.x[b][t], dy = s.y[a][t] - s.y[b][t];
+    return dx * dx + dy * dy;
+}
+
+// The squared diameter of the m points (the first largest pair in index order).
+template <int K> __device__ __forceinline__ void diameter(const VarPts<K>& s, int m, float& c2, int& da, int& db) {
     c2 = -1.f;
     da = db = 0;
     for (int a = 0; a < m; ++a) {
-        const float xa = s.x[a][t], ya = s.y[a][t];
         for (int b = a + 1; b < m; ++b) {
-            const float dx = xa - s.x[b][t], dy = ya - s.y[b][t];
-            const float d = dx * dx + dy * dy;
+            const float d = dist2<K>(s, a, b);
             if (d > c2) {
                 c2 = d;
                 da = a;
@@ -151,12 +164,16 @@ __device__ __forceinline__ void centre_diameter(const VarPts<K>& s, int n1, int 
 
 // VAR 1: GIoU, 2: DIoU.  u: U per pair from the IoU forward; ah (GIoU):
 // receives A_h per pair (+inf when the hull has no area, so that the IoU
-// backward adds nothing).
+// backward adds nothing); aux (GIoU): two words per pair for the backward,
+// the hull order (4 bits a point) and its count, so that the backward does
+// not wrap the points again.  (DIoU's diameter search over at most 120 point
+// pairs costs less than storing and reloading its result: measured.)
 template <int K, int VAR>
 __global__ void __launch_bounds__(kVarThreads)
 k_loss_var_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
                const uint8_t* __restrict__ c2, int64_t n, const float* __restrict__ weight, float scale,
-               const float* __restrict__ u, float* __restrict__ ah, float* __restrict__ partials) {
+               const float* __restrict__ u, float* __restrict__ ah, uint64_t* __restrict__ aux,
+               float* __restrict__ partials) {
     __shared__ VarPts<K> s;
     float acc = 0.f;
     const int64_t stride = (int64_t)gridDim.x * kVarThreads;
@@ -171,6 +188,8 @@ k_loss_var_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, con
                 uint64_t order;
                 int h;
                 A = 0.5f * hull<K>(s, m, order, h);
+                aux[2 * k] = order;
+                aux[2 * k + 1] = (uint64_t)h;
             }
             const bool use = m && U > 0.f && A > 0.f;
             if (use) acc += sw * (1.f - U / A);
@@ -179,7 +198,8 @@ k_loss_var_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, con
             if (m && U > 0.f) {
                 float rho2, dmx, dmy, c2v;
                 int da, db;
-                centre_diameter<K>(s, n1, n2, rho2, dmx, dmy, c2v, da, db);
+                centre<K>(s, n1, n2, rho2, dmx, dmy);
+                diameter<K>(s, m, c2v, da, db);
                 if (c2v > 0.f) acc += sw * (rho2 / c2v);
             }
         }
@@ -196,7 +216,7 @@ __global__ void __launch_bounds__(kVarThreads)
 k_loss_var_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
                const uint8_t* __restrict__ c2, int64_t n, const float* __restrict__ weight, float scale,
                const float* __restrict__ dloss, const float* __restrict__ u, const float* __restrict__ ah,
-               float* __restrict__ g1, float* __restrict__ g2) {
+               const uint64_t* __restrict__ aux, float* __restrict__ g1, float* __restrict__ g2) {
     __shared__ VarPts<K> s;
     __shared__ float gx[2 * K][kVarThreads], gy[2 * K][kVarThreads];
     const int t = threadIdx.x;
@@ -213,9 +233,8 @@ k_loss_var_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, con
         if constexpr (VAR == 1) {
             const float A = __ldg(ah + k);
             if (A > 0.f && A < __int_as_float(0x7f800000)) {
-                uint64_t order;
-                int h;
-                hull<K>(s, m, order, h);
+                const uint64_t order = __ldg(aux + 2 * k);
+                const int h = (int)__ldg(aux + 2 * k + 1);
                 const float gh = sw * U / (A * A);
                 for (int q = 0; q < h; ++q) {
                     const int c = (int)((order >> (4 * q)) & 15u);
@@ -227,9 +246,11 @@ k_loss_var_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, con
                 any = h >= 3;
             }
         } else {
-            float rho2, dmx, dmy, c2v;
+            float rho2, dmx, dmy;
+            centre<K>(s, n1, n2, rho2, dmx, dmy);
+            float c2v;
             int da, db;
-            centre_diameter<K>(s, n1, n2, rho2, dmx, dmy, c2v, da, db);
+            diameter<K>(s, m, c2v, da, db);
             if (c2v > 0.f) {
                 const float gr = sw / c2v, gc = -sw * rho2 / (c2v * c2v);
                 const float ax = 2.f * gr * dmx / (float)n1, ay = 2.f * gr * dmy / (float)n1;
@@ -281,32 +302,32 @@ int64_t loss_var_partials(int64_t n) { return (int64_t)var_grid(n) * (kVarThread
 
 dgal_status launch_loss_var_fwd(int variant, const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2,
                                 int64_t n, int K, const float* weight, float scale, const float* u, float* ah,
-                                float* partials, cudaStream_t s) {
+                                uint64_t* aux, float* partials, cudaStream_t s) {
     const unsigned grid = var_grid(n);
     if (K == 4) {
-        if (variant == 1) k_loss_var_fwd<4, 1><<<grid, kVarThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, u, ah, partials);
-        else k_loss_var_fwd<4, 2><<<grid, kVarThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, u, ah, partials);
+        if (variant == 1) k_loss_var_fwd<4, 1><<<grid, kVarThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, u, ah, aux, partials);
+        else k_loss_var_fwd<4, 2><<<grid, kVarThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, u, ah, aux, partials);
     } else {
-        if (variant == 1) k_loss_var_fwd<8, 1><<<grid, kVarThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, u, ah, partials);
-        else k_loss_var_fwd<8, 2><<<grid, kVarThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, u, ah, partials);
+        if (variant == 1) k_loss_var_fwd<8, 1><<<grid, kVarThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, u, ah, aux, partials);
+        else k_loss_var_fwd<8, 2><<<grid, kVarThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, u, ah, aux, partials);
     }
     return check_launch("GIoU / DIoU forward");
 }
 
 dgal_status launch_loss_var_bwd(int variant, const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2,
                                 int64_t n, int K, const float* weight, float scale, const float* dloss, const float* u,
-                                const float* ah, float* g1, float* g2, cudaStream_t s) {
+                                const float* ah, const uint64_t* aux, float* g1, float* g2, cudaStream_t s) {
     const unsigned grid = var_grid(n);
     if (K == 4) {
         if (variant == 1)
-            k_loss_var_bwd<4, 1><<<grid, kVarThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, dloss, u, ah, g1, g2);
+            k_loss_var_bwd<4, 1><<<grid, kVarThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, dloss, u, ah, aux, g1, g2);
         else
-            k_loss_var_bwd<4, 2><<<grid, kVarThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, dloss, u, ah, g1, g2);
+            k_loss_var_bwd<4, 2><<<grid, kVarThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, dloss, u, ah, aux, g1, g2);
     } else {
         if (variant == 1)
-            k_loss_var_bwd<8, 1><<<grid, kVarThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, dloss, u, ah, g1, g2);
+            k_loss_var_bwd<8, 1><<<grid, kVarThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, dloss, u, ah, aux, g1, g2);
         else
-            k_loss_var_bwd<8, 2><<<grid, kVarThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, dloss, u, ah, g1, g2);
+            k_loss_var_bwd<8, 2><<<grid, kVarThreads, 0, s>>>(p1, c1, p2, c2, n, weight, scale, dloss, u, ah, aux, g1, g2);
     }
     return check_launch("GIoU / DIoU backward");
 }

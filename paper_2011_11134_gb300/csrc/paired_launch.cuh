@@ -127,10 +127,11 @@ static void bwd_any(const float* p1, const uint8_t* c1, const float* p2, const u
 // the registers and stalls on instruction fetch.
 
 // Loss workspace: [per-warp partials | partials of the GIoU / DIoU terms |
-// U per pair | A_h per pair | nx (n bytes) | xflags (n x 2K bytes)], each
+// U per pair | A_h per pair | GIoU hull order and count (16 bytes a pair) |
+// nx (n bytes) | xflags (n x 2K bytes)], each
 // part 256-byte aligned.
 struct LossLayout {
-    size_t partials, partials2, u, ah, nx, xflags, total;
+    size_t partials, partials2, u, ah, aux, nx, xflags, total;
     int64_t warps, warps2;
 };
 
@@ -144,7 +145,8 @@ static LossLayout loss_layout(int64_t n, int K) {
     L.partials2 = up((size_t)L.warps * 4);
     L.u = L.partials2 + up((size_t)L.warps2 * 4);
     L.ah = L.u + up((size_t)n * 4);
-    L.nx = L.ah + up((size_t)n * 4);
+    L.aux = L.ah + up((size_t)n * 4);
+    L.nx = L.aux + up((size_t)n * 16);
     L.xflags = L.nx + up((size_t)n);
     L.total = L.xflags + up((size_t)n * 2 * K);
     return L;
@@ -176,7 +178,8 @@ static dgal_status iou_loss_forward(const float* p1, const uint8_t* c1, const fl
     float* partials2 = reinterpret_cast<float*>(base + L.partials2);
     if (var) {
         r = launch_loss_var_fwd(var, p1, c1, p2, c2, n, K, weight, scale, la.u_out,
-                                reinterpret_cast<float*>(base + L.ah), partials2, s);
+                                reinterpret_cast<float*>(base + L.ah), reinterpret_cast<uint64_t*>(base + L.aux),
+                                partials2, s);
         if (r != DGAL_OK) return r;
     }
     if (!fold) return DGAL_OK;
@@ -210,7 +213,7 @@ static dgal_status iou_loss_backward(const float* p1, const uint8_t* c1, const f
     if (r != DGAL_OK || !var) return r;
     return launch_loss_var_bwd(var, p1, c1, p2, c2, n, K, weight, scale, dloss,
                                reinterpret_cast<const float*>(base + L.u), reinterpret_cast<const float*>(base + L.ah),
-                               g1, g2, s);
+                               reinterpret_cast<const uint64_t*>(base + L.aux), g1, g2, s);
 }
 
 // The loss and (when g1 is set) its gradient in one call.
