@@ -212,14 +212,20 @@ __device__ __forceinline__ void put_fwd(const FwdOut<K>& o, int64_t k, float w, 
     if (degen) degen[k] = (uint8_t)o.degen;
 }
 
-// Minimum resident blocks per SM of the K = 4 paired kernels (a register
-// cap).  Both are issue-bound at 14-17 resident warps; 6 blocks (24 warps, 80
-// registers, a few spilled values) measured fastest on the 1M-pair step
-// (forward 44.1 us, backward 49.1 us, against 44.6 / 51.4 at 5 blocks).  The
-// backward that recomputes the clip carries the forward's code as well and
-// keeps 4 blocks (128 registers).
-constexpr int kFwdMinBlocks = 6;
+// Minimum resident blocks per SM of the paired kernels (a register cap),
+// each measured on its workload's step.  K = 4: the forward at 7 blocks (72
+// registers) and the backward at 6 (80 registers) were fastest; the
+// backward lost 2 and 4 us at 7 and 8 blocks, and 5 blocks were slower for
+// both.  The backward that recomputes the clip carries the forward's code as
+// well and keeps 4 blocks (128 registers).
+constexpr int kFwdMinBlocks = 7;
 constexpr int kBwdMinBlocks = 6;
+// the K = 8 group forward: 8 blocks of 128 per SM (64 registers), measured
+// faster than 5 to 7
+constexpr int kFwdG8MinBlocks = 8;
+// the K = 8 group backward: 10 blocks of 128 per SM (48 registers) measured
+// faster than 5 to 8 or 12, despite its spills (on the rare paths)
+constexpr int kBwdG8MinBlocks = 10;
 
 template <int K, bool COUNTS, bool SAVE, bool LOSS, bool Z3>
 __global__ void __launch_bounds__(kPairThreads, kFwdMinBlocks)
@@ -510,7 +516,7 @@ k_paired_fused(const float* __restrict__ p1, const uint8_t* __restrict__ c1, con
 // KIN: the capacity of the stored polygons (8; or 4, quadrilaterals spread
 // over 8 lanes to cut the latency of small batches).
 template <bool SAVE, bool LOSS, bool Z3, bool DEFER = false, int KIN = 8>
-__global__ void __launch_bounds__(kPairThreads, 7)
+__global__ void __launch_bounds__(kPairThreads, kFwdG8MinBlocks)
 k_paired_fwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
                 const uint8_t* __restrict__ c2, int64_t n, float* __restrict__ iou, uint8_t* __restrict__ nx,
                 uint8_t* __restrict__ xflags, uint8_t* __restrict__ degen, uint32_t flags, uint32_t* status,
@@ -634,7 +640,7 @@ k_paired_fwd_finish(const float* __restrict__ p1, const uint8_t* __restrict__ c1
 }
 
 template <bool RECOMPUTE, bool LOSS, bool Z3, int KIN = 8>
-__global__ void __launch_bounds__(kPairThreads, RECOMPUTE ? 1 : kBwdMinBlocks)
+__global__ void __launch_bounds__(kPairThreads, RECOMPUTE ? 1 : kBwdG8MinBlocks)
 k_paired_bwd_g8(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const float* __restrict__ p2,
                 const uint8_t* __restrict__ c2, int64_t n, const float* __restrict__ grad,
                 const uint8_t* __restrict__ nxs, const uint8_t* __restrict__ xflags, float* __restrict__ g1,
