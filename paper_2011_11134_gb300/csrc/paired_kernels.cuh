@@ -224,7 +224,7 @@ constexpr int kBwdMinBlocks = 6;
 // faster than 5 to 7
 constexpr int kFwdG8MinBlocks = 8;
 // the K = 8 group backward: 10 blocks of 128 per SM (48 registers) measured
-// faster than 5 to 8 or 12, despite its spills (on the rare paths)
+// faster than 5 to 8 or 12, despite the register spills it brings
 constexpr int kBwdG8MinBlocks = 10;
 
 template <int K, bool COUNTS, bool SAVE, bool LOSS, bool Z3>
