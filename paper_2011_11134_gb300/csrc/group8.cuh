@@ -10,7 +10,9 @@
 // Forward (paper Sec. II-B `iou`): lane r computes row r of the orientation
 // tables, S(r,j) = orient(b_j, b_j+1, a_r) and T(r,j) = orient(a_r, a_r+1, b_j);
 // the rows are OR-combined into 64-bit sign masks, after which every lane
-// knows the inside vertices and the crossings (as in fwd_generic).  The area
+// knows the inside vertices and the crossings (as in fwd_generic); with
+// refinement, orientations under the routing threshold first take the FP64
+// definition's sign in their own lane's row (refine_row8).  The area
 // is fwd_generic's select-free sum: lane r adds P1 edge r's vertex term and
 // its row of crossing terms, a group sum adds them up.  Lane r also builds
 // its chunk of the counter-clockwise vertex order: vertex r if inside, the

@@ -47,16 +47,18 @@ template <int K> __device__ __forceinline__ void store_poly(float* __restrict__ 
     for (int v = 0; v < K / 2; ++v) q[v] = make_float4(x[2 * v], y[2 * v], x[2 * v + 1], y[2 * v + 1]);
 }
 
-// Both kernels walk the pairs warp by warp (32 consecutive pairs per warp and
-// step, grid-stride over warps), with no block-wide barrier.  In the forward,
-// a pair the fast path cannot finish (near-degenerate or not in general
-// position, well under 0.1% of random boxes) is finished right after the
+// The K = 4 kernels walk the pairs warp by warp (32 consecutive pairs per
+// warp and step, grid-stride over warps), with no block-wide barrier.  In the
+// forward, a pair the fast path cannot finish (an exactly zero orientation,
+// a sign pattern two convex polygons in general position cannot have, or a
+// thin pair; well under 0.1% of random boxes) is finished right after the
 // step by the whole warp (warp_robust, a non-inlined call, so its registers
-// and slow-path code stay off the common path); the SM keeps issuing from its other
-// warps meanwhile.  In the backward, a pair whose codes the shape derivative
-// cannot take (not in general position, or with refinement a tiny
+// and slow-path code stay off the common path); the SM keeps issuing from its
+// other warps meanwhile.  In the backward, a pair whose codes the shape
+// derivative cannot take (not in general position, or with refinement a tiny
 // intersection) takes the shoelace adjoint after the rest, with the whole
-// warp on it (warp_bwd).
+// warp on it (warp_bwd).  The K = 8 group forward instead marks such pairs
+// and leaves them to a launch of their own (k_paired_fwd_finish).
 
 // IoU-loss mode of the paired kernels (paper Sec. IV-A, the IoU loss over
 // rotated boxes): the forward adds scale * w_k (1 - IoU_k) into one partial
