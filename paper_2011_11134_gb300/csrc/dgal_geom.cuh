@@ -125,6 +125,66 @@ __device__ __forceinline__ uint32_t push_sign(uint32_t acc, float v) {
     return __funnelshift_l(__float_as_uint(v), acc, 1);
 }
 
+// Packed FP32 pairs (sm_100 and later): one instruction rounds two
+// independent FP32 results, each exactly as the scalar add / sub / mul / fma
+// would.  The pair loops below use them to form two columns (j, j + 1) of a
+// row at a time, halving the issue slots of the orientation arithmetic.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pb, {%4, %5};\n\t"
+        "sub.rn.f32x2 pd, pa, pb;\n\t"
+        "mov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+// P2 operands of edges j, j + 1 (lane x: edge j, lane y: edge j + 1).
+struct ColPair {
+    float2 bx, by, ebx, eby;
+};
+template <int K> __device__ __forceinline__ ColPair col_pair(const float (&bx)[K], const float (&by)[K],
+                                                             const float (&ebx)[K], const float (&eby)[K], int h) {
+    const int j = 2 * h;
+    ColPair c;
+    c.bx = f2(bx[j], bx[j + 1]);
+    c.by = f2(by[j], by[j + 1]);
+    c.ebx = f2(ebx[j], ebx[j + 1]);
+    c.eby = f2(eby[j], eby[j + 1]);
+    return c;
+}
+
+// One vertex-edge block for the two P2 edges of q against P1 vertex / edge i:
+//   S  = orient(b_j, b_j+1, a_i)  = ebx_j dy + eby_j mx,
+//   nT = -orient(a_i, a_i+1, b_j) = eax_i dy + eay_i mx,
+//   D  = cross(ea_i, eb_j)        = eax_i eby_j - eay_i ebx_j,
+//   nc = -cross(a_i, b_j)         = ay_i bx_j - ax_i by_j,
+// with mx = bx_j - ax_i and dy = ay_i - by_j (the local differences of the
+// scalar form, one of them negated, so that no P2 operand needs a negated
+// copy).  Each lane's value is the scalar formula's: one rounded difference
+// per coordinate, one rounded product and one fused multiply-add per
+// orientation.  ORIGIN: a_i is the local origin (i = 0), so mx = bx and
+// nc = 0 without arithmetic.  NC: form nc (the forward's area term).
+struct Blk2 {
+    float2 S, nT, D, nc;
+};
+template <bool ORIGIN, bool NC>
+__device__ __forceinline__ Blk2 blk2(float ax, float ay, float eax, float eay, const ColPair& q) {
+    Blk2 b;
+    const float2 mx = ORIGIN ? q.bx : sub2(q.bx, f2(ax, ax));
+    const float2 dy = sub2(f2(ay, ay), q.by);
+    b.S = fma2(q.ebx, dy, mul2(q.eby, mx));
+    b.nT = fma2(f2(eax, eax), dy, mul2(f2(eay, eay), mx));
+    b.D = fma2(f2(eax, eax), q.eby, mul2(f2(-eay, -eay), q.ebx));
+    if constexpr (NC) b.nc = ORIGIN ? f2(0.f, 0.f) : fma2(f2(ay, ay), q.bx, mul2(f2(-ax, -ax), q.by));
+    return b;
+}
+
 // Value at dynamic index idx of a register array (select chain, no local memory).
 template <int K> __device__ __forceinline__ float sel(const float (&a)[K], uint32_t idx) {
     float r = a[0];
@@ -442,22 +502,37 @@ __device__ __forceinline__ bool fwd_generic(const Geo<K>& g, FwdOut<K>& o, const
     M neg_s = 0, neg_t = 0;
     float minabs = __int_as_float(0x7f800000);
     if constexpr (K == 4) {
+        // two P2 edges (j, j + 1) per packed instruction
+        ColPair cp[K / 2];
+#pragma unroll
+        for (int h = 0; h < K / 2; ++h) cp[h] = col_pair<K>(g.bx, g.by, g.ebx, g.eby, h);
         // highest (i, j) first, so that push_sign leaves S(i,j)'s sign in
         // bit i * 4 + j
 #pragma unroll
-        for (int q = KK - 1; q >= 0; --q) {
-            const int i = q / K, j = q % K;
-            const float dx = g.ax[i] - g.bx[j], dy = g.ay[i] - g.by[j];
-            const float s = g.ebx[j] * dy - g.eby[j] * dx;
-            const float t = g.eay[i] * dx - g.eax[i] * dy;
-            const float D = g.eax[i] * g.eby[j] - g.eay[i] * g.ebx[j];
-            const float c = g.ax[i] * g.by[j] - g.ay[i] * g.bx[j];
-            Av[q] = fmaf(c, D, s * t) * __fdividef(1.0f, fabsf(D));
-            const bool valid = !COUNTS || (i < n1 && j < n2);
-            minabs = valid ? fmin3(minabs, fabsf(s), fabsf(t)) : minabs;
-            neg_s = (M)push_sign((uint32_t)neg_s, s);
-            neg_t = (M)push_sign((uint32_t)neg_t, t);
+        for (int i = K - 1; i >= 0; --i) {
+#pragma unroll
+            for (int h = K / 2 - 1; h >= 0; --h) {
+                const int j = 2 * h;
+                Blk2 b;
+                if (i == 0) b = blk2<true, true>(0.f, 0.f, g.eax[0], g.eay[0], cp[h]);
+                else b = blk2<false, true>(g.ax[i], g.ay[i], g.eax[i], g.eay[i], cp[h]);
+                // (c D + S T) / |D| = (-c D + S (-T)) / -|D|
+                const float2 num = fma2(b.nc, b.D, mul2(b.S, b.nT));
+                const float2 A =
+                    mul2(num, f2(__fdividef(1.0f, -fabsf(b.D.x)), __fdividef(1.0f, -fabsf(b.D.y))));
+                Av[i * K + j] = A.x;
+                Av[i * K + j + 1] = A.y;
+                const bool valid1 = !COUNTS || (i < n1 && j + 1 < n2);
+                const bool valid0 = !COUNTS || (i < n1 && j < n2);
+                minabs = valid1 ? fmin3(minabs, fabsf(b.S.y), fabsf(b.nT.y)) : minabs;
+                minabs = valid0 ? fmin3(minabs, fabsf(b.S.x), fabsf(b.nT.x)) : minabs;
+                neg_s = (M)push_sign(push_sign((uint32_t)neg_s, b.S.y), b.S.x);
+                neg_t = (M)push_sign(push_sign((uint32_t)neg_t, b.nT.y), b.nT.x);
+            }
         }
+        // the bits of -T are set where T > 0; a zero T has |T| <= the routing
+        // threshold, so its bit is never used as it stands
+        neg_t = ~neg_t & (M)0xFFFFu;
     } else {
 #pragma unroll
         for (int i = 0; i < K; ++i) {
@@ -1598,24 +1673,33 @@ __device__ __forceinline__ uint32_t bwd_shape(const Geo<K>& g, Adj& adj, uint32_
     // two rows per three-operand instruction
     static_assert(K % 2 == 0, "an even capacity");
     float up[K]; // the previous (even) row's u parameters
+    // two P2 edges (j, j + 1) per packed instruction
+    ColPair cp[K / 2];
+#pragma unroll
+    for (int h = 0; h < K / 2; ++h) cp[h] = col_pair<K>(g.bx, g.by, g.ebx, g.eby, h);
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         float tr[K]; // row i's parameters, reduced after the row
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const bool m = (X >> (i * K + j)) & 1u;
-            const float dx = g.ax[i] - g.bx[j], dy = g.ay[i] - g.by[j];
-            const float S = g.ebx[j] * dy - g.eby[j] * dx;
-            const float T = g.eay[i] * dx - g.eax[i] * dy;
-            const float D = g.eax[i] * g.eby[j] - g.eay[i] * g.ebx[j];
-            const float rD = m ? __fdividef(1.0f, D) : kNaN;
-            const float u = -T * rD;
-            tr[j] = S * rD;
+        for (int h = 0; h < K / 2; ++h) {
+            const int j = 2 * h;
+            Blk2 b;
+            if (i == 0) b = blk2<true, false>(0.f, 0.f, g.eax[0], g.eay[0], cp[h]);
+            else b = blk2<false, false>(g.ax[i], g.ay[i], g.eax[i], g.eay[i], cp[h]);
+            const bool m0 = (X >> (i * K + j)) & 1u, m1 = (X >> (i * K + j + 1)) & 1u;
+            const float2 rD = f2(m0 ? __fdividef(1.0f, b.D.x) : kNaN, m1 ? __fdividef(1.0f, b.D.y) : kNaN);
+            const float2 u = mul2(b.nT, rD);
+            const float2 t = mul2(b.S, rD);
+            tr[j] = t.x;
+            tr[j + 1] = t.y;
             if (i & 1) {
-                u0[j] = fmin3(u0[j], up[j], u);
-                u1[j] = fmax3(u1[j], up[j], u);
+                u0[j] = fmin3(u0[j], up[j], u.x);
+                u1[j] = fmax3(u1[j], up[j], u.x);
+                u0[j + 1] = fmin3(u0[j + 1], up[j + 1], u.y);
+                u1[j + 1] = fmax3(u1[j + 1], up[j + 1], u.y);
             } else {
-                up[j] = u;
+                up[j] = u.x;
+                up[j + 1] = u.y;
             }
         }
 #pragma unroll
