@@ -16,9 +16,12 @@
 //     it;
 //   * for quadrilaterals without counts the walk is table-driven: one 64-bit
 //     table entry per edge gives that edge's block of codes.
-//   Near-degenerate pairs, and pairs whose sign pattern is not that of two
-//   convex polygons in general position, take the warp-cooperative robust
-//   path (candidate gathering and an angular sort; with refinement, FP64
+//   With refinement, orientations too small for their FP32 sign take the
+//   FP64 definition's sign, and exact zeros the sign under an infinitesimal
+//   translation of P2 (tie_neg).  Thin pairs, pairs whose sign pattern is not
+//   that of two convex polygons in general position, and (without
+//   refinement) near-degenerate pairs take the warp-cooperative robust path
+//   (candidate gathering and an angular sort; with refinement, FP64
 //   orientation tests and float-float crossing parameters and areas).
 //
 // Backward (paper Sec. II-B `iou_grad`): the recorded codes rebuild the
@@ -305,13 +308,37 @@ __device__ __forceinline__ double orient_raw(const float* __restrict__ pa, int i
     return __dsub_rn(__dmul_rn(bx, py), __dmul_rn(by, px));
 }
 
+// Sign of an orientation whose exact value is zero (a vertex on the line of
+// an edge), taken as under an infinitesimal translation of P2 by
+// (eps, eps^2).  With eb = b_j+1 - b_j and ea = a_i+1 - a_i,
+//   S(i,j) = orient(b_j, b_j+1, a_i) becomes S + eby eps - ebx eps^2,
+//   T(i,j) = orient(a_i, a_i+1, b_j) becomes T - eay eps + eax eps^2,
+// so a zero S takes the sign of eby (of -ebx when eby = 0) and a zero T the
+// sign of -eay (of eax when eay = 0).  The translated pair has no vertex on
+// the line of any edge (that would need the edge parallel to (eps, eps^2)),
+// so its signs are those of two convex polygons in general position, and
+// since the intersection area is continuous, its clip evaluated at eps = 0
+// gives the exact area.  The edge components come from the raw inputs: an
+// FP32 difference of two floats is zero exactly when they are equal, so its
+// sign is exact.  p1edge: the edge is P1's (a T orientation).  Returns 1 for
+// a negative sign, 0 for a positive one, 2 for an edge of zero length (no
+// decision).
+__device__ __forceinline__ uint32_t tie_neg(const float* __restrict__ raw, int ia, int ib, bool p1edge) {
+    const float2 A = __ldg(reinterpret_cast<const float2*>(raw) + ia);
+    const float2 B = __ldg(reinterpret_cast<const float2*>(raw) + ib);
+    const float ex = B.x - A.x, ey = B.y - A.y;
+    if (ey != 0.f) return ((ey > 0.f) == p1edge) ? 1u : 0u;
+    if (ex != 0.f) return ((ex < 0.f) == p1edge) ? 1u : 0u;
+    return 2u;
+}
+
 // Sign repair for a pair of quadrilaterals (K = 4): `small` marks the
 // orientations whose FP32 value is too small to trust (bit i*4+j: S(i,j) =
 // orient(b_j, b_j+1, a_i); bit 16+i*4+j: T(i,j) = orient(a_i, a_i+1, b_j)),
 // `neg` holds the FP32 signs in the same layout.  Each marked orientation is
-// re-evaluated by orient_raw and its sign bit replaced.  Returns the repaired
-// signs, or bit 32 set when one is exactly zero (a vertex on the line of an
-// edge: the pair is not in general position).  Not inlined: it runs for well
+// re-evaluated by orient_raw and its sign bit replaced; an exact zero takes
+// the sign of the translated pair (tie_neg).  Returns the repaired signs, or
+// bit 32 set when a zero sits on an edge of zero length.  Not inlined: it runs for well
 // under 0.1% of random pairs, and keeping it out of line keeps the fast
 // path's registers unchanged.
 static __device__ __noinline__ uint64_t exact_signs4(const float* __restrict__ raw1, const float* __restrict__ raw2, int n1,
@@ -320,11 +347,14 @@ static __device__ __noinline__ uint64_t exact_signs4(const float* __restrict__ r
         const int b = __ffs(small) - 1;
         small &= small - 1u;
         const int q = b & 15, i = q >> 2, j = q & 3;
-        double v;
-        if (b >= 16) v = orient_raw(raw1, i, (i + 1 < n1) ? i + 1 : 0, raw2, j);
-        else v = orient_raw(raw2, j, (j + 1 < n2) ? j + 1 : 0, raw1, i);
-        if (v == 0.0) return 1ull << 32;
-        neg = (v < 0.0) ? (neg | (1u << b)) : (neg & ~(1u << b));
+        const int i1 = (i + 1 < n1) ? i + 1 : 0, j1 = (j + 1 < n2) ? j + 1 : 0;
+        const double v = (b >= 16) ? orient_raw(raw1, i, i1, raw2, j) : orient_raw(raw2, j, j1, raw1, i);
+        uint32_t ng = (v < 0.0) ? 1u : 0u;
+        if (v == 0.0) {
+            ng = (b >= 16) ? tie_neg(raw1, i, i1, true) : tie_neg(raw2, j, j1, false);
+            if (ng > 1u) return 1ull << 32;
+        }
+        neg = ng ? (neg | (1u << b)) : (neg & ~(1u << b));
     }
     return neg;
 }
@@ -478,9 +508,11 @@ __device__ __forceinline__ bool fwd_finish(const Geo<K>& g, float L, typename Ma
 //
 // raw1, raw2 (optional, K = 4): the pair's unrounded input polygons.  When
 // given, a pair with orientations under the routing threshold is not handed
-// back: those orientations take the FP64 definition's sign (exact_signs4), and
-// only an exact zero (a vertex on the line of an edge) hands the pair back.
-// Their FP32 values still place the crossing points: an FP32 orientation is
+// back: those orientations take the FP64 definition's sign (exact_signs4), an
+// exact zero (a vertex on the line of an edge) the sign under an
+// infinitesimal translation of P2 (tie_neg), and only a zero-length edge
+// hands the pair back.  Their FP32 values still place the crossing points: an
+// FP32 orientation is
 // within 2.9e-6 L^2 of the exact one, which moves a crossing point along its
 // P1 edge and changes the intersection area by at most about 1.5e-6 L^2 per
 // crossing, whatever the crossing angle (the same bound as for any pair of

@@ -170,15 +170,19 @@ __device__ __forceinline__ uint64_t col0_mask() {
 // sign (orient_raw, the definition's operand order, from the raw inputs).
 // The row's FP32 values are formed again from the lane's data; the margin
 // covers a different rounding (contraction) of that second evaluation.
-// sneg, tneg: the row's FP32 sign bits (bit j: column j).  Returns the
-// repaired bits (S in bits 0-7, T in bits 8-15), or bit 32 set when one
-// orientation is exactly zero (a vertex on the line of an edge).  It runs only
-// for pairs with an orientation under the threshold.
+// sneg, tneg: the row's FP32 sign bits (bit j: column j).  An exactly zero
+// orientation (a vertex on the line of an edge) takes the sign it has when P2
+// is translated by an infinitesimal (eps, eps^2) (tie_neg).  Returns the
+// repaired bits (S in bits 0-7, T in bits 8-15) and the zero orientations
+// (S in bits 16-23, T in bits 24-31), or bit 32 set when a zero sits on an
+// edge of zero length.  It runs only for pairs with an orientation under the
+// threshold.
 __device__ __forceinline__ uint64_t refine_row8(const Lane& L, const float* __restrict__ raw1,
                                                 const float* __restrict__ raw2, int n1, int n2, int r, float thr,
                                                 uint32_t sneg, uint32_t tneg) {
     const float wide = 3.f * thr;
     const int rn = (r + 1 < n1) ? r + 1 : 0;
+    uint32_t zs = 0, zt = 0;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         if (j >= n2) break;
@@ -186,17 +190,28 @@ __device__ __forceinline__ uint64_t refine_row8(const Lane& L, const float* __re
         const float sv = L.ebx[j] * dy - L.eby[j] * dx;
         const float tv = L.eay * dx - L.eax * dy;
         if (!(fabsf(sv) > wide)) {
-            const double v = orient_raw(raw2, j, (j + 1 < n2) ? j + 1 : 0, raw1, r);
-            if (v == 0.0) return 1ull << 32;
-            sneg = (v < 0.0) ? (sneg | (1u << j)) : (sneg & ~(1u << j));
+            const int j1 = (j + 1 < n2) ? j + 1 : 0;
+            const double v = orient_raw(raw2, j, j1, raw1, r);
+            uint32_t ng = (v < 0.0) ? 1u : 0u;
+            if (v == 0.0) {
+                ng = tie_neg(raw2, j, j1, false);
+                if (ng > 1u) return 1ull << 32;
+                zs |= 1u << j;
+            }
+            sneg = ng ? (sneg | (1u << j)) : (sneg & ~(1u << j));
         }
         if (!(fabsf(tv) > wide)) {
             const double v = orient_raw(raw1, r, rn, raw2, j);
-            if (v == 0.0) return 1ull << 32;
-            tneg = (v < 0.0) ? (tneg | (1u << j)) : (tneg & ~(1u << j));
+            uint32_t ng = (v < 0.0) ? 1u : 0u;
+            if (v == 0.0) {
+                ng = tie_neg(raw1, r, rn, true);
+                if (ng > 1u) return 1ull << 32;
+                zt |= 1u << j;
+            }
+            tneg = ng ? (tneg | (1u << j)) : (tneg & ~(1u << j));
         }
     }
-    return (uint64_t)(sneg & 0xFFu) | ((uint64_t)(tneg & 0xFFu) << 8);
+    return (uint64_t)((sneg & 0xFFu) | ((tneg & 0xFFu) << 8) | (zs << 16) | (zt << 24));
 }
 
 struct FwdG {
@@ -210,9 +225,10 @@ struct FwdG {
 // Group forward.  Returns false (in every lane of the group) when the pair
 // must take the warp-cooperative robust path.  raw1, raw2 (refinement on):
 // the pair's input polygons; orientations under the routing threshold then
-// take the FP64 definition's sign (refine_row8), and only an exact zero hands
-// the pair back.  Their FP32 values still place the crossing points, as in
-// the quadrilateral forward.
+// take the FP64 definition's sign (refine_row8), exact zeros the sign under
+// an infinitesimal translation of P2, and only a zero-length edge hands the
+// pair back.  Their FP32 values still place the crossing points, as in the
+// quadrilateral forward.
 template <int KIN = 8>
 __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out, const float* __restrict__ raw1 = nullptr,
                                           const float* __restrict__ raw2 = nullptr) {
@@ -262,42 +278,62 @@ __device__ __forceinline__ bool fwd_group(const Lane& L, FwdG& out, const float*
     }
     mn = gmin(gm, mn);
     if (!(Lr > 0.f)) return false;
-    uint32_t refined = 0u;
+    uint32_t refined = 0u, zrow = 0u;
+    bool tie = false; // some orientation of the pair is exactly zero (group-uniform)
     if (!(mn > thr)) {
         if (raw1 == nullptr) return false;
         const uint64_t rr = liveA ? refine_row8(L, raw1, raw2, n1, n2, r, thr, sneg, tneg) : 0ull;
-        if (gor32(gm, (uint32_t)(rr >> 32))) return false;
+        const uint32_t gf = gor32(gm, (uint32_t)(rr >> 32) | ((((uint32_t)rr >> 16) != 0u) ? 2u : 0u));
+        if (gf & 1u) return false;
+        tie = (gf & 2u) != 0u;
         if (liveA) {
             sneg = (uint32_t)rr & 0xFFu;
             tneg = (uint32_t)(rr >> 8) & 0xFFu;
+            zrow = (uint32_t)rr >> 16;
         }
         refined = 2u;
     }
     out.degen = ((mn <= kDegenRel * Lr * Lr) ? 1u : 0u) | refined;
     const uint32_t colv = (1u << n2) - 1u;
-    const uint64_t sp = gor64(gm, liveA ? (uint64_t)(~sneg & colv) << (8 * r) : 0ull);
-    const uint64_t tp = gor64(gm, liveA ? (uint64_t)(~tneg & colv) << (8 * r) : 0ull);
     const uint64_t col0 = 0x0101010101010101ull;
     const uint64_t rows = (n1 >= 8) ? ~0ull : ((1ull << (8 * n1)) - 1ull);
     const uint64_t cols = col0 * colv;
     const uint64_t V = rows & cols;
-    const uint64_t sp_next = ((sp >> 8) & ~(0xFFull << (8 * (n1 - 1)))) | ((sp & 0xFFull) << (8 * (n1 - 1)));
-    const uint64_t tp_next = ((tp >> 1) & ~(col0 << (n2 - 1))) | ((tp & col0) << (n2 - 1));
-    const uint64_t X = (sp ^ sp_next) & (tp ^ tp_next) & V;
-    const uint64_t entry1 = X & ~sp, exit1 = X & sp;
-    if ((X & tp) != entry1) return false;
-    // in1: rows of sp equal to all valid columns (exact zero-byte test on sp ^ cols)
-    const uint64_t z = (sp ^ cols) & rows;
-    const uint64_t hi7 = 0x7F7F7F7F7F7F7F7Full;
-    const uint64_t zb = ~(((z & hi7) + hi7) | z | hi7) & rows; // 0x80 in each zero byte of a valid row
-    const uint32_t in1 = (uint32_t)(((zb >> 7) * 0x0102040810204080ull) >> 56);
-    // in2: columns of tp set in every valid row (AND over the rows' bytes)
-    uint64_t a = tp | ~rows;
-    a &= a >> 32;
-    a &= a >> 16;
-    a &= a >> 8;
-    const uint32_t in2 = (uint32_t)(a & 0xFFull) & colv;
-    const uint32_t cnt = (uint32_t)(__popc(in1) + __popc(in2) + __popcll(X));
+    uint64_t sp, tp, X, entry1, exit1;
+    uint32_t in1, in2, cnt;
+    for (int pass = 0;; ++pass) {
+        sp = gor64(gm, liveA ? (uint64_t)(~sneg & colv) << (8 * r) : 0ull);
+        tp = gor64(gm, liveA ? (uint64_t)(~tneg & colv) << (8 * r) : 0ull);
+        const uint64_t sp_next = ((sp >> 8) & ~(0xFFull << (8 * (n1 - 1)))) | ((sp & 0xFFull) << (8 * (n1 - 1)));
+        const uint64_t tp_next = ((tp >> 1) & ~(col0 << (n2 - 1))) | ((tp & col0) << (n2 - 1));
+        X = (sp ^ sp_next) & (tp ^ tp_next) & V;
+        entry1 = X & ~sp;
+        exit1 = X & sp;
+        if ((X & tp) != entry1) return false;
+        // in1: rows of sp equal to all valid columns (exact zero-byte test on sp ^ cols)
+        const uint64_t z = (sp ^ cols) & rows;
+        const uint64_t hi7 = 0x7F7F7F7F7F7F7F7Full;
+        const uint64_t zb = ~(((z & hi7) + hi7) | z | hi7) & rows; // 0x80 in each zero byte of a valid row
+        in1 = (uint32_t)(((zb >> 7) * 0x0102040810204080ull) >> 56);
+        // in2: columns of tp set in every valid row (AND over the rows' bytes)
+        uint64_t a = tp | ~rows;
+        a &= a >> 32;
+        a &= a >> 16;
+        a &= a >> 8;
+        in2 = (uint32_t)(a & 0xFFull) & colv;
+        cnt = (uint32_t)(__popc(in1) + __popc(in2) + __popcll(X));
+        // A pair with an exactly zero orientation whose clip under the
+        // translation by (eps, eps^2) is not empty is clipped once more under
+        // the opposite translation (-eps, -eps^2), which flips the sign of every
+        // zero: an equally valid perturbation with the same limit area.  When
+        // the interiors do not meet (a shared edge, a touching vertex), the
+        // directions that make them overlap form a cone narrower than a
+        // half-plane, so one of the two translations separates the polygons,
+        // and the pair gets an empty clip instead of a sliver of zero area.
+        if (pass == 1 || !tie || cnt == 0u) break;
+        sneg ^= zrow & 0xFFu;
+        tneg ^= zrow >> 8;
+    }
     out.nx = 0;
     out.iou = 0.f;
     out.ai = 0.f;

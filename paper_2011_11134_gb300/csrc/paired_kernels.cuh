@@ -49,9 +49,9 @@ template <int K> __device__ __forceinline__ void store_poly(float* __restrict__ 
 
 // The K = 4 kernels walk the pairs warp by warp (32 consecutive pairs per
 // warp and step, grid-stride over warps), with no block-wide barrier.  In the
-// forward, a pair the fast path cannot finish (an exactly zero orientation,
-// a sign pattern two convex polygons in general position cannot have, or a
-// thin pair; well under 0.1% of random boxes) is finished right after the
+// forward, a pair the fast path cannot finish (a sign pattern two convex
+// polygons in general position cannot have, a thin pair, or without
+// refinement a near-degenerate one; well under 0.1% of random boxes) is finished right after the
 // step by the whole warp (warp_robust, a non-inlined call, so its registers
 // and slow-path code stay off the common path); the SM keeps issuing from its
 // other warps meanwhile.  In the backward, a pair whose codes the shape
