@@ -146,7 +146,7 @@ k_nms_mask(const float* __restrict__ sboxes, const uint8_t* __restrict__ scounts
            float thr, uint64_t* __restrict__ mask, uint32_t* __restrict__ sup, uint32_t flags, uint32_t* status) {
     __shared__ float4 s_rbox[kNmsTileRows];
     __shared__ uint16_t s_q[kNmsTileRows * kPwThreads];
-    __shared__ int s_nq;
+    __shared__ int s_nq[kPwMaxWarps];
     __shared__ unsigned long long s_bits[kNmsTileRows * 2];
     __shared__ unsigned s_tbits[kPwThreads];
     const int t = threadIdx.x;
@@ -161,7 +161,7 @@ k_nms_mask(const float* __restrict__ sboxes, const uint8_t* __restrict__ scounts
     s_tbits[t] = 0u;
     uint32_t err = 0;
     const NmsBitsOut out{s_bits, s_tbits, i0, j0, thr};
-    pw_tile<K, COUNTS>(sboxes, scounts, N, sboxes, scounts, N, i0, j0, kNmsTileRows, s_rbox, s_q, &s_nq, refine, err,
+    pw_tile<K, COUNTS>(sboxes, scounts, N, sboxes, scounts, N, i0, j0, kNmsTileRows, s_rbox, s_q, s_nq, refine, err,
                        out);
     // pw_tile ends with a barrier: the bits are final
     if (t < kNmsTileRows * 2) {

@@ -50,13 +50,13 @@ k_pairwise(const float* __restrict__ a, const uint8_t* __restrict__ ca, int64_t 
            uint32_t flags, uint32_t* status) {
     __shared__ float4 s_rbox[kTileRows];
     __shared__ uint16_t s_q[kTileRows * kPwThreads];
-    __shared__ int s_nq;
+    __shared__ int s_nq[kPwMaxWarps];
     const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
     const int64_t cblocks = (M + kPwThreads - 1) / kPwThreads;
     const int64_t rb = blockIdx.x / cblocks;
     uint32_t err = 0;
     pw_tile<K, COUNTS>(a, ca, N, b, cb, M, rb * kTileRows, ((int64_t)blockIdx.x - rb * cblocks) * kPwThreads,
-                       kTileRows, s_rbox, s_q, &s_nq, refine, err, PwMatrixOut{iou, nx, M});
+                       kTileRows, s_rbox, s_q, s_nq, refine, err, PwMatrixOut{iou, nx, M});
     if (err) atomicOr(status, err);
 }
 
@@ -160,7 +160,7 @@ __global__ void k_batched(int S, const int64_t* __restrict__ a_off, const int64_
     __shared__ float4 s_rbox[kMaxTileRows];
     __shared__ int64_t s_tile;
     __shared__ int s_scene;
-    __shared__ int s_nq;
+    __shared__ int s_nq[kPwMaxWarps];
     const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
     const int64_t total = tile_start[S];
     const int64_t cols = blockDim.x;
@@ -189,7 +189,7 @@ __global__ void k_batched(int S, const int64_t* __restrict__ a_off, const int64_
         const PwMatrixOut out{iou + o0, nx ? nx + o0 : nullptr, Ms};
         pw_tile<K, COUNTS>(a + a0 * 2 * K, COUNTS && ca ? ca + a0 : nullptr, Ns, b + b0 * 2 * K,
                            COUNTS && cb ? cb + b0 : nullptr, Ms, rb * rows, (lt - rb * cblocks) * cols, rows, s_rbox,
-                           s_q, &s_nq, refine, err, out);
+                           s_q, s_nq, refine, err, out);
     }
     if (err) atomicOr(status, err);
 }

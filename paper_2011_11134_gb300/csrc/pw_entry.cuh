@@ -11,6 +11,8 @@
 namespace dgal {
 
 constexpr int kPwThreads = 128;
+// Most warps a pairwise tile block may have (pw_tile keeps one queue count per warp).
+constexpr int kPwMaxWarps = 8;
 
 // Fast path for one matrix entry.  Returns true when the entry must be
 // finished by the warp-cooperative robust path; otherwise sets iou / nxo.
@@ -124,13 +126,18 @@ struct PwMatrixOut {
 //   2. every wanted entry is tested on the boxes (exact comparisons of the
 //      float inputs); a disjoint pair has IoU 0 and nx 0 by definition and is
 //      reported at once (consecutive threads, consecutive columns), the others
-//      are queued in shared memory (s_q, codes r << 8 | c);
+//      are queued in shared memory (codes r << 8 | c).  Each warp queues its
+//      own 32 columns in its own region of s_q (R x 32 codes at w R 32) with a
+//      running count in a register (a ballot and a prefix count per row, no
+//      shared-memory atomic), and leaves its count in s_nq[w];
 //   3. the block's warps clip the queued entries densely (pw_fast, with the
-//      warp-cooperative finish for the ones it hands back).
+//      warp-cooperative finish for the ones it hands back), reading the warps'
+//      regions as one queue.
 // In bird's-eye scenes about 2% of the entries have meeting boxes; without the
 // queue a warp runs the clip whenever one of its 32 entries needs it.  Every
-// thread of the block calls this (it has block barriers); blockDim.x <= 256
-// and R <= 256 (8-bit fields of the queue codes).
+// thread of the block calls this (it has block barriers); blockDim.x is a
+// multiple of 32 and at most kPwMaxWarps * 32, R <= 256 (8-bit fields of the
+// queue codes); s_q holds R x blockDim.x codes, s_nq one count per warp.
 template <int K, bool COUNTS, class Out>
 __device__ __forceinline__ void pw_tile(const float* __restrict__ a, const uint8_t* __restrict__ ca, int64_t N,
                                         const float* __restrict__ b, const uint8_t* __restrict__ cb, int64_t M,
@@ -148,8 +155,11 @@ __device__ __forceinline__ void pw_tile(const float* __restrict__ a, const uint8
         s_rbox[t] = (i < N) ? poly_box<K, COUNTS>(a + i * 2 * K, (COUNTS && ca) ? (int)ca[i] : K)
                             : make_float4(inf, inf, -inf, -inf);
     }
-    if (t == 0) *s_nq = 0;
     __syncthreads();
+    const int w = t >> 5, nw = C >> 5;
+    uint16_t* q_w = s_q + w * R * 32;
+    const unsigned below = (1u << lane) - 1u;
+    int cnt = 0;
 #pragma unroll 4
     for (int r = 0; r < R; ++r) {
         const int64_t i = i0 + r;
@@ -158,17 +168,26 @@ __device__ __forceinline__ void pw_tile(const float* __restrict__ a, const uint8
         const bool meet = v && !(rbx.z < cbx.x || cbx.z < rbx.x || rbx.w < cbx.y || cbx.w < rbx.y);
         if (v && !meet) out.disjoint(i, j);
         const unsigned bal = __ballot_sync(full, meet);
-        int pos = 0;
-        if (lane == 0 && bal) pos = atomicAdd(s_nq, __popc(bal));
-        pos = __shfl_sync(full, pos, 0);
-        if (meet) s_q[pos + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)((r << 8) | t);
+        if (meet) q_w[cnt + __popc(bal & below)] = (uint16_t)((r << 8) | t);
+        cnt += __popc(bal);
     }
+    if (lane == 0) s_nq[w] = cnt;
     __syncthreads();
-    const int nq = *s_nq;
+    int nq = 0;
+    for (int u = 0; u < nw; ++u) nq += s_nq[u];
     for (int qb = t & ~31; qb < nq; qb += C) {
         const int q = qb + lane;
         const bool act = q < nq;
-        const int code = act ? (int)s_q[q] : 0;
+        // entry q of the joined queue: warp src's entry rem (the counts are
+        // read from shared memory, so they take no registers)
+        int src = 0, rem = q;
+        for (int u = 0; u + 1 < nw; ++u) {
+            const int c = s_nq[u];
+            const bool past = src == u && rem >= c;
+            rem -= past ? c : 0;
+            src += past ? 1 : 0;
+        }
+        const int code = act ? (int)s_q[src * R * 32 + rem] : 0;
         const int64_t i = i0 + (code >> 8), jj = j0 + (code & 0xFF);
         const int n1 = (COUNTS && ca && act) ? (int)ca[i] : K;
         const int n2 = (COUNTS && cb && act) ? (int)cb[jj] : K;
