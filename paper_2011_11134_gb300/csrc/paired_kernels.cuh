@@ -239,6 +239,10 @@ k_paired_fwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * kPairThreads;
     const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
+    // a backward launched right after this grid with programmatic stream
+    // serialisation may be scheduled once every block of this grid has started
+    // (it waits for this grid's completion before touching memory)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     uint32_t err = 0;
     float acc = 0.f;
     for (int64_t base = (int64_t)blockIdx.x * kPairThreads + (threadIdx.x & ~31); base < n; base += stride) {
@@ -316,6 +320,12 @@ k_paired_bwd(const float* __restrict__ p1, const uint8_t* __restrict__ c1, const
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * kPairThreads;
     const bool refine = (flags & kFlagRefine) && !(flags & kFlagPlain);
+    // Launched with programmatic stream serialisation (launch_pdl), the blocks
+    // may start while the grid before this one (the forward) is finishing:
+    // wait for its completion and its memory before the first global access,
+    // so no input, including the flags and partials it wrote, is read early.
+    // Without that launch attribute this returns at once.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if constexpr (LOSS) loss_fold(la);
     uint32_t err = 0;
     for (int64_t base = (int64_t)blockIdx.x * kPairThreads + (threadIdx.x & ~31); base < n; base += stride) {
