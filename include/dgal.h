@@ -77,6 +77,14 @@ typedef enum {
                                  straightforward launch; the backward recomputes the clip */
 #define DGAL_LOSS_GIOU 0x4u   /* dgal_iou_loss: the generalized IoU loss (see there) */
 #define DGAL_LOSS_DIOU 0x8u   /* dgal_iou_loss: the distance IoU loss (see there) */
+#define DGAL_VALIDATE 0x10u   /* debug: before its kernels, the call checks every input polygon
+                                 for strict convexity and counter-clockwise order (the input
+                                 contract, paper Sec. III) with dgal_validate_polygons'
+                                 kernel; a polygon that fails sets DGAL_DEV_NOT_CONVEX, and
+                                 the results for its pairs are undefined.  Applies to the
+                                 paired, pairwise, 3D and loss calls (not to the ragged batch,
+                                 whose polygon counts live on the device: check its arrays with
+                                 dgal_validate_polygons).  Costs one extra pass over the polygons. */
 #define DGAL_TEST_EXPIRE_WAIT 0x100u /* dgal_nms_rotated, for tests of the failure path: the
                                         greedy pass takes its wait-expiry path (DGAL_DEV_TIMEOUT,
                                         results incomplete) at its second block, once that block's
@@ -88,6 +96,8 @@ typedef enum {
 #define DGAL_DEV_BAD_FLAGS 0x4u /* backward: nx > 2K or a code naming a missing vertex/edge */
 #define DGAL_DEV_BAD_OFFSETS 0x8u /* ragged batch: offsets not starting at 0 or not N_s x M_s (scene skipped) */
 #define DGAL_DEV_TIMEOUT 0x10u    /* a bounded wait on an asynchronous copy ran out (results incomplete) */
+#define DGAL_DEV_NOT_CONVEX 0x20u /* DGAL_VALIDATE / dgal_validate_polygons: an input polygon is not strictly
+                                     convex in counter-clockwise order */
 
 /*
  * Paired IoU forward (paper Sec. II-B, `iou`): for k < n,
@@ -427,6 +437,22 @@ dgal_status dgal_get_batched_config(int K, int32_t out[3]);
 /* The launch shape currently used by the paired calls for K: *group_below =
  * the batch size (pairs) below which a group of 8 lanes takes each pair. */
 dgal_status dgal_get_paired_config(int K, int64_t* group_below);
+
+/*
+ * Input check (the paper's convex, counter-clockwise polygons, Sec. III; the
+ * library's results are undefined for other input): polygon k, its first
+ * c[k] vertices (all K when c is NULL), passes when every vertex lies strictly
+ * left of every edge it is not an end of, orient(v_i, v_i+1, v_m) > 0.  That
+ * rejects clockwise order, reflex vertices, self-intersecting outlines and
+ * repeated or collinear vertices.  Each test is decided in FP32 when its value
+ * exceeds the FP32 error bound, else in FP64 from the raw inputs (exact sign).
+ *   p    float [n][K][2], 16-byte aligned, device; c uint8 [n] or NULL;
+ *   bad  uint8 [n] (device, nullable): 1 for a failing polygon, else 0;
+ *   a failing polygon also sets DGAL_DEV_NOT_CONVEX in the device status word.
+ * Counts outside [3, K] are not checked here (the IoU calls report them as
+ * DGAL_DEV_BAD_COUNT; bad[k] = 0).  Asynchronous on `stream`.
+ */
+dgal_status dgal_validate_polygons(const float* p, const uint8_t* c, int64_t n, int K, uint8_t* bad, void* stream);
 
 /* Reads (and, if clear != 0, resets) the current device's status word;
  * synchronises the device. */

@@ -14,6 +14,8 @@ Python binding of libdgal's C ABI (include/dgal.h), with the same call names:
     BatchedGraph               the ragged batch captured in a CUDA graph
     dgal_autotune              launch-shape tuner for the ragged batch
     dgal_get_device_status     device-side error bits
+    dgal_validate_polygons     input check: strictly convex, counter-clockwise
+                               (also run inside a call by flags=DGAL_VALIDATE)
 
 and ``IoU`` / ``iou``: a ``torch.autograd.Function`` whose backward consumes
 the recorded (nx, xflags) or, in recompute mode, re-runs the clip.
@@ -32,8 +34,8 @@ import torch
 
 from . import _lib
 from ._lib import (DGAL_DEV_BAD_COUNT, DGAL_DEV_BAD_FLAGS, DGAL_DEV_BAD_OFFSETS, DGAL_DEV_OVERFLOW,
-                   DGAL_DEV_TIMEOUT, DGAL_FP64_REFINE, DGAL_LOSS_DIOU, DGAL_LOSS_GIOU, DGAL_PLAIN,
-                   DGAL_TEST_EXPIRE_WAIT, DgalError)
+                   DGAL_DEV_NOT_CONVEX, DGAL_DEV_TIMEOUT, DGAL_FP64_REFINE, DGAL_LOSS_DIOU, DGAL_LOSS_GIOU,
+                   DGAL_PLAIN, DGAL_TEST_EXPIRE_WAIT, DGAL_VALIDATE, DgalError)
 
 __all__ = [
     "dgal_iou_paired", "dgal_iou_backward", "dgal_iou_fwd_bwd", "dgal_iou_pairwise", "dgal_iou_pairwise_batched",
@@ -48,6 +50,7 @@ __all__ = [
     "dgal_intersect_paired", "dgal_area", "dgal_line_from_points", "dgal_line_from_points_backward",
     "dgal_line_intersect", "dgal_line_intersect_backward", "LineFromPoints", "LineIntersect",
     "line_from_points", "line_intersect", "dgal_iou_fwd_bwd_host", "dgal_iou_host_workspace_bytes",
+    "dgal_validate_polygons", "DGAL_VALIDATE", "DGAL_DEV_NOT_CONVEX",
 ]
 
 
@@ -336,6 +339,18 @@ def dgal_intersect_paired(p1, p2, c1=None, c2=None, flags=DGAL_FP64_REFINE, stre
     _lib.call("dgal_intersect_paired", _lib.ptr(p1), _lib.ptr(c1), _lib.ptr(p2), _lib.ptr(c2), n, K,
               _lib.ptr(verts), _lib.ptr(area), _lib.ptr(nx), _lib.ptr(xflags), flags, _lib.stream_ptr(stream))
     return verts, area, nx, xflags
+
+
+def dgal_validate_polygons(p, c=None, stream=None):
+    """Input check of polygons [n, K, 2] (with counts c): uint8 [n], 1 where a
+    polygon is not strictly convex in counter-clockwise order (such a polygon
+    also sets DGAL_DEV_NOT_CONVEX in the device status word)."""
+    _poly(p, "p")
+    n, K = p.shape[0], p.shape[1]
+    c = _counts(c, n, "c", p.device)
+    bad = torch.empty(n, device=p.device, dtype=torch.uint8)
+    _lib.call("dgal_validate_polygons", _lib.ptr(p), _lib.ptr(c), n, K, _lib.ptr(bad), _lib.stream_ptr(stream))
+    return bad
 
 
 def dgal_area(p, c=None, stream=None):

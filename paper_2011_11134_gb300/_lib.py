@@ -20,12 +20,14 @@ DGAL_FP64_REFINE = 0x1
 DGAL_PLAIN = 0x2
 DGAL_LOSS_GIOU = 0x4
 DGAL_LOSS_DIOU = 0x8
+DGAL_VALIDATE = 0x10
 DGAL_TEST_EXPIRE_WAIT = 0x100
 DGAL_DEV_TIMEOUT = 0x10
 DGAL_DEV_BAD_COUNT = 0x1
 DGAL_DEV_OVERFLOW = 0x2
 DGAL_DEV_BAD_FLAGS = 0x4
 DGAL_DEV_BAD_OFFSETS = 0x8
+DGAL_DEV_NOT_CONVEX = 0x20
 
 STATUS_NAMES = {0: "DGAL_OK", 1: "DGAL_ERR_INVALID_ARG", 2: "DGAL_ERR_UNSUPPORTED_K", 3: "DGAL_ERR_ALIGNMENT",
                 4: "DGAL_ERR_CUDA", 5: "DGAL_ERR_WORKSPACE", 6: "DGAL_ERR_DEVICE_STATUS"}
@@ -60,6 +62,7 @@ _SIG = {
     "dgal_nms_rotated": (_I, [_P, _P, _P, _I64, _I, ctypes.c_float, _P, _P, _P, ctypes.c_size_t, _U32, _P]),
     "dgal_intersect_paired": (_I, [_P, _P, _P, _P, _I64, _I, _P, _P, _P, _P, _U32, _P]),
     "dgal_area": (_I, [_P, _P, _I64, _I, _P, _P]),
+    "dgal_validate_polygons": (_I, [_P, _P, _I64, _I, _P, _P]),
     "dgal_line_from_points": (_I, [_P, _P, _I64, _P, _P]),
     "dgal_line_from_points_backward": (_I, [_P, _P, _I64, _P, _P, _P, _P]),
     "dgal_line_intersect": (_I, [_P, _P, _I64, _P, _P]),

@@ -129,6 +129,13 @@ dgal_status check_poly_ptr(const void* p, const char* name) {
         if (_st != DGAL_OK) return _st; \
     } while (0)
 
+// DGAL_VALIDATE: the convexity / orientation check of a call's polygon
+// arrays, launched before its kernels on the same stream
+dgal_status maybe_validate(uint32_t flags, const float* p, const uint8_t* c, int64_t n, int K, cudaStream_t s) {
+    if (!(flags & DGAL_VALIDATE)) return DGAL_OK;
+    return launch_validate(p, c, n, K, nullptr, s);
+}
+
 } // namespace
 
 extern "C" {
@@ -136,6 +143,15 @@ extern "C" {
 int dgal_version(void) { return 100; }
 
 const char* dgal_last_error(void) { return t_last_error.c_str(); }
+
+dgal_status dgal_validate_polygons(const float* p, const uint8_t* c, int64_t n, int K, uint8_t* bad, void* stream) {
+    t_last_error.clear();
+    DGAL_TRY(check_K(K));
+    if (n < 0) return fail(DGAL_ERR_INVALID_ARG, "n = %lld is negative", (long long)n);
+    if (n == 0) return DGAL_OK;
+    DGAL_TRY(check_poly_ptr(p, "p"));
+    return launch_validate(p, c, n, K, bad, (cudaStream_t)stream);
+}
 
 dgal_status dgal_iou_paired(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
                             int K, float* iou, uint8_t* nx, uint8_t* xflags, uint8_t* degen, uint32_t flags,
@@ -152,6 +168,8 @@ dgal_status dgal_iou_paired(const float* p1, const uint8_t* c1, const float* p2,
         return fail(DGAL_ERR_INVALID_ARG, "nx and xflags must be both NULL or both set");
     if (xflags && !aligned(xflags, K == 4 ? 8 : 16))
         return fail(DGAL_ERR_ALIGNMENT, "xflags is not %d-byte aligned", K == 4 ? 8 : 16);
+    DGAL_TRY(maybe_validate(flags, p1, c1, n, K, (cudaStream_t)stream));
+    DGAL_TRY(maybe_validate(flags, p2, c2, n, K, (cudaStream_t)stream));
     return launch_paired_fwd(p1, c1, p2, c2, n, K, iou, nx, xflags, degen, flags, (cudaStream_t)stream);
 }
 
@@ -172,6 +190,8 @@ dgal_status dgal_iou_backward(const float* p1, const uint8_t* c1, const float* p
         return fail(DGAL_ERR_INVALID_ARG, "nx and xflags must be both NULL or both set");
     if (xflags && !aligned(xflags, K == 4 ? 8 : 16))
         return fail(DGAL_ERR_ALIGNMENT, "xflags is not %d-byte aligned", K == 4 ? 8 : 16);
+    DGAL_TRY(maybe_validate(flags, p1, c1, n, K, (cudaStream_t)stream));
+    DGAL_TRY(maybe_validate(flags, p2, c2, n, K, (cudaStream_t)stream));
     return launch_paired_bwd(p1, c1, p2, c2, n, K, grad_iou, nx, xflags, grad_p1, grad_p2, flags,
                              (cudaStream_t)stream);
 }
@@ -190,6 +210,8 @@ dgal_status dgal_iou_fwd_bwd(const float* p1, const uint8_t* c1, const float* p2
     if (!grad_iou || !iou) return fail(DGAL_ERR_INVALID_ARG, "grad_iou or iou is NULL");
     if (!aligned(grad_iou, 4) || !aligned(iou, 4)) return fail(DGAL_ERR_ALIGNMENT, "grad_iou or iou is not 4-byte aligned");
     const cudaStream_t s = (cudaStream_t)stream;
+    DGAL_TRY(maybe_validate(flags, p1, c1, n, K, s));
+    DGAL_TRY(maybe_validate(flags, p2, c2, n, K, s));
     if (K == 4) return launch_paired_fused(p1, c1, p2, c2, n, K, grad_iou, iou, grad_p1, grad_p2, flags, s);
     // K = 8: the forward saves the flags in the caller's scratch, the backward reads them
     if (!nx || !xflags) return fail(DGAL_ERR_INVALID_ARG, "K = 8 needs nx and xflags scratch");
@@ -210,6 +232,8 @@ dgal_status dgal_iou_pairwise(const float* a, const uint8_t* ca, int64_t N, cons
     DGAL_TRY(check_poly_ptr(b, "b"));
     if (!iou) return fail(DGAL_ERR_INVALID_ARG, "iou is NULL");
     if (!aligned(iou, 4)) return fail(DGAL_ERR_ALIGNMENT, "iou is not 4-byte aligned");
+    DGAL_TRY(maybe_validate(flags, a, ca, N, K, (cudaStream_t)stream));
+    DGAL_TRY(maybe_validate(flags, b, cb, M, K, (cudaStream_t)stream));
     return launch_pairwise(a, ca, N, b, cb, M, K, iou, nx, flags, (cudaStream_t)stream);
 }
 
@@ -238,6 +262,8 @@ dgal_status dgal_iou3d_paired(const float* p1, const uint8_t* c1, const float* z
         return fail(DGAL_ERR_INVALID_ARG, "nx and xflags must be both NULL or both set");
     if (xflags && !aligned(xflags, K == 4 ? 8 : 16))
         return fail(DGAL_ERR_ALIGNMENT, "xflags is not %d-byte aligned", K == 4 ? 8 : 16);
+    DGAL_TRY(maybe_validate(flags, p1, c1, n, K, (cudaStream_t)stream));
+    DGAL_TRY(maybe_validate(flags, p2, c2, n, K, (cudaStream_t)stream));
     return launch_paired3d_fwd(p1, c1, z1, p2, c2, z2, n, K, iou, nx, xflags, degen, flags, (cudaStream_t)stream);
 }
 
@@ -263,6 +289,8 @@ dgal_status dgal_iou3d_backward(const float* p1, const uint8_t* c1, const float*
         return fail(DGAL_ERR_INVALID_ARG, "nx and xflags must be both NULL or both set");
     if (xflags && !aligned(xflags, K == 4 ? 8 : 16))
         return fail(DGAL_ERR_ALIGNMENT, "xflags is not %d-byte aligned", K == 4 ? 8 : 16);
+    DGAL_TRY(maybe_validate(flags, p1, c1, n, K, (cudaStream_t)stream));
+    DGAL_TRY(maybe_validate(flags, p2, c2, n, K, (cudaStream_t)stream));
     return launch_paired3d_bwd(p1, c1, z1, p2, c2, z2, n, K, grad_iou, nx, xflags, grad_p1, grad_z1, grad_p2, grad_z2,
                                flags, (cudaStream_t)stream);
 }
@@ -356,6 +384,8 @@ dgal_status dgal_iou_loss(const float* p1, const uint8_t* c1, const float* p2, c
     if (!aligned(workspace, 16)) return fail(DGAL_ERR_ALIGNMENT, "workspace is not 16-byte aligned");
     if (ws_bytes < loss_workspace_bytes(n, K))
         return fail(DGAL_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", ws_bytes, loss_workspace_bytes(n, K));
+    DGAL_TRY(maybe_validate(flags, p1, c1, n, K, (cudaStream_t)stream));
+    DGAL_TRY(maybe_validate(flags, p2, c2, n, K, (cudaStream_t)stream));
     return launch_iou_loss(p1, c1, p2, c2, n, K, weight, scale, loss, iou, grad_p1, grad_p2, workspace, flags,
                            (cudaStream_t)stream);
 }
@@ -393,6 +423,8 @@ dgal_status dgal_iou3d_loss(const float* p1, const uint8_t* c1, const float* z1,
     if (!aligned(workspace, 16)) return fail(DGAL_ERR_ALIGNMENT, "workspace is not 16-byte aligned");
     if (ws_bytes < loss_workspace_bytes(n, K))
         return fail(DGAL_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", ws_bytes, loss_workspace_bytes(n, K));
+    DGAL_TRY(maybe_validate(flags, p1, c1, n, K, (cudaStream_t)stream));
+    DGAL_TRY(maybe_validate(flags, p2, c2, n, K, (cudaStream_t)stream));
     return launch_iou3d_loss(p1, c1, z1, p2, c2, z2, n, K, weight, scale, loss, iou, grad_p1, grad_z1, grad_p2, grad_z2,
                              workspace, flags, (cudaStream_t)stream);
 }

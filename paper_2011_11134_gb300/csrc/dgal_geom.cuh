@@ -64,6 +64,7 @@ constexpr uint32_t kDevOverflow = 0x2u;
 constexpr uint32_t kDevBadFlags = 0x4u;
 constexpr uint32_t kDevBadOffsets = 0x8u;
 constexpr uint32_t kDevTimeout = 0x10u;
+constexpr uint32_t kDevNotConvex = 0x20u;
 
 // flag bits of the C ABI
 constexpr uint32_t kFlagRefine = 0x1u;

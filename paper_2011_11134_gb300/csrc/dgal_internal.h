@@ -47,6 +47,9 @@ void set_paired_config(int K, PairedConfig c);
 // Launchers (no validation; called from the C ABI after checks).
 // n_shape: the batch size that picks the launch shape (default n; a chunk of
 // a larger batch passes the whole batch's size so that results match).
+// DGAL_VALIDATE / dgal_validate_polygons: the convexity and orientation check
+// of n polygons (geom_ops.cu); bad (nullable) receives 1 per failing polygon.
+dgal_status launch_validate(const float* p, const uint8_t* c, int64_t n, int K, uint8_t* bad, cudaStream_t s);
 dgal_status launch_paired_fwd(const float* p1, const uint8_t* c1, const float* p2, const uint8_t* c2, int64_t n,
                               int K, float* iou, uint8_t* nx, uint8_t* xflags, uint8_t* degen, uint32_t flags,
                               cudaStream_t s, int64_t n_shape = -1);

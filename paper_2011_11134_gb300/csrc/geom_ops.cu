@@ -185,6 +185,62 @@ k_line_intersect_bwd(const float* __restrict__ l1, const float* __restrict__ l2,
     }
 }
 
+// Input check of the DGAL_VALIDATE debug flag and dgal_validate_polygons:
+// polygon k (its first n_k vertices) is a strictly convex polygon in
+// counter-clockwise order exactly when every vertex lies strictly left of
+// every edge it is not an end of, orient(v_i, v_i+1, v_m) > 0.  That also
+// rejects clockwise order, reflex vertices, self-intersecting (star) outlines,
+// repeated and collinear vertices.  Each test is taken in FP32 about v_i and
+// trusted when its magnitude exceeds the FP32 error bound of the 2 x 2
+// determinant of rounded differences, 8u (|ex dy| + |ey dx|); below that
+// the FP64 value from the raw inputs decides (exact differences and products,
+// so its sign is exact).  One thread per polygon, at most K (K - 2) tests; a
+// count outside [3, K] is left to the other kernels (DGAL_DEV_BAD_COUNT).
+template <int K>
+__global__ void __launch_bounds__(kOpsThreads)
+k_validate(const float* __restrict__ p, const uint8_t* __restrict__ c, int64_t n, uint8_t* __restrict__ bad,
+           uint32_t* status) {
+    uint32_t err = 0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const float* pk = p + k * 2 * K;
+        float x[K], y[K];
+        load_poly<K>(pk, x, y);
+        const int m = c ? (int)c[k] : K;
+        bool ok = true;
+        if (m >= 3 && m <= K) {
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                if (i >= m) break;
+                const int i1 = (i + 1 < m) ? i + 1 : 0;
+                const float ex = sel<K>(x, (uint32_t)i1) - x[i], ey = sel<K>(y, (uint32_t)i1) - y[i];
+#pragma unroll
+                for (int v = 0; v < K; ++v) {
+                    if (v >= m || v == i || v == i1) continue;
+                    const float dx = x[v] - x[i], dy = y[v] - y[i];
+                    const float a = ex * dy, b = ey * dx;
+                    const float o = a - b;
+                    const float bound = 8.f * 5.9604645e-8f * (fabsf(a) + fabsf(b));
+                    bool left = o > 0.f;
+                    if (!(fabsf(o) > bound)) left = orient_raw(pk, i, i1, pk, v) > 0.0;
+                    ok = ok && left;
+                }
+            }
+        }
+        if (bad) bad[k] = ok ? 0 : 1;
+        if (!ok) err |= kDevNotConvex;
+    }
+    if (err) atomicOr(status, err);
+}
+
+dgal_status launch_validate(const float* p, const uint8_t* c, int64_t n, int K, uint8_t* bad, cudaStream_t s) {
+    uint32_t* st = device_status_ptr();
+    if (!st) return fail(DGAL_ERR_CUDA, "device status word unavailable");
+    if (n <= 0) return DGAL_OK;
+    if (K == 4) k_validate<4><<<ops_grid(n), kOpsThreads, 0, s>>>(p, c, n, bad, st);
+    else k_validate<8><<<ops_grid(n), kOpsThreads, 0, s>>>(p, c, n, bad, st);
+    return check_launch("validate polygons");
+}
+
 } // namespace dgal
 
 using namespace dgal;
