@@ -423,3 +423,33 @@ def test_fwd_bwd_one_call(dg, orc, K, n):
     z = torch.zeros((0, K, 2), device="cuda")
     e = dg.dgal_iou_fwd_bwd(z, z, torch.zeros(0, device="cuda"))
     assert e[0].numel() == 0
+
+
+def test_forward_backward_in_cuda_graph(dg):
+    """The forward and the backward (launched as a programmatic dependent of
+    the forward) captured in one CUDA graph and replayed give the eager
+    calls' bytes."""
+    import torch
+
+    d = W.loss_pairs_1m(seed=4, n=50_000)
+    p1, p2 = dev(d["p1"]), dev(d["p2"])
+    grad = torch.rand(p1.shape[0], device="cuda")
+    iou, nx, xf, _ = dg.dgal_iou_paired(p1, p2)
+    g1, g2 = dg.dgal_iou_backward(p1, p2, grad, nx, xf)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        dg.dgal_iou_paired(p1, p2)  # warm call on the capture stream
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            giou, gnx, gxf, _ = dg.dgal_iou_paired(p1, p2)
+            h1, h2 = dg.dgal_iou_backward(p1, p2, grad, gnx, gxf)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(giou, iou) and torch.equal(gnx, nx) and torch.equal(gxf, xf)
+    assert torch.equal(h1, g1) and torch.equal(h2, g2)
+    assert dg.dgal_get_device_status() == 0
