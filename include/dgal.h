@@ -82,9 +82,10 @@ typedef enum {
                                  contract, paper Sec. III) with dgal_validate_polygons'
                                  kernel; a polygon that fails sets DGAL_DEV_NOT_CONVEX, and
                                  the results for its pairs are undefined.  Applies to the
-                                 paired, pairwise, 3D and loss calls (not to the ragged batch,
-                                 whose polygon counts live on the device: check its arrays with
-                                 dgal_validate_polygons).  Costs one extra pass over the polygons. */
+                                 device-memory paired, pairwise, 3D and loss calls; not to the
+                                 ragged batch (its polygon counts live on the device) nor to the
+                                 host-buffer call: check those arrays with
+                                 dgal_validate_polygons.  Costs one extra pass over the polygons. */
 #define DGAL_TEST_EXPIRE_WAIT 0x100u /* dgal_nms_rotated, for tests of the failure path: the
                                         greedy pass takes its wait-expiry path (DGAL_DEV_TIMEOUT,
                                         results incomplete) at its second block, once that block's
