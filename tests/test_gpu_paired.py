@@ -453,3 +453,30 @@ def test_forward_backward_in_cuda_graph(dg):
     assert torch.equal(giou, iou) and torch.equal(gnx, nx) and torch.equal(gxf, xf)
     assert torch.equal(h1, g1) and torch.equal(h2, g2)
     assert dg.dgal_get_device_status() == 0
+
+
+def test_k4_constructed_degenerate(dg, orc):
+    """Quadrilaterals and triangles in K = 4 storage with constructed
+    near-degenerate partners (identical, shared edge, touching vertex,
+    collinear edge 1e-6 off): the one-thread K = 4 kernels, FP64 refinement
+    on, where exact zero orientations take their sign from the infinitesimal
+    translation of P2.  IoU within 1e-5 on every pair, flags and gradients as
+    the oracle's on generic pairs, and bounded gradients on flagged ones."""
+    import torch
+
+    d = W.convex_pairs_4m(seed=23, n=40_000, K=4, degenerate_frac=0.5)
+    kind = d["kind"]
+    assert ((kind == 2) | (kind == 3)).sum() > 5000
+    p1, p2, c1, c2 = dev(d["p1"]), dev(d["p2"]), dev(d["c1"]), dev(d["c2"])
+    iou, nx, xf, degen = dg.dgal_iou_paired(p1, p2, c1, c2, with_degen=True)
+    ref = orc.iou_paired(d["p1"], d["p2"], d["c1"], d["c2"], threads=THREADS)
+    gen = check_forward(host(iou), host(nx), host(xf), host(degen), ref, "K=4 degenerate")
+    assert (host(degen)[kind > 0] & 1).all(), "every constructed degenerate pair is flagged"
+    grad = torch.ones(p1.shape[0], device="cuda")
+    g1, g2 = dg.dgal_iou_backward(p1, p2, grad, nx, xf, c1, c2)
+    o1, o2 = orc.iou_backward_paired(d["p1"], d["p2"], np.ones(p1.shape[0]), ref["nx"], ref["xflags"], d["c1"],
+                                     d["c2"], threads=THREADS)
+    rel = grad_rel_err(host(g1), host(g2), o1, o2, gen)
+    assert rel.max() <= GRAD_RTOL, f"K=4 grads: max rel err {rel.max():.3e}"
+    check_flagged_grads(host(g1), host(g2), d["p1"], d["p2"], d["c1"], d["c2"], ref, ~gen, label="K=4 degenerate")
+    assert dg.dgal_get_device_status() == 0
