@@ -813,7 +813,8 @@ def paired_measure(args, workload, n_pairs, with_e2e, with_cpu, use_graph=False)
                 "step": {"ms": total_ms / args.steps, "alg_bytes_per_pair": fwd_bytes + bwd_bytes,
                          "frac": (fwd_bytes + bwd_bytes) * n / (total_ms / args.steps * 1e-3) / 1e9 / hbm}}
     if K == 8:
-        # 2.7 kflop per pair (the FP32 model of the survey) against the derived FP32 peak
+        # 2.7 kflop per pair (an FP32 operation count of the clip: 64 crossings and 128
+        # orientations forward, the shape derivative backward) against the derived FP32 peak
         roofline["fp32"] = {"achieved_tflops": 2.7e3 * n / (total_ms / args.steps * 1e-3) / 1e12,
                             "peak_tflops": FP32_PEAK_TFLOPS,
                             "frac": 2.7e3 * n / (total_ms / args.steps * 1e-3) / 1e12 / FP32_PEAK_TFLOPS}
