@@ -36,8 +36,11 @@ constexpr int kMaxTileRows = 32;
 constexpr int kTileRows = 32;
 
 // Blocks per SM the K = 4 tile kernel is compiled for (registers <= 65536 /
-// (128 x this)); K = 8 holds its polygons in registers and takes 1.
-constexpr int kPwMinBlocks = 5;
+// (128 x this)); K = 8 holds its polygons in registers and takes 1.  At 7
+// (72 registers, a few spills) the 1008 tiles of a 2000 x 2000 matrix fit in
+// one wave of 152 x 7 blocks: 21.8 -> 19.8 us against 5; 6 and 8 measured
+// 22.4 and 19.9 us.
+constexpr int kPwMinBlocks = 7;
 
 // One N x M matrix: one block per tile of kTileRows x kPwThreads entries
 // (pw_tile).  Without a loop over tiles the kernel holds fewer registers, so
